@@ -1,0 +1,407 @@
+"""FP64 CPU oracle of the fractional-ADE lattice Boltzmann scheme.
+
+TEST INFRASTRUCTURE ONLY.  This module is imported by the tests, by
+``__graft_entry__.smoke()`` and by the CPU-baseline leg of ``bench.py``;
+the product path (the CUDA library and its Python binding) never imports,
+calls or links it, and it imports nothing from the product.
+
+It is a plain, slow, step-by-step FP64 restatement of the scheme of
+Cartalade, Younsi & Neel, "Multiple-Relaxation-Time Lattice Boltzmann scheme
+for Fractional Advection-Diffusion Equation" (arXiv:1706.09161), written with
+plain PyTorch CPU ops so that the discrete adjoint is available through
+autograd.  Every function cites the section / equation it follows:
+
+* lattices D2Q5 / D3Q7, weights, e^2 .......... Section 2.1, Eq. (weights_c), Fig. 1 caption
+* trapezoidal product-integration weights ..... Section 2.4, Eqs. (1Dminus_discret), (c+), (c-)
+* per-axis fractional term F_mu ............... Section 2.4, Eq. (XXminus_discret); Eq. (M2_FADE_3D)
+* equilibrium ................................. Section 2.2, Eqs. (Feq), (CoeffA_FADE3D)
+* BGK relaxation time from D .................. Section 2.2, Eq. (Diffusion_Coefficient_3D)
+* diagonal D under BGK through h_mu ........... Section 2.2 (end)
+* MRT matrices M, Lambda^-1, D <-> lambda ...... Section 2.3, Eqs. (MRT-Coll), (MatrixD2), (MatrixS), (D_ab)
+* streaming (push) ............................ Section 2.2, Eqs. (LBE_Ket), (Def_Translation)
+* Dirichlet walls ............................. Section 2.5, Eq. (Dirichlet_BC)
+* time loop ................................... Section 2.5, Algorithm 1
+
+Readings taken where the paper is silent (the same conventions the CUDA path
+implements, each written out independently):
+
+* grid = nodes per axis including both wall nodes, n = 0..N, N = grid-1;
+* the diagonal l = n of both weight matrices is 1, also at n = 0 (W+) and
+  n = N (W-), where the l = 0 / l = N end formula would be undefined;
+* a wall node with k unknown incoming populations (edges, corners) gives each
+  of them (C_wall - sum of the known populations) / k;
+* the initial populations are the equilibrium of the initial concentration;
+* BGK with a diagonal, non-spherical D: lambda is set by the largest D_mumu
+  and h_mu = D_mumu / max(D) multiplies g_mu;
+* MRT: ``s_free`` are relaxation *rates* 1/lambda_k of the free moments;
+  lambda_0 (conserved moment) is set to 1, it has no effect.
+
+Parity of every function here is pinned by the tests in
+``tests/test_oracle_pins.py`` (closed forms, invariants, special cases).
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Sequence, Tuple
+
+import torch
+
+DT = torch.float64
+
+
+# --------------------------------------------------------------------------- lattice
+
+def lattice(d: int) -> Tuple[torch.Tensor, torch.Tensor, float]:
+    """Velocity array e (d x Q, columns e_i), weights w (Q) and e^2.
+
+    Section 2.1: D3Q7 has e_0 = 0, e_{1,2} = +-b_1, e_{3,4} = +-b_2,
+    e_{5,6} = +-b_3, w_0 = 1/4, w_i = 1/8, e^2 = 1/4; D2Q5 drops e_5, e_6 and
+    has w_0 = 1/3, w_i = 1/6, e^2 = 1/3 (Fig. 1 caption).
+    """
+    if d == 2:
+        cols = [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)]
+        w = [1 / 3] + [1 / 6] * 4
+        e2 = 1 / 3
+    elif d == 3:
+        cols = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+        w = [1 / 4] + [1 / 8] * 6
+        e2 = 1 / 4
+    else:
+        raise ValueError("d must be 2 or 3")
+    e = torch.tensor(cols, dtype=DT).T.contiguous()
+    return e, torch.tensor(w, dtype=DT), e2
+
+
+def moment_matrix(d: int) -> torch.Tensor:
+    """MRT change of basis M, Eq. (MatrixD2) (D3Q7 left, D2Q5 right)."""
+    if d == 3:
+        rows = [[1, 1, 1, 1, 1, 1, 1],
+                [0, 1, -1, 0, 0, 0, 0],
+                [0, 0, 0, 1, -1, 0, 0],
+                [0, 0, 0, 0, 0, 1, -1],
+                [6, -1, -1, -1, -1, -1, -1],
+                [0, 2, 2, -1, -1, -1, -1],
+                [0, 0, 0, 1, 1, -1, -1]]
+    else:
+        rows = [[1, 1, 1, 1, 1],
+                [0, 1, -1, 0, 0],
+                [0, 0, 0, 1, -1],
+                [4, -1, -1, -1, -1],
+                [0, 1, 1, -1, -1]]
+    return torch.tensor(rows, dtype=DT)
+
+
+# --------------------------------------------------------------------------- discrete fractional integrals
+
+def _as_t(x) -> torch.Tensor:
+    return x if isinstance(x, torch.Tensor) else torch.tensor(float(x), dtype=DT)
+
+
+def weight_matrices(gamma, N: int) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Coefficient matrices W+[n, l] = c+_{ln}(gamma) (l <= n) and W-[n, l] = c-_{ln}(gamma, N) (l >= n).
+
+    Eqs. (c+) and (c-), Section 2.4, for nodes n, l = 0..N:
+      c+_{ln} = (1+g) n^g - n^(g+1) + (n-1)^(g+1)           l = 0
+              = (n-l+1)^(g+1) - 2 (n-l)^(g+1) + (n-l-1)^(g+1)  0 < l < n
+              = 1                                            l = n
+      c-_{ln} = (1+g) (N-n)^g - (N-n)^(g+1) + (N-n-1)^(g+1)  l = N
+              = (l-n+1)^(g+1) - 2 (l-n)^(g+1) + (l-n-1)^(g+1)  n < l < N
+              = 1                                            l = n
+    The l = n rule takes precedence where two cases meet (n = 0 in c+, n = N in c-).
+    ``gamma`` may be a tensor that requires grad.
+    """
+    g = _as_t(gamma)
+    s = g + 1.0
+    k = torch.arange(0, N + 2, dtype=DT)
+    kc = torch.clamp(k, min=1.0)                      # keep pow's gradient finite at k = 0
+    pw = torch.where(k > 0, torch.pow(kc, s), torch.zeros((), dtype=DT))   # k^(g+1), 0^(g+1) = 0
+    # interior second differences a[k] = (k+1)^s - 2 k^s + (k-1)^s, k >= 1 (a[0] unused)
+    a = torch.zeros(N + 1, dtype=DT)
+    if N >= 1:
+        a = torch.cat([torch.zeros(1, dtype=DT), pw[2:N + 2] - 2.0 * pw[1:N + 1] + pw[0:N]])
+    # end coefficient b[m] = (1+g) m^g - m^(g+1) + (m-1)^(g+1), m >= 1 (b[0] unused)
+    m = torch.arange(0, N + 1, dtype=DT)
+    mc = torch.clamp(m, min=1.0)
+    pw_m = pw[0:N + 1]                                       # m^(g+1)
+    pw_m1 = torch.cat([torch.zeros(1, dtype=DT), pw[0:N]])   # (m-1)^(g+1)
+    b = torch.where(m > 0, (1.0 + g) * torch.pow(mc, g) - pw_m + pw_m1, torch.zeros((), dtype=DT))
+
+    n_idx = torch.arange(N + 1).view(-1, 1).expand(N + 1, N + 1)
+    l_idx = torch.arange(N + 1).view(1, -1).expand(N + 1, N + 1)
+    one = torch.ones((), dtype=DT)
+    zero = torch.zeros((), dtype=DT)
+
+    a_lo = a[(n_idx - l_idx).clamp(min=0)]
+    b_n = b[n_idx]
+    Wp = torch.where(l_idx == n_idx, one,
+                     torch.where((l_idx == 0) & (n_idx > 0), b_n,
+                                 torch.where((l_idx > 0) & (l_idx < n_idx), a_lo, zero)))
+    a_up = a[(l_idx - n_idx).clamp(min=0)]
+    b_Nn = b[(N - n_idx).clamp(min=0)]
+    Wm = torch.where(l_idx == n_idx, one,
+                     torch.where((l_idx == N) & (n_idx < N), b_Nn,
+                                 torch.where((l_idx > n_idx) & (l_idx < N), a_up, zero)))
+    return Wp, Wm
+
+
+def frac_matrix(alpha, p, g, N: int, dx: float = 1.0) -> torch.Tensor:
+    """K such that (K c)[n] = p I+^gamma(g c)(n dx) + (1-p) I-^gamma(g c)(n dx), gamma = 2 - alpha.
+
+    Eq. (1Dminus_discret) / (XXminus_discret): I+-^gamma f(n dx) ~ dx^gamma / Gamma(2+gamma)
+    * sum_l f(l dx) c+-_{ln}; the fractional term of Eq. (CoeffA_FADE3D) weights the two
+    one-sided integrals of g C by p and 1 - p.  ``alpha``, ``p``, ``g`` may be tensors.
+    """
+    gamma = 2.0 - _as_t(alpha)
+    Wp, Wm = weight_matrices(gamma, N)
+    scale = _as_t(g) * torch.pow(torch.tensor(float(dx), dtype=DT), gamma) / torch.exp(torch.lgamma(2.0 + gamma))
+    p = _as_t(p)
+    return scale * (p * Wp + (1.0 - p) * Wm)
+
+
+def apply_along_axis(K: torch.Tensor, C: torch.Tensor, mu: int) -> torch.Tensor:
+    """(K applied along axis mu)[.., n, ..] = sum_l K[n, l] C[.., l, ..]  (Eq. XXminus_discret).
+
+    Axis mu = 0 is x (last array dim), mu = 1 is y, mu = 2 is z.
+    """
+    dim = C.dim() - 1 - mu
+    out = torch.tensordot(K, C, dims=([1], [dim]))   # axis moved to front
+    return torch.movedim(out, 0, dim)
+
+
+# --------------------------------------------------------------------------- problem -> operators
+
+class Operators:
+    """All per-problem quantities of Algorithm 1's initialisation (items 1-3), as FP64 tensors.
+
+    Differentiable w.r.t. alpha, p, D (diagonal entries or full tensor) and u when they are
+    passed as tensors with requires_grad.
+    """
+
+    def __init__(self, pb, alpha=None, p=None, D=None, u=None, g=None):
+        self.d = d = pb.d
+        self.grid = tuple(int(n) for n in pb.grid)
+        self.collision = pb.collision
+        self.dx, self.dt = float(pb.dx), float(pb.dt)
+        self.C_wall = float(pb.C_wall)
+        self.e, self.w, self.e2 = lattice(d)
+        self.Q = self.e.shape[1]
+        self.alpha = _vec(alpha if alpha is not None else pb.alpha, d)
+        self.p = _vec(p if p is not None else pb.p, d)
+        self.g = _vec(g if g is not None else pb.g, d)
+        self.u = _vec(u if u is not None else pb.u, d)
+        if D is None:
+            Dm = torch.tensor(pb.D, dtype=DT)
+        else:
+            Dm = _as_t(D) if isinstance(D, torch.Tensor) else torch.tensor(D, dtype=DT)
+            if Dm.dim() == 1:
+                Dm = torch.diag(Dm)
+        self.D = Dm
+        self.h = torch.ones(d, dtype=DT)
+        self.Omega = self._collision_matrix(pb)
+        self.K = [frac_matrix(self.alpha[mu], self.p[mu], self.g[mu] * self.h[mu], self.grid[mu] - 1, self.dx)
+                  for mu in range(d)]
+
+    def _collision_matrix(self, pb) -> torch.Tensor:
+        """Omega such that the collision is f - Omega (f - feq).
+
+        BGK: Omega = I / lambda with D = e^2 (lambda - 1/2) dx^2 / dt, Eq. (Diffusion_Coefficient_3D).
+        MRT: Omega = M^-1 Lambda M, Eq. (MRT-Coll), with Lambda^-1 = diag(lambda_0, lambdabar,
+        lambda_{d+1..Q-1}) (Eq. MatrixS) and lambdabar = D dt / (e^2 dx^2) + Id/2 (Eq. D_ab).
+        """
+        d, Q, e2 = self.d, self.Q, self.e2
+        ratio = self.dt / (self.dx * self.dx)
+        if self.collision == "bgk":
+            Dd = torch.diagonal(self.D)
+            if not bool(torch.all(self.D == torch.diag(Dd))):
+                raise ValueError("BGK needs a diagonal D")
+            Dmax = torch.max(Dd)
+            lam = Dmax * ratio / e2 + 0.5
+            self.h = Dd / Dmax                       # diagonal non-spherical D (end of Section 2.2)
+            self.lam = lam
+            return torch.eye(Q, dtype=DT) / lam
+        if self.collision != "mrt":
+            raise ValueError("collision must be 'bgk' or 'mrt'")
+        s_free = list(pb.s_free)
+        if len(s_free) != Q - d - 1:
+            raise ValueError("MRT needs Q-d-1 free rates")
+        lam_inv = torch.zeros(Q, Q, dtype=DT)
+        lam_inv[0, 0] = 1.0
+        lam_inv[1:d + 1, 1:d + 1] = self.D * ratio / e2 + 0.5 * torch.eye(d, dtype=DT)
+        for k, s in enumerate(s_free):
+            lam_inv[d + 1 + k, d + 1 + k] = 1.0 / float(s)
+        Lam = torch.linalg.inv(lam_inv)
+        M = moment_matrix(d)
+        return torch.linalg.inv(M) @ Lam @ M
+
+
+def _vec(x, d) -> torch.Tensor:
+    if isinstance(x, torch.Tensor):
+        return x.to(DT).reshape(d)
+    return torch.tensor([float(v) for v in x], dtype=DT)
+
+
+# --------------------------------------------------------------------------- the time step
+
+def fractional_terms(ops: Operators, C: torch.Tensor) -> List[torch.Tensor]:
+    """F_mu = p_mu I+^{2-alpha_mu}(g_mu C) + (1-p_mu) I-^{2-alpha_mu}(g_mu C), Algorithm 1 loop item 1."""
+    return [apply_along_axis(ops.K[mu], C, mu) for mu in range(ops.d)]
+
+
+def equilibrium(ops: Operators, C: torch.Tensor, F: Sequence[torch.Tensor]) -> torch.Tensor:
+    """|feq> = |A> + (C/e^2)(dt/dx) u_mu |e_mu w>, Eqs. (Feq) and (CoeffA_FADE3D).
+
+    A_0 = C - w_0 sum_mu F_mu,  A_{2mu-1} = A_{2mu} = w_i F_mu.
+    """
+    Q, d = ops.Q, ops.d
+    sumF = sum(F)
+    A = [C - ops.w[0] * sumF]
+    for mu in range(d):
+        A.append(ops.w[2 * mu + 1] * F[mu])
+        A.append(ops.w[2 * mu + 2] * F[mu])
+    adv_scale = (ops.dt / ops.dx) / ops.e2
+    feq = []
+    for i in range(Q):
+        ue = sum(ops.u[mu] * ops.e[mu, i] for mu in range(d))
+        feq.append(A[i] + adv_scale * C * ue * ops.w[i])
+    return torch.stack(feq)
+
+
+def collide(ops: Operators, f: torch.Tensor, feq: torch.Tensor) -> torch.Tensor:
+    """Right-hand side of Eq. (LBE_Ket) / (MRT-Coll) without source: f - Omega (f - feq)."""
+    return f - torch.einsum("ij,j...->i...", ops.Omega, f - feq)
+
+
+def _shift(x: torch.Tensor, dim: int, s: int) -> torch.Tensor:
+    """y[.., k + s, ..] = x[.., k, ..]; entries with no source node are 0."""
+    y = torch.zeros_like(x)
+    n = x.shape[dim]
+    src = [slice(None)] * x.dim()
+    dst = [slice(None)] * x.dim()
+    if s > 0:
+        src[dim] = slice(0, n - s)
+        dst[dim] = slice(s, n)
+    else:
+        src[dim] = slice(-s, n)
+        dst[dim] = slice(0, n + s)
+    y[tuple(dst)] = x[tuple(src)]
+    return y
+
+
+def _axis_of(ops: "Operators", i: int) -> Tuple[int, int]:
+    """(mu, sign) of the moving velocity e_i = sign * b_mu."""
+    col = ops.e[:, i]
+    mu = int(torch.nonzero(col).flatten()[0])
+    return mu, int(col[mu])
+
+
+def unknown_mask(ops: "Operators") -> torch.Tensor:
+    """unknown[i, x] is True where x - e_i lies outside the domain (Section 2.5)."""
+    shape = tuple(reversed(ops.grid))
+    m = torch.zeros((ops.Q,) + shape, dtype=torch.bool)
+    for i in range(1, ops.Q):
+        mu, s = _axis_of(ops, i)
+        dim = len(shape) - 1 - mu
+        idx = [slice(None)] * len(shape)
+        idx[dim] = 0 if s > 0 else shape[dim] - 1
+        m[(i,) + tuple(idx)] = True
+    return m
+
+
+def stream(ops: Operators, fstar: torch.Tensor) -> torch.Tensor:
+    """Push translation of Eq. (Def_Translation): f_i(x + e_i dx, t+dt) = f*_i(x, t).
+
+    Populations that leave the domain are dropped; populations whose source
+    node lies outside are set to 0 here and assigned by ``dirichlet``.
+    """
+    out = [fstar[0]]
+    for i in range(1, ops.Q):
+        mu, s = _axis_of(ops, i)
+        out.append(_shift(fstar[i], fstar.dim() - 2 - mu, s))
+    return torch.stack(out)
+
+
+def dirichlet(ops: Operators, f: torch.Tensor) -> torch.Tensor:
+    """Eq. (Dirichlet_BC): unknown inward populations f_b = C0 - sum_{i != b} f_i.
+
+    With k > 1 unknowns at a node (edges, corners) each gets (C0 - sum of known)/k.
+    """
+    unknown = unknown_mask(ops)
+    known_sum = torch.where(unknown, torch.zeros((), dtype=DT), f).sum(0)
+    k = unknown.sum(0).to(DT)
+    fill = (ops.C_wall - known_sum) / torch.clamp(k, min=1.0)
+    return torch.where(unknown, fill.unsqueeze(0).expand_as(f), f)
+
+
+def concentration(f: torch.Tensor) -> torch.Tensor:
+    """C = <1|f>, Algorithm 1 loop item 5."""
+    return f.sum(0)
+
+
+def init_populations(ops: Operators, C0: torch.Tensor) -> torch.Tensor:
+    """Initial populations: the equilibrium of the initial concentration."""
+    return equilibrium(ops, C0, fractional_terms(ops, C0))
+
+
+def step(ops: Operators, f: torch.Tensor) -> torch.Tensor:
+    """One pass of Algorithm 1's time loop (items 1-5) from populations f(t) to f(t+dt)."""
+    C = concentration(f)
+    F = fractional_terms(ops, C)                 # item 1
+    feq = equilibrium(ops, C, F)                 # item 2
+    fstar = collide(ops, f, feq)                 # item 2 (right-hand side)
+    fnew = stream(ops, fstar)                    # item 3
+    fnew = dirichlet(ops, fnew)                  # item 4
+    return fnew                                  # item 5: C = concentration(fnew)
+
+
+def run(pb, C0, nsteps: int, ops: Operators = None) -> torch.Tensor:
+    """Populations after ``nsteps`` steps from f(0) = feq(C0)."""
+    ops = ops or Operators(pb)
+    f = init_populations(ops, _field(C0))
+    for _ in range(nsteps):
+        f = step(ops, f)
+    return f
+
+
+def run_C(pb, C0, nsteps: int) -> torch.Tensor:
+    return concentration(run(pb, C0, nsteps))
+
+
+def _field(C0) -> torch.Tensor:
+    if isinstance(C0, torch.Tensor):
+        return C0.to(DT)
+    return torch.as_tensor(C0, dtype=DT)
+
+
+# --------------------------------------------------------------------------- inverse problem (adjoint)
+
+def snapshot_loss(pb, C0, snap_steps: Sequence[int], obs: torch.Tensor, alpha, p, Ddiag, u) -> torch.Tensor:
+    """L = sum_k sum_x (C(x, t_k) - obs_k(x))^2 for the scheme run with (alpha, p, diag D, u).
+
+    The gradient of this FP64 loss by autograd is the exact discrete adjoint of the
+    scheme (every stage above is differentiable in the parameters).
+    """
+    ops = Operators(pb, alpha=alpha, p=p, D=torch.diag(Ddiag), u=u)
+    f = init_populations(ops, _field(C0))
+    loss = torch.zeros((), dtype=DT)
+    t = 0
+    for k, ts in enumerate(snap_steps):
+        while t < ts:
+            f = step(ops, f)
+            t += 1
+        r = concentration(f) - obs[k]
+        loss = loss + (r * r).sum()
+    return loss
+
+
+def loss_and_grad(pb, C0, snap_steps, obs) -> Tuple[float, torch.Tensor]:
+    """Loss and its gradient w.r.t. theta = [alpha_1..d, p_1..d, D_11..D_dd, u_1..d] (FP64 autograd)."""
+    d = pb.d
+    alpha = torch.tensor(pb.alpha, dtype=DT, requires_grad=True)
+    p = torch.tensor(pb.p, dtype=DT, requires_grad=True)
+    Dd = torch.tensor([pb.D[i][i] for i in range(d)], dtype=DT, requires_grad=True)
+    u = torch.tensor(pb.u, dtype=DT, requires_grad=True)
+    obs_t = torch.as_tensor(obs, dtype=DT)
+    loss = snapshot_loss(pb, C0, snap_steps, obs_t, alpha, p, Dd, u)
+    loss.backward()
+    grad = torch.cat([alpha.grad, p.grad, Dd.grad, u.grad])
+    return float(loss.detach()), grad
