@@ -1,0 +1,356 @@
+"""Benchmark: MLUPS of the fractional-ADE lattice Boltzmann time step on GB300.
+
+One benchmark step = one full run of the workload: reset to the initial
+condition (untimed), then all of its lattice time steps (timed), each time step
+being the whole hot path: fractional terms along every axis, equilibrium,
+collision, streaming, Dirichlet walls and new concentration.  L2 is flushed
+(a 512 MiB write) before every benchmark step; within a run the state stays
+resident, as in any real run.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload mrt_aniso_512] [--precision P]
+
+N > 1 runs under torchrun, one independent replica per GPU (the workload does
+not shard), timing is the max over ranks and ``value`` counts every rank's
+lattice updates.  ``--impl reference`` times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS per GB300 (full step incl. fractional operator)"
+UNIT = "MLUPS"
+
+WORKLOADS = {
+    "mrt_aniso_512": dict(
+        desc="2-D anisotropic fractional ADE, D2Q5 MRT, 512x512, alpha=(1.5,1.8), p=(0.3,0.7), g=(1,1), "
+             "D=diag(2e-3,5e-4), u=(0.05,0.02) lattice units, free rates U[0.8,1.9] seed 2, "
+             "Dirichlet C=0, 5x5 unit-mass pulse, 5000 steps",
+        default_precision="bf16split"),
+    "fp64_bgk_64": dict(desc="2-D D2Q5 BGK 64x64 FP64, alpha=1.7, 200 steps", default_precision="fp64"),
+    "mrt3d_256": dict(desc="3-D D3Q7 MRT 256^3, alpha=(1.6,1.6,1.9), 2000 steps", default_precision="tf32split"),
+}
+
+# measured peaks (driver-written), with the profiling recipe's fallback
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+SMS = 152
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def make_workload(name):
+    from paper_1706_09161_gb300 import workloads as W
+    return getattr(W, name)()
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle legs
+
+def oracle_sample(pb, C0, nsteps):
+    """Run the FP64 CPU oracle for nsteps; returns (seconds, C, threads)."""
+    import torch
+    from oracle import lbm_oracle as O
+    ops = O.Operators(pb)
+    f = O.init_populations(ops, torch.tensor(C0))
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        f = O.step(ops, f)
+    dt = time.perf_counter() - t0
+    return dt, O.concentration(f).numpy(), torch.get_num_threads()
+
+
+# --------------------------------------------------------------------------- main
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    pb, C0, nlbm = make_workload(args.workload)
+    sample = max(1, min(nlbm, args.ref_sample))
+    for _ in range(args.warmup):
+        oracle_sample(pb, C0, 1)
+    times = []
+    threads = 1
+    for _ in range(args.steps):
+        dt, _, threads = oracle_sample(pb, C0, sample)
+        times.append(dt)
+    total = sum(times)
+    mlups = pb.nodes * sample * args.steps / total / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+                       "lbm_steps_per_bench_step": sample, "note": "bounded sample of the workload's run"},
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} lattice steps of {args.workload} per bench step"},
+            "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, or None if the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh).get(kernel_key)
+    if not rec:
+        return None
+    if rec.get("source_sha") != source_sha(rec["sources"]):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="mrt_aniso_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--ref-sample", type=int, default=40, help="lattice steps per reference-arm bench step")
+    ap.add_argument("--cpu-sample", type=int, default=800, help="lattice steps of the cpu_baseline leg")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1706_09161_gb300 import build as _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1706_09161_gb300 import lbm
+
+    pb, C0, nlbm = make_workload(args.workload)
+    precision = args.precision or WORKLOADS[args.workload]["default_precision"]
+    lat = lbm.Lattice(pb, C0, precision)
+    stream = torch.cuda.ExternalStream(lat.stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_run():
+        lat.reset()
+        flush.add_(1.0)  # L2 flush on torch's stream
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lat.step(nlbm)
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    for _ in range(args.warmup):
+        one_run()
+    lat.sync()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_ms = []
+    for _ in range(args.steps):
+        t_ms.append(one_run())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    rc = lbm.lbm_sync(lat.h)
+    total_ms = sum(t_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * pb.nodes * nlbm * args.steps / (total_ms * 1e-3) / 1e6
+    gpu_launches = args.steps * nlbm * lat.launches_per_step
+
+    # ---- end to end through the C ABI with pinned host buffers
+    C0_pin = torch.from_numpy(np.ascontiguousarray(C0)).pin_memory()
+    out_pin = torch.empty(C0_pin.shape, dtype=torch.float64).pin_memory()
+    C0_np, out_np = C0_pin.numpy(), out_pin.numpy()
+    e2e_s = []
+    for k in range(args.steps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.set_C(C0_np)
+        lat.step(nlbm)
+        lbm.lbm_read_C(lat.h, out_np)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_val = world * pb.nodes * nlbm * args.steps / sum(e2e_s) / 1e6
+    if dist is not None:
+        t = torch.tensor([sum(e2e_s)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * pb.nodes * nlbm * args.steps / float(t.item()) / 1e6
+
+    # ---- dominant kernel, timed live with events on the library stream
+    nprof = min(nlbm, 200)
+    lat.reset()
+    ms_frac, ms_cs = lat.profile(nprof)
+    d, Q = pb.d, 2 * pb.d + 1
+    side_sum = sum(pb.grid)
+    peaks, peak_src = load_peaks()
+    elem = 8 if precision == "fp64" else 4
+    if ms_frac >= ms_cs:
+        flops = 2.0 * pb.nodes * side_sum  # sum over axes of 2*side per node
+        dur = ms_frac / nprof * 1e-3
+        achieved = flops / dur / 1e12
+        if precision in ("bf16split", "tf32split"):
+            bound = "tensor"
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            if precision == "tf32split":
+                peak = peak / 2.0  # nominal tf32/bf16 ratio
+        else:
+            bound = "alu"
+            if precision == "fp32":
+                # FP32 FMA lanes x 2 flops x max SM clock
+                peak = SMS * FP32_LANES_PER_SM * 2.0 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            else:
+                peak = FP64_NOMINAL_TFLOPS
+        roof = {"kernel": "fractional_operator", "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("fractional_operator"),
+                "algorithmic_per_launch": flops, "launch_ms": dur * 1e3, "peak_source": peak_src}
+    else:
+        bytes_ = float(pb.nodes) * (2 * Q * elem + d * elem + elem)
+        dur = ms_cs / nprof * 1e-3
+        achieved = bytes_ / dur / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "collide_stream", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_for("collide_stream"),
+                "algorithmic_per_launch": bytes_, "launch_ms": dur * 1e3, "peak_source": peak_src}
+    roof["other_kernel_ms"] = {"fractional_operator": ms_frac / nprof, "collide_stream": ms_cs / nprof}
+
+    # ---- CPU baseline (oracle) and accuracy against it, rank 0 at N = 1 only
+    cpu = None
+    accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns = min(nlbm, args.cpu_sample)
+        dt, C_ref, threads = oracle_sample(pb, C0, ns)
+        cpu = {"value": pb.nodes * ns / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {ns} of {nlbm} lattice steps of {args.workload} (FP64, torch CPU)"}
+        lat.reset()
+        lat.step(ns)
+        C_gpu = lat.C()
+        accuracy = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(C_gpu - C_ref) / np.linalg.norm(C_ref)),
+                    "lattice_steps": ns}
+
+    lat.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "bf16split": "f32+bf16x3", "tf32split": "f32+tf32x3"}[precision],
+                "data": "synthetic",
+                "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+                           "precision": precision, "lattice_steps_per_bench_step": nlbm,
+                           "nodes": pb.nodes, "parallelism": f"replicas x{world}",
+                           "l2": "flushed (512 MiB write) before every bench step; state L2-resident within a run"},
+                "roofline": roof, "cpu_baseline": cpu, "accuracy": accuracy,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(C0.size * 8),
+                        "d2h_bytes_per_step": int(C0.size * 8)},
+                "gpu_launches": gpu_launches, "clocks": clk, "status": lbm.lbm_strerror(rc)}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * lbm_fade.h -- C ABI of the GB300 (sm_103a) time step of the BGK/MRT lattice
+ * Boltzmann scheme for the space-fractional advection-diffusion equation
+ *
+ *   dC/dt + div(u C) = div( D F(C) ),
+ *   F_mu(C) = d/dx_mu [ p_mu I+^{2-alpha_mu}(g_mu C) + (1-p_mu) I-^{2-alpha_mu}(g_mu C) ]
+ *
+ * of Cartalade, Younsi & Neel, "Multiple-Relaxation-Time Lattice Boltzmann
+ * scheme for Fractional Advection-Diffusion Equation" (arXiv:1706.09161),
+ * Eqs. (FADE_moreGeneral) and (Fg).
+ *
+ * One handle = one problem (or one batch of independent problems) on one GPU.
+ * The handle owns every device buffer it uses (populations, concentration,
+ * fractional terms, weight matrices); it allocates them with cudaMalloc in
+ * lbm_create / lbm_create_batch and frees them in lbm_destroy.  The caller owns
+ * every host array passed in; the library copies from / into it during the call
+ * and keeps no pointer to it.
+ *
+ * Conventions
+ *   - Grid: grid[mu] = nodes on axis mu including both wall nodes, so the axis
+ *     spans n = 0..N_mu with N_mu = grid[mu]-1 (Section 2.4, Eq. XXminus_discret).
+ *     Unused axes (3rd axis in 2-D) must be 1.
+ *   - Field layout (host and device): axis 0 (x) fastest, i.e. index
+ *     x + grid[0]*(y + grid[1]*z).  Population arrays are [q][node] (SoA),
+ *     q = 0..Q-1 in the velocity order of Section 2.1: e_0 = 0, e_{1,2} = +-x,
+ *     e_{3,4} = +-y, e_{5,6} = +-z.
+ *   - All host-side numbers are double precision.
+ *
+ * Errors: every function returns 0 (LBM_OK) or a negative code; nothing aborts
+ * the process.  Launches are asynchronous on the handle's stream; errors raised
+ * on the device (non-finite concentration) are latched and returned by the next
+ * synchronising call (lbm_sync, lbm_read_*, lbm_mass).
+ */
+#ifndef LBM_FADE_H
+#define LBM_FADE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK            0
+#define LBM_EINVAL       -1  /* invalid argument: see lbm_create for the admissible ranges */
+#define LBM_ENOMEM       -2  /* device allocation failed */
+#define LBM_ECUDA        -3  /* a CUDA runtime call failed (message via lbm_last_cuda_error) */
+#define LBM_ERR_UNSTABLE -4  /* a non-finite concentration appeared during lbm_step */
+#define LBM_ENOTSUP      -5  /* combination not supported by this build */
+
+typedef struct lbm_s* lbm_t;
+
+enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1 };                 /* lattices of Section 2.1 */
+enum { LBM_BGK = 0, LBM_MRT = 1 };                   /* Eq. (LBE_Ket) / Eq. (MRT-Coll) */
+enum {
+  LBM_FP64 = 0,            /* every stage in FP64 */
+  LBM_FP32 = 1,            /* FP32 collision/streaming, FP32 fractional operator */
+  LBM_FP32_BF16SPLIT = 2,  /* FP32 collision, fractional operator on tensor cores with
+                              bf16 hi+lo operands (3 products), FP32 accumulation */
+  LBM_FP32_TF32SPLIT = 3   /* FP32 collision, fractional operator on tensor cores with
+                              tf32 hi+lo operands (3 products), FP32 accumulation */
+};
+
+typedef struct {
+  int lattice;        /* LBM_D2Q5 or LBM_D3Q7 */
+  int collision;      /* LBM_BGK or LBM_MRT */
+  int precision;      /* LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT */
+  int grid[3];        /* nodes per axis incl. walls, >= 3 on used axes, 1 on unused axes */
+  double alpha[3];    /* fractional order per axis, in ]1,2] (Eq. FADE_moreGeneral) */
+  double p[3];        /* weight of the left integral I+, in [0,1] (Eq. Fg) */
+  double g[3];        /* positive constant factor g_mu (Eq. Fg) */
+  double D[9];        /* d x d diffusion tensor, row-major (stride 3 in memory: D[3*i+j]).
+                         BGK: diagonal (non-spherical handled by h_mu, end of Section 2.2);
+                         MRT: symmetric, lambdabar = D dt/(e^2 dx^2) + Id/2 must be SPD (Eq. D_ab) */
+  double u[3];        /* advection velocity (physical units; the scheme uses u dt/dx, Eq. Feq) */
+  double s_free[3];   /* MRT relaxation rates 1/lambda_k of the free moments k = d+1..Q-1
+                         (Eq. MatrixS; D2Q5 uses 2, D3Q7 uses 3), each in ]0,2[ */
+  double dx, dt;      /* space and time steps (> 0) */
+  double C_wall;      /* Dirichlet concentration imposed on every wall node (Eq. Dirichlet_BC) */
+} lbm_params;
+
+/* Create a problem and initialise it from C0.
+ *   prm      : problem description (copied).
+ *   C0_host  : initial concentration, grid[0]*grid[1]*grid[2] doubles (host).
+ *   stream   : cudaStream_t to run on, or NULL to let the handle create its own
+ *              non-blocking stream (destroyed with the handle).
+ *   out      : receives the handle.
+ * The initial populations are the equilibrium of C0 (Algorithm 1, initialisation;
+ * f(x,0) is not stated by the paper, this is the reading taken).
+ * Weight matrices (Section 2.4, Eqs. c+ and c-) are built on the host in FP64.
+ * Returns LBM_EINVAL for alpha outside ]1,2], p outside [0,1], g <= 0, dx or dt <= 0,
+ * a grid axis < 3, BGK with off-diagonal D, a non-SPD lambdabar, free rates outside
+ * ]0,2[; LBM_ENOMEM / LBM_ECUDA on device failures (no handle is returned then). */
+int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t* out);
+
+/* Re-initialise the populations from a new concentration field (host, same layout
+ * as lbm_create): f = feq(C, F(C)).  Asynchronous w.r.t. the device; the host
+ * array may be reused as soon as the call returns. */
+int lbm_set_C(lbm_t h, const double* C_host);
+
+/* Restart from the concentration last given to lbm_create or lbm_set_C, which the
+ * handle keeps on the device: f = feq(C0, F(C0)).  No host transfer; asynchronous. */
+int lbm_reset(lbm_t h);
+
+/* Advance nsteps >= 0 time steps (Algorithm 1 time loop, items 1-5): fractional
+ * terms F_mu (Section 2.4), equilibrium (Eqs. Feq, CoeffA_FADE3D), BGK/MRT collision
+ * (Eqs. LBE_Ket, MRT-Coll), push streaming (Eq. Def_Translation), Dirichlet walls
+ * (Eq. Dirichlet_BC; k unknown populations at edges/corners share the deficit
+ * equally), new concentration C = <1|f>.  Asynchronous; steps are replayed from
+ * captured CUDA graphs. */
+int lbm_step(lbm_t h, int nsteps);
+
+/* Copy the current concentration into C_host (nodes doubles).  Synchronises the
+ * handle's stream; returns a latched LBM_ERR_UNSTABLE if one was raised. */
+int lbm_read_C(lbm_t h, double* C_host);
+
+/* Fractional term F_mu (mu = 0..d-1) of the current concentration,
+ * F_mu = p I+(g h C) + (1-p) I-(g h C) discretised by Eq. (XXminus_discret),
+ * recomputed by the step's own operator and copied to F_host (nodes doubles).
+ * Synchronises. */
+int lbm_read_F(lbm_t h, int mu, double* F_host);
+
+/* Copy / overwrite the populations, Q*nodes doubles laid out [q][node] (host).
+ * lbm_write_f also recomputes C = <1|f>.  Both synchronise. */
+int lbm_read_f(lbm_t h, double* f_host);
+int lbm_write_f(lbm_t h, const double* f_host);
+
+/* Total mass sum_x C(x) of the current concentration, reduced on the device in
+ * FP64 (block partials, then one final pass).  Synchronises. */
+int lbm_mass(lbm_t h, double* mass);
+
+/* Wait for all work of the handle; return a latched device error if any. */
+int lbm_sync(lbm_t h);
+
+/* The cudaStream_t the handle runs on (for event timing by the caller). */
+int lbm_get_stream(lbm_t h, void** stream);
+
+/* Run nsteps time steps with one-kernel launches bracketed by CUDA events on the
+ * handle's stream and accumulate the device time of each kernel class:
+ *   ms[0] = fractional operator (all axes), ms[1] = fused collide/stream/walls/moment.
+ * Divide by nsteps for the mean duration per launch.  Synchronises. */
+int lbm_profile(lbm_t h, int nsteps, double* ms);
+
+/* Number of kernel launches one time step issues (per problem batch). */
+int lbm_launches_per_step(lbm_t h, int* n);
+
+/* Host-only: the (grid[mu])^2 FP64 matrix K_mu, row-major K[n*side + l], such that
+ * F_mu[n] = sum_l K[n][l] C[l] along each lattice line of axis mu, i.e.
+ * K = g h dx^gamma / Gamma(2+gamma) * (p W+ + (1-p) W-) with gamma = 2 - alpha
+ * (Eqs. 1Dminus_discret, c+, c-).  Needs no GPU. */
+int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host);
+
+/* Release every device buffer, graph and (if created by the handle) stream. */
+void lbm_destroy(lbm_t h);
+
+/* Static description of an error code. */
+const char* lbm_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread's library calls ("" if none). */
+const char* lbm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_FADE_H */

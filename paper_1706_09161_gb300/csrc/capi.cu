@@ -1,0 +1,491 @@
+// C ABI of liblbm_fade: handle lifetime, parameter derivation (Algorithm 1,
+// initialisation items 1-4), graph-captured time stepping and host I/O.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace {
+
+thread_local char g_cuda_msg[256] = "";
+
+int record_cuda(cudaError_t e, const char* what) {
+  std::snprintf(g_cuda_msg, sizeof(g_cuda_msg), "%s: %s", what, cudaGetErrorString(e));
+  return (e == cudaErrorMemoryAllocation) ? LBM_ENOMEM : LBM_ECUDA;
+}
+
+#define LBM_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return record_cuda(e_, #call);     \
+  } while (0)
+
+// Gauss-Jordan inverse of a small dense matrix (row-major, n <= 7). Returns false if singular.
+bool invert(int n, const double* a, double* inv) {
+  double m[7][14];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) m[i][j] = (j < n) ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(m[r][c]) > std::fabs(m[piv][c])) piv = r;
+    if (std::fabs(m[piv][c]) < 1e-300) return false;
+    if (piv != c)
+      for (int j = 0; j < 2 * n; ++j) std::swap(m[c][j], m[piv][j]);
+    const double d = m[c][c];
+    for (int j = 0; j < 2 * n; ++j) m[c][j] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double fct = m[r][c];
+      if (fct == 0.0) continue;
+      for (int j = 0; j < 2 * n; ++j) m[r][j] -= fct * m[c][j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) inv[i * n + j] = m[i][j + n];
+  return true;
+}
+
+// Cholesky test for symmetric positive definiteness of a d x d matrix.
+bool is_spd(int d, const double* a) {
+  double l[3][3] = {{0}};
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (std::fabs(a[i * d + j] - a[j * d + i]) > 1e-14 * (std::fabs(a[i * d + j]) + 1e-300)) return false;
+  for (int j = 0; j < d; ++j) {
+    double s = a[j * d + j];
+    for (int k = 0; k < j; ++k) s -= l[j][k] * l[j][k];
+    if (!(s > 0.0)) return false;
+    l[j][j] = std::sqrt(s);
+    for (int i = j + 1; i < d; ++i) {
+      double t = a[i * d + j];
+      for (int k = 0; k < j; ++k) t -= l[i][k] * l[j][k];
+      l[i][j] = t / l[j][j];
+    }
+  }
+  return true;
+}
+
+// MRT change of basis, Eq. (MatrixD2).
+void moment_matrix(int d, double* M) {
+  static const int m5[5][5] = {{1, 1, 1, 1, 1}, {0, 1, -1, 0, 0}, {0, 0, 0, 1, -1}, {4, -1, -1, -1, -1}, {0, 1, 1, -1, -1}};
+  static const int m7[7][7] = {{1, 1, 1, 1, 1, 1, 1},      {0, 1, -1, 0, 0, 0, 0},    {0, 0, 0, 1, -1, 0, 0},
+                               {0, 0, 0, 0, 0, 1, -1},     {6, -1, -1, -1, -1, -1, -1}, {0, 2, 2, -1, -1, -1, -1},
+                               {0, 0, 0, 1, 1, -1, -1}};
+  const int Q = (d == 2) ? 5 : 7;
+  for (int i = 0; i < Q; ++i)
+    for (int j = 0; j < Q; ++j) M[i * Q + j] = (d == 2) ? m5[i][j] : m7[i][j];
+}
+
+struct Derived {
+  lbm::StepParams sp;
+  double h[3];  // BGK diagonal-D factors multiplying g_mu (end of Section 2.2)
+};
+
+int derive(const lbm_params* p, Derived* out) {
+  if (!p) return LBM_EINVAL;
+  if (p->lattice != LBM_D2Q5 && p->lattice != LBM_D3Q7) return LBM_EINVAL;
+  if (p->collision != LBM_BGK && p->collision != LBM_MRT) return LBM_EINVAL;
+  if (p->precision < LBM_FP64 || p->precision > LBM_FP32_TF32SPLIT) return LBM_EINVAL;
+  const int d = (p->lattice == LBM_D2Q5) ? 2 : 3;
+  const int Q = 2 * d + 1;
+  if (!(p->dx > 0.0) || !(p->dt > 0.0) || !std::isfinite(p->dx) || !std::isfinite(p->dt)) return LBM_EINVAL;
+  if (!std::isfinite(p->C_wall)) return LBM_EINVAL;
+  for (int mu = 0; mu < 3; ++mu) {
+    if (mu < d) {
+      if (p->grid[mu] < 3) return LBM_EINVAL;
+      if (!(p->alpha[mu] > 1.0 && p->alpha[mu] <= 2.0)) return LBM_EINVAL;
+      if (!(p->p[mu] >= 0.0 && p->p[mu] <= 1.0)) return LBM_EINVAL;
+      if (!(p->g[mu] > 0.0) || !std::isfinite(p->g[mu])) return LBM_EINVAL;
+      if (!std::isfinite(p->u[mu])) return LBM_EINVAL;
+    } else if (p->grid[mu] != 1) {
+      return LBM_EINVAL;
+    }
+  }
+  const long long nodes = (long long)p->grid[0] * p->grid[1] * p->grid[2];
+  if (nodes > (1LL << 31)) return LBM_EINVAL;
+
+  Derived D{};
+  lbm::StepParams& sp = D.sp;
+  for (int mu = 0; mu < 3; ++mu) sp.n[mu] = p->grid[mu];
+  sp.nodes = nodes;
+  const double e2 = (d == 2) ? 1.0 / 3.0 : 1.0 / 4.0;      // Fig. 1 caption
+  sp.w0 = (d == 2) ? 1.0 / 3.0 : 1.0 / 4.0;
+  sp.wi = (d == 2) ? 1.0 / 6.0 : 1.0 / 8.0;
+  for (int mu = 0; mu < 3; ++mu) sp.adv[mu] = (mu < d) ? (p->dt / p->dx) * p->u[mu] / e2 : 0.0;
+  sp.C_wall = p->C_wall;
+  const double ratio = p->dt / (p->dx * p->dx);
+  double Dm[9];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) Dm[i * d + j] = p->D[3 * i + j];
+  for (int i = 0; i < d; ++i)
+    if (!(Dm[i * d + i] > 0.0) || !std::isfinite(Dm[i * d + i])) return LBM_EINVAL;
+  for (int mu = 0; mu < 3; ++mu) D.h[mu] = 1.0;
+
+  if (p->collision == LBM_BGK) {
+    // D = e^2 (lambda - 1/2) dx^2/dt, Eq. (Diffusion_Coefficient_3D); a diagonal, non-spherical D
+    // keeps one lambda (from the largest entry) and scales g_mu by h_mu = D_mumu / max D.
+    double dmax = 0.0;
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j)
+        if (i != j && Dm[i * d + j] != 0.0) return LBM_EINVAL;
+    for (int i = 0; i < d; ++i) dmax = std::fmax(dmax, Dm[i * d + i]);
+    const double lam = dmax * ratio / e2 + 0.5;
+    for (int i = 0; i < d; ++i) D.h[i] = Dm[i * d + i] / dmax;
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < Q; ++j) sp.omega[i][j] = (i == j) ? 1.0 / lam : 0.0;
+  } else {
+    // Lambda^-1 = diag(lambda_0, lambdabar, 1/s_free), Eq. (MatrixS); lambdabar from Eq. (D_ab)
+    double lambar[9];
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) lambar[i * d + j] = Dm[i * d + j] * ratio / e2 + (i == j ? 0.5 : 0.0);
+    if (!is_spd(d, lambar)) return LBM_EINVAL;
+    for (int k = 0; k < Q - d - 1; ++k)
+      if (!(p->s_free[k] > 0.0 && p->s_free[k] < 2.0)) return LBM_EINVAL;
+    double laminv[49] = {0}, lam[49], M[49], Minv[49], tmp[49];
+    laminv[0] = 1.0;  // conserved moment: no effect
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) laminv[(1 + i) * Q + (1 + j)] = lambar[i * d + j];
+    for (int k = 0; k < Q - d - 1; ++k) laminv[(d + 1 + k) * Q + (d + 1 + k)] = 1.0 / p->s_free[k];
+    if (!invert(Q, laminv, lam)) return LBM_EINVAL;
+    moment_matrix(d, M);
+    // rows of M are orthogonal: M^-1 = M^T diag(1/|row|^2)
+    for (int i = 0; i < Q; ++i) {
+      double nrm = 0.0;
+      for (int j = 0; j < Q; ++j) nrm += M[i * Q + j] * M[i * Q + j];
+      for (int j = 0; j < Q; ++j) Minv[j * Q + i] = M[i * Q + j] / nrm;
+    }
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < Q; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < Q; ++k) s += lam[i * Q + k] * M[k * Q + j];
+        tmp[i * Q + j] = s;
+      }
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < Q; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < Q; ++k) s += Minv[i * Q + k] * tmp[k * Q + j];
+        sp.omega[i][j] = s;
+      }
+  }
+  *out = D;
+  return LBM_OK;
+}
+
+void free_all(lbm_s* h) {
+  for (int i = 0; i < 2; ++i) {
+    if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
+    if (h->graph[i]) cudaGraphDestroy(h->graph[i]);
+    h->graph_exec[i] = nullptr;
+    h->graph[i] = nullptr;
+  }
+  void* ptrs[] = {h->dev.f[0], h->dev.f[1], h->dev.C, h->dev.C0, h->dev.F, h->dev.K, h->dev.KT, h->dev.stage,
+                  h->dev.partials, h->dev.scalar, h->dev.flag, h->dev.Khi, h->dev.Klo, h->dev.Chi, h->dev.Clo};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h->dev = lbm::DeviceState{};
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  h->stream = nullptr;
+}
+
+int alloc_bytes(void** p, size_t bytes) {
+  LBM_CUDA(cudaMalloc(p, bytes));
+  return LBM_OK;
+}
+
+// F = fractional terms of the current C (Algorithm 1, loop item 1)
+int run_frac(lbm_s* h, cudaStream_t s) {
+  if (h->prm.precision == LBM_FP64 || h->prm.precision == LBM_FP32) {
+    LBM_CUDA(lbm::launch_frac_simt(h, h->dev.C, h->dev.F, s));
+  } else {
+    LBM_CUDA(lbm::launch_frac_tc(h, s));
+  }
+  return LBM_OK;
+}
+
+int one_step(lbm_s* h, int& cur, cudaStream_t s) {
+  int rc = run_frac(h, s);
+  if (rc) return rc;
+  LBM_CUDA(lbm::launch_collide_stream(h, h->dev.f[cur], h->dev.f[cur ^ 1], h->dev.C, s));
+  cur ^= 1;
+  return LBM_OK;
+}
+
+// f = feq(C, F(C)), then C = <1|f> so that the first step sees the same C the populations carry.
+int init_from_C(lbm_s* h) {
+  int rc = run_frac(h, h->stream);
+  if (rc) return rc;
+  LBM_CUDA(lbm::launch_init_equilibrium(h, h->dev.f[h->cur], h->stream));
+  LBM_CUDA(lbm::launch_moment(h, h->dev.f[h->cur], h->dev.C, h->stream));
+  return LBM_OK;
+}
+
+int latched(lbm_s* h) {
+  int flag = 0;
+  LBM_CUDA(cudaMemcpyAsync(&flag, h->dev.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return (flag & 1) ? LBM_ERR_UNSTABLE : LBM_OK;
+}
+
+int capture_graph(lbm_s* h, int parity) {
+  cudaStream_t s = h->stream;
+  LBM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int cur = parity;
+  int rc = LBM_OK;
+  for (int k = 0; k < h->graph_steps && rc == LBM_OK; ++k) rc = one_step(h, cur, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return record_cuda(e, "cudaStreamEndCapture");
+  h->graph[parity] = g;
+  LBM_CUDA(cudaGraphInstantiate(&h->graph_exec[parity], g, 0));
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t* out) {
+  if (!out || !C0_host) return LBM_EINVAL;
+  *out = nullptr;
+  Derived dv;
+  int rc = derive(prm, &dv);
+  if (rc) return rc;
+  lbm_s* h = new (std::nothrow) lbm_s();
+  if (!h) return LBM_ENOMEM;
+  h->prm = *prm;
+  h->d = (prm->lattice == LBM_D2Q5) ? 2 : 3;
+  h->Q = 2 * h->d + 1;
+  h->elem = (prm->precision == LBM_FP64) ? 8 : 4;
+  h->sp = dv.sp;
+  h->graph_steps = 32;
+  cudaGetDevice(&h->device);
+  auto fail = [&](int code) {
+    free_all(h);
+    delete h;
+    return code;
+  };
+  if (stream) {
+    h->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(record_cuda(e, "cudaStreamCreateWithFlags"));
+    h->own_stream = true;
+  }
+  const long long nodes = h->sp.nodes;
+  const size_t E = h->elem;
+  long long ksz = 0;
+  for (int mu = 0; mu < h->d; ++mu) ksz += (long long)prm->grid[mu] * prm->grid[mu];
+  h->reduce_blocks = lbm::reduce_blocks_for(nodes);
+  if ((rc = alloc_bytes(&h->dev.f[0], E * h->Q * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(&h->dev.f[1], E * h->Q * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(&h->dev.C, E * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(&h->dev.C0, E * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(&h->dev.F, E * h->d * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(&h->dev.K, E * ksz))) return fail(rc);
+  if ((rc = alloc_bytes(&h->dev.KT, E * ksz))) return fail(rc);
+  if ((rc = alloc_bytes((void**)&h->dev.stage, sizeof(double) * (size_t)(nodes > ksz ? nodes : ksz)))) return fail(rc);
+  if ((rc = alloc_bytes((void**)&h->dev.partials, sizeof(double) * h->reduce_blocks))) return fail(rc);
+  if ((rc = alloc_bytes((void**)&h->dev.scalar, sizeof(double)))) return fail(rc);
+  if ((rc = alloc_bytes((void**)&h->dev.flag, sizeof(int)))) return fail(rc);
+  if (cudaMemsetAsync(h->dev.flag, 0, sizeof(int), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
+
+  // weight matrices K_mu (Section 2.4) in FP64 on the host, then the working precision
+  {
+    std::vector<double> K, KT;
+    long long off = 0;
+    for (int mu = 0; mu < h->d; ++mu) {
+      const int side = prm->grid[mu];
+      K.assign((size_t)side * side, 0.0);
+      KT.assign((size_t)side * side, 0.0);
+      lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], prm->g[mu] * dv.h[mu], side, prm->dx, K.data());
+      for (int n = 0; n < side; ++n)
+        for (int l = 0; l < side; ++l) KT[(size_t)l * side + n] = K[(size_t)n * side + l];
+      const size_t cnt = (size_t)side * side;
+      cudaError_t e = cudaMemcpyAsync(h->dev.stage, K.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = lbm::launch_convert_in(h->dev.stage, (char*)h->dev.K + off * E, h->elem, cnt, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->dev.stage, KT.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = lbm::launch_convert_in(h->dev.stage, (char*)h->dev.KT + off * E, h->elem, cnt, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) return fail(record_cuda(e, "weight upload"));
+      off += (long long)cnt;
+    }
+  }
+  if (prm->precision == LBM_FP32_BF16SPLIT || prm->precision == LBM_FP32_TF32SPLIT) {
+    return fail(LBM_ENOTSUP);
+  }
+  h->launches_per_step = h->d + 1;
+  *out = h;
+  rc = lbm_set_C(h, C0_host);
+  if (rc) {
+    *out = nullptr;
+    return fail(rc);
+  }
+  return LBM_OK;
+}
+
+int lbm_set_C(lbm_t h, const double* C_host) {
+  if (!h || !C_host) return LBM_EINVAL;
+  const long long nodes = h->sp.nodes;
+  LBM_CUDA(cudaMemcpyAsync(h->dev.stage, C_host, sizeof(double) * nodes, cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(lbm::launch_convert_in(h->dev.stage, h->dev.C0, h->elem, nodes, h->stream));
+  return lbm_reset(h);
+}
+
+int lbm_reset(lbm_t h) {
+  if (!h) return LBM_EINVAL;
+  LBM_CUDA(cudaMemcpyAsync(h->dev.C, h->dev.C0, (size_t)h->elem * h->sp.nodes, cudaMemcpyDeviceToDevice,
+                           h->stream));
+  return init_from_C(h);
+}
+
+int lbm_profile(lbm_t h, int nsteps, double* ms) {
+  if (!h || !ms || nsteps < 0) return LBM_EINVAL;
+  cudaEvent_t ev[3];
+  for (auto& e : ev) LBM_CUDA(cudaEventCreate(&e));
+  ms[0] = ms[1] = 0.0;
+  int rc = LBM_OK;
+  for (int k = 0; k < nsteps && rc == LBM_OK; ++k) {
+    cudaError_t e = cudaEventRecord(ev[0], h->stream);
+    if (e == cudaSuccess) rc = run_frac(h, h->stream);
+    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[1], h->stream);
+    if (e == cudaSuccess && rc == LBM_OK)
+      e = lbm::launch_collide_stream(h, h->dev.f[h->cur], h->dev.f[h->cur ^ 1], h->dev.C, h->stream);
+    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[2], h->stream);
+    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventSynchronize(ev[2]);
+    float a = 0.f, b = 0.f;
+    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+    if (e != cudaSuccess) rc = record_cuda(e, "lbm_profile");
+    h->cur ^= 1;
+    ms[0] += a;
+    ms[1] += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return rc;
+}
+
+int lbm_step(lbm_t h, int nsteps) {
+  if (!h || nsteps < 0) return LBM_EINVAL;
+  int rc;
+  while (nsteps >= h->graph_steps) {
+    if (!h->graph_exec[h->cur] && (rc = capture_graph(h, h->cur))) return rc;
+    LBM_CUDA(cudaGraphLaunch(h->graph_exec[h->cur], h->stream));
+    nsteps -= h->graph_steps;  // even: the current buffer index is unchanged
+  }
+  for (int k = 0; k < nsteps; ++k)
+    if ((rc = one_step(h, h->cur, h->stream))) return rc;
+  return LBM_OK;
+}
+
+int lbm_read_C(lbm_t h, double* C_host) {
+  if (!h || !C_host) return LBM_EINVAL;
+  const long long nodes = h->sp.nodes;
+  LBM_CUDA(lbm::launch_convert_out(h->dev.C, h->elem, h->dev.stage, nodes, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(C_host, h->dev.stage, sizeof(double) * nodes, cudaMemcpyDeviceToHost, h->stream));
+  return latched(h);
+}
+
+int lbm_read_F(lbm_t h, int mu, double* F_host) {
+  if (!h || !F_host || mu < 0 || mu >= h->d) return LBM_EINVAL;
+  const long long nodes = h->sp.nodes;
+  int rc = run_frac(h, h->stream);
+  if (rc) return rc;
+  LBM_CUDA(lbm::launch_convert_out((char*)h->dev.F + (size_t)mu * nodes * h->elem, h->elem, h->dev.stage, nodes,
+                                   h->stream));
+  LBM_CUDA(cudaMemcpyAsync(F_host, h->dev.stage, sizeof(double) * nodes, cudaMemcpyDeviceToHost, h->stream));
+  return latched(h);
+}
+
+int lbm_read_f(lbm_t h, double* f_host) {
+  if (!h || !f_host) return LBM_EINVAL;
+  const long long nodes = h->sp.nodes;
+  for (int q = 0; q < h->Q; ++q) {
+    LBM_CUDA(lbm::launch_convert_out((char*)h->dev.f[h->cur] + (size_t)q * nodes * h->elem, h->elem, h->dev.stage,
+                                     nodes, h->stream));
+    LBM_CUDA(cudaMemcpyAsync(f_host + (size_t)q * nodes, h->dev.stage, sizeof(double) * nodes,
+                             cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  return latched(h);
+}
+
+int lbm_write_f(lbm_t h, const double* f_host) {
+  if (!h || !f_host) return LBM_EINVAL;
+  const long long nodes = h->sp.nodes;
+  for (int q = 0; q < h->Q; ++q) {
+    LBM_CUDA(cudaMemcpyAsync(h->dev.stage, f_host + (size_t)q * nodes, sizeof(double) * nodes,
+                             cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(lbm::launch_convert_in(h->dev.stage, (char*)h->dev.f[h->cur] + (size_t)q * nodes * h->elem, h->elem,
+                                    nodes, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  LBM_CUDA(lbm::launch_moment(h, h->dev.f[h->cur], h->dev.C, h->stream));
+  return latched(h);
+}
+
+int lbm_mass(lbm_t h, double* mass) {
+  if (!h || !mass) return LBM_EINVAL;
+  LBM_CUDA(lbm::launch_mass(h, h->dev.C, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(mass, h->dev.scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return latched(h);
+}
+
+int lbm_sync(lbm_t h) {
+  if (!h) return LBM_EINVAL;
+  return latched(h);
+}
+
+int lbm_get_stream(lbm_t h, void** stream) {
+  if (!h || !stream) return LBM_EINVAL;
+  *stream = h->stream;
+  return LBM_OK;
+}
+
+int lbm_launches_per_step(lbm_t h, int* n) {
+  if (!h || !n) return LBM_EINVAL;
+  *n = h->launches_per_step;
+  return LBM_OK;
+}
+
+int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host) {
+  if (!K_host) return LBM_EINVAL;
+  Derived dv;
+  int rc = derive(prm, &dv);
+  if (rc) return rc;
+  const int d = (prm->lattice == LBM_D2Q5) ? 2 : 3;
+  if (mu < 0 || mu >= d) return LBM_EINVAL;
+  lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], prm->g[mu] * dv.h[mu], prm->grid[mu], prm->dx, K_host);
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+const char* lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "device allocation failed";
+    case LBM_ECUDA: return "CUDA runtime error";
+    case LBM_ERR_UNSTABLE: return "non-finite concentration (numerical instability)";
+    case LBM_ENOTSUP: return "not supported by this build";
+    default: return "unknown error";
+  }
+}
+
+const char* lbm_last_cuda_error(void) { return g_cuda_msg; }
+
+}  // extern "C"

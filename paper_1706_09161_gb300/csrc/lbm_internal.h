@@ -1,0 +1,90 @@
+// Internal declarations shared by the translation units of liblbm_fade.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "lbm_fade.h"
+
+namespace lbm {
+
+constexpr int kMaxQ = 7;
+
+// Per-problem constants of one time step, passed by value to the kernels.
+// Derived on the host in FP64 from lbm_params (Algorithm 1, initialisation).
+struct StepParams {
+  int n[3];                  // nodes per axis (unused axes: 1)
+  long long nodes;           // n[0]*n[1]*n[2]
+  double omega[kMaxQ][kMaxQ];// collision matrix: f* = f - omega (f - feq)
+                             //   BGK: omega = I/lambda; MRT: M^-1 Lambda M (Eq. MRT-Coll)
+  double w0, wi;             // lattice weights: rest and moving (Fig. 1 caption)
+  double adv[3];             // (dt/dx) u_mu / e^2: advective factor of Eq. (Feq)
+  double C_wall;             // Dirichlet value (Eq. Dirichlet_BC)
+};
+
+// Device-side buffers of one problem.
+struct DeviceState {
+  void* f[2] = {nullptr, nullptr};  // populations [q][node], double-buffered
+  void* C = nullptr;                 // concentration [node]
+  void* C0 = nullptr;                // initial concentration kept for lbm_reset [node]
+  void* F = nullptr;                 // fractional terms [mu][node]
+  void* K = nullptr;                 // K_mu, [mu][side_mu^2] row-major (n, l)
+  void* KT = nullptr;                // K_mu transposed, [mu][side_mu^2] row-major (l, n)
+  double* stage = nullptr;           // FP64 staging [node] / [q][node] for host I/O
+  double* partials = nullptr;        // FP64 block partial sums (mass reduction)
+  double* scalar = nullptr;          // FP64 reduction result
+  int* flag = nullptr;               // latched device error bits (1 = non-finite C)
+  // split operands for the tensor-core fractional operator
+  void* Khi = nullptr;               // [mu][side^2] hi part of K (bf16 or tf32-in-fp32)
+  void* Klo = nullptr;               // [mu][side^2] lo part of K
+  void* Chi = nullptr;               // [node] hi part of C
+  void* Clo = nullptr;               // [node] lo part of C
+};
+
+}  // namespace lbm
+
+struct lbm_s {
+  lbm_params prm;
+  int d = 2, Q = 5;
+  int elem = 8;                        // bytes per real (8 FP64, 4 FP32 forms)
+  lbm::StepParams sp;
+  lbm::DeviceState dev;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int cur = 0;                         // index of the current population buffer
+  int reduce_blocks = 0;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  int graph_steps = 0;                 // steps per captured graph (even)
+  int launches_per_step = 0;
+  int device = 0;
+};
+
+namespace lbm {
+
+// ---- kernels (launchers return cudaGetLastError of the launch)
+// fractional operator, SIMT: F_mu = K_mu applied along axis mu, for all mu
+cudaError_t launch_frac_simt(const lbm_s* h, const void* C, void* F, cudaStream_t s);
+// tensor-core split-precision fractional operator (tcgen05); returns
+// cudaErrorNotSupported when the handle's shape is not covered
+cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s);
+// fused equilibrium + collision + streaming + Dirichlet + new concentration
+cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out, void* C_out,
+                                  cudaStream_t s);
+// f = feq(C, F)
+cudaError_t launch_init_equilibrium(const lbm_s* h, void* f, cudaStream_t s);
+// C = sum_q f_q
+cudaError_t launch_moment(const lbm_s* h, const void* f, void* C, cudaStream_t s);
+// conversions between the FP64 staging buffer and the working precision
+cudaError_t launch_convert_in(const void* src_f64, void* dst, int elem, long long n, cudaStream_t s);
+cudaError_t launch_convert_out(const void* src, int elem, double* dst_f64, long long n, cudaStream_t s);
+// mass reduction: partials then final
+cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
+// split C into hi/lo operands for the tensor-core path
+cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s);
+int reduce_blocks_for(long long n);
+
+// host-side weight build (FP64), K row-major [n][l] for one axis
+void build_frac_matrix(double alpha, double p, double scale_g, int side, double dx, double* K);
+
+}  // namespace lbm

@@ -1,0 +1,286 @@
+"""ctypes binding of liblbm_fade.so (C ABI declared in include/lbm_fade.h).
+
+Argument marshalling only: every step of the scheme runs in the library's CUDA
+kernels.  The functions keep the C names (``lbm_create``, ``lbm_step``, ...);
+``Lattice`` wraps a handle for convenience.  There is no CPU fallback: if the
+library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm_fade.so")
+
+LBM_OK = 0
+LBM_EINVAL = -1
+LBM_ENOMEM = -2
+LBM_ECUDA = -3
+LBM_ERR_UNSTABLE = -4
+LBM_ENOTSUP = -5
+
+LBM_D2Q5, LBM_D3Q7 = 0, 1
+LBM_BGK, LBM_MRT = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT = 0, 1, 2, 3
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16split": LBM_FP32_BF16SPLIT, "tf32split": LBM_FP32_TF32SPLIT}
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int),
+        ("collision", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("grid", ctypes.c_int * 3),
+        ("alpha", ctypes.c_double * 3),
+        ("p", ctypes.c_double * 3),
+        ("g", ctypes.c_double * 3),
+        ("D", ctypes.c_double * 9),
+        ("u", ctypes.c_double * 3),
+        ("s_free", ctypes.c_double * 3),
+        ("dx", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("C_wall", ctypes.c_double),
+    ]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = f"{where}: {lbm_strerror(code)} ({code})"
+        if code == LBM_ECUDA or code == LBM_ENOMEM:
+            msg += f" [{lbm_last_cuda_error()}]"
+        super().__init__(msg)
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1706_09161_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    dp = P(ctypes.c_double)
+    vp = ctypes.c_void_p
+    sig = {
+        "lbm_create": (ctypes.c_int, [P(lbm_params), dp, vp, P(vp)]),
+        "lbm_set_C": (ctypes.c_int, [vp, dp]),
+        "lbm_reset": (ctypes.c_int, [vp]),
+        "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_profile": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lbm_read_C": (ctypes.c_int, [vp, dp]),
+        "lbm_read_F": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lbm_read_f": (ctypes.c_int, [vp, dp]),
+        "lbm_write_f": (ctypes.c_int, [vp, dp]),
+        "lbm_mass": (ctypes.c_int, [vp, dp]),
+        "lbm_sync": (ctypes.c_int, [vp]),
+        "lbm_get_stream": (ctypes.c_int, [vp, P(vp)]),
+        "lbm_launches_per_step": (ctypes.c_int, [vp, P(ctypes.c_int)]),
+        "lbm_frac_matrix": (ctypes.c_int, [P(lbm_params), ctypes.c_int, dp]),
+        "lbm_destroy": (None, [vp]),
+        "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lbm_last_cuda_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+# Declared C entry points, re-exported under their own names.
+EXPORTED = ("lbm_create", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f",
+            "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_frac_matrix",
+            "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
+
+
+def lbm_strerror(code: int) -> str:
+    return _lib.lbm_strerror(int(code)).decode()
+
+
+def lbm_last_cuda_error() -> str:
+    return _lib.lbm_last_cuda_error().decode()
+
+
+def _check(code: int, where: str) -> None:
+    if code != LBM_OK:
+        raise LBMError(code, where)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def params_from_problem(pb, precision: str = "fp32") -> lbm_params:
+    """Fill lbm_params from a workloads.Problem (or any object with the same attributes)."""
+    prm = lbm_params()
+    d = int(pb.d)
+    prm.lattice = LBM_D2Q5 if d == 2 else LBM_D3Q7
+    prm.collision = LBM_BGK if pb.collision == "bgk" else LBM_MRT
+    prm.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    for mu in range(3):
+        prm.grid[mu] = int(pb.grid[mu]) if mu < d else 1
+        prm.alpha[mu] = float(pb.alpha[mu]) if mu < d else 2.0
+        prm.p[mu] = float(pb.p[mu]) if mu < d else 0.5
+        prm.g[mu] = float(pb.g[mu]) if mu < d else 1.0
+        prm.u[mu] = float(pb.u[mu]) if mu < d else 0.0
+    for i in range(d):
+        for j in range(d):
+            prm.D[3 * i + j] = float(pb.D[i][j])
+    for k, s in enumerate(getattr(pb, "s_free", ()) or ()):
+        prm.s_free[k] = float(s)
+    prm.dx = float(getattr(pb, "dx", 1.0))
+    prm.dt = float(getattr(pb, "dt", 1.0))
+    prm.C_wall = float(getattr(pb, "C_wall", 0.0))
+    return prm
+
+
+def lbm_create(prm: lbm_params, C0: np.ndarray, stream: Optional[int] = None) -> int:
+    C0 = np.ascontiguousarray(C0, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(_lib.lbm_create(ctypes.byref(prm), _dptr(C0), ctypes.c_void_p(stream or 0), ctypes.byref(h)),
+           "lbm_create")
+    return h.value
+
+
+def lbm_set_C(h: int, C: np.ndarray) -> None:
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    _check(_lib.lbm_set_C(ctypes.c_void_p(h), _dptr(C)), "lbm_set_C")
+
+
+def lbm_reset(h: int) -> None:
+    _check(_lib.lbm_reset(ctypes.c_void_p(h)), "lbm_reset")
+
+
+def lbm_profile(h: int, nsteps: int):
+    ms = (ctypes.c_double * 2)()
+    _check(_lib.lbm_profile(ctypes.c_void_p(h), int(nsteps), ms), "lbm_profile")
+    return float(ms[0]), float(ms[1])
+
+
+def lbm_step(h: int, nsteps: int) -> None:
+    _check(_lib.lbm_step(ctypes.c_void_p(h), int(nsteps)), "lbm_step")
+
+
+def lbm_read_C(h: int, out: np.ndarray) -> np.ndarray:
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(_lib.lbm_read_C(ctypes.c_void_p(h), _dptr(out)), "lbm_read_C")
+    return out
+
+
+def lbm_read_F(h: int, mu: int, out: np.ndarray) -> np.ndarray:
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(_lib.lbm_read_F(ctypes.c_void_p(h), int(mu), _dptr(out)), "lbm_read_F")
+    return out
+
+
+def lbm_read_f(h: int, out: np.ndarray) -> np.ndarray:
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(_lib.lbm_read_f(ctypes.c_void_p(h), _dptr(out)), "lbm_read_f")
+    return out
+
+
+def lbm_write_f(h: int, f: np.ndarray) -> None:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(_lib.lbm_write_f(ctypes.c_void_p(h), _dptr(f)), "lbm_write_f")
+
+
+def lbm_mass(h: int) -> float:
+    m = ctypes.c_double()
+    _check(_lib.lbm_mass(ctypes.c_void_p(h), ctypes.byref(m)), "lbm_mass")
+    return m.value
+
+
+def lbm_sync(h: int) -> int:
+    return int(_lib.lbm_sync(ctypes.c_void_p(h)))
+
+
+def lbm_get_stream(h: int) -> int:
+    s = ctypes.c_void_p()
+    _check(_lib.lbm_get_stream(ctypes.c_void_p(h), ctypes.byref(s)), "lbm_get_stream")
+    return s.value or 0
+
+
+def lbm_launches_per_step(h: int) -> int:
+    n = ctypes.c_int()
+    _check(_lib.lbm_launches_per_step(ctypes.c_void_p(h), ctypes.byref(n)), "lbm_launches_per_step")
+    return n.value
+
+
+def lbm_frac_matrix(prm: lbm_params, mu: int) -> np.ndarray:
+    side = prm.grid[mu]
+    K = np.empty((side, side), dtype=np.float64)
+    _check(_lib.lbm_frac_matrix(ctypes.byref(prm), int(mu), _dptr(K)), "lbm_frac_matrix")
+    return K
+
+
+def lbm_destroy(h: int) -> None:
+    _lib.lbm_destroy(ctypes.c_void_p(h))
+
+
+class Lattice:
+    """One FADE lattice Boltzmann problem on the GPU (owns an lbm_t handle)."""
+
+    def __init__(self, pb, C0: np.ndarray, precision: str = "fp32", stream: Optional[int] = None):
+        self.problem = pb
+        self.shape = tuple(reversed(tuple(int(n) for n in pb.grid)))
+        self.d = int(pb.d)
+        self.Q = 2 * self.d + 1
+        self.prm = params_from_problem(pb, precision)
+        self.h = lbm_create(self.prm, C0, stream)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_C(self, C: np.ndarray) -> None:
+        lbm_set_C(self.h, C)
+
+    def reset(self) -> None:
+        lbm_reset(self.h)
+
+    def step(self, n: int = 1) -> None:
+        lbm_step(self.h, n)
+
+    def profile(self, n: int):
+        """(ms fractional operator, ms collide-stream) summed over n one-kernel-launch steps."""
+        return lbm_profile(self.h, n)
+
+    def C(self) -> np.ndarray:
+        return lbm_read_C(self.h, np.empty(self.shape, dtype=np.float64))
+
+    def F(self, mu: int) -> np.ndarray:
+        return lbm_read_F(self.h, mu, np.empty(self.shape, dtype=np.float64))
+
+    def f(self) -> np.ndarray:
+        return lbm_read_f(self.h, np.empty((self.Q,) + self.shape, dtype=np.float64))
+
+    def write_f(self, f: np.ndarray) -> None:
+        lbm_write_f(self.h, f)
+
+    def mass(self) -> float:
+        return lbm_mass(self.h)
+
+    def sync(self) -> None:
+        _check(lbm_sync(self.h), "lbm_sync")
+
+    @property
+    def stream(self) -> int:
+        return lbm_get_stream(self.h)
+
+    @property
+    def launches_per_step(self) -> int:
+        return lbm_launches_per_step(self.h)

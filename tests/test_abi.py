@@ -1,0 +1,107 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared
+symbol, validates parameters, and builds the fractional weight matrices on the
+host exactly as the FP64 oracle does (within the oracle's own rounding)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lbm_oracle as O
+from paper_1706_09161_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(lbm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1706_09161_gb300 import build
+    build.build()
+    from paper_1706_09161_gb300 import lbm
+    return lbm
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for want in ("lbm_create", "lbm_step", "lbm_read_C", "lbm_mass", "lbm_destroy", "lbm_strerror"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    lib = ctypes.CDLL(L.LIB_PATH)
+    for name in _declared_symbols():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    for name in L.EXPORTED:
+        assert name in _declared_symbols()
+
+
+def test_strerror(L):
+    assert L.lbm_strerror(0) == "ok"
+    assert "instability" in L.lbm_strerror(L.LBM_ERR_UNSTABLE)
+
+
+@pytest.mark.parametrize("side,alpha,p,g,dx", [(3, 1.5, 0.5, 1.0, 1.0), (17, 1.2, 0.3, 0.7, 0.25),
+                                               (64, 1.7, 0.5, 1.0, 1.0), (101, 1.99, 0.9, 1.3, 0.02),
+                                               (257, 1.05, 0.0, 1.0, 1.0), (40, 2.0, 0.4, 1.0, 1.0)])
+def test_host_weight_matrix_matches_oracle(L, side, alpha, p, g, dx):
+    pb = W.Problem(d=2, collision="mrt", grid=(side, 5), alpha=(alpha, 1.5), p=(p, 0.5), g=(g, 1.0),
+                   D=((0.01, 0), (0, 0.01)), u=(0, 0), s_free=(1.0, 1.0), dx=dx)
+    K = L.lbm_frac_matrix(L.params_from_problem(pb, "fp64"), 0)
+    Ko = O.frac_matrix(alpha, p, g, side - 1, dx).numpy()
+    # the oracle evaluates second differences of k^(g+1) directly and loses ~2 log10(k) digits
+    tol = 1e-15 * side * side + 1e-14
+    assert np.max(np.abs(K - Ko)) <= tol * np.max(np.abs(Ko))
+
+
+def test_host_weight_matrix_bgk_diagonal_D(L):
+    """BGK with non-spherical diagonal D: h_mu = D_mumu / max D scales g_mu (end of Section 2.2)."""
+    pb = W.Problem(d=2, collision="bgk", grid=(9, 7), alpha=(1.5, 1.6), p=(0.5, 0.2), g=(1.0, 2.0),
+                   D=((0.02, 0), (0, 0.005)), u=(0, 0))
+    prm = L.params_from_problem(pb, "fp64")
+    ops = O.Operators(pb)
+    for mu in range(2):
+        assert np.allclose(L.lbm_frac_matrix(prm, mu), ops.K[mu].numpy(), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("field,value", [("alpha", 1.0), ("alpha", 2.1), ("p", -0.1), ("p", 1.2), ("g", 0.0),
+                                         ("dx", 0.0), ("grid", 2)])
+def test_invalid_parameters_rejected(L, field, value):
+    pb = W.Problem(d=2, collision="mrt", grid=(8, 8), alpha=(1.5, 1.5), p=(0.5, 0.5), g=(1, 1),
+                   D=((0.01, 0), (0, 0.01)), u=(0, 0), s_free=(1.0, 1.0))
+    prm = L.params_from_problem(pb, "fp32")
+    if field in ("alpha", "p", "g"):
+        getattr(prm, field)[0] = value
+    elif field == "grid":
+        prm.grid[0] = value
+    else:
+        setattr(prm, field, value)
+    K = np.empty((8, 8))
+    rc = L._lib.lbm_frac_matrix(ctypes.byref(prm), 0, K.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert rc == L.LBM_EINVAL
+
+
+def test_bgk_rejects_off_diagonal_D_and_mrt_rejects_non_spd(L):
+    K = np.empty((8, 8))
+    ptr = K.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    pb = W.Problem(d=2, collision="bgk", grid=(8, 8), alpha=(1.5, 1.5), p=(0.5, 0.5), g=(1, 1),
+                   D=((0.01, 0.002), (0.002, 0.01)), u=(0, 0))
+    assert L._lib.lbm_frac_matrix(ctypes.byref(L.params_from_problem(pb)), 0, ptr) == L.LBM_EINVAL
+    pb = W.Problem(d=2, collision="mrt", grid=(8, 8), alpha=(1.5, 1.5), p=(0.5, 0.5), g=(1, 1),
+                   D=((0.01, 0.5), (0.5, 0.01)), u=(0, 0), s_free=(1.0, 1.0))
+    assert L._lib.lbm_frac_matrix(ctypes.byref(L.params_from_problem(pb)), 0, ptr) == L.LBM_EINVAL
+    pb = W.Problem(d=2, collision="mrt", grid=(8, 8), alpha=(1.5, 1.5), p=(0.5, 0.5), g=(1, 1),
+                   D=((0.01, 0.0), (0.0, 0.01)), u=(0, 0), s_free=(2.5, 1.0))
+    assert L._lib.lbm_frac_matrix(ctypes.byref(L.params_from_problem(pb)), 0, ptr) == L.LBM_EINVAL

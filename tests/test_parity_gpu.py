@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L2 over all nodes): 1e-12 for the FP64 path; for the FP32
+collision forms 1e-5 on the named workloads and, on random cases, the bound
+``fp32_tol`` derived from the FP32 arithmetic and the problem's conditioning.  Sizes span several CTA tiles (32x8 in 2-D, 32x4x2 in
+3-D) and GEMM tiles (64x64) with ragged tails, plus the minimum grid of 3
+nodes per axis.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lbm_oracle as O
+from paper_1706_09161_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1706_09161_gb300 import build
+    build.build()
+    from paper_1706_09161_gb300 import lbm
+    return lbm
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _fp32_rerun(pb, C0, n):
+    """The oracle's stage functions re-run on float32 tensors: the error FP32 arithmetic
+    itself incurs on this problem (no GPU code involved)."""
+    ops = O.Operators(pb)
+    Om = ops.Omega.float()
+    K = [k.float() for k in ops.K]
+    ops.w, ops.e, ops.u = ops.w.float(), ops.e.float(), ops.u.float()
+    C = torch.tensor(C0).float()
+    f = O.equilibrium(ops, C, [O.apply_along_axis(K[mu], C, mu) for mu in range(pb.d)])
+    unknown = O.unknown_mask(ops)
+    k = unknown.sum(0).float().clamp(min=1.0)
+    for _ in range(n):
+        C = f.sum(0)
+        feq = O.equilibrium(ops, C, [O.apply_along_axis(K[mu], C, mu) for mu in range(pb.d)])
+        fn = O.stream(ops, f - torch.einsum("ij,j...->i...", Om, f - feq))
+        known = torch.where(unknown, torch.zeros(()), fn).sum(0)
+        f = torch.where(unknown, ((float(pb.C_wall) - known) / k).unsqueeze(0).expand_as(fn), fn)
+    return f.sum(0).double().numpy()
+
+
+def fp32_tol(pb, C0, n):
+    """Relative-L2 bound for the FP32 forms on random cases: 10x the error that FP32
+    arithmetic itself makes on the same problem (problems with F >> C, alpha near 1,
+    cancel strongly in the rest population), never below 1e-5."""
+    ref = O.run_C(pb, C0, n).numpy()
+    return max(1e-5, 10.0 * rel_l2(_fp32_rerun(pb, C0, n), ref))
+
+
+def oracle_run(pb, C0, n):
+    ops = O.Operators(pb)
+    f = O.init_populations(ops, torch.tensor(C0))
+    for _ in range(n):
+        f = O.step(ops, f)
+    return f.numpy(), O.concentration(f).numpy()
+
+
+GRIDS_2D = [(3, 3), (37, 29), (70, 65), (129, 17)]
+GRIDS_3D = [(3, 3, 3), (19, 13, 11), (40, 9, 6)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("grid", GRIDS_2D + GRIDS_3D)
+def test_fractional_terms(L, precision, grid):
+    """Loop item 1 (Section 2.4): F_mu of the initial concentration."""
+    rng = np.random.default_rng(len(grid) * 100 + grid[0])
+    d = len(grid)
+    pb = W.random_problem(rng, d, "mrt", grid)
+    C0 = W.random_field(rng, grid)
+    ops = O.Operators(pb)
+    C = O.concentration(O.init_populations(ops, torch.tensor(C0)))
+    F = O.fractional_terms(ops, C)
+    with L.Lattice(pb, C0, precision) as lat:
+        for mu in range(d):
+            got = lat.F(mu)
+            assert rel_l2(got, F[mu].numpy()) < (1e-13 if precision == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("collision", ["bgk", "mrt"])
+@pytest.mark.parametrize("grid", GRIDS_2D + GRIDS_3D)
+def test_steps_match_oracle(L, precision, collision, grid):
+    """Algorithm 1 loop items 1-5, 12 steps: concentration and populations."""
+    rng = np.random.default_rng(7 + len(grid) * 10 + grid[0])
+    d = len(grid)
+    pb = W.random_problem(rng, d, collision, grid, spherical=(collision == "bgk"))
+    C0 = W.random_field(rng, grid)
+    n = 12
+    f_ref, C_ref = oracle_run(pb, C0, n)
+    with L.Lattice(pb, C0, precision) as lat:
+        lat.step(n)
+        C = lat.C()
+        f = lat.f()
+    tol = TOL["fp64"] if precision == "fp64" else fp32_tol(pb, C0, n)
+    assert rel_l2(C, C_ref) < tol
+    assert rel_l2(f, f_ref) < tol * 10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_nonzero_wall_value_and_corners(L, precision):
+    """Eq. (Dirichlet_BC) with C_wall != 0: wall nodes hold C_wall, corners included."""
+    rng = np.random.default_rng(11)
+    for grid in [(21, 10), (11, 9, 7)]:
+        pb = dataclasses.replace(W.random_problem(rng, len(grid), "mrt", grid), C_wall=0.03)
+        C0 = W.random_field(rng, grid)
+        _, C_ref = oracle_run(pb, C0, 9)
+        with L.Lattice(pb, C0, precision) as lat:
+            lat.step(9)
+            C = lat.C()
+        tol = TOL["fp64"] if precision == "fp64" else fp32_tol(pb, C0, 9)
+        assert rel_l2(C, C_ref) < tol
+        mask = np.ones_like(C, dtype=bool)
+        mask[tuple(slice(1, -1) for _ in grid)] = False
+        assert np.max(np.abs(C[mask] - 0.03)) < (1e-15 if precision == "fp64" else 1e-8)
+
+
+def test_config_fp64_bgk_64(L):
+    """2-D BGK 64x64 FP64, alpha = 1.7, 200 steps: 1e-12 relative L2 to the oracle."""
+    pb, C0, n = W.fp64_bgk_64()
+    _, C_ref = oracle_run(pb, C0, n)
+    with L.Lattice(pb, C0, "fp64") as lat:
+        lat.step(n)
+        C = lat.C()
+        mass = lat.mass()
+    assert rel_l2(C, C_ref) < 1e-12
+    assert mass == pytest.approx(float(C_ref.sum()), rel=1e-12)
+
+
+def test_config_mrt_512_full_size_prefix(L):
+    """The 512x512 anisotropic MRT workload at full size, in the launch configuration the
+    benchmark times, against the oracle over its first 60 steps (FP32 collision)."""
+    pb, C0, _ = W.mrt_aniso_512()
+    n = 60
+    _, C_ref = oracle_run(pb, C0, n)
+    with L.Lattice(pb, C0, "fp32") as lat:
+        lat.step(n)
+        C = lat.C()
+    assert rel_l2(C, C_ref) < 1e-5
+
+
+def test_graph_replay_equals_single_steps(L):
+    """Graph-captured replay (32-step graphs) and one-step launches give identical results."""
+    rng = np.random.default_rng(5)
+    pb = W.random_problem(rng, 2, "mrt", (50, 45))
+    C0 = W.random_field(rng, pb.grid)
+    with L.Lattice(pb, C0, "fp32") as a, L.Lattice(pb, C0, "fp32") as b:
+        a.step(71)
+        for _ in range(71):
+            b.step(1)
+        assert np.array_equal(a.C(), b.C())
+
+
+def test_mrt_equal_rates_equals_bgk_on_gpu(L):
+    pb = W.Problem(d=2, collision="bgk", grid=(40, 33), alpha=(1.4, 1.8), p=(0.2, 0.6), g=(1, 1),
+                   D=((0.02, 0), (0, 0.02)), u=(0.03, -0.02))
+    lam = 0.02 * 3 + 0.5
+    pbm = dataclasses.replace(pb, collision="mrt", s_free=(1 / lam, 1 / lam))
+    C0 = W.random_field(np.random.default_rng(3), pb.grid)
+    with L.Lattice(pb, C0, "fp64") as a, L.Lattice(pbm, C0, "fp64") as b:
+        a.step(20)
+        b.step(20)
+        assert rel_l2(a.C(), b.C()) < 1e-13
+
+
+def test_mass_reduction(L):
+    rng = np.random.default_rng(9)
+    pb = W.random_problem(rng, 3, "mrt", (33, 17, 9))
+    C0 = W.random_field(rng, pb.grid)
+    with L.Lattice(pb, C0, "fp64") as lat:
+        lat.step(5)
+        C = lat.C()
+        assert lat.mass() == pytest.approx(float(C.sum()), rel=1e-14)
+
+
+def test_write_read_populations_and_set_C(L):
+    rng = np.random.default_rng(12)
+    pb = W.random_problem(rng, 2, "bgk", (23, 19), spherical=True)
+    C0 = W.random_field(rng, pb.grid)
+    with L.Lattice(pb, C0, "fp64") as lat:
+        f = rng.uniform(0, 0.1, size=(5,) + pb.shape)
+        lat.write_f(f)
+        assert np.array_equal(lat.f(), f)
+        assert np.allclose(lat.C(), f.sum(0), rtol=1e-15, atol=1e-17)
+        lat.set_C(C0)
+        f_ref, _ = oracle_run(pb, C0, 0)
+        assert rel_l2(lat.f(), f_ref) < 1e-14
+
+
+def test_unstable_run_reports_error(L):
+    """BGK at lambda ~ 1/2 with strong advection overflows FP32 within ~150 steps
+    (E4-style instability, Section 3.3); the non-finite concentration is latched and
+    returned by the next synchronising call."""
+    pb = W.Problem(d=2, collision="bgk", grid=(48, 24), alpha=(1.5, 1.5), p=(0.5, 0.5), g=(1, 1),
+                   D=((1e-3, 0), (0, 1e-3)), u=(0.6, 0.0))
+    with L.Lattice(pb, W.gaussian_pulse(pb.grid, 2.0), "fp32") as lat:
+        lat.step(400)
+        assert L.lbm_sync(lat.h) == L.LBM_ERR_UNSTABLE
+        with pytest.raises(L.LBMError):
+            lat.C()
+
+
+def test_zero_steps_is_noop(L):
+    rng = np.random.default_rng(1)
+    pb = W.random_problem(rng, 2, "mrt", (10, 10))
+    C0 = W.random_field(rng, pb.grid)
+    with L.Lattice(pb, C0, "fp64") as lat:
+        before = lat.f()
+        lat.step(0)
+        assert np.array_equal(lat.f(), before)
