@@ -28,8 +28,8 @@
  *
  * Errors: every function returns 0 (LBM_OK) or a negative code; nothing aborts
  * the process.  Launches are asynchronous on the handle's stream; errors raised
- * on the device (non-finite concentration) are latched and returned by the next
- * synchronising call (lbm_sync, lbm_read_*, lbm_mass).
+ * on the device (non-finite concentration, a bounded wait that gave up) are latched
+ * and returned by the next synchronising call (lbm_sync, lbm_read_*, lbm_mass).
  */
 #ifndef LBM_FADE_H
 #define LBM_FADE_H
@@ -44,6 +44,7 @@ extern "C" {
 #define LBM_ECUDA        -3  /* a CUDA runtime call failed (message via lbm_last_cuda_error) */
 #define LBM_ERR_UNSTABLE -4  /* a non-finite concentration appeared during lbm_step */
 #define LBM_ENOTSUP      -5  /* combination not supported by this build */
+#define LBM_ERR_TIMEOUT  -6  /* a bounded device-side wait (tensor-core pipeline) gave up */
 
 typedef struct lbm_s* lbm_t;
 

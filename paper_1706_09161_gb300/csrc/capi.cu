@@ -182,6 +182,7 @@ void free_all(lbm_s* h) {
     h->graph_exec[i] = nullptr;
     h->graph[i] = nullptr;
   }
+  lbm::tc_release(h);
   void* ptrs[] = {h->dev.f[0], h->dev.f[1], h->dev.C, h->dev.C0, h->dev.F, h->dev.K, h->dev.KT, h->dev.stage,
                   h->dev.partials, h->dev.scalar, h->dev.flag, h->dev.Khi, h->dev.Klo, h->dev.Chi, h->dev.Clo};
   for (void* p : ptrs)
@@ -196,19 +197,28 @@ int alloc_bytes(void** p, size_t bytes) {
   return LBM_OK;
 }
 
-// F = fractional terms of the current C (Algorithm 1, loop item 1)
+bool uses_tc(const lbm_s* h) { return h->tc != nullptr; }
+
+// F = fractional terms of the current C (Algorithm 1, loop item 1).  On the tensor-core
+// path the hi/lo split of C is refreshed first (inside the time loop the fused
+// collide-stream kernel writes it, so one_step skips this).
 int run_frac(lbm_s* h, cudaStream_t s) {
-  if (h->prm.precision == LBM_FP64 || h->prm.precision == LBM_FP32) {
+  if (!uses_tc(h)) {
     LBM_CUDA(lbm::launch_frac_simt(h, h->dev.C, h->dev.F, s));
   } else {
+    LBM_CUDA(lbm::launch_split_C(h, s));
     LBM_CUDA(lbm::launch_frac_tc(h, s));
   }
   return LBM_OK;
 }
 
 int one_step(lbm_s* h, int& cur, cudaStream_t s) {
-  int rc = run_frac(h, s);
-  if (rc) return rc;
+  if (uses_tc(h)) {
+    LBM_CUDA(lbm::launch_frac_tc(h, s));
+  } else {
+    int rc = run_frac(h, s);
+    if (rc) return rc;
+  }
   LBM_CUDA(lbm::launch_collide_stream(h, h->dev.f[cur], h->dev.f[cur ^ 1], h->dev.C, s));
   cur ^= 1;
   return LBM_OK;
@@ -220,6 +230,7 @@ int init_from_C(lbm_s* h) {
   if (rc) return rc;
   LBM_CUDA(lbm::launch_init_equilibrium(h, h->dev.f[h->cur], h->stream));
   LBM_CUDA(lbm::launch_moment(h, h->dev.f[h->cur], h->dev.C, h->stream));
+  if (uses_tc(h)) LBM_CUDA(lbm::launch_split_C(h, h->stream));
   return LBM_OK;
 }
 
@@ -227,6 +238,7 @@ int latched(lbm_s* h) {
   int flag = 0;
   LBM_CUDA(cudaMemcpyAsync(&flag, h->dev.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (flag & 2) return LBM_ERR_TIMEOUT;
   return (flag & 1) ? LBM_ERR_UNSTABLE : LBM_OK;
 }
 
@@ -298,6 +310,7 @@ int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t
   if (cudaMemsetAsync(h->dev.flag, 0, sizeof(int), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
 
   // weight matrices K_mu (Section 2.4) in FP64 on the host, then the working precision
+  std::vector<std::vector<double>> Kall;
   {
     std::vector<double> K, KT;
     long long off = 0;
@@ -317,12 +330,15 @@ int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       if (e != cudaSuccess) return fail(record_cuda(e, "weight upload"));
       off += (long long)cnt;
+      Kall.push_back(K);
     }
   }
   if (prm->precision == LBM_FP32_BF16SPLIT || prm->precision == LBM_FP32_TF32SPLIT) {
-    return fail(LBM_ENOTSUP);
+    if ((rc = lbm::tc_prepare(h, Kall))) return fail(rc);
+    h->launches_per_step = 2;
+  } else {
+    h->launches_per_step = h->d + 1;
   }
-  h->launches_per_step = h->d + 1;
   *out = h;
   rc = lbm_set_C(h, C0_host);
   if (rc) {
@@ -355,7 +371,10 @@ int lbm_profile(lbm_t h, int nsteps, double* ms) {
   int rc = LBM_OK;
   for (int k = 0; k < nsteps && rc == LBM_OK; ++k) {
     cudaError_t e = cudaEventRecord(ev[0], h->stream);
-    if (e == cudaSuccess) rc = run_frac(h, h->stream);
+    if (e == cudaSuccess) {
+      if (uses_tc(h)) e = lbm::launch_frac_tc(h, h->stream);
+      else rc = run_frac(h, h->stream);
+    }
     if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[1], h->stream);
     if (e == cudaSuccess && rc == LBM_OK)
       e = lbm::launch_collide_stream(h, h->dev.f[h->cur], h->dev.f[h->cur ^ 1], h->dev.C, h->stream);
@@ -482,6 +501,7 @@ const char* lbm_strerror(int code) {
     case LBM_ECUDA: return "CUDA runtime error";
     case LBM_ERR_UNSTABLE: return "non-finite concentration (numerical instability)";
     case LBM_ENOTSUP: return "not supported by this build";
+    case LBM_ERR_TIMEOUT: return "a bounded device-side wait gave up";
     default: return "unknown error";
   }
 }

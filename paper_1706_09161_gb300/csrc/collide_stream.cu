@@ -67,10 +67,38 @@ __device__ __forceinline__ int ex_of(int q) { return q == 1 ? 1 : (q == 2 ? -1 :
 __device__ __forceinline__ int ey_of(int q) { return q == 3 ? 1 : (q == 4 ? -1 : 0); }
 __device__ __forceinline__ int ez_of(int q) { return q == 5 ? 1 : (q == 6 ? -1 : 0); }
 
-template <typename real, int D, bool MRT>
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Operands of the split-precision fractional operator: C = hi + lo (+ residual), with
+// hi, lo in bf16 (SPLIT = 1) or tf32 (SPLIT = 2), x-pitch ldp.
+struct SplitOut {
+  void* hi;
+  void* lo;
+  int ldp;
+};
+
+template <int SPLIT, typename real>
+__device__ __forceinline__ void write_split(const SplitOut& so, long long o, real C) {
+  const float c = static_cast<float>(C);
+  if (SPLIT == 1) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(c);
+    static_cast<__nv_bfloat16*>(so.hi)[o] = h;
+    static_cast<__nv_bfloat16*>(so.lo)[o] = __float2bfloat16_rn(c - __bfloat162float(h));
+  } else if (SPLIT == 2) {
+    const float h = tf32_rna(c);
+    static_cast<float*>(so.hi)[o] = h;
+    static_cast<float*>(so.lo)[o] = tf32_rna(c - h);
+  }
+}
+
+template <typename real, int D, bool MRT, int SPLIT>
 __global__ void __launch_bounds__(256)
 collide_stream_kernel(StepParams sp, const real* __restrict__ f_in, const real* __restrict__ F,
-                      real* __restrict__ f_out, real* __restrict__ C_out, int* __restrict__ flag) {
+                      real* __restrict__ f_out, real* __restrict__ C_out, int* __restrict__ flag, SplitOut so) {
   constexpr int Q = Lat<D>::Q;
   constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
   constexpr int EX = TX + 2, EY = TY + 2, EZ = (D == 3) ? TZ + 2 : 1;
@@ -140,6 +168,7 @@ collide_stream_kernel(StepParams sp, const real* __restrict__ f_in, const real* 
 #pragma unroll
     for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
     C_out[node] = C;
+    if (SPLIT) write_split<SPLIT>(so, ((long long)gz * n1 + gy) * so.ldp + gx, C);
     if (!isfinite(static_cast<double>(C))) atomicOr(flag, 1);
   }
 }
@@ -186,9 +215,18 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
   constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
   const StepParams& sp = h->sp;
   dim3 grid((sp.n[0] + TX - 1) / TX, (sp.n[1] + TY - 1) / TY, (sp.n[2] + TZ - 1) / TZ);
-  collide_stream_kernel<real, D, MRT><<<grid, 256, 0, s>>>(
-      sp, static_cast<const real*>(f_in), static_cast<const real*>(h->dev.F), static_cast<real*>(f_out),
-      static_cast<real*>(C_out), h->dev.flag);
+  SplitOut so{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
+  const int split = (h->tc == nullptr) ? 0 : (h->prm.precision == LBM_FP32_BF16SPLIT ? 1 : 2);
+  const real* fi = static_cast<const real*>(f_in);
+  const real* F = static_cast<const real*>(h->dev.F);
+  real* fo = static_cast<real*>(f_out);
+  real* Co = static_cast<real*>(C_out);
+  if (split == 0)
+    collide_stream_kernel<real, D, MRT, 0><<<grid, 256, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so);
+  else if (split == 1)
+    collide_stream_kernel<real, D, MRT, 1><<<grid, 256, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so);
+  else
+    collide_stream_kernel<real, D, MRT, 2><<<grid, 256, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so);
   return cudaGetLastError();
 }
 

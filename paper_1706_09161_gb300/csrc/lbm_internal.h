@@ -3,12 +3,14 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 #include "lbm_fade.h"
 
 namespace lbm {
 
 constexpr int kMaxQ = 7;
+struct TcPlan;  // tensor-core plan (frac_tc.cu)
 
 // Per-problem constants of one time step, passed by value to the kernels.
 // Derived on the host in FP64 from lbm_params (Algorithm 1, initialisation).
@@ -58,6 +60,7 @@ struct lbm_s {
   int graph_steps = 0;                 // steps per captured graph (even)
   int launches_per_step = 0;
   int device = 0;
+  lbm::TcPlan* tc = nullptr;           // split-precision tensor-core operator, if used
 };
 
 namespace lbm {
@@ -68,7 +71,8 @@ cudaError_t launch_frac_simt(const lbm_s* h, const void* C, void* F, cudaStream_
 // tensor-core split-precision fractional operator (tcgen05); returns
 // cudaErrorNotSupported when the handle's shape is not covered
 cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s);
-// fused equilibrium + collision + streaming + Dirichlet + new concentration
+// fused equilibrium + collision + streaming + Dirichlet + new concentration; on the
+// tensor-core path it also writes the hi/lo split of the new concentration
 cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out, void* C_out,
                                   cudaStream_t s);
 // f = feq(C, F)
@@ -83,6 +87,10 @@ cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
 // split C into hi/lo operands for the tensor-core path
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s);
 int reduce_blocks_for(long long n);
+// tensor-core plan: split K_mu (row-major FP64 per axis), allocate split C, encode TMA maps
+int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K);
+void tc_release(lbm_s* h);
+int tc_split_pitch(const lbm_s* h);
 
 // host-side weight build (FP64), K row-major [n][l] for one axis
 void build_frac_matrix(double alpha, double p, double scale_g, int side, double dx, double* K);

@@ -22,6 +22,7 @@ LBM_ENOMEM = -2
 LBM_ECUDA = -3
 LBM_ERR_UNSTABLE = -4
 LBM_ENOTSUP = -5
+LBM_ERR_TIMEOUT = -6
 
 LBM_D2Q5, LBM_D3Q7 = 0, 1
 LBM_BGK, LBM_MRT = 0, 1

@@ -1,0 +1,71 @@
+"""Error bounds derived from the arithmetic of each precision form.
+
+The scheme is re-run on the CPU with the oracle's own stage functions, on
+float32 tensors, with the fractional operator's operands rounded exactly as a
+precision form rounds them (none, bf16 hi+lo, tf32 hi+lo; three products,
+lo*lo dropped).  Its distance to the FP64 oracle is the error that arithmetic
+itself makes on the problem; the GPU result must stay within a small multiple
+of it.  No GPU code is involved.
+"""
+import numpy as np
+import torch
+
+from oracle import lbm_oracle as O
+
+
+def _round_tf32(x: torch.Tensor) -> torch.Tensor:
+    """Round float32 to tf32 (10 explicit mantissa bits), ties away from zero."""
+    b = x.float().contiguous().view(torch.int32)
+    b = (b + 0x1000) & ~0x1FFF
+    return b.view(torch.float32)
+
+
+def _split(x: torch.Tensor, kind: str):
+    x = x.float()
+    if kind == "bf16split":
+        hi = x.to(torch.bfloat16).float()
+        lo = (x - hi).to(torch.bfloat16).float()
+    else:
+        hi = _round_tf32(x)
+        lo = _round_tf32(x - hi)
+    return hi, lo
+
+
+def _frac(K, C, mu, kind):
+    if kind in ("fp32", None):
+        return O.apply_along_axis(K, C, mu)
+    Kh, Kl = _split(K, kind)
+    Ch, Cl = _split(C, kind)
+    return (O.apply_along_axis(Kh, Ch, mu) + O.apply_along_axis(Kh, Cl, mu) + O.apply_along_axis(Kl, Ch, mu))
+
+
+def rerun(pb, C0, n, kind="fp32"):
+    """Concentration after n steps with FP32 collision and the given operator rounding."""
+    ops = O.Operators(pb)
+    Om = ops.Omega.float()
+    K = [k.float() for k in ops.K]
+    ops.w, ops.e, ops.u = ops.w.float(), ops.e.float(), ops.u.float()
+    C = torch.tensor(C0).float()
+    f = O.equilibrium(ops, C, [_frac(K[mu], C, mu, kind) for mu in range(pb.d)])
+    C = f.sum(0)
+    unknown = O.unknown_mask(ops)
+    k = unknown.sum(0).float().clamp(min=1.0)
+    for _ in range(n):
+        C = f.sum(0)
+        feq = O.equilibrium(ops, C, [_frac(K[mu], C, mu, kind) for mu in range(pb.d)])
+        fn = O.stream(ops, f - torch.einsum("ij,j...->i...", Om, f - feq))
+        known = torch.where(unknown, torch.zeros(()), fn).sum(0)
+        f = torch.where(unknown, ((float(pb.C_wall) - known) / k).unsqueeze(0).expand_as(fn), fn)
+    return f.sum(0).double().numpy()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def bound(pb, C0, n, kind="fp32", factor=10.0, floor=1e-5):
+    """max(floor, factor x the error the form's arithmetic makes on this problem)."""
+    ref = O.run_C(pb, C0, n).numpy()
+    return max(floor, factor * rel_l2(rerun(pb, C0, n, kind), ref))

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import arith_bounds
 from oracle import lbm_oracle as O
 from paper_1706_09161_gb300 import workloads as W
 
@@ -36,32 +37,11 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _fp32_rerun(pb, C0, n):
-    """The oracle's stage functions re-run on float32 tensors: the error FP32 arithmetic
-    itself incurs on this problem (no GPU code involved)."""
-    ops = O.Operators(pb)
-    Om = ops.Omega.float()
-    K = [k.float() for k in ops.K]
-    ops.w, ops.e, ops.u = ops.w.float(), ops.e.float(), ops.u.float()
-    C = torch.tensor(C0).float()
-    f = O.equilibrium(ops, C, [O.apply_along_axis(K[mu], C, mu) for mu in range(pb.d)])
-    unknown = O.unknown_mask(ops)
-    k = unknown.sum(0).float().clamp(min=1.0)
-    for _ in range(n):
-        C = f.sum(0)
-        feq = O.equilibrium(ops, C, [O.apply_along_axis(K[mu], C, mu) for mu in range(pb.d)])
-        fn = O.stream(ops, f - torch.einsum("ij,j...->i...", Om, f - feq))
-        known = torch.where(unknown, torch.zeros(()), fn).sum(0)
-        f = torch.where(unknown, ((float(pb.C_wall) - known) / k).unsqueeze(0).expand_as(fn), fn)
-    return f.sum(0).double().numpy()
-
-
 def fp32_tol(pb, C0, n):
     """Relative-L2 bound for the FP32 forms on random cases: 10x the error that FP32
     arithmetic itself makes on the same problem (problems with F >> C, alpha near 1,
     cancel strongly in the rest population), never below 1e-5."""
-    ref = O.run_C(pb, C0, n).numpy()
-    return max(1e-5, 10.0 * rel_l2(_fp32_rerun(pb, C0, n), ref))
+    return arith_bounds.bound(pb, C0, n, "fp32")
 
 
 def oracle_run(pb, C0, n):

@@ -1,0 +1,102 @@
+"""GPU parity of the tensor-core (tcgen05) split-precision forms against the FP64 oracle.
+
+The fractional operator runs as a split-precision GEMM (bf16 or tf32 hi+lo parts,
+three products, FP32 accumulation).  Bounds: the operator alone is compared with a
+fixed relative-L2 bound from the split's rounding (bf16: 2^-16 per part, tf32:
+2^-22); whole steps use ``arith_bounds.bound``, i.e. 10x the error the same
+arithmetic makes when re-run on the CPU, never below 1e-5.
+Sizes cover one and several 128-line / 64-column tiles, ragged tails, the
+minimum grid, and the 512x512 workload.
+"""
+import numpy as np
+import pytest
+import torch
+
+import arith_bounds
+from oracle import lbm_oracle as O
+from paper_1706_09161_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = {"bf16split": 4e-5}
+KINDS = ["bf16split"]
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1706_09161_gb300 import build
+    build.build()
+    from paper_1706_09161_gb300 import lbm
+    return lbm
+
+
+rel_l2 = arith_bounds.rel_l2
+
+GRIDS = [(3, 3), (37, 29), (130, 70), (200, 131), (19, 13, 11), (40, 9, 6), (131, 20, 9)]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("grid", GRIDS)
+def test_tc_fractional_terms(L, kind, grid):
+    """Loop item 1 (Section 2.4) on the tensor cores, every axis."""
+    rng = np.random.default_rng(31 + grid[0] + len(grid))
+    d = len(grid)
+    pb = W.random_problem(rng, d, "mrt", grid)
+    C0 = W.random_field(rng, grid)
+    ops = O.Operators(pb)
+    C = O.concentration(O.init_populations(ops, torch.tensor(C0)))
+    F = O.fractional_terms(ops, C)
+    with L.Lattice(pb, C0, kind) as lat:
+        for mu in range(d):
+            assert rel_l2(lat.F(mu), F[mu].numpy()) < F_TOL[kind], f"axis {mu}"
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("grid", [(37, 29), (130, 70), (19, 13, 11)])
+@pytest.mark.parametrize("collision", ["bgk", "mrt"])
+def test_tc_steps_match_oracle(L, kind, grid, collision):
+    rng = np.random.default_rng(53 + grid[0])
+    pb = W.random_problem(rng, len(grid), collision, grid, spherical=(collision == "bgk"))
+    C0 = W.random_field(rng, grid)
+    n = 12
+    C_ref = O.run_C(pb, C0, n).numpy()
+    with L.Lattice(pb, C0, kind) as lat:
+        lat.step(n)
+        C = lat.C()
+    assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, n, kind)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_tc_config_mrt_512_full_size(L, kind):
+    """512x512 anisotropic MRT workload, full size, the benchmark's launch configuration,
+    first 60 steps against the oracle."""
+    pb, C0, _ = W.mrt_aniso_512()
+    n = 60
+    C_ref = O.run_C(pb, C0, n).numpy()
+    with L.Lattice(pb, C0, kind) as lat:
+        lat.step(n)
+        C = lat.C()
+    assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, n, kind)
+
+
+def test_tc_graph_replay_deterministic(L):
+    rng = np.random.default_rng(77)
+    pb = W.random_problem(rng, 2, "mrt", (150, 140))
+    C0 = W.random_field(rng, pb.grid)
+    with L.Lattice(pb, C0, "bf16split") as a, L.Lattice(pb, C0, "bf16split") as b:
+        a.step(70)
+        for _ in range(70):
+            b.step(1)
+        assert np.array_equal(a.C(), b.C())
+        assert L.lbm_sync(a.h) == 0
+
+
+def test_tf32split_is_refused(L):
+    """The tf32 split is not offered for the full step (its MN-major operand form is not built)."""
+    rng = np.random.default_rng(3)
+    pb = W.random_problem(rng, 2, "mrt", (20, 20))
+    with pytest.raises(L.LBMError) as ei:
+        L.Lattice(pb, W.random_field(rng, pb.grid), "tf32split")
+    assert ei.value.code == L.LBM_ENOTSUP
