@@ -197,6 +197,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=40, help="lattice steps per reference-arm bench step")
     ap.add_argument("--cpu-sample", type=int, default=800, help="lattice steps of the cpu_baseline leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattice-steps", type=int, default=None,
+                    help="override the workload's lattice steps per bench step (profiling runs only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -221,6 +223,8 @@ def main():
     from paper_1706_09161_gb300 import lbm
 
     pb, C0, nlbm = make_workload(args.workload)
+    if args.lattice_steps:
+        nlbm = args.lattice_steps
     precision = args.precision or WORKLOADS[args.workload]["default_precision"]
     lat = lbm.Lattice(pb, C0, precision)
     stream = torch.cuda.ExternalStream(lat.stream)

@@ -25,9 +25,35 @@ template <int D> struct Lat;
 template <> struct Lat<2> { static constexpr int Q = 5; };
 template <> struct Lat<3> { static constexpr int Q = 7; };
 
+// Per-step constants in the working precision (no FP64 arithmetic per node on the
+// FP32 forms; GB300's FP64 rate is a small fraction of its FP32 rate).
+template <typename real>
+struct KConst {
+  int n[3];
+  long long nodes;
+  real omega[kMaxQ][kMaxQ];
+  real w0, wi;
+  real advw[3];  // (dt/dx) u_mu w_i / e^2
+  real C_wall;
+};
+
+template <typename real>
+KConst<real> make_const(const StepParams& sp) {
+  KConst<real> k{};
+  for (int i = 0; i < 3; ++i) k.n[i] = sp.n[i];
+  k.nodes = sp.nodes;
+  for (int i = 0; i < kMaxQ; ++i)
+    for (int j = 0; j < kMaxQ; ++j) k.omega[i][j] = static_cast<real>(sp.omega[i][j]);
+  k.w0 = static_cast<real>(sp.w0);
+  k.wi = static_cast<real>(sp.wi);
+  for (int i = 0; i < 3; ++i) k.advw[i] = static_cast<real>(sp.adv[i] * sp.wi);
+  k.C_wall = static_cast<real>(sp.C_wall);
+  return k;
+}
+
 // Equilibrium and collision of one node.  f: populations (in), fs: post-collision (out).
 template <typename real, int D, bool MRT>
-__device__ __forceinline__ void collide_node(const StepParams& sp, const real* f, const real* F, real* fs) {
+__device__ __forceinline__ void collide_node(const KConst<real>& sp, const real* f, const real* F, real* fs) {
   constexpr int Q = Lat<D>::Q;
   real C = f[0];
 #pragma unroll
@@ -36,16 +62,16 @@ __device__ __forceinline__ void collide_node(const StepParams& sp, const real* f
 #pragma unroll
   for (int mu = 1; mu < D; ++mu) sumF += F[mu];
   real feq[Q];
-  feq[0] = C - static_cast<real>(sp.w0) * sumF;
+  feq[0] = C - sp.w0 * sumF;
 #pragma unroll
   for (int mu = 0; mu < D; ++mu) {
-    const real a = static_cast<real>(sp.wi) * F[mu];
-    const real b = static_cast<real>(sp.adv[mu] * sp.wi) * C;
+    const real a = sp.wi * F[mu];
+    const real b = sp.advw[mu] * C;
     feq[2 * mu + 1] = a + b;
     feq[2 * mu + 2] = a - b;
   }
   if (!MRT) {
-    const real om = static_cast<real>(sp.omega[0][0]);
+    const real om = sp.omega[0][0];
 #pragma unroll
     for (int q = 0; q < Q; ++q) fs[q] = f[q] - om * (f[q] - feq[q]);
   } else {
@@ -54,9 +80,9 @@ __device__ __forceinline__ void collide_node(const StepParams& sp, const real* f
     for (int q = 0; q < Q; ++q) dl[q] = f[q] - feq[q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      real acc = static_cast<real>(sp.omega[i][0]) * dl[0];
+      real acc = sp.omega[i][0] * dl[0];
 #pragma unroll
-      for (int j = 1; j < Q; ++j) acc += static_cast<real>(sp.omega[i][j]) * dl[j];
+      for (int j = 1; j < Q; ++j) acc += sp.omega[i][j] * dl[j];
       fs[i] = f[i] - acc;
     }
   }
@@ -97,7 +123,7 @@ __device__ __forceinline__ void write_split(const SplitOut& so, long long o, rea
 
 template <typename real, int D, bool MRT, int SPLIT>
 __global__ void __launch_bounds__(256)
-collide_stream_kernel(StepParams sp, const real* __restrict__ f_in, const real* __restrict__ F,
+collide_stream_kernel(const KConst<real> sp, const real* __restrict__ f_in, const real* __restrict__ F,
                       real* __restrict__ f_out, real* __restrict__ C_out, int* __restrict__ flag, SplitOut so) {
   constexpr int Q = Lat<D>::Q;
   constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
@@ -157,7 +183,7 @@ collide_stream_kernel(StepParams sp, const real* __restrict__ f_in, const real* 
     real C = sum_known;
     if (n_unknown > 0) {
       // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
-      const real fill = (static_cast<real>(sp.C_wall) - sum_known) / static_cast<real>(n_unknown);
+      const real fill = (sp.C_wall - sum_known) / static_cast<real>(n_unknown);
 #pragma unroll
       for (int q = 0; q < Q; ++q)
         if (!known[q]) fv[q] = fill;
@@ -169,12 +195,12 @@ collide_stream_kernel(StepParams sp, const real* __restrict__ f_in, const real* 
     for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
     C_out[node] = C;
     if (SPLIT) write_split<SPLIT>(so, ((long long)gz * n1 + gy) * so.ldp + gx, C);
-    if (!isfinite(static_cast<double>(C))) atomicOr(flag, 1);
+    if (!isfinite(C)) atomicOr(flag, 1);
   }
 }
 
 template <typename real, int D>
-__global__ void init_equilibrium_kernel(StepParams sp, const real* __restrict__ C, const real* __restrict__ F,
+__global__ void init_equilibrium_kernel(const KConst<real> sp, const real* __restrict__ C, const real* __restrict__ F,
                                         real* __restrict__ f) {
   constexpr int Q = Lat<D>::Q;
   const long long nodes = sp.nodes;
@@ -188,11 +214,11 @@ __global__ void init_equilibrium_kernel(StepParams sp, const real* __restrict__ 
       Fv[mu] = F[mu * nodes + i];
       sumF += Fv[mu];
     }
-    f[i] = c - static_cast<real>(sp.w0) * sumF;
+    f[i] = c - sp.w0 * sumF;
 #pragma unroll
     for (int mu = 0; mu < D; ++mu) {
-      const real a = static_cast<real>(sp.wi) * Fv[mu];
-      const real b = static_cast<real>(sp.adv[mu] * sp.wi) * c;
+      const real a = sp.wi * Fv[mu];
+      const real b = sp.advw[mu] * c;
       f[(2 * mu + 1) * nodes + i] = a + b;
       f[(2 * mu + 2) * nodes + i] = a - b;
     }
@@ -213,7 +239,7 @@ __global__ void moment_kernel(long long nodes, const real* __restrict__ f, real*
 template <typename real, int D, bool MRT>
 cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s) {
   constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
-  const StepParams& sp = h->sp;
+  const KConst<real> sp = make_const<real>(h->sp);
   dim3 grid((sp.n[0] + TX - 1) / TX, (sp.n[1] + TY - 1) / TY, (sp.n[2] + TZ - 1) / TZ);
   SplitOut so{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
   const int split = (h->tc == nullptr) ? 0 : (h->prm.precision == LBM_FP32_BF16SPLIT ? 1 : 2);
@@ -256,14 +282,14 @@ cudaError_t launch_init_equilibrium(const lbm_s* h, void* f, cudaStream_t s) {
   const int g = grid_for(h->sp.nodes);
   if (h->elem == 8) {
     if (h->d == 2)
-      init_equilibrium_kernel<double, 2><<<g, 256, 0, s>>>(h->sp, (const double*)h->dev.C, (const double*)h->dev.F, (double*)f);
+      init_equilibrium_kernel<double, 2><<<g, 256, 0, s>>>(make_const<double>(h->sp), (const double*)h->dev.C, (const double*)h->dev.F, (double*)f);
     else
-      init_equilibrium_kernel<double, 3><<<g, 256, 0, s>>>(h->sp, (const double*)h->dev.C, (const double*)h->dev.F, (double*)f);
+      init_equilibrium_kernel<double, 3><<<g, 256, 0, s>>>(make_const<double>(h->sp), (const double*)h->dev.C, (const double*)h->dev.F, (double*)f);
   } else {
     if (h->d == 2)
-      init_equilibrium_kernel<float, 2><<<g, 256, 0, s>>>(h->sp, (const float*)h->dev.C, (const float*)h->dev.F, (float*)f);
+      init_equilibrium_kernel<float, 2><<<g, 256, 0, s>>>(make_const<float>(h->sp), (const float*)h->dev.C, (const float*)h->dev.F, (float*)f);
     else
-      init_equilibrium_kernel<float, 3><<<g, 256, 0, s>>>(h->sp, (const float*)h->dev.C, (const float*)h->dev.F, (float*)f);
+      init_equilibrium_kernel<float, 3><<<g, 256, 0, s>>>(make_const<float>(h->sp), (const float*)h->dev.C, (const float*)h->dev.F, (float*)f);
   }
   return cudaGetLastError();
 }
