@@ -45,6 +45,7 @@ extern "C" {
 #define LBM_ERR_UNSTABLE -4  /* a non-finite concentration appeared during lbm_step */
 #define LBM_ENOTSUP      -5  /* combination not supported by this build */
 #define LBM_ERR_TIMEOUT  -6  /* a bounded device-side wait (tensor-core pipeline) gave up */
+#define LBM_ETOOBIG      -7  /* input larger than a fixed-capacity (static) scratch area */
 
 typedef struct lbm_s* lbm_t;
 
@@ -147,6 +148,24 @@ int lbm_launches_per_step(lbm_t h, int* n);
  * K = g h dx^gamma / Gamma(2+gamma) * (p W+ + (1-p) W-) with gamma = 2 - alpha
  * (Eqs. 1Dminus_discret, c+, c-).  Needs no GPU. */
 int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host);
+
+/* FP64 sum of n device values (elem_bytes 4: float, 8: double) written to *sum_dev,
+ * a caller-owned device double, asynchronously on `stream` (NULL: legacy default).
+ * The paper has no counterpart: this is the lbm_mass reduction for callers that
+ * cannot allocate device memory -- plug-ins running inside a host framework that
+ * owns all GPU memory and hands out only pointers, and code that must not call
+ * cudaMalloc because an allocation can synchronise the device.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: its partial sums live in a
+ * static device array of 65,536 doubles (512 KiB) that every GPU which loads this
+ * library holds until the process exits.  n may be at most 67,108,864
+ * (65,536 partials of 1,024 elements); larger n returns LBM_ETOOBIG, n < 0 or a
+ * bad pointer / elem_bytes returns LBM_EINVAL.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array, which keeps the last call's partials: each call overwrites every
+ * partial it reads, and calls that overlap on the GPU (different streams, no
+ * ordering between them) race on it and must be serialised by the caller. */
+int lbm_mass_static(const void* x_dev, int elem_bytes, long long n, double* sum_dev, void* stream);
 
 /* Release every device buffer, graph and (if created by the handle) stream. */
 void lbm_destroy(lbm_t h);

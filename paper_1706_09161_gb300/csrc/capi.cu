@@ -502,6 +502,7 @@ const char* lbm_strerror(int code) {
     case LBM_ERR_UNSTABLE: return "non-finite concentration (numerical instability)";
     case LBM_ENOTSUP: return "not supported by this build";
     case LBM_ERR_TIMEOUT: return "a bounded device-side wait gave up";
+    case LBM_ETOOBIG: return "input exceeds the static scratch capacity";
     default: return "unknown error";
   }
 }

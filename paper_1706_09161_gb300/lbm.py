@@ -23,6 +23,7 @@ LBM_ECUDA = -3
 LBM_ERR_UNSTABLE = -4
 LBM_ENOTSUP = -5
 LBM_ERR_TIMEOUT = -6
+LBM_ETOOBIG = -7
 
 LBM_D2Q5, LBM_D3Q7 = 0, 1
 LBM_BGK, LBM_MRT = 0, 1
@@ -79,6 +80,7 @@ def _load() -> ctypes.CDLL:
         "lbm_get_stream": (ctypes.c_int, [vp, P(vp)]),
         "lbm_launches_per_step": (ctypes.c_int, [vp, P(ctypes.c_int)]),
         "lbm_frac_matrix": (ctypes.c_int, [P(lbm_params), ctypes.c_int, dp]),
+        "lbm_mass_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_longlong, vp, vp]),
         "lbm_destroy": (None, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_last_cuda_error": (ctypes.c_char_p, []),
@@ -95,7 +97,7 @@ _lib = _load()
 # Declared C entry points, re-exported under their own names.
 EXPORTED = ("lbm_create", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f",
             "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_frac_matrix",
-            "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
+            "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
 
 
 def lbm_strerror(code: int) -> str:
@@ -216,6 +218,12 @@ def lbm_frac_matrix(prm: lbm_params, mu: int) -> np.ndarray:
     K = np.empty((side, side), dtype=np.float64)
     _check(_lib.lbm_frac_matrix(ctypes.byref(prm), int(mu), _dptr(K)), "lbm_frac_matrix")
     return K
+
+
+def lbm_mass_static(x_dev: int, elem_bytes: int, n: int, sum_dev: int, stream: Optional[int] = None) -> int:
+    """Return code of the static-scratch FP64 sum (the result lands in *sum_dev)."""
+    return int(_lib.lbm_mass_static(ctypes.c_void_p(x_dev), int(elem_bytes), int(n), ctypes.c_void_p(sum_dev),
+                                     ctypes.c_void_p(stream or 0)))
 
 
 def lbm_destroy(h: int) -> None:
