@@ -4,26 +4,33 @@
 // line of axis mu, F_mu[n] = sum_l K_mu[n][l] C[l].  Over all lines of an axis this is
 // a dense GEMM (the weight matrix is Toeplitz up to its end columns, Eqs. c+ / c-):
 //
-//   D[m][n] = sum_l A[m][l] * B[n][l]
-//     A = the C panel: m runs over the lines (x axis: rows y at fixed z, K-major,
-//         i.e. l = x contiguous; y and z axes: m = x, "MN-major", m contiguous)
-//     B = K_mu (row n, column l), K-major
-//     D = F_mu, one 128 x BN FP32 accumulator tile in tensor memory per CTA.
+//   D[m][n] = sum_l A[m][l] * B[n][l], accumulator lanes m always run along x so
+//   that the epilogue stores are coalesced:
+//     x axis:    A = K_x (m = output node x, K-major), B = C rows (n = y at fixed z,
+//                K-major, l = x contiguous)
+//     y, z axes: A = C panel (m = x, "MN-major": m contiguous), B = K_mu (n = output
+//                node along mu, K-major)
+//   one 128 x BN FP32 accumulator tile in tensor memory per CTA.
 //
 // Split precision: A = A_hi + A_lo and B = B_hi + B_lo with each part in bf16
 // (kind::f16) or tf32 (kind::tf32); every K step issues three MMAs
 // (hi*hi + hi*lo + lo*hi) into the same FP32 accumulator; lo*lo is dropped.
 //
 // Per CTA: warp 0 / lane 0 issues TMA loads (128B-swizzled tiles, no multicast)
-// into a STAGES-deep ring guarded by mbarriers, warp 1 / lane 0 issues the MMAs and
-// releases ring slots with tcgen05.commit, then all four warps drain the accumulator
-// (tcgen05.ld, one lane quarter per warp) and store F.  Every mbarrier wait is
+// into a STAGES-deep ring guarded by mbarriers (the first loads leave before the
+// accumulator is allocated), warp 1 / lane 0 issues the MMAs and releases ring slots
+// with tcgen05.commit, then all four warps drain the accumulator (tcgen05.ld, one
+// lane quarter per warp) into a shared [BN][128] tile that one TMA store writes to F.
+// Small problems split the contraction over a cluster of ksplit CTAs per tile; their
+// partial tiles are summed through distributed shared memory in rank order, so the
+// result does not depend on timing.  Every mbarrier wait is
 // bounded by a 2 s %globaltimer budget; a wait that gives up sets bit 2 of the
 // handle's error flag and the CTA skips the rest of its work and releases TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -46,6 +53,8 @@ struct TcParams {
   int n0, n1, n2;
   int naxes;
   int total_tiles;
+  int ksplit;     // CTAs (one cluster) per output tile, each contracting a k-range
+  int tma_store;  // F rows are 16-byte aligned (n0 % 4 == 0): store tiles with TMA
   long long nodes;
   TcAxis ax[3];
   float* F;
@@ -53,8 +62,9 @@ struct TcParams {
 };
 
 struct TcMaps {
-  CUtensorMap a_hi[3], a_lo[3];
-  CUtensorMap b_hi[3], b_lo[3];
+  CUtensorMap c_hi[3], c_lo[3];  // C split; box per axis (x: B rows; y, z: MN-major A)
+  CUtensorMap k_hi[3], k_lo[3];  // K_mu split; box BK x 128 for the x axis (A), BK x BN else (B)
+  CUtensorMap f[3];              // F_mu (FP32), box 128 x (BN / ksplit) output rows
 };
 
 struct TcPlan {
@@ -192,10 +202,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 template <int E, int BN>
 struct Cfg {
   static constexpr int BK = 128 / E;                 // contraction elements per 128-byte row
-  static constexpr int STAGES = (BN <= 64) ? 4 : 3;
+  static constexpr int STAGES = (BN <= 64) ? 4 : (BN <= 128 ? 3 : 2);
   static constexpr uint32_t A_BYTES = BM * 128;      // one operand part of A: 128 rows x 128 B
   static constexpr uint32_t B_BYTES = BN * 128;
   static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
@@ -207,7 +232,7 @@ struct Cfg {
   static constexpr uint32_t IDESC_MN = IDESC_K | (1u << 15);
 };
 
-template <int E, int BN>
+template <int E, int BN, int KS>
 __global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
   using G = Cfg<E, BN>;
   extern __shared__ uint8_t smem_raw[];
@@ -217,19 +242,56 @@ __global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__
   uint64_t* done = empty + G::STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
 
-  // ---- which axis / tile
+  // ---- which axis / tile / k-range: blocks of one tile form a cluster of ksplit CTAs,
+  // CTA `rank` of the cluster contracts k-blocks [kb0, kb1)
+  constexpr int ks = KS;
+  const int cid = blockIdx.x / ks, rank = blockIdx.x % ks;
   int mu = 0;
-  while (mu + 1 < P.naxes && static_cast<int>(blockIdx.x) >= P.ax[mu + 1].tile_begin) ++mu;
+  while (mu + 1 < P.naxes && cid >= P.ax[mu + 1].tile_begin) ++mu;
   const TcAxis ax = P.ax[mu];
-  const int lt = blockIdx.x - ax.tile_begin;
+  const int lt = cid - ax.tile_begin;
   const int mt = lt / ax.tiles_n, nt = lt % ax.tiles_n;
   const int ncol0 = nt * BN;
-  // line-tile coordinates: x axis -> (y0, z); y axis -> (x0, z); z axis -> (x0, y)
-  const int m_in = (mt % ax.msub) * BM;
-  const int m_out = mt / ax.msub;
+  const int m_in = (mt % ax.msub) * BM;  // first x of the tile
+  const int m_out = mt / ax.msub;        // z (x, y axes) or y (z axis)
+  const int kb0 = rank * ax.kblocks / ks, kb1 = (rank + 1) * ax.kblocks / ks;
+  const int nkb = kb1 - kb0;
 
+  auto issue = [&](int i) {
+    const int s = i % G::STAGES;
+    uint8_t* st = smem + (size_t)s * G::STAGE;
+    uint8_t* a_hi = st;
+    uint8_t* a_lo = st + G::A_BYTES;
+    uint8_t* b_hi = st + 2 * G::A_BYTES;
+    uint8_t* b_lo = b_hi + G::B_BYTES;
+    mbar_expect_tx(&full[s], G::STAGE);
+    const int k0 = (kb0 + i) * G::BK;
+    if (mu == 0) {
+      // A = K_x rows n = m_in.., B = C rows y = ncol0.. at z = m_out
+      tma_load_2d(a_hi, &maps.k_hi[0], k0, m_in, &full[s]);
+      tma_load_2d(a_lo, &maps.k_lo[0], k0, m_in, &full[s]);
+      tma_load_3d(b_hi, &maps.c_hi[0], k0, ncol0, m_out, &full[s]);
+      tma_load_3d(b_lo, &maps.c_lo[0], k0, ncol0, m_out, &full[s]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int x = m_in + j * (128 / E);
+        if (mu == 1) {
+          tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[1], x, k0, m_out, &full[s]);
+          tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[1], x, k0, m_out, &full[s]);
+        } else {
+          tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[2], x, m_out, k0, &full[s]);
+          tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[2], x, m_out, k0, &full[s]);
+        }
+      }
+      tma_load_2d(b_hi, &maps.k_hi[mu], k0, ncol0, &full[s]);
+      tma_load_2d(b_lo, &maps.k_lo[mu], k0, ncol0, &full[s]);
+    }
+  };
+
+  // ---- prologue: the first loads go out before the accumulator is allocated
   if (threadIdx.x == 0) {
     for (int s = 0; s < G::STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -237,8 +299,9 @@ __global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int i = 0; i < G::STAGES && i < nkb; ++i) issue(i);
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(BN)
                  : "memory");
@@ -249,46 +312,19 @@ __global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const int KB = ax.kblocks;
   if (threadIdx.x == 0) {
-    // ---------------- producer
-    for (int kb = 0; kb < KB; ++kb) {
-      const int s = kb % G::STAGES;
-      if (kb >= G::STAGES && !mbar_wait(&empty[s], ((kb / G::STAGES) - 1) & 1, P.flag)) break;
-      uint8_t* st = smem + (size_t)s * G::STAGE;
-      uint8_t* a_hi = st;
-      uint8_t* a_lo = st + G::A_BYTES;
-      uint8_t* b_hi = st + 2 * G::A_BYTES;
-      uint8_t* b_lo = b_hi + G::B_BYTES;
-      mbar_expect_tx(&full[s], G::STAGE);
-      const int k0 = kb * G::BK;
-      if (mu == 0) {
-        tma_load_3d(a_hi, &maps.a_hi[0], k0, m_in, m_out, &full[s]);
-        tma_load_3d(a_lo, &maps.a_lo[0], k0, m_in, m_out, &full[s]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < E; ++j) {
-          const int x = m_in + j * (128 / E);
-          if (mu == 1) {
-            tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.a_hi[1], x, k0, m_out, &full[s]);
-            tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.a_lo[1], x, k0, m_out, &full[s]);
-          } else {
-            tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.a_hi[2], x, m_out, k0, &full[s]);
-            tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.a_lo[2], x, m_out, k0, &full[s]);
-          }
-        }
-      }
-      tma_load_2d(b_hi, &maps.b_hi[mu], k0, ncol0, &full[s]);
-      tma_load_2d(b_lo, &maps.b_lo[mu], k0, ncol0, &full[s]);
+    // ---------------- producer (remaining k-blocks)
+    for (int i = G::STAGES; i < nkb; ++i) {
+      const int s = i % G::STAGES;
+      if (!mbar_wait(&empty[s], ((i / G::STAGES) - 1) & 1, P.flag)) break;
+      issue(i);
     }
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer
     const uint32_t idesc = (mu == 0) ? G::IDESC_K : G::IDESC_MN;
-    bool ok = true;
-    for (int kb = 0; kb < KB && ok; ++kb) {
-      const int s = kb % G::STAGES;
-      ok = mbar_wait(&full[s], (kb / G::STAGES) & 1, P.flag);
-      if (!ok) break;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % G::STAGES;
+      if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(smem + (size_t)s * G::STAGE);
       const uint32_t a_hi = st, a_lo = st + G::A_BYTES;
@@ -308,7 +344,7 @@ __global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__
         const uint64_t dal = smem_desc(a_lo + a_off, a_lbo, 1024);
         const uint64_t dbh = smem_desc(b_hi + b_off, 16, 1024);
         const uint64_t dbl = smem_desc(b_lo + b_off, 16, 1024);
-        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
         mma<E>(tmem, dah, dbh, idesc, acc);
         mma<E>(tmem, dah, dbl, idesc, 1u);
         mma<E>(tmem, dal, dbh, idesc, 1u);
@@ -319,47 +355,106 @@ __global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__
   }
   __syncwarp();
 
-  // ---------------- epilogue: TMEM -> registers -> F
+  // ---------------- epilogue: TMEM -> shared tile [BN][128] (lane = x) -> F
   const bool have = mbar_wait(done, 0, P.flag);
   tc_fence_after();
-  if (have) {
-    const int row = warp * 32 + lane;  // accumulator lane = line index within the tile
-    const long long nodes = P.nodes;
-    float* F = P.F + (long long)mu * nodes;
-    const int n0 = P.n0, n1 = P.n1;
+  float* tile = reinterpret_cast<float*>(smem);  // the operand ring is idle once `done` fired
+  const int row = threadIdx.x;                   // accumulator lane = x offset in the tile
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-      if (mu == 0) {
-        const int y = m_in + row, z = m_out;
-        if (y < n1) {
-          float* dst = F + ((long long)z * n1 + y) * n0;
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    float v[32];
+    tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int x = ncol0 + c0 + j;
-            if (x < n0) dst[x] = v[j];
-          }
-        }
+    for (int j = 0; j < 32; ++j) tile[(c0 + j) * BM + row] = have ? v[j] : 0.0f;
+  }
+
+  int r0 = 0, r1 = BN;  // tile rows (output nodes n) this CTA writes
+  if (ks > 1) {
+    // partial tiles of the cluster are complete; CTA `rank` sums rows
+    // [rank*BN/ks, (rank+1)*BN/ks) over ranks 0..ks-1 in that order
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    const int rows = BN / ks;
+    r0 = rank * rows;
+    r1 = r0 + rows;
+    const uint32_t tbase = smem_u32(tile);
+    constexpr int PER = (BN / KS) * (BM / 4) / 128;  // float4 elements per thread
+    uint32_t offs[PER];
+    float4 acc[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + k * 128;
+      offs[k] = static_cast<uint32_t>(((r0 + e / (BM / 4)) * BM + (e % (BM / 4)) * 4) * 4);
+      acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < KS; ++r) {  // rank order: the sum does not depend on timing
+      float4 b[PER];
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        uint32_t raddr;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(tbase + offs[k]), "r"(r));
+        asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(b[k].x), "=f"(b[k].y), "=f"(b[k].z), "=f"(b[k].w)
+                     : "r"(raddr)
+                     : "memory");
+      }
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        acc[k].x += b[k].x;
+        acc[k].y += b[k].y;
+        acc[k].z += b[k].z;
+        acc[k].w += b[k].w;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+      *reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(tile) + offs[k]) = acc[k];
+  }
+
+  const long long nodes = P.nodes;
+  float* F = P.F + (long long)mu * nodes;
+  const int n0 = P.n0, n1 = P.n1;
+  if (P.tma_store) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && have) {
+      int c1, c2;
+      if (mu == 2) {
+        c1 = m_out;
+        c2 = ncol0 + r0;
       } else {
-        const int x = m_in + row;
-        if (x < n0) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = ncol0 + c0 + j;
-            if (n < ax.side) {
-              const long long idx = (mu == 1) ? ((long long)m_out * n1 + n) * n0 + x
-                                              : ((long long)n * n1 + m_out) * n0 + x;
-              F[idx] = v[j];
-            }
-          }
-        }
+        c1 = ncol0 + r0;
+        c2 = m_out;
+      }
+      asm volatile(
+          "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+              reinterpret_cast<uint64_t>(&maps.f[mu])),
+          "r"(m_in), "r"(c1), "r"(c2), "r"(smem_u32(tile + r0 * BM))
+          : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+  } else {
+    // rows of F that are not 16-byte aligned: plain stores, coalesced along x
+    __syncthreads();
+    const int x = m_in + row;
+    if (have && x < n0) {
+      for (int rr = r0; rr < r1; ++rr) {
+        const int n = ncol0 + rr;  // x axis: row y at z = m_out; y/z axes: node along mu
+        const int lim = (mu == 0) ? n1 : ax.side;
+        if (n >= lim) break;
+        const long long idx = (mu == 2) ? ((long long)n * n1 + m_out) * n0 + x : ((long long)m_out * n1 + n) * n0 + x;
+        F[idx] = tile[rr * BM + row];
       }
     }
   }
+  if (ks > 1) {
+    // no CTA leaves while another still reads its tile
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
   }
@@ -446,17 +541,42 @@ bool encode(CUtensorMap* m, int elem, int rank, void* base, const cuuint64_t* di
   return r == CUDA_SUCCESS;
 }
 
-template <int E, int BN>
+template <int E, int BN, int KS>
 cudaError_t launch_kernel(const TcPlan* p, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(frac_tc_kernel<E, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(frac_tc_kernel<E, BN, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg<E, BN>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  frac_tc_kernel<E, BN><<<p->prm.total_tiles, 128, Cfg<E, BN>::SMEM, s>>>(p->maps, p->prm);
-  return cudaGetLastError();
+  if (KS == 1) {
+    frac_tc_kernel<E, BN, KS><<<p->prm.total_tiles, 128, Cfg<E, BN>::SMEM, s>>>(p->maps, p->prm);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p->prm.total_tiles * KS, 1, 1);
+  cfg.blockDim = dim3(128, 1, 1);
+  cfg.dynamicSmemBytes = Cfg<E, BN>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = KS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, frac_tc_kernel<E, BN, KS>, p->maps, p->prm);
+}
+
+template <int BN>
+cudaError_t launch_bn(const TcPlan* p, cudaStream_t s) {
+  switch (p->prm.ksplit) {
+    case 1: return launch_kernel<2, BN, 1>(p, s);
+    case 2: return launch_kernel<2, BN, 2>(p, s);
+    case 4: return launch_kernel<2, BN, 4>(p, s);
+    default: return launch_kernel<2, BN, 8>(p, s);
+  }
 }
 
 }  // namespace
@@ -475,9 +595,7 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K) {
   const int n[3] = {h->sp.n[0], h->sp.n[1], h->sp.n[2]};
   int maxside = 0;
   for (int mu = 0; mu < h->d; ++mu) maxside = n[mu] > maxside ? n[mu] : maxside;
-  p->bn = (maxside >= 1024) ? 128 : 64;
-  p->smem = (p->bn == 64) ? ((E == 2) ? Cfg<2, 64>::SMEM : Cfg<4, 64>::SMEM)
-                          : ((E == 2) ? Cfg<2, 128>::SMEM : Cfg<4, 128>::SMEM);
+  (void)maxside;
   const int ldp = (n[0] + 7) / 8 * 8;
   p->ldp = ldp;
   const size_t split_elems = (size_t)ldp * n[1] * n[2];
@@ -535,38 +653,76 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K) {
   P.flag = h->dev.flag;
   const cuuint64_t cdims[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
   const cuuint64_t cstr[2] = {(cuuint64_t)ldp * E, (cuuint64_t)ldp * n[1] * E};
+  // Column tiles of 128 (an M = 128 MMA costs the same for any N <= 128) or 256 when
+  // that still fills the GPU; small problems split the contraction over a cluster of
+  // up to 8 CTAs per tile so that about one CTA per SM is busy.
+  auto count_tiles = [&](int bn) {
+    long long t = 0;
+    for (int mu = 0; mu < h->d; ++mu) {
+      const long long msub = (n[0] + BM - 1) / BM;
+      const long long outer = (mu == 0 || mu == 1) ? n[2] : n[1];
+      const long long ncols = (mu == 0) ? n[1] : n[mu];
+      t += msub * outer * ((ncols + bn - 1) / bn);
+    }
+    return t;
+  };
+  constexpr int kSMs = 152;
+  p->bn = (count_tiles(256) >= kSMs) ? 256 : 128;
+  int kbmin = 1 << 30;
+  for (int mu = 0; mu < h->d; ++mu) kbmin = std::min(kbmin, (n[mu] + BK - 1) / BK);
+  int ks = 1;
+  const long long nt = count_tiles(p->bn);
+  while (ks * 2 <= 8 && ks * 2 <= kbmin && nt * ks * 2 <= kSMs) ks *= 2;
+  P.ksplit = ks;
+  P.tma_store = (n[0] % 4 == 0) ? 1 : 0;
   int tiles = 0;
   for (int mu = 0; mu < h->d; ++mu) {
     TcAxis& a = P.ax[mu];
     a.form = (mu == 0) ? 0 : 1;
     a.side = n[mu];
     a.kblocks = (n[mu] + BK - 1) / BK;
-    a.tiles_n = (n[mu] + p->bn - 1) / p->bn;
+    a.msub = (n[0] + BM - 1) / BM;  // 128-wide x tiles on every axis
     cuuint32_t box[3];
-    if (mu == 0) {  // lines = rows y (128 per tile) at fixed z
-      a.msub = (n[1] + BM - 1) / BM;
+    if (mu == 0) {  // B = C rows: BN rows y at fixed z
       a.tiles_m = a.msub * n[2];
-      box[0] = BK; box[1] = BM; box[2] = 1;
-    } else if (mu == 1) {  // lines = x (128 per tile) at fixed z
-      a.msub = (n[0] + BM - 1) / BM;
+      a.tiles_n = (n[1] + p->bn - 1) / p->bn;
+      box[0] = BK; box[1] = p->bn; box[2] = 1;
+    } else if (mu == 1) {  // A = C panel, lines = x at fixed z
       a.tiles_m = a.msub * n[2];
+      a.tiles_n = (n[1] + p->bn - 1) / p->bn;
       box[0] = MNW; box[1] = BK; box[2] = 1;
     } else {  // lines = x at fixed y
-      a.msub = (n[0] + BM - 1) / BM;
       a.tiles_m = a.msub * n[1];
+      a.tiles_n = (n[2] + p->bn - 1) / p->bn;
       box[0] = MNW; box[1] = 1; box[2] = BK;
     }
     a.tile_begin = tiles;
     tiles += a.tiles_m * a.tiles_n;
-    if (!encode(&p->maps.a_hi[mu], E, 3, h->dev.Chi, cdims, cstr, box)) return LBM_ECUDA;
-    if (!encode(&p->maps.a_lo[mu], E, 3, h->dev.Clo, cdims, cstr, box)) return LBM_ECUDA;
+    if (!encode(&p->maps.c_hi[mu], E, 3, h->dev.Chi, cdims, cstr, box)) return LBM_ECUDA;
+    if (!encode(&p->maps.c_lo[mu], E, 3, h->dev.Clo, cdims, cstr, box)) return LBM_ECUDA;
     const cuuint64_t kdims[2] = {(cuuint64_t)n[mu], (cuuint64_t)n[mu]};
     const cuuint64_t kstr[1] = {(cuuint64_t)ldk[mu] * E};
-    const cuuint32_t kbox[2] = {(cuuint32_t)BK, (cuuint32_t)p->bn};
-    if (!encode(&p->maps.b_hi[mu], E, 2, static_cast<uint8_t*>(h->dev.Khi) + koff[mu] * E, kdims, kstr, kbox))
+    const cuuint32_t kbox[2] = {(cuuint32_t)BK, (cuuint32_t)(mu == 0 ? BM : p->bn)};
+    if (!encode(&p->maps.k_hi[mu], E, 2, static_cast<uint8_t*>(h->dev.Khi) + koff[mu] * E, kdims, kstr, kbox))
       return LBM_ECUDA;
-    if (!encode(&p->maps.b_lo[mu], E, 2, static_cast<uint8_t*>(h->dev.Klo) + koff[mu] * E, kdims, kstr, kbox))
+    if (!encode(&p->maps.k_lo[mu], E, 2, static_cast<uint8_t*>(h->dev.Klo) + koff[mu] * E, kdims, kstr, kbox))
       return LBM_ECUDA;
+  }
+  if (P.tma_store) {
+    for (int mu = 0; mu < h->d; ++mu) {
+      const cuuint64_t fd[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
+      const cuuint64_t fs[2] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4};
+      const cuuint32_t rows = (cuuint32_t)(p->bn / ks);
+      const cuuint32_t fb[3] = {BM, mu == 2 ? 1u : rows, mu == 2 ? rows : 1u};
+      const cuuint32_t es[3] = {1, 1, 1};
+      EncodeTiled enc = get_encoder();
+      if (!enc) return LBM_ECUDA;
+      CUresult r = enc(&p->maps.f[mu], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                       static_cast<float*>(h->dev.F) + (size_t)mu * h->sp.nodes, fd, fs, fb, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return LBM_ECUDA;
+    }
   }
   P.total_tiles = tiles;
   return LBM_OK;
@@ -581,9 +737,8 @@ int tc_split_pitch(const lbm_s* h) { return h->tc ? h->tc->ldp : 0; }
 
 cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s) {
   const TcPlan* p = h->tc;
-  if (!p) return cudaErrorNotSupported;
-  if (p->elem == 2) return (p->bn == 64) ? launch_kernel<2, 64>(p, s) : launch_kernel<2, 128>(p, s);
-  return (p->bn == 64) ? launch_kernel<4, 64>(p, s) : launch_kernel<4, 128>(p, s);
+  if (!p || p->elem != 2) return cudaErrorNotSupported;
+  return (p->bn == 128) ? launch_bn<128>(p, s) : launch_bn<256>(p, s);
 }
 
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s) {
