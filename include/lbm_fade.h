@@ -93,12 +93,13 @@ typedef struct {
 int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t* out);
 
 /* Re-initialise the populations from a new concentration field (host, same layout
- * as lbm_create): f = feq(C, F(C)).  Asynchronous w.r.t. the device; the host
+ * as lbm_create): f = feq(C, F(C)); clears any latched device error.  Asynchronous w.r.t. the device; the host
  * array may be reused as soon as the call returns. */
 int lbm_set_C(lbm_t h, const double* C_host);
 
 /* Restart from the concentration last given to lbm_create or lbm_set_C, which the
- * handle keeps on the device: f = feq(C0, F(C0)).  No host transfer; asynchronous. */
+ * handle keeps on the device: f = feq(C0, F(C0)), and clear any latched device
+ * error.  No host transfer; asynchronous. */
 int lbm_reset(lbm_t h);
 
 /* Advance nsteps >= 0 time steps (Algorithm 1 time loop, items 1-5): fractional

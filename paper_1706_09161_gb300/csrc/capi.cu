@@ -358,6 +358,7 @@ int lbm_set_C(lbm_t h, const double* C_host) {
 
 int lbm_reset(lbm_t h) {
   if (!h) return LBM_EINVAL;
+  LBM_CUDA(cudaMemsetAsync(h->dev.flag, 0, sizeof(int), h->stream));  // a restart clears latched errors
   LBM_CUDA(cudaMemcpyAsync(h->dev.C, h->dev.C0, (size_t)h->elem * h->sp.nodes, cudaMemcpyDeviceToDevice,
                            h->stream));
   return init_from_C(h);

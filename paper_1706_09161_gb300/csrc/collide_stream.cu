@@ -7,19 +7,17 @@
 //   item 4  walls         f_b = C_wall - sum_{i != b} f_i                   Eq. (Dirichlet_BC)
 //   item 5  moment        C = <1|f>
 // Populations are stored after streaming and boundary treatment, so a CTA
-// collides its tile plus a one-node halo into shared memory, then gathers
-// ("pulls") each population from the node it came from.  The halo nodes are
-// collided redundantly by the neighbouring CTAs; their loads hit L2.
+// collides its nodes plus a one-node ring and gathers ("pulls") each population
+// from the node it came from; the ring's collisions are recomputed by the
+// neighbouring CTAs and their loads mostly hit L2.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "lbm_internal.h"
 
 namespace lbm {
 namespace {
-
-template <int D> struct Tile;
-template <> struct Tile<2> { static constexpr int X = 32, Y = 8, Z = 1; };
-template <> struct Tile<3> { static constexpr int X = 32, Y = 4, Z = 2; };
 
 template <int D> struct Lat;
 template <> struct Lat<2> { static constexpr int Q = 5; };
@@ -88,11 +86,6 @@ __device__ __forceinline__ void collide_node(const KConst<real>& sp, const real*
   }
 }
 
-// velocity components of population q (Section 2.1 order)
-__device__ __forceinline__ int ex_of(int q) { return q == 1 ? 1 : (q == 2 ? -1 : 0); }
-__device__ __forceinline__ int ey_of(int q) { return q == 3 ? 1 : (q == 4 ? -1 : 0); }
-__device__ __forceinline__ int ez_of(int q) { return q == 5 ? 1 : (q == 6 ? -1 : 0); }
-
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -121,82 +114,156 @@ __device__ __forceinline__ void write_split(const SplitOut& so, long long o, rea
   }
 }
 
-template <typename real, int D, bool MRT, int SPLIT>
-__global__ void __launch_bounds__(256)
-collide_stream_kernel(const KConst<real> sp, const real* __restrict__ f_in, const real* __restrict__ F,
-                      real* __restrict__ f_out, real* __restrict__ C_out, int* __restrict__ flag, SplitOut so) {
-  constexpr int Q = Lat<D>::Q;
-  constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
-  constexpr int EX = TX + 2, EY = TY + 2, EZ = (D == 3) ? TZ + 2 : 1;
-  constexpr int EXT = EX * EY * EZ;
-  __shared__ real s_f[Q][EXT];
+// Thread block: 16 warps own a 32 x 16 tile of nodes (one node per thread, full
+// 128-byte rows), and three more warps collide the one-node ring the pull needs: the
+// x-ring (16 + 16 nodes, one warp) and the rows below and above (one warp each).
+// The block marches along z through a chunk of planes, colliding every plane once; the
+// in-plane movers (e_1..e_4) of the current plane go through shared memory, the z
+// movers (e_5, e_6) stay in registers (previous plane's f*_5, next plane's f*_6).
+// In 2-D the block handles one plane.  Each node is loaded ~1.19 times per step.
+constexpr int TX = 32, TY = 16, HALO_WARPS = 3;
 
+template <typename real, int D, bool MRT>
+__device__ __forceinline__ void collide_at(const KConst<real>& sp, const real* __restrict__ f_in,
+                                           const real* __restrict__ F, bool inside, long long node, real* fs) {
+  constexpr int Q = Lat<D>::Q;
+  if (!inside) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fs[q] = static_cast<real>(0);
+    return;
+  }
+  const long long nodes = sp.nodes;
+  real f[Q], Fv[D];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) f[q] = f_in[q * nodes + node];
+#pragma unroll
+  for (int mu = 0; mu < D; ++mu) Fv[mu] = F[mu * nodes + node];
+  collide_node<real, D, MRT>(sp, f, Fv, fs);
+}
+
+template <typename real, int D, bool MRT, int SPLIT>
+__global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
+collide_stream_march_kernel(const KConst<real> sp, const real* __restrict__ f_in, const real* __restrict__ F,
+                            real* __restrict__ f_out, real* __restrict__ C_out, int* __restrict__ flag, SplitOut so,
+                            int zchunk) {
+  constexpr int Q = Lat<D>::Q;
+  // movers of the current plane on the tile plus ring: [buffer][mover 1..4][y+1][x+1]
+  __shared__ real s_m[2][4][TY + 2][TX + 2];
   const int n0 = sp.n[0], n1 = sp.n[1], n2 = sp.n[2];
   const long long nodes = sp.nodes;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const long long plane = (long long)n0 * n1;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, n2);
 
-  // phase 1: collide tile + face halo into shared memory
-  for (int e = threadIdx.x; e < EXT; e += blockDim.x) {
-    const int ex = e % EX;
-    const int ey = (e / EX) % EY;
-    const int ez = (D == 3) ? e / (EX * EY) : 1;
-    const int outx = (ex == 0 || ex == EX - 1), outy = (ey == 0 || ey == EY - 1);
-    const int outz = (D == 3) ? (ez == 0 || ez == EZ - 1) : 0;
-    if (outx + outy + outz > 1) continue;  // edge/corner of the halo: never read
-    const int gx = x0 + ex - 1, gy = y0 + ey - 1, gz = (D == 3) ? z0 + ez - 1 : 0;
-    if (gx < 0 || gx >= n0 || gy < 0 || gy >= n1 || gz < 0 || gz >= n2) continue;
-    const long long node = gx + (long long)n0 * (gy + (long long)n1 * gz);
-    real f[Q], Fv[D], fs[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) f[q] = f_in[q * nodes + node];
-#pragma unroll
-    for (int mu = 0; mu < D; ++mu) Fv[mu] = F[mu * nodes + node];
-    collide_node<real, D, MRT>(sp, f, Fv, fs);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) s_f[q][e] = fs[q];
+  // the node this thread collides every plane, and where its movers go
+  int gx, gy, sx, sy;
+  const bool owner = wy < TY;
+  if (owner) {
+    gx = x0 + lane;
+    gy = y0 + wy;
+  } else if (wy == TY) {  // x-ring: left column (lanes 0-15), right column (16-31)
+    gx = (lane < 16) ? x0 - 1 : x0 + TX;
+    gy = y0 + (lane & 15);
+  } else {                // rows below (wy = TY+1) and above (wy = TY+2)
+    gx = x0 + lane;
+    gy = (wy == TY + 1) ? y0 - 1 : y0 + TY;
   }
-  __syncthreads();
+  sx = gx - x0 + 1;
+  sy = gy - y0 + 1;
+  const bool in_xy = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
+  const long long col = gx + (long long)n0 * gy;
+  bool bad = false;
 
-  // phase 2: pull-stream into the tile, impose the walls, new concentration
-  for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
-    const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
-    const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-    if (gx >= n0 || gy >= n1 || gz >= n2) continue;
-    const long long node = gx + (long long)n0 * (gy + (long long)n1 * gz);
-    real fv[Q];
-    bool known[Q];
-    real sum_known = static_cast<real>(0);
-    int n_unknown = 0;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int sx = gx - ex_of(q), sy = gy - ey_of(q), sz = gz - ez_of(q);
-      known[q] = (sx >= 0 && sx < n0 && sy >= 0 && sy < n1 && sz >= 0 && sz < n2);
-      if (known[q]) {
-        const int e = (sx - x0 + 1) + EX * ((sy - y0 + 1) + EY * ((D == 3) ? (sz - z0 + 1) : 0));
-        fv[q] = s_f[q][e];
-        sum_known += fv[q];
+  real cur[Q], nxt[Q];
+  real prev5 = static_cast<real>(0);
+  if (owner) {
+    if (D == 3) {
+      real t[Q];
+      collide_at<real, D, MRT>(sp, f_in, F, in_xy && z0 > 0, col + (z0 - 1) * plane, t);
+      prev5 = t[5];
+    }
+    collide_at<real, D, MRT>(sp, f_in, F, in_xy, col + z0 * plane, cur);
+  }
+  int buf = 0;
+  for (int z = z0; z < z1; ++z) {
+    if (owner) {
+      if (D == 3) collide_at<real, D, MRT>(sp, f_in, F, in_xy && z + 1 < n2, col + (z + 1) * plane, nxt);
+      s_m[buf][0][sy][sx] = cur[1];
+      s_m[buf][1][sy][sx] = cur[2];
+      s_m[buf][2][sy][sx] = cur[3];
+      s_m[buf][3][sy][sx] = cur[4];
+    } else {
+      real h[Q];
+      collide_at<real, D, MRT>(sp, f_in, F, in_xy, col + z * plane, h);
+      if (wy == TY) {
+        if (lane < 16) s_m[buf][0][sy][sx] = h[1];  // moves +x into the tile
+        else s_m[buf][1][sy][sx] = h[2];            // moves -x into the tile
+      } else if (wy == TY + 1) {
+        s_m[buf][2][sy][sx] = h[3];                 // moves +y into the tile
       } else {
-        fv[q] = static_cast<real>(0);
-        ++n_unknown;
+        s_m[buf][3][sy][sx] = h[4];                 // moves -y into the tile
       }
     }
-    real C = sum_known;
-    if (n_unknown > 0) {
-      // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
-      const real fill = (sp.C_wall - sum_known) / static_cast<real>(n_unknown);
+    __syncthreads();
+    if (owner && in_xy) {
+      real fv[Q];
+      bool known[Q];
+      fv[0] = cur[0];
+      known[0] = true;
+      known[1] = gx > 0;
+      known[2] = gx + 1 < n0;
+      known[3] = gy > 0;
+      known[4] = gy + 1 < n1;
+      fv[1] = s_m[buf][0][sy][sx - 1];
+      fv[2] = s_m[buf][1][sy][sx + 1];
+      fv[3] = s_m[buf][2][sy - 1][sx];
+      fv[4] = s_m[buf][3][sy + 1][sx];
+      if (D == 3) {
+        known[5] = z > 0;
+        known[6] = z + 1 < n2;
+        fv[5] = prev5;
+        fv[6] = nxt[6];
+      }
+      real sum_known = static_cast<real>(0);
+      int n_unknown = 0;
 #pragma unroll
-      for (int q = 0; q < Q; ++q)
-        if (!known[q]) fv[q] = fill;
-      C = fv[0];
+      for (int q = 0; q < Q; ++q) {
+        if (known[q]) {
+          sum_known += fv[q];
+        } else {
+          fv[q] = static_cast<real>(0);
+          ++n_unknown;
+        }
+      }
+      real C = sum_known;
+      if (n_unknown > 0) {
+        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
+        const real fill = (sp.C_wall - sum_known) / static_cast<real>(n_unknown);
 #pragma unroll
-      for (int q = 1; q < Q; ++q) C += fv[q];
+        for (int q = 0; q < Q; ++q)
+          if (!known[q]) fv[q] = fill;
+        C = fv[0];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) C += fv[q];
+      }
+      const long long node = col + z * plane;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
+      C_out[node] = C;
+      if (SPLIT) write_split<SPLIT>(so, ((long long)z * n1 + gy) * so.ldp + gx, C);
+      bad |= !isfinite(C);
     }
+    if (owner && D == 3) {
+      prev5 = cur[5];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
-    C_out[node] = C;
-    if (SPLIT) write_split<SPLIT>(so, ((long long)gz * n1 + gy) * so.ldp + gx, C);
-    if (!isfinite(C)) atomicOr(flag, 1);
+      for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
+    }
+    buf ^= 1;
   }
+  // one flag update per warp at most
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
 }
 
 template <typename real, int D>
@@ -238,21 +305,30 @@ __global__ void moment_kernel(long long nodes, const real* __restrict__ f, real*
 
 template <typename real, int D, bool MRT>
 cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s) {
-  constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
   const KConst<real> sp = make_const<real>(h->sp);
-  dim3 grid((sp.n[0] + TX - 1) / TX, (sp.n[1] + TY - 1) / TY, (sp.n[2] + TZ - 1) / TZ);
   SplitOut so{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
   const int split = (h->tc == nullptr) ? 0 : (h->prm.precision == LBM_FP32_BF16SPLIT ? 1 : 2);
   const real* fi = static_cast<const real*>(f_in);
   const real* F = static_cast<const real*>(h->dev.F);
   real* fo = static_cast<real*>(f_out);
   real* Co = static_cast<real*>(C_out);
+  const int bx = (sp.n[0] + TX - 1) / TX, by = (sp.n[1] + TY - 1) / TY;
+  // z chunks: enough blocks for ~3 resident per SM, but chunks of >= 16 planes
+  int zchunk = sp.n[2];
+  if (D == 3) {
+    const long long cols = (long long)bx * by;
+    int nz = static_cast<int>((3LL * 152 + cols - 1) / cols);
+    nz = std::max(1, std::min(nz, sp.n[2] / 16));
+    zchunk = (sp.n[2] + nz - 1) / nz;
+  }
+  dim3 grid(bx, by, (sp.n[2] + zchunk - 1) / zchunk);
+  dim3 block(TX, TY + HALO_WARPS);
   if (split == 0)
-    collide_stream_kernel<real, D, MRT, 0><<<grid, 256, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so);
+    collide_stream_march_kernel<real, D, MRT, 0><<<grid, block, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so, zchunk);
   else if (split == 1)
-    collide_stream_kernel<real, D, MRT, 1><<<grid, 256, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so);
+    collide_stream_march_kernel<real, D, MRT, 1><<<grid, block, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so, zchunk);
   else
-    collide_stream_kernel<real, D, MRT, 2><<<grid, 256, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so);
+    collide_stream_march_kernel<real, D, MRT, 2><<<grid, block, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so, zchunk);
   return cudaGetLastError();
 }
 

@@ -194,6 +194,8 @@ def test_unstable_run_reports_error(L):
         assert L.lbm_sync(lat.h) == L.LBM_ERR_UNSTABLE
         with pytest.raises(L.LBMError):
             lat.C()
+        lat.reset()  # a restart clears the latched error
+        assert L.lbm_sync(lat.h) == L.LBM_OK
 
 
 def test_zero_steps_is_noop(L):

@@ -81,6 +81,18 @@ def test_tc_config_mrt_512_full_size(L, kind):
     assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, n, kind)
 
 
+def test_tc_config_mrt3d_256_full_size(L):
+    """256^3 D3Q7 MRT workload at full size (bf16 split), first 2 steps against the oracle."""
+    pb, C0, _ = W.mrt3d_256()
+    n = 2
+    C_ref = O.run_C(pb, C0, n).numpy()
+    with L.Lattice(pb, C0, "bf16split") as lat:
+        lat.step(n)
+        C = lat.C()
+        assert rel_l2(C, C_ref) < 1e-5
+        assert lat.mass() == pytest.approx(float(C_ref.sum()), rel=1e-5)
+
+
 def test_tc_graph_replay_deterministic(L):
     rng = np.random.default_rng(77)
     pb = W.random_problem(rng, 2, "mrt", (150, 140))
