@@ -42,6 +42,8 @@ WORKLOADS = {
              "Dirichlet C=0, 5x5 unit-mass pulse, 5000 steps",
         default_precision="bf16split"),
     "fp64_bgk_64": dict(desc="2-D D2Q5 BGK 64x64 FP64, alpha=1.7, 200 steps", default_precision="fp64"),
+    "mrt3d_128": dict(desc="3-D D3Q7 MRT 128^3 with the 256^3 workload's parameters (profiling captures only)",
+                      default_precision="bf16split"),
     "mrt3d_256": dict(desc="3-D fractional ADE, D3Q7 MRT, 256^3, alpha=(1.6,1.6,1.9), p=(0.5,0.2,0.8), g=(1,1,1), "
                            "D=diag(1e-3,1e-3,4e-4), u=(0.03,0,0) lattice units, free rates U[0.8,1.9] seed 3, "
                            "Dirichlet C=0, unit-mass Gaussian sigma=3, 2000 steps",
@@ -65,6 +67,8 @@ def load_peaks():
 
 def make_workload(name):
     from paper_1706_09161_gb300 import workloads as W
+    if name == "mrt3d_128":
+        return W.mrt3d_256(128)
     return getattr(W, name)()
 
 
@@ -175,8 +179,9 @@ def source_sha(paths):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel_key):
+def traffic_for(workload, kernel):
     """DRAM bytes per launch from the committed ncu summary, or None if the kernel changed since."""
+    kernel_key = f"{workload}:{kernel}"
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -313,7 +318,7 @@ def main():
             else:
                 peak = FP64_NOMINAL_TFLOPS
         roof = {"kernel": "fractional_operator", "bound": bound, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("fractional_operator"),
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for(args.workload, "fractional_operator"),
                 "algorithmic_per_launch": flops, "launch_ms": dur * 1e3, "peak_source": peak_src}
     else:
         bytes_ = float(pb.nodes) * (2 * Q * elem + d * elem + elem)
@@ -321,7 +326,7 @@ def main():
         achieved = bytes_ / dur / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         roof = {"kernel": "collide_stream", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_for("collide_stream"),
+                "frac": achieved / peak, "traffic": traffic_for(args.workload, "collide_stream"),
                 "algorithmic_per_launch": bytes_, "launch_ms": dur * 1e3, "peak_source": peak_src}
     roof["other_kernel_ms"] = {"fractional_operator": ms_frac / nprof, "collide_stream": ms_cs / nprof}
 
