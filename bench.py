@@ -42,6 +42,10 @@ WORKLOADS = {
              "Dirichlet C=0, 5x5 unit-mass pulse, 5000 steps",
         default_precision="bf16split"),
     "fp64_bgk_64": dict(desc="2-D D2Q5 BGK 64x64 FP64, alpha=1.7, 200 steps", default_precision="fp64"),
+    "batch64": dict(desc="64 independent 2-D D2Q5 MRT problems, sides U{128,256,384,512,768,1024} (seed 4), "
+                         "alpha~U[1.2,2], p~U[0,1], D~U[1e-4,3e-3] diagonal, |u|<=0.08, Gaussian pulses sigma~U[2,6], "
+                         "free rates U[0.8,1.9], 1000 steps each, grouped launches",
+                    default_precision="bf16split"),
     "mrt3d_128": dict(desc="3-D D3Q7 MRT 128^3 with the 256^3 workload's parameters (profiling captures only)",
                       default_precision="bf16split"),
     "mrt3d_256": dict(desc="3-D fractional ADE, D3Q7 MRT, 256^3, alpha=(1.6,1.6,1.9), p=(0.5,0.2,0.8), g=(1,1,1), "
@@ -66,10 +70,12 @@ def load_peaks():
 
 
 def make_workload(name):
+    """(problems, initial fields, lattice steps) of a named workload."""
     from paper_1706_09161_gb300 import workloads as W
-    if name == "mrt3d_128":
-        return W.mrt3d_256(128)
-    return getattr(W, name)()
+    if name == "batch64":
+        return W.batch64()
+    pb, C0, n = W.mrt3d_256(128) if name == "mrt3d_128" else getattr(W, name)()
+    return [pb], [C0], n
 
 
 # --------------------------------------------------------------------------- clocks
@@ -148,17 +154,22 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    pb, C0, nlbm = make_workload(args.workload)
-    sample = max(1, min(nlbm, args.ref_sample))
+    probs, fields, nlbm = make_workload(args.workload)
+    nodes = sum(pb.nodes for pb in probs)
+    sample = max(1, min(nlbm, args.ref_sample, int(2e7 // nodes) or 1))
     for _ in range(args.warmup):
-        oracle_sample(pb, C0, 1)
+        for pb, C0 in zip(probs, fields):
+            oracle_sample(pb, C0, 1)
     times = []
     threads = 1
     for _ in range(args.steps):
-        dt, _, threads = oracle_sample(pb, C0, sample)
+        dt = 0.0
+        for pb, C0 in zip(probs, fields):
+            t, _, threads = oracle_sample(pb, C0, sample)
+            dt += t
         times.append(dt)
     total = sum(times)
-    mlups = pb.nodes * sample * args.steps / total / 1e6
+    mlups = nodes * sample * args.steps / total / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -230,11 +241,13 @@ def main():
         dist.barrier()
     from paper_1706_09161_gb300 import lbm
 
-    pb, C0, nlbm = make_workload(args.workload)
+    probs, fields, nlbm = make_workload(args.workload)
     if args.lattice_steps:
         nlbm = args.lattice_steps
     precision = args.precision or WORKLOADS[args.workload]["default_precision"]
-    lat = lbm.Lattice(pb, C0, precision)
+    batched = len(probs) > 1
+    nodes = sum(pb.nodes for pb in probs)
+    lat = lbm.Batch(probs, fields, precision) if batched else lbm.Lattice(probs[0], fields[0], precision)
     stream = torch.cuda.ExternalStream(lat.stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -269,40 +282,47 @@ def main():
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * pb.nodes * nlbm * args.steps / (total_ms * 1e-3) / 1e6
+    value = world * nodes * nlbm * args.steps / (total_ms * 1e-3) / 1e6
     gpu_launches = args.steps * nlbm * lat.launches_per_step
 
     # ---- end to end through the C ABI with pinned host buffers
-    C0_pin = torch.from_numpy(np.ascontiguousarray(C0)).pin_memory()
-    out_pin = torch.empty(C0_pin.shape, dtype=torch.float64).pin_memory()
-    C0_np, out_np = C0_pin.numpy(), out_pin.numpy()
+    pins = [torch.from_numpy(np.ascontiguousarray(C0)).pin_memory() for C0 in fields]
+    outs = [torch.empty(p.shape, dtype=torch.float64).pin_memory() for p in pins]
     e2e_s = []
     for k in range(args.steps):
         flush.add_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lat.set_C(C0_np)
+        for i, p in enumerate(pins):
+            if batched:
+                lat.set_C(i, p.numpy())
+            else:
+                lat.set_C(p.numpy())
         lat.step(nlbm)
-        rc_e2e = lbm._lib.lbm_read_C(lat.h, lbm._dptr(out_np))  # data is copied; a latched instability is only reported
+        for i, o in enumerate(outs):
+            # data is copied; a latched instability is only reported
+            rc_e2e = (lbm._lib.lbm_batch_read_C(lat.h, i, lbm._dptr(o.numpy())) if batched
+                      else lbm._lib.lbm_read_C(lat.h, lbm._dptr(o.numpy())))
+            if rc_e2e not in (lbm.LBM_OK, lbm.LBM_ERR_UNSTABLE):
+                raise lbm.LBMError(rc_e2e, "read C")
         e2e_s.append(time.perf_counter() - t0)
-        if rc_e2e not in (lbm.LBM_OK, lbm.LBM_ERR_UNSTABLE):
-            raise lbm.LBMError(rc_e2e, "lbm_read_C")
-    e2e_val = world * pb.nodes * nlbm * args.steps / sum(e2e_s) / 1e6
+    e2e_val = world * nodes * nlbm * args.steps / sum(e2e_s) / 1e6
     if dist is not None:
         t = torch.tensor([sum(e2e_s)], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * pb.nodes * nlbm * args.steps / float(t.item()) / 1e6
+        e2e_val = world * nodes * nlbm * args.steps / float(t.item()) / 1e6
+    io_bytes = int(sum(C0.size for C0 in fields) * 8)
 
     # ---- dominant kernel, timed live with events on the library stream
     nprof = min(nlbm, 200)
     lat.reset()
     ms_frac, ms_cs = lat.profile(nprof)
-    d, Q = pb.d, 2 * pb.d + 1
-    side_sum = sum(pb.grid)
+    d = probs[0].d
+    Q = 2 * d + 1
     peaks, peak_src = load_peaks()
     elem = 8 if precision == "fp64" else 4
     if ms_frac >= ms_cs:
-        flops = 2.0 * pb.nodes * side_sum  # sum over axes of 2*side per node
+        flops = float(sum(2.0 * pb.nodes * sum(pb.grid) for pb in probs))  # 2 side flops per node per axis
         dur = ms_frac / nprof * 1e-3
         achieved = flops / dur / 1e12
         if precision in ("bf16split", "tf32split"):
@@ -321,7 +341,7 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for(args.workload, "fractional_operator"),
                 "algorithmic_per_launch": flops, "launch_ms": dur * 1e3, "peak_source": peak_src}
     else:
-        bytes_ = float(pb.nodes) * (2 * Q * elem + d * elem + elem)
+        bytes_ = float(nodes) * (2 * Q * elem + d * elem + elem)
         dur = ms_cs / nprof * 1e-3
         achieved = bytes_ / dur / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
@@ -334,15 +354,20 @@ def main():
     cpu = None
     accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ns = max(2, min(nlbm, args.cpu_sample, int(1e8 // pb.nodes)))
-        dt, C_ref, threads = oracle_sample(pb, C0, ns)
-        cpu = {"value": pb.nodes * ns / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+        ns = max(2, min(nlbm, args.cpu_sample, int(1e8 // nodes)))
+        dt, refs, threads = 0.0, [], 1
+        for pb, C0 in zip(probs, fields):
+            t, C_ref, threads = oracle_sample(pb, C0, ns)
+            dt += t
+            refs.append(C_ref)
+        cpu = {"value": nodes * ns / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"first {ns} of {nlbm} lattice steps of {args.workload} (FP64, torch CPU)"}
         lat.reset()
         lat.step(ns)
-        C_gpu = lat.C()
-        accuracy = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(C_gpu - C_ref) / np.linalg.norm(C_ref)),
-                    "lattice_steps": ns}
+        got = [lat.C(i) for i in range(len(probs))] if batched else [lat.C()]
+        num = sum(float(np.sum((g - r) ** 2)) for g, r in zip(got, refs))
+        den = sum(float(np.sum(r ** 2)) for r in refs)
+        accuracy = {"rel_l2_vs_fp64_oracle": float(np.sqrt(num / den)), "lattice_steps": ns}
 
     lat.close()
     if rank == 0:
@@ -353,11 +378,11 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
                            "precision": precision, "lattice_steps_per_bench_step": nlbm,
-                           "nodes": pb.nodes, "parallelism": f"replicas x{world}",
+                           "nodes": nodes, "problems": len(probs), "parallelism": f"replicas x{world}",
                            "l2": "flushed (512 MiB write) before every bench step; state L2-resident within a run"},
                 "roofline": roof, "cpu_baseline": cpu, "accuracy": accuracy,
-                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(C0.size * 8),
-                        "d2h_bytes_per_step": int(C0.size * 8)},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                        "d2h_bytes_per_step": io_bytes},
                 "gpu_launches": gpu_launches, "clocks": clk,
                 "status": lbm.lbm_strerror(rc if rc else warm_status)}
         print(json.dumps(line))

@@ -92,6 +92,33 @@ typedef struct {
  * ]0,2[; LBM_ENOMEM / LBM_ECUDA on device failures (no handle is returned then). */
 int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t* out);
 
+/* A batch of nprob independent problems advanced together (each one is the scheme of
+ * Algorithm 1, exactly as lbm_create would run it).  All problems share lattice,
+ * collision and precision (LBM_FP32 or LBM_FP32_BF16SPLIT); grids and every other
+ * parameter may differ.  prms[i] and C0_host[i] (host array of the problem's nodes)
+ * describe problem i.  One time step is one grouped tensor-core launch covering every
+ * problem's tiles (FP32: one SIMT launch per problem and axis) and one grouped
+ * collide-stream launch covering every problem's nodes.  On a batch handle lbm_step,
+ * lbm_reset, lbm_sync, lbm_profile, lbm_get_stream, lbm_launches_per_step and
+ * lbm_destroy act on all problems; the per-problem accessors are lbm_batch_read_C and
+ * lbm_batch_mass; the single-problem accessors return LBM_EINVAL.
+ * Errors: LBM_EINVAL for mixed lattices/collisions/precisions or any invalid problem,
+ * LBM_ENOTSUP for other precisions, LBM_ENOMEM / LBM_ECUDA as lbm_create. */
+int lbm_create_batch(int nprob, const lbm_params* prms, const double* const* C0_host, void* stream, lbm_t* out);
+
+/* Number of problems of a handle (1 for a single-problem handle). */
+int lbm_batch_size(lbm_t h, int* nprob);
+
+/* Concentration of problem `prob` (its nodes, host doubles); synchronises and returns
+ * that problem's latched error, as lbm_read_C. */
+int lbm_batch_read_C(lbm_t h, int prob, double* C_host);
+
+/* Re-initialise problem `prob` from a new concentration (host doubles), as lbm_set_C. */
+int lbm_batch_set_C(lbm_t h, int prob, const double* C_host);
+
+/* FP64 mass of problem `prob`, as lbm_mass. */
+int lbm_batch_mass(lbm_t h, int prob, double* mass);
+
 /* Re-initialise the populations from a new concentration field (host, same layout
  * as lbm_create): f = feq(C, F(C)); clears any latched device error.  Asynchronous w.r.t. the device; the host
  * array may be reused as soon as the call returns. */

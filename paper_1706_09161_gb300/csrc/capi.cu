@@ -213,6 +213,17 @@ int run_frac(lbm_s* h, cudaStream_t s) {
 }
 
 int one_step(lbm_s* h, int& cur, cudaStream_t s) {
+  if (h->is_batch()) {
+    // grouped operator (or one SIMT operator per problem), then one grouped collide-stream
+    if (h->batch_tc_blocks > 0) {
+      LBM_CUDA(lbm::launch_frac_tc_batch(h, s));
+    } else {
+      for (lbm_s* p : h->subs) LBM_CUDA(lbm::launch_frac_simt(p, p->dev.C, p->dev.F, s));
+    }
+    LBM_CUDA(lbm::launch_collide_stream_batch(h, cur, s));
+    cur ^= 1;
+    return LBM_OK;
+  }
   if (uses_tc(h)) {
     LBM_CUDA(lbm::launch_frac_tc(h, s));
   } else {
@@ -264,7 +275,10 @@ int capture_graph(lbm_s* h, int parity) {
 
 extern "C" {
 
-int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t* out) {
+// One problem: validation, buffers, weights, initial state.  Sub-problems of a batch
+// (batched = true) run their operator as part of a grouped launch: 128-wide column
+// tiles, no k-split.
+static int create_problem(const lbm_params* prm, const double* C0_host, void* stream, bool batched, lbm_t* out) {
   if (!out || !C0_host) return LBM_EINVAL;
   *out = nullptr;
   Derived dv;
@@ -334,7 +348,7 @@ int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t
     }
   }
   if (prm->precision == LBM_FP32_BF16SPLIT || prm->precision == LBM_FP32_TF32SPLIT) {
-    if ((rc = lbm::tc_prepare(h, Kall))) return fail(rc);
+    if ((rc = lbm::tc_prepare(h, Kall, batched ? 128 : 0, batched ? 1 : 0))) return fail(rc);
     h->launches_per_step = 2;
   } else {
     h->launches_per_step = h->d + 1;
@@ -348,8 +362,93 @@ int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t
   return LBM_OK;
 }
 
-int lbm_set_C(lbm_t h, const double* C_host) {
+int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t* out) {
+  return create_problem(prm, C0_host, stream, false, out);
+}
+
+int lbm_create_batch(int nprob, const lbm_params* prms, const double* const* C0_host, void* stream, lbm_t* out) {
+  if (!out || !prms || !C0_host || nprob < 1) return LBM_EINVAL;
+  *out = nullptr;
+  const lbm_params& p0 = prms[0];
+  if (p0.precision != LBM_FP32 && p0.precision != LBM_FP32_BF16SPLIT) return LBM_ENOTSUP;
+  for (int i = 0; i < nprob; ++i) {
+    if (!C0_host[i]) return LBM_EINVAL;
+    if (prms[i].lattice != p0.lattice || prms[i].collision != p0.collision || prms[i].precision != p0.precision)
+      return LBM_EINVAL;
+    Derived dv;
+    int rc = derive(&prms[i], &dv);
+    if (rc) return rc;
+  }
+  lbm_s* b = new (std::nothrow) lbm_s();
+  if (!b) return LBM_ENOMEM;
+  b->prm = p0;
+  b->d = (p0.lattice == LBM_D2Q5) ? 2 : 3;
+  b->Q = 2 * b->d + 1;
+  b->elem = 4;
+  b->graph_steps = 32;
+  cudaGetDevice(&b->device);
+  auto fail = [&](int code) {
+    lbm_destroy(b);
+    return code;
+  };
+  if (stream) {
+    b->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return record_cuda(e, "cudaStreamCreateWithFlags");
+    }
+    b->own_stream = true;
+  }
+  for (int i = 0; i < nprob; ++i) {
+    lbm_t sub = nullptr;
+    int rc = create_problem(&prms[i], C0_host[i], b->stream, true, &sub);
+    if (rc) return fail(rc);
+    b->subs.push_back(sub);
+  }
+  int rc = LBM_OK;
+  if (p0.precision == LBM_FP32_BF16SPLIT) {
+    if ((rc = lbm::tc_batch_prepare(b))) return fail(rc);
+    b->launches_per_step = 2;
+  } else {
+    b->launches_per_step = nprob * b->d + 1;
+  }
+  if ((rc = lbm::cs_batch_prepare(b))) return fail(rc);
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_size(lbm_t h, int* nprob) {
+  if (!h || !nprob) return LBM_EINVAL;
+  *nprob = h->is_batch() ? static_cast<int>(h->subs.size()) : 1;
+  return LBM_OK;
+}
+
+int lbm_batch_read_C(lbm_t h, int prob, double* C_host) {
   if (!h || !C_host) return LBM_EINVAL;
+  if (!h->is_batch()) return prob == 0 ? lbm_read_C(h, C_host) : LBM_EINVAL;
+  if (prob < 0 || prob >= static_cast<int>(h->subs.size())) return LBM_EINVAL;
+  return lbm_read_C(h->subs[prob], C_host);
+}
+
+int lbm_batch_set_C(lbm_t h, int prob, const double* C_host) {
+  if (!h || !C_host) return LBM_EINVAL;
+  if (!h->is_batch()) return prob == 0 ? lbm_set_C(h, C_host) : LBM_EINVAL;
+  if (prob < 0 || prob >= static_cast<int>(h->subs.size())) return LBM_EINVAL;
+  h->subs[prob]->cur = h->cur;
+  return lbm_set_C(h->subs[prob], C_host);
+}
+
+int lbm_batch_mass(lbm_t h, int prob, double* mass) {
+  if (!h || !mass) return LBM_EINVAL;
+  if (!h->is_batch()) return prob == 0 ? lbm_mass(h, mass) : LBM_EINVAL;
+  if (prob < 0 || prob >= static_cast<int>(h->subs.size())) return LBM_EINVAL;
+  return lbm_mass(h->subs[prob], mass);
+}
+
+int lbm_set_C(lbm_t h, const double* C_host) {
+  if (!h || !C_host || h->is_batch()) return LBM_EINVAL;
   const long long nodes = h->sp.nodes;
   LBM_CUDA(cudaMemcpyAsync(h->dev.stage, C_host, sizeof(double) * nodes, cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA(lbm::launch_convert_in(h->dev.stage, h->dev.C0, h->elem, nodes, h->stream));
@@ -358,6 +457,14 @@ int lbm_set_C(lbm_t h, const double* C_host) {
 
 int lbm_reset(lbm_t h) {
   if (!h) return LBM_EINVAL;
+  if (h->is_batch()) {
+    for (lbm_s* p : h->subs) {
+      p->cur = h->cur;
+      int rc = lbm_reset(p);
+      if (rc) return rc;
+    }
+    return LBM_OK;
+  }
   LBM_CUDA(cudaMemsetAsync(h->dev.flag, 0, sizeof(int), h->stream));  // a restart clears latched errors
   LBM_CUDA(cudaMemcpyAsync(h->dev.C, h->dev.C0, (size_t)h->elem * h->sp.nodes, cudaMemcpyDeviceToDevice,
                            h->stream));
@@ -373,12 +480,20 @@ int lbm_profile(lbm_t h, int nsteps, double* ms) {
   for (int k = 0; k < nsteps && rc == LBM_OK; ++k) {
     cudaError_t e = cudaEventRecord(ev[0], h->stream);
     if (e == cudaSuccess) {
-      if (uses_tc(h)) e = lbm::launch_frac_tc(h, h->stream);
-      else rc = run_frac(h, h->stream);
+      if (h->is_batch() && h->batch_tc_blocks > 0) e = lbm::launch_frac_tc_batch(h, h->stream);
+      else if (h->is_batch())
+        for (lbm_s* p : h->subs)
+          if (e == cudaSuccess) e = lbm::launch_frac_simt(p, p->dev.C, p->dev.F, h->stream);
+      if (!h->is_batch()) {
+        if (uses_tc(h)) e = lbm::launch_frac_tc(h, h->stream);
+        else rc = run_frac(h, h->stream);
+      }
     }
     if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[1], h->stream);
-    if (e == cudaSuccess && rc == LBM_OK)
-      e = lbm::launch_collide_stream(h, h->dev.f[h->cur], h->dev.f[h->cur ^ 1], h->dev.C, h->stream);
+    if (e == cudaSuccess && rc == LBM_OK) {
+      if (h->is_batch()) e = lbm::launch_collide_stream_batch(h, h->cur, h->stream);
+      else e = lbm::launch_collide_stream(h, h->dev.f[h->cur], h->dev.f[h->cur ^ 1], h->dev.C, h->stream);
+    }
     if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[2], h->stream);
     if (e == cudaSuccess && rc == LBM_OK) e = cudaEventSynchronize(ev[2]);
     float a = 0.f, b = 0.f;
@@ -386,6 +501,7 @@ int lbm_profile(lbm_t h, int nsteps, double* ms) {
     if (e == cudaSuccess && rc == LBM_OK) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
     if (e != cudaSuccess) rc = record_cuda(e, "lbm_profile");
     h->cur ^= 1;
+    for (lbm_s* p : h->subs) p->cur = h->cur;
     ms[0] += a;
     ms[1] += b;
   }
@@ -403,11 +519,13 @@ int lbm_step(lbm_t h, int nsteps) {
   }
   for (int k = 0; k < nsteps; ++k)
     if ((rc = one_step(h, h->cur, h->stream))) return rc;
+  for (lbm_s* p : h->subs) p->cur = h->cur;
   return LBM_OK;
 }
 
 int lbm_read_C(lbm_t h, double* C_host) {
   if (!h || !C_host) return LBM_EINVAL;
+  if (h->is_batch()) return LBM_EINVAL;
   const long long nodes = h->sp.nodes;
   LBM_CUDA(lbm::launch_convert_out(h->dev.C, h->elem, h->dev.stage, nodes, h->stream));
   LBM_CUDA(cudaMemcpyAsync(C_host, h->dev.stage, sizeof(double) * nodes, cudaMemcpyDeviceToHost, h->stream));
@@ -416,6 +534,7 @@ int lbm_read_C(lbm_t h, double* C_host) {
 
 int lbm_read_F(lbm_t h, int mu, double* F_host) {
   if (!h || !F_host || mu < 0 || mu >= h->d) return LBM_EINVAL;
+  if (h->is_batch()) return LBM_EINVAL;
   const long long nodes = h->sp.nodes;
   int rc = run_frac(h, h->stream);
   if (rc) return rc;
@@ -427,6 +546,7 @@ int lbm_read_F(lbm_t h, int mu, double* F_host) {
 
 int lbm_read_f(lbm_t h, double* f_host) {
   if (!h || !f_host) return LBM_EINVAL;
+  if (h->is_batch()) return LBM_EINVAL;
   const long long nodes = h->sp.nodes;
   for (int q = 0; q < h->Q; ++q) {
     LBM_CUDA(lbm::launch_convert_out((char*)h->dev.f[h->cur] + (size_t)q * nodes * h->elem, h->elem, h->dev.stage,
@@ -440,6 +560,7 @@ int lbm_read_f(lbm_t h, double* f_host) {
 
 int lbm_write_f(lbm_t h, const double* f_host) {
   if (!h || !f_host) return LBM_EINVAL;
+  if (h->is_batch()) return LBM_EINVAL;
   const long long nodes = h->sp.nodes;
   for (int q = 0; q < h->Q; ++q) {
     LBM_CUDA(cudaMemcpyAsync(h->dev.stage, f_host + (size_t)q * nodes, sizeof(double) * nodes,
@@ -454,6 +575,7 @@ int lbm_write_f(lbm_t h, const double* f_host) {
 
 int lbm_mass(lbm_t h, double* mass) {
   if (!h || !mass) return LBM_EINVAL;
+  if (h->is_batch()) return LBM_EINVAL;
   LBM_CUDA(lbm::launch_mass(h, h->dev.C, h->stream));
   LBM_CUDA(cudaMemcpyAsync(mass, h->dev.scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   return latched(h);
@@ -461,6 +583,15 @@ int lbm_mass(lbm_t h, double* mass) {
 
 int lbm_sync(lbm_t h) {
   if (!h) return LBM_EINVAL;
+  if (h->is_batch()) {
+    int worst = LBM_OK;
+    for (lbm_s* p : h->subs) {
+      const int rc = latched(p);
+      if (rc == LBM_ERR_TIMEOUT || rc == LBM_ECUDA || rc == LBM_ENOMEM) return rc;
+      if (rc) worst = rc;
+    }
+    return worst;
+  }
   return latched(h);
 }
 
@@ -490,6 +621,12 @@ int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host) {
 void lbm_destroy(lbm_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (lbm_s* p : h->subs) lbm_destroy(p);
+  h->subs.clear();
+  if (h->batch_cs) cudaFree(h->batch_cs);
+  if (h->batch_cs_start) cudaFree(h->batch_cs_start);
+  h->batch_cs = nullptr;
+  h->batch_cs_start = nullptr;
   free_all(h);
   delete h;
 }

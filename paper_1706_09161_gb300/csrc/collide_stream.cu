@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "lbm_internal.h"
 
@@ -100,6 +101,17 @@ struct SplitOut {
   int ldp;
 };
 
+// Per-problem entry of a grouped (batched) collide-stream launch.
+struct BatchCS {
+  KConst<float> k;
+  const float* f[2];  // population buffers; the launch's parity picks input and output
+  const float* F;
+  float* C;
+  SplitOut so;
+  int* flag;
+  int bx, by, zchunk;  // blocks in x, y and the z chunk length
+};
+
 template <int SPLIT, typename real>
 __device__ __forceinline__ void write_split(const SplitOut& so, long long o, real C) {
   const float c = static_cast<float>(C);
@@ -141,11 +153,12 @@ __device__ __forceinline__ void collide_at(const KConst<real>& sp, const real* _
   collide_node<real, D, MRT>(sp, f, Fv, fs);
 }
 
+// One block's column (tile bx, by; z chunk bz) of one problem.
 template <typename real, int D, bool MRT, int SPLIT>
-__global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
-collide_stream_march_kernel(const KConst<real> sp, const real* __restrict__ f_in, const real* __restrict__ F,
-                            real* __restrict__ f_out, real* __restrict__ C_out, int* __restrict__ flag, SplitOut so,
-                            int zchunk) {
+__device__ __forceinline__ void march_body(const KConst<real>& sp, const real* __restrict__ f_in,
+                                           const real* __restrict__ F, real* __restrict__ f_out,
+                                           real* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
+                                           int zchunk, int bx, int by, int bz) {
   constexpr int Q = Lat<D>::Q;
   // movers of the current plane on the tile plus ring: [buffer][mover 1..4][y+1][x+1]
   __shared__ real s_m[2][4][TY + 2][TX + 2];
@@ -153,8 +166,8 @@ collide_stream_march_kernel(const KConst<real> sp, const real* __restrict__ f_in
   const long long nodes = sp.nodes;
   const long long plane = (long long)n0 * n1;
   const int lane = threadIdx.x, wy = threadIdx.y;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * zchunk;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int z0 = bz * zchunk;
   const int z1 = min(z0 + zchunk, n2);
 
   // the node this thread collides every plane, and where its movers go
@@ -266,6 +279,41 @@ collide_stream_march_kernel(const KConst<real> sp, const real* __restrict__ f_in
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
 }
 
+template <typename real, int D, bool MRT, int SPLIT>
+__global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
+collide_stream_march_kernel(const KConst<real> sp, const real* __restrict__ f_in, const real* __restrict__ F,
+                            real* __restrict__ f_out, real* __restrict__ C_out, int* __restrict__ flag, SplitOut so,
+                            int zchunk) {
+  march_body<real, D, MRT, SPLIT>(sp, f_in, F, f_out, C_out, flag, so, zchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Grouped form for a batch of independent problems: one launch covers every block of
+// every problem; block_start[p] is the first block of problem p (ascending).  The
+// problem's constants are staged in shared memory.
+template <int D, bool MRT, int SPLIT>
+__global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
+collide_stream_batch_kernel(const BatchCS* __restrict__ tab, const int* __restrict__ block_start, int nprob,
+                            int parity) {
+  __shared__ KConst<float> s_k;
+  const int b = blockIdx.x;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&block_start[mid]) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchCS& e = tab[lo];
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  constexpr int words = sizeof(KConst<float>) / sizeof(int);
+  for (int i = tid; i < words; i += TX * (TY + HALO_WARPS))
+    reinterpret_cast<int*>(&s_k)[i] = reinterpret_cast<const int*>(&e.k)[i];
+  __syncthreads();
+  const int lb = b - __ldg(&block_start[lo]);
+  const int bx = lb % e.bx, rest = lb / e.bx;
+  march_body<float, D, MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
+                                   e.zchunk, bx, rest % e.by, rest / e.by);
+}
+
 template <typename real, int D>
 __global__ void init_equilibrium_kernel(const KConst<real> sp, const real* __restrict__ C, const real* __restrict__ F,
                                         real* __restrict__ f) {
@@ -352,6 +400,57 @@ cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out,
                             : launch_cs<float, 2, false>(h, f_in, f_out, C_out, s);
   return mrt ? launch_cs<float, 3, true>(h, f_in, f_out, C_out, s)
              : launch_cs<float, 3, false>(h, f_in, f_out, C_out, s);
+}
+
+int cs_batch_prepare(lbm_s* b) {
+  const int P = static_cast<int>(b->subs.size());
+  std::vector<BatchCS> tab(P);
+  std::vector<int> start(P);
+  int total = 0;
+  for (int i = 0; i < P; ++i) {
+    const lbm_s* h = b->subs[i];
+    if (h->elem != 4) return LBM_EINVAL;
+    BatchCS& e = tab[i];
+    e.k = make_const<float>(h->sp);
+    e.f[0] = static_cast<const float*>(h->dev.f[0]);
+    e.f[1] = static_cast<const float*>(h->dev.f[1]);
+    e.F = static_cast<const float*>(h->dev.F);
+    e.C = static_cast<float*>(h->dev.C);
+    e.so = SplitOut{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
+    e.flag = h->dev.flag;
+    e.bx = (h->sp.n[0] + TX - 1) / TX;
+    e.by = (h->sp.n[1] + TY - 1) / TY;
+    e.zchunk = h->sp.n[2];
+    start[i] = total;
+    total += e.bx * e.by;
+  }
+  if (cudaMalloc(&b->batch_cs, sizeof(BatchCS) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (cudaMalloc(&b->batch_cs_start, sizeof(int) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (cudaMemcpy(b->batch_cs, tab.data(), sizeof(BatchCS) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->batch_cs_start, start.data(), sizeof(int) * P, cudaMemcpyHostToDevice) != cudaSuccess)
+    return LBM_ECUDA;
+  b->batch_cs_blocks = total;
+  return LBM_OK;
+}
+
+cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t s) {
+  const lbm_s* h0 = b->subs[0];
+  const bool mrt = h0->prm.collision == LBM_MRT;
+  const int split = (h0->tc == nullptr) ? 0 : 1;
+  const BatchCS* tab = static_cast<const BatchCS*>(b->batch_cs);
+  const int P = static_cast<int>(b->subs.size());
+  dim3 block(TX, TY + HALO_WARPS);
+  const int g = b->batch_cs_blocks;
+#define LBM_CSB(D_, M_, S_) collide_stream_batch_kernel<D_, M_, S_><<<g, block, 0, s>>>(tab, b->batch_cs_start, P, parity)
+  if (h0->d == 2) {
+    if (mrt) { if (split) LBM_CSB(2, true, 1); else LBM_CSB(2, true, 0); }
+    else { if (split) LBM_CSB(2, false, 1); else LBM_CSB(2, false, 0); }
+  } else {
+    if (mrt) { if (split) LBM_CSB(3, true, 1); else LBM_CSB(3, true, 0); }
+    else { if (split) LBM_CSB(3, false, 1); else LBM_CSB(3, false, 0); }
+  }
+#undef LBM_CSB
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init_equilibrium(const lbm_s* h, void* f, cudaStream_t s) {

@@ -232,10 +232,11 @@ struct Cfg {
   static constexpr uint32_t IDESC_MN = IDESC_K | (1u << 15);
 };
 
+// One output tile (or one k-slice of it when KS > 1) of one problem; `block` is the
+// CTA's index among that problem's CTAs.  `maps` may live in parameter or global memory.
 template <int E, int BN, int KS>
-__global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
+__device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams& P, int block, uint8_t* smem_raw) {
   using G = Cfg<E, BN>;
-  extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)G::STAGES * G::STAGE);
   uint64_t* empty = full + G::STAGES;
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__
   // ---- which axis / tile / k-range: blocks of one tile form a cluster of ksplit CTAs,
   // CTA `rank` of the cluster contracts k-blocks [kb0, kb1)
   constexpr int ks = KS;
-  const int cid = blockIdx.x / ks, rank = blockIdx.x % ks;
+  const int cid = block / ks, rank = block % ks;
   int mu = 0;
   while (mu + 1 < P.naxes && cid >= P.ax[mu + 1].tile_begin) ++mu;
   const TcAxis ax = P.ax[mu];
@@ -460,6 +461,29 @@ __global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__
   }
 }
 
+template <int E, int BN, int KS>
+__global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  frac_tc_tile<E, BN, KS>(maps, P, blockIdx.x, smem_raw);
+}
+
+// Grouped form for a batch of independent problems: one launch covers every tile of
+// every problem; block_start[p] is the first CTA of problem p (ascending).
+template <int E, int BN>
+__global__ void __launch_bounds__(128, 1)
+frac_tc_batch_kernel(const TcMaps* __restrict__ maps, const TcParams* __restrict__ prm,
+                     const int* __restrict__ block_start, int nprob) {
+  extern __shared__ uint8_t smem_raw[];
+  const int b = blockIdx.x;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&block_start[mid]) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  frac_tc_tile<E, BN, 1>(maps[lo], prm[lo], b - __ldg(&block_start[lo]), smem_raw);
+}
+
 // ---------------------------------------------------------------------------- splits
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -582,7 +606,7 @@ cudaError_t launch_bn(const TcPlan* p, cudaStream_t s) {
 }  // namespace
 
 // Allocate the split operands, split K_mu on the host, encode the tensor maps.
-int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K) {
+int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn, int force_ks) {
   TcPlan* p = new (std::nothrow) TcPlan();
   if (!p) return LBM_ENOMEM;
   h->tc = p;
@@ -673,6 +697,10 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K) {
   int ks = 1;
   const long long nt = count_tiles(p->bn);
   while (ks * 2 <= 8 && ks * 2 <= kbmin && nt * ks * 2 <= kSMs) ks *= 2;
+  if (force_bn > 0) {
+    p->bn = force_bn;
+    ks = std::max(1, force_ks);
+  }
   P.ksplit = ks;
   P.tma_store = (n[0] % 4 == 0) ? 1 : 0;
   int tiles = 0;
@@ -731,6 +759,50 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K) {
 void tc_release(lbm_s* h) {
   delete h->tc;
   h->tc = nullptr;
+  if (h->batch_tc_maps) cudaFree(h->batch_tc_maps);
+  if (h->batch_tc_prm) cudaFree(h->batch_tc_prm);
+  if (h->batch_tc_start) cudaFree(h->batch_tc_start);
+  h->batch_tc_maps = h->batch_tc_prm = nullptr;
+  h->batch_tc_start = nullptr;
+}
+
+int tc_batch_prepare(lbm_s* b) {
+  const int P = static_cast<int>(b->subs.size());
+  std::vector<TcMaps> maps(P);
+  std::vector<TcParams> prm(P);
+  std::vector<int> start(P);
+  int total = 0;
+  for (int i = 0; i < P; ++i) {
+    const TcPlan* t = b->subs[i]->tc;
+    if (!t || t->bn != 128 || t->prm.ksplit != 1 || t->elem != 2) return LBM_EINVAL;
+    maps[i] = t->maps;
+    prm[i] = t->prm;
+    start[i] = total;
+    total += t->prm.total_tiles;
+  }
+  if (cudaMalloc(&b->batch_tc_maps, sizeof(TcMaps) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (cudaMalloc(&b->batch_tc_prm, sizeof(TcParams) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (cudaMalloc(&b->batch_tc_start, sizeof(int) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (cudaMemcpy(b->batch_tc_maps, maps.data(), sizeof(TcMaps) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->batch_tc_prm, prm.data(), sizeof(TcParams) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->batch_tc_start, start.data(), sizeof(int) * P, cudaMemcpyHostToDevice) != cudaSuccess)
+    return LBM_ECUDA;
+  b->batch_tc_blocks = total;
+  return LBM_OK;
+}
+
+cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(frac_tc_batch_kernel<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg<2, 128>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  frac_tc_batch_kernel<2, 128><<<b->batch_tc_blocks, 128, Cfg<2, 128>::SMEM, s>>>(
+      static_cast<const TcMaps*>(b->batch_tc_maps), static_cast<const TcParams*>(b->batch_tc_prm), b->batch_tc_start,
+      static_cast<int>(b->subs.size()));
+  return cudaGetLastError();
 }
 
 int tc_split_pitch(const lbm_s* h) { return h->tc ? h->tc->ldp : 0; }

@@ -61,6 +61,16 @@ struct lbm_s {
   int launches_per_step = 0;
   int device = 0;
   lbm::TcPlan* tc = nullptr;           // split-precision tensor-core operator, if used
+  // batch of independent problems: one sub-handle per problem (each owns its buffers)
+  std::vector<lbm_s*> subs;
+  void* batch_tc_maps = nullptr;       // device table of per-problem tensor maps
+  void* batch_tc_prm = nullptr;        // device table of per-problem operator parameters
+  int* batch_tc_start = nullptr;       // first CTA of each problem (grouped operator)
+  int batch_tc_blocks = 0;
+  void* batch_cs = nullptr;            // device table of per-problem collide-stream entries
+  int* batch_cs_start = nullptr;       // first block of each problem (grouped collide-stream)
+  int batch_cs_blocks = 0;
+  bool is_batch() const { return !subs.empty(); }
 };
 
 namespace lbm {
@@ -88,7 +98,13 @@ cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s);
 int reduce_blocks_for(long long n);
 // tensor-core plan: split K_mu (row-major FP64 per axis), allocate split C, encode TMA maps
-int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K);
+// force_bn / force_ks (> 0) fix the column-tile width and k-split (grouped batches use 128 / 1)
+int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn, int force_ks);
+// grouped launches over the sub-problems of a batch handle
+int tc_batch_prepare(lbm_s* b);
+cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s);
+int cs_batch_prepare(lbm_s* b);
+cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t s);
 void tc_release(lbm_s* h);
 int tc_split_pitch(const lbm_s* h);
 

@@ -67,6 +67,11 @@ def _load() -> ctypes.CDLL:
     vp = ctypes.c_void_p
     sig = {
         "lbm_create": (ctypes.c_int, [P(lbm_params), dp, vp, P(vp)]),
+        "lbm_create_batch": (ctypes.c_int, [ctypes.c_int, P(lbm_params), P(dp), vp, P(vp)]),
+        "lbm_batch_size": (ctypes.c_int, [vp, P(ctypes.c_int)]),
+        "lbm_batch_read_C": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lbm_batch_mass": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lbm_batch_set_C": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "lbm_set_C": (ctypes.c_int, [vp, dp]),
         "lbm_reset": (ctypes.c_int, [vp]),
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -95,7 +100,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 
 # Declared C entry points, re-exported under their own names.
-EXPORTED = ("lbm_create", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f",
+EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_read_C", "lbm_batch_mass", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f",
             "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_frac_matrix",
             "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
 
@@ -147,6 +152,39 @@ def lbm_create(prm: lbm_params, C0: np.ndarray, stream: Optional[int] = None) ->
     _check(_lib.lbm_create(ctypes.byref(prm), _dptr(C0), ctypes.c_void_p(stream or 0), ctypes.byref(h)),
            "lbm_create")
     return h.value
+
+
+def lbm_create_batch(prms, C0s, stream: Optional[int] = None) -> int:
+    n = len(prms)
+    arr = (lbm_params * n)(*prms)
+    fields = [np.ascontiguousarray(c, dtype=np.float64) for c in C0s]
+    ptrs = (ctypes.POINTER(ctypes.c_double) * n)(*[_dptr(f) for f in fields])
+    h = ctypes.c_void_p()
+    _check(_lib.lbm_create_batch(n, arr, ptrs, ctypes.c_void_p(stream or 0), ctypes.byref(h)), "lbm_create_batch")
+    return h.value
+
+
+def lbm_batch_size(h: int) -> int:
+    n = ctypes.c_int()
+    _check(_lib.lbm_batch_size(ctypes.c_void_p(h), ctypes.byref(n)), "lbm_batch_size")
+    return n.value
+
+
+def lbm_batch_read_C(h: int, prob: int, out: np.ndarray) -> np.ndarray:
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(_lib.lbm_batch_read_C(ctypes.c_void_p(h), int(prob), _dptr(out)), "lbm_batch_read_C")
+    return out
+
+
+def lbm_batch_set_C(h: int, prob: int, C: np.ndarray) -> None:
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    _check(_lib.lbm_batch_set_C(ctypes.c_void_p(h), int(prob), _dptr(C)), "lbm_batch_set_C")
+
+
+def lbm_batch_mass(h: int, prob: int) -> float:
+    m = ctypes.c_double()
+    _check(_lib.lbm_batch_mass(ctypes.c_void_p(h), int(prob), ctypes.byref(m)), "lbm_batch_mass")
+    return m.value
 
 
 def lbm_set_C(h: int, C: np.ndarray) -> None:
@@ -285,6 +323,61 @@ class Lattice:
 
     def sync(self) -> None:
         _check(lbm_sync(self.h), "lbm_sync")
+
+    @property
+    def stream(self) -> int:
+        return lbm_get_stream(self.h)
+
+    @property
+    def launches_per_step(self) -> int:
+        return lbm_launches_per_step(self.h)
+
+
+class Batch:
+    """Independent problems advanced together by grouped launches (owns an lbm_t handle)."""
+
+    def __init__(self, problems, fields, precision: str = "bf16split", stream: Optional[int] = None):
+        self.problems = list(problems)
+        self.shapes = [tuple(reversed(tuple(int(n) for n in pb.grid))) for pb in self.problems]
+        self.h = lbm_create_batch([params_from_problem(pb, precision) for pb in self.problems], fields, stream)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self) -> int:
+        return lbm_batch_size(self.h)
+
+    def step(self, n: int = 1) -> None:
+        lbm_step(self.h, n)
+
+    def reset(self) -> None:
+        lbm_reset(self.h)
+
+    def C(self, prob: int) -> np.ndarray:
+        return lbm_batch_read_C(self.h, prob, np.empty(self.shapes[prob], dtype=np.float64))
+
+    def set_C(self, prob: int, C: np.ndarray) -> None:
+        lbm_batch_set_C(self.h, prob, C)
+
+    def mass(self, prob: int) -> float:
+        return lbm_batch_mass(self.h, prob)
+
+    def sync(self) -> None:
+        _check(lbm_sync(self.h), "lbm_sync")
+
+    def profile(self, n: int):
+        return lbm_profile(self.h, n)
 
     @property
     def stream(self) -> int:
