@@ -195,6 +195,17 @@ int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host);
  * ordering between them) race on it and must be serialised by the caller. */
 int lbm_mass_static(const void* x_dev, int elem_bytes, long long n, double* sum_dev, void* stream);
 
+/* Host-only: derivatives of K_mu (as lbm_frac_matrix) with respect to alpha_mu and
+ * p_mu, FP64, row-major (grid[mu])^2 each.  With gamma = 2 - alpha:
+ * dK/dp = s (W+ - W-), dK/dalpha = -d/dgamma [ s (p W+ + (1-p) W-) ],
+ * s = g h dx^gamma / Gamma(2+gamma), ds/dgamma = s (ln dx - psi(2+gamma))
+ * (Eqs. 1Dminus_discret, c+, c- differentiated in gamma).  Needs no GPU. */
+int lbm_frac_matrix_grad(const lbm_params* prm, int mu, double* dK_dalpha, double* dK_dp);
+
+/* Host-only: digamma psi(x), x > 0 (recurrence + asymptotic series, Abramowitz &
+ * Stegun 6.3.5 / 6.3.18), used by lbm_frac_matrix_grad. */
+double lbm_digamma(double x);
+
 /* Release every device buffer, graph and (if created by the handle) stream. */
 void lbm_destroy(lbm_t h);
 

@@ -618,6 +618,20 @@ int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host) {
   return LBM_OK;
 }
 
+int lbm_frac_matrix_grad(const lbm_params* prm, int mu, double* dK_dalpha, double* dK_dp) {
+  if (!dK_dalpha || !dK_dp) return LBM_EINVAL;
+  Derived dv;
+  int rc = derive(prm, &dv);
+  if (rc) return rc;
+  const int d = (prm->lattice == LBM_D2Q5) ? 2 : 3;
+  if (mu < 0 || mu >= d) return LBM_EINVAL;
+  lbm::build_frac_matrix_grad(prm->alpha[mu], prm->p[mu], prm->g[mu] * dv.h[mu], prm->grid[mu], prm->dx, dK_dalpha,
+                              dK_dp);
+  return LBM_OK;
+}
+
+double lbm_digamma(double x) { return lbm::digamma_fn(x); }
+
 void lbm_destroy(lbm_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);

@@ -110,5 +110,8 @@ int tc_split_pitch(const lbm_s* h);
 
 // host-side weight build (FP64), K row-major [n][l] for one axis
 void build_frac_matrix(double alpha, double p, double scale_g, int side, double dx, double* K);
+// its derivatives dK/dalpha and dK/dp (FP64, same layout)
+void build_frac_matrix_grad(double alpha, double p, double scale_g, int side, double dx, double* dKda, double* dKdp);
+double digamma_fn(double x);
 
 }  // namespace lbm

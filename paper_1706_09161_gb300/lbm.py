@@ -85,6 +85,8 @@ def _load() -> ctypes.CDLL:
         "lbm_get_stream": (ctypes.c_int, [vp, P(vp)]),
         "lbm_launches_per_step": (ctypes.c_int, [vp, P(ctypes.c_int)]),
         "lbm_frac_matrix": (ctypes.c_int, [P(lbm_params), ctypes.c_int, dp]),
+        "lbm_frac_matrix_grad": (ctypes.c_int, [P(lbm_params), ctypes.c_int, dp, dp]),
+        "lbm_digamma": (ctypes.c_double, [ctypes.c_double]),
         "lbm_mass_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_longlong, vp, vp]),
         "lbm_destroy": (None, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -102,7 +104,7 @@ _lib = _load()
 # Declared C entry points, re-exported under their own names.
 EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_read_C", "lbm_batch_mass", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f",
             "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_frac_matrix",
-            "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
+            "lbm_frac_matrix_grad", "lbm_digamma", "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
 
 
 def lbm_strerror(code: int) -> str:
@@ -262,6 +264,18 @@ def lbm_mass_static(x_dev: int, elem_bytes: int, n: int, sum_dev: int, stream: O
     """Return code of the static-scratch FP64 sum (the result lands in *sum_dev)."""
     return int(_lib.lbm_mass_static(ctypes.c_void_p(x_dev), int(elem_bytes), int(n), ctypes.c_void_p(sum_dev),
                                      ctypes.c_void_p(stream or 0)))
+
+
+def lbm_frac_matrix_grad(prm: lbm_params, mu: int):
+    side = prm.grid[mu]
+    da = np.empty((side, side), dtype=np.float64)
+    dp_ = np.empty((side, side), dtype=np.float64)
+    _check(_lib.lbm_frac_matrix_grad(ctypes.byref(prm), int(mu), _dptr(da), _dptr(dp_)), "lbm_frac_matrix_grad")
+    return da, dp_
+
+
+def lbm_digamma(x: float) -> float:
+    return float(_lib.lbm_digamma(float(x)))
 
 
 def lbm_destroy(h: int) -> None:

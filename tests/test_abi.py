@@ -105,3 +105,30 @@ def test_bgk_rejects_off_diagonal_D_and_mrt_rejects_non_spd(L):
     pb = W.Problem(d=2, collision="mrt", grid=(8, 8), alpha=(1.5, 1.5), p=(0.5, 0.5), g=(1, 1),
                    D=((0.01, 0.0), (0.0, 0.01)), u=(0, 0), s_free=(2.5, 1.0))
     assert L._lib.lbm_frac_matrix(ctypes.byref(L.params_from_problem(pb)), 0, ptr) == L.LBM_EINVAL
+
+
+def test_digamma_closed_values_and_lgamma_slope(L):
+    """psi(1) = -gamma_E, psi(2) = 1 - gamma_E, psi(1/2) = -gamma_E - 2 ln 2, and psi = (ln Gamma)'."""
+    import math
+    eg = 0.5772156649015329
+    assert L.lbm_digamma(1.0) == pytest.approx(-eg, abs=1e-14)
+    assert L.lbm_digamma(2.0) == pytest.approx(1 - eg, abs=1e-14)
+    assert L.lbm_digamma(0.5) == pytest.approx(-eg - 2 * math.log(2.0), abs=1e-14)
+    for x in (2.05, 2.5, 2.95, 7.3):
+        h = 1e-5
+        fd = (math.lgamma(x + h) - math.lgamma(x - h)) / (2 * h)
+        assert L.lbm_digamma(x) == pytest.approx(fd, abs=1e-9)
+
+
+@pytest.mark.parametrize("side,alpha,p,dx", [(9, 1.5, 0.3, 1.0), (40, 1.2, 0.7, 0.05), (257, 1.8, 0.5, 1.0)])
+def test_host_weight_matrix_derivatives_match_oracle_autograd(L, side, alpha, p, dx):
+    pb = W.Problem(d=2, collision="mrt", grid=(side, 5), alpha=(alpha, 1.5), p=(p, 0.5), g=(1.3, 1.0),
+                   D=((0.01, 0), (0, 0.01)), u=(0, 0), s_free=(1.0, 1.0), dx=dx)
+    da, dp = L.lbm_frac_matrix_grad(L.params_from_problem(pb, "fp64"), 0)
+    a = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+    pp = torch.tensor(p, dtype=torch.float64, requires_grad=True)
+    K = O.frac_matrix(a, pp, 1.3, side - 1, dx)
+    w = torch.tensor(np.random.default_rng(side).normal(size=(side, side)))
+    (K * w).sum().backward()
+    assert float((torch.tensor(da) * w).sum()) == pytest.approx(float(a.grad), rel=1e-9, abs=1e-12)
+    assert float((torch.tensor(dp) * w).sum()) == pytest.approx(float(pp.grad), rel=1e-9, abs=1e-12)
