@@ -195,6 +195,24 @@ int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host);
  * ordering between them) race on it and must be serialised by the caller. */
 int lbm_mass_static(const void* x_dev, int elem_bytes, long long n, double* sum_dev, void* stream);
 
+/* Loss and gradient of a snapshot misfit (the inverse problem):
+ *   L(theta) = sum_k sum_x ( C(x, t_k) - obs_k(x) )^2,
+ * C from the scheme started at the handle's initial concentration (lbm_create /
+ * lbm_set_C) with the handle's parameters theta; grad receives 4d doubles,
+ * dL/d[alpha_1..d, p_1..d, D_11..D_dd, u_1..d] (D: diagonal entries, physical units).
+ * Computed with the discrete adjoint of the step (the exact transpose of Algorithm 1's
+ * loop items 1-5 for fixed theta: walls, streaming, collision, equilibrium, K_mu^T),
+ * parameter derivatives of K_mu (lbm_frac_matrix_grad), of Omega (Eqs. MatrixS, D_ab)
+ * and of the advective equilibrium term (Eq. Feq), including the initial populations
+ * feq(C0, K C0).  Forward states are recomputed from checkpoints taken every
+ * ckpt_every steps (memory: ckpt_every + T/ckpt_every states); sums are FP64.
+ *   snap_steps : nsnap strictly increasing step indices >= 0 (the last one is T)
+ *   obs        : nsnap x nodes host doubles (field layout as lbm_create)
+ * MRT handles with the FP64 or FP32 forms only (LBM_ENOTSUP otherwise).  Synchronises;
+ * leaves the handle reset to its initial state. */
+int lbm_grad(lbm_t h, int nsnap, const int* snap_steps, const double* obs, int ckpt_every, double* loss,
+             double* grad);
+
 /* Host-only: derivatives of K_mu (as lbm_frac_matrix) with respect to alpha_mu and
  * p_mu, FP64, row-major (grid[mu])^2 each.  With gamma = 2 - alpha:
  * dK/dp = s (W+ - W-), dK/dalpha = -d/dgamma [ s (p W+ + (1-p) W-) ],

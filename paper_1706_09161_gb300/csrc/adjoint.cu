@@ -1,0 +1,466 @@
+// Discrete adjoint of the time step and parameter gradients of a snapshot loss.
+//
+// With the parameters fixed, one step (Algorithm 1, loop items 1-5) is linear in the
+// populations f: C = <1|f>, F_mu = K_mu C along axis mu, feq = E(C, F) (Eqs. Feq,
+// CoeffA_FADE3D), f* = f - Omega (f - feq) (Eqs. LBE_Ket / MRT-Coll), push streaming
+// (Eq. Def_Translation) and the walls (Eq. Dirichlet_BC, affine).  Its transpose, in
+// reverse order, with mu = dL/df(t+1):
+//   walls      each known population b at a wall node z:  mu_b - (1/k) sum_{unknown u} mu_u
+//   streaming  lambda*_q(y) = (walls^T mu)_q(y + e_q), 0 where y + e_q leaves the domain
+//   collision  lambda_f = (I - Omega)^T lambda*,  lambda_feq = Omega^T lambda*
+//   equilibrium lambda_C += lambda_feq_0 + sum_mu a_mu (lambda_feq_{2mu+1} - lambda_feq_{2mu+2})
+//              lambda_F_mu = -w_0 lambda_feq_0 + w_i (lambda_feq_{2mu+1} + lambda_feq_{2mu+2})
+//   operator   lambda_C += sum_mu K_mu^T lambda_F_mu   (the SIMT GEMM with K and K^T swapped)
+//   moment     dL/df_q(t) = lambda_f_q + lambda_C (+ the snapshot residual 2 (C - obs)).
+// Parameter gradients (sums over steps of lambda^T dA/dtheta f):
+//   alpha_mu, p_mu : <dK_mu/dtheta, G_mu>,  G_mu[n][l] = sum_t sum_lines lambda_F(n) C_t(l)
+//   D_mumu        : - sum lambda*^T (dOmega/dD_mumu) (f - feq)
+//   u_mu          : sum (dt/dx)(w_i/e^2) C (lambda_feq_{2mu+1} - lambda_feq_{2mu+2})
+// plus the initial condition f(0) = feq(C0, K C0).  Forward states are recomputed from
+// checkpoints taken every `ckpt` steps.  Gradient sums are FP64.
+#include <cmath>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename real>
+struct AdjConst {
+  int n[3];
+  long long nodes;
+  real omT[kMaxQ][kMaxQ];       // Omega^T
+  real dOm[3][kMaxQ][kMaxQ];    // dOmega / dD_mumu
+  real w0, wi;
+  real advw[3];                 // dfeq_{2mu+1}/dC = (dt/dx) u_mu w_i / e^2
+  real cu;                      // dfeq_{2mu+1}/du_mu per unit C = (dt/dx) w_i / e^2
+};
+
+__device__ __forceinline__ void evec(int q, int& ex, int& ey, int& ez) {
+  ex = (q == 1) - (q == 2);
+  ey = (q == 3) - (q == 4);
+  ez = (q == 5) - (q == 6);
+}
+
+// (1/k) sum of mu over the k unknown (wall-filled) populations of node (x, y, z); 0 inside
+template <typename real, int D>
+__device__ __forceinline__ real wall_nu(const AdjConst<real>& c, const real* __restrict__ lam, long long node, int x,
+                                        int y, int z) {
+  constexpr int Q = 2 * D + 1;
+  real s = static_cast<real>(0);
+  int k = 0;
+#pragma unroll
+  for (int q = 1; q < Q; ++q) {
+    int ex, ey, ez;
+    evec(q, ex, ey, ez);
+    const int sx = x - ex, sy = y - ey, sz = z - ez;
+    if (sx < 0 || sx >= c.n[0] || sy < 0 || sy >= c.n[1] || sz < 0 || sz >= c.n[2]) {
+      s += lam[q * c.nodes + node];
+      ++k;
+    }
+  }
+  return k ? s / static_cast<real>(k) : static_cast<real>(0);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Adds the block's sums of v[0..K) to part[blockIdx.x * K + k] (fixed order, so repeated
+// calls with the same grid accumulate deterministically).
+template <int K>
+__device__ __forceinline__ void block_accumulate(const double* v, double* __restrict__ part) {
+  __shared__ double s[K][kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double w = warp_sum(v[k]);
+    if (lane == 0) s[k][wid] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double acc = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) acc += s[threadIdx.x][i];
+    part[blockIdx.x * K + threadIdx.x] += acc;
+  }
+}
+
+template <typename real, int D>
+__global__ void __launch_bounds__(kThreads)
+adj_step_kernel(const AdjConst<real> c, const real* __restrict__ f, const real* __restrict__ F,
+                const real* __restrict__ lam, real* __restrict__ lf, real* __restrict__ lcl, real* __restrict__ lF,
+                double* __restrict__ part) {
+  constexpr int Q = 2 * D + 1;
+  const long long nodes = c.nodes;
+  const long long node = blockIdx.x * (long long)kThreads + threadIdx.x;
+  double g[2 * D];
+#pragma unroll
+  for (int k = 0; k < 2 * D; ++k) g[k] = 0.0;
+  if (node < nodes) {
+    const int n0 = c.n[0], n1 = c.n[1];
+    const int x = static_cast<int>(node % n0);
+    const int y = static_cast<int>((node / n0) % n1);
+    const int z = static_cast<int>(node / ((long long)n0 * n1));
+    // lambda* (adjoint of the post-collision populations of this node)
+    real ls[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      int ex, ey, ez;
+      evec(q, ex, ey, ez);
+      const int tx = x + ex, ty = y + ey, tz = z + ez;
+      if (tx < 0 || tx >= n0 || ty < 0 || ty >= n1 || tz < 0 || tz >= c.n[2]) {
+        ls[q] = static_cast<real>(0);
+      } else {
+        const long long t = tx + (long long)n0 * (ty + (long long)n1 * tz);
+        ls[q] = lam[q * nodes + t] - wall_nu<real, D>(c, lam, t, tx, ty, tz);
+      }
+    }
+    // forward state of this node
+    real fv[Q], Fv[D];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fv[q] = f[q * nodes + node];
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) Fv[mu] = F[mu * nodes + node];
+    real C = fv[0];
+#pragma unroll
+    for (int q = 1; q < Q; ++q) C += fv[q];
+    real sumF = Fv[0];
+#pragma unroll
+    for (int mu = 1; mu < D; ++mu) sumF += Fv[mu];
+    real dl[Q];  // f - feq
+    dl[0] = fv[0] - (C - c.w0 * sumF);
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) {
+      const real a = c.wi * Fv[mu], b = c.advw[mu] * C;
+      dl[2 * mu + 1] = fv[2 * mu + 1] - (a + b);
+      dl[2 * mu + 2] = fv[2 * mu + 2] - (a - b);
+    }
+    // collision transpose
+    real le[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      real acc = c.omT[i][0] * ls[0];
+#pragma unroll
+      for (int j = 1; j < Q; ++j) acc += c.omT[i][j] * ls[j];
+      le[i] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lf[q * nodes + node] = ls[q] - le[q];
+    real lc = le[0];
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) lc += c.advw[mu] * (le[2 * mu + 1] - le[2 * mu + 2]);
+    lcl[node] = lc;
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) {
+      lF[mu * nodes + node] = -c.w0 * le[0] + c.wi * (le[2 * mu + 1] + le[2 * mu + 2]);
+      g[mu] = static_cast<double>(c.cu) * static_cast<double>(C) *
+              static_cast<double>(le[2 * mu + 1] - le[2 * mu + 2]);
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        real row = static_cast<real>(0);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) row += c.dOm[mu][i][j] * dl[j];
+        acc += static_cast<double>(ls[i]) * static_cast<double>(row);
+      }
+      g[D + mu] = -acc;
+    }
+  }
+  block_accumulate<2 * D>(g, part);
+}
+
+// f(0) = feq(C0, K C0): lambda_F of the initial fractional terms and the u-gradient part
+template <typename real, int D>
+__global__ void __launch_bounds__(kThreads)
+adj_init_kernel(const AdjConst<real> c, const real* __restrict__ C0, const real* __restrict__ lam,
+                real* __restrict__ lF, double* __restrict__ part) {
+  const long long nodes = c.nodes;
+  const long long node = blockIdx.x * (long long)kThreads + threadIdx.x;
+  double g[2 * D];
+#pragma unroll
+  for (int k = 0; k < 2 * D; ++k) g[k] = 0.0;
+  if (node < nodes) {
+    const real l0 = lam[node];
+    const real C = C0[node];
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) {
+      const real a = lam[(2 * mu + 1) * nodes + node], b = lam[(2 * mu + 2) * nodes + node];
+      lF[mu * nodes + node] = -c.w0 * l0 + c.wi * (a + b);
+      g[mu] = static_cast<double>(c.cu) * static_cast<double>(C) * static_cast<double>(a - b);
+    }
+  }
+  block_accumulate<2 * D>(g, part);
+}
+
+// lambda(t) = lambda_f + lambda_C(local) + sum_mu K_mu^T lambda_F_mu (+ 2 (C - obs))
+template <typename real, int D>
+__global__ void adj_combine_kernel(long long nodes, const real* __restrict__ lf, const real* __restrict__ lcl,
+                                   const real* __restrict__ lcf, const real* __restrict__ C,
+                                   const real* __restrict__ obs, real* __restrict__ lam) {
+  constexpr int Q = 2 * D + 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+       i += (long long)gridDim.x * blockDim.x) {
+    real r = lcl[i];
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) r += lcf[mu * nodes + i];
+    if (obs) r += static_cast<real>(2) * (C[i] - obs[i]);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lam[q * nodes + i] = lf[q * nodes + i] + r;
+  }
+}
+
+// lambda = 2 (C - obs) on every population (the last snapshot)
+template <typename real, int Q>
+__global__ void adj_residual_kernel(long long nodes, const real* __restrict__ C, const real* __restrict__ obs,
+                                    real* __restrict__ lam) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+       i += (long long)gridDim.x * blockDim.x) {
+    const real r = static_cast<real>(2) * (C[i] - obs[i]);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lam[q * nodes + i] = r;
+  }
+}
+
+// node index of (line o, position k along axis mu)
+__device__ __forceinline__ long long line_node(int mu, long long o, int k, int n0, int n1) {
+  if (mu == 0) return o * n0 + k;
+  if (mu == 1) {
+    const long long z = o / n0, x = o % n0;
+    return (z * n1 + k) * n0 + x;
+  }
+  return (long long)k * n0 * n1 + o;
+}
+
+// G[n][l] += sum over the lines of axis mu of A(line, n) B(line, l), FP64
+template <typename real>
+__global__ void adj_G_kernel(int mu, int n0, int n1, int n2, const real* __restrict__ A, const real* __restrict__ B,
+                             double* __restrict__ G) {
+  const int side = (mu == 0) ? n0 : (mu == 1 ? n1 : n2);
+  const long long lines = (long long)n0 * n1 * n2 / side;
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.y * blockDim.y + threadIdx.y;
+  if (l >= side || n >= side) return;
+  double acc = 0.0;
+  for (long long o = 0; o < lines; ++o)
+    acc += static_cast<double>(A[line_node(mu, o, n, n0, n1)]) * static_cast<double>(B[line_node(mu, o, l, n0, n1)]);
+  G[(long long)n * side + l] += acc;
+}
+
+// sum (C - obs)^2 into *out (FP64; partial sums per block then one block)
+template <typename real>
+__global__ void __launch_bounds__(kThreads)
+adj_loss_partials(long long nodes, const real* __restrict__ C, const real* __restrict__ obs, double* __restrict__ part) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < nodes; i += (long long)gridDim.x * kThreads) {
+    const double r = static_cast<double>(C[i]) - static_cast<double>(obs[i]);
+    acc += r * r;
+  }
+  double v[1] = {acc};
+  // reuse the fixed-order block reduction on a zeroed slot
+  if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
+  __syncthreads();
+  block_accumulate<1>(v, part);
+}
+
+__global__ void adj_sum_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) acc += part[i];
+    *out = acc;
+  }
+}
+
+template <typename real>
+AdjConst<real> make_adj(const lbm_s* h, const double dOm[3][kMaxQ][kMaxQ]) {
+  AdjConst<real> c{};
+  for (int i = 0; i < 3; ++i) c.n[i] = h->sp.n[i];
+  c.nodes = h->sp.nodes;
+  for (int i = 0; i < kMaxQ; ++i)
+    for (int j = 0; j < kMaxQ; ++j) {
+      c.omT[i][j] = static_cast<real>(h->sp.omega[j][i]);
+      for (int mu = 0; mu < 3; ++mu) c.dOm[mu][i][j] = static_cast<real>(dOm[mu][i][j]);
+    }
+  c.w0 = static_cast<real>(h->sp.w0);
+  c.wi = static_cast<real>(h->sp.wi);
+  for (int mu = 0; mu < 3; ++mu) c.advw[mu] = static_cast<real>(h->sp.adv[mu] * h->sp.wi);
+  const double e2 = (h->d == 2) ? 1.0 / 3.0 : 1.0 / 4.0;
+  c.cu = static_cast<real>((h->prm.dt / h->prm.dx) * h->sp.wi / e2);
+  return c;
+}
+
+struct Buffers {
+  std::vector<void*> ptrs;
+  void* get(size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    return p;
+  }
+  ~Buffers() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+template <typename real, int D>
+int run_adjoint(lbm_s* h, const AdjHooks& hooks, int nsnap, const int* snaps, const double* obs_host, int ckpt,
+                const double dOm[3][kMaxQ][kMaxQ], double* loss, double* G_host, double* gpart_host) {
+  constexpr int Q = 2 * D + 1;
+  cudaStream_t s = h->stream;
+  const long long nodes = h->sp.nodes;
+  const size_t E = sizeof(real);
+  const int T = snaps[nsnap - 1];
+  const int nck = T / ckpt + 1;
+  const int seglen = ckpt < T ? ckpt : (T > 0 ? T : 1);
+  const int nb = static_cast<int>((nodes + kThreads - 1) / kThreads);
+  const int cb = std::min<long long>((nodes + kThreads - 1) / kThreads, 152 * 8);
+  Buffers B;
+  real* obs = static_cast<real*>(B.get(E * nodes * nsnap));
+  real* ck = static_cast<real*>(B.get(E * Q * nodes * nck));
+  real* sf = static_cast<real*>(B.get(E * Q * nodes * seglen));
+  real* sF = static_cast<real*>(B.get(E * D * nodes * seglen));
+  real* sC = static_cast<real*>(B.get(E * nodes * seglen));
+  real* lam = static_cast<real*>(B.get(E * Q * nodes));
+  real* lf = static_cast<real*>(B.get(E * Q * nodes));
+  real* lcl = static_cast<real*>(B.get(E * nodes));
+  real* lF = static_cast<real*>(B.get(E * D * nodes));
+  real* lcf = static_cast<real*>(B.get(E * D * nodes));
+  size_t gsz = 0;
+  for (int mu = 0; mu < D; ++mu) gsz += (size_t)h->sp.n[mu] * h->sp.n[mu];
+  double* G = static_cast<double*>(B.get(sizeof(double) * gsz));
+  double* gpart = static_cast<double*>(B.get(sizeof(double) * nb * 2 * D));
+  double* lpart = static_cast<double*>(B.get(sizeof(double) * nb));
+  double* lossd = static_cast<double*>(B.get(sizeof(double) * nsnap));
+  if (!obs || !ck || !sf || !sF || !sC || !lam || !lf || !lcl || !lF || !lcf || !G || !gpart || !lpart || !lossd)
+    return LBM_ENOMEM;
+#define CK(x)                                    \
+  do {                                           \
+    if ((x) != cudaSuccess) return LBM_ECUDA;    \
+  } while (0)
+  // observations in the working precision
+  for (int k = 0; k < nsnap; ++k) {
+    CK(cudaMemcpyAsync(h->dev.stage, obs_host + (size_t)k * nodes, sizeof(double) * nodes, cudaMemcpyHostToDevice, s));
+    CK(launch_convert_in(h->dev.stage, obs + (size_t)k * nodes, (int)E, nodes, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(cudaMemsetAsync(G, 0, sizeof(double) * gsz, s));
+  CK(cudaMemsetAsync(gpart, 0, sizeof(double) * nb * 2 * D, s));
+  CK(cudaMemsetAsync(lossd, 0, sizeof(double) * nsnap, s));
+  const AdjConst<real> c = make_adj<real>(h, dOm);
+  auto snap_index = [&](int t) {
+    for (int k = 0; k < nsnap; ++k)
+      if (snaps[k] == t) return k;
+    return -1;
+  };
+  auto loss_at = [&](int k, const real* C) -> cudaError_t {
+    adj_loss_partials<real><<<nb, kThreads, 0, s>>>(nodes, C, obs + (size_t)k * nodes, lpart);
+    adj_sum_kernel<<<1, 32, 0, s>>>(lpart, nb, lossd + k);
+    return cudaGetLastError();
+  };
+
+  // ---- forward pass from the initial state, checkpoints every ckpt steps, losses
+  int rc = hooks.reset(h);
+  if (rc) return rc;
+  int cur = h->cur;
+  for (int t = 0; t < T; ++t) {
+    if (t % ckpt == 0)
+      CK(cudaMemcpyAsync(ck + (size_t)(t / ckpt) * Q * nodes, h->dev.f[cur], E * Q * nodes, cudaMemcpyDeviceToDevice, s));
+    const int k0 = snap_index(t);
+    if (k0 >= 0) CK(loss_at(k0, static_cast<const real*>(h->dev.C)));
+    if ((rc = hooks.step(h, cur, s))) return rc;
+  }
+  {
+    const int k = snap_index(T);
+    CK(loss_at(k, static_cast<const real*>(h->dev.C)));
+    // lambda(T) = 2 (C(T) - obs)
+    adj_residual_kernel<real, Q><<<cb, kThreads, 0, s>>>(nodes, static_cast<const real*>(h->dev.C),
+                                                          obs + (size_t)k * nodes, lam);
+    CK(cudaGetLastError());
+  }
+
+  // ---- backward, segment by segment
+  const int nseg = (T + ckpt - 1) / ckpt;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int t0 = seg * ckpt, t1 = std::min(t0 + ckpt, T);
+    int c2 = 0;
+    CK(cudaMemcpyAsync(h->dev.f[0], ck + (size_t)seg * Q * nodes, E * Q * nodes, cudaMemcpyDeviceToDevice, s));
+    CK(launch_moment(h, h->dev.f[0], h->dev.C, s));
+    for (int t = t0; t < t1; ++t) {
+      const int i = t - t0;
+      CK(cudaMemcpyAsync(sf + (size_t)i * Q * nodes, h->dev.f[c2], E * Q * nodes, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(sC + (size_t)i * nodes, h->dev.C, E * nodes, cudaMemcpyDeviceToDevice, s));
+      CK(launch_frac_simt(h, h->dev.C, h->dev.F, s));
+      CK(cudaMemcpyAsync(sF + (size_t)i * D * nodes, h->dev.F, E * D * nodes, cudaMemcpyDeviceToDevice, s));
+      CK(launch_collide_stream(h, h->dev.f[c2], h->dev.f[c2 ^ 1], h->dev.C, s));
+      c2 ^= 1;
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      const int i = t - t0;
+      const real* Ct = sC + (size_t)i * nodes;
+      adj_step_kernel<real, D><<<nb, kThreads, 0, s>>>(c, sf + (size_t)i * Q * nodes, sF + (size_t)i * D * nodes, lam,
+                                                       lf, lcl, lF, gpart);
+      CK(cudaGetLastError());
+      CK(launch_frac_simt_T(h, lF, lcf, s));
+      size_t goff = 0;
+      for (int mu = 0; mu < D; ++mu) {
+        const int side = h->sp.n[mu];
+        dim3 blk(32, 8), grd((side + 31) / 32, (side + 7) / 8);
+        adj_G_kernel<real><<<grd, blk, 0, s>>>(mu, h->sp.n[0], h->sp.n[1], h->sp.n[2], lF + (size_t)mu * nodes, Ct,
+                                                G + goff);
+        goff += (size_t)side * side;
+      }
+      const int k = snap_index(t);
+      adj_combine_kernel<real, D><<<cb, kThreads, 0, s>>>(nodes, lf, lcl, lcf, Ct,
+                                                          k >= 0 ? obs + (size_t)k * nodes : nullptr, lam);
+      CK(cudaGetLastError());
+    }
+  }
+  // ---- the initial condition f(0) = feq(C0, K C0)
+  adj_init_kernel<real, D><<<nb, kThreads, 0, s>>>(c, static_cast<const real*>(h->dev.C0), lam, lF, gpart);
+  CK(cudaGetLastError());
+  {
+    size_t goff = 0;
+    for (int mu = 0; mu < D; ++mu) {
+      const int side = h->sp.n[mu];
+      dim3 blk(32, 8), grd((side + 31) / 32, (side + 7) / 8);
+      adj_G_kernel<real><<<grd, blk, 0, s>>>(mu, h->sp.n[0], h->sp.n[1], h->sp.n[2], lF + (size_t)mu * nodes,
+                                              static_cast<const real*>(h->dev.C0), G + goff);
+      goff += (size_t)side * side;
+    }
+    CK(cudaGetLastError());
+  }
+  std::vector<double> lossv(nsnap);
+  CK(cudaMemcpyAsync(lossv.data(), lossd, sizeof(double) * nsnap, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(G_host, G, sizeof(double) * gsz, cudaMemcpyDeviceToHost, s));
+  std::vector<double> gp((size_t)nb * 2 * D);
+  CK(cudaMemcpyAsync(gp.data(), gpart, sizeof(double) * gp.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+#undef CK
+  double L = 0.0;
+  for (double v : lossv) L += v;
+  *loss = L;
+  for (int k = 0; k < 2 * D; ++k) {
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) acc += gp[(size_t)b * 2 * D + k];
+    gpart_host[k] = acc;
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+int adjoint_grad(lbm_s* h, const AdjHooks& hooks, int nsnap, const int* snaps, const double* obs, int ckpt,
+                 const double dOm[3][kMaxQ][kMaxQ], double* loss, double* G, double* gsum) {
+  if (h->elem == 8) {
+    return (h->d == 2) ? run_adjoint<double, 2>(h, hooks, nsnap, snaps, obs, ckpt, dOm, loss, G, gsum)
+                       : run_adjoint<double, 3>(h, hooks, nsnap, snaps, obs, ckpt, dOm, loss, G, gsum);
+  }
+  return (h->d == 2) ? run_adjoint<float, 2>(h, hooks, nsnap, snaps, obs, ckpt, dOm, loss, G, gsum)
+                     : run_adjoint<float, 3>(h, hooks, nsnap, snaps, obs, ckpt, dOm, loss, G, gsum);
+}
+
+}  // namespace lbm

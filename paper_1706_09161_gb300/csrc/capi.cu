@@ -175,6 +175,51 @@ int derive(const lbm_params* p, Derived* out) {
   return LBM_OK;
 }
 
+// dOmega/dD_mumu for MRT: Omega = M^-1 Lambda M, Lambda = (Lambda^-1)^-1 and
+// dLambda^-1/dD_mumu = dt/(e^2 dx^2) at the flux entry (1+mu, 1+mu) (Eqs. MatrixS, D_ab),
+// so dOmega/dD_mumu = -M^-1 Lambda E_mu Lambda M.
+int derive_dOmega(const lbm_params* p, double dOm[3][lbm::kMaxQ][lbm::kMaxQ]) {
+  const int d = (p->lattice == LBM_D2Q5) ? 2 : 3;
+  const int Q = 2 * d + 1;
+  const double e2 = (d == 2) ? 1.0 / 3.0 : 1.0 / 4.0;
+  const double ratio = p->dt / (p->dx * p->dx);
+  double laminv[49] = {0}, lam[49], M[49], Minv[49];
+  laminv[0] = 1.0;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) laminv[(1 + i) * Q + (1 + j)] = p->D[3 * i + j] * ratio / e2 + (i == j ? 0.5 : 0.0);
+  for (int k = 0; k < Q - d - 1; ++k) laminv[(d + 1 + k) * Q + (d + 1 + k)] = 1.0 / p->s_free[k];
+  if (!invert(Q, laminv, lam)) return LBM_EINVAL;
+  moment_matrix(d, M);
+  for (int i = 0; i < Q; ++i) {
+    double nrm = 0.0;
+    for (int j = 0; j < Q; ++j) nrm += M[i * Q + j] * M[i * Q + j];
+    for (int j = 0; j < Q; ++j) Minv[j * Q + i] = M[i * Q + j] / nrm;
+  }
+  for (int mu = 0; mu < 3; ++mu)
+    for (int i = 0; i < lbm::kMaxQ; ++i)
+      for (int j = 0; j < lbm::kMaxQ; ++j) dOm[mu][i][j] = 0.0;
+  for (int mu = 0; mu < d; ++mu) {
+    const int r = 1 + mu;
+    double dL[49], t1[49];
+    // dLambda = -Lambda[:, r] * ratio/e2 * Lambda[r, :]
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < Q; ++j) dL[i * Q + j] = -lam[i * Q + r] * (ratio / e2) * lam[r * Q + j];
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < Q; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < Q; ++k) s += dL[i * Q + k] * M[k * Q + j];
+        t1[i * Q + j] = s;
+      }
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < Q; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < Q; ++k) s += Minv[i * Q + k] * t1[k * Q + j];
+        dOm[mu][i][j] = s;
+      }
+  }
+  return LBM_OK;
+}
+
 void free_all(lbm_s* h) {
   for (int i = 0; i < 2; ++i) {
     if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
@@ -615,6 +660,46 @@ int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host) {
   const int d = (prm->lattice == LBM_D2Q5) ? 2 : 3;
   if (mu < 0 || mu >= d) return LBM_EINVAL;
   lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], prm->g[mu] * dv.h[mu], prm->grid[mu], prm->dx, K_host);
+  return LBM_OK;
+}
+
+static int reset_hook(lbm_s* h) { return lbm_reset(h); }
+static int step_hook(lbm_s* h, int& cur, cudaStream_t s) { return one_step(h, cur, s); }
+
+int lbm_grad(lbm_t h, int nsnap, const int* snap_steps, const double* obs, int ckpt_every, double* loss,
+             double* grad) {
+  if (!h || nsnap < 1 || !snap_steps || !obs || ckpt_every < 1 || !loss || !grad) return LBM_EINVAL;
+  if (h->is_batch() || h->tc || h->prm.collision != LBM_MRT) return LBM_ENOTSUP;
+  for (int k = 0; k < nsnap; ++k)
+    if (snap_steps[k] < 0 || (k > 0 && snap_steps[k] <= snap_steps[k - 1])) return LBM_EINVAL;
+  double dOm[3][lbm::kMaxQ][lbm::kMaxQ];
+  int rc = derive_dOmega(&h->prm, dOm);
+  if (rc) return rc;
+  const int d = h->d;
+  size_t gsz = 0;
+  for (int mu = 0; mu < d; ++mu) gsz += (size_t)h->sp.n[mu] * h->sp.n[mu];
+  std::vector<double> G(gsz), gsum(2 * d);
+  const lbm::AdjHooks hooks{reset_hook, step_hook};
+  rc = lbm::adjoint_grad(h, hooks, nsnap, snap_steps, obs, ckpt_every, dOm, loss, G.data(), gsum.data());
+  const int rc2 = lbm_reset(h);  // the populations were overwritten by the recomputation
+  if (rc) return rc;
+  if (rc2) return rc2;
+  size_t goff = 0;
+  for (int mu = 0; mu < d; ++mu) {
+    const int side = h->sp.n[mu];
+    std::vector<double> da((size_t)side * side), dp((size_t)side * side);
+    lbm::build_frac_matrix_grad(h->prm.alpha[mu], h->prm.p[mu], h->prm.g[mu], side, h->prm.dx, da.data(), dp.data());
+    double sa = 0.0, sp_ = 0.0;
+    for (size_t i = 0; i < da.size(); ++i) {
+      sa += da[i] * G[goff + i];
+      sp_ += dp[i] * G[goff + i];
+    }
+    grad[mu] = sa;
+    grad[d + mu] = sp_;
+    grad[2 * d + mu] = gsum[d + mu];
+    grad[3 * d + mu] = gsum[mu];
+    goff += (size_t)side * side;
+  }
   return LBM_OK;
 }
 

@@ -86,12 +86,15 @@ cudaError_t gemm(int M, int N, int K, int batch, const real* A, long long lda, l
   return cudaGetLastError();
 }
 
+// transpose = false: F_mu = K_mu applied along mu to C (one input for every axis);
+// transpose = true:  F_mu = K_mu^T applied along mu to C_mu (C holds one field per axis)
 template <typename real>
-cudaError_t frac_all_axes(const lbm_s* h, const real* C, real* F, cudaStream_t s) {
+cudaError_t frac_all_axes(const lbm_s* h, const real* C, real* F, cudaStream_t s, bool transpose = false) {
   const int n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
   const long long nodes = h->sp.nodes;
-  const real* K = static_cast<const real*>(h->dev.K);
-  const real* KT = static_cast<const real*>(h->dev.KT);
+  const real* K = static_cast<const real*>(transpose ? h->dev.KT : h->dev.K);
+  const real* KT = static_cast<const real*>(transpose ? h->dev.K : h->dev.KT);
+  const long long cstride = transpose ? nodes : 0;
   long long koff = 0;
   cudaError_t err;
   // axis x: F_0 = C (rows x n0) * K_0^T
@@ -99,19 +102,25 @@ cudaError_t frac_all_axes(const lbm_s* h, const real* C, real* F, cudaStream_t s
   if (err != cudaSuccess) return err;
   koff += (long long)n0 * n0;
   // axis y: for each z-plane b, F_1[b] = K_1 * C[b]  (C[b] is n1 x n0)
-  err = gemm<real>(n1, n0, n1, n2, K + koff, n1, 0, C, n0, (long long)n1 * n0, F + nodes, n0,
+  err = gemm<real>(n1, n0, n1, n2, K + koff, n1, 0, C + cstride, n0, (long long)n1 * n0, F + nodes, n0,
                    (long long)n1 * n0, s);
   if (err != cudaSuccess) return err;
   koff += (long long)n1 * n1;
   if (h->d == 3) {
     // axis z: F_2 = K_2 * C  (C is n2 x (n1 n0))
-    err = gemm<real>(n2, n0 * n1, n2, 1, K + koff, n2, 0, C, (long long)n0 * n1, 0, F + 2 * nodes,
+    err = gemm<real>(n2, n0 * n1, n2, 1, K + koff, n2, 0, C + 2 * cstride, (long long)n0 * n1, 0, F + 2 * nodes,
                      (long long)n0 * n1, 0, s);
   }
   return err;
 }
 
 }  // namespace
+
+cudaError_t launch_frac_simt_T(const lbm_s* h, const void* in, void* out, cudaStream_t s) {
+  if (h->elem == 8)
+    return frac_all_axes<double>(h, static_cast<const double*>(in), static_cast<double*>(out), s, true);
+  return frac_all_axes<float>(h, static_cast<const float*>(in), static_cast<float*>(out), s, true);
+}
 
 cudaError_t launch_frac_simt(const lbm_s* h, const void* C, void* F, cudaStream_t s) {
   if (h->elem == 8) return frac_all_axes<double>(h, static_cast<const double*>(C), static_cast<double*>(F), s);

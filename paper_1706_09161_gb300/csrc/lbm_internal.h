@@ -114,4 +114,14 @@ void build_frac_matrix(double alpha, double p, double scale_g, int side, double 
 void build_frac_matrix_grad(double alpha, double p, double scale_g, int side, double dx, double* dKda, double* dKdp);
 double digamma_fn(double x);
 
+// adjoint driver (adjoint.cu); the handle's own reset and step are passed in
+struct AdjHooks {
+  int (*reset)(lbm_s*);
+  int (*step)(lbm_s*, int&, cudaStream_t);
+};
+int adjoint_grad(lbm_s* h, const AdjHooks& hooks, int nsnap, const int* snaps, const double* obs, int ckpt,
+                 const double dOm[3][kMaxQ][kMaxQ], double* loss, double* G, double* gsum);
+// transpose of the SIMT fractional operator: out_mu = K_mu^T applied along axis mu to in_mu
+cudaError_t launch_frac_simt_T(const lbm_s* h, const void* in, void* out, cudaStream_t s);
+
 }  // namespace lbm

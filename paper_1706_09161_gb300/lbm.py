@@ -85,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "lbm_get_stream": (ctypes.c_int, [vp, P(vp)]),
         "lbm_launches_per_step": (ctypes.c_int, [vp, P(ctypes.c_int)]),
         "lbm_frac_matrix": (ctypes.c_int, [P(lbm_params), ctypes.c_int, dp]),
+        "lbm_grad": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), dp, ctypes.c_int, dp, dp]),
         "lbm_frac_matrix_grad": (ctypes.c_int, [P(lbm_params), ctypes.c_int, dp, dp]),
         "lbm_digamma": (ctypes.c_double, [ctypes.c_double]),
         "lbm_mass_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_longlong, vp, vp]),
@@ -104,7 +105,7 @@ _lib = _load()
 # Declared C entry points, re-exported under their own names.
 EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_read_C", "lbm_batch_mass", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f",
             "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_frac_matrix",
-            "lbm_frac_matrix_grad", "lbm_digamma", "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
+            "lbm_grad", "lbm_frac_matrix_grad", "lbm_digamma", "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
 
 
 def lbm_strerror(code: int) -> str:
@@ -266,6 +267,17 @@ def lbm_mass_static(x_dev: int, elem_bytes: int, n: int, sum_dev: int, stream: O
                                      ctypes.c_void_p(stream or 0)))
 
 
+def lbm_grad(h: int, snap_steps, obs: np.ndarray, ckpt_every: int, d: int):
+    """(loss, grad[4d]) of the snapshot misfit; grad = dL/d[alpha, p, D_diag, u]."""
+    snaps = (ctypes.c_int * len(snap_steps))(*[int(t) for t in snap_steps])
+    obs = np.ascontiguousarray(obs, dtype=np.float64)
+    loss = ctypes.c_double()
+    grad = np.zeros(4 * d, dtype=np.float64)
+    _check(_lib.lbm_grad(ctypes.c_void_p(h), len(snap_steps), snaps, _dptr(obs), int(ckpt_every), ctypes.byref(loss),
+                         _dptr(grad)), "lbm_grad")
+    return loss.value, grad
+
+
 def lbm_frac_matrix_grad(prm: lbm_params, mu: int):
     side = prm.grid[mu]
     da = np.empty((side, side), dtype=np.float64)
@@ -337,6 +349,10 @@ class Lattice:
 
     def sync(self) -> None:
         _check(lbm_sync(self.h), "lbm_sync")
+
+    def grad(self, snap_steps, obs: np.ndarray, ckpt_every: int = 100):
+        """(loss, dL/d[alpha, p, D_diag, u]) of sum_k |C(t_k) - obs_k|^2 via the discrete adjoint."""
+        return lbm_grad(self.h, snap_steps, obs, ckpt_every, self.d)
 
     @property
     def stream(self) -> int:

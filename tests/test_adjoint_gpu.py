@@ -1,0 +1,94 @@
+"""The GPU discrete adjoint (lbm_grad) against the FP64 oracle's adjoint (autograd through
+the plain restatement, itself pinned to central finite differences in the CPU tests).
+
+Bounds: FP64 handles 1e-8 relative per gradient component; FP32 handles 1e-4 relative
+(BASELINE's gradient bar) on gradient components larger than 1e-3 of the largest one."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lbm_oracle as O
+from paper_1706_09161_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1706_09161_gb300 import build
+    build.build()
+    from paper_1706_09161_gb300 import lbm
+    return lbm
+
+
+def observations(pb, C0, snaps, seed, noise=1e-4):
+    """Snapshots of the scheme run with perturbed parameters (oracle), plus N(0, noise^2)."""
+    pb_obs = dataclasses.replace(pb, alpha=tuple(min(2.0, a + 0.04) for a in pb.alpha),
+                                 p=tuple(min(1.0, max(0.0, p - 0.05)) for p in pb.p),
+                                 u=tuple(0.9 * v for v in pb.u))
+    ops = O.Operators(pb_obs)
+    f = O.init_populations(ops, torch.tensor(C0))
+    out, t = [], 0
+    rng = np.random.default_rng(seed)
+    for ts in snaps:
+        while t < ts:
+            f = O.step(ops, f)
+            t += 1
+        out.append(O.concentration(f).numpy() + noise * rng.normal(size=pb.shape) * C0.max())
+    return np.stack(out)
+
+
+def check(L, pb, C0, snaps, ckpt, precision, rtol):
+    obs = observations(pb, C0, snaps, seed=len(snaps))
+    loss_ref, grad_ref = O.loss_and_grad(pb, C0, snaps, torch.tensor(obs))
+    grad_ref = grad_ref.numpy()
+    with L.Lattice(pb, C0, precision) as lat:
+        loss, grad = lat.grad(snaps, obs, ckpt)
+        C_after = lat.C()
+    assert loss == pytest.approx(loss_ref, rel=max(rtol, 1e-12))
+    big = np.abs(grad_ref) > 1e-3 * np.abs(grad_ref).max()
+    rel = np.abs(grad - grad_ref) / np.maximum(np.abs(grad_ref), 1e-300)
+    assert np.all(rel[big] < rtol), (grad, grad_ref)
+    # the handle is left at its initial state
+    assert np.allclose(C_after.sum(), O.concentration(O.init_populations(O.Operators(pb), torch.tensor(C0))).sum(),
+                       rtol=1e-6)
+
+
+@pytest.mark.parametrize("grid,snaps,ckpt", [((24, 20), [10, 20, 30], 7), ((37, 29), [0, 15, 16, 40], 10)])
+def test_adjoint_fp64_2d(L, grid, snaps, ckpt):
+    rng = np.random.default_rng(grid[0])
+    pb = W.random_problem(rng, 2, "mrt", grid)
+    check(L, pb, W.random_field(rng, grid), snaps, ckpt, "fp64", 1e-8)
+
+
+def test_adjoint_fp64_3d(L):
+    rng = np.random.default_rng(41)
+    pb = W.random_problem(rng, 3, "mrt", (12, 10, 9))
+    check(L, pb, W.random_field(rng, pb.grid), [6, 12], 5, "fp64", 1e-8)
+
+
+def test_adjoint_fp32_2d(L):
+    rng = np.random.default_rng(43)
+    pb = W.random_problem(rng, 2, "mrt", (40, 33))
+    check(L, pb, W.random_field(rng, pb.grid), [20, 40, 60], 25, "fp32", 1e-4)
+
+
+def test_adjoint_inverse_workload_reduced(L):
+    """The inverse-problem workload's parameters on a 64x64 grid, 300 steps, 3 snapshots,
+    checkpoint every 100 (FP32 forward and adjoint)."""
+    pb, C0, _ = W.inverse_256(side=64)
+    check(L, pb, C0, [100, 200, 300], 100, "fp32", 1e-4)
+
+
+def test_grad_refuses_unsupported(L):
+    rng = np.random.default_rng(1)
+    pb = W.random_problem(rng, 2, "bgk", (20, 20), spherical=True)
+    C0 = W.random_field(rng, pb.grid)
+    with L.Lattice(pb, C0, "fp32") as lat:
+        with pytest.raises(L.LBMError) as ei:
+            lat.grad([5], np.zeros((1,) + pb.shape), 2)
+        assert ei.value.code == L.LBM_ENOTSUP
