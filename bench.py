@@ -46,6 +46,11 @@ WORKLOADS = {
                          "alpha~U[1.2,2], p~U[0,1], D~U[1e-4,3e-3] diagonal, |u|<=0.08, Gaussian pulses sigma~U[2,6], "
                          "free rates U[0.8,1.9], 1000 steps each, grouped launches",
                     default_precision="bf16split"),
+    "inverse_256": dict(desc="inverse problem: 2-D D2Q5 MRT 256x256, alpha=(1.45,1.75), p=(0.35,0.65), "
+                             "D=diag(1.5e-3,7e-4), u=(0.04,-0.01); loss over 10 snapshots of 3000 steps + N(0,1e-4) noise; "
+                             "one bench step = one loss+gradient evaluation (forward, checkpointed recompute, adjoint; "
+                             "checkpoint every 100); value counts forward lattice updates",
+                        default_precision="fp32"),
     "mrt3d_128": dict(desc="3-D D3Q7 MRT 128^3 with the 256^3 workload's parameters (profiling captures only)",
                       default_precision="bf16split"),
     "mrt3d_256": dict(desc="3-D fractional ADE, D3Q7 MRT, 256^3, alpha=(1.6,1.6,1.9), p=(0.5,0.2,0.8), g=(1,1,1), "
@@ -74,6 +79,9 @@ def make_workload(name):
     from paper_1706_09161_gb300 import workloads as W
     if name == "batch64":
         return W.batch64()
+    if name == "inverse_256":
+        pb, C0, snaps = W.inverse_256()
+        return [pb], [C0], snaps[-1]
     pb, C0, n = W.mrt3d_256(128) if name == "mrt3d_128" else getattr(W, name)()
     return [pb], [C0], n
 
@@ -182,6 +190,18 @@ def run_reference(args):
     return 0
 
 
+def job_value(local_ms, units_per_rank, world, dist=None, device=None):
+    """Whole-job throughput in MLUPS: every rank's lattice updates over the slowest rank's
+    time (max over ranks through an all-reduce), and that time in ms."""
+    t = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * units_per_rank / (t * 1e-3) / 1e6, t
+
+
 def source_sha(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -251,6 +271,20 @@ def main():
     stream = torch.cuda.ExternalStream(lat.stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    inverse = args.workload == "inverse_256"
+    if inverse:
+        from paper_1706_09161_gb300 import workloads as W
+        _, _, snaps = W.inverse_256()
+        # synthetic observations: the GPU forward run itself plus N(0, (1e-4)^2) noise
+        obs = []
+        lat.reset()
+        t = 0
+        for ts in snaps:
+            lat.step(ts - t)
+            t = ts
+            obs.append(lat.C())
+        obs = np.stack(obs) + W.observation_noise((len(snaps),) + probs[0].shape)
+
     def one_run():
         lat.reset()
         flush.add_(1.0)  # L2 flush on torch's stream
@@ -258,7 +292,10 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        lat.step(nlbm)
+        if inverse:
+            lat.grad(snaps, obs, 100)
+        else:
+            lat.step(nlbm)
         ev1.record(stream)
         ev1.synchronize()
         return ev0.elapsed_time(ev1)
@@ -277,18 +314,19 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     rc = lbm.lbm_sync(lat.h)
-    total_ms = sum(t_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * nodes * nlbm * args.steps / (total_ms * 1e-3) / 1e6
+    value, total_ms = job_value(sum(t_ms), nodes * nlbm * args.steps, world, dist, "cuda")
     gpu_launches = args.steps * nlbm * lat.launches_per_step
+    if inverse:
+        d0 = probs[0].d
+        # forward + checkpointed recompute (d+1 each) and adjoint (step, d transposes, d G sums, combine)
+        gpu_launches = args.steps * nlbm * (2 * (d0 + 1) + 2 + 2 * d0)
 
     # ---- end to end through the C ABI with pinned host buffers
     pins = [torch.from_numpy(np.ascontiguousarray(C0)).pin_memory() for C0 in fields]
     outs = [torch.empty(p.shape, dtype=torch.float64).pin_memory() for p in pins]
     e2e_s = []
+    if inverse:
+        obs_pin = torch.from_numpy(np.ascontiguousarray(obs)).pin_memory()
     for k in range(args.steps):
         flush.add_(1.0)
         torch.cuda.synchronize()
@@ -298,6 +336,10 @@ def main():
                 lat.set_C(i, p.numpy())
             else:
                 lat.set_C(p.numpy())
+        if inverse:  # observations go host -> device inside lbm_grad; loss and gradient come back
+            lat.grad(snaps, obs_pin.numpy(), 100)
+            e2e_s.append(time.perf_counter() - t0)
+            continue
         lat.step(nlbm)
         for i, o in enumerate(outs):
             # data is copied; a latched instability is only reported
@@ -306,12 +348,12 @@ def main():
             if rc_e2e not in (lbm.LBM_OK, lbm.LBM_ERR_UNSTABLE):
                 raise lbm.LBMError(rc_e2e, "read C")
         e2e_s.append(time.perf_counter() - t0)
-    e2e_val = world * nodes * nlbm * args.steps / sum(e2e_s) / 1e6
-    if dist is not None:
-        t = torch.tensor([sum(e2e_s)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * nodes * nlbm * args.steps / float(t.item()) / 1e6
+    e2e_val, _ = job_value(1e3 * sum(e2e_s), nodes * nlbm * args.steps, world, dist, "cuda")
     io_bytes = int(sum(C0.size for C0 in fields) * 8)
+    h2d_bytes, d2h_bytes = io_bytes, io_bytes
+    if inverse:
+        h2d_bytes = io_bytes + int(obs.size * 8)
+        d2h_bytes = 8 * (1 + 4 * probs[0].d)
 
     # ---- dominant kernel, timed live with events on the library stream
     nprof = min(nlbm, 200)
@@ -381,8 +423,8 @@ def main():
                            "nodes": nodes, "problems": len(probs), "parallelism": f"replicas x{world}",
                            "l2": "flushed (512 MiB write) before every bench step; state L2-resident within a run"},
                 "roofline": roof, "cpu_baseline": cpu, "accuracy": accuracy,
-                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
-                        "d2h_bytes_per_step": io_bytes},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+                        "d2h_bytes_per_step": d2h_bytes},
                 "gpu_launches": gpu_launches, "clocks": clk,
                 "status": lbm.lbm_strerror(rc if rc else warm_status)}
         print(json.dumps(line))

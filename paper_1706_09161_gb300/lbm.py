@@ -416,3 +416,41 @@ class Batch:
     @property
     def launches_per_step(self) -> int:
         return lbm_launches_per_step(self.h)
+
+
+def _problem_with_theta(problem, theta):
+    """Copy of `problem` whose alpha, p, diagonal D and u are taken from theta (4d values)."""
+    import dataclasses
+    d = int(problem.d)
+    th = [float(v) for v in theta]
+    D = [list(row) for row in problem.D]
+    for i in range(d):
+        D[i][i] = th[2 * d + i]
+    return dataclasses.replace(problem, alpha=tuple(th[:d]), p=tuple(th[d:2 * d]),
+                               D=tuple(tuple(r) for r in D), u=tuple(th[3 * d:4 * d]))
+
+
+def snapshot_loss(problem, C0, snap_steps, obs, theta, precision: str = "fp32", ckpt_every: int = 100):
+    """Differentiable L(theta) = sum_k |C(t_k) - obs_k|^2, theta = [alpha, p, D_diag, u] (torch tensor).
+
+    Forward and gradient are one lbm_grad call (discrete adjoint on the GPU); backward
+    returns the stored gradient scaled by the incoming one.  Each call builds a handle
+    with the current parameters.
+    """
+    import torch
+
+    class _SnapshotLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th):
+            pb = _problem_with_theta(problem, th.detach().cpu().tolist())
+            with Lattice(pb, C0, precision) as lat:
+                loss, grad = lat.grad(snap_steps, obs, ckpt_every)
+            ctx.save_for_backward(torch.as_tensor(grad, dtype=th.dtype, device=th.device))
+            return th.new_tensor(loss)
+
+        @staticmethod
+        def backward(ctx, g):
+            (grad,) = ctx.saved_tensors
+            return g * grad
+
+    return _SnapshotLoss.apply(theta)

@@ -92,3 +92,42 @@ def test_grad_refuses_unsupported(L):
         with pytest.raises(L.LBMError) as ei:
             lat.grad([5], np.zeros((1,) + pb.shape), 2)
         assert ei.value.code == L.LBM_ENOTSUP
+
+
+def test_autograd_function_fits_parameters(L):
+    """snapshot_loss as a torch.autograd.Function: its gradient is lbm_grad's, and a few
+    gradient steps on alpha and u reduce the misfit (parameters fitted to observed plumes)."""
+    rng = np.random.default_rng(47)
+    pb = W.random_problem(rng, 2, "mrt", (32, 30))
+    C0 = W.random_field(rng, pb.grid)
+    snaps = [10, 20]
+    truth = dataclasses.replace(pb, alpha=tuple(min(2.0, a + 0.04) for a in pb.alpha), u=tuple(0.9 * v for v in pb.u))
+    obs = np.stack([O.run_C(truth, C0, ts).numpy() for ts in snaps])
+    d = pb.d
+    theta = torch.tensor(list(pb.alpha) + list(pb.p) + [pb.D[i][i] for i in range(d)] + list(pb.u),
+                         dtype=torch.float64, requires_grad=True)
+    loss = L.snapshot_loss(pb, C0, snaps, obs, theta, "fp64", 5)
+    loss.backward()
+    _, g_ref = O.loss_and_grad(pb, C0, snaps, torch.tensor(obs))
+    assert torch.allclose(theta.grad, g_ref, rtol=1e-8, atol=1e-14)
+    # fit alpha and u by normalised gradient steps with backtracking
+    mask = torch.zeros(4 * d, dtype=torch.float64)
+    mask[:d] = 1.0
+    mask[3 * d:] = 1.0
+    th = theta.detach().clone()
+    L0 = float(loss)
+    cur = L0
+    for _ in range(6):
+        t = th.clone().requires_grad_(True)
+        lt = L.snapshot_loss(pb, C0, snaps, obs, t, "fp64", 5)
+        lt.backward()
+        step = -(t.grad * mask)
+        step = step / step.abs().max() * 0.01
+        for _ in range(6):
+            cand = th + step
+            lc = float(L.snapshot_loss(pb, C0, snaps, obs, cand, "fp64", 5))
+            if lc < cur:
+                th, cur = cand, lc
+                break
+            step = step / 2
+    assert cur < 0.5 * L0
