@@ -52,11 +52,11 @@ WORKLOADS = {
                              "checkpoint every 100); value counts forward lattice updates",
                         default_precision="fp32"),
     "mrt3d_128": dict(desc="3-D D3Q7 MRT 128^3 with the 256^3 workload's parameters (profiling captures only)",
-                      default_precision="bf16split"),
+                      default_precision="tf32split"),
     "mrt3d_256": dict(desc="3-D fractional ADE, D3Q7 MRT, 256^3, alpha=(1.6,1.6,1.9), p=(0.5,0.2,0.8), g=(1,1,1), "
                            "D=diag(1e-3,1e-3,4e-4), u=(0.03,0,0) lattice units, free rates U[0.8,1.9] seed 3, "
                            "Dirichlet C=0, unit-mass Gaussian sigma=3, 2000 steps",
-                      default_precision="bf16split"),
+                      default_precision="tf32split"),
 }
 
 # measured peaks (driver-written), with the profiling recipe's fallback

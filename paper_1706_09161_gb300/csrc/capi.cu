@@ -270,6 +270,7 @@ int one_step(lbm_s* h, int& cur, cudaStream_t s) {
     return LBM_OK;
   }
   if (uses_tc(h)) {
+    LBM_CUDA(lbm::launch_split_T(h, s));  // tf32: transposed operands of the current C
     LBM_CUDA(lbm::launch_frac_tc(h, s));
   } else {
     int rc = run_frac(h, s);
@@ -394,7 +395,7 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   }
   if (prm->precision == LBM_FP32_BF16SPLIT || prm->precision == LBM_FP32_TF32SPLIT) {
     if ((rc = lbm::tc_prepare(h, Kall, batched ? 128 : 0, batched ? 1 : 0))) return fail(rc);
-    h->launches_per_step = 2;
+    h->launches_per_step = (prm->precision == LBM_FP32_TF32SPLIT) ? 2 + (h->d - 1) : 2;
   } else {
     h->launches_per_step = h->d + 1;
   }
@@ -530,7 +531,10 @@ int lbm_profile(lbm_t h, int nsteps, double* ms) {
         for (lbm_s* p : h->subs)
           if (e == cudaSuccess) e = lbm::launch_frac_simt(p, p->dev.C, p->dev.F, h->stream);
       if (!h->is_batch()) {
-        if (uses_tc(h)) e = lbm::launch_frac_tc(h, h->stream);
+        if (uses_tc(h)) {
+          e = lbm::launch_split_T(h, h->stream);
+          if (e == cudaSuccess) e = lbm::launch_frac_tc(h, h->stream);
+        }
         else rc = run_frac(h, h->stream);
       }
     }

@@ -74,6 +74,16 @@ struct TcPlan {
   int bn = 64;
   size_t smem = 0;
   int ldp = 0;       // padded x pitch of the C split arrays (elements)
+  // tf32 only: C split transposed so that axis mu (1: y, 2: z) is contiguous, pitch ldT
+  void* ct_hi[3] = {nullptr, nullptr, nullptr};
+  void* ct_lo[3] = {nullptr, nullptr, nullptr};
+  int ldT[3] = {0, 0, 0};
+  ~TcPlan() {
+    for (int mu = 0; mu < 3; ++mu) {
+      if (ct_hi[mu]) cudaFree(ct_hi[mu]);
+      if (ct_lo[mu]) cudaFree(ct_lo[mu]);
+    }
+  }
 };
 
 namespace {
@@ -275,6 +285,13 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
       tma_load_2d(a_lo, &maps.k_lo[0], k0, m_in, &full[s]);
       tma_load_3d(b_hi, &maps.c_hi[0], k0, ncol0, m_out, &full[s]);
       tma_load_3d(b_lo, &maps.c_lo[0], k0, ncol0, m_out, &full[s]);
+    } else if (E == 4) {
+      // tf32 parts: A = the C split transposed so that the contraction axis is contiguous
+      // (K-major), 128 x-lines per tile; B = K_mu rows
+      tma_load_3d(a_hi, &maps.c_hi[mu], k0, m_in, m_out, &full[s]);
+      tma_load_3d(a_lo, &maps.c_lo[mu], k0, m_in, m_out, &full[s]);
+      tma_load_2d(b_hi, &maps.k_hi[mu], k0, ncol0, &full[s]);
+      tma_load_2d(b_lo, &maps.k_lo[mu], k0, ncol0, &full[s]);
     } else {
 #pragma unroll
       for (int j = 0; j < E; ++j) {
@@ -322,7 +339,8 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     }
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer
-    const uint32_t idesc = (mu == 0) ? G::IDESC_K : G::IDESC_MN;
+    const bool kmajor = (mu == 0) || (E == 4);
+    const uint32_t idesc = kmajor ? G::IDESC_K : G::IDESC_MN;
     for (int i = 0; i < nkb; ++i) {
       const int s = i % G::STAGES;
       if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
@@ -333,7 +351,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
 #pragma unroll
       for (int kk = 0; kk < G::BK / Kind<E>::UK; ++kk) {
         uint32_t a_off, a_lbo;
-        if (mu == 0) {  // K-major A: advance within the 128-byte row
+        if (kmajor) {  // K-major A: advance within the 128-byte row
           a_off = kk * Kind<E>::UK * E;
           a_lbo = 16;
         } else {        // MN-major A: advance by UK rows of 128 bytes
@@ -514,6 +532,32 @@ __global__ void split_C_kernel(const float* __restrict__ C, void* __restrict__ h
   }
 }
 
+// tf32 split of C written transposed: out[(b * nb_rows + j) * ldo + i] for the element
+// in[b * bstride + i * si + j] (i along the contracted axis, j = x), through a 32 x 32
+// shared tile so that both the read (x) and the write (axis) are coalesced.
+__global__ void split_T_kernel(const float* __restrict__ C, float* __restrict__ hi, float* __restrict__ lo, int ni,
+                               int nj, long long si, long long bstride, int ldo) {
+  __shared__ float t[32][33];
+  const int b = blockIdx.z;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const float* in = C + b * bstride;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    t[r][threadIdx.x] = (i < ni && j < nj) ? in[i * si + j] : 0.0f;
+  }
+  __syncthreads();
+  const long long obase = (long long)b * nj * ldo;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, i = i0 + threadIdx.x;
+    if (i < ni && j < nj) {
+      const float c = t[threadIdx.x][r];
+      const float h = tf32_rna(c);
+      hi[obase + (long long)j * ldo + i] = h;
+      lo[obase + (long long)j * ldo + i] = tf32_rna(c - h);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------- host
 
 uint16_t bf16_rne_host(float f) {
@@ -593,13 +637,13 @@ cudaError_t launch_kernel(const TcPlan* p, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, frac_tc_kernel<E, BN, KS>, p->maps, p->prm);
 }
 
-template <int BN>
+template <int E, int BN>
 cudaError_t launch_bn(const TcPlan* p, cudaStream_t s) {
   switch (p->prm.ksplit) {
-    case 1: return launch_kernel<2, BN, 1>(p, s);
-    case 2: return launch_kernel<2, BN, 2>(p, s);
-    case 4: return launch_kernel<2, BN, 4>(p, s);
-    default: return launch_kernel<2, BN, 8>(p, s);
+    case 1: return launch_kernel<E, BN, 1>(p, s);
+    case 2: return launch_kernel<E, BN, 2>(p, s);
+    case 4: return launch_kernel<E, BN, 4>(p, s);
+    default: return launch_kernel<E, BN, 8>(p, s);
   }
 }
 
@@ -612,10 +656,8 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   h->tc = p;
   const int E = (h->prm.precision == LBM_FP32_BF16SPLIT) ? 2 : 4;
   p->elem = E;
-  // tf32 parts are only fed K-major: the y and z axes need an MN-major C panel, whose
-  // tf32 form did not reproduce the oracle, so the tf32 split serves 1-D-contiguous
-  // (x-axis) operators only and is refused for the full step.
-  if (E == 4) return LBM_ENOTSUP;
+  // tf32 parts are fed K-major on every axis: the y and z axes read copies of the C split
+  // transposed so that y (resp. z) is contiguous, written each step by split_T_kernel.
   const int n[3] = {h->sp.n[0], h->sp.n[1], h->sp.n[2]};
   int maxside = 0;
   for (int mu = 0; mu < h->d; ++mu) maxside = n[mu] > maxside ? n[mu] : maxside;
@@ -627,6 +669,17 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   if (cudaMalloc(&h->dev.Clo, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
   cudaMemset(h->dev.Chi, 0, split_elems * E);
   cudaMemset(h->dev.Clo, 0, split_elems * E);
+  if (E == 4) {
+    p->ldT[1] = (n[1] + 3) / 4 * 4;
+    p->ldT[2] = (n[2] + 3) / 4 * 4;
+    for (int mu = 1; mu < h->d; ++mu) {
+      const size_t cnt = (size_t)p->ldT[mu] * h->sp.nodes / n[mu];
+      if (cudaMalloc(&p->ct_hi[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
+      if (cudaMalloc(&p->ct_lo[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
+      cudaMemset(p->ct_hi[mu], 0, cnt * 4);
+      cudaMemset(p->ct_lo[mu], 0, cnt * 4);
+    }
+  }
 
   // weights: per axis, padded row pitch ldk
   size_t ktot = 0;
@@ -726,8 +779,18 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
     }
     a.tile_begin = tiles;
     tiles += a.tiles_m * a.tiles_n;
-    if (!encode(&p->maps.c_hi[mu], E, 3, h->dev.Chi, cdims, cstr, box)) return LBM_ECUDA;
-    if (!encode(&p->maps.c_lo[mu], E, 3, h->dev.Clo, cdims, cstr, box)) return LBM_ECUDA;
+    if (E == 4 && mu > 0) {
+      // transposed copy: dims (axis mu contiguous, x, remaining axis), box BK x 128 x 1
+      const int other = (mu == 1) ? n[2] : n[1];
+      const cuuint64_t tdims[3] = {(cuuint64_t)n[mu], (cuuint64_t)n[0], (cuuint64_t)other};
+      const cuuint64_t tstr[2] = {(cuuint64_t)p->ldT[mu] * 4, (cuuint64_t)p->ldT[mu] * n[0] * 4};
+      const cuuint32_t tbox[3] = {(cuuint32_t)BK, (cuuint32_t)BM, 1};
+      if (!encode(&p->maps.c_hi[mu], E, 3, p->ct_hi[mu], tdims, tstr, tbox)) return LBM_ECUDA;
+      if (!encode(&p->maps.c_lo[mu], E, 3, p->ct_lo[mu], tdims, tstr, tbox)) return LBM_ECUDA;
+    } else {
+      if (!encode(&p->maps.c_hi[mu], E, 3, h->dev.Chi, cdims, cstr, box)) return LBM_ECUDA;
+      if (!encode(&p->maps.c_lo[mu], E, 3, h->dev.Clo, cdims, cstr, box)) return LBM_ECUDA;
+    }
     const cuuint64_t kdims[2] = {(cuuint64_t)n[mu], (cuuint64_t)n[mu]};
     const cuuint64_t kstr[1] = {(cuuint64_t)ldk[mu] * E};
     const cuuint32_t kbox[2] = {(cuuint32_t)BK, (cuuint32_t)(mu == 0 ? BM : p->bn)};
@@ -809,8 +872,27 @@ int tc_split_pitch(const lbm_s* h) { return h->tc ? h->tc->ldp : 0; }
 
 cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s) {
   const TcPlan* p = h->tc;
-  if (!p || p->elem != 2) return cudaErrorNotSupported;
-  return (p->bn == 128) ? launch_bn<128>(p, s) : launch_bn<256>(p, s);
+  if (!p) return cudaErrorNotSupported;
+  if (p->elem == 2) return (p->bn == 128) ? launch_bn<2, 128>(p, s) : launch_bn<2, 256>(p, s);
+  return (p->bn == 128) ? launch_bn<4, 128>(p, s) : launch_bn<4, 256>(p, s);
+}
+
+cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s) {
+  const TcPlan* p = h->tc;
+  if (!p || p->elem != 4) return cudaSuccess;
+  const int n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
+  dim3 blk(32, 8);
+  const float* C = static_cast<const float*>(h->dev.C);
+  // y contiguous: per z plane, element (y, x) at C[z][y][x] -> out[z][x][y]
+  split_T_kernel<<<dim3((n0 + 31) / 32, (n1 + 31) / 32, n2), blk, 0, s>>>(
+      C, static_cast<float*>(p->ct_hi[1]), static_cast<float*>(p->ct_lo[1]), n1, n0, n0, (long long)n0 * n1, p->ldT[1]);
+  if (h->d == 3) {
+    // z contiguous: per y row, element (z, x) at C[z][y][x] -> out[y][x][z]
+    split_T_kernel<<<dim3((n0 + 31) / 32, (n2 + 31) / 32, n1), blk, 0, s>>>(
+        C, static_cast<float*>(p->ct_hi[2]), static_cast<float*>(p->ct_lo[2]), n2, n0, (long long)n0 * n1, n0,
+        p->ldT[2]);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s) {
@@ -824,7 +906,9 @@ cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s) {
   else
     split_C_kernel<4><<<(int)b, 256, 0, s>>>(static_cast<const float*>(h->dev.C), h->dev.Chi, h->dev.Clo, h->sp.n[0],
                                              h->sp.n[1], h->sp.n[2], p->ldp);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_split_T(h, s);
 }
 
 }  // namespace lbm

@@ -94,8 +94,10 @@ cudaError_t launch_convert_in(const void* src_f64, void* dst, int elem, long lon
 cudaError_t launch_convert_out(const void* src, int elem, double* dst_f64, long long n, cudaStream_t s);
 // mass reduction: partials then final
 cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
-// split C into hi/lo operands for the tensor-core path
+// split C into hi/lo operands for the tensor-core path (tf32: also the transposed copies)
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s);
+// tf32 only: the transposed copies of the split of the current C (no-op otherwise)
+cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s);
 int reduce_blocks_for(long long n);
 // tensor-core plan: split K_mu (row-major FP64 per axis), allocate split C, encode TMA maps
 // force_bn / force_ks (> 0) fix the column-tile width and k-split (grouped batches use 128 / 1)

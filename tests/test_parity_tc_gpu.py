@@ -18,8 +18,8 @@ from paper_1706_09161_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-F_TOL = {"bf16split": 4e-5}
-KINDS = ["bf16split"]
+F_TOL = {"bf16split": 4e-5, "tf32split": 2e-6}
+KINDS = ["bf16split", "tf32split"]
 
 
 @pytest.fixture(scope="module")
@@ -105,10 +105,10 @@ def test_tc_graph_replay_deterministic(L):
         assert L.lbm_sync(a.h) == 0
 
 
-def test_tf32split_is_refused(L):
-    """The tf32 split is not offered for the full step (its MN-major operand form is not built)."""
-    rng = np.random.default_rng(3)
-    pb = W.random_problem(rng, 2, "mrt", (20, 20))
-    with pytest.raises(L.LBMError) as ei:
-        L.Lattice(pb, W.random_field(rng, pb.grid), "tf32split")
-    assert ei.value.code == L.LBM_ENOTSUP
+def test_tf32split_config_mrt3d_256_full_size(L):
+    """The 256^3 workload with the tf32 split (its stated form), first 2 steps."""
+    pb, C0, _ = W.mrt3d_256()
+    C_ref = O.run_C(pb, C0, 2).numpy()
+    with L.Lattice(pb, C0, "tf32split") as lat:
+        lat.step(2)
+        assert rel_l2(lat.C(), C_ref) < 1e-5
