@@ -185,6 +185,10 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   }
   sx = gx - x0 + 1;
   sy = gy - y0 + 1;
+  // programmatic dependent launch: the operator's F (and the previous step's f) must be
+  // complete before any load; the next kernel may be scheduled as soon as all blocks run
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const bool in_xy = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
   const long long col = gx + (long long)n0 * gy;
   bool bad = false;
@@ -369,15 +373,21 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
     nz = std::max(1, std::min(nz, sp.n[2] / 16));
     zchunk = (sp.n[2] + nz - 1) / nz;
   }
-  dim3 grid(bx, by, (sp.n[2] + zchunk - 1) / zchunk);
-  dim3 block(TX, TY + HALO_WARPS);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(bx, by, (sp.n[2] + zchunk - 1) / zchunk);
+  cfg.blockDim = dim3(TX, TY + HALO_WARPS);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int* flag = h->dev.flag;
   if (split == 0)
-    collide_stream_march_kernel<real, D, MRT, 0><<<grid, block, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so, zchunk);
-  else if (split == 1)
-    collide_stream_march_kernel<real, D, MRT, 1><<<grid, block, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so, zchunk);
-  else
-    collide_stream_march_kernel<real, D, MRT, 2><<<grid, block, 0, s>>>(sp, fi, F, fo, Co, h->dev.flag, so, zchunk);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 0>, sp, fi, F, fo, Co, flag, so, zchunk);
+  if (split == 1)
+    return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 1>, sp, fi, F, fo, Co, flag, so, zchunk);
+  return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 2>, sp, fi, F, fo, Co, flag, so, zchunk);
 }
 
 int grid_for(long long n) {

@@ -309,7 +309,8 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     }
   };
 
-  // ---- prologue: the first loads go out before the accumulator is allocated
+  // ---- prologue: barrier setup and accumulator allocation overlap the previous kernel
+  // (programmatic dependent launch); operand loads wait for its results
   if (threadIdx.x == 0) {
     for (int s = 0; s < G::STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -317,6 +318,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int i = 0; i < G::STAGES && i < nkb; ++i) issue(i);
   }
   if (warp == 1) {
@@ -329,6 +331,8 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  asm volatile("griddepcontrol.wait;" ::: "memory");        // F is written below
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   if (threadIdx.x == 0) {
     // ---------------- producer (remaining k-blocks)
@@ -618,22 +622,25 @@ cudaError_t launch_kernel(const TcPlan* p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (KS == 1) {
-    frac_tc_kernel<E, BN, KS><<<p->prm.total_tiles, 128, Cfg<E, BN>::SMEM, s>>>(p->maps, p->prm);
-    return cudaGetLastError();
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->prm.total_tiles * KS, 1, 1);
   cfg.blockDim = dim3(128, 1, 1);
   cfg.dynamicSmemBytes = Cfg<E, BN>::SMEM;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = KS;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[na].val.programmaticStreamSerializationAllowed = 1;
+  ++na;
+  if (KS > 1) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = KS;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, frac_tc_kernel<E, BN, KS>, p->maps, p->prm);
 }
 
