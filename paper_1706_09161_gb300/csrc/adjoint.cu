@@ -17,7 +17,8 @@
 //   D_mumu        : - sum lambda*^T (dOmega/dD_mumu) (f - feq)
 //   u_mu          : sum (dt/dx)(w_i/e^2) C (lambda_feq_{2mu+1} - lambda_feq_{2mu+2})
 // plus the initial condition f(0) = feq(C0, K C0).  Forward states are recomputed from
-// checkpoints taken every `ckpt` steps.  Gradient sums are FP64.
+// checkpoints taken every `ckpt` steps.  Gradient sums are FP64; G_mu is one GEMM per
+// checkpoint segment (FP32 forms: products summed in FP32 over 16 terms, then in FP64).
 #include <cmath>
 #include <vector>
 
@@ -94,7 +95,7 @@ template <typename real, int D>
 __global__ void __launch_bounds__(kThreads)
 adj_step_kernel(const AdjConst<real> c, const real* __restrict__ f, const real* __restrict__ F,
                 const real* __restrict__ lam, real* __restrict__ lf, real* __restrict__ lcl, real* __restrict__ lF,
-                double* __restrict__ part) {
+                long long lFs, double* __restrict__ part) {
   constexpr int Q = 2 * D + 1;
   const long long nodes = c.nodes;
   const long long node = blockIdx.x * (long long)kThreads + threadIdx.x;
@@ -157,7 +158,7 @@ adj_step_kernel(const AdjConst<real> c, const real* __restrict__ f, const real* 
     lcl[node] = lc;
 #pragma unroll
     for (int mu = 0; mu < D; ++mu) {
-      lF[mu * nodes + node] = -c.w0 * le[0] + c.wi * (le[2 * mu + 1] + le[2 * mu + 2]);
+      lF[mu * lFs + node] = -c.w0 * le[0] + c.wi * (le[2 * mu + 1] + le[2 * mu + 2]);
       g[mu] = static_cast<double>(c.cu) * static_cast<double>(C) *
               static_cast<double>(le[2 * mu + 1] - le[2 * mu + 2]);
       double acc = 0.0;
@@ -227,28 +228,151 @@ __global__ void adj_residual_kernel(long long nodes, const real* __restrict__ C,
 }
 
 // node index of (line o, position k along axis mu)
-__device__ __forceinline__ long long line_node(int mu, long long o, int k, int n0, int n1) {
-  if (mu == 0) return o * n0 + k;
-  if (mu == 1) {
-    const long long z = o / n0, x = o % n0;
-    return (z * n1 + k) * n0 + x;
+// G_mu[n][l] += sum_t sum_lines lambda_F_mu,t(line, n) C_t(line, l) over the steps of one
+// checkpoint segment, as one SIMT GEMM whose reduction index runs over (step, line).
+// The element (row n, reduction index jk = j * kin + k) of either operand sits at
+// j * sj + n * ldn + k * ldk; the three axes map onto this as
+//   x: ldn = 1,       ldk = n0, kin = steps * lines, nj = 1   (step stride nodes = lines * n0)
+//   y: ldn = n0,      ldk = 1,  kin = n0, sj = n0 n1, nj = steps * n2
+//   z: ldn = n0 n1,   ldk = 1,  kin = n0 n1, sj = nodes, nj = steps.
+// Each block owns a 64x64 tile of G and one slice of the reduction index; partial sums go
+// to their own FP64 slab and are added in slab order (deterministic).  FP32 operands are
+// multiplied and summed in FP32 over one 16-deep slice, then added into FP64 accumulators.
+struct GLayout {
+  int side;
+  long long kin, sj, ldn, ldk, ktotal, kchunk;
+};
+
+constexpr int GB = 64, GK = 16;
+
+template <typename real, bool NCONTIG>
+__global__ void __launch_bounds__(256)
+adj_G_gemm(const GLayout L, const real* __restrict__ A, const real* __restrict__ B, double* __restrict__ part) {
+  __shared__ real As[GK][GB + 4];
+  __shared__ real Bs[GK][GB + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int n0 = blockIdx.y * GB, l0 = blockIdx.x * GB;
+  const long long kb = blockIdx.z * L.kchunk;
+  const long long ke = min(kb + L.kchunk, L.ktotal);
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  constexpr int R = (GB * GK) / 256;
+  // NCONTIG: consecutive threads walk the row index (contiguous); else the reduction index.
+  // (j, k) of each loaded reduction index is stepped by GK per slice (no division in the loop)
+  long long jj[R], kq[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = tid + r * 256;
+    const long long jk = kb + (NCONTIG ? (e / GB) : (e % GK));
+    jj[r] = jk / L.kin;
+    kq[r] = jk - jj[r] * L.kin;
   }
-  return (long long)k * n0 * n1 + o;
+  for (long long k0 = kb; k0 < ke; k0 += GK) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = tid + r * 256;
+      const int rr = NCONTIG ? (e % GB) : (e / GK);
+      const int kk = NCONTIG ? (e / GB) : (e % GK);
+      real a = static_cast<real>(0), b = static_cast<real>(0);
+      if (k0 + kk < ke) {
+        const long long base = jj[r] * L.sj + kq[r] * L.ldk;
+        if (n0 + rr < L.side) a = A[base + (long long)(n0 + rr) * L.ldn];
+        if (l0 + rr < L.side) b = B[base + (long long)(l0 + rr) * L.ldn];
+      }
+      As[kk][rr] = a;
+      Bs[kk][rr] = b;
+      kq[r] += GK;
+      while (kq[r] >= L.kin) {
+        kq[r] -= L.kin;
+        ++jj[r];
+      }
+    }
+    __syncthreads();
+    real sub[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sub[i][j] = static_cast<real>(0);
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      real a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sub[i][j] += a[i] * b[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += static_cast<double>(sub[i][j]);
+    __syncthreads();
+  }
+  double* slab = part + (size_t)blockIdx.z * L.side * L.side;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int n = n0 + ty + 16 * i;
+    if (n >= L.side) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = l0 + tx + 16 * j;
+      if (l < L.side) slab[(size_t)n * L.side + l] = acc[i][j];
+    }
+  }
 }
 
-// G[n][l] += sum over the lines of axis mu of A(line, n) B(line, l), FP64
+__global__ void adj_G_reduce(long long count, int nslab, const double* __restrict__ part, double* __restrict__ G) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < nslab; ++z) acc += part[(size_t)z * count + i];
+    G[i] += acc;
+  }
+}
+
+// slabs of the reduction split for one side x side G: about two blocks per SM, at least
+// 1024 reduction indices per block, at most kMaxSlabs
+constexpr int kMaxSlabs = 32;
+
+int g_slabs(int side, long long ktotal) {
+  const long long tiles = (long long)((side + GB - 1) / GB) * ((side + GB - 1) / GB);
+  long long z = (304 + tiles - 1) / tiles;
+  z = std::min<long long>(z, std::max<long long>(1, ktotal / 1024));
+  return static_cast<int>(std::max<long long>(1, std::min<long long>(z, kMaxSlabs)));
+}
+
+// G_mu += sum over `steps` consecutive steps (operand step stride = nodes)
 template <typename real>
-__global__ void adj_G_kernel(int mu, int n0, int n1, int n2, const real* __restrict__ A, const real* __restrict__ B,
-                             double* __restrict__ G) {
-  const int side = (mu == 0) ? n0 : (mu == 1 ? n1 : n2);
-  const long long lines = (long long)n0 * n1 * n2 / side;
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = blockIdx.y * blockDim.y + threadIdx.y;
-  if (l >= side || n >= side) return;
-  double acc = 0.0;
-  for (long long o = 0; o < lines; ++o)
-    acc += static_cast<double>(A[line_node(mu, o, n, n0, n1)]) * static_cast<double>(B[line_node(mu, o, l, n0, n1)]);
-  G[(long long)n * side + l] += acc;
+cudaError_t accumulate_G(const lbm_s* h, int mu, int steps, const real* lF, const real* C, double* G, double* part,
+                         cudaStream_t s) {
+  const long long n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
+  const long long nodes = h->sp.nodes;
+  GLayout L{};
+  L.side = h->sp.n[mu];
+  if (mu == 0) {
+    L.ldn = 1; L.ldk = n0; L.kin = steps * (nodes / n0); L.sj = 0; L.ktotal = L.kin;
+  } else if (mu == 1) {
+    L.ldn = n0; L.ldk = 1; L.kin = n0; L.sj = n0 * n1; L.ktotal = n0 * (long long)steps * n2;
+  } else {
+    L.ldn = n0 * n1; L.ldk = 1; L.kin = n0 * n1; L.sj = nodes; L.ktotal = n0 * n1 * (long long)steps;
+  }
+  const int nslab = g_slabs(L.side, L.ktotal);
+  L.kchunk = ((L.ktotal + nslab - 1) / nslab + GK - 1) / GK * GK;
+  const int tiles = (L.side + GB - 1) / GB;
+  dim3 grid(tiles, tiles, nslab);
+  if (mu == 0)
+    adj_G_gemm<real, true><<<grid, 256, 0, s>>>(L, lF, C, part);
+  else
+    adj_G_gemm<real, false><<<grid, 256, 0, s>>>(L, lF, C, part);
+  const long long count = (long long)L.side * L.side;
+  adj_G_reduce<<<static_cast<int>(std::min<long long>((count + 255) / 256, 1216)), 256, 0, s>>>(count, nslab, part, G);
+  return cudaGetLastError();
 }
 
 // sum (C - obs)^2 into *out (FP64; partial sums per block then one block)
@@ -327,15 +451,20 @@ int run_adjoint(lbm_s* h, const AdjHooks& hooks, int nsnap, const int* snaps, co
   real* lam = static_cast<real*>(B.get(E * Q * nodes));
   real* lf = static_cast<real*>(B.get(E * Q * nodes));
   real* lcl = static_cast<real*>(B.get(E * nodes));
-  real* lF = static_cast<real*>(B.get(E * D * nodes));
+  // lambda_F of every step of a segment, [mu][step][node], for one G product per segment
+  real* slF = static_cast<real*>(B.get(E * D * nodes * seglen));
   real* lcf = static_cast<real*>(B.get(E * D * nodes));
   size_t gsz = 0;
   for (int mu = 0; mu < D; ++mu) gsz += (size_t)h->sp.n[mu] * h->sp.n[mu];
   double* G = static_cast<double*>(B.get(sizeof(double) * gsz));
+  int gmax = 0;
+  for (int mu = 0; mu < D; ++mu) gmax = std::max(gmax, h->sp.n[mu]);
+  double* Gpart = static_cast<double*>(B.get(sizeof(double) * kMaxSlabs * gmax * gmax));
   double* gpart = static_cast<double*>(B.get(sizeof(double) * nb * 2 * D));
   double* lpart = static_cast<double*>(B.get(sizeof(double) * nb));
   double* lossd = static_cast<double*>(B.get(sizeof(double) * nsnap));
-  if (!obs || !ck || !sf || !sF || !sC || !lam || !lf || !lcl || !lF || !lcf || !G || !gpart || !lpart || !lossd)
+  if (!obs || !ck || !sf || !sF || !sC || !lam || !lf || !lcl || !slF || !lcf || !G || !Gpart || !gpart || !lpart ||
+      !lossd)
     return LBM_ENOMEM;
 #define CK(x)                                    \
   do {                                           \
@@ -398,40 +527,36 @@ int run_adjoint(lbm_s* h, const AdjHooks& hooks, int nsnap, const int* snaps, co
       CK(launch_collide_stream(h, h->dev.f[c2], h->dev.f[c2 ^ 1], h->dev.C, s));
       c2 ^= 1;
     }
+    const long long lFs = (long long)seglen * nodes;
     for (int t = t1 - 1; t >= t0; --t) {
       const int i = t - t0;
       const real* Ct = sC + (size_t)i * nodes;
+      real* lFi = slF + (size_t)i * nodes;
       adj_step_kernel<real, D><<<nb, kThreads, 0, s>>>(c, sf + (size_t)i * Q * nodes, sF + (size_t)i * D * nodes, lam,
-                                                       lf, lcl, lF, gpart);
+                                                       lf, lcl, lFi, lFs, gpart);
       CK(cudaGetLastError());
-      CK(launch_frac_simt_T(h, lF, lcf, s));
-      size_t goff = 0;
-      for (int mu = 0; mu < D; ++mu) {
-        const int side = h->sp.n[mu];
-        dim3 blk(32, 8), grd((side + 31) / 32, (side + 7) / 8);
-        adj_G_kernel<real><<<grd, blk, 0, s>>>(mu, h->sp.n[0], h->sp.n[1], h->sp.n[2], lF + (size_t)mu * nodes, Ct,
-                                                G + goff);
-        goff += (size_t)side * side;
-      }
+      CK(launch_frac_simt_T(h, lFi, lFs, lcf, s));
       const int k = snap_index(t);
       adj_combine_kernel<real, D><<<cb, kThreads, 0, s>>>(nodes, lf, lcl, lcf, Ct,
                                                           k >= 0 ? obs + (size_t)k * nodes : nullptr, lam);
       CK(cudaGetLastError());
     }
+    size_t goff = 0;
+    for (int mu = 0; mu < D; ++mu) {
+      CK(accumulate_G<real>(h, mu, t1 - t0, slF + (size_t)mu * lFs, sC, G + goff, Gpart, s));
+      goff += (size_t)h->sp.n[mu] * h->sp.n[mu];
+    }
   }
   // ---- the initial condition f(0) = feq(C0, K C0)
-  adj_init_kernel<real, D><<<nb, kThreads, 0, s>>>(c, static_cast<const real*>(h->dev.C0), lam, lF, gpart);
+  adj_init_kernel<real, D><<<nb, kThreads, 0, s>>>(c, static_cast<const real*>(h->dev.C0), lam, slF, gpart);
   CK(cudaGetLastError());
   {
     size_t goff = 0;
     for (int mu = 0; mu < D; ++mu) {
-      const int side = h->sp.n[mu];
-      dim3 blk(32, 8), grd((side + 31) / 32, (side + 7) / 8);
-      adj_G_kernel<real><<<grd, blk, 0, s>>>(mu, h->sp.n[0], h->sp.n[1], h->sp.n[2], lF + (size_t)mu * nodes,
-                                              static_cast<const real*>(h->dev.C0), G + goff);
-      goff += (size_t)side * side;
+      CK(accumulate_G<real>(h, mu, 1, slF + (size_t)mu * nodes, static_cast<const real*>(h->dev.C0), G + goff, Gpart,
+                            s));
+      goff += (size_t)h->sp.n[mu] * h->sp.n[mu];
     }
-    CK(cudaGetLastError());
   }
   std::vector<double> lossv(nsnap);
   CK(cudaMemcpyAsync(lossv.data(), lossd, sizeof(double) * nsnap, cudaMemcpyDeviceToHost, s));

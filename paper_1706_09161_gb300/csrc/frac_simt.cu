@@ -6,120 +6,195 @@
 //   axis x (fastest):  F[r][n] = sum_l C[r][l] K[n][l]     = C  * K^T   (rows r = other coords)
 //   axis y, z:         F[b][n][c] = sum_l K[n][l] C[b][l][c] = K * C_b  (b = outer planes, c = inner)
 // Both are written as a row-major NN GEMM D = A B (A: M x K, B: K x N), batched
-// over b with strides; K^T is stored explicitly for the x axis.
+// over b with strides; K^T is stored explicitly for the x axis.  One launch covers
+// every axis: a table maps each block to (axis, batch, tile).
+#include <algorithm>
+
 #include "lbm_internal.h"
 
 namespace lbm {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+struct GemmAxis {
+  const void* A;
+  const void* B;
+  void* C;
+  long long lda, sA, ldb, sB, ldc, sC;
+  int M, N, K;
+  int tm, tn;          // tiles along M and N
+  long long begin;     // first block of this axis
+};
 
-template <typename real>
+struct GemmPlan {
+  GemmAxis ax[3];
+  int naxes;
+  long long total;
+};
+
+// Block tile BM x BN, 256 threads with TM x TN outputs each, reduction slices of BK.
+// A is staged as [m][k] (k contiguous, as it is read from global memory) and B as
+// [k][n]; the next slice is fetched into registers while the current one is
+// multiplied from the other shared-memory buffer.
+template <typename real, int BM, int BN, int TM, int TN>
+struct SimtCfg {
+  static constexpr int BK = sizeof(real) == 8 ? 16 : 32;
+  static constexpr int AL = BM * BK / 256;  // A elements per thread per slice
+  static constexpr int BL = BK * BN / 256;
+  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+};
+
+template <typename real, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256)
-gemm_nn_kernel(int M, int N, int K, const real* __restrict__ A, long long lda, long long sA,
-               const real* __restrict__ B, long long ldb, long long sB, real* __restrict__ Cm,
-               long long ldc, long long sC) {
-  __shared__ real As[BK][BM];
-  __shared__ real Bs[BK][BN + 1];
-  const int bz = blockIdx.z;
-  A += bz * sA;
-  B += bz * sB;
-  Cm += bz * sC;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+frac_simt_kernel(const GemmPlan P) {
+  using G = SimtCfg<real, BM, BN, TM, TN>;
+  constexpr int BK = G::BK;
+  __shared__ real As[2][BM][BK + 1];
+  __shared__ __align__(16) real Bs[2][BK][BN];
+  long long b = blockIdx.x;
+  int a = 0;
+  while (a + 1 < P.naxes && b >= P.ax[a + 1].begin) ++a;
+  const GemmAxis& X = P.ax[a];
+  b -= X.begin;
+  const long long per = (long long)X.tm * X.tn;
+  const long long bz = b / per;
+  const int r = static_cast<int>(b - bz * per);
+  const int m0 = (r / X.tn) * BM, n0 = (r % X.tn) * BN;
+  const real* __restrict__ A = static_cast<const real*>(X.A) + bz * X.sA;
+  const real* __restrict__ B = static_cast<const real*>(X.B) + bz * X.sB;
+  real* __restrict__ Cm = static_cast<real*>(X.C) + bz * X.sC;
+  const int M = X.M, N = X.N, K = X.K;
   const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+
+  real ra[G::AL], rb[G::BL];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < G::AL; ++i) {
+      const int e = tid + i * 256;
+      const int mm = e / BK, kk = e % BK;
+      const int gm = m0 + mm, gk = k0 + kk;
+      ra[i] = (gm < M && gk < K) ? A[gm * X.lda + gk] : static_cast<real>(0);
+    }
+#pragma unroll
+    for (int i = 0; i < G::BL; ++i) {
+      const int e = tid + i * 256;
+      const int kk = e / BN, nn = e % BN;
+      const int gk = k0 + kk, gn = n0 + nn;
+      rb[i] = (gk < K && gn < N) ? B[gk * X.ldb + gn] : static_cast<real>(0);
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < G::AL; ++i) {
+      const int e = tid + i * 256;
+      As[buf][e / BK][e % BK] = ra[i];
+    }
+#pragma unroll
+    for (int i = 0; i < G::BL; ++i) {
+      const int e = tid + i * 256;
+      Bs[buf][e / BN][e % BN] = rb[i];
+    }
+  };
+
   real acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = static_cast<real>(0);
 
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
   for (int k0 = 0; k0 < K; k0 += BK) {
-    // A tile: BM x BK, 4 elements per thread
-#pragma unroll
-    for (int r = 0; r < (BM * BK) / 256; ++r) {
-      const int e = tid + r * 256;
-      const int mm = e / BK, kk = e % BK;
-      const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? A[gm * lda + gk] : static_cast<real>(0);
-    }
-    // B tile: BK x BN
-#pragma unroll
-    for (int r = 0; r < (BK * BN) / 256; ++r) {
-      const int e = tid + r * 256;
-      const int kk = e / BN, nn = e % BN;
-      const int gk = k0 + kk, gn = n0 + nn;
-      Bs[kk][nn] = (gk < K && gn < N) ? B[gk * ldb + gn] : static_cast<real>(0);
-    }
-    __syncthreads();
+    const bool more = k0 + BK < K;
+    if (more) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      real a[TM], b[TN];
+      real av[TM], bv[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) av[i] = As[buf][ty * TM + i][kk];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[buf][kk][tx * TN + j];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+        for (int j = 0; j < TN; ++j) acc[i][j] += av[i] * bv[j];
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
-    const int gm = m0 + ty + 16 * i;
+    const int gm = m0 + ty * TM + i;
     if (gm >= M) continue;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      const int gn = n0 + tx + 16 * j;
-      if (gn < N) Cm[gm * ldc + gn] = acc[i][j];
+      const int gn = n0 + tx * TN + j;
+      if (gn < N) Cm[gm * X.ldc + gn] = acc[i][j];
     }
   }
 }
 
-template <typename real>
-cudaError_t gemm(int M, int N, int K, int batch, const real* A, long long lda, long long sA, const real* B,
-                 long long ldb, long long sB, real* C, long long ldc, long long sC, cudaStream_t s) {
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
-  gemm_nn_kernel<real><<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
-  return cudaGetLastError();
+void add_axis(GemmPlan& P, int BM, int BN, int M, int N, int K, int batch, const void* A, long long lda, long long sA,
+              const void* B, long long ldb, long long sB, void* C, long long ldc, long long sC) {
+  GemmAxis& X = P.ax[P.naxes++];
+  X.A = A; X.B = B; X.C = C;
+  X.lda = lda; X.sA = sA; X.ldb = ldb; X.sB = sB; X.ldc = ldc; X.sC = sC;
+  X.M = M; X.N = N; X.K = K;
+  X.tm = (M + BM - 1) / BM;
+  X.tn = (N + BN - 1) / BN;
+  X.begin = P.total;
+  P.total += (long long)X.tm * X.tn * batch;
 }
 
 // transpose = false: F_mu = K_mu applied along mu to C (one input for every axis);
-// transpose = true:  F_mu = K_mu^T applied along mu to C_mu (C holds one field per axis)
-template <typename real>
-cudaError_t frac_all_axes(const lbm_s* h, const real* C, real* F, cudaStream_t s, bool transpose = false) {
+// transpose = true:  F_mu = K_mu^T applied along mu to C_mu (C holds one field per axis,
+// field mu at C + mu * cstride)
+template <typename real, int BM, int BN>
+GemmPlan make_plan(const lbm_s* h, const real* C, real* F, bool transpose, long long cstride) {
   const int n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
   const long long nodes = h->sp.nodes;
   const real* K = static_cast<const real*>(transpose ? h->dev.KT : h->dev.K);
   const real* KT = static_cast<const real*>(transpose ? h->dev.K : h->dev.KT);
-  const long long cstride = transpose ? nodes : 0;
+  if (!transpose) cstride = 0;
+  GemmPlan P{};
   long long koff = 0;
-  cudaError_t err;
   // axis x: F_0 = C (rows x n0) * K_0^T
-  err = gemm<real>((int)(nodes / n0), n0, n0, 1, C, n0, 0, KT + koff, n0, 0, F, n0, 0, s);
-  if (err != cudaSuccess) return err;
+  add_axis(P, BM, BN, (int)(nodes / n0), n0, n0, 1, C, n0, 0, KT + koff, n0, 0, F, n0, 0);
   koff += (long long)n0 * n0;
   // axis y: for each z-plane b, F_1[b] = K_1 * C[b]  (C[b] is n1 x n0)
-  err = gemm<real>(n1, n0, n1, n2, K + koff, n1, 0, C + cstride, n0, (long long)n1 * n0, F + nodes, n0,
-                   (long long)n1 * n0, s);
-  if (err != cudaSuccess) return err;
+  add_axis(P, BM, BN, n1, n0, n1, n2, K + koff, n1, 0, C + cstride, n0, (long long)n1 * n0, F + nodes, n0,
+           (long long)n1 * n0);
   koff += (long long)n1 * n1;
-  if (h->d == 3) {
-    // axis z: F_2 = K_2 * C  (C is n2 x (n1 n0))
-    err = gemm<real>(n2, n0 * n1, n2, 1, K + koff, n2, 0, C + 2 * cstride, (long long)n0 * n1, 0, F + 2 * nodes,
-                     (long long)n0 * n1, 0, s);
+  // axis z: F_2 = K_2 * C  (C is n2 x (n1 n0))
+  if (h->d == 3)
+    add_axis(P, BM, BN, n2, n0 * n1, n2, 1, K + koff, n2, 0, C + 2 * cstride, (long long)n0 * n1, 0, F + 2 * nodes,
+             (long long)n0 * n1, 0);
+  return P;
+}
+
+// 64 x 64 tiles where they give two blocks per SM, else 32 x 32
+template <typename real>
+cudaError_t frac_all_axes(const lbm_s* h, const real* C, real* F, cudaStream_t s, bool transpose = false,
+                          long long cstride = 0) {
+  const GemmPlan big = make_plan<real, 64, 64>(h, C, F, transpose, cstride);
+  if (big.total >= 2 * 152) {
+    frac_simt_kernel<real, 64, 64, 4, 4><<<static_cast<unsigned>(big.total), 256, 0, s>>>(big);
+  } else {
+    const GemmPlan small = make_plan<real, 32, 32>(h, C, F, transpose, cstride);
+    frac_simt_kernel<real, 32, 32, 2, 2><<<static_cast<unsigned>(small.total), 256, 0, s>>>(small);
   }
-  return err;
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_frac_simt_T(const lbm_s* h, const void* in, void* out, cudaStream_t s) {
+cudaError_t launch_frac_simt_T(const lbm_s* h, const void* in, long long in_stride, void* out, cudaStream_t s) {
   if (h->elem == 8)
-    return frac_all_axes<double>(h, static_cast<const double*>(in), static_cast<double*>(out), s, true);
-  return frac_all_axes<float>(h, static_cast<const float*>(in), static_cast<float*>(out), s, true);
+    return frac_all_axes<double>(h, static_cast<const double*>(in), static_cast<double*>(out), s, true, in_stride);
+  return frac_all_axes<float>(h, static_cast<const float*>(in), static_cast<float*>(out), s, true, in_stride);
 }
 
 cudaError_t launch_frac_simt(const lbm_s* h, const void* C, void* F, cudaStream_t s) {

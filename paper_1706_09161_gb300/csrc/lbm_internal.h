@@ -124,6 +124,7 @@ struct AdjHooks {
 int adjoint_grad(lbm_s* h, const AdjHooks& hooks, int nsnap, const int* snaps, const double* obs, int ckpt,
                  const double dOm[3][kMaxQ][kMaxQ], double* loss, double* G, double* gsum);
 // transpose of the SIMT fractional operator: out_mu = K_mu^T applied along axis mu to in_mu
-cudaError_t launch_frac_simt_T(const lbm_s* h, const void* in, void* out, cudaStream_t s);
+// out_mu = K_mu^T applied along mu to the field at in + mu * in_stride (elements)
+cudaError_t launch_frac_simt_T(const lbm_s* h, const void* in, long long in_stride, void* out, cudaStream_t s);
 
 }  // namespace lbm
