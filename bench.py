@@ -382,6 +382,11 @@ def main():
         roof = {"kernel": "fractional_operator", "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for(args.workload, "fractional_operator"),
                 "algorithmic_per_launch": flops, "launch_ms": dur * 1e3, "peak_source": peak_src}
+        if precision in ("bf16split", "tf32split"):
+            # the split form issues three products (hi*hi, hi*lo, lo*hi) per algorithmic one:
+            # the tensor pipe's own load
+            roof["executed_per_launch"] = 3.0 * flops
+            roof["executed_frac"] = 3.0 * achieved / peak
     else:
         bytes_ = float(nodes) * (2 * Q * elem + d * elem + elem)
         dur = ms_cs / nprof * 1e-3

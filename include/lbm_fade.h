@@ -162,10 +162,14 @@ int lbm_sync(lbm_t h);
 /* The cudaStream_t the handle runs on (for event timing by the caller). */
 int lbm_get_stream(lbm_t h, void** stream);
 
-/* Run nsteps time steps with one-kernel launches bracketed by CUDA events on the
- * handle's stream and accumulate the device time of each kernel class:
- *   ms[0] = fractional operator (all axes), ms[1] = fused collide/stream/walls/moment.
- * Divide by nsteps for the mean duration per launch.  Synchronises. */
+/* Run nsteps time steps (0 <= nsteps <= 4096) with one-kernel launches bracketed by
+ * CUDA events on the handle's stream and accumulate the device time of each kernel
+ * class:
+ *   ms[0] = fractional operator (all axes, with the tf32 transposes),
+ *   ms[1] = fused collide/stream/walls/moment.
+ * All steps are queued before one synchronisation, so the intervals exclude the host's
+ * submission of each launch.  Divide by nsteps for the mean duration per launch.
+ * LBM_EINVAL for nsteps outside that range.  Synchronises. */
 int lbm_profile(lbm_t h, int nsteps, double* ms);
 
 /* Number of kernel launches one time step issues (per problem batch). */

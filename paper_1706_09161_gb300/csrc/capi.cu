@@ -396,8 +396,12 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   if (prm->precision == LBM_FP32_BF16SPLIT || prm->precision == LBM_FP32_TF32SPLIT) {
     if ((rc = lbm::tc_prepare(h, Kall, batched ? 128 : 0, batched ? 1 : 0))) return fail(rc);
     h->launches_per_step = (prm->precision == LBM_FP32_TF32SPLIT) ? 2 + (h->d - 1) : 2;
+    // overlap kernel boundaries only where neither grid needs a second wave; the tf32
+    // transposes between collide-stream and the operator are plain launches anyway
+    h->pdl = !batched && prm->precision == LBM_FP32_BF16SPLIT && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
+    lbm::tc_set_pdl(h, h->pdl);
   } else {
-    h->launches_per_step = h->d + 1;
+    h->launches_per_step = 2;  // one SIMT operator launch over every axis, one collide-stream
   }
   *out = h;
   rc = lbm_set_C(h, C0_host);
@@ -518,13 +522,18 @@ int lbm_reset(lbm_t h) {
 }
 
 int lbm_profile(lbm_t h, int nsteps, double* ms) {
-  if (!h || !ms || nsteps < 0) return LBM_EINVAL;
-  cudaEvent_t ev[3];
-  for (auto& e : ev) LBM_CUDA(cudaEventCreate(&e));
+  if (!h || !ms || nsteps < 0 || nsteps > 4096) return LBM_EINVAL;
   ms[0] = ms[1] = 0.0;
+  // every step's three events are queued before the one synchronisation, so that the
+  // intervals measure the kernels, not the host's submission of each launch
+  std::vector<cudaEvent_t> ev(3 * (size_t)nsteps);
   int rc = LBM_OK;
+  size_t made = 0;
+  for (; made < ev.size(); ++made)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
+  if (made < ev.size()) rc = record_cuda(cudaErrorMemoryAllocation, "lbm_profile");
   for (int k = 0; k < nsteps && rc == LBM_OK; ++k) {
-    cudaError_t e = cudaEventRecord(ev[0], h->stream);
+    cudaError_t e = cudaEventRecord(ev[3 * k], h->stream);
     if (e == cudaSuccess) {
       if (h->is_batch() && h->batch_tc_blocks > 0) e = lbm::launch_frac_tc_batch(h, h->stream);
       else if (h->is_batch())
@@ -538,23 +547,29 @@ int lbm_profile(lbm_t h, int nsteps, double* ms) {
         else rc = run_frac(h, h->stream);
       }
     }
-    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[1], h->stream);
+    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[3 * k + 1], h->stream);
     if (e == cudaSuccess && rc == LBM_OK) {
       if (h->is_batch()) e = lbm::launch_collide_stream_batch(h, h->cur, h->stream);
       else e = lbm::launch_collide_stream(h, h->dev.f[h->cur], h->dev.f[h->cur ^ 1], h->dev.C, h->stream);
     }
-    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[2], h->stream);
-    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventSynchronize(ev[2]);
-    float a = 0.f, b = 0.f;
-    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
-    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+    if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[3 * k + 2], h->stream);
     if (e != cudaSuccess) rc = record_cuda(e, "lbm_profile");
     h->cur ^= 1;
     for (lbm_s* p : h->subs) p->cur = h->cur;
+  }
+  if (rc == LBM_OK && nsteps > 0) {
+    const cudaError_t e = cudaEventSynchronize(ev[3 * (size_t)nsteps - 1]);
+    if (e != cudaSuccess) rc = record_cuda(e, "lbm_profile");
+  }
+  for (int k = 0; k < nsteps && rc == LBM_OK; ++k) {
+    float a = 0.f, b = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]);
+    if (e != cudaSuccess) rc = record_cuda(e, "lbm_profile");
     ms[0] += a;
     ms[1] += b;
   }
-  for (auto& e : ev) cudaEventDestroy(e);
+  for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
   return rc;
 }
 

@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "lbm_internal.h"
@@ -153,12 +154,39 @@ __device__ __forceinline__ void collide_at(const KConst<real>& sp, const real* _
   collide_node<real, D, MRT>(sp, f, Fv, fs);
 }
 
-// One block's column (tile bx, by; z chunk bz) of one problem.
+// Asynchronous prefetch of the 2-D march (FP32): every thread copies the populations and
+// fractional terms of its node in the next two tiles into its own column of a
+// shared-memory ring (cp.async, 4 bytes each), so the loads of later tiles are in
+// flight while the current one is processed.
+constexpr int NT = TX * (TY + HALO_WARPS);
+constexpr int PIPE_STAGES = 3;
+constexpr int PIPE_VALS = 7;  // D2Q5: 5 populations + 2 fractional terms
+constexpr int PIPE_SMEM = PIPE_STAGES * PIPE_VALS * NT * 4;
+
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Programmatic dependent launch: let the next kernel of the stream be scheduled.  A grid
+// that fits in one wave does this at block start (its dependents' prologues overlap it);
+// a longer grid does it at block end, so that early dependents do not take SMs that its
+// later waves need.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One block's column (tile bx, by; planes z0 .. z1-1) of one problem.
 template <typename real, int D, bool MRT, int SPLIT>
 __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* __restrict__ f_in,
                                            const real* __restrict__ F, real* __restrict__ f_out,
                                            real* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
-                                           int zchunk, int bx, int by, int bz) {
+                                           int bx, int by, int z0, int z1) {
   constexpr int Q = Lat<D>::Q;
   // movers of the current plane on the tile plus ring: [buffer][mover 1..4][y+1][x+1]
   __shared__ real s_m[2][4][TY + 2][TX + 2];
@@ -167,8 +195,6 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   const long long plane = (long long)n0 * n1;
   const int lane = threadIdx.x, wy = threadIdx.y;
   const int x0 = bx * TX, y0 = by * TY;
-  const int z0 = bz * zchunk;
-  const int z1 = min(z0 + zchunk, n2);
 
   // the node this thread collides every plane, and where its movers go
   int gx, gy, sx, sy;
@@ -186,9 +212,8 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   sx = gx - x0 + 1;
   sy = gy - y0 + 1;
   // programmatic dependent launch: the operator's F (and the previous step's f) must be
-  // complete before any load; the next kernel may be scheduled as soon as all blocks run
+  // complete before any load
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const bool in_xy = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
   const long long col = gx + (long long)n0 * gy;
   bool bad = false;
@@ -283,12 +308,160 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
 }
 
+// 2-D FP32: the block walks `ychunk` consecutive 32 x 16 tiles up the y axis (tile
+// rows tr0 .. tr0 + ychunk - 1 of column bx), each thread prefetching its node of the
+// next two tiles through the cp.async ring while the current tile is collided.  The
+// per-tile work is that of march_body with one plane.
+template <bool MRT, int SPLIT>
+__device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float* __restrict__ f_in,
+                                            const float* __restrict__ F, float* __restrict__ f_out,
+                                            float* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
+                                            int ychunk, int bx, int byc, float* stage) {
+  constexpr int D = 2, Q = 5;
+  __shared__ float s_m[2][4][TY + 2][TX + 2];
+  const int n0 = sp.n[0], n1 = sp.n[1];
+  const long long nodes = sp.nodes;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const int tid = wy * TX + lane;
+  const int tr0 = byc * ychunk;
+  const int tr1 = min(tr0 + ychunk, (n1 + TY - 1) / TY);
+  // this thread's node relative to the tile origin: owners, x-ring, rows below / above
+  const bool owner = wy < TY;
+  int dx, dy;
+  if (owner) {
+    dx = lane;
+    dy = wy;
+  } else if (wy == TY) {
+    dx = (lane < 16) ? -1 : TX;
+    dy = lane & 15;
+  } else {
+    dx = lane;
+    dy = (wy == TY + 1) ? -1 : TY;
+  }
+  const int gx = bx * TX + dx;
+  const int sx = dx + 1, sy = dy + 1;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const bool in_x = gx >= 0 && gx < n0;
+  auto issue = [&](int tr, int slot) {
+    const int gy = tr * TY + dy;
+    if (in_x && gy >= 0 && gy < n1) {
+      const long long node = gx + (long long)n0 * gy;
+      float* st = stage + (size_t)slot * PIPE_VALS * NT + tid;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) cp_async4(st + q * NT, f_in + q * nodes + node);
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) cp_async4(st + (Q + mu) * NT, F + mu * nodes + node);
+    }
+    cp_async_commit();
+  };
+  issue(tr0, 0);
+  if (tr0 + 1 < tr1) issue(tr0 + 1, 1); else cp_async_commit();
+  bool bad = false;
+  int buf = 0;
+  for (int tr = tr0; tr < tr1; ++tr) {
+    const int slot = (tr - tr0) % PIPE_STAGES;
+    if (tr + 2 < tr1) issue(tr + 2, (tr - tr0 + 2) % PIPE_STAGES); else cp_async_commit();
+    cp_async_wait<2>();  // this thread's copies for tile row tr have landed
+    const int gy = tr * TY + dy;
+    const bool inside = in_x && gy >= 0 && gy < n1;
+    float fs[Q];
+    if (inside) {
+      const float* st = stage + (size_t)slot * PIPE_VALS * NT + tid;
+      float fv[Q], Fv[D];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) fv[q] = st[q * NT];
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) Fv[mu] = st[(Q + mu) * NT];
+      collide_node<float, D, MRT>(sp, fv, Fv, fs);
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) fs[q] = 0.f;
+    }
+    if (owner) {
+      s_m[buf][0][sy][sx] = fs[1];
+      s_m[buf][1][sy][sx] = fs[2];
+      s_m[buf][2][sy][sx] = fs[3];
+      s_m[buf][3][sy][sx] = fs[4];
+    } else if (wy == TY) {
+      if (lane < 16) s_m[buf][0][sy][sx] = fs[1];  // moves +x into the tile
+      else s_m[buf][1][sy][sx] = fs[2];            // moves -x into the tile
+    } else if (wy == TY + 1) {
+      s_m[buf][2][sy][sx] = fs[3];                 // moves +y into the tile
+    } else {
+      s_m[buf][3][sy][sx] = fs[4];                 // moves -y into the tile
+    }
+    __syncthreads();
+    if (owner && inside) {
+      float fv[Q];
+      bool known[Q];
+      fv[0] = fs[0];
+      known[0] = true;
+      known[1] = gx > 0;
+      known[2] = gx + 1 < n0;
+      known[3] = gy > 0;
+      known[4] = gy + 1 < n1;
+      fv[1] = s_m[buf][0][sy][sx - 1];
+      fv[2] = s_m[buf][1][sy][sx + 1];
+      fv[3] = s_m[buf][2][sy - 1][sx];
+      fv[4] = s_m[buf][3][sy + 1][sx];
+      float sum_known = 0.f;
+      int n_unknown = 0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (known[q]) {
+          sum_known += fv[q];
+        } else {
+          fv[q] = 0.f;
+          ++n_unknown;
+        }
+      }
+      float C = sum_known;
+      if (n_unknown > 0) {
+        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
+        const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (!known[q]) fv[q] = fill;
+        C = fv[0];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) C += fv[q];
+      }
+      const long long node = gx + (long long)n0 * gy;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
+      C_out[node] = C;
+      if (SPLIT) write_split<SPLIT>(so, (long long)gy * so.ldp + gx, C);
+      bad |= !isfinite(C);
+    }
+    buf ^= 1;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
+}
+
+template <bool MRT, int SPLIT>
+__global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
+collide_stream_march2_kernel(const KConst<float> sp, const float* __restrict__ f_in, const float* __restrict__ F,
+                             float* __restrict__ f_out, float* __restrict__ C_out, int* __restrict__ flag,
+                             SplitOut so, int ychunk, int early) {
+  extern __shared__ __align__(16) float pipe_stage[];
+  if (early) pdl_trigger();
+  march2_pipe<MRT, SPLIT>(sp, f_in, F, f_out, C_out, flag, so, ychunk, blockIdx.x, blockIdx.y, pipe_stage);
+  if (!early) pdl_trigger();
+}
+
 template <typename real, int D, bool MRT, int SPLIT>
 __global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
 collide_stream_march_kernel(const KConst<real> sp, const real* __restrict__ f_in, const real* __restrict__ F,
                             real* __restrict__ f_out, real* __restrict__ C_out, int* __restrict__ flag, SplitOut so,
-                            int zchunk) {
-  march_body<real, D, MRT, SPLIT>(sp, f_in, F, f_out, C_out, flag, so, zchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+                            int nz, int early) {
+  // z chunk blockIdx.z of nz (boundaries bz * n2 / nz): concurrent blocks march the same
+  // z window, so the ring loads of neighbouring columns hit L2
+  const int n2 = sp.n[2];
+  const int bz = blockIdx.z;
+  const int z0 = static_cast<int>((long long)bz * n2 / nz), z1 = static_cast<int>((long long)(bz + 1) * n2 / nz);
+  if (early) pdl_trigger();
+  march_body<real, D, MRT, SPLIT>(sp, f_in, F, f_out, C_out, flag, so, blockIdx.x, blockIdx.y, z0, z1);
+  if (!early) pdl_trigger();
 }
 
 // Grouped form for a batch of independent problems: one launch covers every block of
@@ -314,8 +487,14 @@ collide_stream_batch_kernel(const BatchCS* __restrict__ tab, const int* __restri
   __syncthreads();
   const int lb = b - __ldg(&block_start[lo]);
   const int bx = lb % e.bx, rest = lb / e.bx;
-  march_body<float, D, MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
-                                   e.zchunk, bx, rest % e.by, rest / e.by);
+  if constexpr (D == 2) {
+    extern __shared__ __align__(16) float pipe_stage[];
+    march2_pipe<MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so, e.zchunk,
+                            bx, rest, pipe_stage);
+  } else {
+    march_body<float, D, MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
+                                     bx, rest, 0, e.k.n[2]);
+  }
 }
 
 template <typename real, int D>
@@ -355,6 +534,49 @@ __global__ void moment_kernel(long long nodes, const real* __restrict__ f, real*
   }
 }
 
+// at most two blocks per SM resident: the grid runs in one wave
+bool one_wave(const dim3& g) { return (long long)g.x * g.y * g.z <= 2 * 152; }
+
+template <bool MRT, int SPLIT>
+cudaError_t launch_march2(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, const float* fi, const float* F,
+                          float* fo, float* Co, int* flag, const SplitOut& so, int ychunk, int early) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(collide_stream_march2_kernel<MRT, SPLIT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return cudaLaunchKernelEx(&cfg, collide_stream_march2_kernel<MRT, SPLIT>, sp, fi, F, fo, Co, flag, so, ychunk,
+                            early);
+}
+
+// z chunks of the 3-D march over `cols` tile columns: the count that maximises the wave
+// efficiency (blocks / 304 over its ceiling, two blocks per SM) per plane collided,
+// each chunk re-colliding two planes at its start; chunks of at least 16 planes
+int z_chunks(long long cols, int n2) {
+  if (n2 < 32) return 1;
+  int best = 1;
+  double best_eff = 0.0;
+  for (int nz = 1; nz <= n2 / 16; ++nz) {
+    const double waves = static_cast<double>(cols * nz) / (2 * 152);
+    const double eff = waves / std::ceil(waves);
+    const double zc = static_cast<double>(n2) / nz;
+    const double score = eff * zc / (zc + 2.0);
+    if (score > best_eff + 1e-9) {
+      best_eff = score;
+      best = nz;
+    }
+  }
+  return best;
+}
+
+// tile rows per 2-D block: ceil(tiles / 304) (one wave of two blocks per SM), at most by
+int ychunk_for(long long tiles, int by) {
+  const long long c = (tiles + 2 * 152 - 1) / (2 * 152);
+  return static_cast<int>(std::max<long long>(1, std::min<long long>(c, by)));
+}
+
 template <typename real, int D, bool MRT>
 cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s) {
   const KConst<real> sp = make_const<real>(h->sp);
@@ -365,29 +587,36 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
   real* fo = static_cast<real*>(f_out);
   real* Co = static_cast<real*>(C_out);
   const int bx = (sp.n[0] + TX - 1) / TX, by = (sp.n[1] + TY - 1) / TY;
-  // z chunks: enough blocks for ~3 resident per SM, but chunks of >= 16 planes
-  int zchunk = sp.n[2];
-  if (D == 3) {
-    const long long cols = (long long)bx * by;
-    int nz = static_cast<int>((3LL * 152 + cols - 1) / cols);
-    nz = std::max(1, std::min(nz, sp.n[2] / 16));
-    zchunk = (sp.n[2] + nz - 1) / nz;
-  }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(bx, by, (sp.n[2] + zchunk - 1) / zchunk);
+  const int nz = z_chunks((long long)bx * by, sp.n[2]);
+  cfg.gridDim = dim3(bx, by, nz);
+  const int early = one_wave(cfg.gridDim) ? 1 : 0;
   cfg.blockDim = dim3(TX, TY + HALO_WARPS);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  at[0].val.programmaticStreamSerializationAllowed = h->pdl ? 1 : 0;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int* flag = h->dev.flag;
+  if constexpr (D == 2 && sizeof(real) == 4) {
+    // tile rows per block: about one wave of two blocks per SM
+    const int ychunk = ychunk_for((long long)bx * by, by);
+    cfg.gridDim = dim3(bx, (by + ychunk - 1) / ychunk, 1);
+    cfg.dynamicSmemBytes = PIPE_SMEM;
+    const int early = one_wave(cfg.gridDim) ? 1 : 0;
+    if (split == 0) return launch_march2<MRT, 0>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
+    if (split == 1) return launch_march2<MRT, 1>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
+    return launch_march2<MRT, 2>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
+  }
   if (split == 0)
-    return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 0>, sp, fi, F, fo, Co, flag, so, zchunk);
+    return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 0>, sp, fi, F, fo, Co, flag, so, nz,
+                              early);
   if (split == 1)
-    return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 1>, sp, fi, F, fo, Co, flag, so, zchunk);
-  return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 2>, sp, fi, F, fo, Co, flag, so, zchunk);
+    return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 1>, sp, fi, F, fo, Co, flag, so, nz,
+                              early);
+  return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 2>, sp, fi, F, fo, Co, flag, so, nz,
+                              early);
 }
 
 int grid_for(long long n) {
@@ -412,6 +641,17 @@ cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out,
              : launch_cs<float, 3, false>(h, f_in, f_out, C_out, s);
 }
 
+constexpr int kBatchYChunk = 8;
+
+bool cs_one_wave(const lbm_s* h) {
+  const int bx = (h->sp.n[0] + TX - 1) / TX, by = (h->sp.n[1] + TY - 1) / TY;
+  if (h->d == 2 && h->elem == 4) {
+    const int ychunk = ychunk_for((long long)bx * by, by);
+    return one_wave(dim3(bx, (by + ychunk - 1) / ychunk, 1));
+  }
+  return one_wave(dim3(bx, by, h->d == 3 ? z_chunks((long long)bx * by, h->sp.n[2]) : 1));
+}
+
 int cs_batch_prepare(lbm_s* b) {
   const int P = static_cast<int>(b->subs.size());
   std::vector<BatchCS> tab(P);
@@ -430,9 +670,10 @@ int cs_batch_prepare(lbm_s* b) {
     e.flag = h->dev.flag;
     e.bx = (h->sp.n[0] + TX - 1) / TX;
     e.by = (h->sp.n[1] + TY - 1) / TY;
-    e.zchunk = h->sp.n[2];
+    // 2-D: tile rows per block (the pipelined y-march); 3-D: the whole z extent
+    e.zchunk = (h->d == 2) ? std::min(e.by, kBatchYChunk) : h->sp.n[2];
     start[i] = total;
-    total += e.bx * e.by;
+    total += e.bx * ((h->d == 2) ? (e.by + e.zchunk - 1) / e.zchunk : e.by);
   }
   if (cudaMalloc(&b->batch_cs, sizeof(BatchCS) * P) != cudaSuccess) return LBM_ENOMEM;
   if (cudaMalloc(&b->batch_cs_start, sizeof(int) * P) != cudaSuccess) return LBM_ENOMEM;
@@ -451,7 +692,20 @@ cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t
   const int P = static_cast<int>(b->subs.size());
   dim3 block(TX, TY + HALO_WARPS);
   const int g = b->batch_cs_blocks;
-#define LBM_CSB(D_, M_, S_) collide_stream_batch_kernel<D_, M_, S_><<<g, block, 0, s>>>(tab, b->batch_cs_start, P, parity)
+  const int smem = (h0->d == 2) ? PIPE_SMEM : 0;
+  if (h0->d == 2) {
+    static bool attr[2][2] = {{false, false}, {false, false}};
+    if (!attr[mrt][split]) {
+      cudaError_t e;
+      if (mrt) e = split ? cudaFuncSetAttribute(collide_stream_batch_kernel<2, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM)
+                         : cudaFuncSetAttribute(collide_stream_batch_kernel<2, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM);
+      else e = split ? cudaFuncSetAttribute(collide_stream_batch_kernel<2, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM)
+                     : cudaFuncSetAttribute(collide_stream_batch_kernel<2, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM);
+      if (e != cudaSuccess) return e;
+      attr[mrt][split] = true;
+    }
+  }
+#define LBM_CSB(D_, M_, S_) collide_stream_batch_kernel<D_, M_, S_><<<g, block, smem, s>>>(tab, b->batch_cs_start, P, parity)
   if (h0->d == 2) {
     if (mrt) { if (split) LBM_CSB(2, true, 1); else LBM_CSB(2, true, 0); }
     else { if (split) LBM_CSB(2, false, 1); else LBM_CSB(2, false, 0); }

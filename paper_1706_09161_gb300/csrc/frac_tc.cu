@@ -21,9 +21,10 @@
 // accumulator is allocated), warp 1 / lane 0 issues the MMAs and releases ring slots
 // with tcgen05.commit, then all four warps drain the accumulator (tcgen05.ld, one
 // lane quarter per warp) into a shared [BN][128] tile that one TMA store writes to F.
-// Small problems split the contraction over a cluster of ksplit CTAs per tile; their
-// partial tiles are summed through distributed shared memory in rank order, so the
-// result does not depend on timing.  Every mbarrier wait is
+// Small problems split the contraction over a cluster of ksplit CTAs per tile; each
+// rank finishes 1/ksplit of the tile's rows, summing the ranks' partial tiles through
+// distributed shared memory in rank order, so the result does not depend on timing.  Problems with many tiles use the persistent kernel further
+// down (two TMEM accumulators, epilogue overlapping the next tile).  Every mbarrier wait is
 // bounded by a 2 s %globaltimer budget; a wait that gives up sets bit 2 of the
 // handle's error flag and the CTA skips the rest of its work and releases TMEM.
 #include <cuda.h>
@@ -55,6 +56,7 @@ struct TcParams {
   int total_tiles;
   int ksplit;     // CTAs (one cluster) per output tile, each contracting a k-range
   int tma_store;  // F rows are 16-byte aligned (n0 % 4 == 0): store tiles with TMA
+  int early_trigger;  // the per-tile grid fits in one wave: release dependents after the prologue
   long long nodes;
   TcAxis ax[3];
   float* F;
@@ -72,6 +74,8 @@ struct TcPlan {
   TcParams prm;
   int elem = 2;      // 2: bf16 parts, 4: tf32 parts
   int bn = 64;
+  bool persist = false;  // one CTA per SM walking the tile list (frac_tc_persist_kernel)
+  bool pdl = false;      // launch with programmatic stream serialization (the handle's choice)
   size_t smem = 0;
   int ldp = 0;       // padded x pitch of the C split arrays (elements)
   // tf32 only: C split transposed so that axis mu (1: y, 2: z) is contiguous, pitch ldT
@@ -142,6 +146,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* f
       return false;
     }
   }
+}
+
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -227,14 +237,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int E, int BN>
+template <int E, int BN, int KS = 1>
 struct Cfg {
   static constexpr int BK = 128 / E;                 // contraction elements per 128-byte row
   static constexpr int STAGES = (BN <= 64) ? 4 : (BN <= 128 ? 3 : 2);
   static constexpr uint32_t A_BYTES = BM * 128;      // one operand part of A: 128 rows x 128 B
   static constexpr uint32_t B_BYTES = BN * 128;
   static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr size_t RING = (size_t)STAGES * STAGE;
+  static constexpr int ROWS = BN / KS;  // KS > 1: tile rows each rank of the cluster finishes
+  static constexpr size_t SMEM = RING + 1024 /*align*/ + 256 /*barriers*/;
   // A, MN-major: E boxes of (128/E) lines x BK rows
   static constexpr uint32_t A_BOX_MN = BK * 128;
   static constexpr uint32_t IDESC_K = (1u << 4) | (Kind<E>::fmt << 7) | (Kind<E>::fmt << 10) |
@@ -242,13 +254,117 @@ struct Cfg {
   static constexpr uint32_t IDESC_MN = IDESC_K | (1u << 15);
 };
 
+// Tile `cid` of a problem: axis mu, first x of the tile (m_in), outer coordinate
+// (m_out: z for the x and y axes, y for the z axis) and first output column (ncol0).
+struct TileAt {
+  int mu, m_in, m_out, ncol0;
+};
+
+__device__ __forceinline__ TileAt decode_tile(const TcParams& P, int cid, int bn) {
+  int mu = 0;
+  while (mu + 1 < P.naxes && cid >= P.ax[mu + 1].tile_begin) ++mu;
+  const TcAxis& ax = P.ax[mu];
+  const int lt = cid - ax.tile_begin;
+  const int mt = lt / ax.tiles_n, nt = lt % ax.tiles_n;
+  return TileAt{mu, (mt % ax.msub) * BM, mt / ax.msub, nt * bn};
+}
+
+// TMA loads of one k-block (contraction offset k0) of tile `t` into ring stage `st`,
+// completing on `bar` (whose expected byte count the caller has set).  The weight
+// parts (K_mu, fixed for the whole run) and the concentration parts (C, written by the
+// previous step) are issued separately, so the former can leave before the previous
+// kernel has finished.
+template <int E, int BN>
+__device__ __forceinline__ void load_stage_weights(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st,
+                                                   uint64_t* bar) {
+  using G = Cfg<E, BN>;
+  if (t.mu == 0) {
+    // A = K_x rows n = m_in..
+    tma_load_2d(st, &maps.k_hi[0], k0, t.m_in, bar);
+    tma_load_2d(st + G::A_BYTES, &maps.k_lo[0], k0, t.m_in, bar);
+  } else {
+    // B = K_mu rows n = ncol0..
+    uint8_t* b_hi = st + 2 * G::A_BYTES;
+    tma_load_2d(b_hi, &maps.k_hi[t.mu], k0, t.ncol0, bar);
+    tma_load_2d(b_hi + G::B_BYTES, &maps.k_lo[t.mu], k0, t.ncol0, bar);
+  }
+}
+
+template <int E, int BN>
+__device__ __forceinline__ void load_stage_conc(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st,
+                                                uint64_t* bar) {
+  using G = Cfg<E, BN>;
+  uint8_t* a_hi = st;
+  uint8_t* a_lo = st + G::A_BYTES;
+  uint8_t* b_hi = st + 2 * G::A_BYTES;
+  uint8_t* b_lo = b_hi + G::B_BYTES;
+  if (t.mu == 0) {
+    // B = C rows y = ncol0.. at z = m_out
+    tma_load_3d(b_hi, &maps.c_hi[0], k0, t.ncol0, t.m_out, bar);
+    tma_load_3d(b_lo, &maps.c_lo[0], k0, t.ncol0, t.m_out, bar);
+  } else if (E == 4) {
+    // tf32 parts: A = the C split transposed so that the contraction axis is contiguous
+    // (K-major), 128 x-lines per tile
+    tma_load_3d(a_hi, &maps.c_hi[t.mu], k0, t.m_in, t.m_out, bar);
+    tma_load_3d(a_lo, &maps.c_lo[t.mu], k0, t.m_in, t.m_out, bar);
+  } else {
+    // bf16 parts: A = the C panel, MN-major (x contiguous), E boxes of 128/E lines
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int x = t.m_in + j * (128 / E);
+      if (t.mu == 1) {
+        tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[1], x, k0, t.m_out, bar);
+        tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[1], x, k0, t.m_out, bar);
+      } else {
+        tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[2], x, t.m_out, k0, bar);
+        tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[2], x, t.m_out, k0, bar);
+      }
+    }
+  }
+}
+
+template <int E, int BN>
+__device__ __forceinline__ void load_stage(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st, uint64_t* bar) {
+  load_stage_weights<E, BN>(maps, t, k0, st, bar);
+  load_stage_conc<E, BN>(maps, t, k0, st, bar);
+}
+
+// The three split products of one k-block from ring stage `st` into accumulator `d`
+// (first = no previous contribution in d).
+template <int E, int BN>
+__device__ __forceinline__ void mma_stage(uint32_t d, uint32_t st, bool kmajor, bool first) {
+  using G = Cfg<E, BN>;
+  const uint32_t idesc = kmajor ? G::IDESC_K : G::IDESC_MN;
+  const uint32_t a_hi = st, a_lo = st + G::A_BYTES;
+  const uint32_t b_hi = st + 2 * G::A_BYTES, b_lo = b_hi + G::B_BYTES;
+#pragma unroll
+  for (int kk = 0; kk < G::BK / Kind<E>::UK; ++kk) {
+    uint32_t a_off, a_lbo;
+    if (kmajor) {  // K-major A: advance within the 128-byte row
+      a_off = kk * Kind<E>::UK * E;
+      a_lbo = 16;
+    } else {        // MN-major A: advance by UK rows of 128 bytes
+      a_off = kk * Kind<E>::UK * 128;
+      a_lbo = G::A_BOX_MN;
+    }
+    const uint32_t b_off = kk * Kind<E>::UK * E;
+    const uint64_t dah = smem_desc(a_hi + a_off, a_lbo, 1024);
+    const uint64_t dal = smem_desc(a_lo + a_off, a_lbo, 1024);
+    const uint64_t dbh = smem_desc(b_hi + b_off, 16, 1024);
+    const uint64_t dbl = smem_desc(b_lo + b_off, 16, 1024);
+    mma<E>(d, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
+    mma<E>(d, dah, dbl, idesc, 1u);
+    mma<E>(d, dal, dbh, idesc, 1u);
+  }
+}
+
 // One output tile (or one k-slice of it when KS > 1) of one problem; `block` is the
 // CTA's index among that problem's CTAs.  `maps` may live in parameter or global memory.
 template <int E, int BN, int KS>
 __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams& P, int block, uint8_t* smem_raw) {
-  using G = Cfg<E, BN>;
+  using G = Cfg<E, BN, KS>;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)G::STAGES * G::STAGE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::RING);
   uint64_t* empty = full + G::STAGES;
   uint64_t* done = empty + G::STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
@@ -259,54 +375,16 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   // CTA `rank` of the cluster contracts k-blocks [kb0, kb1)
   constexpr int ks = KS;
   const int cid = block / ks, rank = block % ks;
-  int mu = 0;
-  while (mu + 1 < P.naxes && cid >= P.ax[mu + 1].tile_begin) ++mu;
+  const TileAt tl = decode_tile(P, cid, BN);
+  const int mu = tl.mu, m_in = tl.m_in, m_out = tl.m_out, ncol0 = tl.ncol0;
   const TcAxis ax = P.ax[mu];
-  const int lt = cid - ax.tile_begin;
-  const int mt = lt / ax.tiles_n, nt = lt % ax.tiles_n;
-  const int ncol0 = nt * BN;
-  const int m_in = (mt % ax.msub) * BM;  // first x of the tile
-  const int m_out = mt / ax.msub;        // z (x, y axes) or y (z axis)
   const int kb0 = rank * ax.kblocks / ks, kb1 = (rank + 1) * ax.kblocks / ks;
   const int nkb = kb1 - kb0;
 
   auto issue = [&](int i) {
     const int s = i % G::STAGES;
-    uint8_t* st = smem + (size_t)s * G::STAGE;
-    uint8_t* a_hi = st;
-    uint8_t* a_lo = st + G::A_BYTES;
-    uint8_t* b_hi = st + 2 * G::A_BYTES;
-    uint8_t* b_lo = b_hi + G::B_BYTES;
     mbar_expect_tx(&full[s], G::STAGE);
-    const int k0 = (kb0 + i) * G::BK;
-    if (mu == 0) {
-      // A = K_x rows n = m_in.., B = C rows y = ncol0.. at z = m_out
-      tma_load_2d(a_hi, &maps.k_hi[0], k0, m_in, &full[s]);
-      tma_load_2d(a_lo, &maps.k_lo[0], k0, m_in, &full[s]);
-      tma_load_3d(b_hi, &maps.c_hi[0], k0, ncol0, m_out, &full[s]);
-      tma_load_3d(b_lo, &maps.c_lo[0], k0, ncol0, m_out, &full[s]);
-    } else if (E == 4) {
-      // tf32 parts: A = the C split transposed so that the contraction axis is contiguous
-      // (K-major), 128 x-lines per tile; B = K_mu rows
-      tma_load_3d(a_hi, &maps.c_hi[mu], k0, m_in, m_out, &full[s]);
-      tma_load_3d(a_lo, &maps.c_lo[mu], k0, m_in, m_out, &full[s]);
-      tma_load_2d(b_hi, &maps.k_hi[mu], k0, ncol0, &full[s]);
-      tma_load_2d(b_lo, &maps.k_lo[mu], k0, ncol0, &full[s]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const int x = m_in + j * (128 / E);
-        if (mu == 1) {
-          tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[1], x, k0, m_out, &full[s]);
-          tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[1], x, k0, m_out, &full[s]);
-        } else {
-          tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[2], x, m_out, k0, &full[s]);
-          tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[2], x, m_out, k0, &full[s]);
-        }
-      }
-      tma_load_2d(b_hi, &maps.k_hi[mu], k0, ncol0, &full[s]);
-      tma_load_2d(b_lo, &maps.k_lo[mu], k0, ncol0, &full[s]);
-    }
+    load_stage<E, BN>(maps, tl, (kb0 + i) * G::BK, smem + (size_t)s * G::STAGE, &full[s]);
   };
 
   // ---- prologue: barrier setup and accumulator allocation overlap the previous kernel
@@ -318,8 +396,15 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the first stages' weight parts do not depend on the previous kernel
+    const int pre = nkb < G::STAGES ? nkb : G::STAGES;
+    for (int i = 0; i < pre; ++i) {
+      mbar_expect_tx(&full[i], G::STAGE);
+      load_stage_weights<E, BN>(maps, tl, (kb0 + i) * G::BK, smem + (size_t)i * G::STAGE, &full[i]);
+    }
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    for (int i = 0; i < G::STAGES && i < nkb; ++i) issue(i);
+    for (int i = 0; i < pre; ++i)
+      load_stage_conc<E, BN>(maps, tl, (kb0 + i) * G::BK, smem + (size_t)i * G::STAGE, &full[i]);
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -331,8 +416,9 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  asm volatile("griddepcontrol.wait;" ::: "memory");        // F is written below
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // F is written below
+  // the next kernel may be scheduled now when this grid runs in one wave, else at the end
+  if (P.early_trigger) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   if (threadIdx.x == 0) {
     // ---------------- producer (remaining k-blocks)
@@ -344,63 +430,42 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer
     const bool kmajor = (mu == 0) || (E == 4);
-    const uint32_t idesc = kmajor ? G::IDESC_K : G::IDESC_MN;
     for (int i = 0; i < nkb; ++i) {
       const int s = i % G::STAGES;
       if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
       tc_fence_after();
-      const uint32_t st = smem_u32(smem + (size_t)s * G::STAGE);
-      const uint32_t a_hi = st, a_lo = st + G::A_BYTES;
-      const uint32_t b_hi = st + 2 * G::A_BYTES, b_lo = b_hi + G::B_BYTES;
-#pragma unroll
-      for (int kk = 0; kk < G::BK / Kind<E>::UK; ++kk) {
-        uint32_t a_off, a_lbo;
-        if (kmajor) {  // K-major A: advance within the 128-byte row
-          a_off = kk * Kind<E>::UK * E;
-          a_lbo = 16;
-        } else {        // MN-major A: advance by UK rows of 128 bytes
-          a_off = kk * Kind<E>::UK * 128;
-          a_lbo = G::A_BOX_MN;
-        }
-        const uint32_t b_off = kk * Kind<E>::UK * E;
-        const uint64_t dah = smem_desc(a_hi + a_off, a_lbo, 1024);
-        const uint64_t dal = smem_desc(a_lo + a_off, a_lbo, 1024);
-        const uint64_t dbh = smem_desc(b_hi + b_off, 16, 1024);
-        const uint64_t dbl = smem_desc(b_lo + b_off, 16, 1024);
-        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
-        mma<E>(tmem, dah, dbh, idesc, acc);
-        mma<E>(tmem, dah, dbl, idesc, 1u);
-        mma<E>(tmem, dal, dbh, idesc, 1u);
-      }
+      mma_stage<E, BN>(tmem, smem_u32(smem + (size_t)s * G::STAGE), kmajor, i == 0);
       mma_commit(&empty[s]);
     }
     mma_commit(done);
   }
   __syncwarp();
 
-  // ---------------- epilogue: TMEM -> shared tile [BN][128] (lane = x) -> F
-  const bool have = mbar_wait(done, 0, P.flag);
+  // ---------------- epilogue
+  bool have = mbar_wait(done, 0, P.flag);
   tc_fence_after();
   float* tile = reinterpret_cast<float*>(smem);  // the operand ring is idle once `done` fired
   const int row = threadIdx.x;                   // accumulator lane = x offset in the tile
+  const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  int r0 = 0, r1 = BN;  // tile rows (output nodes n) this CTA writes
+  // TMEM -> shared tile [BN][128] (lane = x)
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
     float v[32];
-    tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+    tmem_ld32(lane_addr + c0, v);
 #pragma unroll
     for (int j = 0; j < 32; ++j) tile[(c0 + j) * BM + row] = have ? v[j] : 0.0f;
   }
-
-  int r0 = 0, r1 = BN;  // tile rows (output nodes n) this CTA writes
-  if (ks > 1) {
+  if constexpr (KS > 1) {
     // partial tiles of the cluster are complete; CTA `rank` sums rows
-    // [rank*BN/ks, (rank+1)*BN/ks) over ranks 0..ks-1 in that order
+    // [rank*BN/ks, (rank+1)*BN/ks) over ranks 0..ks-1 in that order (the sum does not
+    // depend on timing), reading the other ranks' tiles through distributed shared memory
     asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-    const int rows = BN / ks;
-    r0 = rank * rows;
-    r1 = r0 + rows;
+    constexpr int ROWS = G::ROWS;
+    r0 = rank * ROWS;
+    r1 = r0 + ROWS;
     const uint32_t tbase = smem_u32(tile);
-    constexpr int PER = (BN / KS) * (BM / 4) / 128;  // float4 elements per thread
+    constexpr int PER = ROWS * (BM / 4) / 128;  // float4 elements per thread
     uint32_t offs[PER];
     float4 acc[PER];
 #pragma unroll
@@ -410,12 +475,11 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
       acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int r = 0; r < KS; ++r) {  // rank order: the sum does not depend on timing
+    for (int r = 0; r < KS; ++r) {
       float4 b[PER];
 #pragma unroll
       for (int k = 0; k < PER; ++k) {
-        uint32_t raddr;
-        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(tbase + offs[k]), "r"(r));
+        const uint32_t raddr = cluster_addr(tbase + offs[k], r);
         asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(b[k].x), "=f"(b[k].y), "=f"(b[k].z), "=f"(b[k].w)
                      : "r"(raddr)
@@ -429,10 +493,13 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
         acc[k].w += b[k].w;
       }
     }
+    // rows r0..r1 of this tile are read by no other rank: sum them in place
 #pragma unroll
     for (int k = 0; k < PER; ++k)
       *reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(tile) + offs[k]) = acc[k];
+    tile += r0 * BM;
   }
+  // `tile` now holds rows r0..r1-1 of the result from its start
 
   const long long nodes = P.nodes;
   float* F = P.F + (long long)mu * nodes;
@@ -452,7 +519,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
       asm volatile(
           "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
               reinterpret_cast<uint64_t>(&maps.f[mu])),
-          "r"(m_in), "r"(c1), "r"(c2), "r"(smem_u32(tile + r0 * BM))
+          "r"(m_in), "r"(c1), "r"(c2), "r"(smem_u32(tile))
           : "memory");
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -467,7 +534,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
         const int lim = (mu == 0) ? n1 : ax.side;
         if (n >= lim) break;
         const long long idx = (mu == 2) ? ((long long)n * n1 + m_out) * n0 + x : ((long long)m_out * n1 + n) * n0 + x;
-        F[idx] = tile[rr * BM + row];
+        F[idx] = tile[(rr - r0) * BM + row];
       }
     }
   }
@@ -481,29 +548,269 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
   }
+  if (!P.early_trigger) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 template <int E, int BN, int KS>
-__global__ void __launch_bounds__(128, 1) frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
+__global__ void __launch_bounds__(128, 1)
+frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
   extern __shared__ uint8_t smem_raw[];
   frac_tc_tile<E, BN, KS>(maps, P, blockIdx.x, smem_raw);
 }
 
-// Grouped form for a batch of independent problems: one launch covers every tile of
-// every problem; block_start[p] is the first CTA of problem p (ascending).
-template <int E, int BN>
-__global__ void __launch_bounds__(128, 1)
-frac_tc_batch_kernel(const TcMaps* __restrict__ maps, const TcParams* __restrict__ prm,
-                     const int* __restrict__ block_start, int nprob) {
-  extern __shared__ uint8_t smem_raw[];
-  const int b = blockIdx.x;
-  int lo = 0, hi = nprob - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&block_start[mid]) <= b) lo = mid;
-    else hi = mid - 1;
+// ---------------------------------------------------------------------------- persistent form
+// Problems with many tiles: one CTA per SM walks the tile list (tile t = first,
+// first + stride, ...).  Warp 0 streams the k-blocks of consecutive tiles through the
+// STAGES-deep operand ring without a break at tile boundaries, warp 1 issues each tile's
+// MMAs into one of two TMEM accumulators (the i-th tile of the CTA into buffer i & 1),
+// and warps 2-5 drain the other accumulator (tcgen05.ld, 32 columns at a time, through a
+// double-buffered shared chunk and a TMA store), so a tile's epilogue overlaps the next
+// tile's loads and MMAs.  Every wait is bounded as in the per-tile kernel; on a timeout
+// the CTA stops issuing, waits (bounded) for its copies and MMAs in flight, releases
+// TMEM and returns with bit 2 of the error flag set.
+constexpr int PBN = 128;
+constexpr int kPersistThreads = 192;
+
+template <int E>
+struct PCfg {
+  using G = Cfg<E, PBN>;
+  static constexpr int STAGES = 3;
+  static constexpr uint32_t CHUNK = 32 * BM * 4;  // 32 output rows x 128 x (FP32)
+  static constexpr size_t RING = (size_t)STAGES * G::STAGE;
+  static constexpr size_t SMEM = RING + 2 * CHUNK + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Locate(t, maps, prm, cid): the problem and local tile index of global tile t
+template <int E, class Locate>
+__device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, int* flag, uint8_t* smem_raw) {
+  using C = PCfg<E>;
+  using G = typename C::G;
+  constexpr int STAGES = C::STAGES;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* stage_out = reinterpret_cast<float*>(smem + C::RING);  // [2][32][128]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::RING + 2 * C::CHUNK);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;  // [2]
+  uint64_t* tempty = tfull + 2;      // [2]
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  int* s_ok = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int first = blockIdx.x, stride = gridDim.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 1);
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  frac_tc_tile<E, BN, 1>(maps[lo], prm[lo], b - __ldg(&block_start[lo]), smem_raw);
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * PBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // programmatic dependent launch: C (loaded) and F (stored) belong to the previous kernels
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+  if (threadIdx.x == 0) {
+    // ---------------- producer
+    int r = 0;
+    bool ok = true;
+    for (int t = first; t < ntiles && ok; t += stride) {
+      const TcMaps* maps;
+      const TcParams* P;
+      int cid;
+      locate(t, maps, P, cid);
+      const TileAt tl = decode_tile(*P, cid, PBN);
+      const int nkb = P->ax[tl.mu].kblocks;
+      for (int kb = 0; kb < nkb; ++kb, ++r) {
+        const int s = r % STAGES;
+        if (r >= STAGES && !mbar_wait(&empty[s], ((r / STAGES) - 1) & 1, flag)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full[s], G::STAGE);
+        load_stage<E, PBN>(*maps, tl, kb * G::BK, smem + (size_t)s * G::STAGE, &full[s]);
+      }
+    }
+    // every issued copy has landed before the CTA may leave (bounded)
+    for (int q = (r > STAGES ? r - STAGES : 0); q < r; ++q) mbar_wait(&full[q % STAGES], (q / STAGES) & 1, flag);
+  } else if (threadIdx.x == 32) {
+    // ---------------- MMA issuer
+    int r = 0, i = 0;
+    bool ok = true;
+    for (int t = first; t < ntiles && ok; t += stride, ++i) {
+      const TcMaps* maps;
+      const TcParams* P;
+      int cid;
+      locate(t, maps, P, cid);
+      const TileAt tl = decode_tile(*P, cid, PBN);
+      const int nkb = P->ax[tl.mu].kblocks;
+      const int b = i & 1;
+      if (i >= 2 && !mbar_wait(&tempty[b], ((i >> 1) - 1) & 1, flag)) break;
+      tc_fence_after();
+      const uint32_t d = tmem + b * PBN;
+      const bool kmajor = (tl.mu == 0) || (E == 4);
+      for (int kb = 0; kb < nkb; ++kb, ++r) {
+        const int s = r % STAGES;
+        if (!mbar_wait(&full[s], (r / STAGES) & 1, flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        mma_stage<E, PBN>(d, smem_u32(smem + (size_t)s * G::STAGE), kmajor, kb == 0);
+        mma_commit(&empty[s]);
+      }
+      if (ok) mma_commit(&tfull[b]);
+    }
+    mma_commit(drain);  // fires once every MMA issued above has completed
+  } else if (warp >= 2) {
+    // ---------------- epilogue: 128 threads, TMEM lane quarter = warp % 4
+    const int et = threadIdx.x - 64;
+    const int q = warp & 3;
+    const int row = q * 32 + (threadIdx.x & 31);  // accumulator lane = x offset in the tile
+    int i = 0, chunk = 0;
+    for (int t = first; t < ntiles; t += stride, ++i) {
+      const TcMaps* maps;
+      const TcParams* P;
+      int cid;
+      locate(t, maps, P, cid);
+      const TileAt tl = decode_tile(*P, cid, PBN);
+      const int b = i & 1;
+      if (et == 0) *s_ok = mbar_wait(&tfull[b], (i >> 1) & 1, flag) ? 1 : 0;
+      epi_sync();
+      if (!*s_ok) break;
+      tc_fence_after();
+      const long long nodes = P->nodes;
+      float* F = P->F + (long long)tl.mu * nodes;
+      const int n0 = P->n0, n1 = P->n1;
+      const int lim = (tl.mu == 0) ? n1 : P->ax[tl.mu].side;  // output rows that exist
+      for (int c0 = 0; c0 < PBN; c0 += 32, ++chunk) {
+        float v[32];
+        tmem_ld32(tmem + b * PBN + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
+        if (c0 + 32 >= PBN) {
+          // the accumulator is drained: hand it back to the MMA warp
+          tc_fence_before();
+        }
+        if (P->tma_store) {
+          float* sb = stage_out + (chunk & 1) * (32 * BM);
+          if (et == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          epi_sync();  // the store that last read this buffer is done with it
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sb[j * BM + row] = v[j];
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          epi_sync();
+          if (et == 0) {
+            if (c0 + 32 >= PBN) mbar_arrive(&tempty[b]);
+            if (tl.ncol0 + c0 < lim) {
+              int c1, c2;
+              if (tl.mu == 2) {
+                c1 = tl.m_out;
+                c2 = tl.ncol0 + c0;
+              } else {
+                c1 = tl.ncol0 + c0;
+                c2 = tl.m_out;
+              }
+              asm volatile(
+                  "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                      reinterpret_cast<uint64_t>(&maps->f[tl.mu])),
+                  "r"(tl.m_in), "r"(c1), "r"(c2), "r"(smem_u32(sb))
+                  : "memory");
+            }
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+        } else {
+          // rows of F that are not 16-byte aligned: plain stores, coalesced along x
+          const int x = tl.m_in + row;
+          if (x < n0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int n = tl.ncol0 + c0 + j;
+              const long long idx = (tl.mu == 2) ? ((long long)n * n1 + tl.m_out) * n0 + x
+                                                 : ((long long)tl.m_out * n1 + n) * n0 + x;
+              if (n < lim) F[idx] = v[j];
+            }
+          }
+          if (c0 + 32 >= PBN) {
+            epi_sync();
+            if (et == 0) mbar_arrive(&tempty[b]);
+          }
+        }
+      }
+    }
+    if (et == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    if (threadIdx.x == 32) mbar_wait(drain, 0, flag);
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * PBN) : "memory");
+  }
+}
+
+struct LocateOne {
+  const TcMaps* maps;
+  const TcParams* prm;
+  __device__ __forceinline__ void operator()(int t, const TcMaps*& m, const TcParams*& p, int& cid) const {
+    m = maps;
+    p = prm;
+    cid = t;
+  }
+};
+
+struct LocateBatch {
+  const TcMaps* maps;
+  const TcParams* prm;
+  const int* start;
+  int nprob;
+  __device__ __forceinline__ void operator()(int t, const TcMaps*& m, const TcParams*& p, int& cid) const {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&start[mid]) <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    m = maps + lo;
+    p = prm + lo;
+    cid = t - __ldg(&start[lo]);
+  }
+};
+
+template <int E>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+frac_tc_persist_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  persist_body<E>(LocateOne{&maps, &P}, P.total_tiles, P.flag, smem_raw);
+}
+
+template <int E>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+frac_tc_persist_batch_kernel(const TcMaps* __restrict__ maps, const TcParams* __restrict__ prm,
+                             const int* __restrict__ start, int nprob, int ntiles, int* flag) {
+  extern __shared__ uint8_t smem_raw[];
+  persist_body<E>(LocateBatch{maps, prm, start, nprob}, ntiles, flag, smem_raw);
 }
 
 // ---------------------------------------------------------------------------- splits
@@ -618,19 +925,19 @@ cudaError_t launch_kernel(const TcPlan* p, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(frac_tc_kernel<E, BN, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg<E, BN>::SMEM);
+                                         (int)Cfg<E, BN, KS>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->prm.total_tiles * KS, 1, 1);
   cfg.blockDim = dim3(128, 1, 1);
-  cfg.dynamicSmemBytes = Cfg<E, BN>::SMEM;
+  cfg.dynamicSmemBytes = Cfg<E, BN, KS>::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[2];
   int na = 0;
   at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[na].val.programmaticStreamSerializationAllowed = 1;
+  at[na].val.programmaticStreamSerializationAllowed = p->pdl ? 1 : 0;
   ++na;
   if (KS > 1) {
     at[na].id = cudaLaunchAttributeClusterDimension;
@@ -652,6 +959,30 @@ cudaError_t launch_bn(const TcPlan* p, cudaStream_t s) {
     case 4: return launch_kernel<E, BN, 4>(p, s);
     default: return launch_kernel<E, BN, 8>(p, s);
   }
+}
+
+constexpr int kPersistCTAs = 152;  // one per SM
+
+template <int E>
+cudaError_t launch_persist(const TcPlan* p, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(frac_tc_persist_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PCfg<E>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(std::min(p->prm.total_tiles, kPersistCTAs), 1, 1);
+  cfg.blockDim = dim3(kPersistThreads, 1, 1);
+  cfg.dynamicSmemBytes = PCfg<E>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = p->pdl ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, frac_tc_persist_kernel<E>, p->maps, p->prm);
 }
 
 }  // namespace
@@ -761,6 +1092,14 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
     p->bn = force_bn;
     ks = std::max(1, force_ks);
   }
+  // many tiles: the persistent kernel (128-column tiles, no split) overlaps each tile's
+  // epilogue with the next tile's MMAs; batched handles always use it
+  if (force_bn == PBN && ks == 1) p->persist = true;
+  if (force_bn <= 0 && count_tiles(PBN) >= 2 * kSMs) {
+    p->persist = true;
+    p->bn = PBN;
+    ks = 1;
+  }
   P.ksplit = ks;
   P.tma_store = (n[0] % 4 == 0) ? 1 : 0;
   int tiles = 0;
@@ -810,7 +1149,7 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
     for (int mu = 0; mu < h->d; ++mu) {
       const cuuint64_t fd[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
       const cuuint64_t fs[2] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4};
-      const cuuint32_t rows = (cuuint32_t)(p->bn / ks);
+      const cuuint32_t rows = p->persist ? 32u : (cuuint32_t)(p->bn / ks);  // persistent: 32-row chunks
       const cuuint32_t fb[3] = {BM, mu == 2 ? 1u : rows, mu == 2 ? rows : 1u};
       const cuuint32_t es[3] = {1, 1, 1};
       EncodeTiled enc = get_encoder();
@@ -823,6 +1162,7 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
     }
   }
   P.total_tiles = tiles;
+  P.early_trigger = (tiles * ks <= kSMs) ? 1 : 0;
   return LBM_OK;
 }
 
@@ -844,7 +1184,7 @@ int tc_batch_prepare(lbm_s* b) {
   int total = 0;
   for (int i = 0; i < P; ++i) {
     const TcPlan* t = b->subs[i]->tc;
-    if (!t || t->bn != 128 || t->prm.ksplit != 1 || t->elem != 2) return LBM_EINVAL;
+    if (!t || !t->persist || t->prm.ksplit != 1 || t->elem != 2) return LBM_EINVAL;
     maps[i] = t->maps;
     prm[i] = t->prm;
     start[i] = total;
@@ -864,24 +1204,37 @@ int tc_batch_prepare(lbm_s* b) {
 cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(frac_tc_batch_kernel<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg<2, 128>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(frac_tc_persist_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PCfg<2>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  frac_tc_batch_kernel<2, 128><<<b->batch_tc_blocks, 128, Cfg<2, 128>::SMEM, s>>>(
+  const int grid = std::min(b->batch_tc_blocks, kPersistCTAs);
+  frac_tc_persist_batch_kernel<2><<<grid, kPersistThreads, PCfg<2>::SMEM, s>>>(
       static_cast<const TcMaps*>(b->batch_tc_maps), static_cast<const TcParams*>(b->batch_tc_prm), b->batch_tc_start,
-      static_cast<int>(b->subs.size()));
+      static_cast<int>(b->subs.size()), b->batch_tc_blocks, b->dev.flag);
   return cudaGetLastError();
 }
 
 int tc_split_pitch(const lbm_s* h) { return h->tc ? h->tc->ldp : 0; }
 
+bool tc_one_wave(const lbm_s* h) {
+  const TcPlan* p = h->tc;
+  return p && (p->persist || (long long)p->prm.total_tiles * p->prm.ksplit <= kPersistCTAs);
+}
+
+void tc_set_pdl(lbm_s* h, bool on) {
+  if (h->tc) h->tc->pdl = on;
+}
+
 cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s) {
   const TcPlan* p = h->tc;
   if (!p) return cudaErrorNotSupported;
-  if (p->elem == 2) return (p->bn == 128) ? launch_bn<2, 128>(p, s) : launch_bn<2, 256>(p, s);
-  return (p->bn == 128) ? launch_bn<4, 128>(p, s) : launch_bn<4, 256>(p, s);
+  if (p->persist) return (p->elem == 2) ? launch_persist<2>(p, s) : launch_persist<4>(p, s);
+  // 256-column tiles are chosen only when they alone fill the GPU: never split
+  if (p->bn == 256 && p->prm.ksplit != 1) return cudaErrorInvalidConfiguration;
+  if (p->elem == 2) return (p->bn == 128) ? launch_bn<2, 128>(p, s) : launch_kernel<2, 256, 1>(p, s);
+  return (p->bn == 128) ? launch_bn<4, 128>(p, s) : launch_kernel<4, 256, 1>(p, s);
 }
 
 cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s) {

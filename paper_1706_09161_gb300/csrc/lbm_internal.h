@@ -59,6 +59,9 @@ struct lbm_s {
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int graph_steps = 0;                 // steps per captured graph (even)
   int launches_per_step = 0;
+  // programmatic dependent launch between the operator and collide-stream: only when both
+  // grids run in a single wave (measured: with multi-wave 3-D grids it costs ~30%)
+  bool pdl = false;
   int device = 0;
   lbm::TcPlan* tc = nullptr;           // split-precision tensor-core operator, if used
   // batch of independent problems: one sub-handle per problem (each owns its buffers)
@@ -106,6 +109,9 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
 int tc_batch_prepare(lbm_s* b);
 cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s);
 int cs_batch_prepare(lbm_s* b);
+bool cs_one_wave(const lbm_s* h);  // the collide-stream grid fits in one wave
+bool tc_one_wave(const lbm_s* h);  // the tensor-core operator grid fits in one wave
+void tc_set_pdl(lbm_s* h, bool on);
 cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t s);
 void tc_release(lbm_s* h);
 int tc_split_pitch(const lbm_s* h);

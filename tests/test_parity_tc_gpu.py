@@ -6,7 +6,8 @@ fixed relative-L2 bound from the split's rounding (bf16: 2^-16 per part, tf32:
 2^-22); whole steps use ``arith_bounds.bound``, i.e. 10x the error the same
 arithmetic makes when re-run on the CPU, never below 1e-5.
 Sizes cover one and several 128-line / 64-column tiles, ragged tails, the
-minimum grid, and the 512x512 workload.
+minimum grid, and the 512x512 workload; the two largest 3-D grids have enough
+tiles for the persistent kernel (one with F rows that TMA cannot store, n0 % 4 != 0).
 """
 import numpy as np
 import pytest
@@ -19,6 +20,17 @@ from paper_1706_09161_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 F_TOL = {"bf16split": 4e-5, "tf32split": 2e-6}
+
+
+def f_tol(kind: str, side: int) -> float:
+    """Relative-L2 bound of the split operator along a line of `side` nodes.
+
+    The fixed part covers the split itself (the dropped lo*lo product and the
+    rounding of the parts); the FP32 accumulation of `side` non-negative products
+    adds about sqrt(side) roundings of up to 2^-23 each (tensor-core accumulation is
+    not assumed to round to nearest), counted twice.
+    """
+    return max(F_TOL[kind], 2.0 * np.sqrt(side) * 2.0 ** -23)
 KINDS = ["bf16split", "tf32split"]
 
 
@@ -34,7 +46,8 @@ def L():
 
 rel_l2 = arith_bounds.rel_l2
 
-GRIDS = [(3, 3), (37, 29), (130, 70), (200, 131), (19, 13, 11), (40, 9, 6), (131, 20, 9)]
+GRIDS = [(3, 3), (37, 29), (130, 70), (200, 131), (19, 13, 11), (40, 9, 6), (131, 20, 9), (256, 64, 64),
+         (130, 129, 70)]
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -50,11 +63,11 @@ def test_tc_fractional_terms(L, kind, grid):
     F = O.fractional_terms(ops, C)
     with L.Lattice(pb, C0, kind) as lat:
         for mu in range(d):
-            assert rel_l2(lat.F(mu), F[mu].numpy()) < F_TOL[kind], f"axis {mu}"
+            assert rel_l2(lat.F(mu), F[mu].numpy()) < f_tol(kind, grid[mu]), f"axis {mu}"
 
 
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("grid", [(37, 29), (130, 70), (19, 13, 11)])
+@pytest.mark.parametrize("grid", [(37, 29), (130, 70), (19, 13, 11), (130, 129, 70)])
 @pytest.mark.parametrize("collision", ["bgk", "mrt"])
 def test_tc_steps_match_oracle(L, kind, grid, collision):
     rng = np.random.default_rng(53 + grid[0])
