@@ -148,9 +148,27 @@ int lbm_read_C(lbm_t h, double* C_host);
 int lbm_read_F(lbm_t h, int mu, double* F_host);
 
 /* Copy / overwrite the populations, Q*nodes doubles laid out [q][node] (host).
- * lbm_write_f also recomputes C = <1|f>.  Both synchronise. */
+ * lbm_write_f also recomputes C = <1|f> (and the split operands of the tensor-core
+ * forms).  Both synchronise. */
 int lbm_read_f(lbm_t h, double* f_host);
 int lbm_write_f(lbm_t h, const double* f_host);
+
+/* Checkpoint and resume.  The paper has no counterpart: by Algorithm 1 the
+ * populations f alone determine the rest of a run, so the state is the current f of
+ * every problem of the handle (single or batched), bit for bit in the working
+ * precision, after a header (magic, version, lattice, precision, problem count and
+ * grids).
+ *   lbm_state_size: bytes that lbm_save writes (> 0), or LBM_EINVAL for a null handle.
+ *   lbm_save: writes the state into dst_host (caller-owned, `bytes` long; LBM_EINVAL
+ *             if smaller than lbm_state_size).  Synchronises.
+ *   lbm_load: restores a state saved from a handle with the same lattice, precision
+ *             and grids (LBM_EINVAL otherwise, handle unchanged); recomputes C and the
+ *             split operands and clears the latched instability flag.  Synchronises.
+ * Saving, stepping k times, loading and stepping k times again gives bit-identical
+ * populations. */
+long long lbm_state_size(lbm_t h);
+int lbm_save(lbm_t h, void* dst_host, long long bytes);
+int lbm_load(lbm_t h, const void* src_host, long long bytes);
 
 /* Total mass sum_x C(x) of the current concentration, reduced on the device in
  * FP64 (block partials, then one final pass).  Synchronises. */

@@ -634,7 +634,92 @@ int lbm_write_f(lbm_t h, const double* f_host) {
     LBM_CUDA(cudaStreamSynchronize(h->stream));
   }
   LBM_CUDA(lbm::launch_moment(h, h->dev.f[h->cur], h->dev.C, h->stream));
+  if (uses_tc(h)) LBM_CUDA(lbm::launch_split_C(h, h->stream));
   return latched(h);
+}
+
+namespace {
+
+constexpr uint32_t kStateMagic = 0x464d424cu;  // "LBMF"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t lattice, precision, nprob, pad;
+  int64_t payload;  // bytes of populations after the header and the grid table
+};
+
+std::vector<lbm_s*> members(lbm_s* h) {
+  if (h->is_batch()) return h->subs;
+  return {h};
+}
+
+long long payload_bytes(lbm_s* h) {
+  long long b = 0;
+  for (lbm_s* p : members(h)) b += (long long)p->Q * p->sp.nodes * p->elem;
+  return b;
+}
+
+long long state_bytes(lbm_s* h) {
+  return (long long)sizeof(StateHeader) + 3LL * sizeof(int32_t) * (long long)members(h).size() + payload_bytes(h);
+}
+
+}  // namespace
+
+long long lbm_state_size(lbm_t h) {
+  if (!h) return LBM_EINVAL;
+  return state_bytes(h);
+}
+
+int lbm_save(lbm_t h, void* dst_host, long long bytes) {
+  if (!h || !dst_host || bytes < state_bytes(h)) return LBM_EINVAL;
+  const std::vector<lbm_s*> ms = members(h);
+  StateHeader hd{kStateMagic, kStateVersion, h->prm.lattice, h->prm.precision, (int32_t)ms.size(), 0,
+                 payload_bytes(h)};
+  char* out = static_cast<char*>(dst_host);
+  std::memcpy(out, &hd, sizeof(hd));
+  out += sizeof(hd);
+  for (lbm_s* p : ms) {
+    const int32_t g[3] = {p->sp.n[0], p->sp.n[1], p->sp.n[2]};
+    std::memcpy(out, g, sizeof(g));
+    out += sizeof(g);
+  }
+  for (lbm_s* p : ms) {
+    const size_t b = (size_t)p->Q * p->sp.nodes * p->elem;
+    LBM_CUDA(cudaMemcpyAsync(out, p->dev.f[h->cur], b, cudaMemcpyDeviceToHost, h->stream));
+    out += b;
+  }
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_load(lbm_t h, const void* src_host, long long bytes) {
+  if (!h || !src_host || bytes < (long long)sizeof(StateHeader)) return LBM_EINVAL;
+  const std::vector<lbm_s*> ms = members(h);
+  StateHeader hd;
+  const char* in = static_cast<const char*>(src_host);
+  std::memcpy(&hd, in, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.lattice != h->prm.lattice ||
+      hd.precision != h->prm.precision || hd.nprob != (int32_t)ms.size() || hd.payload != payload_bytes(h) ||
+      bytes < state_bytes(h))
+    return LBM_EINVAL;
+  in += sizeof(hd);
+  for (lbm_s* p : ms) {
+    int32_t g[3];
+    std::memcpy(g, in, sizeof(g));
+    in += sizeof(g);
+    if (g[0] != p->sp.n[0] || g[1] != p->sp.n[1] || g[2] != p->sp.n[2]) return LBM_EINVAL;
+  }
+  for (lbm_s* p : ms) {
+    const size_t b = (size_t)p->Q * p->sp.nodes * p->elem;
+    LBM_CUDA(cudaMemcpyAsync(p->dev.f[h->cur], in, b, cudaMemcpyHostToDevice, h->stream));
+    in += b;
+    LBM_CUDA(lbm::launch_moment(p, p->dev.f[h->cur], p->dev.C, h->stream));
+    if (uses_tc(p)) LBM_CUDA(lbm::launch_split_C(p, h->stream));
+    LBM_CUDA(cudaMemsetAsync(p->dev.flag, 0, sizeof(int), h->stream));
+  }
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
 }
 
 int lbm_mass(lbm_t h, double* mass) {

@@ -80,6 +80,9 @@ def _load() -> ctypes.CDLL:
         "lbm_read_F": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "lbm_read_f": (ctypes.c_int, [vp, dp]),
         "lbm_write_f": (ctypes.c_int, [vp, dp]),
+        "lbm_state_size": (ctypes.c_longlong, [vp]),
+        "lbm_save": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
+        "lbm_load": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
         "lbm_mass": (ctypes.c_int, [vp, dp]),
         "lbm_sync": (ctypes.c_int, [vp]),
         "lbm_get_stream": (ctypes.c_int, [vp, P(vp)]),
@@ -103,7 +106,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 
 # Declared C entry points, re-exported under their own names.
-EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_read_C", "lbm_batch_mass", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f",
+EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_read_C", "lbm_batch_mass", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f", "lbm_state_size", "lbm_save", "lbm_load",
             "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_frac_matrix",
             "lbm_grad", "lbm_frac_matrix_grad", "lbm_digamma", "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
 
@@ -227,6 +230,24 @@ def lbm_read_f(h: int, out: np.ndarray) -> np.ndarray:
     return out
 
 
+def lbm_state_size(h: int) -> int:
+    n = int(_lib.lbm_state_size(ctypes.c_void_p(h)))
+    _check(n if n < 0 else 0, "lbm_state_size")
+    return n
+
+
+def lbm_save(h: int) -> np.ndarray:
+    """The handle's state (header + populations in the working precision) as bytes."""
+    buf = np.empty(lbm_state_size(h), dtype=np.uint8)
+    _check(_lib.lbm_save(ctypes.c_void_p(h), buf.ctypes.data_as(ctypes.c_void_p), buf.size), "lbm_save")
+    return buf
+
+
+def lbm_load(h: int, state: np.ndarray) -> None:
+    state = np.ascontiguousarray(state, dtype=np.uint8)
+    _check(_lib.lbm_load(ctypes.c_void_p(h), state.ctypes.data_as(ctypes.c_void_p), state.size), "lbm_load")
+
+
 def lbm_write_f(h: int, f: np.ndarray) -> None:
     f = np.ascontiguousarray(f, dtype=np.float64)
     _check(_lib.lbm_write_f(ctypes.c_void_p(h), _dptr(f)), "lbm_write_f")
@@ -344,6 +365,14 @@ class Lattice:
     def write_f(self, f: np.ndarray) -> None:
         lbm_write_f(self.h, f)
 
+    def save(self) -> np.ndarray:
+        """Checkpoint: the populations, bit for bit, behind a header (lbm_save)."""
+        return lbm_save(self.h)
+
+    def load(self, state: np.ndarray) -> None:
+        """Resume from a checkpoint of a handle with the same lattice, precision and grid."""
+        lbm_load(self.h, state)
+
     def mass(self) -> float:
         return lbm_mass(self.h)
 
@@ -402,6 +431,13 @@ class Batch:
 
     def mass(self, prob: int) -> float:
         return lbm_batch_mass(self.h, prob)
+
+    def save(self) -> np.ndarray:
+        """Checkpoint of every problem's populations (lbm_save)."""
+        return lbm_save(self.h)
+
+    def load(self, state: np.ndarray) -> None:
+        lbm_load(self.h, state)
 
     def sync(self) -> None:
         _check(lbm_sync(self.h), "lbm_sync")

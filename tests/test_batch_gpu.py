@@ -74,3 +74,18 @@ def test_batch_rejects_mixed_collisions(L):
     with pytest.raises(L.LBMError) as ei:
         L.Batch(probs, fields, "bf16split")
     assert ei.value.code == L.LBM_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16split"])
+def test_batch_save_load_resumes_bit_exact(L, precision):
+    probs, fields, _ = W.batch64(nprob=5, sides=(37, 128, 200), seed=13)
+    with L.Batch(probs, fields, precision) as b:
+        b.step(3)
+        state = b.save()
+        b.step(35)
+        C_a = [b.C(i) for i in range(len(probs))]
+        b.load(state)
+        b.step(35)
+        C_b = [b.C(i) for i in range(len(probs))]
+    for a, c in zip(C_a, C_b):
+        assert np.array_equal(a, c)

@@ -206,3 +206,54 @@ def test_zero_steps_is_noop(L):
         before = lat.f()
         lat.step(0)
         assert np.array_equal(lat.f(), before)
+
+
+# ---------------------------------------------------------------- checkpoint / resume
+
+@pytest.mark.parametrize("kind", ["fp64", "fp32", "bf16split", "tf32split"])
+def test_save_load_resumes_bit_exact(L, kind):
+    """Saving, stepping k times, loading and stepping k times again gives the same f."""
+    rng = np.random.default_rng(91)
+    pb = W.random_problem(rng, 2, "mrt", (130, 70))
+    C0 = W.random_field(rng, pb.grid)
+    with L.Lattice(pb, C0, kind) as lat:
+        lat.step(7)
+        state = lat.save()
+        lat.step(40)  # graph replay and single launches
+        f_a = lat.f()
+        lat.load(state)
+        lat.step(40)
+        f_b = lat.f()
+    assert np.array_equal(f_a, f_b)
+
+
+def test_load_rejects_other_handles(L):
+    rng = np.random.default_rng(92)
+    pb = W.random_problem(rng, 2, "mrt", (37, 29))
+    pb3 = W.random_problem(rng, 3, "mrt", (19, 13, 11))
+    with L.Lattice(pb, W.random_field(rng, pb.grid), "fp32") as a, \
+            L.Lattice(pb3, W.random_field(rng, pb3.grid), "fp32") as b, \
+            L.Lattice(pb, W.random_field(rng, pb.grid), "fp64") as c:
+        s = a.save()
+        for other in (b, c):
+            with pytest.raises(L.LBMError):
+                other.load(s)
+        with pytest.raises(L.LBMError):
+            a.load(s[:-1])  # truncated
+        a.load(s)
+
+
+def test_write_f_refreshes_split_operands(L):
+    """write_f on a tensor-core handle feeds the next step's operator the new C."""
+    rng = np.random.default_rng(93)
+    pb = W.random_problem(rng, 2, "mrt", (130, 70))
+    C0 = W.random_field(rng, pb.grid)
+    C1 = W.random_field(rng, pb.grid)
+    with L.Lattice(pb, C1, "bf16split") as src:
+        f1 = src.f()
+    with L.Lattice(pb, C0, "bf16split") as lat, L.Lattice(pb, C1, "bf16split") as ref:
+        lat.step(3)
+        lat.write_f(f1)
+        lat.step(5)
+        ref.step(5)
+        assert np.array_equal(lat.f(), ref.f())
