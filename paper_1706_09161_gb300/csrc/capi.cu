@@ -228,6 +228,7 @@ void free_all(lbm_s* h) {
     h->graph[i] = nullptr;
   }
   lbm::tc_release(h);
+  lbm::cs_release(h);
   void* ptrs[] = {h->dev.f[0], h->dev.f[1], h->dev.C, h->dev.C0, h->dev.F, h->dev.K, h->dev.KT, h->dev.stage,
                   h->dev.partials, h->dev.scalar, h->dev.flag, h->dev.Khi, h->dev.Klo, h->dev.Chi, h->dev.Clo};
   for (void* p : ptrs)
@@ -403,6 +404,7 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   } else {
     h->launches_per_step = 2;  // one SIMT operator launch over every axis, one collide-stream
   }
+  if (!batched && (rc = lbm::cs_prepare(h))) return fail(rc);
   *out = h;
   rc = lbm_set_C(h, C0_host);
   if (rc) {

@@ -10,10 +10,12 @@
 // collides its nodes plus a one-node ring and gathers ("pulls") each population
 // from the node it came from; the ring's collisions are recomputed by the
 // neighbouring CTAs and their loads mostly hit L2.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
+#include <new>
 #include <vector>
 
 #include "lbm_internal.h"
@@ -464,6 +466,244 @@ collide_stream_march_kernel(const KConst<real> sp, const real* __restrict__ f_in
   if (!early) pdl_trigger();
 }
 
+// ---------------------------------------------------------------------------- TMA-fed 3-D march
+// FP32 forms with n0 % 4 == 0: per plane, one thread loads the block's 40 x 18 window of
+// all Q populations and all d fractional terms (tile, one-node ring, x aligned down to a
+// 16-byte boundary) with two 4-D TMA box loads into a 3-stage shared-memory ring, two
+// planes ahead of the plane being collided; every thread then reads its node (owners)
+// or ring node (the three halo warps) from shared memory.  Nodes outside the domain
+// arrive as zeros (TMA out-of-bounds fill), which the collision maps to zero movers,
+// exactly as the plain march treats them.  The march itself (movers through shared
+// memory, z movers in registers, walls, moment, split) is that of march_body.
+constexpr int TW = TX + 8, TH = TY + 2;  // staged window: x from x0 - 4, y from y0 - 1
+constexpr int TMA_STAGES = 3;
+constexpr uint32_t TMA_F_BYTES = 7u * TH * TW * 4;   // D3Q7 populations
+constexpr uint32_t TMA_FF_BYTES = 3u * TH * TW * 4;  // fractional terms
+constexpr uint32_t TMA_TX = TMA_F_BYTES + TMA_FF_BYTES;  // bytes landing per plane
+constexpr uint32_t TMA_FF_OFF = (TMA_F_BYTES + 127) / 128 * 128;  // 128-byte aligned box starts
+constexpr uint32_t TMA_STAGE = (TMA_FF_OFF + TMA_FF_BYTES + 127) / 128 * 128;
+constexpr size_t TMA_SMEM = (size_t)TMA_STAGES * TMA_STAGE + 128 /*align*/ + 64 /*barriers*/;
+constexpr long long kTmaWaitNs = 2000000000LL;
+
+struct CsPlan {
+  CUtensorMap f[2];  // populations, dims (n0, n1, n2, Q), box (TW, TH, 1, Q)
+  CUtensorMap F;     // fractional terms, dims (n0, n1, n2, d), box (TW, TH, 1, d)
+};
+
+__device__ __forceinline__ uint32_t cs_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool cs_mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(cs_smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false (and bit 2 of the flag) after kTmaWaitNs of %globaltimer
+__device__ __forceinline__ bool cs_mbar_wait(uint64_t* bar, uint32_t parity, int* flag) {
+  if (cs_mbar_try(bar, parity)) return true;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (cs_mbar_try(bar, parity)) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > (unsigned long long)kTmaWaitNs) {
+      atomicOr(flag, 2);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void cs_tma_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(cs_smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(cs_smem_u32(bar))
+      : "memory");
+}
+
+template <bool MRT, int SPLIT>
+__global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
+collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUtensorMap map_f,
+                           const __grid_constant__ CUtensorMap map_F, float* __restrict__ f_out,
+                           float* __restrict__ C_out, int* __restrict__ flag, SplitOut so, int nz, int early) {
+  constexpr int D = 3, Q = 7;
+  extern __shared__ uint8_t cs_raw[];
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(cs_raw) + 127) & ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)TMA_STAGES * TMA_STAGE);
+  __shared__ float s_m[2][4][TY + 2][TX + 2];
+  const int n0 = sp.n[0], n1 = sp.n[1], n2 = sp.n[2];
+  const long long nodes = sp.nodes;
+  const long long plane = (long long)n0 * n1;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const int tid = wy * TX + lane;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int bz = blockIdx.z;
+  const int z0 = static_cast<int>((long long)bz * n2 / nz), z1 = static_cast<int>((long long)(bz + 1) * n2 / nz);
+  if (early) pdl_trigger();
+
+  int gx, gy, sx, sy;
+  const bool owner = wy < TY;
+  if (owner) {
+    gx = x0 + lane;
+    gy = y0 + wy;
+  } else if (wy == TY) {
+    gx = (lane < 16) ? x0 - 1 : x0 + TX;
+    gy = y0 + (lane & 15);
+  } else {
+    gx = x0 + lane;
+    gy = (wy == TY + 1) ? y0 - 1 : y0 + TY;
+  }
+  sx = gx - x0 + 1;
+  sy = gy - y0 + 1;
+  const int lx = gx - (x0 - 4), ly = gy - (y0 - 1);  // position in the staged window
+  const bool in_xy = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
+  const long long col = gx + (long long)n0 * gy;
+
+  // plane p lives in stage (p - z0 + 1) % 3; its k-th use of that stage completes phase k
+  auto stage_of = [&](int p) { return (p - z0 + 1) % TMA_STAGES; };
+  auto parity_of = [&](int p) { return static_cast<uint32_t>(((p - z0 + 1) / TMA_STAGES) & 1); };
+  auto issue = [&](int p) {
+    const int s = stage_of(p);
+    uint8_t* st = ring + (size_t)s * TMA_STAGE;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cs_smem_u32(&full[s])),
+                 "r"(TMA_TX)
+                 : "memory");
+    cs_tma_4d(st, &map_f, x0 - 4, y0 - 1, p, 0, &full[s]);
+    cs_tma_4d(st + TMA_FF_OFF, &map_F, x0 - 4, y0 - 1, p, 0, &full[s]);
+  };
+  auto collide_staged = [&](int p, float* fs) {
+    cs_mbar_wait(&full[stage_of(p)], parity_of(p), flag);
+    const float* st = reinterpret_cast<const float*>(ring + (size_t)stage_of(p) * TMA_STAGE);
+    float fv[Q], Fv[D];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fv[q] = st[(q * TH + ly) * TW + lx];
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) Fv[mu] = st[TMA_FF_OFF / 4 + (mu * TH + ly) * TW + lx];
+    collide_node<float, D, MRT>(sp, fv, Fv, fs);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < TMA_STAGES; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cs_smem_u32(&full[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // programmatic dependent launch: f and F come from the previous kernels
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (tid == 0) {
+    issue(z0 - 1);
+    issue(z0);
+    issue(z0 + 1);  // z0 + 1 <= z1: needed by the owners' first iteration
+  }
+  bool bad = false;
+  float cur[Q], nxt[Q];
+  float prev5 = 0.f;
+  if (owner) {
+    float t[Q];
+    collide_staged(z0 - 1, t);
+    prev5 = t[5];
+    collide_staged(z0, cur);
+  }
+  __syncthreads();  // plane z0 - 1 is read: its stage takes plane z0 + 2
+  if (tid == 0 && z0 + 2 <= z1) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(z0 + 2);
+  }
+  int buf = 0;
+  for (int z = z0; z < z1; ++z) {
+    if (owner) {
+      collide_staged(z + 1, nxt);
+      s_m[buf][0][sy][sx] = cur[1];
+      s_m[buf][1][sy][sx] = cur[2];
+      s_m[buf][2][sy][sx] = cur[3];
+      s_m[buf][3][sy][sx] = cur[4];
+    } else {
+      float h[Q];
+      collide_staged(z, h);
+      if (wy == TY) {
+        if (lane < 16) s_m[buf][0][sy][sx] = h[1];  // moves +x into the tile
+        else s_m[buf][1][sy][sx] = h[2];            // moves -x into the tile
+      } else if (wy == TY + 1) {
+        s_m[buf][2][sy][sx] = h[3];                 // moves +y into the tile
+      } else {
+        s_m[buf][3][sy][sx] = h[4];                 // moves -y into the tile
+      }
+    }
+    __syncthreads();
+    // plane z is read by everyone: its stage takes plane z + 3
+    if (tid == 0 && z + 3 <= z1) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(z + 3);
+    }
+    if (owner && in_xy) {
+      float fv[Q];
+      bool known[Q];
+      fv[0] = cur[0];
+      known[0] = true;
+      known[1] = gx > 0;
+      known[2] = gx + 1 < n0;
+      known[3] = gy > 0;
+      known[4] = gy + 1 < n1;
+      known[5] = z > 0;
+      known[6] = z + 1 < n2;
+      fv[1] = s_m[buf][0][sy][sx - 1];
+      fv[2] = s_m[buf][1][sy][sx + 1];
+      fv[3] = s_m[buf][2][sy - 1][sx];
+      fv[4] = s_m[buf][3][sy + 1][sx];
+      fv[5] = prev5;
+      fv[6] = nxt[6];
+      float sum_known = 0.f;
+      int n_unknown = 0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (known[q]) {
+          sum_known += fv[q];
+        } else {
+          fv[q] = 0.f;
+          ++n_unknown;
+        }
+      }
+      float C = sum_known;
+      if (n_unknown > 0) {
+        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
+        const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (!known[q]) fv[q] = fill;
+        C = fv[0];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) C += fv[q];
+      }
+      const long long node = col + z * plane;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
+      C_out[node] = C;
+      if (SPLIT) write_split<SPLIT>(so, ((long long)z * n1 + gy) * so.ldp + gx, C);
+      bad |= !isfinite(C);
+    }
+    if (owner) {
+      prev5 = cur[5];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
+    }
+    buf ^= 1;
+  }
+  // every issued plane (up to z1) was waited for by the owners; after a timeout make sure
+  // no copy is still in flight into this block's shared memory before it exits
+  if (tid == 0)
+    for (int p = (z1 - 2 > z0 - 1 ? z1 - 2 : z0 - 1); p <= z1; ++p) cs_mbar_wait(&full[stage_of(p)], parity_of(p), flag);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
+  if (!early) pdl_trigger();
+}
+
 // Grouped form for a batch of independent problems: one launch covers every block of
 // every problem; block_start[p] is the first block of problem p (ascending).  The
 // problem's constants are staged in shared memory.
@@ -534,6 +774,20 @@ __global__ void moment_kernel(long long nodes, const real* __restrict__ f, real*
   }
 }
 
+template <bool MRT, int SPLIT>
+cudaError_t launch_tma3(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, const CUtensorMap& mf,
+                        const CUtensorMap& mF, float* fo, float* Co, int* flag, const SplitOut& so, int nz,
+                        int early) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(collide_stream_tma3_kernel<MRT, SPLIT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return cudaLaunchKernelEx(&cfg, collide_stream_tma3_kernel<MRT, SPLIT>, sp, mf, mF, fo, Co, flag, so, nz, early);
+}
+
 // at most two blocks per SM resident: the grid runs in one wave
 bool one_wave(const dim3& g) { return (long long)g.x * g.y * g.z <= 2 * 152; }
 
@@ -586,11 +840,9 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
   const real* F = static_cast<const real*>(h->dev.F);
   real* fo = static_cast<real*>(f_out);
   real* Co = static_cast<real*>(C_out);
+  int* flag = h->dev.flag;
   const int bx = (sp.n[0] + TX - 1) / TX, by = (sp.n[1] + TY - 1) / TY;
   cudaLaunchConfig_t cfg = {};
-  const int nz = z_chunks((long long)bx * by, sp.n[2]);
-  cfg.gridDim = dim3(bx, by, nz);
-  const int early = one_wave(cfg.gridDim) ? 1 : 0;
   cfg.blockDim = dim3(TX, TY + HALO_WARPS);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -598,7 +850,6 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
   at[0].val.programmaticStreamSerializationAllowed = h->pdl ? 1 : 0;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  int* flag = h->dev.flag;
   if constexpr (D == 2 && sizeof(real) == 4) {
     // tile rows per block: about one wave of two blocks per SM
     const int ychunk = ychunk_for((long long)bx * by, by);
@@ -609,6 +860,20 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
     if (split == 1) return launch_march2<MRT, 1>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
     return launch_march2<MRT, 2>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
   }
+  const int nz = z_chunks((long long)bx * by, sp.n[2]);
+  cfg.gridDim = dim3(bx, by, nz);
+  const int early = one_wave(cfg.gridDim) ? 1 : 0;
+  if constexpr (D == 3 && sizeof(real) == 4) {
+    if (h->cs_plan) {
+      // TMA-fed march: the map of whichever population buffer is the input
+      const CsPlan* pl = static_cast<const CsPlan*>(h->cs_plan);
+      const CUtensorMap& mf = pl->f[f_in == h->dev.f[0] ? 0 : 1];
+      cfg.dynamicSmemBytes = TMA_SMEM;
+      if (split == 0) return launch_tma3<MRT, 0>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early);
+      if (split == 1) return launch_tma3<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early);
+      return launch_tma3<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early);
+    }
+  }
   if (split == 0)
     return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 0>, sp, fi, F, fo, Co, flag, so, nz,
                               early);
@@ -616,7 +881,7 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
     return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 1>, sp, fi, F, fo, Co, flag, so, nz,
                               early);
   return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 2>, sp, fi, F, fo, Co, flag, so, nz,
-                              early);
+                            early);
 }
 
 int grid_for(long long n) {
@@ -642,6 +907,33 @@ cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out,
 }
 
 constexpr int kBatchYChunk = 8;
+
+int cs_prepare(lbm_s* h) {
+  if (h->d != 3 || h->elem != 4 || h->sp.n[0] % 4 != 0) return LBM_OK;
+  CsPlan* pl = new (std::nothrow) CsPlan();
+  if (!pl) return LBM_ENOMEM;
+  const unsigned long long n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
+  const unsigned long long nodes = h->sp.nodes;
+  const unsigned long long strides[3] = {n0 * 4, n0 * n1 * 4, nodes * 4};
+  const unsigned long long df[4] = {n0, n1, n2, 7};
+  const unsigned long long dF[4] = {n0, n1, n2, 3};
+  const unsigned int bf[4] = {TW, TH, 1, 7};
+  const unsigned int bF[4] = {TW, TH, 1, 3};
+  bool ok = encode_f32_map(&pl->f[0], 4, h->dev.f[0], df, strides, bf) &&
+            encode_f32_map(&pl->f[1], 4, h->dev.f[1], df, strides, bf) &&
+            encode_f32_map(&pl->F, 4, h->dev.F, dF, strides, bF);
+  if (!ok) {
+    delete pl;
+    return LBM_OK;  // the plain march serves the handle
+  }
+  h->cs_plan = pl;
+  return LBM_OK;
+}
+
+void cs_release(lbm_s* h) {
+  delete static_cast<CsPlan*>(h->cs_plan);
+  h->cs_plan = nullptr;
+}
 
 bool cs_one_wave(const lbm_s* h) {
   const int bx = (h->sp.n[0] + TX - 1) / TX, by = (h->sp.n[1] + TY - 1) / TY;

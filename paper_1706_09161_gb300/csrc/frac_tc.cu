@@ -1218,6 +1218,25 @@ cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s) {
 
 int tc_split_pitch(const lbm_s* h) { return h->tc ? h->tc->ldp : 0; }
 
+bool encode_f32_map(void* map, int rank, void* base, const unsigned long long* dims,
+                    const unsigned long long* strides_bytes, const unsigned int* box) {
+  EncodeTiled enc = get_encoder();
+  if (!enc || rank < 1 || rank > 5) return false;
+  cuuint64_t d[5];
+  cuuint64_t st[4];
+  cuuint32_t b[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    es[i] = 1;
+    if (i + 1 < rank) st[i] = strides_bytes[i];
+  }
+  const CUresult r = enc(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, d, st, b, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool tc_one_wave(const lbm_s* h) {
   const TcPlan* p = h->tc;
   return p && (p->persist || (long long)p->prm.total_tiles * p->prm.ksplit <= kPersistCTAs);

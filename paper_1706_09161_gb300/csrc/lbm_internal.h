@@ -64,6 +64,7 @@ struct lbm_s {
   bool pdl = false;
   int device = 0;
   lbm::TcPlan* tc = nullptr;           // split-precision tensor-core operator, if used
+  void* cs_plan = nullptr;             // TMA-fed 3-D collide-stream (tensor maps), if used
   // batch of independent problems: one sub-handle per problem (each owns its buffers)
   std::vector<lbm_s*> subs;
   void* batch_tc_maps = nullptr;       // device table of per-problem tensor maps
@@ -109,6 +110,13 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
 int tc_batch_prepare(lbm_s* b);
 cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s);
 int cs_batch_prepare(lbm_s* b);
+// TMA-fed 3-D collide-stream: tensor maps of the population and fractional-term buffers
+// (FP32 forms with n0 % 4 == 0); no-op otherwise.  cs_release frees them.
+int cs_prepare(lbm_s* h);
+void cs_release(lbm_s* h);
+// tensor map of an FP32 array (no swizzle, zero fill out of bounds); false on failure
+bool encode_f32_map(void* map, int rank, void* base, const unsigned long long* dims,
+                    const unsigned long long* strides_bytes, const unsigned int* box);
 bool cs_one_wave(const lbm_s* h);  // the collide-stream grid fits in one wave
 bool tc_one_wave(const lbm_s* h);  // the tensor-core operator grid fits in one wave
 void tc_set_pdl(lbm_s* h, bool on);

@@ -53,7 +53,9 @@ def oracle_run(pb, C0, n):
 
 
 GRIDS_2D = [(3, 3), (37, 29), (70, 65), (129, 17)]
-GRIDS_3D = [(3, 3, 3), (19, 13, 11), (40, 9, 6)]
+# (40, 9, 6) and (44, 21, 37) have n0 % 4 == 0: the FP32 form runs the TMA-fed march
+# (ragged x and y tiles, several z chunks for the latter)
+GRIDS_3D = [(3, 3, 3), (19, 13, 11), (40, 9, 6), (44, 21, 37)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -67,7 +67,7 @@ def test_tc_fractional_terms(L, kind, grid):
 
 
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("grid", [(37, 29), (130, 70), (19, 13, 11), (130, 129, 70)])
+@pytest.mark.parametrize("grid", [(37, 29), (130, 70), (19, 13, 11), (130, 129, 70), (44, 21, 37)])
 @pytest.mark.parametrize("collision", ["bgk", "mrt"])
 def test_tc_steps_match_oracle(L, kind, grid, collision):
     rng = np.random.default_rng(53 + grid[0])
