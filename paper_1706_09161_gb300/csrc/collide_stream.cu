@@ -106,13 +106,16 @@ struct SplitOut {
 
 // Per-problem entry of a grouped (batched) collide-stream launch.
 struct BatchCS {
+  CUtensorMap mf[2];  // 2-D members with n0 % 4 == 0: population windows (see march2_tma)
+  CUtensorMap mF;     //   and fractional-term windows
   KConst<float> k;
   const float* f[2];  // population buffers; the launch's parity picks input and output
   const float* F;
   float* C;
   SplitOut so;
   int* flag;
-  int bx, by, zchunk;  // blocks in x, y and the z chunk length
+  int bx, by, zchunk;  // blocks in x, y and the z chunk length (2-D: tile rows per block)
+  int tma;             // the maps above are valid
 };
 
 template <int SPLIT, typename real>
@@ -310,6 +313,10 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
 }
 
+// movers of the current tile plus ring for the 2-D FP32 marches: [buffer][mover 1..4][y+1][x+1]
+// (one array per kernel, whichever 2-D march it runs)
+__shared__ float s_m2[2][4][TY + 2][TX + 2];
+
 // 2-D FP32: the block walks `ychunk` consecutive 32 x 16 tiles up the y axis (tile
 // rows tr0 .. tr0 + ychunk - 1 of column bx), each thread prefetching its node of the
 // next two tiles through the cp.async ring while the current tile is collided.  The
@@ -320,7 +327,7 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
                                             float* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
                                             int ychunk, int bx, int byc, float* stage) {
   constexpr int D = 2, Q = 5;
-  __shared__ float s_m[2][4][TY + 2][TX + 2];
+  auto& s_m = s_m2;
   const int n0 = sp.n[0], n1 = sp.n[1];
   const long long nodes = sp.nodes;
   const int lane = threadIdx.x, wy = threadIdx.y;
@@ -704,6 +711,176 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
   if (!early) pdl_trigger();
 }
 
+// ---------------------------------------------------------------------------- TMA-fed 2-D march
+// FP32 forms with n0 % 4 == 0: the block walks `ychunk` tiles up y; per tile one thread
+// loads the 40 x 18 window of the 5 populations and the 2 fractional terms with two 3-D
+// TMA box loads into a 3-stage ring, two tiles ahead.  Otherwise as march2_pipe.
+constexpr uint32_t TMA2_F_BYTES = 5u * TH * TW * 4;
+constexpr uint32_t TMA2_FF_BYTES = 2u * TH * TW * 4;
+constexpr uint32_t TMA2_TX = TMA2_F_BYTES + TMA2_FF_BYTES;
+constexpr uint32_t TMA2_FF_OFF = (TMA2_F_BYTES + 127) / 128 * 128;
+constexpr uint32_t TMA2_STAGE = (TMA2_FF_OFF + TMA2_FF_BYTES + 127) / 128 * 128;
+constexpr size_t TMA2_SMEM = (size_t)TMA_STAGES * TMA2_STAGE + 128 /*align*/ + 64 /*barriers*/;
+
+__device__ __forceinline__ void cs_tma_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(cs_smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(cs_smem_u32(bar))
+      : "memory");
+}
+
+template <bool MRT, int SPLIT>
+__device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtensorMap* map_f,
+                                           const CUtensorMap* map_F, float* __restrict__ f_out,
+                                           float* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
+                                           int ychunk, int bx, int byc, uint8_t* raw) {
+  constexpr int D = 2, Q = 5;
+  auto& s_m = s_m2;
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)TMA_STAGES * TMA2_STAGE);
+  const int n0 = sp.n[0], n1 = sp.n[1];
+  const long long nodes = sp.nodes;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const int tid = wy * TX + lane;
+  const int x0 = bx * TX;
+  const int tr0 = byc * ychunk;
+  const int tr1 = min(tr0 + ychunk, (n1 + TY - 1) / TY);
+  const bool owner = wy < TY;
+  int dx, dy;
+  if (owner) {
+    dx = lane;
+    dy = wy;
+  } else if (wy == TY) {
+    dx = (lane < 16) ? -1 : TX;
+    dy = lane & 15;
+  } else {
+    dx = lane;
+    dy = (wy == TY + 1) ? -1 : TY;
+  }
+  const int gx = x0 + dx;
+  const int sx = dx + 1, sy = dy + 1;
+  const int lx = dx + 4, ly = dy + 1;  // position in the staged window
+  const bool in_x = gx >= 0 && gx < n0;
+  auto stage_of = [&](int t) { return (t - tr0) % TMA_STAGES; };
+  auto parity_of = [&](int t) { return static_cast<uint32_t>(((t - tr0) / TMA_STAGES) & 1); };
+  auto issue = [&](int t) {
+    const int s = stage_of(t);
+    uint8_t* st = ring + (size_t)s * TMA2_STAGE;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cs_smem_u32(&full[s])),
+                 "r"(TMA2_TX)
+                 : "memory");
+    cs_tma_3d(st, map_f, x0 - 4, t * TY - 1, 0, &full[s]);
+    cs_tma_3d(st + TMA2_FF_OFF, map_F, x0 - 4, t * TY - 1, 0, &full[s]);
+  };
+  if (tid == 0) {
+    for (int s = 0; s < TMA_STAGES; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cs_smem_u32(&full[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // f and F come from the previous kernels
+  if (tid == 0)
+    for (int t = tr0; t < tr1 && t < tr0 + TMA_STAGES; ++t) issue(t);
+  bool bad = false;
+  int buf = 0;
+  for (int tr = tr0; tr < tr1; ++tr) {
+    cs_mbar_wait(&full[stage_of(tr)], parity_of(tr), flag);
+    const float* st = reinterpret_cast<const float*>(ring + (size_t)stage_of(tr) * TMA2_STAGE);
+    float fs[Q];
+    {
+      float fv[Q], Fv[D];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) fv[q] = st[(q * TH + ly) * TW + lx];
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) Fv[mu] = st[TMA2_FF_OFF / 4 + (mu * TH + ly) * TW + lx];
+      collide_node<float, D, MRT>(sp, fv, Fv, fs);
+    }
+    if (owner) {
+      s_m[buf][0][sy][sx] = fs[1];
+      s_m[buf][1][sy][sx] = fs[2];
+      s_m[buf][2][sy][sx] = fs[3];
+      s_m[buf][3][sy][sx] = fs[4];
+    } else if (wy == TY) {
+      if (lane < 16) s_m[buf][0][sy][sx] = fs[1];  // moves +x into the tile
+      else s_m[buf][1][sy][sx] = fs[2];            // moves -x into the tile
+    } else if (wy == TY + 1) {
+      s_m[buf][2][sy][sx] = fs[3];                 // moves +y into the tile
+    } else {
+      s_m[buf][3][sy][sx] = fs[4];                 // moves -y into the tile
+    }
+    __syncthreads();
+    // tile row tr is read by everyone: its stage takes tile row tr + 3
+    if (tid == 0 && tr + TMA_STAGES < tr1) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(tr + TMA_STAGES);
+    }
+    const int gy = tr * TY + dy;
+    if (owner && in_x && gy < n1) {
+      float fv[Q];
+      bool known[Q];
+      fv[0] = fs[0];
+      known[0] = true;
+      known[1] = gx > 0;
+      known[2] = gx + 1 < n0;
+      known[3] = gy > 0;
+      known[4] = gy + 1 < n1;
+      fv[1] = s_m[buf][0][sy][sx - 1];
+      fv[2] = s_m[buf][1][sy][sx + 1];
+      fv[3] = s_m[buf][2][sy - 1][sx];
+      fv[4] = s_m[buf][3][sy + 1][sx];
+      float sum_known = 0.f;
+      int n_unknown = 0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (known[q]) {
+          sum_known += fv[q];
+        } else {
+          fv[q] = 0.f;
+          ++n_unknown;
+        }
+      }
+      float C = sum_known;
+      if (n_unknown > 0) {
+        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
+        const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (!known[q]) fv[q] = fill;
+        C = fv[0];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) C += fv[q];
+      }
+      const long long node = gx + (long long)n0 * gy;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
+      C_out[node] = C;
+      if (SPLIT) write_split<SPLIT>(so, (long long)gy * so.ldp + gx, C);
+      bad |= !isfinite(C);
+    }
+    buf ^= 1;
+  }
+  // after a timeout no copy may still be landing in this block's shared memory
+  if (tid == 0)
+    for (int t = (tr1 - TMA_STAGES > tr0 ? tr1 - TMA_STAGES : tr0); t < tr1; ++t)
+      cs_mbar_wait(&full[stage_of(t)], parity_of(t), flag);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
+}
+
+template <bool MRT, int SPLIT>
+__global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
+collide_stream_tma2_kernel(const KConst<float> sp, const __grid_constant__ CUtensorMap map_f,
+                           const __grid_constant__ CUtensorMap map_F, float* __restrict__ f_out,
+                           float* __restrict__ C_out, int* __restrict__ flag, SplitOut so, int ychunk, int early) {
+  extern __shared__ uint8_t cs_raw2[];
+  if (early) pdl_trigger();
+  march2_tma<MRT, SPLIT>(sp, &map_f, &map_F, f_out, C_out, flag, so, ychunk, blockIdx.x, blockIdx.y, cs_raw2);
+  if (!early) pdl_trigger();
+}
+
+// 2-D batch blocks run either march (per problem): room for the larger ring
+constexpr int BATCH2_SMEM = (int)(TMA2_SMEM > (size_t)PIPE_SMEM ? TMA2_SMEM : (size_t)PIPE_SMEM);
+
 // Grouped form for a batch of independent problems: one launch covers every block of
 // every problem; block_start[p] is the first block of problem p (ascending).  The
 // problem's constants are staged in shared memory.
@@ -728,9 +905,13 @@ collide_stream_batch_kernel(const BatchCS* __restrict__ tab, const int* __restri
   const int lb = b - __ldg(&block_start[lo]);
   const int bx = lb % e.bx, rest = lb / e.bx;
   if constexpr (D == 2) {
-    extern __shared__ __align__(16) float pipe_stage[];
-    march2_pipe<MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so, e.zchunk,
-                            bx, rest, pipe_stage);
+    extern __shared__ __align__(128) uint8_t batch_raw[];
+    if (e.tma)
+      march2_tma<MRT, SPLIT>(s_k, &e.mf[parity], &e.mF, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
+                             e.zchunk, bx, rest, batch_raw);
+    else
+      march2_pipe<MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
+                              e.zchunk, bx, rest, reinterpret_cast<float*>(batch_raw));
   } else {
     march_body<float, D, MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
                                      bx, rest, 0, e.k.n[2]);
@@ -786,6 +967,21 @@ cudaError_t launch_tma3(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, 
     attr = true;
   }
   return cudaLaunchKernelEx(&cfg, collide_stream_tma3_kernel<MRT, SPLIT>, sp, mf, mF, fo, Co, flag, so, nz, early);
+}
+
+template <bool MRT, int SPLIT>
+cudaError_t launch_tma2(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, const CUtensorMap& mf,
+                        const CUtensorMap& mF, float* fo, float* Co, int* flag, const SplitOut& so, int ychunk,
+                        int early) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(collide_stream_tma2_kernel<MRT, SPLIT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA2_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return cudaLaunchKernelEx(&cfg, collide_stream_tma2_kernel<MRT, SPLIT>, sp, mf, mF, fo, Co, flag, so, ychunk,
+                            early);
 }
 
 // at most two blocks per SM resident: the grid runs in one wave
@@ -854,8 +1050,16 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
     // tile rows per block: about one wave of two blocks per SM
     const int ychunk = ychunk_for((long long)bx * by, by);
     cfg.gridDim = dim3(bx, (by + ychunk - 1) / ychunk, 1);
-    cfg.dynamicSmemBytes = PIPE_SMEM;
     const int early = one_wave(cfg.gridDim) ? 1 : 0;
+    if (h->cs_plan) {
+      const CsPlan* pl = static_cast<const CsPlan*>(h->cs_plan);
+      const CUtensorMap& mf = pl->f[f_in == h->dev.f[0] ? 0 : 1];
+      cfg.dynamicSmemBytes = TMA2_SMEM;
+      if (split == 0) return launch_tma2<MRT, 0>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
+      if (split == 1) return launch_tma2<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
+      return launch_tma2<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
+    }
+    cfg.dynamicSmemBytes = PIPE_SMEM;
     if (split == 0) return launch_march2<MRT, 0>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
     if (split == 1) return launch_march2<MRT, 1>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
     return launch_march2<MRT, 2>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
@@ -908,10 +1112,29 @@ cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out,
 
 constexpr int kBatchYChunk = 8;
 
+// window maps of a 2-D handle: populations (n0, n1, 5) and fractional terms (n0, n1, 2)
+bool encode_2d_maps(const lbm_s* h, CUtensorMap* mf, CUtensorMap* mF) {
+  const unsigned long long n0 = h->sp.n[0], n1 = h->sp.n[1];
+  const unsigned long long nodes = h->sp.nodes;
+  const unsigned long long strides[2] = {n0 * 4, nodes * 4};
+  const unsigned long long df[3] = {n0, n1, 5};
+  const unsigned long long dF[3] = {n0, n1, 2};
+  const unsigned int bf[3] = {TW, TH, 5};
+  const unsigned int bF[3] = {TW, TH, 2};
+  return encode_f32_map(&mf[0], 3, h->dev.f[0], df, strides, bf) &&
+         encode_f32_map(&mf[1], 3, h->dev.f[1], df, strides, bf) &&
+         encode_f32_map(mF, 3, h->dev.F, dF, strides, bF);
+}
+
 int cs_prepare(lbm_s* h) {
-  if (h->d != 3 || h->elem != 4 || h->sp.n[0] % 4 != 0) return LBM_OK;
+  if (h->elem != 4 || h->sp.n[0] % 4 != 0) return LBM_OK;
   CsPlan* pl = new (std::nothrow) CsPlan();
   if (!pl) return LBM_ENOMEM;
+  if (h->d == 2) {
+    if (encode_2d_maps(h, pl->f, &pl->F)) h->cs_plan = pl;
+    else delete pl;  // the cp.async march serves the handle
+    return LBM_OK;
+  }
   const unsigned long long n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
   const unsigned long long nodes = h->sp.nodes;
   const unsigned long long strides[3] = {n0 * 4, n0 * n1 * 4, nodes * 4};
@@ -960,6 +1183,7 @@ int cs_batch_prepare(lbm_s* b) {
     e.C = static_cast<float*>(h->dev.C);
     e.so = SplitOut{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
     e.flag = h->dev.flag;
+    e.tma = (h->d == 2 && h->sp.n[0] % 4 == 0 && encode_2d_maps(h, e.mf, &e.mF)) ? 1 : 0;
     e.bx = (h->sp.n[0] + TX - 1) / TX;
     e.by = (h->sp.n[1] + TY - 1) / TY;
     // 2-D: tile rows per block (the pipelined y-march); 3-D: the whole z extent
@@ -984,15 +1208,15 @@ cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t
   const int P = static_cast<int>(b->subs.size());
   dim3 block(TX, TY + HALO_WARPS);
   const int g = b->batch_cs_blocks;
-  const int smem = (h0->d == 2) ? PIPE_SMEM : 0;
+  const int smem = (h0->d == 2) ? BATCH2_SMEM : 0;
   if (h0->d == 2) {
     static bool attr[2][2] = {{false, false}, {false, false}};
     if (!attr[mrt][split]) {
       cudaError_t e;
-      if (mrt) e = split ? cudaFuncSetAttribute(collide_stream_batch_kernel<2, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM)
-                         : cudaFuncSetAttribute(collide_stream_batch_kernel<2, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM);
-      else e = split ? cudaFuncSetAttribute(collide_stream_batch_kernel<2, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM)
-                     : cudaFuncSetAttribute(collide_stream_batch_kernel<2, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM);
+      if (mrt) e = split ? cudaFuncSetAttribute(collide_stream_batch_kernel<2, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, BATCH2_SMEM)
+                         : cudaFuncSetAttribute(collide_stream_batch_kernel<2, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, BATCH2_SMEM);
+      else e = split ? cudaFuncSetAttribute(collide_stream_batch_kernel<2, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, BATCH2_SMEM)
+                     : cudaFuncSetAttribute(collide_stream_batch_kernel<2, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, BATCH2_SMEM);
       if (e != cudaSuccess) return e;
       attr[mrt][split] = true;
     }
