@@ -117,6 +117,8 @@ int derive(const lbm_params* p, Derived* out) {
   sp.wi = (d == 2) ? 1.0 / 6.0 : 1.0 / 8.0;
   for (int mu = 0; mu < 3; ++mu) sp.adv[mu] = (mu < d) ? (p->dt / p->dx) * p->u[mu] / e2 : 0.0;
   sp.C_wall = p->C_wall;
+  sp.ksum = 1;
+  sp.pstride = 0;
   const double ratio = p->dt / (p->dx * p->dx);
   double Dm[9];
   for (int i = 0; i < d; ++i)
@@ -604,8 +606,12 @@ int lbm_read_F(lbm_t h, int mu, double* F_host) {
   const long long nodes = h->sp.nodes;
   int rc = run_frac(h, h->stream);
   if (rc) return rc;
-  LBM_CUDA(lbm::launch_convert_out((char*)h->dev.F + (size_t)mu * nodes * h->elem, h->elem, h->dev.stage, nodes,
-                                   h->stream));
+  if (h->sp.ksum > 1)  // split-K partial sums of the tensor-core operator (FP32 forms)
+    LBM_CUDA(lbm::launch_sum_partials_out(static_cast<const float*>(h->dev.F) + (size_t)mu * nodes, h->sp.ksum,
+                                          h->sp.pstride, h->dev.stage, nodes, h->stream));
+  else
+    LBM_CUDA(lbm::launch_convert_out((char*)h->dev.F + (size_t)mu * nodes * h->elem, h->elem, h->dev.stage, nodes,
+                                     h->stream));
   LBM_CUDA(cudaMemcpyAsync(F_host, h->dev.stage, sizeof(double) * nodes, cudaMemcpyDeviceToHost, h->stream));
   return latched(h);
 }

@@ -37,6 +37,8 @@ struct KConst {
   real w0, wi;
   real advw[3];  // (dt/dx) u_mu w_i / e^2
   real C_wall;
+  int ksum;           // F holds ksum partial sums (split-K operator), added in order
+  long long pstride;  // elements between partial sums
 };
 
 template <typename real>
@@ -50,7 +52,18 @@ KConst<real> make_const(const StepParams& sp) {
   k.wi = static_cast<real>(sp.wi);
   for (int i = 0; i < 3; ++i) k.advw[i] = static_cast<real>(sp.adv[i] * sp.wi);
   k.C_wall = static_cast<real>(sp.C_wall);
+  k.ksum = sp.ksum;
+  k.pstride = sp.pstride;
   return k;
+}
+
+// F_mu at `node`: the sum of the operator's ksum partial sums, in order
+template <typename real>
+__device__ __forceinline__ real frac_term(const KConst<real>& sp, const real* __restrict__ F, int mu, long long node) {
+  const real* p = F + (long long)mu * sp.nodes + node;
+  real acc = p[0];
+  for (int s = 1; s < sp.ksum; ++s) acc += p[s * sp.pstride];
+  return acc;
 }
 
 // Equilibrium and collision of one node.  f: populations (in), fs: post-collision (out).
@@ -155,7 +168,7 @@ __device__ __forceinline__ void collide_at(const KConst<real>& sp, const real* _
 #pragma unroll
   for (int q = 0; q < Q; ++q) f[q] = f_in[q * nodes + node];
 #pragma unroll
-  for (int mu = 0; mu < D; ++mu) Fv[mu] = F[mu * nodes + node];
+  for (int mu = 0; mu < D; ++mu) Fv[mu] = frac_term(sp, F, mu, node);
   collide_node<real, D, MRT>(sp, f, Fv, fs);
 }
 
@@ -358,8 +371,10 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
       float* st = stage + (size_t)slot * PIPE_VALS * NT + tid;
 #pragma unroll
       for (int q = 0; q < Q; ++q) cp_async4(st + q * NT, f_in + q * nodes + node);
+      if (sp.ksum == 1) {
 #pragma unroll
-      for (int mu = 0; mu < D; ++mu) cp_async4(st + (Q + mu) * NT, F + mu * nodes + node);
+        for (int mu = 0; mu < D; ++mu) cp_async4(st + (Q + mu) * NT, F + mu * nodes + node);
+      }
     }
     cp_async_commit();
   };
@@ -379,8 +394,13 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
       float fv[Q], Fv[D];
 #pragma unroll
       for (int q = 0; q < Q; ++q) fv[q] = st[q * NT];
+      if (sp.ksum == 1) {
 #pragma unroll
-      for (int mu = 0; mu < D; ++mu) Fv[mu] = st[(Q + mu) * NT];
+        for (int mu = 0; mu < D; ++mu) Fv[mu] = st[(Q + mu) * NT];
+      } else {  // split-K partials: summed here, in order
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) Fv[mu] = frac_term(sp, F, mu, gx + (long long)n0 * gy);
+      }
       collide_node<float, D, MRT>(sp, fv, Fv, fs);
     } else {
 #pragma unroll
@@ -721,6 +741,16 @@ constexpr uint32_t TMA2_TX = TMA2_F_BYTES + TMA2_FF_BYTES;
 constexpr uint32_t TMA2_FF_OFF = (TMA2_F_BYTES + 127) / 128 * 128;
 constexpr uint32_t TMA2_STAGE = (TMA2_FF_OFF + TMA2_FF_BYTES + 127) / 128 * 128;
 constexpr size_t TMA2_SMEM = (size_t)TMA_STAGES * TMA2_STAGE + 128 /*align*/ + 64 /*barriers*/;
+// with ks split-K partial sums the fractional-term window holds 2 ks planes; two stages
+// then (the ring must leave room for two blocks per SM up to ks = 4)
+__host__ __device__ constexpr uint32_t tma2_ff_bytes(int ks) { return 2u * ks * TH * TW * 4; }
+__host__ __device__ constexpr uint32_t tma2_stage(int ks) {
+  return (TMA2_FF_OFF + tma2_ff_bytes(ks) + 127) / 128 * 128;
+}
+__host__ __device__ constexpr int tma2_nst(int ks) { return ks > 1 ? 2 : TMA_STAGES; }
+__host__ __device__ constexpr size_t tma2_smem(int ks) {
+  return (size_t)tma2_nst(ks) * tma2_stage(ks) + 128 /*align*/ + 64 /*barriers*/;
+}
 
 __device__ __forceinline__ void cs_tma_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
   asm volatile(
@@ -738,7 +768,11 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
   constexpr int D = 2, Q = 5;
   auto& s_m = s_m2;
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
-  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)TMA_STAGES * TMA2_STAGE);
+  const int ks = sp.ksum;
+  const int nst = tma2_nst(ks);
+  const uint32_t stg = tma2_stage(ks);
+  const uint32_t tx = TMA2_F_BYTES + tma2_ff_bytes(ks);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)nst * stg);
   const int n0 = sp.n[0], n1 = sp.n[1];
   const long long nodes = sp.nodes;
   const int lane = threadIdx.x, wy = threadIdx.y;
@@ -762,38 +796,42 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
   const int sx = dx + 1, sy = dy + 1;
   const int lx = dx + 4, ly = dy + 1;  // position in the staged window
   const bool in_x = gx >= 0 && gx < n0;
-  auto stage_of = [&](int t) { return (t - tr0) % TMA_STAGES; };
-  auto parity_of = [&](int t) { return static_cast<uint32_t>(((t - tr0) / TMA_STAGES) & 1); };
+  auto stage_of = [&](int t) { return (t - tr0) % nst; };
+  auto parity_of = [&](int t) { return static_cast<uint32_t>(((t - tr0) / nst) & 1); };
   auto issue = [&](int t) {
     const int s = stage_of(t);
-    uint8_t* st = ring + (size_t)s * TMA2_STAGE;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cs_smem_u32(&full[s])),
-                 "r"(TMA2_TX)
+    uint8_t* st = ring + (size_t)s * stg;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cs_smem_u32(&full[s])), "r"(tx)
                  : "memory");
     cs_tma_3d(st, map_f, x0 - 4, t * TY - 1, 0, &full[s]);
     cs_tma_3d(st + TMA2_FF_OFF, map_F, x0 - 4, t * TY - 1, 0, &full[s]);
   };
   if (tid == 0) {
-    for (int s = 0; s < TMA_STAGES; ++s)
+    for (int s = 0; s < nst; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cs_smem_u32(&full[s])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   asm volatile("griddepcontrol.wait;" ::: "memory");  // f and F come from the previous kernels
   if (tid == 0)
-    for (int t = tr0; t < tr1 && t < tr0 + TMA_STAGES; ++t) issue(t);
+    for (int t = tr0; t < tr1 && t < tr0 + nst; ++t) issue(t);
   bool bad = false;
   int buf = 0;
   for (int tr = tr0; tr < tr1; ++tr) {
     cs_mbar_wait(&full[stage_of(tr)], parity_of(tr), flag);
-    const float* st = reinterpret_cast<const float*>(ring + (size_t)stage_of(tr) * TMA2_STAGE);
+    const float* st = reinterpret_cast<const float*>(ring + (size_t)stage_of(tr) * stg);
     float fs[Q];
     {
       float fv[Q], Fv[D];
 #pragma unroll
       for (int q = 0; q < Q; ++q) fv[q] = st[(q * TH + ly) * TW + lx];
 #pragma unroll
-      for (int mu = 0; mu < D; ++mu) Fv[mu] = st[TMA2_FF_OFF / 4 + (mu * TH + ly) * TW + lx];
+      for (int mu = 0; mu < D; ++mu) {
+        // planes of the window: partial s of axis mu at plane s * D + mu, added in order of s
+        float acc = st[TMA2_FF_OFF / 4 + (mu * TH + ly) * TW + lx];
+        for (int k = 1; k < ks; ++k) acc += st[TMA2_FF_OFF / 4 + ((k * D + mu) * TH + ly) * TW + lx];
+        Fv[mu] = acc;
+      }
       collide_node<float, D, MRT>(sp, fv, Fv, fs);
     }
     if (owner) {
@@ -810,10 +848,10 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       s_m[buf][3][sy][sx] = fs[4];                 // moves -y into the tile
     }
     __syncthreads();
-    // tile row tr is read by everyone: its stage takes tile row tr + 3
-    if (tid == 0 && tr + TMA_STAGES < tr1) {
+    // tile row tr is read by everyone: its stage takes tile row tr + nst
+    if (tid == 0 && tr + nst < tr1) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(tr + TMA_STAGES);
+      issue(tr + nst);
     }
     const int gy = tr * TY + dy;
     if (owner && in_x && gy < n1) {
@@ -862,7 +900,7 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
   }
   // after a timeout no copy may still be landing in this block's shared memory
   if (tid == 0)
-    for (int t = (tr1 - TMA_STAGES > tr0 ? tr1 - TMA_STAGES : tr0); t < tr1; ++t)
+    for (int t = (tr1 - nst > tr0 ? tr1 - nst : tr0); t < tr1; ++t)
       cs_mbar_wait(&full[stage_of(t)], parity_of(t), flag);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
 }
@@ -930,7 +968,7 @@ __global__ void init_equilibrium_kernel(const KConst<real> sp, const real* __res
     real Fv[D];
 #pragma unroll
     for (int mu = 0; mu < D; ++mu) {
-      Fv[mu] = F[mu * nodes + i];
+      Fv[mu] = frac_term(sp, F, mu, i);
       sumF += Fv[mu];
     }
     f[i] = c - sp.w0 * sumF;
@@ -976,7 +1014,7 @@ cudaError_t launch_tma2(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, 
   static bool attr = false;
   if (!attr) {
     const cudaError_t e = cudaFuncSetAttribute(collide_stream_tma2_kernel<MRT, SPLIT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA2_SMEM);
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma2_smem(8));
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -1054,7 +1092,7 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
     if (h->cs_plan) {
       const CsPlan* pl = static_cast<const CsPlan*>(h->cs_plan);
       const CUtensorMap& mf = pl->f[f_in == h->dev.f[0] ? 0 : 1];
-      cfg.dynamicSmemBytes = TMA2_SMEM;
+      cfg.dynamicSmemBytes = tma2_smem(h->sp.ksum);
       if (split == 0) return launch_tma2<MRT, 0>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
       if (split == 1) return launch_tma2<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
       return launch_tma2<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
@@ -1117,10 +1155,11 @@ bool encode_2d_maps(const lbm_s* h, CUtensorMap* mf, CUtensorMap* mF) {
   const unsigned long long n0 = h->sp.n[0], n1 = h->sp.n[1];
   const unsigned long long nodes = h->sp.nodes;
   const unsigned long long strides[2] = {n0 * 4, nodes * 4};
+  const unsigned long long ks = (unsigned long long)h->sp.ksum;  // F: [partial][axis][node]
   const unsigned long long df[3] = {n0, n1, 5};
-  const unsigned long long dF[3] = {n0, n1, 2};
+  const unsigned long long dF[3] = {n0, n1, 2 * ks};
   const unsigned int bf[3] = {TW, TH, 5};
-  const unsigned int bF[3] = {TW, TH, 2};
+  const unsigned int bF[3] = {TW, TH, (unsigned int)(2 * ks)};
   return encode_f32_map(&mf[0], 3, h->dev.f[0], df, strides, bf) &&
          encode_f32_map(&mf[1], 3, h->dev.f[1], df, strides, bf) &&
          encode_f32_map(mF, 3, h->dev.F, dF, strides, bF);
@@ -1128,6 +1167,7 @@ bool encode_2d_maps(const lbm_s* h, CUtensorMap* mf, CUtensorMap* mF) {
 
 int cs_prepare(lbm_s* h) {
   if (h->elem != 4 || h->sp.n[0] % 4 != 0) return LBM_OK;
+  if (h->d == 3 && h->sp.ksum != 1) return LBM_OK;  // the plain 3-D march sums the partials
   CsPlan* pl = new (std::nothrow) CsPlan();
   if (!pl) return LBM_ENOMEM;
   if (h->d == 2) {

@@ -21,9 +21,10 @@
 // accumulator is allocated), warp 1 / lane 0 issues the MMAs and releases ring slots
 // with tcgen05.commit, then all four warps drain the accumulator (tcgen05.ld, one
 // lane quarter per warp) into a shared [BN][128] tile that one TMA store writes to F.
-// Small problems split the contraction over a cluster of ksplit CTAs per tile; each
-// rank finishes 1/ksplit of the tile's rows, summing the ranks' partial tiles through
-// distributed shared memory in rank order, so the result does not depend on timing.  Problems with many tiles use the persistent kernel further
+// Small problems split the contraction over ksplit independent CTAs per tile: CTA
+// `rank` contracts its k-range and stores its partial tile to slot `rank` of F, laid out
+// [rank][axis][node]; the kernels that read F add the ksplit partials in rank order, so
+// the result does not depend on timing (and no CTA waits for another).  Problems with many tiles use the persistent kernel further
 // down (two TMEM accumulators, epilogue overlapping the next tile).  Every mbarrier wait is
 // bounded by a 2 s %globaltimer budget; a wait that gives up sets bit 2 of the
 // handle's error flag and the CTA skips the rest of its work and releases TMEM.
@@ -54,7 +55,7 @@ struct TcParams {
   int n0, n1, n2;
   int naxes;
   int total_tiles;
-  int ksplit;     // CTAs (one cluster) per output tile, each contracting a k-range
+  int ksplit;     // CTAs per output tile, each contracting a k-range into its own partial
   int tma_store;  // F rows are 16-byte aligned (n0 % 4 == 0): store tiles with TMA
   int early_trigger;  // the per-tile grid fits in one wave: release dependents after the prologue
   long long nodes;
@@ -148,11 +149,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* f
   }
 }
 
-__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, int rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
-  return r;
-}
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint64_t* bar) {
@@ -245,7 +241,6 @@ struct Cfg {
   static constexpr uint32_t B_BYTES = BN * 128;
   static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr size_t RING = (size_t)STAGES * STAGE;
-  static constexpr int ROWS = BN / KS;  // KS > 1: tile rows each rank of the cluster finishes
   static constexpr size_t SMEM = RING + 1024 /*align*/ + 256 /*barriers*/;
   // A, MN-major: E boxes of (128/E) lines x BK rows
   static constexpr uint32_t A_BOX_MN = BK * 128;
@@ -371,8 +366,8 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
 
   const int warp = threadIdx.x >> 5;
 
-  // ---- which axis / tile / k-range: blocks of one tile form a cluster of ksplit CTAs,
-  // CTA `rank` of the cluster contracts k-blocks [kb0, kb1)
+  // ---- which axis / tile / k-range: ksplit CTAs share a tile; CTA `rank` contracts
+  // k-blocks [kb0, kb1)
   constexpr int ks = KS;
   const int cid = block / ks, rank = block % ks;
   const TileAt tl = decode_tile(P, cid, BN);
@@ -456,53 +451,11 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
 #pragma unroll
     for (int j = 0; j < 32; ++j) tile[(c0 + j) * BM + row] = have ? v[j] : 0.0f;
   }
-  if constexpr (KS > 1) {
-    // partial tiles of the cluster are complete; CTA `rank` sums rows
-    // [rank*BN/ks, (rank+1)*BN/ks) over ranks 0..ks-1 in that order (the sum does not
-    // depend on timing), reading the other ranks' tiles through distributed shared memory
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-    constexpr int ROWS = G::ROWS;
-    r0 = rank * ROWS;
-    r1 = r0 + ROWS;
-    const uint32_t tbase = smem_u32(tile);
-    constexpr int PER = ROWS * (BM / 4) / 128;  // float4 elements per thread
-    uint32_t offs[PER];
-    float4 acc[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int e = threadIdx.x + k * 128;
-      offs[k] = static_cast<uint32_t>(((r0 + e / (BM / 4)) * BM + (e % (BM / 4)) * 4) * 4);
-      acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int r = 0; r < KS; ++r) {
-      float4 b[PER];
-#pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const uint32_t raddr = cluster_addr(tbase + offs[k], r);
-        asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(b[k].x), "=f"(b[k].y), "=f"(b[k].z), "=f"(b[k].w)
-                     : "r"(raddr)
-                     : "memory");
-      }
-#pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        acc[k].x += b[k].x;
-        acc[k].y += b[k].y;
-        acc[k].z += b[k].z;
-        acc[k].w += b[k].w;
-      }
-    }
-    // rows r0..r1 of this tile are read by no other rank: sum them in place
-#pragma unroll
-    for (int k = 0; k < PER; ++k)
-      *reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(tile) + offs[k]) = acc[k];
-    tile += r0 * BM;
-  }
-  // `tile` now holds rows r0..r1-1 of the result from its start
+  // KS > 1: this CTA's partial sum over its k-range goes to partial slot `rank` of F
+  // (F is [rank][axis][node]); the consumers add the KS partials in rank order
 
   const long long nodes = P.nodes;
-  float* F = P.F + (long long)mu * nodes;
+  float* F = P.F + (long long)rank * P.naxes * nodes + (long long)mu * nodes;
   const int n0 = P.n0, n1 = P.n1;
   if (P.tma_store) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -516,11 +469,18 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
         c1 = ncol0 + r0;
         c2 = m_out;
       }
-      asm volatile(
-          "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-              reinterpret_cast<uint64_t>(&maps.f[mu])),
-          "r"(m_in), "r"(c1), "r"(c2), "r"(smem_u32(tile))
-          : "memory");
+      if (KS == 1)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                reinterpret_cast<uint64_t>(&maps.f[mu])),
+            "r"(m_in), "r"(c1), "r"(c2), "r"(smem_u32(tile))
+            : "memory");
+      else
+        asm volatile(
+            "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                reinterpret_cast<uint64_t>(&maps.f[mu])),
+            "r"(m_in), "r"(c1), "r"(c2), "r"(rank), "r"(smem_u32(tile))
+            : "memory");
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
@@ -537,10 +497,6 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
         F[idx] = tile[(rr - r0) * BM + row];
       }
     }
-  }
-  if (ks > 1) {
-    // no CTA leaves while another still reads its tile
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
@@ -934,20 +890,11 @@ cudaError_t launch_kernel(const TcPlan* p, cudaStream_t s) {
   cfg.blockDim = dim3(128, 1, 1);
   cfg.dynamicSmemBytes = Cfg<E, BN, KS>::SMEM;
   cfg.stream = s;
-  cudaLaunchAttribute at[2];
-  int na = 0;
-  at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[na].val.programmaticStreamSerializationAllowed = p->pdl ? 1 : 0;
-  ++na;
-  if (KS > 1) {
-    at[na].id = cudaLaunchAttributeClusterDimension;
-    at[na].val.clusterDim.x = KS;
-    at[na].val.clusterDim.y = 1;
-    at[na].val.clusterDim.z = 1;
-    ++na;
-  }
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = p->pdl ? 1 : 0;
   cfg.attrs = at;
-  cfg.numAttrs = na;
+  cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, frac_tc_kernel<E, BN, KS>, p->maps, p->prm);
 }
 
@@ -1145,16 +1092,28 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
     if (!encode(&p->maps.k_lo[mu], E, 2, static_cast<uint8_t*>(h->dev.Klo) + koff[mu] * E, kdims, kstr, kbox))
       return LBM_ECUDA;
   }
+  // split contraction: F holds one partial sum per rank, [rank][axis][node]; the
+  // kernels that read F add them in rank order
+  if (ks > 1) {
+    if (h->dev.F) cudaFree(h->dev.F);
+    h->dev.F = nullptr;
+    if (cudaMalloc(&h->dev.F, (size_t)ks * h->d * h->sp.nodes * 4) != cudaSuccess) return LBM_ENOMEM;
+    P.F = static_cast<float*>(h->dev.F);
+  }
+  h->sp.ksum = ks;
+  h->sp.pstride = (ks > 1) ? (long long)h->d * h->sp.nodes : 0;
   if (P.tma_store) {
     for (int mu = 0; mu < h->d; ++mu) {
-      const cuuint64_t fd[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
-      const cuuint64_t fs[2] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4};
-      const cuuint32_t rows = p->persist ? 32u : (cuuint32_t)(p->bn / ks);  // persistent: 32-row chunks
-      const cuuint32_t fb[3] = {BM, mu == 2 ? 1u : rows, mu == 2 ? rows : 1u};
-      const cuuint32_t es[3] = {1, 1, 1};
+      // persistent: 32-row chunks; per tile: the whole tile (one rank's partial when ks > 1)
+      const cuuint32_t rows = p->persist ? 32u : (cuuint32_t)p->bn;
+      const cuuint64_t fd[4] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2], (cuuint64_t)ks};
+      const cuuint64_t fs[3] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4,
+                                (cuuint64_t)h->d * h->sp.nodes * 4};
+      const cuuint32_t fb[4] = {BM, mu == 2 ? 1u : rows, mu == 2 ? rows : 1u, 1u};
+      const cuuint32_t es[4] = {1, 1, 1, 1};
       EncodeTiled enc = get_encoder();
       if (!enc) return LBM_ECUDA;
-      CUresult r = enc(&p->maps.f[mu], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+      CUresult r = enc(&p->maps.f[mu], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ks > 1 ? 4 : 3,
                        static_cast<float*>(h->dev.F) + (size_t)mu * h->sp.nodes, fd, fs, fb, es,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

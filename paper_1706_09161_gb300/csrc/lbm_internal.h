@@ -22,6 +22,10 @@ struct StepParams {
   double w0, wi;             // lattice weights: rest and moving (Fig. 1 caption)
   double adv[3];             // (dt/dx) u_mu / e^2: advective factor of Eq. (Feq)
   double C_wall;             // Dirichlet value (Eq. Dirichlet_BC)
+  // fractional terms held as ksum partial sums over the contraction (split-K operator):
+  // F_mu(node) = sum_{s < ksum} F[s * pstride + mu * nodes + node], added in order of s
+  int ksum;
+  long long pstride;
 };
 
 // Device-side buffers of one problem.
@@ -96,6 +100,9 @@ cudaError_t launch_moment(const lbm_s* h, const void* f, void* C, cudaStream_t s
 // conversions between the FP64 staging buffer and the working precision
 cudaError_t launch_convert_in(const void* src_f64, void* dst, int elem, long long n, cudaStream_t s);
 cudaError_t launch_convert_out(const void* src, int elem, double* dst_f64, long long n, cudaStream_t s);
+// dst_f64[i] = sum_{s < k} src[s * stride + i], FP32 partials added in order of s
+cudaError_t launch_sum_partials_out(const float* src, int k, long long stride, double* dst_f64, long long n,
+                                    cudaStream_t s);
 // mass reduction: partials then final
 cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
 // split C into hi/lo operands for the tensor-core path (tf32: also the transposed copies)

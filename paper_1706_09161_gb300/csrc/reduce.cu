@@ -58,6 +58,16 @@ __global__ void convert_out_kernel(const real* __restrict__ src, double* __restr
     dst[i] = static_cast<double>(src[i]);
 }
 
+// dst[i] = sum_{s < k} src[s * stride + i] (FP32, added in order of s), as FP64
+__global__ void sum_partials_out_kernel(const float* __restrict__ src, int k, long long stride,
+                                        double* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float acc = src[i];
+    for (int s = 1; s < k; ++s) acc += src[s * stride + i];
+    dst[i] = static_cast<double>(acc);
+  }
+}
+
 int blocks_for(long long n) {
   long long b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -86,6 +96,12 @@ cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s) {
 cudaError_t launch_convert_in(const void* src, void* dst, int elem, long long n, cudaStream_t s) {
   if (elem == 8) convert_in_kernel<double><<<blocks_for(n), 256, 0, s>>>((const double*)src, (double*)dst, n);
   else convert_in_kernel<float><<<blocks_for(n), 256, 0, s>>>((const double*)src, (float*)dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials_out(const float* src, int k, long long stride, double* dst, long long n,
+                                    cudaStream_t s) {
+  sum_partials_out_kernel<<<blocks_for(n), 256, 0, s>>>(src, k, stride, dst, n);
   return cudaGetLastError();
 }
 
