@@ -263,6 +263,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=40, help="lattice steps per reference-arm bench step")
     ap.add_argument("--cpu-sample", type=int, default=800, help="lattice steps of the cpu_baseline leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch configuration")
     ap.add_argument("--lattice-steps", type=int, default=None,
                     help="override the workload's lattice steps per bench step (profiling runs only)")
     args = ap.parse_args()
@@ -295,6 +296,9 @@ def main():
     batched = len(probs) > 1
     nodes = sum(pb.nodes for pb in probs)
     lat = lbm.Batch(probs, fields, precision) if batched else lbm.Lattice(probs[0], fields[0], precision)
+    # launch configuration chosen by the library's autotuner on this workload (untimed
+    # setup; the populations are restored afterwards)
+    tuned = None if args.no_autotune else lat.autotune(64)
     stream = torch.cuda.ExternalStream(lat.stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -457,7 +461,8 @@ def main():
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
                            "precision": precision, "lattice_steps_per_bench_step": nlbm,
                            "nodes": nodes, "problems": len(probs), "parallelism": f"replicas x{world}",
-                           "l2": "flushed (512 MiB write) before every bench step; state L2-resident within a run"},
+                           "l2": "flushed (512 MiB write) before every bench step; state L2-resident within a run",
+                           "launch_config": tuned if tuned is not None else "built-in"},
                 "roofline": roof, "roofline_other": roof_other, "cpu_baseline": cpu, "accuracy": accuracy,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
                         "d2h_bytes_per_step": d2h_bytes},

@@ -166,6 +166,27 @@ int lbm_write_f(lbm_t h, const double* f_host);
  *             split operands and clears the latched instability flag.  Synchronises.
  * Saving, stepping k times, loading and stepping k times again gives bit-identical
  * populations. */
+/* Launch-configuration autotuning (no counterpart in the paper): times nsteps steps
+ * (graph replay, after nsteps warm-up steps) of each candidate configuration on the
+ * handle's own data and keeps the fastest:
+ *   tensor-core forms, single problem: the operator's column tile width (64, 128, 256),
+ *     its contraction split (1, 2, 4, 8 partial sums) or the persistent kernel;
+ *   every handle: collide-stream tile rows per block (2-D) or z chunks (3-D);
+ *   batches: tile rows per block of every 2-D member.
+ * The operator plan is searched first with the current collide-stream setting, then the
+ * collide-stream setting with the best plan.  The populations are restored bit for bit
+ * afterwards (as lbm_save / lbm_load), so tuning does not advance the run.  desc, if
+ * not NULL, receives up to desc_len bytes describing the choice.  nsteps in
+ * [2, 100000] (rounded up to even), else LBM_EINVAL.  Synchronises. */
+int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len);
+
+/* Apply a launch configuration directly (for example one lbm_autotune found before):
+ * bn > 0 sets the tensor-core operator plan (bn in {64, 128, 256}, ks in {1, 2, 4, 8},
+ * persist 0/1; combinations the kernels do not cover give LBM_EINVAL), bn = 0 keeps it;
+ * chunk > 0 sets the collide-stream tile rows (2-D) or z chunks (3-D), 0 the built-in
+ * choice.  Non-tensor-core handles accept only bn = ks = persist = 0.  Asynchronous. */
+int lbm_configure(lbm_t h, int bn, int ks, int persist, int chunk);
+
 long long lbm_state_size(lbm_t h);
 int lbm_save(lbm_t h, void* dst_host, long long bytes);
 int lbm_load(lbm_t h, const void* src_host, long long bytes);

@@ -1,5 +1,6 @@
 // C ABI of liblbm_fade: handle lifetime, parameter derivation (Algorithm 1,
 // initialisation items 1-4), graph-captured time stepping and host I/O.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -222,13 +223,17 @@ int derive_dOmega(const lbm_params* p, double dOm[3][lbm::kMaxQ][lbm::kMaxQ]) {
   return LBM_OK;
 }
 
-void free_all(lbm_s* h) {
+void drop_graphs(lbm_s* h) {
   for (int i = 0; i < 2; ++i) {
     if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
     if (h->graph[i]) cudaGraphDestroy(h->graph[i]);
     h->graph_exec[i] = nullptr;
     h->graph[i] = nullptr;
   }
+}
+
+void free_all(lbm_s* h) {
+  drop_graphs(h);
   lbm::tc_release(h);
   lbm::cs_release(h);
   void* ptrs[] = {h->dev.f[0], h->dev.f[1], h->dev.C, h->dev.C0, h->dev.F, h->dev.K, h->dev.KT, h->dev.stage,
@@ -727,6 +732,165 @@ int lbm_load(lbm_t h, const void* src_host, long long bytes) {
     LBM_CUDA(cudaMemsetAsync(p->dev.flag, 0, sizeof(int), h->stream));
   }
   LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+namespace {
+
+struct TuneCfg {
+  int bn, ks, persist, chunk;
+};
+
+// the handle's launch configuration set to c (operator plan for tensor-core handles,
+// collide-stream chunk for every handle); captured graphs are dropped
+int apply_cfg(lbm_s* h, const TuneCfg& c) {
+  int rc = LBM_OK;
+  if (h->is_batch()) {
+    h->cs_chunk = c.chunk;
+    rc = lbm::cs_batch_prepare(h);
+  } else {
+    if (h->tc) {
+      if ((rc = lbm::tc_replan(h, c.bn, c.ks, c.persist))) return rc;
+      lbm::cs_release(h);
+      h->cs_chunk = c.chunk;
+      if ((rc = lbm::cs_prepare(h))) return rc;
+      h->pdl = h->prm.precision == LBM_FP32_BF16SPLIT && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
+      lbm::tc_set_pdl(h, h->pdl);
+    } else {
+      h->cs_chunk = c.chunk;
+    }
+  }
+  drop_graphs(h);
+  return rc;
+}
+
+// device time of one run of nsteps steps (graph replay)
+int time_once(lbm_s* h, int nsteps, float* ms) {
+  int rc = LBM_OK;
+  cudaEvent_t e0, e1;
+  LBM_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return record_cuda(cudaErrorMemoryAllocation, "lbm_autotune");
+  }
+  cudaError_t e = cudaEventRecord(e0, h->stream);
+  if (e == cudaSuccess && (rc = lbm_step(h, nsteps)) == LBM_OK) {
+    e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  return e == cudaSuccess ? LBM_OK : record_cuda(e, "lbm_autotune");
+}
+
+// device time of nsteps steps (graph replay), after as many warm-up steps; the faster of
+// two timed runs
+int time_steps(lbm_s* h, int nsteps, float* ms) {
+  int rc = lbm_step(h, nsteps);  // captures the graphs
+  if (rc) return rc;
+  float best = 0.f;
+  for (int rep = 0; rep < 2; ++rep) {
+    float t = 0.f;
+    if ((rc = time_once(h, nsteps, &t))) return rc;
+    best = (rep == 0 || t < best) ? t : best;
+  }
+  *ms = best;
+  return LBM_OK;
+}
+
+
+}  // namespace
+
+int lbm_configure(lbm_t h, int bn, int ks, int persist, int chunk) {
+  if (!h || chunk < 0) return LBM_EINVAL;
+  TuneCfg c{0, 0, 0, chunk > 0 ? chunk : lbm::cs_chunk_default(h)};
+  if (!h->is_batch() && h->tc) {
+    lbm::tc_config(h, &c.bn, &c.ks, &c.persist);
+    if (bn > 0) {
+      c.bn = bn;
+      c.ks = ks > 0 ? ks : 1;
+      c.persist = persist ? 1 : 0;
+    }
+  } else if (bn > 0 || ks > 0 || persist) {
+    return LBM_EINVAL;  // no tensor-core operator to plan
+  }
+  return apply_cfg(h, c);
+}
+
+int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
+  if (!h || nsteps < 2 || nsteps > 100000) return LBM_EINVAL;
+  nsteps += nsteps & 1;  // even: graph replays keep the buffer parity
+  // the state is restored afterwards, bit for bit
+  std::vector<char> state((size_t)state_bytes(h));
+  int rc = lbm_save(h, state.data(), (long long)state.size());
+  if (rc) return rc;
+  TuneCfg cur{0, 0, 0, h->cs_chunk > 0 ? h->cs_chunk : lbm::cs_chunk_default(h)};
+  if (!h->is_batch() && h->tc) lbm::tc_config(h, &cur.bn, &cur.ks, &cur.persist);
+  // candidate chunks
+  std::vector<int> chunks;
+  if (h->is_batch()) {
+    chunks = {2, 4, 8, 16};
+  } else if (h->d == 2) {
+    const int by = (h->sp.n[1] + 15) / 16;
+    for (int c : {1, 2, 3, 4, 8}) if (c <= by) chunks.push_back(c);
+  } else {
+    const int d0 = lbm::cs_chunk_default(h);
+    for (int c : {d0, d0 / 2, d0 + d0 / 2, d0 * 2, 1}) if (c >= 1 && c <= h->sp.n[2]) chunks.push_back(c);
+  }
+  if (std::find(chunks.begin(), chunks.end(), cur.chunk) == chunks.end()) chunks.push_back(cur.chunk);
+  // candidate operator plans (tensor-core single problems)
+  std::vector<TuneCfg> ops;
+  if (!h->is_batch() && h->tc) {
+    const int kbmin = lbm::tc_kbmin(h);
+    for (int bn : {64, 128, 256})
+      for (int ks : {1, 2, 4, 8}) {
+        if (bn == 256 && ks != 1) continue;
+        if (ks > kbmin) continue;
+        if (lbm::tc_count_tiles(h, bn) * ks > 2 * 152) continue;  // at most two waves
+        ops.push_back({bn, ks, 0, cur.chunk});
+      }
+    if (lbm::tc_count_tiles(h, 128) >= 152) ops.push_back({128, 1, 1, cur.chunk});
+  }
+  // coordinate search: operator plan with the current chunk, then the chunk
+  TuneCfg best = cur;
+  float best_ms = 0.f;
+  // bring the clocks up before the first measurement
+  if ((rc = apply_cfg(h, cur)) || (rc = lbm_step(h, 4 * nsteps)) || (rc = time_steps(h, nsteps, &best_ms))) return rc;
+  const float base_ms = best_ms;
+  for (const TuneCfg& c : ops) {
+    if (c.bn == cur.bn && c.ks == cur.ks && c.persist == cur.persist) continue;
+    float ms = 0.f;
+    if (apply_cfg(h, c) != LBM_OK || time_steps(h, nsteps, &ms) != LBM_OK) continue;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  const TuneCfg op_best = best;
+  for (int ch : chunks) {
+    if (ch == op_best.chunk) continue;
+    TuneCfg c = op_best;
+    c.chunk = ch;
+    float ms = 0.f;
+    if (apply_cfg(h, c) != LBM_OK || time_steps(h, nsteps, &ms) != LBM_OK) continue;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  if ((rc = apply_cfg(h, best))) return rc;
+  if ((rc = lbm_load(h, state.data(), (long long)state.size()))) return rc;
+  if (desc && desc_len > 0) {
+    if (h->tc && !h->is_batch())
+      std::snprintf(desc, (size_t)desc_len, "operator %s bn=%d ks=%d, collide chunk=%d: %.2f us/step (default %.2f)",
+                    best.persist ? "persistent" : "per-tile", best.bn, best.ks, best.chunk,
+                    1e3 * best_ms / nsteps, 1e3 * base_ms / nsteps);
+    else
+      std::snprintf(desc, (size_t)desc_len, "collide chunk=%d: %.2f us/step (default %.2f)", best.chunk,
+                    1e3 * best_ms / nsteps, 1e3 * base_ms / nsteps);
+  }
   return LBM_OK;
 }
 

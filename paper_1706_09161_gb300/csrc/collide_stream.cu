@@ -1085,8 +1085,8 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
   cfg.attrs = at;
   cfg.numAttrs = 1;
   if constexpr (D == 2 && sizeof(real) == 4) {
-    // tile rows per block: about one wave of two blocks per SM
-    const int ychunk = ychunk_for((long long)bx * by, by);
+    // tile rows per block: about one wave of two blocks per SM, unless tuned
+    const int ychunk = h->cs_chunk > 0 ? std::min(h->cs_chunk, by) : ychunk_for((long long)bx * by, by);
     cfg.gridDim = dim3(bx, (by + ychunk - 1) / ychunk, 1);
     const int early = one_wave(cfg.gridDim) ? 1 : 0;
     if (h->cs_plan) {
@@ -1102,7 +1102,7 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
     if (split == 1) return launch_march2<MRT, 1>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
     return launch_march2<MRT, 2>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
   }
-  const int nz = z_chunks((long long)bx * by, sp.n[2]);
+  const int nz = h->cs_chunk > 0 ? std::min(h->cs_chunk, sp.n[2]) : z_chunks((long long)bx * by, sp.n[2]);
   cfg.gridDim = dim3(bx, by, nz);
   const int early = one_wave(cfg.gridDim) ? 1 : 0;
   if constexpr (D == 3 && sizeof(real) == 4) {
@@ -1201,10 +1201,19 @@ void cs_release(lbm_s* h) {
 bool cs_one_wave(const lbm_s* h) {
   const int bx = (h->sp.n[0] + TX - 1) / TX, by = (h->sp.n[1] + TY - 1) / TY;
   if (h->d == 2 && h->elem == 4) {
-    const int ychunk = ychunk_for((long long)bx * by, by);
+    const int ychunk = h->cs_chunk > 0 ? std::min(h->cs_chunk, by) : ychunk_for((long long)bx * by, by);
     return one_wave(dim3(bx, (by + ychunk - 1) / ychunk, 1));
   }
-  return one_wave(dim3(bx, by, h->d == 3 ? z_chunks((long long)bx * by, h->sp.n[2]) : 1));
+  if (h->d == 2) return one_wave(dim3(bx, by, 1));
+  const int nz = h->cs_chunk > 0 ? std::min(h->cs_chunk, h->sp.n[2]) : z_chunks((long long)bx * by, h->sp.n[2]);
+  return one_wave(dim3(bx, by, nz));
+}
+
+int cs_chunk_default(const lbm_s* h) {
+  const int bx = (h->sp.n[0] + TX - 1) / TX, by = (h->sp.n[1] + TY - 1) / TY;
+  if (h->is_batch()) return kBatchYChunk;
+  if (h->d == 2) return h->elem == 4 ? ychunk_for((long long)bx * by, by) : 1;
+  return z_chunks((long long)bx * by, h->sp.n[2]);
 }
 
 int cs_batch_prepare(lbm_s* b) {
@@ -1227,10 +1236,14 @@ int cs_batch_prepare(lbm_s* b) {
     e.bx = (h->sp.n[0] + TX - 1) / TX;
     e.by = (h->sp.n[1] + TY - 1) / TY;
     // 2-D: tile rows per block (the pipelined y-march); 3-D: the whole z extent
-    e.zchunk = (h->d == 2) ? std::min(e.by, kBatchYChunk) : h->sp.n[2];
+    e.zchunk = (h->d == 2) ? std::min(e.by, b->cs_chunk > 0 ? b->cs_chunk : kBatchYChunk) : h->sp.n[2];
     start[i] = total;
     total += e.bx * ((h->d == 2) ? (e.by + e.zchunk - 1) / e.zchunk : e.by);
   }
+  if (b->batch_cs) cudaFree(b->batch_cs);
+  if (b->batch_cs_start) cudaFree(b->batch_cs_start);
+  b->batch_cs = nullptr;
+  b->batch_cs_start = nullptr;
   if (cudaMalloc(&b->batch_cs, sizeof(BatchCS) * P) != cudaSuccess) return LBM_ENOMEM;
   if (cudaMalloc(&b->batch_cs_start, sizeof(int) * P) != cudaSuccess) return LBM_ENOMEM;
   if (cudaMemcpy(b->batch_cs, tab.data(), sizeof(BatchCS) * P, cudaMemcpyHostToDevice) != cudaSuccess ||

@@ -77,6 +77,9 @@ struct TcPlan {
   int bn = 64;
   bool persist = false;  // one CTA per SM walking the tile list (frac_tc_persist_kernel)
   bool pdl = false;      // launch with programmatic stream serialization (the handle's choice)
+  int ldk[3] = {0, 0, 0};     // padded row pitch of K_mu's split parts (elements)
+  size_t koff[3] = {0, 0, 0}; // offset of K_mu's split parts (elements)
+  size_t f_elems = 0;         // capacity of the F buffer (floats)
   size_t smem = 0;
   int ldp = 0;       // padded x pitch of the C split arrays (elements)
   // tf32 only: C split transposed so that axis mu (1: y, 2: z) is contiguous, pitch ldT
@@ -1002,6 +1005,68 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   if (cudaMemcpy(h->dev.Khi, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return LBM_ECUDA;
   if (cudaMemcpy(h->dev.Klo, lbuf.data(), lbuf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return LBM_ECUDA;
 
+  for (int mu = 0; mu < h->d; ++mu) {
+    p->ldk[mu] = ldk[mu];
+    p->koff[mu] = koff[mu];
+  }
+  p->f_elems = (size_t)h->d * h->sp.nodes;
+
+  // default plan: column tiles of 128 (an M = 128 MMA costs the same for any N <= 128)
+  // or 256 when that still fills the GPU; small problems split the contraction over up
+  // to 8 CTAs per tile so that about one CTA per SM is busy; many tiles: the persistent
+  // kernel (128-column tiles, no split); batched handles always use it
+  constexpr int kSMs = 152;
+  int bn = (tc_count_tiles(h, 256) >= kSMs) ? 256 : 128;
+  const int kbmin = tc_kbmin(h);
+  int ks = 1;
+  const long long nt = tc_count_tiles(h, bn);
+  while (ks * 2 <= 8 && ks * 2 <= kbmin && nt * ks * 2 <= kSMs) ks *= 2;
+  bool persist = false;
+  if (force_bn > 0) {
+    bn = force_bn;
+    ks = std::max(1, force_ks);
+    persist = (force_bn == PBN && ks == 1);
+  } else if (tc_count_tiles(h, PBN) >= 2 * kSMs) {
+    persist = true;
+    bn = PBN;
+    ks = 1;
+  }
+  return tc_replan(h, bn, ks, persist ? 1 : 0);
+}
+
+long long tc_count_tiles(const lbm_s* h, int bn) {
+  const int n[3] = {h->sp.n[0], h->sp.n[1], h->sp.n[2]};
+  long long t = 0;
+  for (int mu = 0; mu < h->d; ++mu) {
+    const long long msub = (n[0] + BM - 1) / BM;
+    const long long outer = (mu == 0 || mu == 1) ? n[2] : n[1];
+    const long long ncols = (mu == 0) ? n[1] : n[mu];
+    t += msub * outer * ((ncols + bn - 1) / bn);
+  }
+  return t;
+}
+
+int tc_kbmin(const lbm_s* h) {
+  const int BK = 128 / ((h->prm.precision == LBM_FP32_BF16SPLIT) ? 2 : 4);
+  int kbmin = 1 << 30;
+  for (int mu = 0; mu < h->d; ++mu) kbmin = std::min(kbmin, (h->sp.n[mu] + BK - 1) / BK);
+  return kbmin;
+}
+
+// (Re)plan the operator: column tile width bn, contraction split ks, persistent or per
+// tile; re-encodes every tensor map and grows the F buffer when the split needs it.
+int tc_replan(lbm_s* h, int bn, int ks, int persist) {
+  TcPlan* p = h->tc;
+  if (!p) return LBM_EINVAL;
+  if (!(bn == 64 || bn == 128 || bn == 256) || !(ks == 1 || ks == 2 || ks == 4 || ks == 8)) return LBM_EINVAL;
+  if ((persist && (bn != PBN || ks != 1)) || (bn == 256 && ks != 1) || ks > tc_kbmin(h)) return LBM_EINVAL;
+  const int E = p->elem;
+  const int n[3] = {h->sp.n[0], h->sp.n[1], h->sp.n[2]};
+  const int ldp = p->ldp;
+  const int* ldk = p->ldk;
+  const size_t* koff = p->koff;
+  p->bn = bn;
+  p->persist = persist != 0;
   // tensor maps
   const int BK = 128 / E;
   const int MNW = 128 / E;  // MN-major box width (elements)
@@ -1015,38 +1080,7 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   P.flag = h->dev.flag;
   const cuuint64_t cdims[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
   const cuuint64_t cstr[2] = {(cuuint64_t)ldp * E, (cuuint64_t)ldp * n[1] * E};
-  // Column tiles of 128 (an M = 128 MMA costs the same for any N <= 128) or 256 when
-  // that still fills the GPU; small problems split the contraction over a cluster of
-  // up to 8 CTAs per tile so that about one CTA per SM is busy.
-  auto count_tiles = [&](int bn) {
-    long long t = 0;
-    for (int mu = 0; mu < h->d; ++mu) {
-      const long long msub = (n[0] + BM - 1) / BM;
-      const long long outer = (mu == 0 || mu == 1) ? n[2] : n[1];
-      const long long ncols = (mu == 0) ? n[1] : n[mu];
-      t += msub * outer * ((ncols + bn - 1) / bn);
-    }
-    return t;
-  };
   constexpr int kSMs = 152;
-  p->bn = (count_tiles(256) >= kSMs) ? 256 : 128;
-  int kbmin = 1 << 30;
-  for (int mu = 0; mu < h->d; ++mu) kbmin = std::min(kbmin, (n[mu] + BK - 1) / BK);
-  int ks = 1;
-  const long long nt = count_tiles(p->bn);
-  while (ks * 2 <= 8 && ks * 2 <= kbmin && nt * ks * 2 <= kSMs) ks *= 2;
-  if (force_bn > 0) {
-    p->bn = force_bn;
-    ks = std::max(1, force_ks);
-  }
-  // many tiles: the persistent kernel (128-column tiles, no split) overlaps each tile's
-  // epilogue with the next tile's MMAs; batched handles always use it
-  if (force_bn == PBN && ks == 1) p->persist = true;
-  if (force_bn <= 0 && count_tiles(PBN) >= 2 * kSMs) {
-    p->persist = true;
-    p->bn = PBN;
-    ks = 1;
-  }
   P.ksplit = ks;
   P.tma_store = (n[0] % 4 == 0) ? 1 : 0;
   int tiles = 0;
@@ -1094,12 +1128,15 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   }
   // split contraction: F holds one partial sum per rank, [rank][axis][node]; the
   // kernels that read F add them in rank order
-  if (ks > 1) {
+  const size_t need = (size_t)ks * h->d * h->sp.nodes;
+  if (need > p->f_elems) {
     if (h->dev.F) cudaFree(h->dev.F);
     h->dev.F = nullptr;
-    if (cudaMalloc(&h->dev.F, (size_t)ks * h->d * h->sp.nodes * 4) != cudaSuccess) return LBM_ENOMEM;
-    P.F = static_cast<float*>(h->dev.F);
+    p->f_elems = 0;
+    if (cudaMalloc(&h->dev.F, need * 4) != cudaSuccess) return LBM_ENOMEM;
+    p->f_elems = need;
   }
+  P.F = static_cast<float*>(h->dev.F);
   h->sp.ksum = ks;
   h->sp.pstride = (ks > 1) ? (long long)h->d * h->sp.nodes : 0;
   if (P.tma_store) {
@@ -1196,6 +1233,13 @@ bool encode_f32_map(void* map, int rank, void* base, const unsigned long long* d
   return r == CUDA_SUCCESS;
 }
 
+void tc_config(const lbm_s* h, int* bn, int* ks, int* persist) {
+  const TcPlan* p = h->tc;
+  *bn = p ? p->bn : 0;
+  *ks = p ? p->prm.ksplit : 0;
+  *persist = (p && p->persist) ? 1 : 0;
+}
+
 bool tc_one_wave(const lbm_s* h) {
   const TcPlan* p = h->tc;
   return p && (p->persist || (long long)p->prm.total_tiles * p->prm.ksplit <= kPersistCTAs);
@@ -1211,7 +1255,11 @@ cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s) {
   if (p->persist) return (p->elem == 2) ? launch_persist<2>(p, s) : launch_persist<4>(p, s);
   // 256-column tiles are chosen only when they alone fill the GPU: never split
   if (p->bn == 256 && p->prm.ksplit != 1) return cudaErrorInvalidConfiguration;
-  if (p->elem == 2) return (p->bn == 128) ? launch_bn<2, 128>(p, s) : launch_kernel<2, 256, 1>(p, s);
+  if (p->elem == 2) {
+    if (p->bn == 64) return launch_bn<2, 64>(p, s);
+    return (p->bn == 128) ? launch_bn<2, 128>(p, s) : launch_kernel<2, 256, 1>(p, s);
+  }
+  if (p->bn == 64) return launch_bn<4, 64>(p, s);
   return (p->bn == 128) ? launch_bn<4, 128>(p, s) : launch_kernel<4, 256, 1>(p, s);
 }
 

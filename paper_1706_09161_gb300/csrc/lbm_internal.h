@@ -66,6 +66,8 @@ struct lbm_s {
   // programmatic dependent launch between the operator and collide-stream: only when both
   // grids run in a single wave (measured: with multi-wave 3-D grids it costs ~30%)
   bool pdl = false;
+  // collide-stream work per block: 2-D tile rows, 3-D z chunks (0: the built-in choice)
+  int cs_chunk = 0;
   int device = 0;
   lbm::TcPlan* tc = nullptr;           // split-precision tensor-core operator, if used
   void* cs_plan = nullptr;             // TMA-fed 3-D collide-stream (tensor maps), if used
@@ -113,6 +115,13 @@ int reduce_blocks_for(long long n);
 // tensor-core plan: split K_mu (row-major FP64 per axis), allocate split C, encode TMA maps
 // force_bn / force_ks (> 0) fix the column-tile width and k-split (grouped batches use 128 / 1)
 int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn, int force_ks);
+// operator plan: column tile width bn (64, 128, 256), contraction split ks (1, 2, 4, 8),
+// persistent kernel or one CTA per tile; re-encodes the tensor maps (LBM_EINVAL for a
+// combination the kernels do not cover).  Captured graphs must be dropped afterwards.
+int tc_replan(lbm_s* h, int bn, int ks, int persist);
+long long tc_count_tiles(const lbm_s* h, int bn);  // output tiles of bn columns, all axes
+int tc_kbmin(const lbm_s* h);                      // fewest contraction blocks of any axis
+void tc_config(const lbm_s* h, int* bn, int* ks, int* persist);
 // grouped launches over the sub-problems of a batch handle
 int tc_batch_prepare(lbm_s* b);
 cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s);
@@ -125,6 +134,7 @@ void cs_release(lbm_s* h);
 bool encode_f32_map(void* map, int rank, void* base, const unsigned long long* dims,
                     const unsigned long long* strides_bytes, const unsigned int* box);
 bool cs_one_wave(const lbm_s* h);  // the collide-stream grid fits in one wave
+int cs_chunk_default(const lbm_s* h);  // the built-in tile rows (2-D) / z chunks (3-D)
 bool tc_one_wave(const lbm_s* h);  // the tensor-core operator grid fits in one wave
 void tc_set_pdl(lbm_s* h, bool on);
 cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t s);

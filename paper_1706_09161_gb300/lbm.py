@@ -81,6 +81,8 @@ def _load() -> ctypes.CDLL:
         "lbm_read_f": (ctypes.c_int, [vp, dp]),
         "lbm_write_f": (ctypes.c_int, [vp, dp]),
         "lbm_state_size": (ctypes.c_longlong, [vp]),
+        "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
+        "lbm_configure": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "lbm_save": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
         "lbm_load": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
         "lbm_mass": (ctypes.c_int, [vp, dp]),
@@ -106,7 +108,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 
 # Declared C entry points, re-exported under their own names.
-EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_read_C", "lbm_batch_mass", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f", "lbm_state_size", "lbm_save", "lbm_load",
+EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_read_C", "lbm_batch_mass", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f", "lbm_state_size", "lbm_save", "lbm_load", "lbm_autotune", "lbm_configure",
             "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_frac_matrix",
             "lbm_grad", "lbm_frac_matrix_grad", "lbm_digamma", "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
 
@@ -228,6 +230,17 @@ def lbm_read_f(h: int, out: np.ndarray) -> np.ndarray:
     assert out.dtype == np.float64 and out.flags.c_contiguous
     _check(_lib.lbm_read_f(ctypes.c_void_p(h), _dptr(out)), "lbm_read_f")
     return out
+
+
+def lbm_autotune(h: int, nsteps: int = 64) -> str:
+    """Pick the fastest launch configuration for this handle; returns its description."""
+    buf = ctypes.create_string_buffer(256)
+    _check(_lib.lbm_autotune(ctypes.c_void_p(h), int(nsteps), buf, len(buf)), "lbm_autotune")
+    return buf.value.decode()
+
+
+def lbm_configure(h: int, bn: int = 0, ks: int = 0, persist: int = 0, chunk: int = 0) -> None:
+    _check(_lib.lbm_configure(ctypes.c_void_p(h), int(bn), int(ks), int(persist), int(chunk)), "lbm_configure")
 
 
 def lbm_state_size(h: int) -> int:
@@ -365,6 +378,14 @@ class Lattice:
     def write_f(self, f: np.ndarray) -> None:
         lbm_write_f(self.h, f)
 
+    def autotune(self, nsteps: int = 64) -> str:
+        """Time the candidate launch configurations on this problem and keep the fastest."""
+        return lbm_autotune(self.h, nsteps)
+
+    def configure(self, bn: int = 0, ks: int = 0, persist: int = 0, chunk: int = 0) -> None:
+        """Apply a launch configuration (operator tile width / split / persistent, chunk)."""
+        lbm_configure(self.h, bn, ks, persist, chunk)
+
     def save(self) -> np.ndarray:
         """Checkpoint: the populations, bit for bit, behind a header (lbm_save)."""
         return lbm_save(self.h)
@@ -431,6 +452,10 @@ class Batch:
 
     def mass(self, prob: int) -> float:
         return lbm_batch_mass(self.h, prob)
+
+    def autotune(self, nsteps: int = 64) -> str:
+        """Time the candidate tile rows per collide-stream block and keep the fastest."""
+        return lbm_autotune(self.h, nsteps)
 
     def save(self) -> np.ndarray:
         """Checkpoint of every problem's populations (lbm_save)."""

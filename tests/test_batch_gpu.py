@@ -89,3 +89,16 @@ def test_batch_save_load_resumes_bit_exact(L, precision):
         C_b = [b.C(i) for i in range(len(probs))]
     for a, c in zip(C_a, C_b):
         assert np.array_equal(a, c)
+
+
+def test_batch_autotune_restores_state(L):
+    probs, fields, _ = W.batch64(nprob=5, sides=(37, 128, 200), seed=14)
+    with L.Batch(probs, fields, "bf16split") as b, L.Batch(probs, fields, "bf16split") as ref:
+        b.step(3)
+        ref.step(3)
+        desc = b.autotune(8)
+        assert "chunk" in desc
+        b.step(20)
+        ref.step(20)
+        for i in range(len(probs)):
+            assert np.array_equal(b.C(i), ref.C(i))

@@ -125,3 +125,55 @@ def test_tf32split_config_mrt3d_256_full_size(L):
     with L.Lattice(pb, C0, "tf32split") as lat:
         lat.step(2)
         assert rel_l2(lat.C(), C_ref) < 1e-5
+
+
+# ---------------------------------------------------------------- launch configurations
+
+def _plans(L, pb, kind):
+    """Every operator plan lbm_autotune may pick for this problem."""
+    BK = 64 if kind == "bf16split" else 32
+    kbmin = min((n + BK - 1) // BK for n in pb.grid)
+    out = []
+    for bn in (64, 128, 256):
+        for ks in (1, 2, 4, 8):
+            if (bn == 256 and ks != 1) or ks > kbmin:
+                continue
+            out.append((bn, ks, 0))
+    out.append((128, 1, 1))
+    return out
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("grid", [(130, 70), (200, 131), (44, 21, 37), (40, 9, 6)])
+def test_every_operator_plan_matches_oracle(L, kind, grid):
+    """Each tile width / contraction split / persistent choice gives the oracle's F."""
+    rng = np.random.default_rng(71 + grid[0] + len(grid))
+    d = len(grid)
+    pb = W.random_problem(rng, d, "mrt", grid)
+    C0 = W.random_field(rng, grid)
+    ops = O.Operators(pb)
+    F = O.fractional_terms(ops, O.concentration(O.init_populations(ops, torch.tensor(C0))))
+    with L.Lattice(pb, C0, kind) as lat:
+        for bn, ks, persist in _plans(L, pb, kind):
+            lat.configure(bn, ks, persist)
+            for mu in range(d):
+                assert rel_l2(lat.F(mu), F[mu].numpy()) < f_tol(kind, grid[mu]), (bn, ks, persist, mu)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("grid", [(130, 70), (44, 21, 37)])
+def test_autotune_restores_state_and_keeps_parity(L, kind, grid):
+    rng = np.random.default_rng(81 + grid[0])
+    pb = W.random_problem(rng, len(grid), "mrt", grid)
+    C0 = W.random_field(rng, grid)
+    n = 12
+    C_ref = O.run_C(pb, C0, n).numpy()
+    with L.Lattice(pb, C0, kind) as lat:
+        lat.step(4)
+        f0 = lat.f()
+        desc = lat.autotune(8)
+        assert desc
+        assert np.array_equal(lat.f(), f0)
+        lat.step(n - 4)
+        C = lat.C()
+    assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, n, kind)
