@@ -174,7 +174,9 @@ int lbm_write_f(lbm_t h, const double* f_host);
  *   every handle: collide-stream tile rows per block (2-D) or z chunks (3-D);
  *   batches: tile rows per block of every 2-D member.
  * The operator plan is searched first with the current collide-stream setting, then the
- * collide-stream setting with the best plan.  The populations are restored bit for bit
+ * collide-stream setting with the best plan; 2-D bf16 plans are also tried as a fused
+ * step (operator and collide-stream phases of many steps in one cooperative launch,
+ * separated by bounded grid barriers).  The populations are restored bit for bit
  * afterwards (as lbm_save / lbm_load), so tuning does not advance the run.  desc, if
  * not NULL, receives up to desc_len bytes describing the choice.  nsteps in
  * [2, 100000] (rounded up to even), else LBM_EINVAL.  Synchronises. */
@@ -184,8 +186,11 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len);
  * bn > 0 sets the tensor-core operator plan (bn in {64, 128, 256}, ks in {1, 2, 4, 8},
  * persist 0/1; combinations the kernels do not cover give LBM_EINVAL), bn = 0 keeps it;
  * chunk > 0 sets the collide-stream tile rows (2-D) or z chunks (3-D), 0 the built-in
- * choice.  Non-tensor-core handles accept only bn = ks = persist = 0.  Asynchronous. */
-int lbm_configure(lbm_t h, int bn, int ks, int persist, int chunk);
+ * choice; fused = 1 runs whole steps in one cooperative kernel (2-D bf16 split with a
+ * per-tile plan of 64/128 columns split 2 or 4, rows TMA can address; LBM_ENOTSUP
+ * otherwise).  Non-tensor-core handles accept only bn = ks = persist = fused = 0.
+ * Asynchronous. */
+int lbm_configure(lbm_t h, int bn, int ks, int persist, int chunk, int fused);
 
 long long lbm_state_size(lbm_t h);
 int lbm_save(lbm_t h, void* dst_host, long long bytes);

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "lbm_internal.h"
+#include "tc_dev.cuh"
 
 namespace lbm {
 namespace {
@@ -899,9 +900,12 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
     buf ^= 1;
   }
   // after a timeout no copy may still be landing in this block's shared memory
-  if (tid == 0)
+  if (tid == 0) {
     for (int t = (tr1 - nst > tr0 ? tr1 - nst : tr0); t < tr1; ++t)
       cs_mbar_wait(&full[stage_of(t)], parity_of(t), flag);
+    for (int s = 0; s < nst; ++s)  // the barrier words may hold other data afterwards
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(cs_smem_u32(&full[s])) : "memory");
+  }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
 }
 
@@ -914,6 +918,134 @@ collide_stream_tma2_kernel(const KConst<float> sp, const __grid_constant__ CUten
   if (early) pdl_trigger();
   march2_tma<MRT, SPLIT>(sp, &map_f, &map_F, f_out, C_out, flag, so, ychunk, blockIdx.x, blockIdx.y, cs_raw2);
   if (!early) pdl_trigger();
+}
+
+int ychunk_for(long long tiles, int by);
+
+// ---------------------------------------------------------------------------- fused 2-D step
+// Small 2-D problems on the bf16 split: one cooperative launch runs many whole steps.
+// Every block of (32, 19) threads is resident (one per SM); per step
+//   phase A  warps 0-3 run operator work items (tile, contraction slice) of the per-tile
+//            plan, storing partial tiles of F (op_item);
+//   barrier  all blocks;
+//   phase B  the block runs TMA-fed collide-stream items (tile column, tile rows), which
+//            add the partial tiles in rank order (march2_tma);
+//   barrier  all blocks.
+// The arithmetic is that of the two-kernel step with the same plan, so the results are
+// identical; the kernel boundaries (completion, flush, launch of the next grid) become
+// grid barriers.  A barrier wait is bounded: after 2 s it sets bit 2 of the flag and the
+// block continues, so every block reaches the end.
+__device__ __forceinline__ void grid_sync(unsigned int* gbar, unsigned int target, int* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    atomicAdd(gbar, 1u);
+    unsigned int v;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (true) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gbar) : "memory");
+      if (v >= target) break;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > (unsigned long long)kTmaWaitNs) {
+        atomicOr(flag, 2);
+        break;
+      }
+    }
+    __threadfence();
+    asm volatile("fence.proxy.async.global;" ::: "memory");  // this block's next TMA reads
+  }
+  __syncthreads();
+}
+
+template <int BN, int KS, bool MRT>
+__global__ void __launch_bounds__(NT, 1)
+lbm_fused2_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P, const KConst<float> sp,
+                  const __grid_constant__ CUtensorMap mf0, const __grid_constant__ CUtensorMap mf1,
+                  const __grid_constant__ CUtensorMap mF, float* f0, float* f1, float* C, SplitOut so, int ychunk,
+                  int nsteps, int parity, unsigned int* gbar, int* flag) {
+  extern __shared__ uint8_t fused_raw[];
+  __shared__ uint32_t tmem_slot;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(fused_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  if (threadIdx.y == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int G = gridDim.x;
+  const int op_items = P.total_tiles * KS;
+  const int bxn = (sp.n[0] + TX - 1) / TX, byn = (sp.n[1] + TY - 1) / TY;
+  const int cs_items = bxn * ((byn + ychunk - 1) / ychunk);
+  unsigned int target = 0;
+  for (int st = 0; st < nsteps; ++st) {
+    if (tid < 128)
+      for (int it = blockIdx.x; it < op_items; it += G) op_item<2, BN, KS>(maps, P, it, smem, tmem, tid);
+    target += G;
+    grid_sync(gbar, target, flag);
+    const int par = parity ^ (st & 1);
+    const CUtensorMap* mf = par ? &mf1 : &mf0;
+    float* fo = par ? f0 : f1;
+    for (int it = blockIdx.x; it < cs_items; it += G) {
+      march2_tma<MRT, 1>(sp, mf, &mF, fo, C, flag, so, ychunk, it % bxn, it / bxn, smem);
+      __syncthreads();
+    }
+    target += G;
+    grid_sync(gbar, target, flag);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.y == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+template <int BN, int KS>
+size_t fused_smem() {
+  const size_t a = Cfg<2, BN, KS>::SMEM, b = tma2_smem(KS);
+  return (a > b ? a : b) + 1024;
+}
+
+template <int BN, int KS, bool MRT>
+cudaError_t fused_attr(int* blocks_per_sm) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(lbm_fused2_kernel<BN, KS, MRT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<BN, KS>());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lbm_fused2_kernel<BN, KS, MRT>, NT,
+                                                       fused_smem<BN, KS>());
+}
+
+template <int BN, int KS, bool MRT>
+cudaError_t fused_launch(const lbm_s* h, int nsteps, int grid, cudaStream_t s) {
+  const TcPlan* p = h->tc;
+  const CsPlan* pl = static_cast<const CsPlan*>(h->cs_plan);
+  const KConst<float> sp = make_const<float>(h->sp);
+  SplitOut so{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
+  const int bx = (h->sp.n[0] + TX - 1) / TX, by = (h->sp.n[1] + TY - 1) / TY;
+  const int ychunk = h->cs_chunk > 0 ? std::min(h->cs_chunk, by) : ychunk_for((long long)bx * by, by);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(TX, TY + HALO_WARPS);
+  cfg.dynamicSmemBytes = fused_smem<BN, KS>();
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, lbm_fused2_kernel<BN, KS, MRT>, p->maps, p->prm, sp, pl->f[0], pl->f[1], pl->F,
+                            static_cast<float*>(h->dev.f[0]), static_cast<float*>(h->dev.f[1]),
+                            static_cast<float*>(h->dev.C), so, ychunk, nsteps, h->cur, h->fused_bar, h->dev.flag);
 }
 
 // 2-D batch blocks run either march (per problem): room for the larger ring
@@ -1163,6 +1295,48 @@ bool encode_2d_maps(const lbm_s* h, CUtensorMap* mf, CUtensorMap* mF) {
   return encode_f32_map(&mf[0], 3, h->dev.f[0], df, strides, bf) &&
          encode_f32_map(&mf[1], 3, h->dev.f[1], df, strides, bf) &&
          encode_f32_map(mF, 3, h->dev.F, dF, strides, bF);
+}
+
+// the fused step for this handle's plan: 0 (not covered) or the blocks per SM it gets
+namespace {
+template <int BN, int KS>
+cudaError_t fused_call(lbm_s* h, int nsteps, int grid, cudaStream_t s, int* occ) {
+  const bool mrt = h->prm.collision == LBM_MRT;
+  if (occ) return mrt ? fused_attr<BN, KS, true>(occ) : fused_attr<BN, KS, false>(occ);
+  return mrt ? fused_launch<BN, KS, true>(h, nsteps, grid, s) : fused_launch<BN, KS, false>(h, nsteps, grid, s);
+}
+
+cudaError_t fused_any(lbm_s* h, int nsteps, int grid, cudaStream_t s, int* occ) {
+  int bn = 0, ks = 0, persist = 0;
+  tc_config(h, &bn, &ks, &persist);
+  if (persist) return cudaErrorNotSupported;
+  if (bn == 64 && ks == 2) return fused_call<64, 2>(h, nsteps, grid, s, occ);
+  if (bn == 64 && ks == 4) return fused_call<64, 4>(h, nsteps, grid, s, occ);
+  if (bn == 128 && ks == 2) return fused_call<128, 2>(h, nsteps, grid, s, occ);
+  if (bn == 128 && ks == 4) return fused_call<128, 4>(h, nsteps, grid, s, occ);
+  return cudaErrorNotSupported;
+}
+}  // namespace
+
+int fused_prepare(lbm_s* h) {
+  h->fused_grid = 0;
+  if (h->is_batch() || h->d != 2 || h->prm.precision != LBM_FP32_BF16SPLIT || !h->tc || !h->cs_plan) return LBM_ENOTSUP;
+  if (!tc_tma_store(h)) return LBM_ENOTSUP;
+  int occ = 0;
+  if (fused_any(h, 0, 0, nullptr, &occ) != cudaSuccess || occ < 1) return LBM_ENOTSUP;
+  if (!h->fused_bar && cudaMalloc(&h->fused_bar, sizeof(unsigned int)) != cudaSuccess) return LBM_ENOMEM;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  h->fused_grid = sms * occ;
+  return LBM_OK;
+}
+
+cudaError_t launch_fused(lbm_s* h, int nsteps, cudaStream_t s) {
+  if (h->fused_grid < 1) return cudaErrorNotSupported;
+  const cudaError_t e = cudaMemsetAsync(h->fused_bar, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  return fused_any(h, nsteps, h->fused_grid, s, nullptr);
 }
 
 int cs_prepare(lbm_s* h) {

@@ -38,323 +38,10 @@
 #include <vector>
 
 #include "lbm_internal.h"
+#include "tc_dev.cuh"
 
 namespace lbm {
-
-struct TcAxis {
-  int form;        // 0: A is K-major (x axis); 1: A is MN-major (y, z axes)
-  int tiles_m;     // number of 128-line tiles
-  int tiles_n;     // number of BN-column tiles (over n = 0..side-1)
-  int tile_begin;  // first linear tile index of this axis
-  int side;        // contraction length (nodes on axis mu)
-  int kblocks;     // ceil(side / BK)
-  int msub;        // M tiles per outer index (see decode in the kernel)
-};
-
-struct TcParams {
-  int n0, n1, n2;
-  int naxes;
-  int total_tiles;
-  int ksplit;     // CTAs per output tile, each contracting a k-range into its own partial
-  int tma_store;  // F rows are 16-byte aligned (n0 % 4 == 0): store tiles with TMA
-  int early_trigger;  // the per-tile grid fits in one wave: release dependents after the prologue
-  long long nodes;
-  TcAxis ax[3];
-  float* F;
-  int* flag;
-};
-
-struct TcMaps {
-  CUtensorMap c_hi[3], c_lo[3];  // C split; box per axis (x: B rows; y, z: MN-major A)
-  CUtensorMap k_hi[3], k_lo[3];  // K_mu split; box BK x 128 for the x axis (A), BK x BN else (B)
-  CUtensorMap f[3];              // F_mu (FP32), box 128 x (BN / ksplit) output rows
-};
-
-struct TcPlan {
-  TcMaps maps;
-  TcParams prm;
-  int elem = 2;      // 2: bf16 parts, 4: tf32 parts
-  int bn = 64;
-  bool persist = false;  // one CTA per SM walking the tile list (frac_tc_persist_kernel)
-  bool pdl = false;      // launch with programmatic stream serialization (the handle's choice)
-  int ldk[3] = {0, 0, 0};     // padded row pitch of K_mu's split parts (elements)
-  size_t koff[3] = {0, 0, 0}; // offset of K_mu's split parts (elements)
-  size_t f_elems = 0;         // capacity of the F buffer (floats)
-  size_t smem = 0;
-  int ldp = 0;       // padded x pitch of the C split arrays (elements)
-  // tf32 only: C split transposed so that axis mu (1: y, 2: z) is contiguous, pitch ldT
-  void* ct_hi[3] = {nullptr, nullptr, nullptr};
-  void* ct_lo[3] = {nullptr, nullptr, nullptr};
-  int ldT[3] = {0, 0, 0};
-  ~TcPlan() {
-    for (int mu = 0; mu < 3; ++mu) {
-      if (ct_hi[mu]) cudaFree(ct_hi[mu]);
-      if (ct_lo[mu]) cudaFree(ct_lo[mu]);
-    }
-  }
-};
-
 namespace {
-
-constexpr int BM = 128;
-constexpr long long kWaitNs = 2000000000LL;
-
-template <int E> struct Kind;
-template <> struct Kind<2> {  // bf16 parts: kind::f16, UMMA_K = 16
-  static constexpr int UK = 16;
-  static constexpr uint32_t fmt = 1;
-};
-template <> struct Kind<4> {  // tf32 parts: kind::tf32, UMMA_K = 8
-  static constexpr int UK = 8;
-  static constexpr uint32_t fmt = 2;
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase; false (and flag bit 2) after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flag) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (true) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try(bar, parity)) return true;
-    if (global_ns() - t0 > (unsigned long long)kWaitNs) {
-      atomicOr(flag, 2);
-      return false;
-    }
-  }
-}
-
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-      "[%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor, 128-byte swizzle, sm_100 descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-  d |= static_cast<uint64_t>((lbo & 0x3FFFFu) >> 4) << 16;
-  d |= static_cast<uint64_t>((sbo & 0x3FFFFu) >> 4) << 32;
-  d |= static_cast<uint64_t>(1) << 46;
-  d |= static_cast<uint64_t>(2) << 61;
-  return d;
-}
-
-template <int E>
-__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                    uint32_t accum) {
-  if (E == 2) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-template <int E, int BN, int KS = 1>
-struct Cfg {
-  static constexpr int BK = 128 / E;                 // contraction elements per 128-byte row
-  static constexpr int STAGES = (BN <= 64) ? 4 : (BN <= 128 ? 3 : 2);
-  static constexpr uint32_t A_BYTES = BM * 128;      // one operand part of A: 128 rows x 128 B
-  static constexpr uint32_t B_BYTES = BN * 128;
-  static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr size_t RING = (size_t)STAGES * STAGE;
-  static constexpr size_t SMEM = RING + 1024 /*align*/ + 256 /*barriers*/;
-  // A, MN-major: E boxes of (128/E) lines x BK rows
-  static constexpr uint32_t A_BOX_MN = BK * 128;
-  static constexpr uint32_t IDESC_K = (1u << 4) | (Kind<E>::fmt << 7) | (Kind<E>::fmt << 10) |
-                                      (static_cast<uint32_t>(BN >> 3) << 17) | (static_cast<uint32_t>(BM >> 4) << 24);
-  static constexpr uint32_t IDESC_MN = IDESC_K | (1u << 15);
-};
-
-// Tile `cid` of a problem: axis mu, first x of the tile (m_in), outer coordinate
-// (m_out: z for the x and y axes, y for the z axis) and first output column (ncol0).
-struct TileAt {
-  int mu, m_in, m_out, ncol0;
-};
-
-__device__ __forceinline__ TileAt decode_tile(const TcParams& P, int cid, int bn) {
-  int mu = 0;
-  while (mu + 1 < P.naxes && cid >= P.ax[mu + 1].tile_begin) ++mu;
-  const TcAxis& ax = P.ax[mu];
-  const int lt = cid - ax.tile_begin;
-  const int mt = lt / ax.tiles_n, nt = lt % ax.tiles_n;
-  return TileAt{mu, (mt % ax.msub) * BM, mt / ax.msub, nt * bn};
-}
-
-// TMA loads of one k-block (contraction offset k0) of tile `t` into ring stage `st`,
-// completing on `bar` (whose expected byte count the caller has set).  The weight
-// parts (K_mu, fixed for the whole run) and the concentration parts (C, written by the
-// previous step) are issued separately, so the former can leave before the previous
-// kernel has finished.
-template <int E, int BN>
-__device__ __forceinline__ void load_stage_weights(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st,
-                                                   uint64_t* bar) {
-  using G = Cfg<E, BN>;
-  if (t.mu == 0) {
-    // A = K_x rows n = m_in..
-    tma_load_2d(st, &maps.k_hi[0], k0, t.m_in, bar);
-    tma_load_2d(st + G::A_BYTES, &maps.k_lo[0], k0, t.m_in, bar);
-  } else {
-    // B = K_mu rows n = ncol0..
-    uint8_t* b_hi = st + 2 * G::A_BYTES;
-    tma_load_2d(b_hi, &maps.k_hi[t.mu], k0, t.ncol0, bar);
-    tma_load_2d(b_hi + G::B_BYTES, &maps.k_lo[t.mu], k0, t.ncol0, bar);
-  }
-}
-
-template <int E, int BN>
-__device__ __forceinline__ void load_stage_conc(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st,
-                                                uint64_t* bar) {
-  using G = Cfg<E, BN>;
-  uint8_t* a_hi = st;
-  uint8_t* a_lo = st + G::A_BYTES;
-  uint8_t* b_hi = st + 2 * G::A_BYTES;
-  uint8_t* b_lo = b_hi + G::B_BYTES;
-  if (t.mu == 0) {
-    // B = C rows y = ncol0.. at z = m_out
-    tma_load_3d(b_hi, &maps.c_hi[0], k0, t.ncol0, t.m_out, bar);
-    tma_load_3d(b_lo, &maps.c_lo[0], k0, t.ncol0, t.m_out, bar);
-  } else if (E == 4) {
-    // tf32 parts: A = the C split transposed so that the contraction axis is contiguous
-    // (K-major), 128 x-lines per tile
-    tma_load_3d(a_hi, &maps.c_hi[t.mu], k0, t.m_in, t.m_out, bar);
-    tma_load_3d(a_lo, &maps.c_lo[t.mu], k0, t.m_in, t.m_out, bar);
-  } else {
-    // bf16 parts: A = the C panel, MN-major (x contiguous), E boxes of 128/E lines
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int x = t.m_in + j * (128 / E);
-      if (t.mu == 1) {
-        tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[1], x, k0, t.m_out, bar);
-        tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[1], x, k0, t.m_out, bar);
-      } else {
-        tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[2], x, t.m_out, k0, bar);
-        tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[2], x, t.m_out, k0, bar);
-      }
-    }
-  }
-}
-
-template <int E, int BN>
-__device__ __forceinline__ void load_stage(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st, uint64_t* bar) {
-  load_stage_weights<E, BN>(maps, t, k0, st, bar);
-  load_stage_conc<E, BN>(maps, t, k0, st, bar);
-}
-
-// The three split products of one k-block from ring stage `st` into accumulator `d`
-// (first = no previous contribution in d).
-template <int E, int BN>
-__device__ __forceinline__ void mma_stage(uint32_t d, uint32_t st, bool kmajor, bool first) {
-  using G = Cfg<E, BN>;
-  const uint32_t idesc = kmajor ? G::IDESC_K : G::IDESC_MN;
-  const uint32_t a_hi = st, a_lo = st + G::A_BYTES;
-  const uint32_t b_hi = st + 2 * G::A_BYTES, b_lo = b_hi + G::B_BYTES;
-#pragma unroll
-  for (int kk = 0; kk < G::BK / Kind<E>::UK; ++kk) {
-    uint32_t a_off, a_lbo;
-    if (kmajor) {  // K-major A: advance within the 128-byte row
-      a_off = kk * Kind<E>::UK * E;
-      a_lbo = 16;
-    } else {        // MN-major A: advance by UK rows of 128 bytes
-      a_off = kk * Kind<E>::UK * 128;
-      a_lbo = G::A_BOX_MN;
-    }
-    const uint32_t b_off = kk * Kind<E>::UK * E;
-    const uint64_t dah = smem_desc(a_hi + a_off, a_lbo, 1024);
-    const uint64_t dal = smem_desc(a_lo + a_off, a_lbo, 1024);
-    const uint64_t dbh = smem_desc(b_hi + b_off, 16, 1024);
-    const uint64_t dbl = smem_desc(b_lo + b_off, 16, 1024);
-    mma<E>(d, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
-    mma<E>(d, dah, dbl, idesc, 1u);
-    mma<E>(d, dal, dbh, idesc, 1u);
-  }
-}
 
 // One output tile (or one k-slice of it when KS > 1) of one problem; `block` is the
 // CTA's index among that problem's CTAs.  `maps` may live in parameter or global memory.
@@ -1232,6 +919,8 @@ bool encode_f32_map(void* map, int rank, void* base, const unsigned long long* d
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
+
+bool tc_tma_store(const lbm_s* h) { return h->tc && h->tc->prm.tma_store; }
 
 void tc_config(const lbm_s* h, int* bn, int* ks, int* persist) {
   const TcPlan* p = h->tc;

@@ -68,6 +68,10 @@ struct lbm_s {
   bool pdl = false;
   // collide-stream work per block: 2-D tile rows, 3-D z chunks (0: the built-in choice)
   int cs_chunk = 0;
+  // fused small-problem step (one cooperative launch runs many steps), if selected
+  bool fused = false;
+  int fused_grid = 0;
+  unsigned int* fused_bar = nullptr;   // grid-barrier counter
   int device = 0;
   lbm::TcPlan* tc = nullptr;           // split-precision tensor-core operator, if used
   void* cs_plan = nullptr;             // TMA-fed 3-D collide-stream (tensor maps), if used
@@ -135,6 +139,11 @@ bool encode_f32_map(void* map, int rank, void* base, const unsigned long long* d
                     const unsigned long long* strides_bytes, const unsigned int* box);
 bool cs_one_wave(const lbm_s* h);  // the collide-stream grid fits in one wave
 int cs_chunk_default(const lbm_s* h);  // the built-in tile rows (2-D) / z chunks (3-D)
+// fused 2-D step (bf16 split, per-tile plan with 64/128-column tiles and a split of 2 or
+// 4): LBM_OK if this handle can run it (sets fused_grid), LBM_ENOTSUP otherwise
+int fused_prepare(lbm_s* h);
+cudaError_t launch_fused(lbm_s* h, int nsteps, cudaStream_t s);
+bool tc_tma_store(const lbm_s* h);  // the operator stores F tiles with TMA
 bool tc_one_wave(const lbm_s* h);  // the tensor-core operator grid fits in one wave
 void tc_set_pdl(lbm_s* h, bool on);
 cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t s);

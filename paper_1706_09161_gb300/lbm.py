@@ -82,7 +82,7 @@ def _load() -> ctypes.CDLL:
         "lbm_write_f": (ctypes.c_int, [vp, dp]),
         "lbm_state_size": (ctypes.c_longlong, [vp]),
         "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
-        "lbm_configure": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "lbm_configure": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "lbm_save": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
         "lbm_load": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
         "lbm_mass": (ctypes.c_int, [vp, dp]),
@@ -239,8 +239,9 @@ def lbm_autotune(h: int, nsteps: int = 64) -> str:
     return buf.value.decode()
 
 
-def lbm_configure(h: int, bn: int = 0, ks: int = 0, persist: int = 0, chunk: int = 0) -> None:
-    _check(_lib.lbm_configure(ctypes.c_void_p(h), int(bn), int(ks), int(persist), int(chunk)), "lbm_configure")
+def lbm_configure(h: int, bn: int = 0, ks: int = 0, persist: int = 0, chunk: int = 0, fused: int = 0) -> None:
+    _check(_lib.lbm_configure(ctypes.c_void_p(h), int(bn), int(ks), int(persist), int(chunk), int(fused)),
+           "lbm_configure")
 
 
 def lbm_state_size(h: int) -> int:
@@ -382,9 +383,9 @@ class Lattice:
         """Time the candidate launch configurations on this problem and keep the fastest."""
         return lbm_autotune(self.h, nsteps)
 
-    def configure(self, bn: int = 0, ks: int = 0, persist: int = 0, chunk: int = 0) -> None:
-        """Apply a launch configuration (operator tile width / split / persistent, chunk)."""
-        lbm_configure(self.h, bn, ks, persist, chunk)
+    def configure(self, bn: int = 0, ks: int = 0, persist: int = 0, chunk: int = 0, fused: int = 0) -> None:
+        """Apply a launch configuration (operator tile width / split / persistent, chunk, fused step)."""
+        lbm_configure(self.h, bn, ks, persist, chunk, fused)
 
     def save(self) -> np.ndarray:
         """Checkpoint: the populations, bit for bit, behind a header (lbm_save)."""

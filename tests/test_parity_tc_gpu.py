@@ -177,3 +177,42 @@ def test_autotune_restores_state_and_keeps_parity(L, kind, grid):
         lat.step(n - 4)
         C = lat.C()
     assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, n, kind)
+
+
+# ---------------------------------------------------------------- fused step (one cooperative launch)
+
+FUSED_PLANS = [(64, 2), (64, 4), (128, 2), (128, 4)]
+
+
+@pytest.mark.parametrize("grid", [(200, 132), (44, 29), (512, 512)])
+@pytest.mark.parametrize("plan", FUSED_PLANS)
+def test_fused_step_equals_two_kernel_step(L, grid, plan):
+    """The fused step does the two-kernel step's arithmetic: identical populations,
+    including odd step counts (buffer parity inside the launch)."""
+    bn, ks = plan
+    rng = np.random.default_rng(97 + grid[0])
+    pb = W.random_problem(rng, 2, "mrt", grid)
+    C0 = W.random_field(rng, grid)
+    BK = 64
+    if ks > min((n + BK - 1) // BK for n in grid):
+        pytest.skip("split larger than the contraction blocks")
+    with L.Lattice(pb, C0, "bf16split") as a, L.Lattice(pb, C0, "bf16split") as b:
+        a.configure(bn, ks, 0, 0, 0)
+        b.configure(bn, ks, 0, 0, 1)
+        for n in (7, 33):
+            a.step(n)
+            b.step(n)
+            assert np.array_equal(a.f(), b.f()), (plan, n)
+        a.sync()
+        b.sync()
+
+
+def test_fused_step_matches_oracle_full_size(L):
+    pb, C0, _ = W.mrt_aniso_512()
+    n = 60
+    C_ref = O.run_C(pb, C0, n).numpy()
+    with L.Lattice(pb, C0, "bf16split") as lat:
+        lat.configure(128, 4, 0, 0, 1)
+        lat.step(n)
+        C = lat.C()
+    assert rel_l2(C, C_ref) < 1e-5
