@@ -216,3 +216,23 @@ def test_fused_step_matches_oracle_full_size(L):
         lat.step(n)
         C = lat.C()
     assert rel_l2(C, C_ref) < 1e-5
+
+
+def test_configure_rejects_uncovered_plans(L):
+    rng = np.random.default_rng(99)
+    pb = W.random_problem(rng, 2, "mrt", (130, 70))
+    C0 = W.random_field(rng, pb.grid)
+    with L.Lattice(pb, C0, "bf16split") as lat:
+        for bn, ks, persist, fused in [(96, 1, 0, 0), (128, 3, 0, 0), (256, 2, 0, 0), (64, 1, 1, 0),
+                                       (128, 16, 0, 0), (128, 2, 0, 1)]:
+            # (128, 2, fused): 130 % 4 != 0, no TMA window for the fused step
+            with pytest.raises(L.LBMError):
+                lat.configure(bn, ks, persist, 0, fused)
+        lat.configure(128, 1, 0, 0, 0)  # a covered plan still applies afterwards
+        F = lat.F(0)
+        assert np.isfinite(F).all()
+    with L.Lattice(pb, C0, "fp32") as lat:
+        with pytest.raises(L.LBMError):
+            lat.configure(128, 1, 0, 0, 0)  # no tensor-core operator
+        lat.configure(0, 0, 0, 3, 0)       # a collide-stream chunk is fine
+        lat.step(2)
