@@ -346,7 +346,9 @@ def main():
     clk = clocks.stop()
     rc = lbm.lbm_sync(lat.h)
     value, total_ms = job_value(sum(t_ms), nodes * nlbm * args.steps, world, dist, "cuda")
-    gpu_launches = args.steps * nlbm * lat.launches_per_step
+    lps = lat.launches_per_step
+    # 0: the fused step, one cooperative launch per lbm_step call of up to 4096 steps
+    gpu_launches = args.steps * (nlbm * lps if lps > 0 else -(-nlbm // 4096))
     if inverse:
         d0 = probs[0].d
         # forward + checkpointed recompute (d+1 each) and adjoint (step, d transposes, d G sums, combine)

@@ -216,7 +216,9 @@ int lbm_get_stream(lbm_t h, void** stream);
  * LBM_EINVAL for nsteps outside that range.  Synchronises. */
 int lbm_profile(lbm_t h, int nsteps, double* ms);
 
-/* Number of kernel launches one time step issues (per problem batch). */
+/* Number of kernel launches one time step issues (per problem batch) under the current
+ * launch configuration; 0 for the fused small-problem step, which issues one launch
+ * per lbm_step call of up to 4096 steps. */
 int lbm_launches_per_step(lbm_t h, int* n);
 
 /* Host-only: the (grid[mu])^2 FP64 matrix K_mu, row-major K[n*side + l], such that

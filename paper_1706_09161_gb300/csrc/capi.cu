@@ -280,7 +280,7 @@ int one_step(lbm_s* h, int& cur, cudaStream_t s) {
     return LBM_OK;
   }
   if (uses_tc(h)) {
-    LBM_CUDA(lbm::launch_split_T(h, s));  // tf32: transposed operands of the current C
+    LBM_CUDA(lbm::launch_split_T_step(h, s));  // tf32: transposed operands of the current C
     LBM_CUDA(lbm::launch_frac_tc(h, s));
   } else {
     int rc = run_frac(h, s);
@@ -552,7 +552,7 @@ int lbm_profile(lbm_t h, int nsteps, double* ms) {
           if (e == cudaSuccess) e = lbm::launch_frac_simt(p, p->dev.C, p->dev.F, h->stream);
       if (!h->is_batch()) {
         if (uses_tc(h)) {
-          e = lbm::launch_split_T(h, h->stream);
+          e = lbm::launch_split_T_step(h, h->stream);
           if (e == cudaSuccess) e = lbm::launch_frac_tc(h, h->stream);
         }
         else rc = run_frac(h, h->stream);
@@ -774,6 +774,9 @@ int apply_cfg(lbm_s* h, const TuneCfg& c) {
         if ((rc = lbm::fused_prepare(h))) return rc;
         h->fused = true;
       }
+      // every operand copy of C current: the new plan may take the transposed tf32 copies
+      // from the collide-stream kernel, which the old one did not write
+      LBM_CUDA(lbm::launch_split_C(h, h->stream));
     } else {
       h->cs_chunk = c.chunk;
     }
@@ -961,7 +964,12 @@ int lbm_get_stream(lbm_t h, void** stream) {
 
 int lbm_launches_per_step(lbm_t h, int* n) {
   if (!h || !n) return LBM_EINVAL;
-  *n = h->launches_per_step;
+  int k = h->launches_per_step;
+  if (!h->is_batch() && uses_tc(h)) {
+    if (h->fused) k = 0;  // one cooperative launch per lbm_step call (up to 4096 steps)
+    else k = 2 + ((h->prm.precision == LBM_FP32_TF32SPLIT && !lbm::cs_writes_T(h)) ? h->d - 1 : 0);
+  }
+  *n = k;
   return LBM_OK;
 }
 

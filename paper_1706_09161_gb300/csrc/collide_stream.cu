@@ -116,6 +116,13 @@ struct SplitOut {
   void* hi;
   void* lo;
   int ldp;
+  // tf32 on the TMA-fed marches: the split again, regrouped along y (index 0) and z
+  // (index 1) in groups of 4, the K-major operands of the y and z axes: element (x, y, z)
+  // at thi[0][((z tg1 + y/4) tpx + x) 4 + y%4] and thi[1][((z/4 n1 + y) tpx + x) 4 + z%4]
+  float* thi[2];
+  float* tlo[2];
+  int tg1;  // groups of 4 along y
+  int tpx;  // x pitch (n0 rounded up to 16)
 };
 
 // Per-problem entry of a grouped (batched) collide-stream launch.
@@ -504,6 +511,7 @@ collide_stream_march_kernel(const KConst<real> sp, const real* __restrict__ f_in
 // exactly as the plain march treats them.  The march itself (movers through shared
 // memory, z movers in registers, walls, moment, split) is that of march_body.
 constexpr int TW = TX + 8, TH = TY + 2;  // staged window: x from x0 - 4, y from y0 - 1
+constexpr int TCP = TX;  // row pitch of the tf32 C ring
 constexpr int TMA_STAGES = 3;
 constexpr uint32_t TMA_F_BYTES = 7u * TH * TW * 4;   // D3Q7 populations
 constexpr uint32_t TMA_FF_BYTES = 3u * TH * TW * 4;  // fractional terms
@@ -567,6 +575,9 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(cs_raw) + 127) & ~uintptr_t(127));
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)TMA_STAGES * TMA_STAGE);
   __shared__ float s_m[2][4][TY + 2][TX + 2];
+  // tf32: C of the last four planes (slot z & 3), the source of the transposed split
+  __shared__ float s_c[SPLIT == 2 ? 4 * TY * TCP : 1];
+  const bool wT = SPLIT == 2 && so.thi[0] != nullptr;
   const int n0 = sp.n[0], n1 = sp.n[1], n2 = sp.n[2];
   const long long nodes = sp.nodes;
   const long long plane = (long long)n0 * n1;
@@ -616,6 +627,46 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
 #pragma unroll
     for (int mu = 0; mu < D; ++mu) Fv[mu] = st[TMA_FF_OFF / 4 + (mu * TH + ly) * TW + lx];
     collide_node<float, D, MRT>(sp, fv, Fv, fs);
+  };
+
+  // tf32: planes (ge & ~3 or z0) .. ge of the ring to the regrouped copies.  y copy:
+  // owner warp (plane ge & ~3 + (wy & 3), y group wy >> 2) writes 32 x 16-byte groups
+  // (512 contiguous bytes); z copy: each owner writes its own column's z group.
+  auto flush_T = [&](int ge) {
+    const int gs = max(ge & ~3, z0), cnt = ge - gs + 1;
+    const int zz = (ge & ~3) + (wy & 3), yq = 4 * (wy >> 2);
+    if (zz >= gs && zz <= ge && gx < n0 && y0 + yq < n1) {
+      const float* r = &s_c[((zz & 3) * TY + yq) * TCP + lane];
+      float4 hi, lo;
+      hi.x = tf32_rna(r[0]);       lo.x = tf32_rna(r[0] - hi.x);
+      hi.y = tf32_rna(r[TCP]);     lo.y = tf32_rna(r[TCP] - hi.y);
+      hi.z = tf32_rna(r[2 * TCP]); lo.z = tf32_rna(r[2 * TCP] - hi.z);
+      hi.w = tf32_rna(r[3 * TCP]); lo.w = tf32_rna(r[3 * TCP] - hi.w);
+      const long long o = (((long long)zz * so.tg1 + ((y0 + yq) >> 2)) * so.tpx + gx) * 4;
+      *reinterpret_cast<float4*>(so.thi[0] + o) = hi;
+      *reinterpret_cast<float4*>(so.tlo[0] + o) = lo;
+    }
+    if (in_xy) {
+      const long long o = (((long long)(gs >> 2) * n1 + gy) * so.tpx + gx) * 4 + (gs & 3);
+      if (cnt == 4) {
+        float4 hi, lo;
+        const float c0 = s_c[(0 * TY + wy) * TCP + lane], c1 = s_c[(1 * TY + wy) * TCP + lane];
+        const float c2 = s_c[(2 * TY + wy) * TCP + lane], c3 = s_c[(3 * TY + wy) * TCP + lane];
+        hi.x = tf32_rna(c0); lo.x = tf32_rna(c0 - hi.x);
+        hi.y = tf32_rna(c1); lo.y = tf32_rna(c1 - hi.y);
+        hi.z = tf32_rna(c2); lo.z = tf32_rna(c2 - hi.z);
+        hi.w = tf32_rna(c3); lo.w = tf32_rna(c3 - hi.w);
+        *reinterpret_cast<float4*>(so.thi[1] + o) = hi;
+        *reinterpret_cast<float4*>(so.tlo[1] + o) = lo;
+      } else {
+        for (int k = 0; k < cnt; ++k) {
+          const float c = s_c[(((gs + k) & 3) * TY + wy) * TCP + lane];
+          const float h = tf32_rna(c);
+          so.thi[1][o + k] = h;
+          so.tlo[1][o + k] = tf32_rna(c - h);
+        }
+      }
+    }
   };
 
   if (tid == 0) {
@@ -671,6 +722,11 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(z + 3);
     }
+    if (SPLIT == 2 && wT && z > z0 && ((z - 1) & 3) == 3) {
+      if (owner) flush_T(z - 1);
+      __syncthreads();  // slot z & 3 is rewritten below
+    }
+    float Cn = 0.f;
     if (owner && in_xy) {
       float fv[Q];
       bool known[Q];
@@ -716,13 +772,19 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
       C_out[node] = C;
       if (SPLIT) write_split<SPLIT>(so, ((long long)z * n1 + gy) * so.ldp + gx, C);
       bad |= !isfinite(C);
+      Cn = C;
     }
     if (owner) {
+      if (SPLIT == 2 && wT) s_c[((z & 3) * TY + wy) * TCP + lane] = Cn;  // zero outside the domain
       prev5 = cur[5];
 #pragma unroll
       for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
     }
     buf ^= 1;
+  }
+  if (SPLIT == 2 && wT) {
+    __syncthreads();
+    if (owner) flush_T(z1 - 1);
   }
   // every issued plane (up to z1) was waited for by the owners; after a timeout make sure
   // no copy is still in flight into this block's shared memory before it exits
@@ -761,6 +823,9 @@ __device__ __forceinline__ void cs_tma_3d(void* dst, const CUtensorMap* map, int
       : "memory");
 }
 
+// tf32: C of the last two tile rows (slot t & 1), the source of the y-contiguous split
+__shared__ float s_c2[2 * TY * TCP];
+
 template <bool MRT, int SPLIT>
 __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtensorMap* map_f,
                                            const CUtensorMap* map_F, float* __restrict__ f_out,
@@ -768,6 +833,9 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
                                            int ychunk, int bx, int byc, uint8_t* raw) {
   constexpr int D = 2, Q = 5;
   auto& s_m = s_m2;
+  float* s_c = nullptr;
+  if constexpr (SPLIT == 2) s_c = s_c2;
+  const bool wT = SPLIT == 2 && so.thi[0] != nullptr;
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
   const int ks = sp.ksum;
   const int nst = tma2_nst(ks);
@@ -799,6 +867,22 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
   const bool in_x = gx >= 0 && gx < n0;
   auto stage_of = [&](int t) { return (t - tr0) % nst; };
   auto parity_of = [&](int t) { return static_cast<uint32_t>(((t - tr0) / nst) & 1); };
+  // tile row t to the y copy (element (x, y) at thi[0][(y/4 tpx + x) 4 + y%4]): warp w < 4
+  // writes y group 4t + w for the tile's 32 x (512 contiguous bytes)
+  auto flush_T = [&](int t) {
+    const int xi = lane, yq = 4 * wy;
+    if (wy < 4 && x0 + xi < n0 && t * TY + yq < n1) {
+      const float* r = &s_c[((t & 1) * TY + yq) * TCP + xi];
+      float4 hi, lo;
+      hi.x = tf32_rna(r[0]);       lo.x = tf32_rna(r[0] - hi.x);
+      hi.y = tf32_rna(r[TCP]);     lo.y = tf32_rna(r[TCP] - hi.y);
+      hi.z = tf32_rna(r[2 * TCP]); lo.z = tf32_rna(r[2 * TCP] - hi.z);
+      hi.w = tf32_rna(r[3 * TCP]); lo.w = tf32_rna(r[3 * TCP] - hi.w);
+      const long long o = ((long long)((t * TY + yq) >> 2) * so.tpx + x0 + xi) * 4;
+      *reinterpret_cast<float4*>(so.thi[0] + o) = hi;
+      *reinterpret_cast<float4*>(so.tlo[0] + o) = lo;
+    }
+  };
   auto issue = [&](int t) {
     const int s = stage_of(t);
     uint8_t* st = ring + (size_t)s * stg;
@@ -854,7 +938,9 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(tr + nst);
     }
+    if (wT && tr > tr0) flush_T(tr - 1);  // its slot is rewritten only after the next barrier
     const int gy = tr * TY + dy;
+    if (SPLIT == 2 && wT && owner && !(in_x && gy < n1)) s_c[((tr & 1) * TY + dy) * TCP + dx] = 0.f;
     if (owner && in_x && gy < n1) {
       float fv[Q];
       bool known[Q];
@@ -895,9 +981,14 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
       C_out[node] = C;
       if (SPLIT) write_split<SPLIT>(so, (long long)gy * so.ldp + gx, C);
+      if (SPLIT == 2 && wT) s_c[((tr & 1) * TY + dy) * TCP + dx] = C;
       bad |= !isfinite(C);
     }
     buf ^= 1;
+  }
+  if (wT) {
+    __syncthreads();
+    flush_T(tr1 - 1);
   }
   // after a timeout no copy may still be landing in this block's shared memory
   if (tid == 0) {
@@ -1227,6 +1318,10 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
       cfg.dynamicSmemBytes = tma2_smem(h->sp.ksum);
       if (split == 0) return launch_tma2<MRT, 0>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
       if (split == 1) return launch_tma2<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
+      so.thi[0] = static_cast<float*>(h->tc->ct_hi[1]);  // the y operand of the tf32 operator
+      so.tlo[0] = static_cast<float*>(h->tc->ct_lo[1]);
+      so.tg1 = h->tc->tg[1];
+      so.tpx = h->tc->tpx;
       return launch_tma2<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
     }
     cfg.dynamicSmemBytes = PIPE_SMEM;
@@ -1245,6 +1340,12 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
       cfg.dynamicSmemBytes = TMA_SMEM;
       if (split == 0) return launch_tma3<MRT, 0>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early);
       if (split == 1) return launch_tma3<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early);
+      for (int a = 0; a < 2; ++a) {  // the y and z operands of the tf32 operator
+        so.thi[a] = static_cast<float*>(h->tc->ct_hi[a + 1]);
+        so.tlo[a] = static_cast<float*>(h->tc->ct_lo[a + 1]);
+      }
+      so.tg1 = h->tc->tg[1];
+      so.tpx = h->tc->tpx;
       return launch_tma3<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early);
     }
   }
@@ -1265,6 +1366,12 @@ int grid_for(long long n) {
 }
 
 }  // namespace
+
+// tf32 handles on the TMA-fed marches: the collide-stream kernel writes the transposed split
+bool cs_writes_T(const lbm_s* h) {
+  return !h->is_batch() && h->elem == 4 && h->cs_plan != nullptr && h->tc != nullptr && h->tc->elem == 4 &&
+         h->prm.precision != LBM_FP32_BF16SPLIT;
+}
 
 cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s) {
   const bool mrt = h->prm.collision == LBM_MRT;

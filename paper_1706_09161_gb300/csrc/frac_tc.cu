@@ -114,12 +114,12 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     }
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer
-    const bool kmajor = (mu == 0) || (E == 4);
+    const int amode = a_mode<E>(mu);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % G::STAGES;
       if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
       tc_fence_after();
-      mma_stage<E, BN>(tmem, smem_u32(smem + (size_t)s * G::STAGE), kmajor, i == 0);
+      mma_stage<E, BN>(tmem, smem_u32(smem + (size_t)s * G::STAGE), amode, i == 0);
       mma_commit(&empty[s]);
     }
     mma_commit(done);
@@ -315,7 +315,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
       if (i >= 2 && !mbar_wait(&tempty[b], ((i >> 1) - 1) & 1, flag)) break;
       tc_fence_after();
       const uint32_t d = tmem + b * PBN;
-      const bool kmajor = (tl.mu == 0) || (E == 4);
+      const int amode = a_mode<E>(tl.mu);
       for (int kb = 0; kb < nkb; ++kb, ++r) {
         const int s = r % STAGES;
         if (!mbar_wait(&full[s], (r / STAGES) & 1, flag)) {
@@ -323,7 +323,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
           break;
         }
         tc_fence_after();
-        mma_stage<E, PBN>(d, smem_u32(smem + (size_t)s * G::STAGE), kmajor, kb == 0);
+        mma_stage<E, PBN>(d, smem_u32(smem + (size_t)s * G::STAGE), amode, kb == 0);
         mma_commit(&empty[s]);
       }
       if (ok) mma_commit(&tfull[b]);
@@ -489,30 +489,31 @@ __global__ void split_C_kernel(const float* __restrict__ C, void* __restrict__ h
   }
 }
 
-// tf32 split of C written transposed: out[(b * nb_rows + j) * ldo + i] for the element
-// in[b * bstride + i * si + j] (i along the contracted axis, j = x), through a 32 x 32
-// shared tile so that both the read (x) and the write (axis) are coalesced.
-__global__ void split_T_kernel(const float* __restrict__ C, float* __restrict__ hi, float* __restrict__ lo, int ni,
-                               int nj, long long si, long long bstride, int ldo) {
-  __shared__ float t[32][33];
-  const int b = blockIdx.z;
-  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-  const float* in = C + b * bstride;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int i = i0 + r, j = j0 + threadIdx.x;
-    t[r][threadIdx.x] = (i < ni && j < nj) ? in[i * si + j] : 0.0f;
-  }
-  __syncthreads();
-  const long long obase = (long long)b * nj * ldo;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int j = j0 + r, i = i0 + threadIdx.x;
-    if (i < ni && j < nj) {
-      const float c = t[threadIdx.x][r];
-      const float h = tf32_rna(c);
-      hi[obase + (long long)j * ldo + i] = h;
-      lo[obase + (long long)j * ldo + i] = tf32_rna(c - h);
-    }
-  }
+// tf32 split of C regrouped along axis mu (1: y, 2: z) in groups of 4 (layout at
+// TcPlan::ct_hi): one thread per (x, group, remaining axis) reads the group's 4 values
+// (coalesced over x) and writes one 16-byte group per part (coalesced over x); values
+// past the end of the axis are zero.
+__global__ void split_T_kernel(const float* __restrict__ C, float* __restrict__ hi, float* __restrict__ lo, int n0,
+                               int n1, int n2, int mu, int tg, int tpx) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;   // group along mu
+  const int r = blockIdx.z;   // remaining axis: z for the y copy, y for the z copy
+  if (x >= n0) return;
+  const long long plane = (long long)n0 * n1;
+  const int side = mu == 1 ? n1 : n2;
+  const long long step = mu == 1 ? n0 : plane;  // distance between consecutive mu
+  const long long base = mu == 1 ? (long long)r * plane + x : (long long)r * n0 + x;
+  float v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = (4 * g + k < side) ? C[base + (4 * g + k) * step] : 0.0f;
+  float4 h, l;
+  h.x = tf32_rna(v[0]); l.x = tf32_rna(v[0] - h.x);
+  h.y = tf32_rna(v[1]); l.y = tf32_rna(v[1] - h.y);
+  h.z = tf32_rna(v[2]); l.z = tf32_rna(v[2] - h.z);
+  h.w = tf32_rna(v[3]); l.w = tf32_rna(v[3] - h.w);
+  const long long o = mu == 1 ? (((long long)r * tg + g) * tpx + x) * 4 : (((long long)g * n1 + r) * tpx + x) * 4;
+  *reinterpret_cast<float4*>(hi + o) = h;
+  *reinterpret_cast<float4*>(lo + o) = l;
 }
 
 // ---------------------------------------------------------------------------- host
@@ -556,13 +557,14 @@ EncodeTiled get_encoder() {
 }
 
 bool encode(CUtensorMap* m, int elem, int rank, void* base, const cuuint64_t* dims, const cuuint64_t* strides,
-            const cuuint32_t* box) {
+            const cuuint32_t* box, bool swizzle = true) {
   EncodeTiled enc = get_encoder();
   if (!enc) return false;
-  cuuint32_t es[3] = {1, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt = (elem == 2) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUresult r = enc(m, dt, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -632,7 +634,8 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   const int E = (h->prm.precision == LBM_FP32_BF16SPLIT) ? 2 : 4;
   p->elem = E;
   // tf32 parts are fed K-major on every axis: the y and z axes read copies of the C split
-  // transposed so that y (resp. z) is contiguous, written each step by split_T_kernel.
+  // regrouped along y (resp. z), written each step by the collide-stream kernel (TMA-fed
+  // marches) or by split_T_kernel.
   const int n[3] = {h->sp.n[0], h->sp.n[1], h->sp.n[2]};
   int maxside = 0;
   for (int mu = 0; mu < h->d; ++mu) maxside = n[mu] > maxside ? n[mu] : maxside;
@@ -645,10 +648,10 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   cudaMemset(h->dev.Chi, 0, split_elems * E);
   cudaMemset(h->dev.Clo, 0, split_elems * E);
   if (E == 4) {
-    p->ldT[1] = (n[1] + 3) / 4 * 4;
-    p->ldT[2] = (n[2] + 3) / 4 * 4;
+    p->tpx = (n[0] + 15) / 16 * 16;
     for (int mu = 1; mu < h->d; ++mu) {
-      const size_t cnt = (size_t)p->ldT[mu] * h->sp.nodes / n[mu];
+      p->tg[mu] = (n[mu] + 3) / 4;
+      const size_t cnt = (size_t)4 * p->tg[mu] * p->tpx * (h->sp.nodes / n[0] / n[mu]);
       if (cudaMalloc(&p->ct_hi[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
       if (cudaMalloc(&p->ct_lo[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
       cudaMemset(p->ct_hi[mu], 0, cnt * 4);
@@ -794,13 +797,16 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
     a.tile_begin = tiles;
     tiles += a.tiles_m * a.tiles_n;
     if (E == 4 && mu > 0) {
-      // transposed copy: dims (axis mu contiguous, x, remaining axis), box BK x 128 x 1
-      const int other = (mu == 1) ? n[2] : n[1];
-      const cuuint64_t tdims[3] = {(cuuint64_t)n[mu], (cuuint64_t)n[0], (cuuint64_t)other};
-      const cuuint64_t tstr[2] = {(cuuint64_t)p->ldT[mu] * 4, (cuuint64_t)p->ldT[mu] * n[0] * 4};
-      const cuuint32_t tbox[3] = {(cuuint32_t)BK, (cuuint32_t)BM, 1};
-      if (!encode(&p->maps.c_hi[mu], E, 3, p->ct_hi[mu], tdims, tstr, tbox)) return LBM_ECUDA;
-      if (!encode(&p->maps.c_lo[mu], E, 3, p->ct_lo[mu], tdims, tstr, tbox)) return LBM_ECUDA;
+      // regrouped copy, no swizzle, rows of 16 x-groups (256 bytes): y copy dims (64, x
+      // blocks, y groups, z), box (64, 8, BK / 4, 1); z copy dims (64, x blocks, y, z
+      // groups), box (64, 8, 1, BK / 4)
+      const cuuint64_t g = (cuuint64_t)p->tg[mu], xb = (cuuint64_t)p->tpx / 16;
+      const cuuint64_t tdims[4] = {64, xb, mu == 1 ? g : (cuuint64_t)n[1], mu == 1 ? (cuuint64_t)n[2] : g};
+      const cuuint64_t tstr[3] = {256, (cuuint64_t)16 * p->tpx, (cuuint64_t)16 * p->tpx * tdims[2]};
+      const cuuint32_t tbox[4] = {64, (cuuint32_t)BM / 16, mu == 1 ? (cuuint32_t)(BK / 4) : 1u,
+                                  mu == 1 ? 1u : (cuuint32_t)(BK / 4)};
+      if (!encode(&p->maps.c_hi[mu], E, 4, p->ct_hi[mu], tdims, tstr, tbox, false)) return LBM_ECUDA;
+      if (!encode(&p->maps.c_lo[mu], E, 4, p->ct_lo[mu], tdims, tstr, tbox, false)) return LBM_ECUDA;
     } else {
       if (!encode(&p->maps.c_hi[mu], E, 3, h->dev.Chi, cdims, cstr, box)) return LBM_ECUDA;
       if (!encode(&p->maps.c_lo[mu], E, 3, h->dev.Clo, cdims, cstr, box)) return LBM_ECUDA;
@@ -956,18 +962,15 @@ cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s) {
   const TcPlan* p = h->tc;
   if (!p || p->elem != 4) return cudaSuccess;
   const int n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
-  dim3 blk(32, 8);
   const float* C = static_cast<const float*>(h->dev.C);
-  // y contiguous: per z plane, element (y, x) at C[z][y][x] -> out[z][x][y]
-  split_T_kernel<<<dim3((n0 + 31) / 32, (n1 + 31) / 32, n2), blk, 0, s>>>(
-      C, static_cast<float*>(p->ct_hi[1]), static_cast<float*>(p->ct_lo[1]), n1, n0, n0, (long long)n0 * n1, p->ldT[1]);
-  if (h->d == 3) {
-    // z contiguous: per y row, element (z, x) at C[z][y][x] -> out[y][x][z]
-    split_T_kernel<<<dim3((n0 + 31) / 32, (n2 + 31) / 32, n1), blk, 0, s>>>(
-        C, static_cast<float*>(p->ct_hi[2]), static_cast<float*>(p->ct_lo[2]), n2, n0, (long long)n0 * n1, n0,
-        p->ldT[2]);
-  }
+  for (int mu = 1; mu < h->d; ++mu)
+    split_T_kernel<<<dim3((n0 + 127) / 128, p->tg[mu], mu == 1 ? n2 : n1), 128, 0, s>>>(
+        C, static_cast<float*>(p->ct_hi[mu]), static_cast<float*>(p->ct_lo[mu]), n0, n1, n2, mu, p->tg[mu], p->tpx);
   return cudaGetLastError();
+}
+
+cudaError_t launch_split_T_step(const lbm_s* h, cudaStream_t s) {
+  return cs_writes_T(h) ? cudaSuccess : launch_split_T(h, s);
 }
 
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s) {

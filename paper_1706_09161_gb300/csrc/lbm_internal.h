@@ -115,6 +115,10 @@ cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s);
 // tf32 only: the transposed copies of the split of the current C (no-op otherwise)
 cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s);
+// launch_split_T inside the time loop: a no-op where the collide-stream kernel writes the
+// transposed split itself (cs_writes_T: tf32, 3-D, TMA-fed march)
+cudaError_t launch_split_T_step(const lbm_s* h, cudaStream_t s);
+bool cs_writes_T(const lbm_s* h);
 int reduce_blocks_for(long long n);
 // tensor-core plan: split K_mu (row-major FP64 per axis), allocate split C, encode TMA maps
 // force_bn / force_ks (> 0) fix the column-tile width and k-split (grouped batches use 128 / 1)

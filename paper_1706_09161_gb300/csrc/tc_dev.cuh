@@ -55,10 +55,18 @@ struct TcPlan {
   size_t f_elems = 0;         // capacity of the F buffer (floats)
   size_t smem = 0;
   int ldp = 0;       // padded x pitch of the C split arrays (elements)
-  // tf32 only: C split transposed so that axis mu (1: y, 2: z) is contiguous, pitch ldT
+  // tf32 only: the C split regrouped so that axis mu (1: y, 2: z) is the contraction of a
+  // K-major operand, in groups of 4 along mu (16 bytes) with x next (pitch tpx):
+  //   y copy  element (x, y, z) at ((z * tg[1] + y / 4) * tpx + x) * 4 + y % 4
+  //   z copy  element (x, y, z) at ((z / 4 * n1 + y) * tpx + x) * 4 + z % 4
+  // Entries past the end of an axis are zero.  A TMA box of (16 x, 4) x 8 x-blocks x 8
+  // groups (256-byte rows) lands as the tensor cores' no-swizzle K-major layout (8-row x
+  // 16-byte core matrices), and the collide-stream kernels write whole 16-byte groups of
+  // consecutive x.
   void* ct_hi[3] = {nullptr, nullptr, nullptr};
   void* ct_lo[3] = {nullptr, nullptr, nullptr};
-  int ldT[3] = {0, 0, 0};
+  int tg[3] = {0, 0, 0};  // groups of 4 along axis mu: ceil(n_mu / 4)
+  int tpx = 0;            // x pitch of the regrouped copies: n0 rounded up to 16
   ~TcPlan() {
     for (int mu = 0; mu < 3; ++mu) {
       if (ct_hi[mu]) cudaFree(ct_hi[mu]);
@@ -143,15 +151,38 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// Shared-memory matrix descriptor, 128-byte swizzle, sm_100 descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, sm_100 descriptor version 1; layout 2 = 128-byte
+// swizzle, 0 = no swizzle (8-row x 16-byte core matrices: lbo = stride between core
+// matrices along K, sbo = stride between groups of 8 rows).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout = 2) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
   d |= static_cast<uint64_t>((lbo & 0x3FFFFu) >> 4) << 16;
   d |= static_cast<uint64_t>((sbo & 0x3FFFFu) >> 4) << 32;
   d |= static_cast<uint64_t>(1) << 46;
-  d |= static_cast<uint64_t>(2) << 61;
+  d |= static_cast<uint64_t>(layout) << 61;
   return d;
+}
+
+// Layout of the A operand (the 128-line side) in a ring stage
+enum AMode : int {
+  kAKSw128 = 0,  // K-major, 128-byte swizzle (x axis: K_x rows)
+  kAMNSw128 = 1, // MN-major, 128-byte swizzle (bf16 y, z axes: the C panel, x contiguous)
+  kAKGroup4 = 2  // K-major, no swizzle, [k/4][128 lines][4] (tf32 y, z axes: regrouped C)
+};
+
+template <int E>
+__device__ __forceinline__ int a_mode(int mu) {
+  return mu == 0 ? kAKSw128 : (E == 4 ? kAKGroup4 : kAMNSw128);
 }
 
 template <int E>
@@ -274,10 +305,15 @@ __device__ __forceinline__ void load_stage_conc(const TcMaps& maps, const TileAt
     tma_load_3d(b_hi, &maps.c_hi[0], k0, t.ncol0, t.m_out, bar);
     tma_load_3d(b_lo, &maps.c_lo[0], k0, t.ncol0, t.m_out, bar);
   } else if (E == 4) {
-    // tf32 parts: A = the C split transposed so that the contraction axis is contiguous
-    // (K-major), 128 x-lines per tile
-    tma_load_3d(a_hi, &maps.c_hi[t.mu], k0, t.m_in, t.m_out, bar);
-    tma_load_3d(a_lo, &maps.c_lo[t.mu], k0, t.m_in, t.m_out, bar);
+    // tf32 parts: A = the regrouped C split (contraction in groups of 4), 128 x-lines
+    // (8 blocks of 16), BK / 4 groups: dims (64, x blocks, y groups or y, z or z groups)
+    if (t.mu == 1) {
+      tma_load_4d(a_hi, &maps.c_hi[1], 0, t.m_in / 16, k0 / 4, t.m_out, bar);
+      tma_load_4d(a_lo, &maps.c_lo[1], 0, t.m_in / 16, k0 / 4, t.m_out, bar);
+    } else {
+      tma_load_4d(a_hi, &maps.c_hi[2], 0, t.m_in / 16, t.m_out, k0 / 4, bar);
+      tma_load_4d(a_lo, &maps.c_lo[2], 0, t.m_in / 16, t.m_out, k0 / 4, bar);
+    }
   } else {
     // bf16 parts: A = the C panel, MN-major (x contiguous), E boxes of 128/E lines
 #pragma unroll
@@ -303,24 +339,30 @@ __device__ __forceinline__ void load_stage(const TcMaps& maps, const TileAt& t, 
 // The three split products of one k-block from ring stage `st` into accumulator `d`
 // (first = no previous contribution in d).
 template <int E, int BN>
-__device__ __forceinline__ void mma_stage(uint32_t d, uint32_t st, bool kmajor, bool first) {
+__device__ __forceinline__ void mma_stage(uint32_t d, uint32_t st, int amode, bool first) {
   using G = Cfg<E, BN>;
-  const uint32_t idesc = kmajor ? G::IDESC_K : G::IDESC_MN;
+  const uint32_t idesc = amode == kAMNSw128 ? G::IDESC_MN : G::IDESC_K;
   const uint32_t a_hi = st, a_lo = st + G::A_BYTES;
   const uint32_t b_hi = st + 2 * G::A_BYTES, b_lo = b_hi + G::B_BYTES;
 #pragma unroll
   for (int kk = 0; kk < G::BK / Kind<E>::UK; ++kk) {
-    uint32_t a_off, a_lbo;
-    if (kmajor) {  // K-major A: advance within the 128-byte row
+    uint32_t a_off, a_lbo, a_sbo = 1024, a_lay = 2;
+    if (amode == kAKSw128) {  // K-major A: advance within the 128-byte row
       a_off = kk * Kind<E>::UK * E;
       a_lbo = 16;
-    } else {        // MN-major A: advance by UK rows of 128 bytes
+    } else if (amode == kAMNSw128) {  // MN-major A: advance by UK rows of 128 bytes
       a_off = kk * Kind<E>::UK * 128;
       a_lbo = G::A_BOX_MN;
+    } else {  // grouped K-major A: 16-byte groups of K, 128 lines each (2 KB apart)
+      constexpr uint32_t kGroup = BM * 16;
+      a_off = kk * (Kind<E>::UK * E / 16) * kGroup;
+      a_lbo = kGroup;
+      a_sbo = 8 * 16;
+      a_lay = 0;
     }
     const uint32_t b_off = kk * Kind<E>::UK * E;
-    const uint64_t dah = smem_desc(a_hi + a_off, a_lbo, 1024);
-    const uint64_t dal = smem_desc(a_lo + a_off, a_lbo, 1024);
+    const uint64_t dah = smem_desc(a_hi + a_off, a_lbo, a_sbo, a_lay);
+    const uint64_t dal = smem_desc(a_lo + a_off, a_lbo, a_sbo, a_lay);
     const uint64_t dbh = smem_desc(b_hi + b_off, 16, 1024);
     const uint64_t dbl = smem_desc(b_lo + b_off, 16, 1024);
     mma<E>(d, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
@@ -373,12 +415,12 @@ __device__ __forceinline__ void op_item(const TcMaps& maps, const TcParams& P, i
       issue(i);
     }
   } else if (tid == 32) {
-    const bool kmajor = (tl.mu == 0) || (E == 4);
+    const int amode = a_mode<E>(tl.mu);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % G::STAGES;
       if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
       tc_fence_after();
-      mma_stage<E, BN>(tmem, smem_u32(smem + (size_t)s * G::STAGE), kmajor, i == 0);
+      mma_stage<E, BN>(tmem, smem_u32(smem + (size_t)s * G::STAGE), amode, i == 0);
       mma_commit(&empty[s]);
     }
     mma_commit(done);

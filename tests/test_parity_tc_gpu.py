@@ -236,3 +236,58 @@ def test_configure_rejects_uncovered_plans(L):
             lat.configure(128, 1, 0, 0, 0)  # no tensor-core operator
         lat.configure(0, 0, 0, 3, 0)       # a collide-stream chunk is fine
         lat.step(2)
+
+
+# ---------------------------------------------------------------- tf32 transposed operands
+
+def _step_resplit(lat, n):
+    """n steps, re-splitting C from the populations after each one (lbm_load rebuilds
+    every operand copy of C): the reference for operand copies written by the march."""
+    for _ in range(n):
+        lat.step(1)
+        lat.load(lat.save())
+
+
+@pytest.mark.parametrize("grid", [(44, 21, 37), (64, 70, 66), (64, 70), (96, 45)])
+def test_tf32_transposed_operands_written_by_the_march(L, grid):
+    """The TMA-fed marches write the y- (and z-) contiguous tf32 copies of C themselves.
+    Stepping on them is identical, bit for bit, to stepping on copies rebuilt from C
+    after every step, for every chunking of the march (z chunks per tile column, or tile
+    rows per block; aligned or not to the four-plane groups of the z copy)."""
+    rng = np.random.default_rng(113 + grid[0] + len(grid))
+    pb = W.random_problem(rng, len(grid), "mrt", grid)
+    C0 = W.random_field(rng, grid)
+    n = 9
+    with L.Lattice(pb, C0, "tf32split") as ref:
+        ref.configure(128, 1, 0, 0, 0)
+        _step_resplit(ref, n)
+        f_ref = ref.f()
+    for chunk in (0, 1, 2, 3, 5):
+        with L.Lattice(pb, C0, "tf32split") as lat:
+            lat.configure(128, 1, 0, chunk, 0)
+            lat.step(n)
+            assert np.array_equal(lat.f(), f_ref), chunk
+            C = lat.C()
+    C_ref = O.run_C(pb, C0, n).numpy()
+    assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, n, "tf32split")
+
+
+def test_tf32_plan_switch_keeps_operands_current(L):
+    """3-D: a contraction split moves the step between the TMA-fed march (which writes
+    the transposed copies) and the plain march (copies rebuilt before the operator);
+    switching plans mid-run leaves no stale copy."""
+    grid = (64, 70, 66)
+    rng = np.random.default_rng(127)
+    pb = W.random_problem(rng, 3, "mrt", grid)
+    C0 = W.random_field(rng, grid)
+    plans = [(128, 2), (128, 1), (128, 2), (128, 1)]
+    with L.Lattice(pb, C0, "tf32split") as a, L.Lattice(pb, C0, "tf32split") as b:
+        for bn, ks in plans:
+            a.configure(bn, ks, 0, 0, 0)
+            b.configure(bn, ks, 0, 0, 0)
+            a.step(3)
+            _step_resplit(b, 3)
+            assert np.array_equal(a.f(), b.f()), (bn, ks)
+        C = a.C()
+    C_ref = O.run_C(pb, C0, 3 * len(plans)).numpy()
+    assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, 3 * len(plans), "tf32split")
