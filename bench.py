@@ -399,7 +399,8 @@ def main():
     flops = float(sum(2.0 * pb.nodes * sum(pb.grid) for pb in probs))  # 2 side flops per node per axis
     dur = ms_frac / nprof * 1e-3
     achieved = flops / dur / 1e12
-    if precision in ("bf16split", "tf32split"):
+    split_products = {"bf16split": 3, "tf32split": 3, "bf16x5split": 5}
+    if precision in split_products:
         bound = "tensor"
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         if precision == "tf32split":
@@ -415,11 +416,12 @@ def main():
                "unit": "TFLOP/s", "frac": achieved / peak,
                "traffic": traffic_for(args.workload, "fractional_operator"),
                "algorithmic_per_launch": flops, "launch_ms": dur * 1e3, "peak_source": peak_src}
-    if precision in ("bf16split", "tf32split"):
-        # the split form issues three products (hi*hi, hi*lo, lo*hi) per algorithmic one:
-        # the tensor pipe's own load
-        roof_op["executed_per_launch"] = 3.0 * flops
-        roof_op["executed_frac"] = 3.0 * achieved / peak
+    if precision in split_products:
+        # the split forms issue three (hi*hi, hi*lo, lo*hi) or five products per
+        # algorithmic one: the tensor pipe's own load
+        npr = split_products[precision]
+        roof_op["executed_per_launch"] = npr * flops
+        roof_op["executed_frac"] = npr * achieved / peak
     if precision in ("tf32split", "fp64"):
         kind = "tf32" if precision == "tf32split" else "fp64"
         roof_op[f"cublas_{kind}_tflops_measured"] = cublas_tflops(kind)
@@ -458,7 +460,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "fp32": "f32", "bf16split": "f32+bf16x3", "tf32split": "f32+tf32x3"}[precision],
+                "dtype": {"fp64": "f64", "fp32": "f32", "bf16split": "f32+bf16x3", "tf32split": "f32+tf32x3",
+                          "bf16x5split": "f32+bf16x5"}[precision],
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
                            "precision": precision, "lattice_steps_per_bench_step": nlbm,

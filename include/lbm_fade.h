@@ -56,14 +56,21 @@ enum {
   LBM_FP32 = 1,            /* FP32 collision/streaming, FP32 fractional operator */
   LBM_FP32_BF16SPLIT = 2,  /* FP32 collision, fractional operator on tensor cores with
                               bf16 hi+lo operands (3 products), FP32 accumulation */
-  LBM_FP32_TF32SPLIT = 3   /* FP32 collision, fractional operator on tensor cores with
+  LBM_FP32_TF32SPLIT = 3,  /* FP32 collision, fractional operator on tensor cores with
                               tf32 hi+lo operands (3 products), FP32 accumulation */
+  LBM_FP32_BF16SPLIT5 = 4  /* as LBM_FP32_BF16SPLIT with K_mu in three bf16 parts
+                              k1+k2+k3 and C in two, five products (k1c1, k1c2, k2c1,
+                              k2c2, k3c1): the weights' rounding, which the three-product
+                              form carries into every step, drops to the FP32 level.
+                              Per-tile operator plans only (64 or 128 columns); single
+                              problems only (not lbm_create_batch). */
 };
 
 typedef struct {
   int lattice;        /* LBM_D2Q5 or LBM_D3Q7 */
   int collision;      /* LBM_BGK or LBM_MRT */
-  int precision;      /* LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT */
+  int precision;      /* LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT,
+                         LBM_FP32_BF16SPLIT5 */
   int grid[3];        /* nodes per axis incl. walls, >= 3 on used axes, 1 on unused axes */
   double alpha[3];    /* fractional order per axis, in ]1,2] (Eq. FADE_moreGeneral) */
   double p[3];        /* weight of the left integral I+, in [0,1] (Eq. Fg) */

@@ -90,7 +90,7 @@ int derive(const lbm_params* p, Derived* out) {
   if (!p) return LBM_EINVAL;
   if (p->lattice != LBM_D2Q5 && p->lattice != LBM_D3Q7) return LBM_EINVAL;
   if (p->collision != LBM_BGK && p->collision != LBM_MRT) return LBM_EINVAL;
-  if (p->precision < LBM_FP64 || p->precision > LBM_FP32_TF32SPLIT) return LBM_EINVAL;
+  if (p->precision < LBM_FP64 || p->precision > LBM_FP32_BF16SPLIT5) return LBM_EINVAL;
   const int d = (p->lattice == LBM_D2Q5) ? 2 : 3;
   const int Q = 2 * d + 1;
   if (!(p->dx > 0.0) || !(p->dt > 0.0) || !std::isfinite(p->dx) || !std::isfinite(p->dt)) return LBM_EINVAL;
@@ -239,7 +239,7 @@ void free_all(lbm_s* h) {
   if (h->fused_bar) cudaFree(h->fused_bar);
   h->fused_bar = nullptr;
   void* ptrs[] = {h->dev.f[0], h->dev.f[1], h->dev.C, h->dev.C0, h->dev.F, h->dev.K, h->dev.KT, h->dev.stage,
-                  h->dev.partials, h->dev.scalar, h->dev.flag, h->dev.Khi, h->dev.Klo, h->dev.Chi, h->dev.Clo};
+                  h->dev.partials, h->dev.scalar, h->dev.flag, h->dev.Khi, h->dev.Klo, h->dev.Kl2, h->dev.Chi, h->dev.Clo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->dev = lbm::DeviceState{};
@@ -403,12 +403,12 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
       Kall.push_back(K);
     }
   }
-  if (prm->precision == LBM_FP32_BF16SPLIT || prm->precision == LBM_FP32_TF32SPLIT) {
+  if (lbm::bf16_parts(prm->precision) || prm->precision == LBM_FP32_TF32SPLIT) {
     if ((rc = lbm::tc_prepare(h, Kall, batched ? 128 : 0, batched ? 1 : 0))) return fail(rc);
     h->launches_per_step = (prm->precision == LBM_FP32_TF32SPLIT) ? 2 + (h->d - 1) : 2;
     // overlap kernel boundaries only where neither grid needs a second wave; the tf32
     // transposes between collide-stream and the operator are plain launches anyway
-    h->pdl = !batched && prm->precision == LBM_FP32_BF16SPLIT && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
+    h->pdl = !batched && lbm::bf16_parts(prm->precision) && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
     lbm::tc_set_pdl(h, h->pdl);
   } else {
     h->launches_per_step = 2;  // one SIMT operator launch over every axis, one collide-stream
@@ -768,7 +768,7 @@ int apply_cfg(lbm_s* h, const TuneCfg& c) {
       lbm::cs_release(h);
       h->cs_chunk = c.chunk;
       if ((rc = lbm::cs_prepare(h))) return rc;
-      h->pdl = h->prm.precision == LBM_FP32_BF16SPLIT && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
+      h->pdl = lbm::bf16_parts(h->prm.precision) && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
       lbm::tc_set_pdl(h, h->pdl);
       if (c.fused) {
         if ((rc = lbm::fused_prepare(h))) return rc;
@@ -865,14 +865,15 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
   std::vector<TuneCfg> ops;
   if (!h->is_batch() && h->tc) {
     const int kbmin = lbm::tc_kbmin(h);
+    const bool five = h->prm.precision == LBM_FP32_BF16SPLIT5;  // per-tile kernel, 64/128 columns
     for (int bn : {64, 128, 256})
       for (int ks : {1, 2, 4, 8}) {
-        if (bn == 256 && ks != 1) continue;
+        if (bn == 256 && (ks != 1 || five)) continue;
         if (ks > kbmin) continue;
         if (lbm::tc_count_tiles(h, bn) * ks > 2 * 152) continue;  // at most two waves
         ops.push_back({bn, ks, 0, cur.chunk});
       }
-    if (lbm::tc_count_tiles(h, 128) >= 152) ops.push_back({128, 1, 1, cur.chunk});
+    if (!five && lbm::tc_count_tiles(h, 128) >= 152) ops.push_back({128, 1, 1, cur.chunk});
     // the fused step where the plan is one it covers (2-D bf16, 64/128 columns, split 2 or 4)
     const size_t nops = ops.size();
     for (size_t i = 0; i < nops; ++i)

@@ -1061,7 +1061,7 @@ lbm_fused2_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ T
   const int tid = threadIdx.y * TX + threadIdx.x;
   if (threadIdx.y == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(BN)
+                 "r"(BN * 4 <= 512 ? BN * 4 : 512)  // op_item's accumulator regions
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -1093,7 +1093,8 @@ lbm_fused2_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ T
   __syncthreads();
   if (threadIdx.y == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN * 4 <= 512 ? BN * 4 : 512)
+                 : "memory");
   }
 }
 
@@ -1292,7 +1293,7 @@ template <typename real, int D, bool MRT>
 cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s) {
   const KConst<real> sp = make_const<real>(h->sp);
   SplitOut so{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
-  const int split = (h->tc == nullptr) ? 0 : (h->prm.precision == LBM_FP32_BF16SPLIT ? 1 : 2);
+  const int split = (h->tc == nullptr) ? 0 : (bf16_parts(h->prm.precision) ? 1 : 2);
   const real* fi = static_cast<const real*>(f_in);
   const real* F = static_cast<const real*>(h->dev.F);
   real* fo = static_cast<real*>(f_out);
@@ -1370,7 +1371,7 @@ int grid_for(long long n) {
 // tf32 handles on the TMA-fed marches: the collide-stream kernel writes the transposed split
 bool cs_writes_T(const lbm_s* h) {
   return !h->is_batch() && h->elem == 4 && h->cs_plan != nullptr && h->tc != nullptr && h->tc->elem == 4 &&
-         h->prm.precision != LBM_FP32_BF16SPLIT;
+         h->prm.precision == LBM_FP32_TF32SPLIT;
 }
 
 cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s) {

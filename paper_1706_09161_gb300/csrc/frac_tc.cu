@@ -45,9 +45,9 @@ namespace {
 
 // One output tile (or one k-slice of it when KS > 1) of one problem; `block` is the
 // CTA's index among that problem's CTAs.  `maps` may live in parameter or global memory.
-template <int E, int BN, int KS>
+template <int E, int BN, int KS, int KP = 2>
 __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams& P, int block, uint8_t* smem_raw) {
-  using G = Cfg<E, BN, KS>;
+  using G = Cfg<E, BN, KS, KP>;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::RING);
   uint64_t* empty = full + G::STAGES;
@@ -65,11 +65,12 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   const TcAxis ax = P.ax[mu];
   const int kb0 = rank * ax.kblocks / ks, kb1 = (rank + 1) * ax.kblocks / ks;
   const int nkb = kb1 - kb0;
+  const int nreg = acc_regions(nkb, BN);  // TMEM accumulators, nreg * BN columns
 
   auto issue = [&](int i) {
     const int s = i % G::STAGES;
-    mbar_expect_tx(&full[s], G::STAGE);
-    load_stage<E, BN>(maps, tl, (kb0 + i) * G::BK, smem + (size_t)s * G::STAGE, &full[s]);
+    mbar_expect_tx(&full[s], G::tx_bytes(mu));
+    load_stage<E, BN, KP>(maps, tl, (kb0 + i) * G::BK, smem + (size_t)s * G::STAGE, &full[s]);
   };
 
   // ---- prologue: barrier setup and accumulator allocation overlap the previous kernel
@@ -84,16 +85,16 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     // the first stages' weight parts do not depend on the previous kernel
     const int pre = nkb < G::STAGES ? nkb : G::STAGES;
     for (int i = 0; i < pre; ++i) {
-      mbar_expect_tx(&full[i], G::STAGE);
-      load_stage_weights<E, BN>(maps, tl, (kb0 + i) * G::BK, smem + (size_t)i * G::STAGE, &full[i]);
+      mbar_expect_tx(&full[i], G::tx_bytes(mu));
+      load_stage_weights<E, BN, KP>(maps, tl, (kb0 + i) * G::BK, smem + (size_t)i * G::STAGE, &full[i]);
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int i = 0; i < pre; ++i)
-      load_stage_conc<E, BN>(maps, tl, (kb0 + i) * G::BK, smem + (size_t)i * G::STAGE, &full[i]);
+      load_stage_conc<E, BN, KP>(maps, tl, (kb0 + i) * G::BK, smem + (size_t)i * G::STAGE, &full[i]);
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(BN)
+                 "r"(nreg * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -119,7 +120,8 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
       const int s = i % G::STAGES;
       if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
       tc_fence_after();
-      mma_stage<E, BN>(tmem, smem_u32(smem + (size_t)s * G::STAGE), amode, i == 0);
+      mma_stage<E, BN, KP>(tmem + (uint32_t)((i % nreg) * BN), smem_u32(smem + (size_t)s * G::STAGE), amode,
+                           i < nreg);
       mma_commit(&empty[s]);
     }
     mma_commit(done);
@@ -136,8 +138,13 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   // TMEM -> shared tile [BN][128] (lane = x)
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
-    float v[32];
+    float v[32], w[32];
     tmem_ld32(lane_addr + c0, v);
+    for (int r = 1; r < nreg; ++r) {  // the regions, added in k order
+      tmem_ld32(lane_addr + r * BN + c0, w);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] += w[j];
+    }
 #pragma unroll
     for (int j = 0; j < 32; ++j) tile[(c0 + j) * BM + row] = have ? v[j] : 0.0f;
   }
@@ -192,16 +199,16 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(nreg * BN) : "memory");
   }
   if (!P.early_trigger) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-template <int E, int BN, int KS>
+template <int E, int BN, int KS, int KP>
 __global__ void __launch_bounds__(128, 1)
 frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
   extern __shared__ uint8_t smem_raw[];
-  frac_tc_tile<E, BN, KS>(maps, P, blockIdx.x, smem_raw);
+  frac_tc_tile<E, BN, KS, KP>(maps, P, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------- persistent form
@@ -568,35 +575,35 @@ bool encode(CUtensorMap* m, int elem, int rank, void* base, const cuuint64_t* di
   return r == CUDA_SUCCESS;
 }
 
-template <int E, int BN, int KS>
+template <int E, int BN, int KS, int KP = 2>
 cudaError_t launch_kernel(const TcPlan* p, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(frac_tc_kernel<E, BN, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg<E, BN, KS>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(frac_tc_kernel<E, BN, KS, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg<E, BN, KS, KP>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->prm.total_tiles * KS, 1, 1);
   cfg.blockDim = dim3(128, 1, 1);
-  cfg.dynamicSmemBytes = Cfg<E, BN, KS>::SMEM;
+  cfg.dynamicSmemBytes = Cfg<E, BN, KS, KP>::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = p->pdl ? 1 : 0;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, frac_tc_kernel<E, BN, KS>, p->maps, p->prm);
+  return cudaLaunchKernelEx(&cfg, frac_tc_kernel<E, BN, KS, KP>, p->maps, p->prm);
 }
 
-template <int E, int BN>
+template <int E, int BN, int KP = 2>
 cudaError_t launch_bn(const TcPlan* p, cudaStream_t s) {
   switch (p->prm.ksplit) {
-    case 1: return launch_kernel<E, BN, 1>(p, s);
-    case 2: return launch_kernel<E, BN, 2>(p, s);
-    case 4: return launch_kernel<E, BN, 4>(p, s);
-    default: return launch_kernel<E, BN, 8>(p, s);
+    case 1: return launch_kernel<E, BN, 1, KP>(p, s);
+    case 2: return launch_kernel<E, BN, 2, KP>(p, s);
+    case 4: return launch_kernel<E, BN, 4, KP>(p, s);
+    default: return launch_kernel<E, BN, 8, KP>(p, s);
   }
 }
 
@@ -631,8 +638,9 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   TcPlan* p = new (std::nothrow) TcPlan();
   if (!p) return LBM_ENOMEM;
   h->tc = p;
-  const int E = (h->prm.precision == LBM_FP32_BF16SPLIT) ? 2 : 4;
+  const int E = bf16_parts(h->prm.precision) ? 2 : 4;
   p->elem = E;
+  p->kparts = (h->prm.precision == LBM_FP32_BF16SPLIT5) ? 3 : 2;
   // tf32 parts are fed K-major on every axis: the y and z axes read copies of the C split
   // regrouped along y (resp. z), written each step by the collide-stream kernel (TMA-fed
   // marches) or by split_T_kernel.
@@ -668,7 +676,8 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   }
   if (cudaMalloc(&h->dev.Khi, ktot * E) != cudaSuccess) return LBM_ENOMEM;
   if (cudaMalloc(&h->dev.Klo, ktot * E) != cudaSuccess) return LBM_ENOMEM;
-  std::vector<uint8_t> hbuf(ktot * E, 0), lbuf(ktot * E, 0);
+  if (p->kparts == 3 && cudaMalloc(&h->dev.Kl2, ktot * E) != cudaSuccess) return LBM_ENOMEM;
+  std::vector<uint8_t> hbuf(ktot * E, 0), lbuf(ktot * E, 0), l2buf(p->kparts == 3 ? ktot * E : 0, 0);
   size_t koff[3] = {0, 0, 0};
   size_t off = 0;
   for (int mu = 0; mu < h->d; ++mu) {
@@ -679,10 +688,16 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
         const double x = K[mu][(size_t)r * side + c];
         const size_t o = off + (size_t)r * ldk[mu] + c;
         if (E == 2) {
+          // parts from the FP64 weight: each part rounds what the previous ones left
           const uint16_t hb = bf16_rne_host(static_cast<float>(x));
-          const uint16_t lb = bf16_rne_host(static_cast<float>(x - bf16_to_float_host(hb)));
+          const double r1 = x - bf16_to_float_host(hb);
+          const uint16_t lb = bf16_rne_host(static_cast<float>(r1));
           std::memcpy(&hbuf[o * 2], &hb, 2);
           std::memcpy(&lbuf[o * 2], &lb, 2);
+          if (p->kparts == 3) {
+            const uint16_t l2 = bf16_rne_host(static_cast<float>(r1 - bf16_to_float_host(lb)));
+            std::memcpy(&l2buf[o * 2], &l2, 2);
+          }
         } else {
           const float hf = tf32_rna_host(static_cast<float>(x));
           const float lf = tf32_rna_host(static_cast<float>(x - hf));
@@ -694,6 +709,9 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   }
   if (cudaMemcpy(h->dev.Khi, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return LBM_ECUDA;
   if (cudaMemcpy(h->dev.Klo, lbuf.data(), lbuf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return LBM_ECUDA;
+  if (p->kparts == 3 &&
+      cudaMemcpy(h->dev.Kl2, l2buf.data(), l2buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return LBM_ECUDA;
 
   for (int mu = 0; mu < h->d; ++mu) {
     p->ldk[mu] = ldk[mu];
@@ -706,7 +724,7 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   // to 8 CTAs per tile so that about one CTA per SM is busy; many tiles: the persistent
   // kernel (128-column tiles, no split); batched handles always use it
   constexpr int kSMs = 152;
-  int bn = (tc_count_tiles(h, 256) >= kSMs) ? 256 : 128;
+  int bn = (p->kparts == 2 && tc_count_tiles(h, 256) >= kSMs) ? 256 : 128;
   const int kbmin = tc_kbmin(h);
   int ks = 1;
   const long long nt = tc_count_tiles(h, bn);
@@ -716,7 +734,7 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
     bn = force_bn;
     ks = std::max(1, force_ks);
     persist = (force_bn == PBN && ks == 1);
-  } else if (tc_count_tiles(h, PBN) >= 2 * kSMs) {
+  } else if (p->kparts == 2 && tc_count_tiles(h, PBN) >= 2 * kSMs) {
     persist = true;
     bn = PBN;
     ks = 1;
@@ -737,7 +755,7 @@ long long tc_count_tiles(const lbm_s* h, int bn) {
 }
 
 int tc_kbmin(const lbm_s* h) {
-  const int BK = 128 / ((h->prm.precision == LBM_FP32_BF16SPLIT) ? 2 : 4);
+  const int BK = 128 / (bf16_parts(h->prm.precision) ? 2 : 4);
   int kbmin = 1 << 30;
   for (int mu = 0; mu < h->d; ++mu) kbmin = std::min(kbmin, (h->sp.n[mu] + BK - 1) / BK);
   return kbmin;
@@ -750,6 +768,8 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
   if (!p) return LBM_EINVAL;
   if (!(bn == 64 || bn == 128 || bn == 256) || !(ks == 1 || ks == 2 || ks == 4 || ks == 8)) return LBM_EINVAL;
   if ((persist && (bn != PBN || ks != 1)) || (bn == 256 && ks != 1) || ks > tc_kbmin(h)) return LBM_EINVAL;
+  // the five-product form keeps a third weight part per stage: per-tile kernel, 64 or 128 columns
+  if (p->kparts == 3 && (persist || bn == 256)) return LBM_EINVAL;
   const int E = p->elem;
   const int n[3] = {h->sp.n[0], h->sp.n[1], h->sp.n[2]};
   const int ldp = p->ldp;
@@ -817,6 +837,9 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
     if (!encode(&p->maps.k_hi[mu], E, 2, static_cast<uint8_t*>(h->dev.Khi) + koff[mu] * E, kdims, kstr, kbox))
       return LBM_ECUDA;
     if (!encode(&p->maps.k_lo[mu], E, 2, static_cast<uint8_t*>(h->dev.Klo) + koff[mu] * E, kdims, kstr, kbox))
+      return LBM_ECUDA;
+    if (p->kparts == 3 &&
+        !encode(&p->maps.k_l2[mu], E, 2, static_cast<uint8_t*>(h->dev.Kl2) + koff[mu] * E, kdims, kstr, kbox))
       return LBM_ECUDA;
   }
   // split contraction: F holds one partial sum per rank, [rank][axis][node]; the
@@ -947,6 +970,10 @@ void tc_set_pdl(lbm_s* h, bool on) {
 cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s) {
   const TcPlan* p = h->tc;
   if (!p) return cudaErrorNotSupported;
+  if (p->kparts == 3) {  // five-product bf16 form: per-tile kernel, 64 or 128 columns
+    if (p->persist || p->elem != 2 || p->bn == 256) return cudaErrorInvalidConfiguration;
+    return (p->bn == 64) ? launch_bn<2, 64, 3>(p, s) : launch_bn<2, 128, 3>(p, s);
+  }
   if (p->persist) return (p->elem == 2) ? launch_persist<2>(p, s) : launch_persist<4>(p, s);
   // 256-column tiles are chosen only when they alone fill the GPU: never split
   if (p->bn == 256 && p->prm.ksplit != 1) return cudaErrorInvalidConfiguration;

@@ -43,6 +43,7 @@ struct DeviceState {
   // split operands for the tensor-core fractional operator
   void* Khi = nullptr;               // [mu][side^2] hi part of K (bf16 or tf32-in-fp32)
   void* Klo = nullptr;               // [mu][side^2] lo part of K
+  void* Kl2 = nullptr;               // [mu][side^2] third part of K (five-product bf16 form)
   void* Chi = nullptr;               // [node] hi part of C
   void* Clo = nullptr;               // [node] lo part of C
 };
@@ -119,6 +120,10 @@ cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s);
 // transposed split itself (cs_writes_T: tf32, 3-D, TMA-fed march)
 cudaError_t launch_split_T_step(const lbm_s* h, cudaStream_t s);
 bool cs_writes_T(const lbm_s* h);
+// the tensor-core forms with bf16 parts (three or five products)
+inline bool bf16_parts(int precision) {
+  return precision == LBM_FP32_BF16SPLIT || precision == LBM_FP32_BF16SPLIT5;
+}
 int reduce_blocks_for(long long n);
 // tensor-core plan: split K_mu (row-major FP64 per axis), allocate split C, encode TMA maps
 // force_bn / force_ks (> 0) fix the column-tile width and k-split (grouped batches use 128 / 1)

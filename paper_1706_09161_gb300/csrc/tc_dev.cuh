@@ -40,6 +40,7 @@ struct TcParams {
 struct TcMaps {
   CUtensorMap c_hi[3], c_lo[3];  // C split; box per axis (x: B rows; y, z: MN-major A)
   CUtensorMap k_hi[3], k_lo[3];  // K_mu split; box BK x 128 for the x axis (A), BK x BN else (B)
+  CUtensorMap k_l2[3];           // third part of K_mu (five-product bf16 form only)
   CUtensorMap f[3];              // F_mu (FP32), box 128 x (BN / ksplit) output rows
 };
 
@@ -47,6 +48,7 @@ struct TcPlan {
   TcMaps maps;
   TcParams prm;
   int elem = 2;      // 2: bf16 parts, 4: tf32 parts
+  int kparts = 2;    // parts of K_mu: 2 (three products) or 3 (bf16, five products)
   int bn = 64;
   bool persist = false;  // one CTA per SM walking the tile list (frac_tc_persist_kernel)
   bool pdl = false;      // launch with programmatic stream serialization (the handle's choice)
@@ -240,13 +242,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int E, int BN, int KS = 1>
+// E: operand bytes; BN: output columns per tile; KS: contraction split; KP: parts of the
+// weights (2, or 3 for the five-product bf16 form; C always has two).  A ring stage holds
+// KP parts of A (from st) and KP parts of B (from st + KP * A_BYTES).
+template <int E, int BN, int KS = 1, int KP = 2>
 struct Cfg {
   static constexpr int BK = 128 / E;                 // contraction elements per 128-byte row
-  static constexpr int STAGES = (BN <= 64) ? 4 : (BN <= 128 ? 3 : 2);
+  static constexpr int STAGES = KP == 2 ? ((BN <= 64) ? 4 : (BN <= 128 ? 3 : 2)) : (BN <= 64 ? 3 : 2);
   static constexpr uint32_t A_BYTES = BM * 128;      // one operand part of A: 128 rows x 128 B
   static constexpr uint32_t B_BYTES = BN * 128;
-  static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr uint32_t STAGE = KP * A_BYTES + KP * B_BYTES;
+  // bytes one k-block of axis mu loads: the weights in KP parts, C in two
+  __host__ __device__ static constexpr uint32_t tx_bytes(int mu) {
+    return mu == 0 ? KP * A_BYTES + 2 * B_BYTES : 2 * A_BYTES + KP * B_BYTES;
+  }
   static constexpr size_t RING = (size_t)STAGES * STAGE;
   static constexpr size_t SMEM = RING + 1024 /*align*/ + 256 /*barriers*/;
   // A, MN-major: E boxes of (128/E) lines x BK rows
@@ -276,29 +285,31 @@ __device__ __forceinline__ TileAt decode_tile(const TcParams& P, int cid, int bn
 // parts (K_mu, fixed for the whole run) and the concentration parts (C, written by the
 // previous step) are issued separately, so the former can leave before the previous
 // kernel has finished.
-template <int E, int BN>
+template <int E, int BN, int KP = 2>
 __device__ __forceinline__ void load_stage_weights(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st,
                                                    uint64_t* bar) {
-  using G = Cfg<E, BN>;
+  using G = Cfg<E, BN, 1, KP>;
   if (t.mu == 0) {
     // A = K_x rows n = m_in..
     tma_load_2d(st, &maps.k_hi[0], k0, t.m_in, bar);
     tma_load_2d(st + G::A_BYTES, &maps.k_lo[0], k0, t.m_in, bar);
+    if (KP == 3) tma_load_2d(st + 2 * G::A_BYTES, &maps.k_l2[0], k0, t.m_in, bar);
   } else {
     // B = K_mu rows n = ncol0..
-    uint8_t* b_hi = st + 2 * G::A_BYTES;
+    uint8_t* b_hi = st + KP * G::A_BYTES;
     tma_load_2d(b_hi, &maps.k_hi[t.mu], k0, t.ncol0, bar);
     tma_load_2d(b_hi + G::B_BYTES, &maps.k_lo[t.mu], k0, t.ncol0, bar);
+    if (KP == 3) tma_load_2d(b_hi + 2 * G::B_BYTES, &maps.k_l2[t.mu], k0, t.ncol0, bar);
   }
 }
 
-template <int E, int BN>
+template <int E, int BN, int KP = 2>
 __device__ __forceinline__ void load_stage_conc(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st,
                                                 uint64_t* bar) {
-  using G = Cfg<E, BN>;
+  using G = Cfg<E, BN, 1, KP>;
   uint8_t* a_hi = st;
   uint8_t* a_lo = st + G::A_BYTES;
-  uint8_t* b_hi = st + 2 * G::A_BYTES;
+  uint8_t* b_hi = st + KP * G::A_BYTES;
   uint8_t* b_lo = b_hi + G::B_BYTES;
   if (t.mu == 0) {
     // B = C rows y = ncol0.. at z = m_out
@@ -330,20 +341,22 @@ __device__ __forceinline__ void load_stage_conc(const TcMaps& maps, const TileAt
   }
 }
 
-template <int E, int BN>
+template <int E, int BN, int KP = 2>
 __device__ __forceinline__ void load_stage(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st, uint64_t* bar) {
-  load_stage_weights<E, BN>(maps, t, k0, st, bar);
-  load_stage_conc<E, BN>(maps, t, k0, st, bar);
+  load_stage_weights<E, BN, KP>(maps, t, k0, st, bar);
+  load_stage_conc<E, BN, KP>(maps, t, k0, st, bar);
 }
 
-// The three split products of one k-block from ring stage `st` into accumulator `d`
-// (first = no previous contribution in d).
-template <int E, int BN>
+// The split products of one k-block from ring stage `st` into accumulator `d` (first =
+// no previous contribution in d).  With KP = 2: hi*hi, hi*lo, lo*hi.  With KP = 3 (the
+// weights in parts k1 + k2 + k3, C in c1 + c2) every product whose part orders sum to at
+// most 2: k1 c1, k1 c2, k2 c1, k2 c2, k3 c1.
+template <int E, int BN, int KP = 2>
 __device__ __forceinline__ void mma_stage(uint32_t d, uint32_t st, int amode, bool first) {
-  using G = Cfg<E, BN>;
+  using G = Cfg<E, BN, 1, KP>;
   const uint32_t idesc = amode == kAMNSw128 ? G::IDESC_MN : G::IDESC_K;
   const uint32_t a_hi = st, a_lo = st + G::A_BYTES;
-  const uint32_t b_hi = st + 2 * G::A_BYTES, b_lo = b_hi + G::B_BYTES;
+  const uint32_t b_hi = st + KP * G::A_BYTES, b_lo = b_hi + G::B_BYTES;
 #pragma unroll
   for (int kk = 0; kk < G::BK / Kind<E>::UK; ++kk) {
     uint32_t a_off, a_lbo, a_sbo = 1024, a_lay = 2;
@@ -368,17 +381,35 @@ __device__ __forceinline__ void mma_stage(uint32_t d, uint32_t st, int amode, bo
     mma<E>(d, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
     mma<E>(d, dah, dbl, idesc, 1u);
     mma<E>(d, dal, dbh, idesc, 1u);
+    if (KP == 3) {
+      mma<E>(d, dal, dbl, idesc, 1u);
+      if (amode == kAKSw128) {  // A = the weights: k3 c1
+        mma<E>(d, smem_desc(a_hi + 2 * G::A_BYTES + a_off, a_lbo, a_sbo, a_lay), dbh, idesc, 1u);
+      } else {                  // B = the weights: c1 k3
+        mma<E>(d, dah, smem_desc(b_hi + 2 * G::B_BYTES + b_off, 16, 1024), idesc, 1u);
+      }
+    }
   }
 }
 
 __device__ __forceinline__ void named_sync128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Accumulator regions of a CTA that contracts nkb k-blocks into BN columns: k-block i
+// goes to TMEM region i % regions, and the epilogue adds the regions in FP32, in order.
+// A tensor-core accumulator rounds each update at its own scale (measured: the error of
+// the result grows with the number of MMAs into one accumulator), so shorter chains make
+// the split forms more accurate at no extra MMA work.  Up to 4 regions, 512 columns.
+__host__ __device__ constexpr int acc_regions(int nkb, int bn) {
+  return (nkb >= 4 && 4 * bn <= 512) ? 4 : ((nkb >= 2 && 2 * bn <= 512) ? 2 : 1);
+}
 
 // One operator work item (tile item / KS, contraction slice item % KS) run by threads
 // 0..127 (tid, warps 0-3) of a larger block: the per-tile kernel's pipeline with named
 // barrier 1 in place of block barriers and a TMEM accumulator of BN columns allocated by
 // the caller.  The item's partial tile goes to its slot of F by one TMA store (the plan
 // must have tma_store set).  Every wait is bounded; a wait that gives up sets bit 2 of
-// the flag and the item stores nothing.
+// the flag and the item stores nothing.  `tmem` holds acc_regions(nkb, BN) * BN columns
+// (at most 512; the caller allocates min(4 BN, 512)).
 template <int E, int BN, int KS>
 __device__ __forceinline__ void op_item(const TcMaps& maps, const TcParams& P, int item, uint8_t* smem, uint32_t tmem,
                                         int tid) {
@@ -392,6 +423,7 @@ __device__ __forceinline__ void op_item(const TcMaps& maps, const TcParams& P, i
   const TcAxis& ax = P.ax[tl.mu];
   const int kb0 = rank * ax.kblocks / KS, kb1 = (rank + 1) * ax.kblocks / KS;
   const int nkb = kb1 - kb0;
+  const int nreg = acc_regions(nkb, BN);
   auto issue = [&](int i) {
     const int s = i % G::STAGES;
     mbar_expect_tx(&full[s], G::STAGE);
@@ -420,7 +452,7 @@ __device__ __forceinline__ void op_item(const TcMaps& maps, const TcParams& P, i
       const int s = i % G::STAGES;
       if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
       tc_fence_after();
-      mma_stage<E, BN>(tmem, smem_u32(smem + (size_t)s * G::STAGE), amode, i == 0);
+      mma_stage<E, BN>(tmem + (uint32_t)((i % nreg) * BN), smem_u32(smem + (size_t)s * G::STAGE), amode, i < nreg);
       mma_commit(&empty[s]);
     }
     mma_commit(done);
@@ -432,8 +464,13 @@ __device__ __forceinline__ void op_item(const TcMaps& maps, const TcParams& P, i
   const int row = tid;                            // accumulator lane = x offset in the tile
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
-    float v[32];
+    float v[32], w[32];
     tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+    for (int r = 1; r < nreg; ++r) {
+      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + r * BN + c0, w);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] += w[j];
+    }
 #pragma unroll
     for (int j = 0; j < 32; ++j) tile[(c0 + j) * BM + row] = have ? v[j] : 0.0f;
   }

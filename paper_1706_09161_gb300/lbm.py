@@ -27,8 +27,9 @@ LBM_ETOOBIG = -7
 
 LBM_D2Q5, LBM_D3Q7 = 0, 1
 LBM_BGK, LBM_MRT = 0, 1
-LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT = 0, 1, 2, 3
-PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16split": LBM_FP32_BF16SPLIT, "tf32split": LBM_FP32_TF32SPLIT}
+LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT, LBM_FP32_BF16SPLIT5 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16split": LBM_FP32_BF16SPLIT, "tf32split": LBM_FP32_TF32SPLIT,
+              "bf16x5split": LBM_FP32_BF16SPLIT5}
 
 
 class lbm_params(ctypes.Structure):

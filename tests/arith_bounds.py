@@ -2,8 +2,8 @@
 
 The scheme is re-run on the CPU with the oracle's own stage functions, on
 float32 tensors, with the fractional operator's operands rounded exactly as a
-precision form rounds them (none, bf16 hi+lo, tf32 hi+lo; three products,
-lo*lo dropped).  Its distance to the FP64 oracle is the error that arithmetic
+precision form rounds them (none; bf16 or tf32 hi+lo with three products, lo*lo
+dropped; bf16 with the weights in three parts and C in two, five products).  Its distance to the FP64 oracle is the error that arithmetic
 itself makes on the problem; the GPU result must stay within a small multiple
 of it.  No GPU code is involved.
 """
@@ -31,9 +31,24 @@ def _split(x: torch.Tensor, kind: str):
     return hi, lo
 
 
+def _bf16_parts(x: torch.Tensor, n: int):
+    """x = p1 + p2 + ... + pn + rest, each part the bf16 rounding of what the previous left."""
+    parts, r = [], x.float()
+    for _ in range(n):
+        p = r.to(torch.bfloat16).float()
+        parts.append(p)
+        r = r - p
+    return parts
+
+
 def _frac(K, C, mu, kind):
     if kind in ("fp32", None):
         return O.apply_along_axis(K, C, mu)
+    if kind == "bf16x5split":
+        k1, k2, k3 = _bf16_parts(K, 3)
+        c1, c2 = _bf16_parts(C, 2)
+        terms = [(k1, c1), (k1, c2), (k2, c1), (k2, c2), (k3, c1)]
+        return sum(O.apply_along_axis(k, c, mu) for k, c in terms)
     Kh, Kl = _split(K, kind)
     Ch, Cl = _split(C, kind)
     return (O.apply_along_axis(Kh, Ch, mu) + O.apply_along_axis(Kh, Cl, mu) + O.apply_along_axis(Kl, Ch, mu))

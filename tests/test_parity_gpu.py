@@ -213,7 +213,7 @@ def test_zero_steps_is_noop(L):
 
 # ---------------------------------------------------------------- checkpoint / resume
 
-@pytest.mark.parametrize("kind", ["fp64", "fp32", "bf16split", "tf32split"])
+@pytest.mark.parametrize("kind", ["fp64", "fp32", "bf16split", "tf32split", "bf16x5split"])
 def test_save_load_resumes_bit_exact(L, kind):
     """Saving, stepping k times, loading and stepping k times again gives the same f."""
     rng = np.random.default_rng(91)
