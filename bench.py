@@ -237,15 +237,16 @@ def source_sha(paths):
     return h.hexdigest()[:16]
 
 
-def traffic_for(workload, kernel):
-    """DRAM bytes per launch from the committed ncu summary, or None if the kernel changed since."""
+def traffic_for(workload, kernel, precision):
+    """DRAM bytes per launch from the committed ncu summary of this workload and precision
+    form, or None if there is none or the kernel changed since."""
     kernel_key = f"{workload}:{kernel}"
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         rec = json.load(fh).get(kernel_key)
-    if not rec:
+    if not rec or rec.get("precision") != precision:
         return None
     if rec.get("source_sha") != source_sha(rec["sources"]):
         return None
@@ -414,7 +415,7 @@ def main():
             peak = FP64_NOMINAL_TFLOPS
     roof_op = {"kernel": "fractional_operator", "bound": bound, "achieved": achieved, "peak": peak,
                "unit": "TFLOP/s", "frac": achieved / peak,
-               "traffic": traffic_for(args.workload, "fractional_operator"),
+               "traffic": traffic_for(args.workload, "fractional_operator", precision),
                "algorithmic_per_launch": flops, "launch_ms": dur * 1e3, "peak_source": peak_src}
     if precision in split_products:
         # the split forms issue three (hi*hi, hi*lo, lo*hi) or five products per
@@ -430,8 +431,18 @@ def main():
     achieved = bytes_ / dur / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     roof_cs = {"kernel": "collide_stream", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-               "frac": achieved / peak, "traffic": traffic_for(args.workload, "collide_stream"),
+               "frac": achieved / peak, "traffic": traffic_for(args.workload, "collide_stream", precision),
                "algorithmic_per_launch": bytes_, "launch_ms": dur * 1e3, "peak_source": peak_src}
+    if precision in split_products:
+        # the kernel also writes the operator's operands of the new C: its hi/lo split
+        # (x contiguous) and, for tf32 on the TMA-fed marches (one operator and one
+        # collide-stream launch per step), the copies regrouped along y (and z)
+        per_node = 8 if precision == "tf32split" else 4
+        if precision == "tf32split" and lat.launches_per_step == 2:
+            per_node += 8 * (d - 1)
+        ex = bytes_ + float(nodes) * per_node
+        roof_cs["executed_per_launch"] = ex
+        roof_cs["executed_frac"] = ex / dur / 1e9 / peak
     # the dominant kernel is the roofline; the other one is reported beside it
     roof, roof_other = (roof_op, roof_cs) if ms_frac >= ms_cs else (roof_cs, roof_op)
     roof["other_kernel_ms"] = {"fractional_operator": ms_frac / nprof, "collide_stream": ms_cs / nprof}
