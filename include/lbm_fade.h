@@ -99,6 +99,20 @@ typedef struct {
  * ]0,2[; LBM_ENOMEM / LBM_ECUDA on device failures (no handle is returned then). */
 int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t* out);
 
+/* Device-memory hooks.  A handle created after this call takes every device buffer it
+ * owns (populations, C, F, operands, weights, tables, adjoint checkpoints) from
+ * alloc(bytes, stream, ctx), with `stream` the handle's stream, and returns it through
+ * release(ptr, ctx) when it no longer needs it (after synchronising its stream).  alloc
+ * returns NULL when it cannot serve the request (the creating or stepping call then
+ * returns LBM_ENOMEM) and a pointer aligned to at least 256 bytes otherwise.  Each
+ * handle keeps the hooks it was created with.  Both NULL restores cudaMalloc/cudaFree;
+ * exactly one NULL returns LBM_EINVAL.  Process-wide; the hooks must stay callable until
+ * the last handle created with them is destroyed.  This is how a host framework that
+ * owns the GPU memory (e.g. PyTorch's caching allocator) lends it to the library. */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*lbm_free_fn)(void* ptr, void* ctx);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* ctx);
+
 /* A batch of nprob independent problems advanced together (each one is the scheme of
  * Algorithm 1, exactly as lbm_create would run it).  All problems share lattice,
  * collision and precision (LBM_FP32 or LBM_FP32_BF16SPLIT); grids and every other
@@ -251,6 +265,18 @@ int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host);
  * partial it reads, and calls that overlap on the GPU (different streams, no
  * ordering between them) race on it and must be serialised by the caller. */
 int lbm_mass_static(const void* x_dev, int elem_bytes, long long n, double* sum_dev, void* stream);
+
+/* Check of the bounded device-side wait behind LBM_ERR_TIMEOUT (the paper has no
+ * counterpart).  Every pipelined kernel waits on shared-memory barrier phases (TMA
+ * completions, MMA commits, the fused step's grid barrier) with a %globaltimer limit;
+ * a wait that gives up sets the timeout bit of the handle's status word and the kernel
+ * runs to its end, so the next synchronising call returns LBM_ERR_TIMEOUT and the CUDA
+ * context stays usable.  This runs that same wait, in one block on `stream` (NULL:
+ * legacy default), on a barrier whose phase is completed first (complete != 0: returns
+ * LBM_OK) or never (complete == 0: the wait gives up after limit_us microseconds and
+ * the call returns LBM_ERR_TIMEOUT).  limit_us in [1, 1000000], else LBM_EINVAL.
+ * Allocates and frees one device int; synchronises the stream. */
+int lbm_wait_check(int complete, int limit_us, void* stream);
 
 /* Loss and gradient of a snapshot misfit (the inverse problem):
  *   L(theta) = sum_k sum_x ( C(x, t_k) - obs_k(x) )^2,

@@ -417,16 +417,20 @@ AdjConst<real> make_adj(const lbm_s* h, const double dOm[3][kMaxQ][kMaxQ]) {
   return c;
 }
 
+// the gradient's device buffers, from the handle's allocator, released on scope exit
+// (after the handle's stream has drained)
 struct Buffers {
+  const lbm_s* h;
   std::vector<void*> ptrs;
   void* get(size_t bytes) {
     void* p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    if (dev_alloc(h, &p, bytes) != cudaSuccess) return nullptr;
     ptrs.push_back(p);
     return p;
   }
   ~Buffers() {
-    for (void* p : ptrs) cudaFree(p);
+    if (!ptrs.empty() && h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : ptrs) dev_free(h, p);
   }
 };
 
@@ -442,7 +446,7 @@ int run_adjoint(lbm_s* h, const AdjHooks& hooks, int nsnap, const int* snaps, co
   const int seglen = ckpt < T ? ckpt : (T > 0 ? T : 1);
   const int nb = static_cast<int>((nodes + kThreads - 1) / kThreads);
   const int cb = std::min<long long>((nodes + kThreads - 1) / kThreads, 152 * 8);
-  Buffers B;
+  Buffers B{h, {}};
   real* obs = static_cast<real*>(B.get(E * nodes * nsnap));
   real* ck = static_cast<real*>(B.get(E * Q * nodes * nck));
   real* sf = static_cast<real*>(B.get(E * Q * nodes * seglen));

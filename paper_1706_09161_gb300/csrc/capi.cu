@@ -9,6 +9,26 @@
 
 #include "lbm_internal.h"
 
+#include <mutex>
+
+namespace lbm {
+
+cudaError_t dev_alloc(const lbm_s* h, void** p, size_t bytes) {
+  if (h->mem.alloc) {
+    *p = h->mem.alloc(bytes, h->stream, h->mem.ctx);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+void dev_free(const lbm_s* h, void* p) {
+  if (!p) return;
+  if (h->mem.release) h->mem.release(p, h->mem.ctx);
+  else cudaFree(p);
+}
+
+}  // namespace lbm
+
 namespace {
 
 thread_local char g_cuda_msg[256] = "";
@@ -233,23 +253,33 @@ void drop_graphs(lbm_s* h) {
 }
 
 void free_all(lbm_s* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);  // nothing in flight uses the buffers
   drop_graphs(h);
   lbm::tc_release(h);
   lbm::cs_release(h);
-  if (h->fused_bar) cudaFree(h->fused_bar);
+  lbm::dev_free(h, h->fused_bar);
   h->fused_bar = nullptr;
   void* ptrs[] = {h->dev.f[0], h->dev.f[1], h->dev.C, h->dev.C0, h->dev.F, h->dev.K, h->dev.KT, h->dev.stage,
                   h->dev.partials, h->dev.scalar, h->dev.flag, h->dev.Khi, h->dev.Klo, h->dev.Kl2, h->dev.Chi, h->dev.Clo};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) lbm::dev_free(h, p);
   h->dev = lbm::DeviceState{};
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   h->stream = nullptr;
 }
 
-int alloc_bytes(void** p, size_t bytes) {
-  LBM_CUDA(cudaMalloc(p, bytes));
+int alloc_bytes(const lbm_s* h, void** p, size_t bytes) {
+  const cudaError_t e = lbm::dev_alloc(h, p, bytes);
+  if (e == cudaErrorMemoryAllocation) return LBM_ENOMEM;
+  LBM_CUDA(e);
   return LBM_OK;
+}
+
+std::mutex g_mem_mutex;
+DevMem g_mem;  // hooks for handles created from now on
+
+DevMem current_hooks() {
+  std::lock_guard<std::mutex> lock(g_mem_mutex);
+  return g_mem;
 }
 
 bool uses_tc(const lbm_s* h) { return h->tc != nullptr; }
@@ -348,6 +378,7 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   h->elem = (prm->precision == LBM_FP64) ? 8 : 4;
   h->sp = dv.sp;
   h->graph_steps = 32;
+  h->mem = current_hooks();
   cudaGetDevice(&h->device);
   auto fail = [&](int code) {
     free_all(h);
@@ -366,17 +397,17 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   long long ksz = 0;
   for (int mu = 0; mu < h->d; ++mu) ksz += (long long)prm->grid[mu] * prm->grid[mu];
   h->reduce_blocks = lbm::reduce_blocks_for(nodes);
-  if ((rc = alloc_bytes(&h->dev.f[0], E * h->Q * nodes))) return fail(rc);
-  if ((rc = alloc_bytes(&h->dev.f[1], E * h->Q * nodes))) return fail(rc);
-  if ((rc = alloc_bytes(&h->dev.C, E * nodes))) return fail(rc);
-  if ((rc = alloc_bytes(&h->dev.C0, E * nodes))) return fail(rc);
-  if ((rc = alloc_bytes(&h->dev.F, E * h->d * nodes))) return fail(rc);
-  if ((rc = alloc_bytes(&h->dev.K, E * ksz))) return fail(rc);
-  if ((rc = alloc_bytes(&h->dev.KT, E * ksz))) return fail(rc);
-  if ((rc = alloc_bytes((void**)&h->dev.stage, sizeof(double) * (size_t)(nodes > ksz ? nodes : ksz)))) return fail(rc);
-  if ((rc = alloc_bytes((void**)&h->dev.partials, sizeof(double) * h->reduce_blocks))) return fail(rc);
-  if ((rc = alloc_bytes((void**)&h->dev.scalar, sizeof(double)))) return fail(rc);
-  if ((rc = alloc_bytes((void**)&h->dev.flag, sizeof(int)))) return fail(rc);
+  if ((rc = alloc_bytes(h, &h->dev.f[0], E * h->Q * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(h, &h->dev.f[1], E * h->Q * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(h, &h->dev.C, E * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(h, &h->dev.C0, E * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(h, &h->dev.F, E * h->d * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(h, &h->dev.K, E * ksz))) return fail(rc);
+  if ((rc = alloc_bytes(h, &h->dev.KT, E * ksz))) return fail(rc);
+  if ((rc = alloc_bytes(h, (void**)&h->dev.stage, sizeof(double) * (size_t)(nodes > ksz ? nodes : ksz)))) return fail(rc);
+  if ((rc = alloc_bytes(h, (void**)&h->dev.partials, sizeof(double) * h->reduce_blocks))) return fail(rc);
+  if ((rc = alloc_bytes(h, (void**)&h->dev.scalar, sizeof(double)))) return fail(rc);
+  if ((rc = alloc_bytes(h, (void**)&h->dev.flag, sizeof(int)))) return fail(rc);
   if (cudaMemsetAsync(h->dev.flag, 0, sizeof(int), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
 
   // weight matrices K_mu (Section 2.4) in FP64 on the host, then the working precision
@@ -447,6 +478,7 @@ int lbm_create_batch(int nprob, const lbm_params* prms, const double* const* C0_
   b->Q = 2 * b->d + 1;
   b->elem = 4;
   b->graph_steps = 32;
+  b->mem = current_hooks();
   cudaGetDevice(&b->device);
   auto fail = [&](int code) {
     lbm_destroy(b);
@@ -1039,13 +1071,22 @@ int lbm_frac_matrix_grad(const lbm_params* prm, int mu, double* dK_dalpha, doubl
 
 double lbm_digamma(double x) { return lbm::digamma_fn(x); }
 
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) return LBM_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mem_mutex);
+  g_mem.alloc = alloc;
+  g_mem.release = release;
+  g_mem.ctx = alloc ? ctx : nullptr;
+  return LBM_OK;
+}
+
 void lbm_destroy(lbm_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (lbm_s* p : h->subs) lbm_destroy(p);
   h->subs.clear();
-  if (h->batch_cs) cudaFree(h->batch_cs);
-  if (h->batch_cs_start) cudaFree(h->batch_cs_start);
+  lbm::dev_free(h, h->batch_cs);
+  lbm::dev_free(h, h->batch_cs_start);
   h->batch_cs = nullptr;
   h->batch_cs_start = nullptr;
   free_all(h);

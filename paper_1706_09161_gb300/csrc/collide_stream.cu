@@ -1432,7 +1432,7 @@ int fused_prepare(lbm_s* h) {
   if (!tc_tma_store(h)) return LBM_ENOTSUP;
   int occ = 0;
   if (fused_any(h, 0, 0, nullptr, &occ) != cudaSuccess || occ < 1) return LBM_ENOTSUP;
-  if (!h->fused_bar && cudaMalloc(&h->fused_bar, sizeof(unsigned int)) != cudaSuccess) return LBM_ENOMEM;
+  if (!h->fused_bar && dev_alloc(h, (void**)&h->fused_bar, sizeof(unsigned int)) != cudaSuccess) return LBM_ENOMEM;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1522,12 +1522,12 @@ int cs_batch_prepare(lbm_s* b) {
     start[i] = total;
     total += e.bx * ((h->d == 2) ? (e.by + e.zchunk - 1) / e.zchunk : e.by);
   }
-  if (b->batch_cs) cudaFree(b->batch_cs);
-  if (b->batch_cs_start) cudaFree(b->batch_cs_start);
+  dev_free(b, b->batch_cs);
+  dev_free(b, b->batch_cs_start);
   b->batch_cs = nullptr;
   b->batch_cs_start = nullptr;
-  if (cudaMalloc(&b->batch_cs, sizeof(BatchCS) * P) != cudaSuccess) return LBM_ENOMEM;
-  if (cudaMalloc(&b->batch_cs_start, sizeof(int) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(b, &b->batch_cs, sizeof(BatchCS) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(b, (void**)&b->batch_cs_start, sizeof(int) * P) != cudaSuccess) return LBM_ENOMEM;
   if (cudaMemcpy(b->batch_cs, tab.data(), sizeof(BatchCS) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->batch_cs_start, start.data(), sizeof(int) * P, cudaMemcpyHostToDevice) != cudaSuccess)
     return LBM_ECUDA;

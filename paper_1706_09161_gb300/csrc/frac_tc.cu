@@ -651,8 +651,8 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   const int ldp = (n[0] + 7) / 8 * 8;
   p->ldp = ldp;
   const size_t split_elems = (size_t)ldp * n[1] * n[2];
-  if (cudaMalloc(&h->dev.Chi, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
-  if (cudaMalloc(&h->dev.Clo, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(h, (void**)&h->dev.Chi, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(h, (void**)&h->dev.Clo, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
   cudaMemset(h->dev.Chi, 0, split_elems * E);
   cudaMemset(h->dev.Clo, 0, split_elems * E);
   if (E == 4) {
@@ -660,8 +660,8 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
     for (int mu = 1; mu < h->d; ++mu) {
       p->tg[mu] = (n[mu] + 3) / 4;
       const size_t cnt = (size_t)4 * p->tg[mu] * p->tpx * (h->sp.nodes / n[0] / n[mu]);
-      if (cudaMalloc(&p->ct_hi[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
-      if (cudaMalloc(&p->ct_lo[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
+      if (dev_alloc(h, &p->ct_hi[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
+      if (dev_alloc(h, &p->ct_lo[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
       cudaMemset(p->ct_hi[mu], 0, cnt * 4);
       cudaMemset(p->ct_lo[mu], 0, cnt * 4);
     }
@@ -674,9 +674,9 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
     ldk[mu] = (n[mu] + 7) / 8 * 8;
     ktot += (size_t)ldk[mu] * n[mu];
   }
-  if (cudaMalloc(&h->dev.Khi, ktot * E) != cudaSuccess) return LBM_ENOMEM;
-  if (cudaMalloc(&h->dev.Klo, ktot * E) != cudaSuccess) return LBM_ENOMEM;
-  if (p->kparts == 3 && cudaMalloc(&h->dev.Kl2, ktot * E) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(h, (void**)&h->dev.Khi, ktot * E) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(h, (void**)&h->dev.Klo, ktot * E) != cudaSuccess) return LBM_ENOMEM;
+  if (p->kparts == 3 && dev_alloc(h, (void**)&h->dev.Kl2, ktot * E) != cudaSuccess) return LBM_ENOMEM;
   std::vector<uint8_t> hbuf(ktot * E, 0), lbuf(ktot * E, 0), l2buf(p->kparts == 3 ? ktot * E : 0, 0);
   size_t koff[3] = {0, 0, 0};
   size_t off = 0;
@@ -846,10 +846,10 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
   // kernels that read F add them in rank order
   const size_t need = (size_t)ks * h->d * h->sp.nodes;
   if (need > p->f_elems) {
-    if (h->dev.F) cudaFree(h->dev.F);
+    dev_free(h, h->dev.F);
     h->dev.F = nullptr;
     p->f_elems = 0;
-    if (cudaMalloc(&h->dev.F, need * 4) != cudaSuccess) return LBM_ENOMEM;
+    if (dev_alloc(h, (void**)&h->dev.F, need * 4) != cudaSuccess) return LBM_ENOMEM;
     p->f_elems = need;
   }
   P.F = static_cast<float*>(h->dev.F);
@@ -879,11 +879,16 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
 }
 
 void tc_release(lbm_s* h) {
+  if (h->tc)
+    for (int mu = 0; mu < 3; ++mu) {
+      dev_free(h, h->tc->ct_hi[mu]);
+      dev_free(h, h->tc->ct_lo[mu]);
+    }
   delete h->tc;
   h->tc = nullptr;
-  if (h->batch_tc_maps) cudaFree(h->batch_tc_maps);
-  if (h->batch_tc_prm) cudaFree(h->batch_tc_prm);
-  if (h->batch_tc_start) cudaFree(h->batch_tc_start);
+  dev_free(h, h->batch_tc_maps);
+  dev_free(h, h->batch_tc_prm);
+  dev_free(h, h->batch_tc_start);
   h->batch_tc_maps = h->batch_tc_prm = nullptr;
   h->batch_tc_start = nullptr;
 }
@@ -902,9 +907,9 @@ int tc_batch_prepare(lbm_s* b) {
     start[i] = total;
     total += t->prm.total_tiles;
   }
-  if (cudaMalloc(&b->batch_tc_maps, sizeof(TcMaps) * P) != cudaSuccess) return LBM_ENOMEM;
-  if (cudaMalloc(&b->batch_tc_prm, sizeof(TcParams) * P) != cudaSuccess) return LBM_ENOMEM;
-  if (cudaMalloc(&b->batch_tc_start, sizeof(int) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(b, (void**)&b->batch_tc_maps, sizeof(TcMaps) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(b, (void**)&b->batch_tc_prm, sizeof(TcParams) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(b, (void**)&b->batch_tc_start, sizeof(int) * P) != cudaSuccess) return LBM_ENOMEM;
   if (cudaMemcpy(b->batch_tc_maps, maps.data(), sizeof(TcMaps) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->batch_tc_prm, prm.data(), sizeof(TcParams) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->batch_tc_start, start.data(), sizeof(int) * P, cudaMemcpyHostToDevice) != cudaSuccess)

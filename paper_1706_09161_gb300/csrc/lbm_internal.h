@@ -50,8 +50,16 @@ struct DeviceState {
 
 }  // namespace lbm
 
+// device-memory hooks a handle was created with (lbm_set_allocator; null: cudaMalloc)
+struct DevMem {
+  lbm_alloc_fn alloc = nullptr;
+  lbm_free_fn release = nullptr;
+  void* ctx = nullptr;
+};
+
 struct lbm_s {
   lbm_params prm;
+  DevMem mem;
   int d = 2, Q = 5;
   int elem = 8;                        // bytes per real (8 FP64, 4 FP32 forms)
   lbm::StepParams sp;
@@ -89,6 +97,10 @@ struct lbm_s {
 };
 
 namespace lbm {
+
+// a handle's device memory: through its hooks, else cudaMalloc / cudaFree
+cudaError_t dev_alloc(const lbm_s* h, void** p, size_t bytes);
+void dev_free(const lbm_s* h, void* p);
 
 // ---- kernels (launchers return cudaGetLastError of the launch)
 // fractional operator, SIMT: F_mu = K_mu applied along axis mu, for all mu

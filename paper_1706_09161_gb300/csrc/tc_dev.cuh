@@ -69,12 +69,6 @@ struct TcPlan {
   void* ct_lo[3] = {nullptr, nullptr, nullptr};
   int tg[3] = {0, 0, 0};  // groups of 4 along axis mu: ceil(n_mu / 4)
   int tpx = 0;            // x pitch of the regrouped copies: n0 rounded up to 16
-  ~TcPlan() {
-    for (int mu = 0; mu < 3; ++mu) {
-      if (ct_hi[mu]) cudaFree(ct_hi[mu]);
-      if (ct_lo[mu]) cudaFree(ct_lo[mu]);
-    }
-  }
 };
 
 namespace {
@@ -121,14 +115,14 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; false (and flag bit 2) after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flag) {
+// Bounded wait on an mbarrier phase; false (and flag bit 2) after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flag, long long limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
     for (int i = 0; i < 64; ++i)
       if (mbar_try(bar, parity)) return true;
-    if (global_ns() - t0 > (unsigned long long)kWaitNs) {
+    if (global_ns() - t0 > (unsigned long long)limit_ns) {
       atomicOr(flag, 2);
       return false;
     }

@@ -90,6 +90,8 @@ def _load() -> ctypes.CDLL:
         "lbm_sync": (ctypes.c_int, [vp]),
         "lbm_get_stream": (ctypes.c_int, [vp, P(vp)]),
         "lbm_launches_per_step": (ctypes.c_int, [vp, P(ctypes.c_int)]),
+        "lbm_wait_check": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp]),
+        "lbm_set_allocator": (ctypes.c_int, [vp, vp, vp]),
         "lbm_frac_matrix": (ctypes.c_int, [P(lbm_params), ctypes.c_int, dp]),
         "lbm_grad": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), dp, ctypes.c_int, dp, dp]),
         "lbm_frac_matrix_grad": (ctypes.c_int, [P(lbm_params), ctypes.c_int, dp, dp]),
@@ -110,7 +112,8 @@ _lib = _load()
 
 # Declared C entry points, re-exported under their own names.
 EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_read_C", "lbm_batch_mass", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f", "lbm_state_size", "lbm_save", "lbm_load", "lbm_autotune", "lbm_configure",
-            "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_frac_matrix",
+            "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_wait_check", "lbm_set_allocator",
+            "lbm_frac_matrix",
             "lbm_grad", "lbm_frac_matrix_grad", "lbm_digamma", "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
 
 
@@ -301,6 +304,48 @@ def lbm_mass_static(x_dev: int, elem_bytes: int, n: int, sum_dev: int, stream: O
     """Return code of the static-scratch FP64 sum (the result lands in *sum_dev)."""
     return int(_lib.lbm_mass_static(ctypes.c_void_p(x_dev), int(elem_bytes), int(n), ctypes.c_void_p(sum_dev),
                                      ctypes.c_void_p(stream or 0)))
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_hook_refs = []  # callbacks stay alive for the handles created with them
+
+
+def lbm_set_allocator(alloc, release, ctx: Optional[int] = None) -> None:
+    """Install device-memory hooks (ctypes callbacks of the C signatures) for handles
+    created from now on; (None, None) restores cudaMalloc/cudaFree."""
+    alloc = _ALLOC_FN(alloc) if alloc is not None else None
+    release = _FREE_FN(release) if release is not None else None
+    _hook_refs.append((alloc, release))
+    a = ctypes.cast(alloc, ctypes.c_void_p) if alloc is not None else None
+    r = ctypes.cast(release, ctypes.c_void_p) if release is not None else None
+    _check(_lib.lbm_set_allocator(a, r, ctypes.c_void_p(ctx or 0)), "lbm_set_allocator")
+
+
+def use_torch_allocator(on: bool = True) -> None:
+    """Handles created from now on take their device memory from PyTorch's caching
+    allocator (on the handle's stream) and give it back there; off: cudaMalloc again."""
+    if not on:
+        lbm_set_allocator(None, None)
+        return
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+        except Exception:  # out of memory: the library reports LBM_ENOMEM
+            return None
+
+    def release(ptr, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    lbm_set_allocator(alloc, release)
+
+
+def lbm_wait_check(complete: bool, limit_us: int, stream: Optional[int] = None) -> int:
+    """Return code of one bounded device-side wait on a barrier completed (LBM_OK) or
+    left incomplete (LBM_ERR_TIMEOUT after limit_us microseconds)."""
+    return int(_lib.lbm_wait_check(1 if complete else 0, int(limit_us), ctypes.c_void_p(stream or 0)))
 
 
 def lbm_grad(h: int, snap_steps, obs: np.ndarray, ckpt_every: int, d: int):
