@@ -192,6 +192,7 @@ int lbm_write_f(lbm_t h, const double* f_host);
  * handle's own data and keeps the fastest:
  *   tensor-core forms, single problem: the operator's column tile width (64, 128, 256),
  *     its contraction split (1, 2, 4, 8 partial sums) or the persistent kernel;
+ *   FP32 form, single problem: the SIMT operator's contraction split (1, 2, 4, 8);
  *   every handle: collide-stream tile rows per block (2-D) or z chunks (3-D);
  *   batches: tile rows per block of every 2-D member.
  * The operator plan is searched first with the current collide-stream setting, then the
@@ -209,8 +210,10 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len);
  * chunk > 0 sets the collide-stream tile rows (2-D) or z chunks (3-D), 0 the built-in
  * choice; fused = 1 runs whole steps in one cooperative kernel (2-D bf16 split with a
  * per-tile plan of 64/128 columns split 2 or 4, rows TMA can address; LBM_ENOTSUP
- * otherwise).  Non-tensor-core handles accept only bn = ks = persist = fused = 0.
- * Asynchronous. */
+ * otherwise).  FP32 single problems take ks > 0 as the SIMT operator's contraction split
+ * (1, 2, 4, 8, at most the 32-wide contraction blocks of the shortest axis) with
+ * bn = persist = fused = 0; other non-tensor-core handles accept only
+ * bn = ks = persist = fused = 0.  Synchronises when the split needs a larger F. */
 int lbm_configure(lbm_t h, int bn, int ks, int persist, int chunk, int fused);
 
 long long lbm_state_size(lbm_t h);

@@ -527,7 +527,11 @@ int run_adjoint(lbm_s* h, const AdjHooks& hooks, int nsnap, const int* snaps, co
       CK(cudaMemcpyAsync(sf + (size_t)i * Q * nodes, h->dev.f[c2], E * Q * nodes, cudaMemcpyDeviceToDevice, s));
       CK(cudaMemcpyAsync(sC + (size_t)i * nodes, h->dev.C, E * nodes, cudaMemcpyDeviceToDevice, s));
       CK(launch_frac_simt(h, h->dev.C, h->dev.F, s));
-      CK(cudaMemcpyAsync(sF + (size_t)i * D * nodes, h->dev.F, E * D * nodes, cudaMemcpyDeviceToDevice, s));
+      if (h->sp.ksum > 1)  // the FP32 operator's partial sums, added as the collide-stream kernel adds them
+        CK(launch_sum_partials(reinterpret_cast<const float*>(h->dev.F), h->sp.ksum, h->sp.pstride,
+                               reinterpret_cast<float*>(sF + (size_t)i * D * nodes), (long long)D * nodes, s));
+      else
+        CK(cudaMemcpyAsync(sF + (size_t)i * D * nodes, h->dev.F, E * D * nodes, cudaMemcpyDeviceToDevice, s));
       CK(launch_collide_stream(h, h->dev.f[c2], h->dev.f[c2 ^ 1], h->dev.C, s));
       c2 ^= 1;
     }

@@ -394,6 +394,11 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   }
   const long long nodes = h->sp.nodes;
   const size_t E = h->elem;
+  if (prm->precision == LBM_FP32 && !batched) {
+    // small FP32 problems: the SIMT operator's contraction split (F holds the partials)
+    h->sp.ksum = lbm::simt_ksplit(h);
+    h->sp.pstride = h->sp.ksum > 1 ? (long long)h->d * nodes : 0;
+  }
   long long ksz = 0;
   for (int mu = 0; mu < h->d; ++mu) ksz += (long long)prm->grid[mu] * prm->grid[mu];
   h->reduce_blocks = lbm::reduce_blocks_for(nodes);
@@ -401,7 +406,8 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   if ((rc = alloc_bytes(h, &h->dev.f[1], E * h->Q * nodes))) return fail(rc);
   if ((rc = alloc_bytes(h, &h->dev.C, E * nodes))) return fail(rc);
   if ((rc = alloc_bytes(h, &h->dev.C0, E * nodes))) return fail(rc);
-  if ((rc = alloc_bytes(h, &h->dev.F, E * h->d * nodes))) return fail(rc);
+  if ((rc = alloc_bytes(h, &h->dev.F, E * h->d * nodes * h->sp.ksum))) return fail(rc);
+  h->f_elems = (size_t)h->d * nodes * h->sp.ksum;
   if ((rc = alloc_bytes(h, &h->dev.K, E * ksz))) return fail(rc);
   if ((rc = alloc_bytes(h, &h->dev.KT, E * ksz))) return fail(rc);
   if ((rc = alloc_bytes(h, (void**)&h->dev.stage, sizeof(double) * (size_t)(nodes > ksz ? nodes : ksz)))) return fail(rc);
@@ -786,8 +792,33 @@ struct TuneCfg {
   int fused = 0;
 };
 
-// the handle's launch configuration set to c (operator plan for tensor-core handles,
-// collide-stream chunk for every handle); captured graphs are dropped
+// FP32 SIMT operator of a single problem: contraction split ks (1, 2, 4 or 8, at most
+// the contraction blocks of 32 of the shortest axis); F grows to ks partial sums and the
+// collide-stream tensor maps are re-encoded for it
+int simt_replan(lbm_s* h, int ks) {
+  if (!(ks == 1 || ks == 2 || ks == 4 || ks == 8)) return LBM_EINVAL;
+  int kbmin = 1 << 30;
+  for (int mu = 0; mu < h->d; ++mu) kbmin = std::min(kbmin, (h->sp.n[mu] + 31) / 32);
+  if (ks > kbmin) return LBM_EINVAL;
+  const size_t need = (size_t)ks * h->d * h->sp.nodes;
+  if (need > h->f_elems) {
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    lbm::dev_free(h, h->dev.F);
+    h->dev.F = nullptr;
+    h->f_elems = 0;
+    const int rc = alloc_bytes(h, &h->dev.F, need * sizeof(float));
+    if (rc) return rc;
+    h->f_elems = need;
+  }
+  h->sp.ksum = ks;
+  h->sp.pstride = ks > 1 ? (long long)h->d * h->sp.nodes : 0;
+  lbm::cs_release(h);
+  return lbm::cs_prepare(h);
+}
+
+// the handle's launch configuration set to c (operator plan for tensor-core handles, the
+// contraction split of the FP32 SIMT operator, collide-stream chunk for every handle);
+// captured graphs are dropped
 int apply_cfg(lbm_s* h, const TuneCfg& c) {
   int rc = LBM_OK;
   if (h->is_batch()) {
@@ -811,6 +842,7 @@ int apply_cfg(lbm_s* h, const TuneCfg& c) {
       LBM_CUDA(lbm::launch_split_C(h, h->stream));
     } else {
       h->cs_chunk = c.chunk;
+      if (c.ks > 0 && h->elem == 4 && (rc = simt_replan(h, c.ks))) return rc;
     }
   }
   drop_graphs(h);
@@ -866,6 +898,8 @@ int lbm_configure(lbm_t h, int bn, int ks, int persist, int chunk, int fused) {
       c.ks = ks > 0 ? ks : 1;
       c.persist = persist ? 1 : 0;
     }
+  } else if (!h->is_batch() && h->elem == 4 && bn == 0 && !persist && !fused) {
+    c.ks = ks > 0 ? ks : h->sp.ksum;  // FP32 SIMT operator: its contraction split only
   } else if (bn > 0 || ks > 0 || persist || fused) {
     return LBM_EINVAL;  // no tensor-core operator to plan
   }
@@ -881,6 +915,8 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
   if (rc) return rc;
   TuneCfg cur{0, 0, 0, h->cs_chunk > 0 ? h->cs_chunk : lbm::cs_chunk_default(h), h->fused ? 1 : 0};
   if (!h->is_batch() && h->tc) lbm::tc_config(h, &cur.bn, &cur.ks, &cur.persist);
+  const bool simt32 = !h->is_batch() && !h->tc && h->elem == 4;  // FP32 SIMT operator
+  if (simt32) cur.ks = h->sp.ksum;
   // candidate chunks
   std::vector<int> chunks;
   if (h->is_batch()) {
@@ -893,8 +929,14 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
     for (int c : {d0, d0 / 2, d0 + d0 / 2, d0 * 2, 1}) if (c >= 1 && c <= h->sp.n[2]) chunks.push_back(c);
   }
   if (std::find(chunks.begin(), chunks.end(), cur.chunk) == chunks.end()) chunks.push_back(cur.chunk);
-  // candidate operator plans (tensor-core single problems)
+  // candidate operator plans (tensor-core single problems; the FP32 SIMT split)
   std::vector<TuneCfg> ops;
+  if (simt32)
+    for (int ks : {1, 2, 4, 8}) {
+      int kbmin = 1 << 30;
+      for (int mu = 0; mu < h->d; ++mu) kbmin = std::min(kbmin, (h->sp.n[mu] + 31) / 32);
+      if (ks <= kbmin) ops.push_back({0, ks, 0, cur.chunk});
+    }
   if (!h->is_batch() && h->tc) {
     const int kbmin = lbm::tc_kbmin(h);
     const bool five = h->prm.precision == LBM_FP32_BF16SPLIT5;  // per-tile kernel, 64/128 columns
@@ -960,6 +1002,9 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
                     "%soperator %s bn=%d ks=%d, collide chunk=%d: %.2f us/step (default %.2f)",
                     best.fused ? "fused step, " : "", best.persist ? "persistent" : "per-tile", best.bn, best.ks,
                     best.chunk, 1e3 * best_ms / nsteps, 1e3 * base_ms / nsteps);
+    else if (simt32)
+      std::snprintf(desc, (size_t)desc_len, "operator SIMT ks=%d, collide chunk=%d: %.2f us/step (default %.2f)",
+                    best.ks, best.chunk, 1e3 * best_ms / nsteps, 1e3 * base_ms / nsteps);
     else
       std::snprintf(desc, (size_t)desc_len, "collide chunk=%d: %.2f us/step (default %.2f)", best.chunk,
                     1e3 * best_ms / nsteps, 1e3 * base_ms / nsteps);

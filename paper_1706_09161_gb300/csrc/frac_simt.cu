@@ -7,7 +7,10 @@
 //   axis y, z:         F[b][n][c] = sum_l K[n][l] C[b][l][c] = K * C_b  (b = outer planes, c = inner)
 // Both are written as a row-major NN GEMM D = A B (A: M x K, B: K x N), batched
 // over b with strides; K^T is stored explicitly for the x axis.  One launch covers
-// every axis: a table maps each block to (axis, batch, tile).
+// every axis: a table maps each block to (axis, batch, tile, contraction slice).  Small
+// FP32 problems split the contraction over ks blocks per tile (enough blocks to fill
+// the GPU twice); slice r writes its partial sum to F + r * pstride and the consumers
+// add the ks partials in order, as for the tensor-core operator's split.
 #include <algorithm>
 
 #include "lbm_internal.h"
@@ -28,6 +31,8 @@ struct GemmAxis {
 struct GemmPlan {
   GemmAxis ax[3];
   int naxes;
+  int ks;              // contraction slices per tile
+  long long pstride;   // elements between the slices' partial outputs
   long long total;
 };
 
@@ -55,14 +60,20 @@ frac_simt_kernel(const GemmPlan P) {
   while (a + 1 < P.naxes && b >= P.ax[a + 1].begin) ++a;
   const GemmAxis& X = P.ax[a];
   b -= X.begin;
+  const int rank = static_cast<int>(b % P.ks);  // contraction slice
+  b /= P.ks;
   const long long per = (long long)X.tm * X.tn;
   const long long bz = b / per;
   const int r = static_cast<int>(b - bz * per);
   const int m0 = (r / X.tn) * BM, n0 = (r % X.tn) * BN;
   const real* __restrict__ A = static_cast<const real*>(X.A) + bz * X.sA;
   const real* __restrict__ B = static_cast<const real*>(X.B) + bz * X.sB;
-  real* __restrict__ Cm = static_cast<real*>(X.C) + bz * X.sC;
-  const int M = X.M, N = X.N, K = X.K;
+  real* __restrict__ Cm = static_cast<real*>(X.C) + bz * X.sC + rank * P.pstride;
+  const int M = X.M, N = X.N;
+  // slices of whole BK blocks: [kbeg, kend)
+  const int nkb = (X.K + BK - 1) / BK;
+  const int kbeg = (rank * nkb / P.ks) * BK;
+  const int K = min(X.K, ((rank + 1) * nkb / P.ks) * BK);
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
 
@@ -102,11 +113,11 @@ frac_simt_kernel(const GemmPlan P) {
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = static_cast<real>(0);
 
-  fetch(0);
+  fetch(kbeg);
   stash(0);
   __syncthreads();
   int buf = 0;
-  for (int k0 = 0; k0 < K; k0 += BK) {
+  for (int k0 = kbeg; k0 < K; k0 += BK) {
     const bool more = k0 + BK < K;
     if (more) fetch(k0 + BK);
 #pragma unroll
@@ -139,6 +150,7 @@ frac_simt_kernel(const GemmPlan P) {
 
 void add_axis(GemmPlan& P, int BM, int BN, int M, int N, int K, int batch, const void* A, long long lda, long long sA,
               const void* B, long long ldb, long long sB, void* C, long long ldc, long long sC) {
+  // (blocks of this axis = tiles x batch x P.ks)
   GemmAxis& X = P.ax[P.naxes++];
   X.A = A; X.B = B; X.C = C;
   X.lda = lda; X.sA = sA; X.ldb = ldb; X.sB = sB; X.ldc = ldc; X.sC = sC;
@@ -146,20 +158,23 @@ void add_axis(GemmPlan& P, int BM, int BN, int M, int N, int K, int batch, const
   X.tm = (M + BM - 1) / BM;
   X.tn = (N + BN - 1) / BN;
   X.begin = P.total;
-  P.total += (long long)X.tm * X.tn * batch;
+  P.total += (long long)X.tm * X.tn * batch * P.ks;
 }
 
 // transpose = false: F_mu = K_mu applied along mu to C (one input for every axis);
 // transpose = true:  F_mu = K_mu^T applied along mu to C_mu (C holds one field per axis,
 // field mu at C + mu * cstride)
 template <typename real, int BM, int BN>
-GemmPlan make_plan(const lbm_s* h, const real* C, real* F, bool transpose, long long cstride) {
+GemmPlan make_plan(const lbm_s* h, const real* C, real* F, bool transpose, long long cstride, int ks = 1,
+                   long long pstride = 0) {
   const int n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
   const long long nodes = h->sp.nodes;
   const real* K = static_cast<const real*>(transpose ? h->dev.KT : h->dev.K);
   const real* KT = static_cast<const real*>(transpose ? h->dev.K : h->dev.KT);
   if (!transpose) cstride = 0;
   GemmPlan P{};
+  P.ks = ks;
+  P.pstride = pstride;
   long long koff = 0;
   // axis x: F_0 = C (rows x n0) * K_0^T
   add_axis(P, BM, BN, (int)(nodes / n0), n0, n0, 1, C, n0, 0, KT + koff, n0, 0, F, n0, 0);
@@ -175,12 +190,14 @@ GemmPlan make_plan(const lbm_s* h, const real* C, real* F, bool transpose, long 
   return P;
 }
 
-// 64 x 64 tiles where they give two blocks per SM, else 32 x 32
+// 64 x 64 tiles where they give two blocks per SM (with the handle's contraction split,
+// forward operator only), else 32 x 32
 template <typename real>
 cudaError_t frac_all_axes(const lbm_s* h, const real* C, real* F, cudaStream_t s, bool transpose = false,
                           long long cstride = 0) {
-  const GemmPlan big = make_plan<real, 64, 64>(h, C, F, transpose, cstride);
-  if (big.total >= 2 * 152) {
+  const int ks = transpose ? 1 : h->sp.ksum;
+  const GemmPlan big = make_plan<real, 64, 64>(h, C, F, transpose, cstride, ks, ks > 1 ? h->sp.pstride : 0);
+  if (big.total >= 2 * 152 || ks > 1) {
     frac_simt_kernel<real, 64, 64, 4, 4><<<static_cast<unsigned>(big.total), 256, 0, s>>>(big);
   } else {
     const GemmPlan small = make_plan<real, 32, 32>(h, C, F, transpose, cstride);
@@ -190,6 +207,20 @@ cudaError_t frac_all_axes(const lbm_s* h, const real* C, real* F, cudaStream_t s
 }
 
 }  // namespace
+
+int simt_ksplit(const lbm_s* h) {
+  if (h->elem != 4) return 1;
+  const long long n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
+  auto t64 = [](long long m, long long n) { return ((m + 63) / 64) * ((n + 63) / 64); };
+  // 64 x 64 tiles of the forward plan: x (nodes / n0 x n0), y (n1 x n0, n2 of them), z (n2 x n0 n1)
+  long long tiles = t64(h->sp.nodes / n0, n0) + t64(n1, n0) * n2;
+  if (h->d == 3) tiles += t64(n2, n0 * n1);
+  int kbmin = 1 << 30;
+  for (int mu = 0; mu < h->d; ++mu) kbmin = std::min(kbmin, (h->sp.n[mu] + 31) / 32);  // BK = 32 (FP32)
+  int ks = 1;
+  while (ks * 2 <= 8 && ks * 2 <= kbmin && tiles * ks < 2 * 152) ks *= 2;
+  return ks;
+}
 
 cudaError_t launch_frac_simt_T(const lbm_s* h, const void* in, long long in_stride, void* out, cudaStream_t s) {
   if (h->elem == 8)

@@ -72,6 +72,7 @@ struct lbm_s {
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int graph_steps = 0;                 // steps per captured graph (even)
   int launches_per_step = 0;
+  size_t f_elems = 0;                  // capacity of dev.F (elements) for the SIMT operator's partials
   // programmatic dependent launch between the operator and collide-stream: only when both
   // grids run in a single wave (measured: with multi-wave 3-D grids it costs ~30%)
   bool pdl = false;
@@ -105,6 +106,9 @@ void dev_free(const lbm_s* h, void* p);
 // ---- kernels (launchers return cudaGetLastError of the launch)
 // fractional operator, SIMT: F_mu = K_mu applied along axis mu, for all mu
 cudaError_t launch_frac_simt(const lbm_s* h, const void* C, void* F, cudaStream_t s);
+// contraction split of the FP32 SIMT operator for a single problem: F then holds that
+// many partial sums ([rank][axis][node], like the tensor-core split), 1 for FP64
+int simt_ksplit(const lbm_s* h);
 // tensor-core split-precision fractional operator (tcgen05); returns
 // cudaErrorNotSupported when the handle's shape is not covered
 cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s);
@@ -122,6 +126,9 @@ cudaError_t launch_convert_out(const void* src, int elem, double* dst_f64, long 
 // dst_f64[i] = sum_{s < k} src[s * stride + i], FP32 partials added in order of s
 cudaError_t launch_sum_partials_out(const float* src, int k, long long stride, double* dst_f64, long long n,
                                     cudaStream_t s);
+// dst[i] = sum_{s < k} src[s * stride + i] in FP32, in order of s (as the collide-stream
+// kernels add the operator's partial sums)
+cudaError_t launch_sum_partials(const float* src, int k, long long stride, float* dst, long long n, cudaStream_t s);
 // mass reduction: partials then final
 cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
 // split C into hi/lo operands for the tensor-core path (tf32: also the transposed copies)

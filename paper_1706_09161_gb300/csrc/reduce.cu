@@ -68,6 +68,15 @@ __global__ void sum_partials_out_kernel(const float* __restrict__ src, int k, lo
   }
 }
 
+__global__ void sum_partials_kernel(const float* __restrict__ src, int k, long long stride, float* __restrict__ dst,
+                                    long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float acc = src[i];
+    for (int s = 1; s < k; ++s) acc += src[s * stride + i];
+    dst[i] = acc;
+  }
+}
+
 int blocks_for(long long n) {
   long long b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -102,6 +111,11 @@ cudaError_t launch_convert_in(const void* src, void* dst, int elem, long long n,
 cudaError_t launch_sum_partials_out(const float* src, int k, long long stride, double* dst, long long n,
                                     cudaStream_t s) {
   sum_partials_out_kernel<<<blocks_for(n), 256, 0, s>>>(src, k, stride, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const float* src, int k, long long stride, float* dst, long long n, cudaStream_t s) {
+  sum_partials_kernel<<<blocks_for(n), 256, 0, s>>>(src, k, stride, dst, n);
   return cudaGetLastError();
 }
 

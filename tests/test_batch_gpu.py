@@ -49,6 +49,8 @@ def test_batch_equals_single_problem_handles(L):
         got = [b.C(i) for i in range(len(probs))]
     for i, (pb, C0) in enumerate(zip(probs, fields)):
         with L.Lattice(pb, C0, "fp32") as lat:
+            lat.configure(0, 1)  # single FP32 problems split the contraction by default
+            lat.reset()          # initial populations from the unsplit operator too
             lat.step(40)
             assert np.array_equal(lat.C(), got[i])
 

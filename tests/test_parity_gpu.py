@@ -260,3 +260,33 @@ def test_write_f_refreshes_split_operands(L):
         lat.step(5)
         ref.step(5)
         assert np.array_equal(lat.f(), ref.f())
+
+
+# ---------------------------------------------------------------- FP32 SIMT contraction split
+
+@pytest.mark.parametrize("grid", [(130, 70), (64, 48, 40)])
+def test_fp32_contraction_split_matches_oracle(L, grid):
+    """Every contraction split of the FP32 SIMT operator (partial sums added by the
+    consumers) gives the oracle's F and steps, also when the split changes mid-run."""
+    rng = np.random.default_rng(161 + len(grid))
+    pb = W.random_problem(rng, len(grid), "mrt", grid)
+    C0 = W.random_field(rng, grid)
+    ops = O.Operators(pb)
+    F = O.fractional_terms(ops, O.concentration(O.init_populations(ops, torch.tensor(C0))))
+    n = 6
+    C_ref = O.run_C(pb, C0, 2 * n).numpy()
+    kbmin = min((s + 31) // 32 for s in grid)
+    for ks in (1, 2, 4, 8):
+        if ks > kbmin:
+            with L.Lattice(pb, C0, "fp32") as lat:
+                with pytest.raises(L.LBMError):
+                    lat.configure(0, ks)
+            continue
+        with L.Lattice(pb, C0, "fp32") as lat:
+            lat.configure(0, ks)
+            for mu in range(len(grid)):
+                assert rel_l2(lat.F(mu), F[mu].numpy()) < 1e-6, (ks, mu)
+            lat.step(n)
+            lat.configure(0, 1 if ks > 1 else min(2, kbmin))
+            lat.step(n)
+            assert rel_l2(lat.C(), C_ref) < arith_bounds.bound(pb, C0, 2 * n, "fp32"), ks
