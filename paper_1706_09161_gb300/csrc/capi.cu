@@ -948,6 +948,7 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
         ops.push_back({bn, ks, 0, cur.chunk});
       }
     if (!five && lbm::tc_count_tiles(h, 128) >= 152) ops.push_back({128, 1, 1, cur.chunk});
+    if (!five && lbm::tc_count_tiles(h, 256) >= 152) ops.push_back({256, 1, 1, cur.chunk});
     // the fused step where the plan is one it covers (2-D bf16, 64/128 columns, split 2 or 4)
     const size_t nops = ops.size();
     for (size_t i = 0; i < nops; ++i)

@@ -224,10 +224,11 @@ frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
 constexpr int PBN = 128;
 constexpr int kPersistThreads = 192;
 
-template <int E>
+// BN = 128 (three ring stages) or 256 (two; the double accumulator then fills TMEM)
+template <int E, int BN = PBN>
 struct PCfg {
-  using G = Cfg<E, PBN>;
-  static constexpr int STAGES = 3;
+  using G = Cfg<E, BN>;
+  static constexpr int STAGES = BN == 128 ? 3 : 2;
   static constexpr uint32_t CHUNK = 32 * BM * 4;  // 32 output rows x 128 x (FP32)
   static constexpr size_t RING = (size_t)STAGES * G::STAGE;
   static constexpr size_t SMEM = RING + 2 * CHUNK + 1024 /*align*/ + 256 /*barriers*/;
@@ -240,9 +241,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // Locate(t, maps, prm, cid): the problem and local tile index of global tile t
-template <int E, class Locate>
+template <int E, int BN, class Locate>
 __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, int* flag, uint8_t* smem_raw) {
-  using C = PCfg<E>;
+  using C = PCfg<E, BN>;
   using G = typename C::G;
   constexpr int STAGES = C::STAGES;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -272,7 +273,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * PBN)
+                 "r"(2 * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -293,7 +294,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
       const TcParams* P;
       int cid;
       locate(t, maps, P, cid);
-      const TileAt tl = decode_tile(*P, cid, PBN);
+      const TileAt tl = decode_tile(*P, cid, BN);
       const int nkb = P->ax[tl.mu].kblocks;
       for (int kb = 0; kb < nkb; ++kb, ++r) {
         const int s = r % STAGES;
@@ -302,7 +303,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
           break;
         }
         mbar_expect_tx(&full[s], G::STAGE);
-        load_stage<E, PBN>(*maps, tl, kb * G::BK, smem + (size_t)s * G::STAGE, &full[s]);
+        load_stage<E, BN>(*maps, tl, kb * G::BK, smem + (size_t)s * G::STAGE, &full[s]);
       }
     }
     // every issued copy has landed before the CTA may leave (bounded)
@@ -316,12 +317,12 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
       const TcParams* P;
       int cid;
       locate(t, maps, P, cid);
-      const TileAt tl = decode_tile(*P, cid, PBN);
+      const TileAt tl = decode_tile(*P, cid, BN);
       const int nkb = P->ax[tl.mu].kblocks;
       const int b = i & 1;
       if (i >= 2 && !mbar_wait(&tempty[b], ((i >> 1) - 1) & 1, flag)) break;
       tc_fence_after();
-      const uint32_t d = tmem + b * PBN;
+      const uint32_t d = tmem + b * BN;
       const int amode = a_mode<E>(tl.mu);
       for (int kb = 0; kb < nkb; ++kb, ++r) {
         const int s = r % STAGES;
@@ -330,7 +331,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
           break;
         }
         tc_fence_after();
-        mma_stage<E, PBN>(d, smem_u32(smem + (size_t)s * G::STAGE), amode, kb == 0);
+        mma_stage<E, BN>(d, smem_u32(smem + (size_t)s * G::STAGE), amode, kb == 0);
         mma_commit(&empty[s]);
       }
       if (ok) mma_commit(&tfull[b]);
@@ -347,7 +348,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
       const TcParams* P;
       int cid;
       locate(t, maps, P, cid);
-      const TileAt tl = decode_tile(*P, cid, PBN);
+      const TileAt tl = decode_tile(*P, cid, BN);
       const int b = i & 1;
       if (et == 0) *s_ok = mbar_wait(&tfull[b], (i >> 1) & 1, flag) ? 1 : 0;
       epi_sync();
@@ -357,10 +358,10 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
       float* F = P->F + (long long)tl.mu * nodes;
       const int n0 = P->n0, n1 = P->n1;
       const int lim = (tl.mu == 0) ? n1 : P->ax[tl.mu].side;  // output rows that exist
-      for (int c0 = 0; c0 < PBN; c0 += 32, ++chunk) {
+      for (int c0 = 0; c0 < BN; c0 += 32, ++chunk) {
         float v[32];
-        tmem_ld32(tmem + b * PBN + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
-        if (c0 + 32 >= PBN) {
+        tmem_ld32(tmem + b * BN + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
+        if (c0 + 32 >= BN) {
           // the accumulator is drained: hand it back to the MMA warp
           tc_fence_before();
         }
@@ -373,7 +374,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           epi_sync();
           if (et == 0) {
-            if (c0 + 32 >= PBN) mbar_arrive(&tempty[b]);
+            if (c0 + 32 >= BN) mbar_arrive(&tempty[b]);
             if (tl.ncol0 + c0 < lim) {
               int c1, c2;
               if (tl.mu == 2) {
@@ -403,7 +404,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
               if (n < lim) F[idx] = v[j];
             }
           }
-          if (c0 + 32 >= PBN) {
+          if (c0 + 32 >= BN) {
             epi_sync();
             if (et == 0) mbar_arrive(&tempty[b]);
           }
@@ -419,7 +420,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
     if (threadIdx.x == 32) mbar_wait(drain, 0, flag);
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * PBN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
   }
 }
 
@@ -451,11 +452,11 @@ struct LocateBatch {
   }
 };
 
-template <int E>
+template <int E, int BN>
 __global__ void __launch_bounds__(kPersistThreads, 1)
 frac_tc_persist_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P) {
   extern __shared__ uint8_t smem_raw[];
-  persist_body<E>(LocateOne{&maps, &P}, P.total_tiles, P.flag, smem_raw);
+  persist_body<E, BN>(LocateOne{&maps, &P}, P.total_tiles, P.flag, smem_raw);
 }
 
 template <int E>
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
 frac_tc_persist_batch_kernel(const TcMaps* __restrict__ maps, const TcParams* __restrict__ prm,
                              const int* __restrict__ start, int nprob, int ntiles, int* flag) {
   extern __shared__ uint8_t smem_raw[];
-  persist_body<E>(LocateBatch{maps, prm, start, nprob}, ntiles, flag, smem_raw);
+  persist_body<E, PBN>(LocateBatch{maps, prm, start, nprob}, ntiles, flag, smem_raw);
 }
 
 // ---------------------------------------------------------------------------- splits
@@ -609,26 +610,26 @@ cudaError_t launch_bn(const TcPlan* p, cudaStream_t s) {
 
 constexpr int kPersistCTAs = 152;  // one per SM
 
-template <int E>
+template <int E, int BN>
 cudaError_t launch_persist(const TcPlan* p, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(frac_tc_persist_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)PCfg<E>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(frac_tc_persist_kernel<E, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PCfg<E, BN>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::min(p->prm.total_tiles, kPersistCTAs), 1, 1);
   cfg.blockDim = dim3(kPersistThreads, 1, 1);
-  cfg.dynamicSmemBytes = PCfg<E>::SMEM;
+  cfg.dynamicSmemBytes = PCfg<E, BN>::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = p->pdl ? 1 : 0;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, frac_tc_persist_kernel<E>, p->maps, p->prm);
+  return cudaLaunchKernelEx(&cfg, frac_tc_persist_kernel<E, BN>, p->maps, p->prm);
 }
 
 }  // namespace
@@ -767,7 +768,8 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
   TcPlan* p = h->tc;
   if (!p) return LBM_EINVAL;
   if (!(bn == 64 || bn == 128 || bn == 256) || !(ks == 1 || ks == 2 || ks == 4 || ks == 8)) return LBM_EINVAL;
-  if ((persist && (bn != PBN || ks != 1)) || (bn == 256 && ks != 1) || ks > tc_kbmin(h)) return LBM_EINVAL;
+  if ((persist && ((bn != PBN && bn != 256) || ks != 1)) || (bn == 256 && ks != 1) || ks > tc_kbmin(h))
+    return LBM_EINVAL;
   // the five-product form keeps a third weight part per stage: per-tile kernel, 64 or 128 columns
   if (p->kparts == 3 && (persist || bn == 256)) return LBM_EINVAL;
   const int E = p->elem;
@@ -979,7 +981,10 @@ cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s) {
     if (p->persist || p->elem != 2 || p->bn == 256) return cudaErrorInvalidConfiguration;
     return (p->bn == 64) ? launch_bn<2, 64, 3>(p, s) : launch_bn<2, 128, 3>(p, s);
   }
-  if (p->persist) return (p->elem == 2) ? launch_persist<2>(p, s) : launch_persist<4>(p, s);
+  if (p->persist) {
+    if (p->bn == 256) return (p->elem == 2) ? launch_persist<2, 256>(p, s) : launch_persist<4, 256>(p, s);
+    return (p->elem == 2) ? launch_persist<2, 128>(p, s) : launch_persist<4, 128>(p, s);
+  }
   // 256-column tiles are chosen only when they alone fill the GPU: never split
   if (p->bn == 256 && p->prm.ksplit != 1) return cudaErrorInvalidConfiguration;
   if (p->elem == 2) {

@@ -142,7 +142,7 @@ def _plans(L, pb, kind):
                 continue
             out.append((bn, ks, 0))
     if not five:
-        out.append((128, 1, 1))
+        out += [(128, 1, 1), (256, 1, 1)]
     return out
 
 
