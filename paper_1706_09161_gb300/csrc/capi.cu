@@ -267,6 +267,15 @@ void free_all(lbm_s* h) {
   h->stream = nullptr;
 }
 
+// Programmatic dependent launch between the operator and collide-stream kernels: only
+// where both grids run in one wave (measured: with multi-wave 3-D grids the early CTAs
+// cost ~30%) and no other launch sits between them (tf32: the regrouped operands come
+// from the collide-stream kernel itself)
+bool pdl_fits(const lbm_s* h) {
+  const bool adjacent = lbm::bf16_parts(h->prm.precision) || lbm::cs_writes_T(h);
+  return adjacent && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
+}
+
 int alloc_bytes(const lbm_s* h, void** p, size_t bytes) {
   const cudaError_t e = lbm::dev_alloc(h, p, bytes);
   if (e == cudaErrorMemoryAllocation) return LBM_ENOMEM;
@@ -310,7 +319,7 @@ int one_step(lbm_s* h, int& cur, cudaStream_t s) {
     return LBM_OK;
   }
   if (uses_tc(h)) {
-    LBM_CUDA(lbm::launch_split_T_step(h, s));  // tf32: transposed operands of the current C
+    LBM_CUDA(lbm::launch_split_T_step(h, s));  // tf32: regrouped y/z operands of the current C
     LBM_CUDA(lbm::launch_frac_tc(h, s));
   } else {
     int rc = run_frac(h, s);
@@ -442,15 +451,15 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   }
   if (lbm::bf16_parts(prm->precision) || prm->precision == LBM_FP32_TF32SPLIT) {
     if ((rc = lbm::tc_prepare(h, Kall, batched ? 128 : 0, batched ? 1 : 0))) return fail(rc);
-    h->launches_per_step = (prm->precision == LBM_FP32_TF32SPLIT) ? 2 + (h->d - 1) : 2;
-    // overlap kernel boundaries only where neither grid needs a second wave; the tf32
-    // transposes between collide-stream and the operator are plain launches anyway
-    h->pdl = !batched && lbm::bf16_parts(prm->precision) && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
-    lbm::tc_set_pdl(h, h->pdl);
+    h->launches_per_step = 2;  // (lbm_launches_per_step counts the tf32 regrouping launches)
   } else {
     h->launches_per_step = 2;  // one SIMT operator launch over every axis, one collide-stream
   }
   if (!batched && (rc = lbm::cs_prepare(h))) return fail(rc);
+  if (!batched && h->tc) {
+    h->pdl = pdl_fits(h);
+    lbm::tc_set_pdl(h, h->pdl);
+  }
   *out = h;
   rc = lbm_set_C(h, C0_host);
   if (rc) {
@@ -831,13 +840,13 @@ int apply_cfg(lbm_s* h, const TuneCfg& c) {
       lbm::cs_release(h);
       h->cs_chunk = c.chunk;
       if ((rc = lbm::cs_prepare(h))) return rc;
-      h->pdl = lbm::bf16_parts(h->prm.precision) && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
+      h->pdl = pdl_fits(h);
       lbm::tc_set_pdl(h, h->pdl);
       if (c.fused) {
         if ((rc = lbm::fused_prepare(h))) return rc;
         h->fused = true;
       }
-      // every operand copy of C current: the new plan may take the transposed tf32 copies
+      // every operand copy of C current: the new plan may take the regrouped tf32 copies
       // from the collide-stream kernel, which the old one did not write
       LBM_CUDA(lbm::launch_split_C(h, h->stream));
     } else {

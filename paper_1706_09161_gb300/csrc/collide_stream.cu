@@ -575,7 +575,7 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(cs_raw) + 127) & ~uintptr_t(127));
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)TMA_STAGES * TMA_STAGE);
   __shared__ float s_m[2][4][TY + 2][TX + 2];
-  // tf32: C of the last four planes (slot z & 3), the source of the transposed split
+  // tf32: C of the last four planes (slot z & 3), the source of the regrouped split
   __shared__ float s_c[SPLIT == 2 ? 4 * TY * TCP : 1];
   const bool wT = SPLIT == 2 && so.thi[0] != nullptr;
   const int n0 = sp.n[0], n1 = sp.n[1], n2 = sp.n[2];
@@ -1183,7 +1183,6 @@ collide_stream_batch_kernel(const BatchCS* __restrict__ tab, const int* __restri
 template <typename real, int D>
 __global__ void init_equilibrium_kernel(const KConst<real> sp, const real* __restrict__ C, const real* __restrict__ F,
                                         real* __restrict__ f) {
-  constexpr int Q = Lat<D>::Q;
   const long long nodes = sp.nodes;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
        i += (long long)gridDim.x * blockDim.x) {
@@ -1368,7 +1367,7 @@ int grid_for(long long n) {
 
 }  // namespace
 
-// tf32 handles on the TMA-fed marches: the collide-stream kernel writes the transposed split
+// tf32 handles on the TMA-fed marches: the collide-stream kernel writes the regrouped split
 bool cs_writes_T(const lbm_s* h) {
   return !h->is_batch() && h->elem == 4 && h->cs_plan != nullptr && h->tc != nullptr && h->tc->elem == 4 &&
          h->prm.precision == LBM_FP32_TF32SPLIT;

@@ -131,7 +131,7 @@ cudaError_t launch_sum_partials_out(const float* src, int k, long long stride, d
 cudaError_t launch_sum_partials(const float* src, int k, long long stride, float* dst, long long n, cudaStream_t s);
 // mass reduction: partials then final
 cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
-// split C into hi/lo operands for the tensor-core path (tf32: also the transposed copies)
+// split C into hi/lo operands for the tensor-core path (tf32: also the regrouped copies)
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s);
 // tf32 only: the transposed copies of the split of the current C (no-op otherwise)
 cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s);
