@@ -272,6 +272,8 @@ void free_all(lbm_s* h) {
 // cost ~30%) and no other launch sits between them (tf32: the regrouped operands come
 // from the collide-stream kernel itself)
 bool pdl_fits(const lbm_s* h) {
+  if (h->is_batch()) return false;
+  if (!h->tc) return h->elem == 4 && lbm::cs_one_wave(h) && lbm::simt_one_wave(h);  // FP32 SIMT operator
   const bool adjacent = lbm::bf16_parts(h->prm.precision) || lbm::cs_writes_T(h);
   return adjacent && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
 }
@@ -456,9 +458,9 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
     h->launches_per_step = 2;  // one SIMT operator launch over every axis, one collide-stream
   }
   if (!batched && (rc = lbm::cs_prepare(h))) return fail(rc);
-  if (!batched && h->tc) {
+  if (!batched) {
     h->pdl = pdl_fits(h);
-    lbm::tc_set_pdl(h, h->pdl);
+    if (h->tc) lbm::tc_set_pdl(h, h->pdl);
   }
   *out = h;
   rc = lbm_set_C(h, C0_host);
@@ -852,6 +854,7 @@ int apply_cfg(lbm_s* h, const TuneCfg& c) {
     } else {
       h->cs_chunk = c.chunk;
       if (c.ks > 0 && h->elem == 4 && (rc = simt_replan(h, c.ks))) return rc;
+      h->pdl = pdl_fits(h);
     }
   }
   drop_graphs(h);

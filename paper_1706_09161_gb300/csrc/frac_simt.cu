@@ -34,6 +34,7 @@ struct GemmPlan {
   int ks;              // contraction slices per tile
   long long pstride;   // elements between the slices' partial outputs
   long long total;
+  int early;           // one-wave grid: let the next kernel be scheduled at block start
 };
 
 // Block tile BM x BN, 256 threads with TM x TN outputs each, reduction slices of BK.
@@ -55,6 +56,9 @@ frac_simt_kernel(const GemmPlan P) {
   constexpr int BK = G::BK;
   __shared__ real As[2][BM][BK + 1];
   __shared__ __align__(16) real Bs[2][BK][BN];
+  // programmatic dependent launch: C (read) and F (written) belong to the previous kernel
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (P.early) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   long long b = blockIdx.x;
   int a = 0;
   while (a + 1 < P.naxes && b >= P.ax[a + 1].begin) ++a;
@@ -146,6 +150,7 @@ frac_simt_kernel(const GemmPlan P) {
       if (gn < N) Cm[gm * X.ldc + gn] = acc[i][j];
     }
   }
+  if (!P.early) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 void add_axis(GemmPlan& P, int BM, int BN, int M, int N, int K, int batch, const void* A, long long lda, long long sA,
@@ -190,23 +195,57 @@ GemmPlan make_plan(const lbm_s* h, const real* C, real* F, bool transpose, long 
   return P;
 }
 
+// the grid of `blocks` blocks is resident at once (one wave)
+template <typename real, int BM, int BN, int TM, int TN>
+bool simt_blocks_fit(long long blocks) {
+  static int per_sm = -1;
+  if (per_sm < 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, frac_simt_kernel<real, BM, BN, TM, TN>, 256, 0) !=
+          cudaSuccess)
+    per_sm = 0;
+  return blocks <= (long long)per_sm * 152;
+}
+
 // 64 x 64 tiles where they give two blocks per SM (with the handle's contraction split,
 // forward operator only), else 32 x 32
 template <typename real>
 cudaError_t frac_all_axes(const lbm_s* h, const real* C, real* F, cudaStream_t s, bool transpose = false,
                           long long cstride = 0) {
   const int ks = transpose ? 1 : h->sp.ksum;
-  const GemmPlan big = make_plan<real, 64, 64>(h, C, F, transpose, cstride, ks, ks > 1 ? h->sp.pstride : 0);
+  // the forward operator of a handle with programmatic dependent launch overlaps the
+  // previous collide-stream kernel's tail
+  const bool pdl = !transpose && h->pdl;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  GemmPlan big = make_plan<real, 64, 64>(h, C, F, transpose, cstride, ks, ks > 1 ? h->sp.pstride : 0);
   if (big.total >= 2 * 152 || ks > 1) {
-    frac_simt_kernel<real, 64, 64, 4, 4><<<static_cast<unsigned>(big.total), 256, 0, s>>>(big);
-  } else {
-    const GemmPlan small = make_plan<real, 32, 32>(h, C, F, transpose, cstride);
-    frac_simt_kernel<real, 32, 32, 2, 2><<<static_cast<unsigned>(small.total), 256, 0, s>>>(small);
+    big.early = pdl && simt_blocks_fit<real, 64, 64, 4, 4>(big.total);
+    cfg.gridDim = dim3(static_cast<unsigned>(big.total), 1, 1);
+    return cudaLaunchKernelEx(&cfg, frac_simt_kernel<real, 64, 64, 4, 4>, big);
   }
-  return cudaGetLastError();
+  GemmPlan small = make_plan<real, 32, 32>(h, C, F, transpose, cstride);
+  small.early = pdl && simt_blocks_fit<real, 32, 32, 2, 2>(small.total);
+  cfg.gridDim = dim3(static_cast<unsigned>(small.total), 1, 1);
+  return cudaLaunchKernelEx(&cfg, frac_simt_kernel<real, 32, 32, 2, 2>, small);
 }
 
 }  // namespace
+
+bool simt_one_wave(const lbm_s* h) {
+  if (h->elem != 4) return false;
+  const float* C = static_cast<const float*>(h->dev.C);
+  float* F = static_cast<float*>(h->dev.F);
+  GemmPlan big = make_plan<float, 64, 64>(h, C, F, false, 0, h->sp.ksum, h->sp.pstride);
+  if (big.total >= 2 * 152 || h->sp.ksum > 1) return simt_blocks_fit<float, 64, 64, 4, 4>(big.total);
+  GemmPlan small = make_plan<float, 32, 32>(h, C, F, false, 0);
+  return simt_blocks_fit<float, 32, 32, 2, 2>(small.total);
+}
 
 int simt_ksplit(const lbm_s* h) {
   if (h->elem != 4) return 1;

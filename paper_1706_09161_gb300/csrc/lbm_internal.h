@@ -109,6 +109,8 @@ cudaError_t launch_frac_simt(const lbm_s* h, const void* C, void* F, cudaStream_
 // contraction split of the FP32 SIMT operator for a single problem: F then holds that
 // many partial sums ([rank][axis][node], like the tensor-core split), 1 for FP64
 int simt_ksplit(const lbm_s* h);
+// the FP32 SIMT operator's grid is resident at once (programmatic dependent launch)
+bool simt_one_wave(const lbm_s* h);
 // tensor-core split-precision fractional operator (tcgen05); returns
 // cudaErrorNotSupported when the handle's shape is not covered
 cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s);
