@@ -132,3 +132,19 @@ def test_host_weight_matrix_derivatives_match_oracle_autograd(L, side, alpha, p,
     (K * w).sum().backward()
     assert float((torch.tensor(da) * w).sum()) == pytest.approx(float(a.grad), rel=1e-9, abs=1e-12)
     assert float((torch.tensor(dp) * w).sum()) == pytest.approx(float(pp.grad), rel=1e-9, abs=1e-12)
+
+
+def test_allocator_hooks_come_in_pairs(L):
+    """lbm_set_allocator: both hooks or neither (host-side check, no GPU call)."""
+    with pytest.raises(L.LBMError):
+        L.lbm_set_allocator(lambda n, s, c: None, None)
+    with pytest.raises(L.LBMError):
+        L.lbm_set_allocator(None, lambda p, c: None)
+    L.lbm_set_allocator(None, None)  # restores cudaMalloc / cudaFree
+
+
+def test_wait_check_validates_its_limit(L):
+    """lbm_wait_check rejects limits outside [1 us, 1 s] before touching a GPU."""
+    assert L.lbm_wait_check(False, 0) == L.LBM_EINVAL
+    assert L.lbm_wait_check(True, -5) == L.LBM_EINVAL
+    assert L.lbm_wait_check(False, 1000001) == L.LBM_EINVAL
