@@ -201,7 +201,8 @@ int lbm_write_f(lbm_t h, const double* f_host);
  * separated by bounded grid barriers).  The populations are restored bit for bit
  * afterwards (as lbm_save / lbm_load), so tuning does not advance the run.  desc, if
  * not NULL, receives up to desc_len bytes describing the choice.  nsteps in
- * [2, 100000] (rounded up to even), else LBM_EINVAL.  Synchronises. */
+ * [2, 100000] (rounded up to whole graph replays: 128 steps, 32 for batches), else
+ * LBM_EINVAL.  Synchronises. */
 int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len);
 
 /* Apply a launch configuration directly (for example one lbm_autotune found before):

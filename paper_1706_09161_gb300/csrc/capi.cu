@@ -388,7 +388,7 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   h->Q = 2 * h->d + 1;
   h->elem = (prm->precision == LBM_FP64) ? 8 : 4;
   h->sp = dv.sp;
-  h->graph_steps = 32;
+  h->graph_steps = 128;  // steps per captured graph (even); longer graphs, fewer replay boundaries
   h->mem = current_hooks();
   cudaGetDevice(&h->device);
   auto fail = [&](int code) {
@@ -920,7 +920,8 @@ int lbm_configure(lbm_t h, int bn, int ks, int persist, int chunk, int fused) {
 
 int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
   if (!h || nsteps < 2 || nsteps > 100000) return LBM_EINVAL;
-  nsteps += nsteps & 1;  // even: graph replays keep the buffer parity
+  // whole graph replays, as lbm_step runs them (their length is even: buffer parity kept)
+  nsteps = (nsteps + h->graph_steps - 1) / h->graph_steps * h->graph_steps;
   // the state is restored afterwards, bit for bit
   std::vector<char> state((size_t)state_bytes(h));
   int rc = lbm_save(h, state.data(), (long long)state.size());

@@ -139,13 +139,13 @@ def test_config_mrt_512_full_size_prefix(L):
 
 
 def test_graph_replay_equals_single_steps(L):
-    """Graph-captured replay (32-step graphs) and one-step launches give identical results."""
+    """Graph-captured replay (128-step graphs) and one-step launches give identical results."""
     rng = np.random.default_rng(5)
     pb = W.random_problem(rng, 2, "mrt", (50, 45))
     C0 = W.random_field(rng, pb.grid)
     with L.Lattice(pb, C0, "fp32") as a, L.Lattice(pb, C0, "fp32") as b:
-        a.step(71)
-        for _ in range(71):
+        a.step(263)
+        for _ in range(263):
             b.step(1)
         assert np.array_equal(a.C(), b.C())
 
@@ -222,10 +222,10 @@ def test_save_load_resumes_bit_exact(L, kind):
     with L.Lattice(pb, C0, kind) as lat:
         lat.step(7)
         state = lat.save()
-        lat.step(40)  # graph replay and single launches
+        lat.step(140)  # graph replay and single launches
         f_a = lat.f()
         lat.load(state)
-        lat.step(40)
+        lat.step(140)
         f_b = lat.f()
     assert np.array_equal(f_a, f_b)
 

@@ -112,8 +112,8 @@ def test_tc_graph_replay_deterministic(L):
     pb = W.random_problem(rng, 2, "mrt", (150, 140))
     C0 = W.random_field(rng, pb.grid)
     with L.Lattice(pb, C0, "bf16split") as a, L.Lattice(pb, C0, "bf16split") as b:
-        a.step(70)
-        for _ in range(70):
+        a.step(135)  # one 128-step graph replay and single launches
+        for _ in range(135):
             b.step(1)
         assert np.array_equal(a.C(), b.C())
         assert L.lbm_sync(a.h) == 0
