@@ -954,27 +954,31 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       fv[2] = s_m[buf][1][sy][sx + 1];
       fv[3] = s_m[buf][2][sy - 1][sx];
       fv[4] = s_m[buf][3][sy + 1][sx];
-      float sum_known = 0.f;
-      int n_unknown = 0;
+      float C = 0.f;
+      if (x0 > 0 && x0 + TX < n0 && tr * TY > 0 && tr * TY + TY < n1) {  // no wall within reach (block-uniform)
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        if (known[q]) {
-          sum_known += fv[q];
-        } else {
-          fv[q] = 0.f;
-          ++n_unknown;
+        for (int q = 0; q < Q; ++q) C += fv[q];
+      } else {
+        int n_unknown = 0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          if (known[q]) {
+            C += fv[q];
+          } else {
+            fv[q] = 0.f;
+            ++n_unknown;
+          }
         }
-      }
-      float C = sum_known;
-      if (n_unknown > 0) {
-        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
-        const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
+        if (n_unknown > 0) {
+          // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
+          const float fill = (sp.C_wall - C) / static_cast<float>(n_unknown);
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
-          if (!known[q]) fv[q] = fill;
-        C = fv[0];
+          for (int q = 0; q < Q; ++q)
+            if (!known[q]) fv[q] = fill;
+          C = fv[0];
 #pragma unroll
-        for (int q = 1; q < Q; ++q) C += fv[q];
+          for (int q = 1; q < Q; ++q) C += fv[q];
+        }
       }
       const long long node = gx + (long long)n0 * gy;
 #pragma unroll
