@@ -1391,7 +1391,7 @@ cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out,
              : launch_cs<float, 3, false>(h, f_in, f_out, C_out, s);
 }
 
-constexpr int kBatchYChunk = 8;
+constexpr int kBatchYChunk = 16;  // tile rows per block (the autotuner's usual choice on mixed batches)
 
 // window maps of a 2-D handle: populations (n0, n1, 5) and fractional terms (n0, n1, 2)
 bool encode_2d_maps(const lbm_s* h, CUtensorMap* mf, CUtensorMap* mF) {
