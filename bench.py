@@ -8,12 +8,22 @@ collision, streaming, Dirichlet walls and new concentration.  L2 is flushed
 resident, as in any real run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload mrt_aniso_512] [--precision P]
+                  [--workload mrt_aniso_512] [--precision P] [--no-extra]
 
-N > 1 runs under torchrun, one independent replica per GPU (the workload does
-not shard), timing is the max over ranks and ``value`` counts every rank's
-lattice updates.  ``--impl reference`` times the FP64 CPU oracle on the host
-cores on a bounded sample of the same workload.
+The headline line is the 512^2 anisotropic MRT workload in the five-product bf16
+form (the split form within 1e-5 of the FP64 oracle); the other precision forms
+of the same workload are reported beside it (``forms``), and at N = 1 the other
+named workloads (3-D 256^3, the 64-problem batch, the FP64 64^2 case and the
+inverse problem's loss + gradient) each get an entry in ``workloads`` with their
+own MLUPS, end-to-end MLUPS, rooflines of both kernels and accuracy against an
+oracle sample.
+
+N > 1 runs under torchrun.  The batch workload is partitioned: each rank takes a
+cost-balanced subset of the problems (no collective on the data path).  A single
+lattice does not shard: every rank runs an independent replica.  Timing is the
+max over ranks and ``value`` counts every rank's lattice updates.
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
 """
 from __future__ import annotations
 
@@ -40,28 +50,37 @@ WORKLOADS = {
         desc="2-D anisotropic fractional ADE, D2Q5 MRT, 512x512, alpha=(1.5,1.8), p=(0.3,0.7), g=(1,1), "
              "D=diag(2e-3,5e-4), u=(0.05,0.02) lattice units, free rates U[0.8,1.9] seed 2, "
              "Dirichlet C=0, 5x5 unit-mass pulse, 5000 steps",
-        default_precision="bf16split"),
-    "fp64_bgk_64": dict(desc="2-D D2Q5 BGK 64x64 FP64, alpha=1.7, 200 steps", default_precision="fp64"),
+        default_precision="bf16x5split", oracle_steps=1000),
+    "fp64_bgk_64": dict(desc="2-D D2Q5 BGK 64x64 FP64, alpha=1.7, p=0.5, D=1e-3, unit-mass Gaussian sigma=2, "
+                             "200 steps", default_precision="fp64", oracle_steps=200),
     "batch64": dict(desc="64 independent 2-D D2Q5 MRT problems, sides U{128,256,384,512,768,1024} (seed 4), "
                          "alpha~U[1.2,2], p~U[0,1], D~U[1e-4,3e-3] diagonal, |u|<=0.08, Gaussian pulses sigma~U[2,6], "
                          "free rates U[0.8,1.9], 1000 steps each, grouped launches",
-                    default_precision="bf16split"),
+                    default_precision="bf16split", oracle_steps=6),
     "inverse_256": dict(desc="inverse problem: 2-D D2Q5 MRT 256x256, alpha=(1.45,1.75), p=(0.35,0.65), "
                              "D=diag(1.5e-3,7e-4), u=(0.04,-0.01); loss over 10 snapshots of 3000 steps + N(0,1e-4) noise; "
                              "one bench step = one loss+gradient evaluation (forward, checkpointed recompute, adjoint; "
                              "checkpoint every 100); value counts forward lattice updates",
-                        default_precision="fp32"),
+                        default_precision="fp32", oracle_steps=100),
     "mrt3d_128": dict(desc="3-D D3Q7 MRT 128^3 with the 256^3 workload's parameters (profiling captures only)",
-                      default_precision="tf32split"),
+                      default_precision="tf32split", oracle_steps=20),
     "mrt3d_256": dict(desc="3-D fractional ADE, D3Q7 MRT, 256^3, alpha=(1.6,1.6,1.9), p=(0.5,0.2,0.8), g=(1,1,1), "
                            "D=diag(1e-3,1e-3,4e-4), u=(0.03,0,0) lattice units, free rates U[0.8,1.9] seed 3, "
                            "Dirichlet C=0, unit-mass Gaussian sigma=3, 2000 steps",
-                      default_precision="tf32split"),
+                      default_precision="tf32split", oracle_steps=20),
 }
+# the other precision forms of the headline workload reported beside it ("forms"); fp32 is
+# the plain FP32 form (SIMT operator) the split forms are compared with
+HEADLINE_FORMS = ("bf16split", "tf32split", "fp32")
+# the other named workloads measured at N = 1 ("workloads")
+EXTRA_WORKLOADS = ("mrt3d_256", "batch64", "fp64_bgk_64", "inverse_256")
+
+DTYPES = {"fp64": "f64", "fp32": "f32", "bf16split": "f32+bf16x3", "tf32split": "f32+tf32x3",
+          "bf16x5split": "f32+bf16x5"}
+SPLIT_PRODUCTS = {"bf16split": 3, "tf32split": 3, "bf16x5split": 5}
 
 # measured peaks (driver-written), with the profiling recipe's fallback
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
-SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate
 
@@ -111,6 +130,47 @@ def make_workload(name):
         return [pb], [C0], snaps[-1]
     pb, C0, n = W.mrt3d_256(128) if name == "mrt3d_128" else getattr(W, name)()
     return [pb], [C0], n
+
+
+# --------------------------------------------------------------------------- multi-GPU partition
+
+def problem_cost(pb) -> float:
+    """Relative GPU time of one step of problem `pb`: collide-stream work grows with the
+    nodes, the fractional operator with nodes x side (2 d side flops per node).  Measured
+    on the 64-problem batch: ~14.3 ps per node of collide-stream and ~0.0093 ps per node per
+    unit of side of (bf16x3) operator, i.e. cost ~ nodes (1 + side / 1536)."""
+    side = max(int(n) for n in pb.grid)
+    return float(pb.nodes) * (1.0 + side / 1536.0)
+
+
+def partition(probs, world: int):
+    """Problem indices per rank: longest-processing-time-first greedy assignment of the
+    problems (by problem_cost) to the least-loaded rank; deterministic (ties by index)."""
+    order = sorted(range(len(probs)), key=lambda i: (-problem_cost(probs[i]), i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += problem_cost(probs[i])
+    return [sorted(p) for p in parts]
+
+
+def job_value(local_ms, units_per_rank, world, dist=None, device=None):
+    """Whole-job throughput in MLUPS: every rank's lattice updates (summed over ranks) over
+    the slowest rank's time (max over ranks), and that time in ms."""
+    t = float(local_ms)
+    units = float(units_per_rank)
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        uu = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+        t, units = float(tt.item()), float(uu.item())
+    else:
+        units = world * units
+    return units / (t * 1e-3) / 1e6, t
 
 
 # --------------------------------------------------------------------------- clocks
@@ -182,6 +242,246 @@ def oracle_sample(pb, C0, nsteps):
     return dt, O.concentration(f).numpy(), torch.get_num_threads()
 
 
+def oracle_refs(probs, fields, nsteps):
+    """Oracle C of every problem after nsteps; (refs, seconds, threads)."""
+    refs, dt, threads = [], 0.0, 1
+    for pb, C0 in zip(probs, fields):
+        t, C_ref, threads = oracle_sample(pb, C0, nsteps)
+        dt += t
+        refs.append(C_ref)
+    return refs, dt, threads
+
+
+def errors(got, refs):
+    """Relative L2 over all problems' nodes, and the per-node bound max|C - C_ref| / max|C_ref|
+    (worst problem), walls included."""
+    num = sum(float(np.sum((g - r) ** 2)) for g, r in zip(got, refs))
+    den = sum(float(np.sum(r ** 2)) for r in refs)
+    node = max(float(np.max(np.abs(g - r))) / max(float(np.max(np.abs(r))), 1e-300) for g, r in zip(got, refs))
+    return {"rel_l2_vs_fp64_oracle": float(np.sqrt(num / den)), "max_node_err_rel_to_max": node}
+
+
+# --------------------------------------------------------------------------- GPU legs
+
+class Runner:
+    """One workload in one precision form on the GPU: handle, timed runs, e2e runs,
+    rooflines and accuracy."""
+
+    def __init__(self, lbm, torch, name, probs, fields, nlbm, precision, autotune, flush, subset=None):
+        self.lbm, self.torch = lbm, torch
+        self.name, self.precision = name, precision
+        self.probs, self.fields, self.nlbm = probs, fields, nlbm
+        self.batched = len(probs) > 1
+        self.nodes = sum(pb.nodes for pb in probs)
+        self.lat = (lbm.Batch(probs, fields, precision) if self.batched
+                    else lbm.Lattice(probs[0], fields[0], precision))
+        # launch configuration chosen by the library's autotuner on this workload (untimed
+        # setup; the populations are restored afterwards)
+        self.tuned = self.lat.autotune(64) if autotune else None
+        self.stream = torch.cuda.ExternalStream(self.lat.stream)
+        self.flush = flush
+        self.inverse = name == "inverse_256"
+        if self.inverse:
+            self._make_observations()
+
+    def _make_observations(self):
+        from paper_1706_09161_gb300 import workloads as W
+        _, _, self.snaps = W.inverse_256()
+        # synthetic observations: the GPU forward run itself plus N(0, (1e-4)^2) noise
+        obs = []
+        self.lat.reset()
+        t = 0
+        for ts in self.snaps:
+            self.lat.step(ts - t)
+            t = ts
+            obs.append(self.lat.C())
+        self.obs = np.stack(obs) + W.observation_noise((len(self.snaps),) + self.probs[0].shape)
+
+    def close(self):
+        self.lat.close()
+
+    def run_once(self):
+        torch = self.torch
+        self.lat.reset()
+        self.flush.add_(1.0)  # L2 flush on torch's stream
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(self.stream)
+        if self.inverse:
+            self.lat.grad(self.snaps, self.obs, 100)
+        else:
+            self.lat.step(self.nlbm)
+        ev1.record(self.stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    def timed(self, steps, warmup):
+        for _ in range(warmup):
+            self.run_once()
+        warm = self.lbm.lbm_sync(self.lat.h)  # a latched instability does not change the work timed
+        self.torch.cuda.synchronize()
+        t = [self.run_once() for _ in range(steps)]
+        self.torch.cuda.synchronize()
+        return t, warm
+
+    def launches_per_bench_step(self):
+        lps = self.lat.launches_per_step
+        if self.inverse:
+            d0 = self.probs[0].d
+            # forward + checkpointed recompute (d+1 each) and adjoint (step, d transposes, d G sums, combine)
+            return self.nlbm * (2 * (d0 + 1) + 2 + 2 * d0)
+        # 0: the fused step, one cooperative launch per lbm_step call of up to 4096 steps
+        return self.nlbm * lps if lps > 0 else -(-self.nlbm // 4096)
+
+    def e2e(self, steps):
+        """Seconds per bench step through the C ABI with pinned host buffers: the initial
+        fields go host -> device, the run, C of every problem device -> host."""
+        torch, lbm = self.torch, self.lbm
+        pins = [torch.from_numpy(np.ascontiguousarray(C0)).pin_memory() for C0 in self.fields]
+        outs = [torch.empty(p.shape, dtype=torch.float64).pin_memory() for p in pins]
+        if self.inverse:
+            obs_pin = torch.from_numpy(np.ascontiguousarray(self.obs)).pin_memory()
+        secs = []
+        for _ in range(steps):
+            self.flush.add_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i, p in enumerate(pins):
+                if self.batched:
+                    self.lat.set_C(i, p.numpy())
+                else:
+                    self.lat.set_C(p.numpy())
+            if self.inverse:  # observations go host -> device inside lbm_grad; loss and gradient come back
+                self.lat.grad(self.snaps, obs_pin.numpy(), 100)
+                secs.append(time.perf_counter() - t0)
+                continue
+            self.lat.step(self.nlbm)
+            for i, o in enumerate(outs):
+                # data is copied; a latched instability is only reported
+                rc = lbm._lib.lbm_read_C(self.lat.h, i, o.numpy().ctypes.data_as(lbm.ctypes.c_void_p), 0)
+                if rc not in (lbm.LBM_OK, lbm.LBM_ERR_UNSTABLE):
+                    raise lbm.LBMError(rc, "lbm_read_C")
+            secs.append(time.perf_counter() - t0)
+        io = int(sum(C0.size for C0 in self.fields) * 8)
+        h2d, d2h = io, io
+        if self.inverse:
+            h2d = io + int(self.obs.size * 8)
+            d2h = 8 * (1 + 4 * self.probs[0].d)
+        return secs, h2d, d2h
+
+    def rooflines(self, peaks, peak_src):
+        """Both kernels, timed live with CUDA events on the library stream (lbm_profile)."""
+        nprof = min(self.nlbm, 200)
+        self.lat.reset()
+        ms_frac, ms_cs = self.lat.profile(nprof)
+        probs, precision = self.probs, self.precision
+        d = probs[0].d
+        Q = 2 * d + 1
+        elem = 8 if precision == "fp64" else 4
+        flops = float(sum(2.0 * pb.nodes * sum(pb.grid) for pb in probs))  # 2 side flops per node per axis
+        dur = ms_frac / nprof * 1e-3
+        achieved = flops / dur / 1e12
+        if precision in SPLIT_PRODUCTS:
+            bound = "tensor"
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            if precision == "tf32split":
+                peak = peak / 2.0  # nominal tf32/bf16 ratio
+        else:
+            bound = "alu"
+            if precision == "fp32":
+                # FP32 FMA lanes x 2 flops x max SM clock
+                import torch
+                sms = torch.cuda.get_device_properties(0).multi_processor_count
+                peak = sms * FP32_LANES_PER_SM * 2.0 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            else:
+                peak = FP64_NOMINAL_TFLOPS
+        roof_op = {"kernel": "fractional_operator", "bound": bound, "achieved": achieved, "peak": peak,
+                   "unit": "TFLOP/s", "frac": achieved / peak,
+                   "traffic": traffic_for(self.name, "fractional_operator", precision),
+                   "algorithmic_per_launch": flops, "launch_ms": dur * 1e3, "peak_source": peak_src}
+        if precision in SPLIT_PRODUCTS:
+            # the split forms issue three (hi*hi, hi*lo, lo*hi) or five products per
+            # algorithmic one: the tensor pipe's own load
+            npr = SPLIT_PRODUCTS[precision]
+            roof_op["executed_per_launch"] = npr * flops
+            roof_op["executed_frac"] = npr * achieved / peak
+        bytes_ = float(self.nodes) * (2 * Q * elem + d * elem + elem)
+        dur = ms_cs / nprof * 1e-3
+        achieved = bytes_ / dur / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof_cs = {"kernel": "collide_stream", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                   "frac": achieved / peak, "traffic": traffic_for(self.name, "collide_stream", precision),
+                   "algorithmic_per_launch": bytes_, "launch_ms": dur * 1e3, "peak_source": peak_src}
+        if precision in SPLIT_PRODUCTS:
+            # the kernel also writes the operator's operands of the new C: its hi/lo split
+            # (x contiguous) and, for tf32 on the TMA-fed marches (one operator and one
+            # collide-stream launch per step), the copies regrouped along y (and z)
+            per_node = 8 if precision == "tf32split" else 4
+            if precision == "tf32split" and self.lat.launches_per_step == 2:
+                per_node += 8 * (d - 1)
+            ex = bytes_ + float(self.nodes) * per_node
+            roof_cs["executed_per_launch"] = ex
+            roof_cs["executed_frac"] = ex / dur / 1e9 / peak
+        roof, other = (roof_op, roof_cs) if ms_frac >= ms_cs else (roof_cs, roof_op)
+        roof["other_kernel_ms"] = {"fractional_operator": ms_frac / nprof, "collide_stream": ms_cs / nprof}
+        return roof, other
+
+    def accuracy(self, refs, nsteps):
+        self.lat.reset()
+        self.lat.step(nsteps)
+        got = [self.lat.C(i) for i in range(len(self.probs))] if self.batched else [self.lat.C()]
+        acc = errors(got, refs)
+        acc["lattice_steps"] = nsteps
+        return acc
+
+
+def oracle_gradient_accuracy(Lattice, pb, C0, nsteps):
+    """GPU loss and gradient of a short snapshot misfit (snapshots at nsteps/2 and nsteps)
+    against the FP64 oracle's autograd adjoint of the same loss."""
+    from oracle import lbm_oracle as O
+    snaps = [nsteps // 2, nsteps]
+    rng = np.random.default_rng(7)
+    obs = rng.normal(0.0, 1e-4, size=(2,) + pb.shape)
+    t0 = time.perf_counter()
+    loss_ref, g_ref = O.loss_and_grad(pb, C0, snaps, obs)
+    dt = time.perf_counter() - t0
+    with Lattice(pb, C0, "fp32") as l2:
+        loss, g = l2.grad(snaps, obs, 25)
+    g_ref = g_ref.numpy()
+    d = pb.d
+    fam = {}
+    for k, nm in enumerate(("alpha", "p", "D", "u")):
+        a, b = g[k * d:(k + 1) * d], g_ref[k * d:(k + 1) * d]
+        fam[nm] = float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+    return {"lattice_steps": nsteps, "snapshots": snaps, "loss_rel_err": abs(loss - loss_ref) / abs(loss_ref),
+            "grad_rel_err_per_family": fam, "oracle_seconds": dt}
+
+
+def traffic_for(workload, kernel, precision):
+    """DRAM bytes per launch from the committed ncu summary of this workload and precision
+    form, or None if there is none or the kernel changed since."""
+    kernel_key = f"{workload}:{kernel}"
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh).get(kernel_key)
+    if not rec or rec.get("precision") != precision:
+        return None
+    if rec.get("source_sha") != source_sha(rec["sources"]):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 # --------------------------------------------------------------------------- main
 
 def run_reference(args):
@@ -205,52 +505,61 @@ def run_reference(args):
         times.append(dt)
     total = sum(times)
     mlups = nodes * sample * args.steps / total / 1e6
+    precision = args.precision or WORKLOADS[args.workload]["default_precision"]
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+                       "gb300_arm_precision": precision,
                        "lbm_steps_per_bench_step": sample, "note": "bounded sample of the workload's run"},
-            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": threads, "host_cpus": os.cpu_count(),
+                             "kind": "oracle",
                              "sample": f"{sample} lattice steps of {args.workload} per bench step"},
             "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def job_value(local_ms, units_per_rank, world, dist=None, device=None):
-    """Whole-job throughput in MLUPS: every rank's lattice updates over the slowest rank's
-    time (max over ranks through an all-reduce), and that time in ms."""
-    t = float(local_ms)
-    if dist is not None and world > 1:
-        import torch
-        tt = torch.tensor([t], dtype=torch.float64, device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    return world * units_per_rank / (t * 1e-3) / 1e6, t
-
-
-def source_sha(paths):
-    h = hashlib.sha256()
-    for p in paths:
-        with open(os.path.join(ROOT, p), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
-def traffic_for(workload, kernel, precision):
-    """DRAM bytes per launch from the committed ncu summary of this workload and precision
-    form, or None if there is none or the kernel changed since."""
-    kernel_key = f"{workload}:{kernel}"
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
-    with open(path) as fh:
-        rec = json.load(fh).get(kernel_key)
-    if not rec or rec.get("precision") != precision:
-        return None
-    if rec.get("source_sha") != source_sha(rec["sources"]):
-        return None
-    return rec.get("bytes_per_launch")
+def measure_extra(lbm, torch, name, flush, peaks, peak_src, autotune, steps=2, warmup=1):
+    """One entry of the `workloads` block: MLUPS (device and e2e), both rooflines and
+    accuracy against an oracle sample (or, for the inverse problem, the gradient against
+    the oracle's adjoint over a short horizon)."""
+    probs, fields, nlbm = make_workload(name)
+    precision = WORKLOADS[name]["default_precision"]
+    nodes = sum(pb.nodes for pb in probs)
+    run = Runner(lbm, torch, name, probs, fields, nlbm, precision, autotune, flush)
+    try:
+        t_ms, warm = run.timed(steps, warmup)
+        ms = sum(t_ms) / len(t_ms)
+        e2e_s, h2d, d2h = run.e2e(steps)
+        roof, other = run.rooflines(peaks, peak_src)
+        ent = {"desc": WORKLOADS[name]["desc"], "precision": precision, "dtype": DTYPES[precision],
+               "problems": len(probs), "nodes": nodes, "lattice_steps_per_bench_step": nlbm,
+               "bench_steps": steps, "warmup": warmup, "ms_per_bench_step": ms,
+               "us_per_lattice_step": 1e3 * ms / nlbm, "value": nodes * nlbm / (ms * 1e-3) / 1e6, "unit": UNIT,
+               "e2e": {"value": nodes * nlbm / (sum(e2e_s) / len(e2e_s)) / 1e6, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+               "roofline": roof, "roofline_other": other,
+               "launch_config": run.tuned if run.tuned is not None else "built-in",
+               "gpu_launches_per_bench_step": run.launches_per_bench_step(),
+               "status": lbm.lbm_strerror(warm)}
+        if precision == "tf32split" or precision == "fp64":
+            kind = "tf32" if precision == "tf32split" else "fp64"
+            roof_op = roof if roof["kernel"] == "fractional_operator" else other
+            roof_op[f"cublas_{kind}_tflops_measured"] = cublas_tflops(kind)
+        if name == "inverse_256":
+            ent["accuracy"] = oracle_gradient_accuracy(lbm.Lattice, probs[0], fields[0],
+                                                       WORKLOADS[name]["oracle_steps"])
+        else:
+            ns = min(nlbm, WORKLOADS[name]["oracle_steps"])
+            refs, dt, threads = oracle_refs(probs, fields, ns)
+            ent["accuracy"] = run.accuracy(refs, ns)
+            ent["cpu_baseline"] = {"value": nodes * ns / dt / 1e6, "unit": UNIT, "cores": threads,
+                                   "host_cpus": os.cpu_count(), "kind": "oracle",
+                                   "sample": f"first {ns} of {nlbm} lattice steps (FP64, torch CPU)"}
+        return ent
+    finally:
+        run.close()
 
 
 def main():
@@ -262,8 +571,10 @@ def main():
     ap.add_argument("--workload", default="mrt_aniso_512", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None)
     ap.add_argument("--ref-sample", type=int, default=40, help="lattice steps per reference-arm bench step")
-    ap.add_argument("--cpu-sample", type=int, default=800, help="lattice steps of the cpu_baseline leg")
+    ap.add_argument("--oracle-steps", type=int, default=None,
+                    help="lattice steps of the accuracy / cpu_baseline oracle sample (default per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other forms and workloads")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch configuration")
     ap.add_argument("--lattice-steps", type=int, default=None,
                     help="override the workload's lattice steps per bench step (profiling runs only)")
@@ -294,228 +605,89 @@ def main():
     if args.lattice_steps:
         nlbm = args.lattice_steps
     precision = args.precision or WORKLOADS[args.workload]["default_precision"]
-    batched = len(probs) > 1
+    parallelism = f"replicas x{world}"
+    if len(probs) > 1 and world > 1:
+        # independent problems: each rank takes a cost-balanced subset
+        mine = partition(probs, world)[rank]
+        probs, fields = [probs[i] for i in mine], [fields[i] for i in mine]
+        parallelism = f"problems partitioned over {world} ranks (cost-balanced, no collective)"
     nodes = sum(pb.nodes for pb in probs)
-    lat = lbm.Batch(probs, fields, precision) if batched else lbm.Lattice(probs[0], fields[0], precision)
-    # launch configuration chosen by the library's autotuner on this workload (untimed
-    # setup; the populations are restored afterwards)
-    tuned = None if args.no_autotune else lat.autotune(64)
-    stream = torch.cuda.ExternalStream(lat.stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peaks, peak_src = load_peaks()
 
-    inverse = args.workload == "inverse_256"
-    if inverse:
-        from paper_1706_09161_gb300 import workloads as W
-        _, _, snaps = W.inverse_256()
-        # synthetic observations: the GPU forward run itself plus N(0, (1e-4)^2) noise
-        obs = []
-        lat.reset()
-        t = 0
-        for ts in snaps:
-            lat.step(ts - t)
-            t = ts
-            obs.append(lat.C())
-        obs = np.stack(obs) + W.observation_noise((len(snaps),) + probs[0].shape)
-
-    def one_run():
-        lat.reset()
-        flush.add_(1.0)  # L2 flush on torch's stream
-        torch.cuda.synchronize()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        if inverse:
-            lat.grad(snaps, obs, 100)
-        else:
-            lat.step(nlbm)
-        ev1.record(stream)
-        ev1.synchronize()
-        return ev0.elapsed_time(ev1)
-
+    run = Runner(lbm, torch, args.workload, probs, fields, nlbm, precision, not args.no_autotune, flush)
     for _ in range(args.warmup):
-        one_run()
-    warm_status = lbm.lbm_sync(lat.h)  # a latched instability does not change the work timed
+        run.run_once()
+    warm_status = lbm.lbm_sync(run.lat.h)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    t_ms = []
-    for _ in range(args.steps):
-        t_ms.append(one_run())
+    t_ms = [run.run_once() for _ in range(args.steps)]
     torch.cuda.synchronize()
     clk = clocks.stop()
-    rc = lbm.lbm_sync(lat.h)
+    rc = lbm.lbm_sync(run.lat.h)
     value, total_ms = job_value(sum(t_ms), nodes * nlbm * args.steps, world, dist, "cuda")
-    lps = lat.launches_per_step
-    # 0: the fused step, one cooperative launch per lbm_step call of up to 4096 steps
-    gpu_launches = args.steps * (nlbm * lps if lps > 0 else -(-nlbm // 4096))
-    if inverse:
-        d0 = probs[0].d
-        # forward + checkpointed recompute (d+1 each) and adjoint (step, d transposes, d G sums, combine)
-        gpu_launches = args.steps * nlbm * (2 * (d0 + 1) + 2 + 2 * d0)
-
-    # ---- end to end through the C ABI with pinned host buffers
-    pins = [torch.from_numpy(np.ascontiguousarray(C0)).pin_memory() for C0 in fields]
-    outs = [torch.empty(p.shape, dtype=torch.float64).pin_memory() for p in pins]
-    e2e_s = []
-    if inverse:
-        obs_pin = torch.from_numpy(np.ascontiguousarray(obs)).pin_memory()
-    for k in range(args.steps):
-        flush.add_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i, p in enumerate(pins):
-            if batched:
-                lat.set_C(i, p.numpy())
-            else:
-                lat.set_C(p.numpy())
-        if inverse:  # observations go host -> device inside lbm_grad; loss and gradient come back
-            lat.grad(snaps, obs_pin.numpy(), 100)
-            e2e_s.append(time.perf_counter() - t0)
-            continue
-        lat.step(nlbm)
-        for i, o in enumerate(outs):
-            # data is copied; a latched instability is only reported
-            rc_e2e = (lbm._lib.lbm_batch_read_C(lat.h, i, lbm._dptr(o.numpy())) if batched
-                      else lbm._lib.lbm_read_C(lat.h, lbm._dptr(o.numpy())))
-            if rc_e2e not in (lbm.LBM_OK, lbm.LBM_ERR_UNSTABLE):
-                raise lbm.LBMError(rc_e2e, "read C")
-        e2e_s.append(time.perf_counter() - t0)
+    gpu_launches = args.steps * run.launches_per_bench_step()
+    e2e_s, h2d_bytes, d2h_bytes = run.e2e(args.steps)
     e2e_val, _ = job_value(1e3 * sum(e2e_s), nodes * nlbm * args.steps, world, dist, "cuda")
-    io_bytes = int(sum(C0.size for C0 in fields) * 8)
-    h2d_bytes, d2h_bytes = io_bytes, io_bytes
-    if inverse:
-        h2d_bytes = io_bytes + int(obs.size * 8)
-        d2h_bytes = 8 * (1 + 4 * probs[0].d)
-
-    # ---- dominant kernel, timed live with events on the library stream
-    nprof = min(nlbm, 200)
-    lat.reset()
-    ms_frac, ms_cs = lat.profile(nprof)
-    d = probs[0].d
-    Q = 2 * d + 1
-    peaks, peak_src = load_peaks()
-    elem = 8 if precision == "fp64" else 4
-    flops = float(sum(2.0 * pb.nodes * sum(pb.grid) for pb in probs))  # 2 side flops per node per axis
-    dur = ms_frac / nprof * 1e-3
-    achieved = flops / dur / 1e12
-    split_products = {"bf16split": 3, "tf32split": 3, "bf16x5split": 5}
-    if precision in split_products:
-        bound = "tensor"
-        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        if precision == "tf32split":
-            peak = peak / 2.0  # nominal tf32/bf16 ratio
-    else:
-        bound = "alu"
-        if precision == "fp32":
-            # FP32 FMA lanes x 2 flops x max SM clock
-            peak = SMS * FP32_LANES_PER_SM * 2.0 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        else:
-            peak = FP64_NOMINAL_TFLOPS
-    roof_op = {"kernel": "fractional_operator", "bound": bound, "achieved": achieved, "peak": peak,
-               "unit": "TFLOP/s", "frac": achieved / peak,
-               "traffic": traffic_for(args.workload, "fractional_operator", precision),
-               "algorithmic_per_launch": flops, "launch_ms": dur * 1e3, "peak_source": peak_src}
-    if precision in split_products:
-        # the split forms issue three (hi*hi, hi*lo, lo*hi) or five products per
-        # algorithmic one: the tensor pipe's own load
-        npr = split_products[precision]
-        roof_op["executed_per_launch"] = npr * flops
-        roof_op["executed_frac"] = npr * achieved / peak
+    roof, roof_other = run.rooflines(peaks, peak_src)
     if precision in ("tf32split", "fp64"):
         kind = "tf32" if precision == "tf32split" else "fp64"
+        roof_op = roof if roof["kernel"] == "fractional_operator" else roof_other
         roof_op[f"cublas_{kind}_tflops_measured"] = cublas_tflops(kind)
-    bytes_ = float(nodes) * (2 * Q * elem + d * elem + elem)
-    dur = ms_cs / nprof * 1e-3
-    achieved = bytes_ / dur / 1e9
-    peak = peaks.get("hbm_gbs", 6800.0)
-    roof_cs = {"kernel": "collide_stream", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-               "frac": achieved / peak, "traffic": traffic_for(args.workload, "collide_stream", precision),
-               "algorithmic_per_launch": bytes_, "launch_ms": dur * 1e3, "peak_source": peak_src}
-    if precision in split_products:
-        # the kernel also writes the operator's operands of the new C: its hi/lo split
-        # (x contiguous) and, for tf32 on the TMA-fed marches (one operator and one
-        # collide-stream launch per step), the copies regrouped along y (and z)
-        per_node = 8 if precision == "tf32split" else 4
-        if precision == "tf32split" and lat.launches_per_step == 2:
-            per_node += 8 * (d - 1)
-        ex = bytes_ + float(nodes) * per_node
-        roof_cs["executed_per_launch"] = ex
-        roof_cs["executed_frac"] = ex / dur / 1e9 / peak
-    # the dominant kernel is the roofline; the other one is reported beside it
-    roof, roof_other = (roof_op, roof_cs) if ms_frac >= ms_cs else (roof_cs, roof_op)
-    roof["other_kernel_ms"] = {"fractional_operator": ms_frac / nprof, "collide_stream": ms_cs / nprof}
 
     # ---- CPU baseline (oracle) and accuracy against it, rank 0 at N = 1 only
-    cpu = None
-    accuracy = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ns = max(2, min(nlbm, args.cpu_sample, int(1e8 // nodes)))
-        dt, refs, threads = 0.0, [], 1
-        for pb, C0 in zip(probs, fields):
-            t, C_ref, threads = oracle_sample(pb, C0, ns)
-            dt += t
-            refs.append(C_ref)
-        cpu = {"value": nodes * ns / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {ns} of {nlbm} lattice steps of {args.workload} (FP64, torch CPU)"}
-        lat.reset()
-        lat.step(ns)
-        got = [lat.C(i) for i in range(len(probs))] if batched else [lat.C()]
-        num = sum(float(np.sum((g - r) ** 2)) for g, r in zip(got, refs))
-        den = sum(float(np.sum(r ** 2)) for r in refs)
-        accuracy = {"rel_l2_vs_fp64_oracle": float(np.sqrt(num / den)), "lattice_steps": ns}
+    cpu, accuracy, refs, ns = None, None, None, 0
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not run.inverse:
+        ns = min(nlbm, args.oracle_steps or WORKLOADS[args.workload]["oracle_steps"])
+        refs, dt, threads = oracle_refs(probs, fields, ns)
+        cpu = {"value": nodes * ns / dt / 1e6, "unit": UNIT, "cores": threads, "host_cpus": os.cpu_count(),
+               "kind": "oracle", "sample": f"first {ns} of {nlbm} lattice steps of {args.workload} (FP64, torch CPU)"}
+        accuracy = run.accuracy(refs, ns)
+    tuned = run.tuned
+    run.close()
 
-    lat.close()
-
-    # the same workload in the five-product bf16 form, the split form that meets the 1e-5
-    # error target: timed the same way (library stream, L2 flushed per bench step) and
+    # ---- the other precision forms of the headline workload, timed the same way and
     # checked against the same oracle sample
-    at_target = None
-    if accuracy is not None and precision == "bf16split" and not batched and not inverse:
-        alt = "bf16x5split"
-        with lbm.Lattice(probs[0], fields[0], alt) as l5:
-            tuned5 = None if args.no_autotune else l5.autotune(64)
-            s5 = torch.cuda.ExternalStream(l5.stream)
+    forms = None
+    if refs is not None and args.workload == "mrt_aniso_512" and not args.no_extra:
+        forms = {}
+        for alt in HEADLINE_FORMS:
+            if alt == precision:
+                continue
+            r = Runner(lbm, torch, args.workload, probs, fields, nlbm, alt, not args.no_autotune, flush)
+            try:
+                ta, st = r.timed(max(2, args.steps // 2), args.warmup)
+                ms = sum(ta) / len(ta)
+                forms[alt] = {"dtype": DTYPES[alt], "value": nodes * nlbm / (ms * 1e-3) / 1e6, "unit": UNIT,
+                              "ms_per_step": ms, "launch_config": r.tuned if r.tuned is not None else "built-in",
+                              "accuracy": r.accuracy(refs, ns), "status": lbm.lbm_strerror(st)}
+            finally:
+                r.close()
 
-            def run5():
-                l5.reset()
-                flush.add_(1.0)
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(s5)
-                l5.step(nlbm)
-                e1.record(s5)
-                e1.synchronize()
-                return e0.elapsed_time(e1)
+    # ---- the other named workloads (N = 1 only)
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra and args.workload == "mrt_aniso_512":
+        extra = {}
+        for name in EXTRA_WORKLOADS:
+            try:
+                extra[name] = measure_extra(lbm, torch, name, flush, peaks, peak_src, not args.no_autotune)
+            except Exception as exc:  # reported, not hidden: the entry says what failed
+                extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
 
-            for _ in range(args.warmup):
-                run5()
-            ms5 = sum(run5() for _ in range(args.steps)) / args.steps
-            st5 = lbm.lbm_sync(l5.h)
-            l5.reset()
-            l5.step(accuracy["lattice_steps"])
-            C5 = l5.C()
-        err5 = float(np.sqrt(np.sum((C5 - refs[0]) ** 2) / np.sum(refs[0] ** 2)))
-        at_target = {"precision": alt, "dtype": "f32+bf16x5", "value": nodes * nlbm / (ms5 * 1e-3) / 1e6,
-                     "unit": UNIT, "ms_per_step": ms5, "launch_config": tuned5 if tuned5 is not None else "built-in",
-                     "accuracy": {"rel_l2_vs_fp64_oracle": err5, "lattice_steps": accuracy["lattice_steps"]},
-                     "status": lbm.lbm_strerror(st5)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "fp32": "f32", "bf16split": "f32+bf16x3", "tf32split": "f32+tf32x3",
-                          "bf16x5split": "f32+bf16x5"}[precision],
-                "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[precision], "data": "synthetic",
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
                            "precision": precision, "lattice_steps_per_bench_step": nlbm,
-                           "nodes": nodes, "problems": len(probs), "parallelism": f"replicas x{world}",
+                           "nodes": nodes, "problems": len(probs), "parallelism": parallelism,
                            "l2": "flushed (512 MiB write) before every bench step; state L2-resident within a run",
                            "launch_config": tuned if tuned is not None else "built-in"},
                 "roofline": roof, "roofline_other": roof_other, "cpu_baseline": cpu, "accuracy": accuracy,
-                "at_error_target": at_target,
+                "forms": forms, "workloads": extra,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
                         "d2h_bytes_per_step": d2h_bytes},
                 "gpu_launches": gpu_launches, "clocks": clk,

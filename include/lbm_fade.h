@@ -11,10 +11,13 @@
  *
  * One handle = one problem (or one batch of independent problems) on one GPU.
  * The handle owns every device buffer it uses (populations, concentration,
- * fractional terms, weight matrices); it allocates them with cudaMalloc in
- * lbm_create / lbm_create_batch and frees them in lbm_destroy.  The caller owns
- * every host array passed in; the library copies from / into it during the call
- * and keeps no pointer to it.
+ * fractional terms, weight matrices, tables, adjoint checkpoints).  It takes them,
+ * in lbm_create / lbm_create_batch (and lbm_grad for the checkpoints), from the
+ * device-memory hooks installed by lbm_set_allocator when the handle was created
+ * (for example PyTorch's caching allocator), otherwise from cudaMalloc, and gives
+ * them back the same way in lbm_destroy.  The caller owns every array passed in
+ * (host or device); the library copies from / into it during the call and keeps
+ * no pointer to it.
  *
  * Conventions
  *   - Grid: grid[mu] = nodes on axis mu including both wall nodes, so the axis
@@ -30,6 +33,11 @@
  * the process.  Launches are asynchronous on the handle's stream; errors raised
  * on the device (non-finite concentration, a bounded wait that gave up) are latched
  * and returned by the next synchronising call (lbm_sync, lbm_read_*, lbm_mass).
+ *
+ * Problems: a handle made by lbm_create holds one problem (index 0); one made by
+ * lbm_create_batch holds nprob problems (indices 0..nprob-1).  The accessors that
+ * take `prob` (lbm_read_C, lbm_mass, lbm_batch_set_C) return LBM_EINVAL for an index
+ * outside that range.
  */
 #ifndef LBM_FADE_H
 #define LBM_FADE_H
@@ -88,16 +96,16 @@ typedef struct {
 /* Create a problem and initialise it from C0.
  *   prm      : problem description (copied).
  *   C0_host  : initial concentration, grid[0]*grid[1]*grid[2] doubles (host).
+ *   out      : receives the handle.
  *   stream   : cudaStream_t to run on, or NULL to let the handle create its own
  *              non-blocking stream (destroyed with the handle).
- *   out      : receives the handle.
  * The initial populations are the equilibrium of C0 (Algorithm 1, initialisation;
  * f(x,0) is not stated by the paper, this is the reading taken).
  * Weight matrices (Section 2.4, Eqs. c+ and c-) are built on the host in FP64.
  * Returns LBM_EINVAL for alpha outside ]1,2], p outside [0,1], g <= 0, dx or dt <= 0,
  * a grid axis < 3, BGK with off-diagonal D, a non-SPD lambdabar, free rates outside
  * ]0,2[; LBM_ENOMEM / LBM_ECUDA on device failures (no handle is returned then). */
-int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t* out);
+int lbm_create(const lbm_params* prm, const double* C0_host, lbm_t* out, void* stream);
 
 /* Device-memory hooks.  A handle created after this call takes every device buffer it
  * owns (populations, C, F, operands, weights, tables, adjoint checkpoints) from
@@ -121,24 +129,17 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* ctx);
  * problem's tiles (FP32: one SIMT launch per problem and axis) and one grouped
  * collide-stream launch covering every problem's nodes.  On a batch handle lbm_step,
  * lbm_reset, lbm_sync, lbm_profile, lbm_get_stream, lbm_launches_per_step and
- * lbm_destroy act on all problems; the per-problem accessors are lbm_batch_read_C and
- * lbm_batch_mass; the single-problem accessors return LBM_EINVAL.
+ * lbm_destroy act on all problems; lbm_read_C, lbm_mass and lbm_batch_set_C take the
+ * problem's index; the other single-problem accessors return LBM_EINVAL.
  * Errors: LBM_EINVAL for mixed lattices/collisions/precisions or any invalid problem,
  * LBM_ENOTSUP for other precisions, LBM_ENOMEM / LBM_ECUDA as lbm_create. */
-int lbm_create_batch(int nprob, const lbm_params* prms, const double* const* C0_host, void* stream, lbm_t* out);
+int lbm_create_batch(int nprob, const lbm_params* prms, const double* const* C0_host, lbm_t* out, void* stream);
 
 /* Number of problems of a handle (1 for a single-problem handle). */
 int lbm_batch_size(lbm_t h, int* nprob);
 
-/* Concentration of problem `prob` (its nodes, host doubles); synchronises and returns
- * that problem's latched error, as lbm_read_C. */
-int lbm_batch_read_C(lbm_t h, int prob, double* C_host);
-
 /* Re-initialise problem `prob` from a new concentration (host doubles), as lbm_set_C. */
 int lbm_batch_set_C(lbm_t h, int prob, const double* C_host);
-
-/* FP64 mass of problem `prob`, as lbm_mass. */
-int lbm_batch_mass(lbm_t h, int prob, double* mass);
 
 /* Re-initialise the populations from a new concentration field (host, same layout
  * as lbm_create): f = feq(C, F(C)); clears any latched device error.  Asynchronous w.r.t. the device; the host
@@ -158,9 +159,14 @@ int lbm_reset(lbm_t h);
  * captured CUDA graphs. */
 int lbm_step(lbm_t h, int nsteps);
 
-/* Copy the current concentration into C_host (nodes doubles).  Synchronises the
- * handle's stream; returns a latched LBM_ERR_UNSTABLE if one was raised. */
-int lbm_read_C(lbm_t h, double* C_host);
+/* Current concentration C = <1|f> of problem `prob` (Algorithm 1, loop item 5), as
+ * that problem's grid[0]*grid[1]*grid[2] doubles in the field layout above, written to
+ * dst: a host array (dst_is_device = 0) or a device array of the handle's GPU
+ * (dst_is_device != 0; converted to FP64 on the device, no host round trip), owned by
+ * the caller.  Synchronises the handle's stream; returns that problem's latched
+ * LBM_ERR_UNSTABLE or LBM_ERR_TIMEOUT if one was raised (the data is copied even then);
+ * LBM_EINVAL for a null dst or a bad problem index. */
+int lbm_read_C(lbm_t h, int prob, void* dst, int dst_is_device);
 
 /* Fractional term F_mu (mu = 0..d-1) of the current concentration,
  * F_mu = p I+(g h C) + (1-p) I-(g h C) discretised by Eq. (XXminus_discret),
@@ -221,9 +227,11 @@ long long lbm_state_size(lbm_t h);
 int lbm_save(lbm_t h, void* dst_host, long long bytes);
 int lbm_load(lbm_t h, const void* src_host, long long bytes);
 
-/* Total mass sum_x C(x) of the current concentration, reduced on the device in
- * FP64 (block partials, then one final pass).  Synchronises. */
-int lbm_mass(lbm_t h, double* mass);
+/* Total mass sum_x C(x) of problem `prob`'s current concentration (Algorithm 1, loop
+ * item 5), reduced on the device in FP64 (block partials, then one final pass), into
+ * the host double *mass.  Synchronises; returns the problem's latched error as
+ * lbm_read_C does. */
+int lbm_mass(lbm_t h, int prob, double* mass);
 
 /* Wait for all work of the handle; return a latched device error if any. */
 int lbm_sync(lbm_t h);
@@ -264,7 +272,10 @@ int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host);
  * (65,536 partials of 1,024 elements); larger n returns LBM_ETOOBIG, n < 0 or a
  * bad pointer / elem_bytes returns LBM_EINVAL.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the one
+ * make that first call before any stream capture.  The address is cached for the
+ * life of the process: after a cudaDeviceReset of that device in the same process
+ * the cached address is stale and the entry point must not be called again.  All
+ * calls share the one
  * array, which keeps the last call's partials: each call overwrites every
  * partial it reads, and calls that overlap on the GPU (different streams, no
  * ordering between them) race on it and must be serialised by the caller. */

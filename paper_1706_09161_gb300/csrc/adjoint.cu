@@ -445,7 +445,7 @@ int run_adjoint(lbm_s* h, const AdjHooks& hooks, int nsnap, const int* snaps, co
   const int nck = T / ckpt + 1;
   const int seglen = ckpt < T ? ckpt : (T > 0 ? T : 1);
   const int nb = static_cast<int>((nodes + kThreads - 1) / kThreads);
-  const int cb = std::min<long long>((nodes + kThreads - 1) / kThreads, 152 * 8);
+  const int cb = std::min<long long>((nodes + kThreads - 1) / kThreads, 8LL * device_sms());
   Buffers B{h, {}};
   real* obs = static_cast<real*>(B.get(E * nodes * nsnap));
   real* ck = static_cast<real*>(B.get(E * Q * nodes * nck));

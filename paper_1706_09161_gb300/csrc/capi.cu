@@ -13,6 +13,21 @@
 
 namespace lbm {
 
+int device_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev >= 0 && dev < kMaxDev) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+  if (dev >= 0 && dev < kMaxDev) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
 cudaError_t dev_alloc(const lbm_s* h, void** p, size_t bytes) {
   if (h->mem.alloc) {
     *p = h->mem.alloc(bytes, h->stream, h->mem.ctx);
@@ -471,11 +486,11 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   return LBM_OK;
 }
 
-int lbm_create(const lbm_params* prm, const double* C0_host, void* stream, lbm_t* out) {
+int lbm_create(const lbm_params* prm, const double* C0_host, lbm_t* out, void* stream) {
   return create_problem(prm, C0_host, stream, false, out);
 }
 
-int lbm_create_batch(int nprob, const lbm_params* prms, const double* const* C0_host, void* stream, lbm_t* out) {
+int lbm_create_batch(int nprob, const lbm_params* prms, const double* const* C0_host, lbm_t* out, void* stream) {
   if (!out || !prms || !C0_host || nprob < 1) return LBM_EINVAL;
   *out = nullptr;
   const lbm_params& p0 = prms[0];
@@ -535,26 +550,12 @@ int lbm_batch_size(lbm_t h, int* nprob) {
   return LBM_OK;
 }
 
-int lbm_batch_read_C(lbm_t h, int prob, double* C_host) {
-  if (!h || !C_host) return LBM_EINVAL;
-  if (!h->is_batch()) return prob == 0 ? lbm_read_C(h, C_host) : LBM_EINVAL;
-  if (prob < 0 || prob >= static_cast<int>(h->subs.size())) return LBM_EINVAL;
-  return lbm_read_C(h->subs[prob], C_host);
-}
-
 int lbm_batch_set_C(lbm_t h, int prob, const double* C_host) {
   if (!h || !C_host) return LBM_EINVAL;
   if (!h->is_batch()) return prob == 0 ? lbm_set_C(h, C_host) : LBM_EINVAL;
   if (prob < 0 || prob >= static_cast<int>(h->subs.size())) return LBM_EINVAL;
   h->subs[prob]->cur = h->cur;
   return lbm_set_C(h->subs[prob], C_host);
-}
-
-int lbm_batch_mass(lbm_t h, int prob, double* mass) {
-  if (!h || !mass) return LBM_EINVAL;
-  if (!h->is_batch()) return prob == 0 ? lbm_mass(h, mass) : LBM_EINVAL;
-  if (prob < 0 || prob >= static_cast<int>(h->subs.size())) return LBM_EINVAL;
-  return lbm_mass(h->subs[prob], mass);
 }
 
 int lbm_set_C(lbm_t h, const double* C_host) {
@@ -657,13 +658,26 @@ int lbm_step(lbm_t h, int nsteps) {
   return LBM_OK;
 }
 
-int lbm_read_C(lbm_t h, double* C_host) {
-  if (!h || !C_host) return LBM_EINVAL;
-  if (h->is_batch()) return LBM_EINVAL;
-  const long long nodes = h->sp.nodes;
-  LBM_CUDA(lbm::launch_convert_out(h->dev.C, h->elem, h->dev.stage, nodes, h->stream));
-  LBM_CUDA(cudaMemcpyAsync(C_host, h->dev.stage, sizeof(double) * nodes, cudaMemcpyDeviceToHost, h->stream));
-  return latched(h);
+// problem `prob` of a handle: the handle itself (single problem, prob 0) or a batch member
+static lbm_s* member(lbm_t h, int prob) {
+  if (!h) return nullptr;
+  if (!h->is_batch()) return prob == 0 ? h : nullptr;
+  if (prob < 0 || prob >= static_cast<int>(h->subs.size())) return nullptr;
+  return h->subs[prob];
+}
+
+int lbm_read_C(lbm_t h, int prob, void* dst, int dst_is_device) {
+  lbm_s* p = member(h, prob);
+  if (!p || !dst) return LBM_EINVAL;
+  const long long nodes = p->sp.nodes;
+  if (dst_is_device) {
+    // straight into the caller's device array, converted to FP64 on the way
+    LBM_CUDA(lbm::launch_convert_out(p->dev.C, p->elem, static_cast<double*>(dst), nodes, h->stream));
+  } else {
+    LBM_CUDA(lbm::launch_convert_out(p->dev.C, p->elem, p->dev.stage, nodes, h->stream));
+    LBM_CUDA(cudaMemcpyAsync(dst, p->dev.stage, sizeof(double) * nodes, cudaMemcpyDeviceToHost, h->stream));
+  }
+  return latched(p);
 }
 
 int lbm_read_F(lbm_t h, int mu, double* F_host) {
@@ -951,17 +965,18 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
       if (ks <= kbmin) ops.push_back({0, ks, 0, cur.chunk});
     }
   if (!h->is_batch() && h->tc) {
+    const int sms = lbm::device_sms();
     const int kbmin = lbm::tc_kbmin(h);
     const bool five = h->prm.precision == LBM_FP32_BF16SPLIT5;  // per-tile kernel, 64/128 columns
     for (int bn : {64, 128, 256})
       for (int ks : {1, 2, 4, 8}) {
         if (bn == 256 && (ks != 1 || five)) continue;
         if (ks > kbmin) continue;
-        if (lbm::tc_count_tiles(h, bn) * ks > 2 * 152) continue;  // at most two waves
+        if (lbm::tc_count_tiles(h, bn) * ks > 2LL * sms) continue;  // at most two waves
         ops.push_back({bn, ks, 0, cur.chunk});
       }
-    if (!five && lbm::tc_count_tiles(h, 128) >= 152) ops.push_back({128, 1, 1, cur.chunk});
-    if (!five && lbm::tc_count_tiles(h, 256) >= 152) ops.push_back({256, 1, 1, cur.chunk});
+    if (!five && lbm::tc_count_tiles(h, 128) >= sms) ops.push_back({128, 1, 1, cur.chunk});
+    if (!five && lbm::tc_count_tiles(h, 256) >= sms) ops.push_back({256, 1, 1, cur.chunk});
     // the fused step where the plan is one it covers (2-D bf16, 64/128 columns, split 2 or 4)
     const size_t nops = ops.size();
     for (size_t i = 0; i < nops; ++i)
@@ -1026,12 +1041,12 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
   return LBM_OK;
 }
 
-int lbm_mass(lbm_t h, double* mass) {
-  if (!h || !mass) return LBM_EINVAL;
-  if (h->is_batch()) return LBM_EINVAL;
-  LBM_CUDA(lbm::launch_mass(h, h->dev.C, h->stream));
-  LBM_CUDA(cudaMemcpyAsync(mass, h->dev.scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  return latched(h);
+int lbm_mass(lbm_t h, int prob, double* mass) {
+  lbm_s* p = member(h, prob);
+  if (!p || !mass) return LBM_EINVAL;
+  LBM_CUDA(lbm::launch_mass(p, p->dev.C, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(mass, p->dev.scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return latched(p);
 }
 
 int lbm_sync(lbm_t h) {

@@ -1110,13 +1110,8 @@ size_t fused_smem() {
 
 template <int BN, int KS, bool MRT>
 cudaError_t fused_attr(int* blocks_per_sm) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(lbm_fused2_kernel<BN, KS, MRT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<BN, KS>());
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (const cudaError_t e = smem_attr_once(attr, lbm_fused2_kernel<BN, KS, MRT>, (int)fused_smem<BN, KS>()); e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lbm_fused2_kernel<BN, KS, MRT>, NT,
                                                        fused_smem<BN, KS>());
 }
@@ -1224,13 +1219,8 @@ template <bool MRT, int SPLIT>
 cudaError_t launch_tma3(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, const CUtensorMap& mf,
                         const CUtensorMap& mF, float* fo, float* Co, int* flag, const SplitOut& so, int nz,
                         int early) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(collide_stream_tma3_kernel<MRT, SPLIT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (const cudaError_t e = smem_attr_once(attr, collide_stream_tma3_kernel<MRT, SPLIT>, (int)TMA_SMEM); e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, collide_stream_tma3_kernel<MRT, SPLIT>, sp, mf, mF, fo, Co, flag, so, nz, early);
 }
 
@@ -1238,30 +1228,20 @@ template <bool MRT, int SPLIT>
 cudaError_t launch_tma2(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, const CUtensorMap& mf,
                         const CUtensorMap& mF, float* fo, float* Co, int* flag, const SplitOut& so, int ychunk,
                         int early) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(collide_stream_tma2_kernel<MRT, SPLIT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma2_smem(8));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (const cudaError_t e = smem_attr_once(attr, collide_stream_tma2_kernel<MRT, SPLIT>, (int)tma2_smem(8)); e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, collide_stream_tma2_kernel<MRT, SPLIT>, sp, mf, mF, fo, Co, flag, so, ychunk,
                             early);
 }
 
 // at most two blocks per SM resident: the grid runs in one wave
-bool one_wave(const dim3& g) { return (long long)g.x * g.y * g.z <= 2 * 152; }
+bool one_wave(const dim3& g) { return (long long)g.x * g.y * g.z <= 2LL * device_sms(); }
 
 template <bool MRT, int SPLIT>
 cudaError_t launch_march2(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, const float* fi, const float* F,
                           float* fo, float* Co, int* flag, const SplitOut& so, int ychunk, int early) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(collide_stream_march2_kernel<MRT, SPLIT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (const cudaError_t e = smem_attr_once(attr, collide_stream_march2_kernel<MRT, SPLIT>, PIPE_SMEM); e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, collide_stream_march2_kernel<MRT, SPLIT>, sp, fi, F, fo, Co, flag, so, ychunk,
                             early);
 }
@@ -1271,10 +1251,11 @@ cudaError_t launch_march2(const cudaLaunchConfig_t& cfg, const KConst<float>& sp
 // each chunk re-colliding two planes at its start; chunks of at least 16 planes
 int z_chunks(long long cols, int n2) {
   if (n2 < 32) return 1;
+  const int sms = device_sms();
   int best = 1;
   double best_eff = 0.0;
   for (int nz = 1; nz <= n2 / 16; ++nz) {
-    const double waves = static_cast<double>(cols * nz) / (2 * 152);
+    const double waves = static_cast<double>(cols * nz) / (2 * sms);
     const double eff = waves / std::ceil(waves);
     const double zc = static_cast<double>(n2) / nz;
     const double score = eff * zc / (zc + 2.0);
@@ -1288,7 +1269,8 @@ int z_chunks(long long cols, int n2) {
 
 // tile rows per 2-D block: ceil(tiles / 304) (one wave of two blocks per SM), at most by
 int ychunk_for(long long tiles, int by) {
-  const long long c = (tiles + 2 * 152 - 1) / (2 * 152);
+  const long long w = 2LL * device_sms();
+  const long long c = (tiles + w - 1) / w;
   return static_cast<int>(std::max<long long>(1, std::min<long long>(c, by)));
 }
 
@@ -1365,7 +1347,8 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
 
 int grid_for(long long n) {
   long long b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  const long long cap = 16LL * device_sms();
+  if (b > cap) b = cap;
   return static_cast<int>(b < 1 ? 1 : b);
 }
 
@@ -1548,16 +1531,13 @@ cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t
   const int g = b->batch_cs_blocks;
   const int smem = (h0->d == 2) ? BATCH2_SMEM : 0;
   if (h0->d == 2) {
-    static bool attr[2][2] = {{false, false}, {false, false}};
-    if (!attr[mrt][split]) {
-      cudaError_t e;
-      if (mrt) e = split ? cudaFuncSetAttribute(collide_stream_batch_kernel<2, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, BATCH2_SMEM)
-                         : cudaFuncSetAttribute(collide_stream_batch_kernel<2, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, BATCH2_SMEM);
-      else e = split ? cudaFuncSetAttribute(collide_stream_batch_kernel<2, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, BATCH2_SMEM)
-                     : cudaFuncSetAttribute(collide_stream_batch_kernel<2, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, BATCH2_SMEM);
-      if (e != cudaSuccess) return e;
-      attr[mrt][split] = true;
-    }
+    static std::atomic<unsigned long long> attr[2][2] = {{{0}, {0}}, {{0}, {0}}};
+    cudaError_t e;
+    if (mrt) e = split ? smem_attr_once(attr[1][1], collide_stream_batch_kernel<2, true, 1>, BATCH2_SMEM)
+                       : smem_attr_once(attr[1][0], collide_stream_batch_kernel<2, true, 0>, BATCH2_SMEM);
+    else e = split ? smem_attr_once(attr[0][1], collide_stream_batch_kernel<2, false, 1>, BATCH2_SMEM)
+                   : smem_attr_once(attr[0][0], collide_stream_batch_kernel<2, false, 0>, BATCH2_SMEM);
+    if (e != cudaSuccess) return e;
   }
 #define LBM_CSB(D_, M_, S_) collide_stream_batch_kernel<D_, M_, S_><<<g, block, smem, s>>>(tab, b->batch_cs_start, P, parity)
   if (h0->d == 2) {

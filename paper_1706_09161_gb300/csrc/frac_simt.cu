@@ -203,7 +203,7 @@ bool simt_blocks_fit(long long blocks) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, frac_simt_kernel<real, BM, BN, TM, TN>, 256, 0) !=
           cudaSuccess)
     per_sm = 0;
-  return blocks <= (long long)per_sm * 152;
+  return blocks <= (long long)per_sm * device_sms();
 }
 
 // 64 x 64 tiles where they give two blocks per SM (with the handle's contraction split,
@@ -224,7 +224,7 @@ cudaError_t frac_all_axes(const lbm_s* h, const real* C, real* F, cudaStream_t s
   cfg.attrs = at;
   cfg.numAttrs = 1;
   GemmPlan big = make_plan<real, 64, 64>(h, C, F, transpose, cstride, ks, ks > 1 ? h->sp.pstride : 0);
-  if (big.total >= 2 * 152 || ks > 1) {
+  if (big.total >= 2LL * device_sms() || ks > 1) {
     big.early = pdl && simt_blocks_fit<real, 64, 64, 4, 4>(big.total);
     cfg.gridDim = dim3(static_cast<unsigned>(big.total), 1, 1);
     return cudaLaunchKernelEx(&cfg, frac_simt_kernel<real, 64, 64, 4, 4>, big);
@@ -242,7 +242,7 @@ bool simt_one_wave(const lbm_s* h) {
   const float* C = static_cast<const float*>(h->dev.C);
   float* F = static_cast<float*>(h->dev.F);
   GemmPlan big = make_plan<float, 64, 64>(h, C, F, false, 0, h->sp.ksum, h->sp.pstride);
-  if (big.total >= 2 * 152 || h->sp.ksum > 1) return simt_blocks_fit<float, 64, 64, 4, 4>(big.total);
+  if (big.total >= 2LL * device_sms() || h->sp.ksum > 1) return simt_blocks_fit<float, 64, 64, 4, 4>(big.total);
   GemmPlan small = make_plan<float, 32, 32>(h, C, F, false, 0);
   return simt_blocks_fit<float, 32, 32, 2, 2>(small.total);
 }
@@ -257,7 +257,8 @@ int simt_ksplit(const lbm_s* h) {
   int kbmin = 1 << 30;
   for (int mu = 0; mu < h->d; ++mu) kbmin = std::min(kbmin, (h->sp.n[mu] + 31) / 32);  // BK = 32 (FP32)
   int ks = 1;
-  while (ks * 2 <= 8 && ks * 2 <= kbmin && tiles * ks < 2 * 152) ks *= 2;
+  const long long w = 2LL * device_sms();
+  while (ks * 2 <= 8 && ks * 2 <= kbmin && tiles * ks < w) ks *= 2;
   return ks;
 }
 

@@ -578,13 +578,8 @@ bool encode(CUtensorMap* m, int elem, int rank, void* base, const cuuint64_t* di
 
 template <int E, int BN, int KS, int KP = 2>
 cudaError_t launch_kernel(const TcPlan* p, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(frac_tc_kernel<E, BN, KS, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg<E, BN, KS, KP>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (const cudaError_t e = smem_attr_once(attr, frac_tc_kernel<E, BN, KS, KP>, (int)Cfg<E, BN, KS, KP>::SMEM); e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->prm.total_tiles * KS, 1, 1);
   cfg.blockDim = dim3(128, 1, 1);
@@ -608,19 +603,13 @@ cudaError_t launch_bn(const TcPlan* p, cudaStream_t s) {
   }
 }
 
-constexpr int kPersistCTAs = 152;  // one per SM
 
 template <int E, int BN>
 cudaError_t launch_persist(const TcPlan* p, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(frac_tc_persist_kernel<E, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)PCfg<E, BN>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (const cudaError_t e = smem_attr_once(attr, frac_tc_persist_kernel<E, BN>, (int)PCfg<E, BN>::SMEM); e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(std::min(p->prm.total_tiles, kPersistCTAs), 1, 1);
+  cfg.gridDim = dim3(std::min(p->prm.total_tiles, device_sms()), 1, 1);  // one CTA per SM
   cfg.blockDim = dim3(kPersistThreads, 1, 1);
   cfg.dynamicSmemBytes = PCfg<E, BN>::SMEM;
   cfg.stream = s;
@@ -724,7 +713,7 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   // or 256 when that still fills the GPU; small problems split the contraction over up
   // to 8 CTAs per tile so that about one CTA per SM is busy; many tiles: the persistent
   // kernel (128-column tiles, no split); batched handles always use it
-  constexpr int kSMs = 152;
+  const int kSMs = device_sms();
   int bn = (p->kparts == 2 && tc_count_tiles(h, 256) >= kSMs) ? 256 : 128;
   const int kbmin = tc_kbmin(h);
   int ks = 1;
@@ -792,7 +781,7 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
   P.flag = h->dev.flag;
   const cuuint64_t cdims[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
   const cuuint64_t cstr[2] = {(cuuint64_t)ldp * E, (cuuint64_t)ldp * n[1] * E};
-  constexpr int kSMs = 152;
+  const int kSMs = device_sms();
   P.ksplit = ks;
   P.tma_store = (n[0] % 4 == 0) ? 1 : 0;
   int tiles = 0;
@@ -921,14 +910,9 @@ int tc_batch_prepare(lbm_s* b) {
 }
 
 cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(frac_tc_persist_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)PCfg<2>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int grid = std::min(b->batch_tc_blocks, kPersistCTAs);
+  static std::atomic<unsigned long long> attr{0};
+  if (const cudaError_t e = smem_attr_once(attr, frac_tc_persist_batch_kernel<2>, (int)PCfg<2>::SMEM); e != cudaSuccess) return e;
+  const int grid = std::min(b->batch_tc_blocks, device_sms());  // one CTA per SM
   frac_tc_persist_batch_kernel<2><<<grid, kPersistThreads, PCfg<2>::SMEM, s>>>(
       static_cast<const TcMaps*>(b->batch_tc_maps), static_cast<const TcParams*>(b->batch_tc_prm), b->batch_tc_start,
       static_cast<int>(b->subs.size()), b->batch_tc_blocks, b->dev.flag);
@@ -967,7 +951,7 @@ void tc_config(const lbm_s* h, int* bn, int* ks, int* persist) {
 
 bool tc_one_wave(const lbm_s* h) {
   const TcPlan* p = h->tc;
-  return p && (p->persist || (long long)p->prm.total_tiles * p->prm.ksplit <= kPersistCTAs);
+  return p && (p->persist || (long long)p->prm.total_tiles * p->prm.ksplit <= device_sms());
 }
 
 void tc_set_pdl(lbm_s* h, bool on) {
@@ -1014,7 +998,8 @@ cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s) {
   const TcPlan* p = h->tc;
   if (!p) return cudaErrorNotSupported;
   long long b = (h->sp.nodes + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  const long long cap = 16LL * device_sms();
+  if (b > cap) b = cap;
   if (p->elem == 2)
     split_C_kernel<2><<<(int)b, 256, 0, s>>>(static_cast<const float*>(h->dev.C), h->dev.Chi, h->dev.Clo, h->sp.n[0],
                                              h->sp.n[1], h->sp.n[2], p->ldp);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <vector>
 
@@ -98,6 +99,24 @@ struct lbm_s {
 };
 
 namespace lbm {
+
+// streaming multiprocessors of the current device (queried once per device)
+int device_sms();
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per device for one kernel:
+// `done` is a static of the calling launcher (one per kernel instantiation), bit d of it
+// stands for device d.
+template <typename Kernel>
+cudaError_t smem_attr_once(std::atomic<unsigned long long>& done, Kernel k, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // a handle's device memory: through its hooks, else cudaMalloc / cudaFree
 cudaError_t dev_alloc(const lbm_s* h, void** p, size_t bytes);

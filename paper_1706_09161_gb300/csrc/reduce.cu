@@ -79,7 +79,8 @@ __global__ void sum_partials_kernel(const float* __restrict__ src, int k, long l
 
 int blocks_for(long long n) {
   long long b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  const long long cap = 16LL * device_sms();
+  if (b > cap) b = cap;
   return static_cast<int>(b < 1 ? 1 : b);
 }
 

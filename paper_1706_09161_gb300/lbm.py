@@ -67,17 +67,15 @@ def _load() -> ctypes.CDLL:
     dp = P(ctypes.c_double)
     vp = ctypes.c_void_p
     sig = {
-        "lbm_create": (ctypes.c_int, [P(lbm_params), dp, vp, P(vp)]),
-        "lbm_create_batch": (ctypes.c_int, [ctypes.c_int, P(lbm_params), P(dp), vp, P(vp)]),
+        "lbm_create": (ctypes.c_int, [P(lbm_params), dp, P(vp), vp]),
+        "lbm_create_batch": (ctypes.c_int, [ctypes.c_int, P(lbm_params), P(dp), P(vp), vp]),
         "lbm_batch_size": (ctypes.c_int, [vp, P(ctypes.c_int)]),
-        "lbm_batch_read_C": (ctypes.c_int, [vp, ctypes.c_int, dp]),
-        "lbm_batch_mass": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "lbm_batch_set_C": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "lbm_set_C": (ctypes.c_int, [vp, dp]),
         "lbm_reset": (ctypes.c_int, [vp]),
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_profile": (ctypes.c_int, [vp, ctypes.c_int, dp]),
-        "lbm_read_C": (ctypes.c_int, [vp, dp]),
+        "lbm_read_C": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
         "lbm_read_F": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "lbm_read_f": (ctypes.c_int, [vp, dp]),
         "lbm_write_f": (ctypes.c_int, [vp, dp]),
@@ -86,7 +84,7 @@ def _load() -> ctypes.CDLL:
         "lbm_configure": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "lbm_save": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
         "lbm_load": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
-        "lbm_mass": (ctypes.c_int, [vp, dp]),
+        "lbm_mass": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "lbm_sync": (ctypes.c_int, [vp]),
         "lbm_get_stream": (ctypes.c_int, [vp, P(vp)]),
         "lbm_launches_per_step": (ctypes.c_int, [vp, P(ctypes.c_int)]),
@@ -111,7 +109,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 
 # Declared C entry points, re-exported under their own names.
-EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_read_C", "lbm_batch_mass", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f", "lbm_state_size", "lbm_save", "lbm_load", "lbm_autotune", "lbm_configure",
+EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f", "lbm_state_size", "lbm_save", "lbm_load", "lbm_autotune", "lbm_configure",
             "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_wait_check", "lbm_set_allocator",
             "lbm_frac_matrix",
             "lbm_grad", "lbm_frac_matrix_grad", "lbm_digamma", "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
@@ -161,7 +159,7 @@ def params_from_problem(pb, precision: str = "fp32") -> lbm_params:
 def lbm_create(prm: lbm_params, C0: np.ndarray, stream: Optional[int] = None) -> int:
     C0 = np.ascontiguousarray(C0, dtype=np.float64)
     h = ctypes.c_void_p()
-    _check(_lib.lbm_create(ctypes.byref(prm), _dptr(C0), ctypes.c_void_p(stream or 0), ctypes.byref(h)),
+    _check(_lib.lbm_create(ctypes.byref(prm), _dptr(C0), ctypes.byref(h), ctypes.c_void_p(stream or 0)),
            "lbm_create")
     return h.value
 
@@ -172,7 +170,7 @@ def lbm_create_batch(prms, C0s, stream: Optional[int] = None) -> int:
     fields = [np.ascontiguousarray(c, dtype=np.float64) for c in C0s]
     ptrs = (ctypes.POINTER(ctypes.c_double) * n)(*[_dptr(f) for f in fields])
     h = ctypes.c_void_p()
-    _check(_lib.lbm_create_batch(n, arr, ptrs, ctypes.c_void_p(stream or 0), ctypes.byref(h)), "lbm_create_batch")
+    _check(_lib.lbm_create_batch(n, arr, ptrs, ctypes.byref(h), ctypes.c_void_p(stream or 0)), "lbm_create_batch")
     return h.value
 
 
@@ -182,21 +180,9 @@ def lbm_batch_size(h: int) -> int:
     return n.value
 
 
-def lbm_batch_read_C(h: int, prob: int, out: np.ndarray) -> np.ndarray:
-    assert out.dtype == np.float64 and out.flags.c_contiguous
-    _check(_lib.lbm_batch_read_C(ctypes.c_void_p(h), int(prob), _dptr(out)), "lbm_batch_read_C")
-    return out
-
-
 def lbm_batch_set_C(h: int, prob: int, C: np.ndarray) -> None:
     C = np.ascontiguousarray(C, dtype=np.float64)
     _check(_lib.lbm_batch_set_C(ctypes.c_void_p(h), int(prob), _dptr(C)), "lbm_batch_set_C")
-
-
-def lbm_batch_mass(h: int, prob: int) -> float:
-    m = ctypes.c_double()
-    _check(_lib.lbm_batch_mass(ctypes.c_void_p(h), int(prob), ctypes.byref(m)), "lbm_batch_mass")
-    return m.value
 
 
 def lbm_set_C(h: int, C: np.ndarray) -> None:
@@ -218,10 +204,16 @@ def lbm_step(h: int, nsteps: int) -> None:
     _check(_lib.lbm_step(ctypes.c_void_p(h), int(nsteps)), "lbm_step")
 
 
-def lbm_read_C(h: int, out: np.ndarray) -> np.ndarray:
+def lbm_read_C(h: int, prob: int, out: np.ndarray) -> np.ndarray:
+    """Concentration of problem `prob` into a host float64 array."""
     assert out.dtype == np.float64 and out.flags.c_contiguous
-    _check(_lib.lbm_read_C(ctypes.c_void_p(h), _dptr(out)), "lbm_read_C")
+    _check(_lib.lbm_read_C(ctypes.c_void_p(h), int(prob), out.ctypes.data_as(ctypes.c_void_p), 0), "lbm_read_C")
     return out
+
+
+def lbm_read_C_device(h: int, prob: int, dst_ptr: int) -> None:
+    """Concentration of problem `prob` into a caller-owned device float64 array (by address)."""
+    _check(_lib.lbm_read_C(ctypes.c_void_p(h), int(prob), ctypes.c_void_p(dst_ptr), 1), "lbm_read_C")
 
 
 def lbm_read_F(h: int, mu: int, out: np.ndarray) -> np.ndarray:
@@ -271,9 +263,9 @@ def lbm_write_f(h: int, f: np.ndarray) -> None:
     _check(_lib.lbm_write_f(ctypes.c_void_p(h), _dptr(f)), "lbm_write_f")
 
 
-def lbm_mass(h: int) -> float:
+def lbm_mass(h: int, prob: int = 0) -> float:
     m = ctypes.c_double()
-    _check(_lib.lbm_mass(ctypes.c_void_p(h), ctypes.byref(m)), "lbm_mass")
+    _check(_lib.lbm_mass(ctypes.c_void_p(h), int(prob), ctypes.byref(m)), "lbm_mass")
     return m.value
 
 
@@ -414,7 +406,13 @@ class Lattice:
         return lbm_profile(self.h, n)
 
     def C(self) -> np.ndarray:
-        return lbm_read_C(self.h, np.empty(self.shape, dtype=np.float64))
+        return lbm_read_C(self.h, 0, np.empty(self.shape, dtype=np.float64))
+
+    def C_into(self, out) -> None:
+        """Concentration into a CUDA float64 tensor of the field's shape (no host round trip)."""
+        assert out.is_cuda and out.dtype.is_floating_point and out.element_size() == 8 and out.is_contiguous()
+        assert tuple(out.shape) == self.shape
+        lbm_read_C_device(self.h, 0, out.data_ptr())
 
     def F(self, mu: int) -> np.ndarray:
         return lbm_read_F(self.h, mu, np.empty(self.shape, dtype=np.float64))
@@ -442,7 +440,7 @@ class Lattice:
         lbm_load(self.h, state)
 
     def mass(self) -> float:
-        return lbm_mass(self.h)
+        return lbm_mass(self.h, 0)
 
     def sync(self) -> None:
         _check(lbm_sync(self.h), "lbm_sync")
@@ -492,13 +490,19 @@ class Batch:
         lbm_reset(self.h)
 
     def C(self, prob: int) -> np.ndarray:
-        return lbm_batch_read_C(self.h, prob, np.empty(self.shapes[prob], dtype=np.float64))
+        return lbm_read_C(self.h, prob, np.empty(self.shapes[prob], dtype=np.float64))
+
+    def C_into(self, prob: int, out) -> None:
+        """Concentration of problem `prob` into a CUDA float64 tensor of its shape."""
+        assert out.is_cuda and out.element_size() == 8 and out.is_contiguous()
+        assert tuple(out.shape) == self.shapes[prob]
+        lbm_read_C_device(self.h, prob, out.data_ptr())
 
     def set_C(self, prob: int, C: np.ndarray) -> None:
         lbm_batch_set_C(self.h, prob, C)
 
     def mass(self, prob: int) -> float:
-        return lbm_batch_mass(self.h, prob)
+        return lbm_mass(self.h, prob)
 
     def autotune(self, nsteps: int = 64) -> str:
         """Time the candidate tile rows per collide-stream block and keep the fastest."""

@@ -5,7 +5,8 @@ float32 tensors, with the fractional operator's operands rounded exactly as a
 precision form rounds them (none; bf16 or tf32 hi+lo with three products, lo*lo
 dropped; bf16 with the weights in three parts and C in two, five products).  Its distance to the FP64 oracle is the error that arithmetic
 itself makes on the problem; the GPU result must stay within a small multiple
-of it.  No GPU code is involved.
+of it, both as a relative L2 over all nodes and node by node (max |error| over
+max |C|).  No GPU code is involved.
 """
 import numpy as np
 import torch
@@ -80,7 +81,37 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def node_err(a, b):
+    """Largest error at any node, relative to the largest |value|: max|a - b| / max|b|."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
 def bound(pb, C0, n, kind="fp32", factor=10.0, floor=1e-5):
     """max(floor, factor x the error the form's arithmetic makes on this problem)."""
     ref = O.run_C(pb, C0, n).numpy()
     return max(floor, factor * rel_l2(rerun(pb, C0, n, kind), ref))
+
+
+def bounds(pb, C0, n, kind="fp32", factor=4.0, floor=1e-5, C_ref=None):
+    """(relative-L2 bound, per-node bound) for the form `kind` on this problem: `factor`
+    x the errors the form's own arithmetic makes when re-run on the CPU (relative L2 and
+    max|C - C_ref| / max|C_ref|), never below `floor`; and the oracle's C."""
+    ref = O.run_C(pb, C0, n).numpy() if C_ref is None else C_ref
+    cpu = rerun(pb, C0, n, kind)
+    return (max(floor, factor * rel_l2(cpu, ref)), max(floor, factor * node_err(cpu, ref)), ref)
+
+
+def assert_close(C, C_ref, l2_tol, node_tol, what=""):
+    """Whole-field relative L2 AND every node (walls, corners, tile seams included):
+    max|C - C_ref| <= node_tol x max|C_ref|."""
+    e2, en = rel_l2(C, C_ref), node_err(C, C_ref)
+    assert e2 < l2_tol, f"{what}: relative L2 {e2:.3e} >= {l2_tol:.3e}"
+    assert en < node_tol, f"{what}: node error {en:.3e} (of max |C|) >= {node_tol:.3e}"
+
+
+def check_form(C, pb, C0, n, kind, what="", factor=4.0):
+    """C after n steps of form `kind` against the oracle, both bounds from the arithmetic."""
+    l2_tol, node_tol, ref = bounds(pb, C0, n, kind, factor)
+    assert_close(C, ref, l2_tol, node_tol, what)

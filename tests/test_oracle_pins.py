@@ -440,6 +440,21 @@ def test_discrete_adjoint_matches_central_differences():
         assert float(grad[k]) == pytest.approx(fd, rel=1e-5, abs=1e-9 * max(1.0, abs(loss)))
 
 
+def test_checkpointed_gradient_equals_plain_adjoint():
+    """The test harness's checkpointed recomputation (tests/oracle_ckpt.py) changes what
+    autograd stores, not the arithmetic: same loss and gradient as the plain oracle."""
+    import oracle_ckpt
+    rng = np.random.default_rng(17)
+    pb = W.random_problem(rng, 2, "mrt", (13, 11))
+    C0 = W.random_field(rng, pb.grid)
+    snaps = [5, 17, 23]
+    obs = torch.tensor(rng.normal(0.0, 1e-3, size=(3,) + pb.shape))
+    l0, g0 = O.loss_and_grad(pb, C0, snaps, obs)
+    l1, g1 = oracle_ckpt.loss_and_grad(pb, C0, snaps, obs, seg=4)
+    assert l1 == pytest.approx(l0, rel=1e-14)
+    assert torch.allclose(g1, g0, rtol=1e-12, atol=0.0)
+
+
 # --------------------------------------------------------------------------- planted mistakes
 
 def _pins_pass():

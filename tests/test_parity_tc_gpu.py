@@ -79,7 +79,8 @@ def test_tc_steps_match_oracle(L, kind, grid, collision):
     with L.Lattice(pb, C0, kind) as lat:
         lat.step(n)
         C = lat.C()
-    assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, n, kind)
+    l2_tol, node_tol, _ = arith_bounds.bounds(pb, C0, n, kind, C_ref=C_ref)
+    arith_bounds.assert_close(C, C_ref, l2_tol, node_tol, f"{grid} {collision} {kind}")
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -92,7 +93,8 @@ def test_tc_config_mrt_512_full_size(L, kind):
     with L.Lattice(pb, C0, kind) as lat:
         lat.step(n)
         C = lat.C()
-    assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, n, kind)
+    l2_tol, node_tol, _ = arith_bounds.bounds(pb, C0, n, kind, C_ref=C_ref)
+    arith_bounds.assert_close(C, C_ref, l2_tol, node_tol, f"mrt_aniso_512 {kind}")
 
 
 def test_tc_config_mrt3d_256_full_size(L):
@@ -179,7 +181,8 @@ def test_autotune_restores_state_and_keeps_parity(L, kind, grid):
         assert np.array_equal(lat.f(), f0)
         lat.step(n - 4)
         C = lat.C()
-    assert rel_l2(C, C_ref) < arith_bounds.bound(pb, C0, n, kind)
+    l2_tol, node_tol, _ = arith_bounds.bounds(pb, C0, n, kind, C_ref=C_ref)
+    arith_bounds.assert_close(C, C_ref, l2_tol, node_tol, f"autotuned {kind}")
 
 
 # ---------------------------------------------------------------- fused step (one cooperative launch)
@@ -218,7 +221,8 @@ def test_fused_step_matches_oracle_full_size(L):
         lat.configure(128, 4, 0, 0, 1)
         lat.step(n)
         C = lat.C()
-    assert rel_l2(C, C_ref) < 1e-5
+    l2_tol, node_tol, _ = arith_bounds.bounds(pb, C0, n, "bf16split", C_ref=C_ref)
+    arith_bounds.assert_close(C, C_ref, l2_tol, node_tol, "fused step")
 
 
 def test_configure_rejects_uncovered_plans(L):
@@ -298,17 +302,20 @@ def test_tf32_plan_switch_keeps_operands_current(L):
 
 # ---------------------------------------------------------------- five-product bf16 form
 
-def test_bf16x5_meets_1e5_over_the_bench_horizon(L):
-    """512x512 workload, 381 steps (the benchmark's accuracy horizon): the three-product
-    bf16 form drifts to ~2.3e-5 there through the rounding of the weights; with the
-    weights in three parts the concentration stays within 1e-5 of the FP64 oracle."""
+def test_bf16x5_meets_1e5_over_1000_steps(L):
+    """512x512 workload over its first 1000 steps (max |C| is still ~0.03 there; the FP64
+    scheme itself grows after ~1000 steps in lattice units): the three-product bf16 form
+    drifts past 1e-5 through the rounding of the weights; with the weights in three parts
+    the concentration stays within 1e-5 of the FP64 oracle, as a relative L2 and node by
+    node, in the launch configuration the benchmark picks."""
     pb, C0, _ = W.mrt_aniso_512()
-    n = 381
+    n = 1000
     C_ref = O.run_C(pb, C0, n).numpy()
     with L.Lattice(pb, C0, "bf16x5split") as lat:
+        lat.autotune(64)
         lat.step(n)
         C = lat.C()
-    assert rel_l2(C, C_ref) < 1e-5
+    arith_bounds.assert_close(C, C_ref, 1e-5, 1e-5, "bf16x5 1000 steps")
 
 
 def test_bf16x5_rejects_plans_it_does_not_cover(L):

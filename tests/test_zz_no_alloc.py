@@ -45,6 +45,24 @@ def test_static_scratch_sum_matches_lbm_mass_twice(L, precision, dtype):
             assert got == pytest.approx(want, rel=1e-13, abs=1e-300)
 
 
+def test_static_scratch_at_its_capacity(L):
+    """n = 67,108,864 FP32 values (256 MiB): every one of the 65,536 partials is used,
+    the last one included.  Values k/1024 (k = i mod 1024) and a marker in the last
+    element make every partial sum exact in FP64, so the result is compared exactly;
+    two calls in a row give the same value."""
+    n = 67_108_864
+    x = (torch.arange(n, device="cuda", dtype=torch.int64) % 1024).to(torch.float32) / 1024.0
+    x[-1] = 4096.0  # replaces 1023/1024 in the last partial
+    want = (n // 1024) * (1023 * 1024 / 2) / 1024.0 - 1023.0 / 1024.0 + 4096.0
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.cuda.synchronize()
+        assert L.lbm_mass_static(x.data_ptr(), 4, n, out.data_ptr(), None) == L.LBM_OK
+        torch.cuda.synchronize()
+        assert float(out.item()) == want
+    del x
+
+
 def test_static_scratch_rejects_oversize_and_bad_arguments(L):
     x = torch.zeros(16, dtype=torch.float32, device="cuda")
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
