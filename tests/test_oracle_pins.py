@@ -440,6 +440,82 @@ def test_discrete_adjoint_matches_central_differences():
         assert float(grad[k]) == pytest.approx(fd, rel=1e-5, abs=1e-9 * max(1.0, abs(loss)))
 
 
+# --------------------------------------------------------------------------- killed stable walk
+
+@pytest.mark.parametrize("alpha,beta", [(1.5, 0.0), (1.5, -0.4), (1.7, 0.6), (1.2, 1.0), (2.0, 0.3)])
+def test_stable_sampler_characteristic_function(alpha, beta):
+    """Appendix A, Eqs. (stb)-(stbb): E[exp(i k S)] = exp(-|k|^a) exp(i b sign(k) tan(pi a/2) |k|^a)
+    for the Chambers-Mallows-Stuck / Weron draws (empirical mean of 4e5 draws, 5 sigma)."""
+    from oracle import levy_walk as LW
+    rng = np.random.default_rng(int(alpha * 100) + int(beta * 10) + 50)
+    n = 400_000
+    S = LW.stable_from_uniforms(alpha, beta, rng.uniform(size=n), rng.uniform(size=n))
+    for k in (-1.3, -0.4, 0.3, 0.8, 1.6):
+        ka = abs(k) ** alpha
+        want = math.exp(-ka) * complex(math.cos(beta * math.tan(math.pi * alpha / 2) * ka * math.copysign(1, k)),
+                                       math.sin(beta * math.tan(math.pi * alpha / 2) * ka * math.copysign(1, k)))
+        if alpha == 2.0:  # Gaussian of variance 2, beta has no effect
+            want = complex(math.exp(-k * k), 0.0)
+        got = complex(np.mean(np.cos(k * S)), np.mean(np.sin(k * S)))
+        assert abs(got - want) < 5.0 / math.sqrt(n), (k, got, want)
+
+
+def _killed_walk_case(p):
+    """2-D FADE on [0,1]^2 with C = 0 on the walls (physical units: dx = 1/40, lambda = 1),
+    alpha = (1.5, 1.7), a Gaussian of unit mass (sigma 0.08) at the centre, t = 0.25."""
+    N = 40
+    dx = 1.0 / N
+    alpha, D = (1.5, 1.7), (0.1, 0.1)
+    dt = 0.5 * (1.0 / 3.0) * dx * dx / D[0]  # lambda = D dt / (e^2 dx^2) + 1/2 = 1
+    nsteps = 240
+    x = np.arange(N + 1) * dx
+    sig = 0.08
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    C0 = W.zero_walls(np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / (2 * sig * sig)) / (2 * math.pi * sig * sig))
+    pb = W.Problem(d=2, collision="mrt", grid=(N + 1, N + 1), alpha=alpha, p=p, g=(1.0, 1.0),
+                   D=((D[0], 0.0), (0.0, D[1])), u=(0.0, 0.0), s_free=(1.2, 1.2), dx=dx, dt=dt)
+    return pb, C0, nsteps, sig
+
+
+def test_killed_stable_walk_matches_the_oracle():
+    """Section 3.1 (Eqs. RW_STABLE, distri; the bounded-domain subsection): the density of
+    stable walks killed at their first exit solves the FADE with C = 0 on the walls.  The
+    oracle's x- and y-marginals agree with the walk's histograms (cells of width dx at the
+    interior nodes) within 4 standard errors plus 2% of the peak (the lattice's own
+    discretisation error), and its remaining mass with the surviving fraction.  With p and
+    1 - p exchanged (the skewness direction) the same comparison fails by > 10 sigma."""
+    from oracle import levy_walk as LW
+    p = (0.3, 0.8)
+    pb, C0, nsteps, sig = _killed_walk_case(p)
+    dx = pb.dx
+    C = O.run_C(pb, C0, nsteps).numpy()
+    mass = float(C.sum()) * dx * dx
+    rng = np.random.default_rng(2017)
+    n = 100_000
+    X0 = np.stack([rng.normal(0.5, sig, n), rng.normal(0.5, sig, n)], 1)
+    X, alive = LW.killed_walk(X0, pb.alpha, pb.p, [pb.D[0][0], pb.D[1][1]], pb.g, pb.u, (0.0, 0.0), (1.0, 1.0),
+                              pb.dt, nsteps, rng)
+    surv = float(alive.mean())
+    assert abs(surv - mass) < 4.0 * math.sqrt(surv * (1 - surv) / n) + 2e-3, (surv, mass)
+    assert mass < 0.97  # the walls remove a visible share of the mass
+    N = pb.grid[0] - 1
+    edges = (np.arange(N + 2) - 0.5) * dx
+
+    def zmax(Cfield):
+        worst = 0.0
+        for mu in range(2):
+            hist = np.histogram(X[alive][:, mu], bins=edges)[0][1:-1] / n / dx
+            marg = (Cfield.sum(axis=0) if mu == 0 else Cfield.sum(axis=1))[1:-1] * dx
+            se = np.sqrt(np.maximum(hist, 1e-3) * dx / n) / dx
+            worst = max(worst, float(np.max(np.abs(hist - marg) / (4.0 * se + 0.02 * marg.max()))))
+        return worst
+
+    assert zmax(C) < 1.0
+    import dataclasses
+    C_swapped = O.run_C(dataclasses.replace(pb, p=(1 - p[0], 1 - p[1])), C0, nsteps).numpy()
+    assert zmax(C_swapped) > 2.5
+
+
 def test_checkpointed_gradient_equals_plain_adjoint():
     """The test harness's checkpointed recomputation (tests/oracle_ckpt.py) changes what
     autograd stores, not the arithmetic: same loss and gradient as the plain oracle."""
