@@ -18,6 +18,9 @@ autograd.  Every function cites the section / equation it follows:
 * BGK relaxation time from D .................. Section 2.2, Eq. (Diffusion_Coefficient_3D)
 * diagonal D under BGK through h_mu ........... Section 2.2 (end)
 * MRT matrices M, Lambda^-1, D <-> lambda ...... Section 2.3, Eqs. (MRT-Coll), (MatrixD2), (MatrixS), (D_ab)
+* spatially varying D(x), g(x), u(x) .......... Section 1 (D and g may depend on x), Eq. (Fg) with
+                                                 g_mu(x) inside the integrals, Eqs. (MatrixS), (D_ab) with
+                                                 lambda_{mu nu}(x), Eq. (Feq) with u(x)
 * streaming (push) ............................ Section 2.2, Eqs. (LBE_Ket), (Def_Translation)
 * Dirichlet walls ............................. Section 2.5, Eq. (Dirichlet_BC)
 * time loop ................................... Section 2.5, Algorithm 1
@@ -177,7 +180,7 @@ class Operators:
     passed as tensors with requires_grad.
     """
 
-    def __init__(self, pb, alpha=None, p=None, D=None, u=None, g=None):
+    def __init__(self, pb, alpha=None, p=None, D=None, u=None, g=None, fields=None):
         self.d = d = pb.d
         self.grid = tuple(int(n) for n in pb.grid)
         self.collision = pb.collision
@@ -197,9 +200,59 @@ class Operators:
                 Dm = torch.diag(Dm)
         self.D = Dm
         self.h = torch.ones(d, dtype=DT)
+        self.fields = None
+        if fields:
+            self._set_fields(pb, fields)
+            return
         self.Omega = self._collision_matrix(pb)
         self.K = [frac_matrix(self.alpha[mu], self.p[mu], self.g[mu] * self.h[mu], self.grid[mu] - 1, self.dx)
                   for mu in range(d)]
+
+    def _set_fields(self, pb, fields):
+        """Coefficients that depend on the node (Section 1: D and g may depend on x).
+
+        fields: dict with optional entries (numpy or torch, array order = reversed grid)
+          "D": (d, d, *shape) diffusion tensor per node, "g": (d, *shape), "u": (d, *shape);
+        an absent entry takes the problem's constant value at every node.
+        * Eq. (Fg): F_mu = p I+^gamma(g_mu C) + (1-p) I-^gamma(g_mu C): g_mu(x) multiplies C
+          inside the integrals, so K_mu is built with g = 1.
+        * Eqs. (MatrixS), (D_ab): Lambda^-1(x) has the flux block D(x) dt/(e^2 dx^2) + Id/2;
+          Omega(x) = M^-1 Lambda(x) M with Lambda(x) the inverse of Lambda^-1(x), node by node.
+          BGK (Eq. Diffusion_Coefficient_3D with lambda(x)) needs D(x) spherical at every node.
+        * Eq. (Feq): the advective part uses u(x).
+        """
+        d, Q, e2 = self.d, self.Q, self.e2
+        shape = tuple(reversed(self.grid))
+        ones = torch.ones(shape, dtype=DT)
+
+        def get(name, const):
+            v = fields.get(name)
+            return torch.as_tensor(v, dtype=DT).clone() if v is not None else const
+        self.Dfield = get("D", self.D.reshape(d, d, *([1] * len(shape))) * ones)
+        self.gfield = get("g", self.g.reshape(d, *([1] * len(shape))) * ones)
+        self.ufield = get("u", self.u.reshape(d, *([1] * len(shape))) * ones)
+        ratio = self.dt / (self.dx * self.dx)
+        if self.collision == "bgk":
+            Dd = torch.stack([self.Dfield[i, i] for i in range(d)])
+            off = self.Dfield - torch.diag_embed(Dd.movedim(0, -1)).movedim(-1, 0).movedim(-1, 0)
+            if not (bool(torch.all(Dd == Dd[0])) and bool(torch.all(off == 0))):
+                raise ValueError("BGK with a D field needs D(x) spherical at every node")
+            lam = Dd[0] * ratio / e2 + 0.5
+            self.Omega = torch.eye(Q, dtype=DT).reshape(Q, Q, *([1] * len(shape))) / lam
+        else:
+            s_free = list(pb.s_free)
+            lam_inv = torch.zeros(shape + (Q, Q), dtype=DT)
+            lam_inv[..., 0, 0] = 1.0
+            lam_inv[..., 1:d + 1, 1:d + 1] = self.Dfield.movedim(0, -1).movedim(0, -1) * ratio / e2 \
+                + 0.5 * torch.eye(d, dtype=DT)
+            for k, sf in enumerate(s_free):
+                lam_inv[..., d + 1 + k, d + 1 + k] = 1.0 / float(sf)
+            Lam = torch.linalg.inv(lam_inv)
+            M = moment_matrix(d)
+            Om = torch.linalg.inv(M) @ Lam @ M                     # (*shape, Q, Q)
+            self.Omega = Om.movedim(-1, 0).movedim(-1, 0)           # (Q, Q, *shape)
+        self.K = [frac_matrix(self.alpha[mu], self.p[mu], 1.0, self.grid[mu] - 1, self.dx) for mu in range(d)]
+        self.fields = True
 
     def _collision_matrix(self, pb) -> torch.Tensor:
         """Omega such that the collision is f - Omega (f - feq).
@@ -244,6 +297,8 @@ def _vec(x, d) -> torch.Tensor:
 
 def fractional_terms(ops: Operators, C: torch.Tensor) -> List[torch.Tensor]:
     """F_mu = p_mu I+^{2-alpha_mu}(g_mu C) + (1-p_mu) I-^{2-alpha_mu}(g_mu C), Algorithm 1 loop item 1."""
+    if ops.fields:
+        return [apply_along_axis(ops.K[mu], ops.gfield[mu] * C, mu) for mu in range(ops.d)]
     return [apply_along_axis(ops.K[mu], C, mu) for mu in range(ops.d)]
 
 
@@ -260,14 +315,18 @@ def equilibrium(ops: Operators, C: torch.Tensor, F: Sequence[torch.Tensor]) -> t
         A.append(ops.w[2 * mu + 2] * F[mu])
     adv_scale = (ops.dt / ops.dx) / ops.e2
     feq = []
+    u = ops.ufield if ops.fields else ops.u
     for i in range(Q):
-        ue = sum(ops.u[mu] * ops.e[mu, i] for mu in range(d))
+        ue = sum(u[mu] * ops.e[mu, i] for mu in range(d))
         feq.append(A[i] + adv_scale * C * ue * ops.w[i])
     return torch.stack(feq)
 
 
 def collide(ops: Operators, f: torch.Tensor, feq: torch.Tensor) -> torch.Tensor:
-    """Right-hand side of Eq. (LBE_Ket) / (MRT-Coll) without source: f - Omega (f - feq)."""
+    """Right-hand side of Eq. (LBE_Ket) / (MRT-Coll) without source: f - Omega (f - feq),
+    with Omega(x) node by node when the coefficients vary in space."""
+    if ops.Omega.dim() > 2:
+        return f - torch.einsum("ij...,j...->i...", ops.Omega, f - feq)
     return f - torch.einsum("ij,j...->i...", ops.Omega, f - feq)
 
 
@@ -351,6 +410,11 @@ def step(ops: Operators, f: torch.Tensor) -> torch.Tensor:
     fnew = stream(ops, fstar)                    # item 3
     fnew = dirichlet(ops, fnew)                  # item 4
     return fnew                                  # item 5: C = concentration(fnew)
+
+
+def run_fields_C(pb, C0, nsteps: int, fields) -> torch.Tensor:
+    """C after nsteps with spatially varying coefficients (see Operators._set_fields)."""
+    return concentration(run(pb, C0, nsteps, Operators(pb, fields=fields)))
 
 
 def run(pb, C0, nsteps: int, ops: Operators = None) -> torch.Tensor:
