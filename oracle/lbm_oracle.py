@@ -21,6 +21,9 @@ autograd.  Every function cites the section / equation it follows:
 * spatially varying D(x), g(x), u(x) .......... Section 1 (D and g may depend on x), Eq. (Fg) with
                                                  g_mu(x) inside the integrals, Eqs. (MatrixS), (D_ab) with
                                                  lambda_{mu nu}(x), Eq. (Feq) with u(x)
+* source term w_i S_c(x, t) dt ................ Section 2.2, Eqs. (LBE_FADE), (LBE_Ket), (MRT-Coll)
+* time-dependent, non-homogeneous walls ........ Section 2.5 (C_0 varies with position and time),
+                                                 Section 3.4 (Eqs. Def_D_AS, exsolFADE_3D)
 * streaming (push) ............................ Section 2.2, Eqs. (LBE_Ket), (Def_Translation)
 * Dirichlet walls ............................. Section 2.5, Eq. (Dirichlet_BC)
 * time loop ................................... Section 2.5, Algorithm 1
@@ -37,7 +40,11 @@ implements, each written out independently):
 * BGK with a diagonal, non-spherical D: lambda is set by the largest D_mumu
   and h_mu = D_mumu / max(D) multiplies g_mu;
 * MRT: ``s_free`` are relaxation *rates* 1/lambda_k of the free moments;
-  lambda_0 (conserved moment) is set to 1, it has no effect.
+  lambda_0 (conserved moment) is set to 1, it has no effect;
+* a source S_c(x, t) enters the step from t to t + dt at time t, added after the
+  collision as w_i S_c dt; the wall values of that step are those of time t + dt
+  (the populations being assigned are those of t + dt).  Both are taken in the
+  separable form profile(x) exp(rate t), which covers Section 3.4's solution.
 
 Parity of every function here is pinned by the tests in
 ``tests/test_oracle_pins.py`` (closed forms, invariants, special cases).
@@ -201,6 +208,8 @@ class Operators:
         self.D = Dm
         self.h = torch.ones(d, dtype=DT)
         self.fields = None
+        self.source = None   # (S(x) tensor of the field's shape, rate): S_c(x, t) = S(x) exp(rate t)
+        self.walls = None    # (C_w(x) tensor, rate): C_0(x, t) = C_w(x) exp(rate t) on the wall nodes
         if fields:
             self._set_fields(pb, fields)
             return
@@ -379,16 +388,29 @@ def stream(ops: Operators, fstar: torch.Tensor) -> torch.Tensor:
     return torch.stack(out)
 
 
-def dirichlet(ops: Operators, f: torch.Tensor) -> torch.Tensor:
+def dirichlet(ops: Operators, f: torch.Tensor, t: float = 0.0) -> torch.Tensor:
     """Eq. (Dirichlet_BC): unknown inward populations f_b = C0 - sum_{i != b} f_i.
 
     With k > 1 unknowns at a node (edges, corners) each gets (C0 - sum of known)/k.
+    C0 is the constant C_wall, or C_w(x) exp(rate t) at time t when the wall values vary
+    with position and time (Section 2.5).
     """
     unknown = unknown_mask(ops)
     known_sum = torch.where(unknown, torch.zeros((), dtype=DT), f).sum(0)
     k = unknown.sum(0).to(DT)
-    fill = (ops.C_wall - known_sum) / torch.clamp(k, min=1.0)
+    C0 = ops.C_wall
+    if ops.walls is not None:
+        Cw, rate = ops.walls
+        C0 = Cw * math.exp(rate * t)
+    fill = (C0 - known_sum) / torch.clamp(k, min=1.0)
     return torch.where(unknown, fill.unsqueeze(0).expand_as(f), f)
+
+
+def source_term(ops: Operators, t: float) -> torch.Tensor:
+    """|w> S_c(x, t) dt of Eqs. (LBE_Ket) / (MRT-Coll), S_c(x, t) = S(x) exp(rate t)."""
+    S, rate = ops.source
+    St = S * math.exp(rate * t) * ops.dt
+    return torch.stack([ops.w[i] * St for i in range(ops.Q)])
 
 
 def concentration(f: torch.Tensor) -> torch.Tensor:
@@ -401,14 +423,17 @@ def init_populations(ops: Operators, C0: torch.Tensor) -> torch.Tensor:
     return equilibrium(ops, C0, fractional_terms(ops, C0))
 
 
-def step(ops: Operators, f: torch.Tensor) -> torch.Tensor:
-    """One pass of Algorithm 1's time loop (items 1-5) from populations f(t) to f(t+dt)."""
+def step(ops: Operators, f: torch.Tensor, n: int = 0) -> torch.Tensor:
+    """One pass of Algorithm 1's time loop (items 1-5) from populations f(t) to f(t+dt),
+    t = n dt (the time matters only for a source or wall values that depend on it)."""
     C = concentration(f)
     F = fractional_terms(ops, C)                 # item 1
     feq = equilibrium(ops, C, F)                 # item 2
     fstar = collide(ops, f, feq)                 # item 2 (right-hand side)
+    if ops.source is not None:
+        fstar = fstar + source_term(ops, n * ops.dt)
     fnew = stream(ops, fstar)                    # item 3
-    fnew = dirichlet(ops, fnew)                  # item 4
+    fnew = dirichlet(ops, fnew, (n + 1) * ops.dt)  # item 4
     return fnew                                  # item 5: C = concentration(fnew)
 
 
@@ -421,9 +446,19 @@ def run(pb, C0, nsteps: int, ops: Operators = None) -> torch.Tensor:
     """Populations after ``nsteps`` steps from f(0) = feq(C0)."""
     ops = ops or Operators(pb)
     f = init_populations(ops, _field(C0))
-    for _ in range(nsteps):
-        f = step(ops, f)
+    for n in range(nsteps):
+        f = step(ops, f, n)
     return f
+
+
+def with_source_and_walls(ops: Operators, source=None, walls=None) -> Operators:
+    """Attach S_c(x, t) = S(x) exp(rate t) (source = (S, rate)) and wall values
+    C_w(x) exp(rate t) (walls = (C_w, rate)); arrays in the field's shape."""
+    if source is not None:
+        ops.source = (torch.as_tensor(source[0], dtype=DT), float(source[1]))
+    if walls is not None:
+        ops.walls = (torch.as_tensor(walls[0], dtype=DT), float(walls[1]))
+    return ops
 
 
 def run_C(pb, C0, nsteps: int) -> torch.Tensor:

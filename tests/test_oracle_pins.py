@@ -634,6 +634,85 @@ def test_fields_step_equals_brute_force_loops(coll, grid):
     assert np.max(np.abs(f1 - ref)) < 1e-13 * np.max(np.abs(ref))
 
 
+# --------------------------------------------------------------------------- source term, time-dependent walls
+
+def _e5(N, alpha=(1.5, 1.7), a=(0.4, 0.7), T=0.5, source_sign=1.0):
+    """Section 3.4: on ]0,1[^2 with p = 1, g = 1, u = 0, D_mumu(x) = x_mu^alpha_mu
+    Gamma(a_mu + 2 - alpha_mu) / Gamma(a_mu + 2) (Eq. Def_D_AS) and the source
+    S_c = -(d+1) exp(-t) x^a1 y^a2, C = exp(-t) x^a1 y^a2 (Eq. exsolFADE_3D) solves the FADE;
+    initial and wall values from it.  MRT, dt such that lambda <= 1.  Returns the relative
+    L2 error of C at t = T against the exact solution."""
+    dx = 1.0 / N
+    x = np.arange(N + 1) * dx
+    X = np.broadcast_to(x[None, :], (N + 1, N + 1))
+    Y = np.broadcast_to(x[:, None], (N + 1, N + 1))
+    D = np.zeros((2, 2, N + 1, N + 1))
+    D[0, 0] = X ** alpha[0] * math.gamma(a[0] + 2 - alpha[0]) / math.gamma(a[0] + 2)
+    D[1, 1] = Y ** alpha[1] * math.gamma(a[1] + 2 - alpha[1]) / math.gamma(a[1] + 2)
+    dt = 0.5 * (1.0 / 3.0) * dx * dx / float(D.max())
+    n = int(round(T / dt))
+    dt = T / n
+    pb = W.Problem(d=2, collision="mrt", grid=(N + 1, N + 1), alpha=alpha, p=(1.0, 1.0), g=(1.0, 1.0),
+                   D=((0.1, 0.0), (0.0, 0.1)), u=(0.0, 0.0), s_free=(1.2, 1.2), dx=dx, dt=dt)
+    prof = X ** a[0] * Y ** a[1]
+    ops = O.with_source_and_walls(O.Operators(pb, fields={"D": D}), source=(-3.0 * source_sign * prof, -1.0),
+                                  walls=(prof, -1.0))
+    f = O.init_populations(ops, torch.tensor(prof))
+    for k in range(n):
+        f = O.step(ops, f, k)
+    exact = math.exp(-T) * prof
+    return float(np.linalg.norm(O.concentration(f).numpy() - exact) / np.linalg.norm(exact))
+
+
+def test_exact_solution_with_source_varying_D_and_time_dependent_walls():
+    """The closed-form end-to-end pin of Section 3.4 (Fig. Bench_MRT-AnalySol's case:
+    alpha = (1.5, 1.7), a = (0.4, 0.7)): within 1% at dx = 1/40, converging with dx;
+    with the source's sign flipped the error exceeds 30%."""
+    e20, e40 = _e5(20), _e5(40)
+    assert e40 < 1e-2
+    assert e40 < 0.7 * e20
+    assert _e5(20, source_sign=-1.0) > 0.3
+
+
+def test_source_adds_its_mass_every_step():
+    """Eq. (LBE_Ket): the source adds sum_i w_i S dt = S dt per node and step (sum_i w_i = 1);
+    away from the walls the mass grows by sum_x S(x, t) dt, t the start of the step."""
+    pb = W.Problem(d=2, collision="mrt", grid=(64, 60), alpha=(1.8, 1.6), p=(0.4, 0.7), g=(1, 1),
+                   D=((0.03, 0), (0, 0.02)), u=(0.02, -0.01), s_free=(1.2, 1.4), dt=0.5)
+    pb = dataclasses.replace(pb, alpha=(2.0, 2.0))
+    S = np.zeros(pb.shape)
+    S[27:33, 29:35] = 0.01
+    rate = -0.3
+    ops = O.with_source_and_walls(O.Operators(pb), source=(S, rate))
+    # all mass comes from the source patch, 27+ cells from the walls (15 steps move it < 16)
+    f = O.init_populations(ops, torch.zeros(pb.shape, dtype=torch.float64))
+    m = float(O.concentration(f).sum())
+    for k in range(15):
+        f = O.step(ops, f, k)
+        m_new = float(O.concentration(f).sum())
+        assert m_new - m == pytest.approx(S.sum() * math.exp(rate * k * pb.dt) * pb.dt, rel=1e-10)
+        m = m_new
+
+
+@pytest.mark.parametrize("grid", [(17, 13), (9, 8, 7)])
+def test_time_dependent_wall_values_imposed(grid):
+    """Eq. (Dirichlet_BC) with C_0(x, t) = C_w(x) exp(rate t): after the step ending at
+    t = (n+1) dt every wall node holds C_w(x) exp(rate t), corners and edges included."""
+    rng = np.random.default_rng(77 + len(grid))
+    pb = dataclasses.replace(W.random_problem(rng, len(grid), "mrt", grid), dt=0.7)
+    Cw = rng.uniform(0.01, 0.05, size=pb.shape)
+    rate = -0.2
+    ops = O.with_source_and_walls(O.Operators(pb), walls=(Cw, rate))
+    f = O.init_populations(ops, torch.tensor(W.random_field(rng, grid)))
+    wall = np.ones(pb.shape, dtype=bool)
+    wall[tuple(slice(1, -1) for _ in grid)] = False
+    for k in range(6):
+        f = O.step(ops, f, k)
+        C = O.concentration(f).numpy()
+        want = Cw * math.exp(rate * (k + 1) * pb.dt)
+        assert np.max(np.abs(C[wall] - want[wall])) < 1e-15
+
+
 # --------------------------------------------------------------------------- killed stable walk
 
 @pytest.mark.parametrize("alpha,beta", [(1.5, 0.0), (1.5, -0.4), (1.7, 0.6), (1.2, 1.0), (2.0, 0.3)])
@@ -782,7 +861,7 @@ def test_planted_mistakes_are_caught(monkeypatch):
         feq[0] = feq[0] + ops.w[0] * sum(F) * 0.5
         return feq
 
-    def bc_ignores_corners(ops, f):
+    def bc_ignores_corners(ops, f, t=0.0):
         unknown = O.unknown_mask(ops)
         known_sum = torch.where(unknown, torch.zeros((), dtype=torch.float64), f).sum(0)
         return torch.where(unknown, (ops.C_wall - known_sum).unsqueeze(0).expand_as(f), f)
