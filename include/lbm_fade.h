@@ -66,19 +66,24 @@ enum {
                               bf16 hi+lo operands (3 products), FP32 accumulation */
   LBM_FP32_TF32SPLIT = 3,  /* FP32 collision, fractional operator on tensor cores with
                               tf32 hi+lo operands (3 products), FP32 accumulation */
-  LBM_FP32_BF16SPLIT5 = 4  /* as LBM_FP32_BF16SPLIT with K_mu in three bf16 parts
+  LBM_FP32_BF16SPLIT5 = 4, /* as LBM_FP32_BF16SPLIT with K_mu in three bf16 parts
                               k1+k2+k3 and C in two, five products (k1c1, k1c2, k2c1,
                               k2c2, k3c1): the weights' rounding, which the three-product
                               form carries into every step, drops to the FP32 level.
-                              Per-tile operator plans only (64 or 128 columns); single
-                              problems only (not lbm_create_batch). */
+                              Operator plans with 64- or 128-column tiles (per tile, or
+                              persistent with 128); single problems and batches. */
+  LBM_FP32_BF16SPLIT6 = 5  /* as LBM_FP32_BF16SPLIT5 with C in three bf16 parts as well
+                              (c1+c2+c3 = C exactly in FP32), six products (adds k1c3):
+                              the operator's operands carry FP32's precision, so the form
+                              matches the plain FP32 form's accuracy.  Same plans as
+                              LBM_FP32_BF16SPLIT5. */
 };
 
 typedef struct {
   int lattice;        /* LBM_D2Q5 or LBM_D3Q7 */
   int collision;      /* LBM_BGK or LBM_MRT */
   int precision;      /* LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT,
-                         LBM_FP32_BF16SPLIT5 */
+                         LBM_FP32_BF16SPLIT5, LBM_FP32_BF16SPLIT6 */
   int grid[3];        /* nodes per axis incl. walls, >= 3 on used axes, 1 on unused axes */
   double alpha[3];    /* fractional order per axis, in ]1,2] (Eq. FADE_moreGeneral) */
   double p[3];        /* weight of the left integral I+, in [0,1] (Eq. Fg) */
@@ -123,7 +128,8 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* ctx);
 
 /* A batch of nprob independent problems advanced together (each one is the scheme of
  * Algorithm 1, exactly as lbm_create would run it).  All problems share lattice,
- * collision and precision (LBM_FP32 or LBM_FP32_BF16SPLIT); grids and every other
+ * collision and precision (LBM_FP32 or a bf16 split form: LBM_FP32_BF16SPLIT, _BF16SPLIT5,
+ * _BF16SPLIT6); grids and every other
  * parameter may differ.  prms[i] and C0_host[i] (host array of the problem's nodes)
  * describe problem i.  One time step is one grouped tensor-core launch covering every
  * problem's tiles (FP32: one SIMT launch per problem and axis) and one grouped
@@ -228,10 +234,64 @@ int lbm_save(lbm_t h, void* dst_host, long long bytes);
 int lbm_load(lbm_t h, const void* src_host, long long bytes);
 
 /* Total mass sum_x C(x) of problem `prob`'s current concentration (Algorithm 1, loop
- * item 5), reduced on the device in FP64 (block partials, then one final pass), into
- * the host double *mass.  Synchronises; returns the problem's latched error as
+ * item 5), in FP64, into the host double *mass.  After a step the mass is a by-product
+ * of the collide-stream kernel: each of its blocks adds the concentrations it wrote in
+ * FP64 and stores one partial; this call adds the partials of the latest step in one
+ * small pass (a fixed order: the same result every time).  Right after lbm_create,
+ * lbm_set_C, lbm_reset, lbm_write_f or lbm_load it reduces C itself (block partials,
+ * then one final pass).  Synchronises; returns the problem's latched error as
  * lbm_read_C does. */
 int lbm_mass(lbm_t h, int prob, double* mass);
+
+/* Mass check for instability detection (the paper has no counterpart; Section 3.3
+ * reports the scheme's instability at high Peclet number).  With limit > 0, every
+ * synchronising call (lbm_sync, lbm_read_*, lbm_mass) first adds the latest step's mass
+ * partials and latches LBM_ERR_UNSTABLE when that mass is not finite or its magnitude
+ * exceeds `limit` (a run whose mass explodes, positive or negative); the check costs one
+ * small launch per synchronising call and nothing per step.  limit = 0 (the default)
+ * turns the check off; a non-finite concentration is latched in any case.  Applies to
+ * every problem of the handle.  LBM_EINVAL for a negative or non-finite limit. */
+int lbm_set_mass_limit(lbm_t h, double limit);
+
+/* Coefficients that vary in space (Section 1: the scheme is meant for a diffusion tensor D
+ * and factors g that depend on x; Eq. (Fg) with g_mu(x) multiplying C inside the integrals,
+ * Eqs. (MatrixS), (D_ab) with lambda_{mu nu}(x), Eq. (Feq) with u(x)).  Each argument is a
+ * host array of the handle's nodes (field layout above), or NULL for the constant value of
+ * lbm_params at every node:
+ *   D_field: d*d*nodes doubles, entry (a, b) of node i at D_field[(a*d + b)*nodes + i];
+ *            symmetric, lambdabar(x) = D(x) dt/(e^2 dx^2) + Id/2 SPD at every node (MRT);
+ *            BGK needs D(x) spherical at every node (one relaxation time lambda(x), Eq.
+ *            Diffusion_Coefficient_3D; the constant-D h_mu trick does not apply);
+ *   g_field: d*nodes doubles (g_mu(x) > 0 at g_field[mu*nodes + i]);
+ *   u_field: d*nodes doubles (u_mu(x), physical units).
+ * All three NULL returns to the constant coefficients.  The step then collides in moment
+ * space with the rates of each node and the operator contracts g_mu(x) C along each axis;
+ * the handle re-initialises from its initial concentration (as lbm_reset).  The arrays are
+ * copied.  Single-problem handles in the LBM_FP64 or LBM_FP32 form (LBM_ENOTSUP for the
+ * tensor-core forms, LBM_EINVAL for batches); LBM_EINVAL for a non-finite entry, g <= 0 or a
+ * D that breaks the conditions above (the handle is unchanged then).  lbm_grad returns
+ * LBM_ENOTSUP on a handle with varying coefficients.  Synchronises. */
+int lbm_set_fields(lbm_t h, const double* D_field, const double* g_field, const double* u_field);
+
+/* Source term S_c(x, t) = S(x) exp(rate t) of Eq. (FADE_moreGeneral), added after the collision
+ * as w_i S_c(x, t) dt (Eqs. LBE_FADE, LBE_Ket, MRT-Coll) with t the time at the start of the
+ * step (t = n dt after n steps since the last re-initialisation; the exponential form covers
+ * Section 3.4's exact solution, S_c = -(d+1) exp(-t) prod x_mu^a_mu).  S_field: host array of
+ * the handle's nodes (copied), or NULL to remove the source.  rate finite.  Runs the step on
+ * the per-node path (as lbm_set_fields, constant coefficients unless set), re-initialises from
+ * the initial concentration (as lbm_reset, time 0).  The time is carried by the step counter
+ * (lbm_save / lbm_load keep it).  Single FP64 / FP32 problems (LBM_ENOTSUP for the tensor-core
+ * forms, LBM_EINVAL for batches); LBM_EINVAL for a non-finite value.  Synchronises; every
+ * lbm_step call of a handle with a time-dependent source or wall values waits for the
+ * handle's earlier work once per 128 steps (it copies that range's time factors). */
+int lbm_set_source(lbm_t h, const double* S_field, double rate);
+
+/* Dirichlet values that vary with position and time, C_0(x, t) = C_w(x) exp(rate t) on every
+ * wall node (Eq. Dirichlet_BC, Section 2.5: the same update with C_0 depending on x and t;
+ * Section 3.4 takes them from the exact solution), imposed after the step that ends at time t.
+ * Cw_field: host array of the handle's nodes (only the wall nodes are read), or NULL for the
+ * constant C_wall of lbm_params.  Otherwise as lbm_set_source. */
+int lbm_set_wall_values(lbm_t h, const double* Cw_field, double rate);
 
 /* Wait for all work of the handle; return a latched device error if any. */
 int lbm_sync(lbm_t h);

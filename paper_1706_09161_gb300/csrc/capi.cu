@@ -125,7 +125,7 @@ int derive(const lbm_params* p, Derived* out) {
   if (!p) return LBM_EINVAL;
   if (p->lattice != LBM_D2Q5 && p->lattice != LBM_D3Q7) return LBM_EINVAL;
   if (p->collision != LBM_BGK && p->collision != LBM_MRT) return LBM_EINVAL;
-  if (p->precision < LBM_FP64 || p->precision > LBM_FP32_BF16SPLIT5) return LBM_EINVAL;
+  if (p->precision < LBM_FP64 || p->precision > LBM_FP32_BF16SPLIT6) return LBM_EINVAL;
   const int d = (p->lattice == LBM_D2Q5) ? 2 : 3;
   const int Q = 2 * d + 1;
   if (!(p->dx > 0.0) || !(p->dt > 0.0) || !std::isfinite(p->dx) || !std::isfinite(p->dt)) return LBM_EINVAL;
@@ -183,6 +183,7 @@ int derive(const lbm_params* p, Derived* out) {
     if (!is_spd(d, lambar)) return LBM_EINVAL;
     for (int k = 0; k < Q - d - 1; ++k)
       if (!(p->s_free[k] > 0.0 && p->s_free[k] < 2.0)) return LBM_EINVAL;
+    for (int k = 0; k < Q - d - 1; ++k) sp.sfree[k] = p->s_free[k];
     double laminv[49] = {0}, lam[49], M[49], Minv[49], tmp[49];
     laminv[0] = 1.0;  // conserved moment: no effect
     for (int i = 0; i < d; ++i)
@@ -274,8 +275,15 @@ void free_all(lbm_s* h) {
   lbm::cs_release(h);
   lbm::dev_free(h, h->fused_bar);
   h->fused_bar = nullptr;
-  void* ptrs[] = {h->dev.f[0], h->dev.f[1], h->dev.C, h->dev.C0, h->dev.F, h->dev.K, h->dev.KT, h->dev.stage,
-                  h->dev.partials, h->dev.scalar, h->dev.flag, h->dev.Khi, h->dev.Klo, h->dev.Kl2, h->dev.Chi, h->dev.Clo};
+  lbm::dev_free(h, h->cs_part);
+  h->cs_part = nullptr;
+  h->cs_part_cap = 0;
+  for (void* p : {h->fld.coll, h->fld.advw, h->fld.g, h->fld.G, h->fld.src, h->fld.cw, (void*)h->fld.tf})
+    lbm::dev_free(h, p);
+  h->fld = lbm::FieldState{};
+  void* ptrs[] = {h->dev.f[0], h->dev.f[1], h->dev.C,   h->dev.C0,  h->dev.F,   h->dev.K,   h->dev.KT,
+                  h->dev.stage, h->dev.partials, h->dev.scalar, h->dev.flag, h->dev.Khi, h->dev.Klo, h->dev.Kl2,
+                  h->dev.Chi,  h->dev.Clo, h->dev.Cl2};
   for (void* p : ptrs) lbm::dev_free(h, p);
   h->dev = lbm::DeviceState{};
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -315,6 +323,7 @@ bool uses_tc(const lbm_s* h) { return h->tc != nullptr; }
 // collide-stream kernel writes it, so one_step skips this).
 int run_frac(lbm_s* h, cudaStream_t s) {
   if (!uses_tc(h)) {
+    if (h->fld.on) LBM_CUDA(lbm::launch_scale_fields(h, s));  // G_mu = g_mu(x) C
     LBM_CUDA(lbm::launch_frac_simt(h, h->dev.C, h->dev.F, s));
   } else {
     LBM_CUDA(lbm::launch_split_C(h, s));
@@ -323,7 +332,7 @@ int run_frac(lbm_s* h, cudaStream_t s) {
   return LBM_OK;
 }
 
-int one_step(lbm_s* h, int& cur, cudaStream_t s) {
+int one_step(lbm_s* h, int& cur, cudaStream_t s, int tk = 0) {
   if (h->is_batch()) {
     // grouped operator (or one SIMT operator per problem), then one grouped collide-stream
     if (h->batch_tc_blocks > 0) {
@@ -338,26 +347,51 @@ int one_step(lbm_s* h, int& cur, cudaStream_t s) {
   if (uses_tc(h)) {
     LBM_CUDA(lbm::launch_split_T_step(h, s));  // tf32: regrouped y/z operands of the current C
     LBM_CUDA(lbm::launch_frac_tc(h, s));
+  } else if (h->fld.on) {
+    // G_mu = g_mu(x) C of the current C: written by the previous collide-stream launch (or
+    // by the re-initialisation)
+    LBM_CUDA(lbm::launch_frac_simt(h, h->dev.C, h->dev.F, s));
   } else {
     int rc = run_frac(h, s);
     if (rc) return rc;
   }
-  LBM_CUDA(lbm::launch_collide_stream(h, h->dev.f[cur], h->dev.f[cur ^ 1], h->dev.C, s));
+  LBM_CUDA(lbm::launch_collide_stream(h, h->dev.f[cur], h->dev.f[cur ^ 1], h->dev.C, s, tk));
   cur ^= 1;
+  return LBM_OK;
+}
+
+// time factors of the next n steps (from step t_steps) into the slots 0..n-1 read by the
+// collide-stream launches of a source or of wall values that vary in time: exp(rate_S t) dt
+// at each step's start and exp(rate_w (t + dt)) at its end.  A pageable copy: the host
+// waits for the stream's earlier work (once per graph replay of 128 steps).
+int upload_time(lbm_s* h, int n) {
+  if (!h->fld.tf) return LBM_OK;
+  std::vector<double> v(2 * (size_t)n);
+  const double dt = h->prm.dt;
+  for (int j = 0; j < n; ++j) {
+    const double t = (double)(h->t_steps + j) * dt;
+    v[2 * j] = std::exp(h->fld.src_rate * t) * dt;
+    v[2 * j + 1] = std::exp(h->fld.cw_rate * (t + dt));
+  }
+  LBM_CUDA(cudaMemcpyAsync(h->fld.tf, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, h->stream));
   return LBM_OK;
 }
 
 // f = feq(C, F(C)), then C = <1|f> so that the first step sees the same C the populations carry.
 int init_from_C(lbm_s* h) {
+  h->mass_valid = false;  // C now comes from the re-initialisation, not from a step
+  h->t_steps = 0;
   int rc = run_frac(h, h->stream);
   if (rc) return rc;
   LBM_CUDA(lbm::launch_init_equilibrium(h, h->dev.f[h->cur], h->stream));
   LBM_CUDA(lbm::launch_moment(h, h->dev.f[h->cur], h->dev.C, h->stream));
   if (uses_tc(h)) LBM_CUDA(lbm::launch_split_C(h, h->stream));
+  if (h->fld.on) LBM_CUDA(lbm::launch_scale_fields(h, h->stream));
   return LBM_OK;
 }
 
 int latched(lbm_s* h) {
+  if (h->mass_limit > 0.0 && h->mass_valid) LBM_CUDA(lbm::launch_step_mass(h, h->mass_limit, h->stream));
   int flag = 0;
   LBM_CUDA(cudaMemcpyAsync(&flag, h->dev.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
@@ -370,7 +404,7 @@ int capture_graph(lbm_s* h, int parity) {
   LBM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int cur = parity;
   int rc = LBM_OK;
-  for (int k = 0; k < h->graph_steps && rc == LBM_OK; ++k) rc = one_step(h, cur, s);
+  for (int k = 0; k < h->graph_steps && rc == LBM_OK; ++k) rc = one_step(h, cur, s, k);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (rc) {
@@ -384,6 +418,36 @@ int capture_graph(lbm_s* h, int parity) {
 }
 
 }  // namespace
+
+// K_mu and K_mu^T (Section 2.4, Eqs. 1Dminus_discret, c+, c-) built in FP64 on the host and
+// stored in the working precision; the scale carries g_mu h_mu, or 1 when g varies in space
+// (then g_mu(x) multiplies C inside the integrals, Eq. Fg).  Kall receives the FP64 matrices.
+static int upload_weights(lbm_s* h, const double* hfac, std::vector<std::vector<double>>* Kall) {
+  const lbm_params* prm = &h->prm;
+  const size_t E = h->elem;
+  std::vector<double> K, KT;
+  long long off = 0;
+  for (int mu = 0; mu < h->d; ++mu) {
+    const int side = prm->grid[mu];
+    K.assign((size_t)side * side, 0.0);
+    KT.assign((size_t)side * side, 0.0);
+    const double scale = h->fld.on ? 1.0 : prm->g[mu] * hfac[mu];
+    lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], scale, side, prm->dx, K.data());
+    for (int n = 0; n < side; ++n)
+      for (int l = 0; l < side; ++l) KT[(size_t)l * side + n] = K[(size_t)n * side + l];
+    const size_t cnt = (size_t)side * side;
+    cudaError_t e = cudaMemcpyAsync(h->dev.stage, K.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = lbm::launch_convert_in(h->dev.stage, (char*)h->dev.K + off * E, h->elem, cnt, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dev.stage, KT.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = lbm::launch_convert_in(h->dev.stage, (char*)h->dev.KT + off * E, h->elem, cnt, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return record_cuda(e, "weight upload");
+    off += (long long)cnt;
+    if (Kall) Kall->push_back(K);
+  }
+  return LBM_OK;
+}
 
 extern "C" {
 
@@ -440,32 +504,14 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   if ((rc = alloc_bytes(h, (void**)&h->dev.partials, sizeof(double) * h->reduce_blocks))) return fail(rc);
   if ((rc = alloc_bytes(h, (void**)&h->dev.scalar, sizeof(double)))) return fail(rc);
   if ((rc = alloc_bytes(h, (void**)&h->dev.flag, sizeof(int)))) return fail(rc);
+  // one mass partial per collide-stream block: at most one block per 32 x 16 tile and plane
+  h->cs_part_cap = (long long)((prm->grid[0] + 31) / 32) * ((prm->grid[1] + 15) / 16) * prm->grid[2];
+  if ((rc = alloc_bytes(h, (void**)&h->cs_part, sizeof(double) * h->cs_part_cap))) return fail(rc);
   if (cudaMemsetAsync(h->dev.flag, 0, sizeof(int), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
 
   // weight matrices K_mu (Section 2.4) in FP64 on the host, then the working precision
   std::vector<std::vector<double>> Kall;
-  {
-    std::vector<double> K, KT;
-    long long off = 0;
-    for (int mu = 0; mu < h->d; ++mu) {
-      const int side = prm->grid[mu];
-      K.assign((size_t)side * side, 0.0);
-      KT.assign((size_t)side * side, 0.0);
-      lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], prm->g[mu] * dv.h[mu], side, prm->dx, K.data());
-      for (int n = 0; n < side; ++n)
-        for (int l = 0; l < side; ++l) KT[(size_t)l * side + n] = K[(size_t)n * side + l];
-      const size_t cnt = (size_t)side * side;
-      cudaError_t e = cudaMemcpyAsync(h->dev.stage, K.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-      if (e == cudaSuccess) e = lbm::launch_convert_in(h->dev.stage, (char*)h->dev.K + off * E, h->elem, cnt, h->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(h->dev.stage, KT.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-      if (e == cudaSuccess) e = lbm::launch_convert_in(h->dev.stage, (char*)h->dev.KT + off * E, h->elem, cnt, h->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-      if (e != cudaSuccess) return fail(record_cuda(e, "weight upload"));
-      off += (long long)cnt;
-      Kall.push_back(K);
-    }
-  }
+  if ((rc = upload_weights(h, dv.h, &Kall))) return fail(rc);
   if (lbm::bf16_parts(prm->precision) || prm->precision == LBM_FP32_TF32SPLIT) {
     if ((rc = lbm::tc_prepare(h, Kall, batched ? 128 : 0, batched ? 1 : 0))) return fail(rc);
     h->launches_per_step = 2;  // (lbm_launches_per_step counts the tf32 regrouping launches)
@@ -494,7 +540,7 @@ int lbm_create_batch(int nprob, const lbm_params* prms, const double* const* C0_
   if (!out || !prms || !C0_host || nprob < 1) return LBM_EINVAL;
   *out = nullptr;
   const lbm_params& p0 = prms[0];
-  if (p0.precision != LBM_FP32 && p0.precision != LBM_FP32_BF16SPLIT) return LBM_ENOTSUP;
+  if (p0.precision != LBM_FP32 && !lbm::bf16_parts(p0.precision)) return LBM_ENOTSUP;
   for (int i = 0; i < nprob; ++i) {
     if (!C0_host[i]) return LBM_EINVAL;
     if (prms[i].lattice != p0.lattice || prms[i].collision != p0.collision || prms[i].precision != p0.precision)
@@ -533,7 +579,7 @@ int lbm_create_batch(int nprob, const lbm_params* prms, const double* const* C0_
     b->subs.push_back(sub);
   }
   int rc = LBM_OK;
-  if (p0.precision == LBM_FP32_BF16SPLIT) {
+  if (lbm::bf16_parts(p0.precision)) {
     if ((rc = lbm::tc_batch_prepare(b))) return fail(rc);
     b->launches_per_step = 2;
   } else {
@@ -585,6 +631,10 @@ int lbm_reset(lbm_t h) {
 int lbm_profile(lbm_t h, int nsteps, double* ms) {
   if (!h || !ms || nsteps < 0 || nsteps > 4096) return LBM_EINVAL;
   ms[0] = ms[1] = 0.0;
+  if (nsteps > 0) {
+    h->mass_valid = true;
+    for (lbm_s* p : h->subs) p->mass_valid = true;
+  }
   // every step's three events are queued before the one synchronisation, so that the
   // intervals measure the kernels, not the host's submission of each launch
   std::vector<cudaEvent_t> ev(3 * (size_t)nsteps);
@@ -594,6 +644,7 @@ int lbm_profile(lbm_t h, int nsteps, double* ms) {
     if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
   if (made < ev.size()) rc = record_cuda(cudaErrorMemoryAllocation, "lbm_profile");
   for (int k = 0; k < nsteps && rc == LBM_OK; ++k) {
+    if ((rc = upload_time(h, 1))) break;
     cudaError_t e = cudaEventRecord(ev[3 * k], h->stream);
     if (e == cudaSuccess) {
       if (h->is_batch() && h->batch_tc_blocks > 0) e = lbm::launch_frac_tc_batch(h, h->stream);
@@ -616,6 +667,7 @@ int lbm_profile(lbm_t h, int nsteps, double* ms) {
     if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[3 * k + 2], h->stream);
     if (e != cudaSuccess) rc = record_cuda(e, "lbm_profile");
     h->cur ^= 1;
+    ++h->t_steps;
     for (lbm_s* p : h->subs) p->cur = h->cur;
   }
   if (rc == LBM_OK && nsteps > 0) {
@@ -637,6 +689,10 @@ int lbm_profile(lbm_t h, int nsteps, double* ms) {
 int lbm_step(lbm_t h, int nsteps) {
   if (!h || nsteps < 0) return LBM_EINVAL;
   int rc;
+  if (nsteps > 0) {
+    h->mass_valid = true;  // the collide-stream kernel leaves the new C's mass partials
+    for (lbm_s* p : h->subs) p->mass_valid = true;
+  }
   if (h->fused) {
     // one cooperative launch per (up to) 4096 steps; it flips the buffer parity per step
     while (nsteps > 0) {
@@ -649,11 +705,15 @@ int lbm_step(lbm_t h, int nsteps) {
   }
   while (nsteps >= h->graph_steps) {
     if (!h->graph_exec[h->cur] && (rc = capture_graph(h, h->cur))) return rc;
+    if ((rc = upload_time(h, h->graph_steps))) return rc;
     LBM_CUDA(cudaGraphLaunch(h->graph_exec[h->cur], h->stream));
     nsteps -= h->graph_steps;  // even: the current buffer index is unchanged
+    h->t_steps += h->graph_steps;
   }
-  for (int k = 0; k < nsteps; ++k)
-    if ((rc = one_step(h, h->cur, h->stream))) return rc;
+  for (int k = 0; k < nsteps; ++k) {
+    if ((rc = upload_time(h, 1)) || (rc = one_step(h, h->cur, h->stream))) return rc;
+    ++h->t_steps;
+  }
   for (lbm_s* p : h->subs) p->cur = h->cur;
   return LBM_OK;
 }
@@ -723,6 +783,8 @@ int lbm_write_f(lbm_t h, const double* f_host) {
   }
   LBM_CUDA(lbm::launch_moment(h, h->dev.f[h->cur], h->dev.C, h->stream));
   if (uses_tc(h)) LBM_CUDA(lbm::launch_split_C(h, h->stream));
+  if (h->fld.on) LBM_CUDA(lbm::launch_scale_fields(h, h->stream));
+  h->mass_valid = false;
   return latched(h);
 }
 
@@ -762,8 +824,9 @@ long long lbm_state_size(lbm_t h) {
 int lbm_save(lbm_t h, void* dst_host, long long bytes) {
   if (!h || !dst_host || bytes < state_bytes(h)) return LBM_EINVAL;
   const std::vector<lbm_s*> ms = members(h);
-  StateHeader hd{kStateMagic, kStateVersion, h->prm.lattice, h->prm.precision, (int32_t)ms.size(), 0,
-                 payload_bytes(h)};
+  // the header's spare word carries the step counter (time of a source or wall values)
+  StateHeader hd{kStateMagic, kStateVersion, h->prm.lattice, h->prm.precision, (int32_t)ms.size(),
+                 (int32_t)std::min<long long>(h->t_steps, 0x7fffffff), payload_bytes(h)};
   char* out = static_cast<char*>(dst_host);
   std::memcpy(out, &hd, sizeof(hd));
   out += sizeof(hd);
@@ -804,9 +867,12 @@ int lbm_load(lbm_t h, const void* src_host, long long bytes) {
     in += b;
     LBM_CUDA(lbm::launch_moment(p, p->dev.f[h->cur], p->dev.C, h->stream));
     if (uses_tc(p)) LBM_CUDA(lbm::launch_split_C(p, h->stream));
+    if (p->fld.on) LBM_CUDA(lbm::launch_scale_fields(p, h->stream));
     LBM_CUDA(cudaMemsetAsync(p->dev.flag, 0, sizeof(int), h->stream));
+    p->mass_valid = false;
   }
   LBM_CUDA(cudaStreamSynchronize(h->stream));
+  h->t_steps = hd.pad;
   return LBM_OK;
 }
 
@@ -967,7 +1033,8 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
   if (!h->is_batch() && h->tc) {
     const int sms = lbm::device_sms();
     const int kbmin = lbm::tc_kbmin(h);
-    const bool five = h->prm.precision == LBM_FP32_BF16SPLIT5;  // per-tile kernel, 64/128 columns
+    // the forms with three weight parts take 64/128 columns
+    const bool five = h->prm.precision == LBM_FP32_BF16SPLIT5 || h->prm.precision == LBM_FP32_BF16SPLIT6;
     for (int bn : {64, 128, 256})
       for (int ks : {1, 2, 4, 8}) {
         if (bn == 256 && (ks != 1 || five)) continue;
@@ -975,7 +1042,7 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
         if (lbm::tc_count_tiles(h, bn) * ks > 2LL * sms) continue;  // at most two waves
         ops.push_back({bn, ks, 0, cur.chunk});
       }
-    if (!five && lbm::tc_count_tiles(h, 128) >= sms) ops.push_back({128, 1, 1, cur.chunk});
+    if (lbm::tc_count_tiles(h, 128) >= sms) ops.push_back({128, 1, 1, cur.chunk});
     if (!five && lbm::tc_count_tiles(h, 256) >= sms) ops.push_back({256, 1, 1, cur.chunk});
     // the fused step where the plan is one it covers (2-D bf16, 64/128 columns, split 2 or 4)
     const size_t nops = ops.size();
@@ -1044,9 +1111,209 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
 int lbm_mass(lbm_t h, int prob, double* mass) {
   lbm_s* p = member(h, prob);
   if (!p || !mass) return LBM_EINVAL;
-  LBM_CUDA(lbm::launch_mass(p, p->dev.C, h->stream));
+  if (p->mass_valid)  // the latest step's block partials: one small pass
+    LBM_CUDA(lbm::launch_step_mass(p, 0.0, h->stream));
+  else                // C from a re-initialisation: reduce C itself
+    LBM_CUDA(lbm::launch_mass(p, p->dev.C, h->stream));
   LBM_CUDA(cudaMemcpyAsync(mass, p->dev.scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   return latched(p);
+}
+
+int lbm_set_mass_limit(lbm_t h, double limit) {
+  if (!h || !(limit >= 0.0) || !std::isfinite(limit)) return LBM_EINVAL;
+  h->mass_limit = limit;
+  for (lbm_s* p : h->subs) p->mass_limit = limit;
+  return LBM_OK;
+}
+
+// The per-node path's coefficient buffers from the arrays kept in fld (empty: the constants of
+// lbm_params at every node), or freed when neither coefficients, a source nor wall values
+// ask for that path; K_mu rebuilt accordingly; graphs dropped; re-initialised.
+static int rebuild_fields(lbm_s* h) {
+  const int d = h->d;
+  const long long nodes = h->sp.nodes;
+  const lbm_params& P = h->prm;
+  const double e2 = (d == 2) ? 1.0 / 3.0 : 1.0 / 4.0, wi = h->sp.wi;
+  const double ratio = P.dt / (P.dx * P.dx);
+  const double* D_field = h->fld.D_host.empty() ? nullptr : h->fld.D_host.data();
+  const double* g_field = h->fld.g_host.empty() ? nullptr : h->fld.g_host.data();
+  const double* u_field = h->fld.u_host.empty() ? nullptr : h->fld.u_host.data();
+  const bool on = D_field || g_field || u_field || h->fld.src || h->fld.cw;
+  const int NC = (P.collision == LBM_MRT) ? d * (d + 1) / 2 : 1;
+  std::vector<double> coll, advw, gv;
+  if (on) {
+    coll.assign((size_t)NC * nodes, 0.0);
+    advw.assign((size_t)d * nodes, 0.0);
+    gv.assign((size_t)d * nodes, 0.0);
+    if (P.collision == LBM_BGK && !D_field) {
+      // BGK keeps one relaxation time per node: the constant D must be spherical as well
+      for (int a = 1; a < d; ++a)
+        if (P.D[3 * a + a] != P.D[0]) return LBM_EINVAL;
+    }
+    for (long long i = 0; i < nodes; ++i) {
+      double Dm[9];
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) Dm[a * d + b] = D_field ? D_field[((size_t)a * d + b) * nodes + i] : P.D[3 * a + b];
+      for (int k = 0; k < d * d; ++k)
+        if (!std::isfinite(Dm[k])) return LBM_EINVAL;
+      if (P.collision == LBM_BGK) {
+        // one relaxation time per node: D(x) spherical (Eq. Diffusion_Coefficient_3D)
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b)
+            if ((a == b && Dm[a * d + b] != Dm[0]) || (a != b && Dm[a * d + b] != 0.0)) return LBM_EINVAL;
+        if (!(Dm[0] > 0.0)) return LBM_EINVAL;
+        coll[i] = 1.0 / (Dm[0] * ratio / e2 + 0.5);
+      } else {
+        // flux block of Lambda^-1: lambdabar(x) = D(x) dt/(e^2 dx^2) + Id/2 (Eq. D_ab), SPD;
+        // its inverse R(x) holds the rates of the flux moments (Eq. MatrixS)
+        double lb[9], R[9];
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) lb[a * d + b] = Dm[a * d + b] * ratio / e2 + (a == b ? 0.5 : 0.0);
+        if (!is_spd(d, lb) || !invert(d, lb, R)) return LBM_EINVAL;
+        int k = 0;
+        for (int a = 0; a < d; ++a)
+          for (int b = a; b < d; ++b) coll[(size_t)(k++) * nodes + i] = 0.5 * (R[a * d + b] + R[b * d + a]);
+      }
+      for (int mu = 0; mu < d; ++mu) {
+        const double g = g_field ? g_field[(size_t)mu * nodes + i] : P.g[mu];
+        const double u = u_field ? u_field[(size_t)mu * nodes + i] : P.u[mu];
+        if (!(g > 0.0) || !std::isfinite(g) || !std::isfinite(u)) return LBM_EINVAL;
+        gv[(size_t)mu * nodes + i] = g;
+        advw[(size_t)mu * nodes + i] = (P.dt / P.dx) * u * wi / e2;
+      }
+    }
+  }
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  drop_graphs(h);  // the captured launches take other kernels and arguments now
+  for (void* p : {h->fld.coll, h->fld.advw, h->fld.g, h->fld.G}) lbm::dev_free(h, p);
+  h->fld.coll = h->fld.advw = h->fld.g = h->fld.G = nullptr;
+  h->fld.on = false;
+  int rc = LBM_OK;
+  if (on) {
+    const size_t E = h->elem;
+    if ((rc = alloc_bytes(h, &h->fld.coll, E * NC * nodes)) || (rc = alloc_bytes(h, &h->fld.advw, E * d * nodes)) ||
+        (rc = alloc_bytes(h, &h->fld.g, E * d * nodes)) || (rc = alloc_bytes(h, &h->fld.G, E * d * nodes)))
+      return rc;
+    const std::pair<const std::vector<double>*, void*> ups[3] = {{&coll, h->fld.coll}, {&advw, h->fld.advw},
+                                                                 {&gv, h->fld.g}};
+    for (const auto& up : ups) {
+      const std::vector<double>& v = *up.first;
+      for (size_t off = 0; off < v.size(); off += (size_t)nodes) {  // one plane of nodes at a time
+        LBM_CUDA(cudaMemcpyAsync(h->dev.stage, v.data() + off, sizeof(double) * nodes, cudaMemcpyHostToDevice,
+                                 h->stream));
+        LBM_CUDA(lbm::launch_convert_in(h->dev.stage, (char*)up.second + off * E, h->elem, nodes, h->stream));
+        LBM_CUDA(cudaStreamSynchronize(h->stream));
+      }
+    }
+    h->fld.on = true;
+  }
+  Derived dv;
+  if ((rc = derive(&h->prm, &dv))) return rc;
+  if ((rc = upload_weights(h, dv.h, nullptr))) return rc;  // g inside the integrals, or folded into K
+  return lbm_reset(h);
+}
+
+// the per-node path applies to single FP64 / FP32 problems
+static int fields_supported(lbm_t h) {
+  if (!h || h->is_batch()) return LBM_EINVAL;
+  if (h->tc || (h->prm.precision != LBM_FP64 && h->prm.precision != LBM_FP32)) return LBM_ENOTSUP;
+  return LBM_OK;
+}
+
+// host array of `count` nodes-long planes into a device array in the working precision
+static int upload_planes(lbm_s* h, const double* host, int count, void** dst) {
+  const long long nodes = h->sp.nodes;
+  lbm::dev_free(h, *dst);
+  *dst = nullptr;
+  int rc = alloc_bytes(h, dst, (size_t)h->elem * count * nodes);
+  if (rc) return rc;
+  for (int k = 0; k < count; ++k) {
+    LBM_CUDA(cudaMemcpyAsync(h->dev.stage, host + (size_t)k * nodes, sizeof(double) * nodes, cudaMemcpyHostToDevice,
+                             h->stream));
+    LBM_CUDA(lbm::launch_convert_in(h->dev.stage, (char*)*dst + (size_t)k * nodes * h->elem, h->elem, nodes,
+                                    h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+// the slot table of the time factors exists while a source or wall values are set
+static int ensure_time_table(lbm_s* h) {
+  const bool want = h->fld.src || h->fld.cw;
+  if (want && !h->fld.tf) {
+    h->fld.tf_slots = h->graph_steps;
+    return alloc_bytes(h, (void**)&h->fld.tf, sizeof(double) * 2 * h->fld.tf_slots);
+  }
+  if (!want && h->fld.tf) {
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    lbm::dev_free(h, h->fld.tf);
+    h->fld.tf = nullptr;
+    h->fld.tf_slots = 0;
+  }
+  return LBM_OK;
+}
+
+int lbm_set_fields(lbm_t h, const double* D_field, const double* g_field, const double* u_field) {
+  int rc = fields_supported(h);
+  if (rc) return rc;
+  const size_t nodes = (size_t)h->sp.nodes, d = (size_t)h->d;
+  // validate on a copy first: the handle stays unchanged when the arrays are rejected
+  lbm::FieldState keep;
+  keep.D_host.swap(h->fld.D_host);
+  keep.g_host.swap(h->fld.g_host);
+  keep.u_host.swap(h->fld.u_host);
+  if (D_field) h->fld.D_host.assign(D_field, D_field + d * d * nodes);
+  if (g_field) h->fld.g_host.assign(g_field, g_field + d * nodes);
+  if (u_field) h->fld.u_host.assign(u_field, u_field + d * nodes);
+  h->fld.coeff = D_field || g_field || u_field;
+  rc = rebuild_fields(h);
+  if (rc == LBM_EINVAL) {  // restore the previous arrays
+    h->fld.D_host.swap(keep.D_host);
+    h->fld.g_host.swap(keep.g_host);
+    h->fld.u_host.swap(keep.u_host);
+    h->fld.coeff = !h->fld.D_host.empty() || !h->fld.g_host.empty() || !h->fld.u_host.empty();
+    const int rc2 = rebuild_fields(h);
+    return rc2 ? rc2 : LBM_EINVAL;
+  }
+  return rc;
+}
+
+int lbm_set_source(lbm_t h, const double* S_field, double rate) {
+  int rc = fields_supported(h);
+  if (rc) return rc;
+  if (!std::isfinite(rate)) return LBM_EINVAL;
+  if (S_field)
+    for (long long i = 0; i < h->sp.nodes; ++i)
+      if (!std::isfinite(S_field[i])) return LBM_EINVAL;
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (S_field) {
+    if ((rc = upload_planes(h, S_field, 1, &h->fld.src))) return rc;
+  } else {
+    lbm::dev_free(h, h->fld.src);
+    h->fld.src = nullptr;
+  }
+  h->fld.src_rate = rate;
+  if ((rc = ensure_time_table(h))) return rc;
+  return rebuild_fields(h);
+}
+
+int lbm_set_wall_values(lbm_t h, const double* Cw_field, double rate) {
+  int rc = fields_supported(h);
+  if (rc) return rc;
+  if (!std::isfinite(rate)) return LBM_EINVAL;
+  if (Cw_field)
+    for (long long i = 0; i < h->sp.nodes; ++i)
+      if (!std::isfinite(Cw_field[i])) return LBM_EINVAL;
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (Cw_field) {
+    if ((rc = upload_planes(h, Cw_field, 1, &h->fld.cw))) return rc;
+  } else {
+    lbm::dev_free(h, h->fld.cw);
+    h->fld.cw = nullptr;
+  }
+  h->fld.cw_rate = rate;
+  if ((rc = ensure_time_table(h))) return rc;
+  return rebuild_fields(h);
 }
 
 int lbm_sync(lbm_t h) {
@@ -1097,7 +1364,7 @@ static int step_hook(lbm_s* h, int& cur, cudaStream_t s) { return one_step(h, cu
 int lbm_grad(lbm_t h, int nsnap, const int* snap_steps, const double* obs, int ckpt_every, double* loss,
              double* grad) {
   if (!h || nsnap < 1 || !snap_steps || !obs || ckpt_every < 1 || !loss || !grad) return LBM_EINVAL;
-  if (h->is_batch() || h->tc || h->prm.collision != LBM_MRT) return LBM_ENOTSUP;
+  if (h->is_batch() || h->tc || h->fld.on || h->prm.collision != LBM_MRT) return LBM_ENOTSUP;
   for (int k = 0; k < nsnap; ++k)
     if (snap_steps[k] < 0 || (k > 0 && snap_steps[k] <= snap_steps[k - 1])) return LBM_EINVAL;
   double dOm[3][lbm::kMaxQ][lbm::kMaxQ];

@@ -40,6 +40,27 @@ struct KConst {
   real C_wall;
   int ksum;           // F holds ksum partial sums (split-K operator), added in order
   long long pstride;  // elements between partial sums
+  real sfree[3];      // MRT rates of the free moments d+1..Q-1 (spatially varying coefficients)
+};
+
+// Coefficients that vary from node to node (lbm_set_fields), working precision, [k][node]:
+//   coll: BGK 1/lambda(x); MRT the symmetric rate block R(x) = lambdabar(x)^-1 of the flux
+//         moments, entries (00, 01, 11) in 2-D, (00, 01, 02, 11, 12, 22) in 3-D
+//   advw: (dt/dx) u_mu(x) w_i / e^2, the advective factor of Eq. (Feq)
+//   g:    g_mu(x); the kernel writes G_mu = g_mu(x) C(x), the operator's input along mu
+//   src:  S(x) of a source S_c(x, t) = S(x) exp(rate t) (or null), added after the collision
+//         as w_i S_c dt (Eq. LBE_Ket); cw: wall values C_w(x) of C_0(x, t) = C_w(x) exp(rate t)
+//         (or null: the constant C_wall); tf: this launch's time factors, tf[0] =
+//         exp(rate_S t) dt at the step's start t, tf[1] = exp(rate_w (t + dt)) at its end.
+template <typename real>
+struct FieldPtrs {
+  const real* coll;
+  const real* advw;
+  const real* g;
+  real* G;
+  const real* src;
+  const real* cw;
+  const double* tf;
 };
 
 template <typename real>
@@ -55,6 +76,7 @@ KConst<real> make_const(const StepParams& sp) {
   k.C_wall = static_cast<real>(sp.C_wall);
   k.ksum = sp.ksum;
   k.pstride = sp.pstride;
+  for (int i = 0; i < 3; ++i) k.sfree[i] = static_cast<real>(sp.sfree[i]);
   return k;
 }
 
@@ -104,6 +126,119 @@ __device__ __forceinline__ void collide_node(const KConst<real>& sp, const real*
   }
 }
 
+// MRT change of basis, Eq. (MatrixD2): entry (i, q) of M for D2Q5 (D = 2) or D3Q7 (D = 3),
+// and the squared norm of row i (the rows are orthogonal: M^-1 = M^T diag(1 / norm))
+__host__ __device__ constexpr int mom(int D, int i, int q) {
+  if (i == 0) return 1;
+  if (i <= D) return q == 2 * i - 1 ? 1 : (q == 2 * i ? -1 : 0);  // flux moments
+  if (D == 2) return i == 3 ? (q == 0 ? 4 : -1) : (q == 0 ? 0 : (q <= 2 ? 1 : -1));
+  if (i == 4) return q == 0 ? 6 : -1;
+  if (i == 5) return q == 0 ? 0 : (q <= 2 ? 2 : -1);
+  return (q == 0 || q <= 2) ? 0 : (q <= 4 ? 1 : -1);
+}
+__host__ __device__ constexpr int mom_norm(int D, int i) {
+  int n = 0;
+  for (int q = 0; q < 2 * D + 1; ++q) n += mom(D, i, q) * mom(D, i, q);
+  return n;
+}
+static_assert(mom_norm(2, 3) == 20 && mom_norm(3, 4) == 42 && mom_norm(3, 5) == 12 && mom_norm(3, 6) == 4,
+              "moment rows of Eq. (MatrixD2)");
+
+template <typename real, int D>
+__device__ __forceinline__ void collide_moments(const KConst<real>& sp, const FieldPtrs<real>& fp, long long node,
+                                                const real* f, const real* dl, real* fs);
+
+// Equilibrium and collision of one node with coefficients of that node (FieldPtrs):
+// Eq. (Feq) with u(x); BGK f* = f - (f - feq)/lambda(x); MRT in moment space
+// f* = f - M^-1 Lambda(x) M (f - feq), Lambda(x) = diag(1, R(x), s_free) (Eqs. MRT-Coll,
+// MatrixS, D_ab with lambda_{mu nu}(x)).
+template <typename real, int D, bool MRT>
+__device__ __forceinline__ void collide_node_field(const KConst<real>& sp, const FieldPtrs<real>& fp, long long node,
+                                                   const real* f, const real* F, real* fs) {
+  constexpr int Q = Lat<D>::Q;
+  const long long nodes = sp.nodes;
+  real C = f[0];
+#pragma unroll
+  for (int q = 1; q < Q; ++q) C += f[q];
+  real sumF = F[0];
+#pragma unroll
+  for (int mu = 1; mu < D; ++mu) sumF += F[mu];
+  real dl[Q];
+  dl[0] = f[0] - (C - sp.w0 * sumF);
+#pragma unroll
+  for (int mu = 0; mu < D; ++mu) {
+    const real a = sp.wi * F[mu];
+    const real b = fp.advw[mu * nodes + node] * C;
+    dl[2 * mu + 1] = f[2 * mu + 1] - (a + b);
+    dl[2 * mu + 2] = f[2 * mu + 2] - (a - b);
+  }
+  if (!MRT) {
+    const real om = fp.coll[node];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fs[q] = f[q] - om * dl[q];
+  } else {
+    collide_moments<real, D>(sp, fp, node, f, dl, fs);
+  }
+  if (fp.src) {  // |w> S_c(x, t) dt, Eq. (LBE_Ket)
+    const real sv = fp.src[node] * static_cast<real>(fp.tf[0]);
+    fs[0] += sp.w0 * sv;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) fs[q] += sp.wi * sv;
+  }
+}
+
+// MRT collision in moment space with the rates of the node: f* = f - M^-1 Lambda(x) M dl,
+// dl = f - feq, Lambda(x) = diag(1, R(x), s_free) (Eqs. MRT-Coll, MatrixS, D_ab)
+template <typename real, int D>
+__device__ __forceinline__ void collide_moments(const KConst<real>& sp, const FieldPtrs<real>& fp, long long node,
+                                                const real* f, const real* dl, real* fs) {
+  constexpr int Q = Lat<D>::Q;
+  const long long nodes = sp.nodes;
+  real dm[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    real acc = static_cast<real>(mom(D, i, 0)) * dl[0];
+#pragma unroll
+    for (int q = 1; q < Q; ++q)
+      if (mom(D, i, q) != 0) acc += static_cast<real>(mom(D, i, q)) * dl[q];
+    dm[i] = acc;
+  }
+  real R[D][D];
+  if (D == 2) {
+    R[0][0] = fp.coll[node];
+    R[0][1] = R[1][0] = fp.coll[nodes + node];
+    R[1][1] = fp.coll[2 * nodes + node];
+  } else {
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = a; b < D; ++b) {
+        R[a][b] = R[b][a] = fp.coll[k * nodes + node];
+        ++k;
+      }
+  }
+  real dmp[Q];
+  dmp[0] = dm[0];  // conserved moment: rate 1, no effect (dm[0] = 0 up to rounding)
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    real acc = R[a][0] * dm[1];
+#pragma unroll
+    for (int b = 1; b < D; ++b) acc += R[a][b] * dm[1 + b];
+    dmp[1 + a] = acc;
+  }
+#pragma unroll
+  for (int k = D + 1; k < Q; ++k) dmp[k] = sp.sfree[k - D - 1] * dm[k];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    real acc = static_cast<real>(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      if (mom(D, i, q) != 0) acc += static_cast<real>(mom(D, i, q)) * dmp[i] / static_cast<real>(mom_norm(D, i));
+    fs[q] = f[q] - acc;
+  }
+}
+
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -123,6 +258,7 @@ struct SplitOut {
   float* tlo[2];
   int tg1;  // groups of 4 along y
   int tpx;  // x pitch (n0 rounded up to 16)
+  void* lo2;  // bf16 with C in three parts (SPLIT = 3): the third part
 };
 
 // Per-problem entry of a grouped (batched) collide-stream launch.
@@ -135,21 +271,53 @@ struct BatchCS {
   float* C;
   SplitOut so;
   int* flag;
+  double* mpart;       // the problem's mass partials, one per block of it
   int bx, by, zchunk;  // blocks in x, y and the z chunk length (2-D: tile rows per block)
   int tma;             // the maps above are valid
 };
 
+// SPLIT: 1 = bf16 hi + lo, 3 = bf16 in three parts (each the rounding of what the previous
+// ones left: the three add up to C exactly), 2 = tf32 hi + lo
 template <int SPLIT, typename real>
 __device__ __forceinline__ void write_split(const SplitOut& so, long long o, real C) {
   const float c = static_cast<float>(C);
-  if (SPLIT == 1) {
+  if (SPLIT == 1 || SPLIT == 3) {
     const __nv_bfloat16 h = __float2bfloat16_rn(c);
+    const float r1 = c - __bfloat162float(h);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1);
     static_cast<__nv_bfloat16*>(so.hi)[o] = h;
-    static_cast<__nv_bfloat16*>(so.lo)[o] = __float2bfloat16_rn(c - __bfloat162float(h));
+    static_cast<__nv_bfloat16*>(so.lo)[o] = l;
+    if (SPLIT == 3) static_cast<__nv_bfloat16*>(so.lo2)[o] = __float2bfloat16_rn(r1 - __bfloat162float(l));
   } else if (SPLIT == 2) {
     const float h = tf32_rna(c);
     static_cast<float*>(so.hi)[o] = h;
     static_cast<float*>(so.lo)[o] = tf32_rna(c - h);
+  }
+}
+
+// Block partial of the mass of the new concentration (Algorithm 1, loop item 5): every
+// thread adds the C it wrote in FP64 (macc), the block reduces them in a fixed order
+// (warp shuffles, then warp 0 over the warps) and stores one FP64 partial at part[slot];
+// the handle adds the partials of the latest step in one small pass when asked
+// (lbm_mass), so the mass is a by-product of the step.  Called by every thread of the
+// block; part may be null (no partial wanted).
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void block_mass(double macc, double* part, int slot) {
+  __shared__ double s_wm[32];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  macc = warp_sum_d(macc);
+  if ((tid & 31) == 0) s_wm[tid >> 5] = macc;
+  __syncthreads();
+  if (tid < 32) {
+    double v = tid < nw ? s_wm[tid] : 0.0;
+    v = warp_sum_d(v);
+    if (tid == 0 && part) part[slot] = v;
   }
 }
 
@@ -162,9 +330,10 @@ __device__ __forceinline__ void write_split(const SplitOut& so, long long o, rea
 // In 2-D the block handles one plane.  Each node is loaded ~1.19 times per step.
 constexpr int TX = 32, TY = 16, HALO_WARPS = 3;
 
-template <typename real, int D, bool MRT>
+template <typename real, int D, bool MRT, bool FLD = false>
 __device__ __forceinline__ void collide_at(const KConst<real>& sp, const real* __restrict__ f_in,
-                                           const real* __restrict__ F, bool inside, long long node, real* fs) {
+                                           const real* __restrict__ F, bool inside, long long node, real* fs,
+                                           const FieldPtrs<real>& fp) {
   constexpr int Q = Lat<D>::Q;
   if (!inside) {
 #pragma unroll
@@ -177,7 +346,8 @@ __device__ __forceinline__ void collide_at(const KConst<real>& sp, const real* _
   for (int q = 0; q < Q; ++q) f[q] = f_in[q * nodes + node];
 #pragma unroll
   for (int mu = 0; mu < D; ++mu) Fv[mu] = frac_term(sp, F, mu, node);
-  collide_node<real, D, MRT>(sp, f, Fv, fs);
+  if (FLD) collide_node_field<real, D, MRT>(sp, fp, node, f, Fv, fs);
+  else collide_node<real, D, MRT>(sp, f, Fv, fs);
 }
 
 // Asynchronous prefetch of the 2-D march (FP32): every thread copies the populations and
@@ -208,11 +378,12 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // One block's column (tile bx, by; planes z0 .. z1-1) of one problem.
-template <typename real, int D, bool MRT, int SPLIT>
+template <typename real, int D, bool MRT, int SPLIT, bool FLD = false>
 __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* __restrict__ f_in,
                                            const real* __restrict__ F, real* __restrict__ f_out,
                                            real* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
-                                           int bx, int by, int z0, int z1) {
+                                           int bx, int by, int z0, int z1, double* mpart, int mslot,
+                                           const FieldPtrs<real> fp = FieldPtrs<real>{}) {
   constexpr int Q = Lat<D>::Q;
   // movers of the current plane on the tile plus ring: [buffer][mover 1..4][y+1][x+1]
   __shared__ real s_m[2][4][TY + 2][TX + 2];
@@ -243,28 +414,29 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   const bool in_xy = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
   const long long col = gx + (long long)n0 * gy;
   bool bad = false;
+  double macc = 0.0;
 
   real cur[Q], nxt[Q];
   real prev5 = static_cast<real>(0);
   if (owner) {
     if (D == 3) {
       real t[Q];
-      collide_at<real, D, MRT>(sp, f_in, F, in_xy && z0 > 0, col + (z0 - 1) * plane, t);
+      collide_at<real, D, MRT, FLD>(sp, f_in, F, in_xy && z0 > 0, col + (z0 - 1) * plane, t, fp);
       prev5 = t[5];
     }
-    collide_at<real, D, MRT>(sp, f_in, F, in_xy, col + z0 * plane, cur);
+    collide_at<real, D, MRT, FLD>(sp, f_in, F, in_xy, col + z0 * plane, cur, fp);
   }
   int buf = 0;
   for (int z = z0; z < z1; ++z) {
     if (owner) {
-      if (D == 3) collide_at<real, D, MRT>(sp, f_in, F, in_xy && z + 1 < n2, col + (z + 1) * plane, nxt);
+      if (D == 3) collide_at<real, D, MRT, FLD>(sp, f_in, F, in_xy && z + 1 < n2, col + (z + 1) * plane, nxt, fp);
       s_m[buf][0][sy][sx] = cur[1];
       s_m[buf][1][sy][sx] = cur[2];
       s_m[buf][2][sy][sx] = cur[3];
       s_m[buf][3][sy][sx] = cur[4];
     } else {
       real h[Q];
-      collide_at<real, D, MRT>(sp, f_in, F, in_xy, col + z * plane, h);
+      collide_at<real, D, MRT, FLD>(sp, f_in, F, in_xy, col + z * plane, h, fp);
       if (wy == TY) {
         if (lane < 16) s_m[buf][0][sy][sx] = h[1];  // moves +x into the tile
         else s_m[buf][1][sy][sx] = h[2];            // moves -x into the tile
@@ -307,8 +479,11 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
       }
       real C = sum_known;
       if (n_unknown > 0) {
-        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
-        const real fill = (sp.C_wall - sum_known) / static_cast<real>(n_unknown);
+        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit; the
+        // wall value varies with position and time when given (Section 2.5)
+        real cwall = sp.C_wall;
+        if (FLD && fp.cw) cwall = fp.cw[col + z * plane] * static_cast<real>(fp.tf[1]);
+        const real fill = (cwall - sum_known) / static_cast<real>(n_unknown);
 #pragma unroll
         for (int q = 0; q < Q; ++q)
           if (!known[q]) fv[q] = fill;
@@ -321,7 +496,12 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
       for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
       C_out[node] = C;
       if (SPLIT) write_split<SPLIT>(so, ((long long)z * n1 + gy) * so.ldp + gx, C);
+      if (FLD) {  // the operator's inputs of the next step: g_mu(x) C, one field per axis
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) fp.G[mu * nodes + node] = fp.g[mu * nodes + node] * C;
+      }
       bad |= !isfinite(C);
+      macc += static_cast<double>(C);
     }
     if (owner && D == 3) {
       prev5 = cur[5];
@@ -332,6 +512,7 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   }
   // one flag update per warp at most
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
+  block_mass(macc, mpart, mslot);
 }
 
 // movers of the current tile plus ring for the 2-D FP32 marches: [buffer][mover 1..4][y+1][x+1]
@@ -346,7 +527,7 @@ template <bool MRT, int SPLIT>
 __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float* __restrict__ f_in,
                                             const float* __restrict__ F, float* __restrict__ f_out,
                                             float* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
-                                            int ychunk, int bx, int byc, float* stage) {
+                                            int ychunk, int bx, int byc, float* stage, double* mpart, int mslot) {
   constexpr int D = 2, Q = 5;
   auto& s_m = s_m2;
   const int n0 = sp.n[0], n1 = sp.n[1];
@@ -389,6 +570,7 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
   issue(tr0, 0);
   if (tr0 + 1 < tr1) issue(tr0 + 1, 1); else cp_async_commit();
   bool bad = false;
+  double macc = 0.0;
   int buf = 0;
   for (int tr = tr0; tr < tr1; ++tr) {
     const int slot = (tr - tr0) % PIPE_STAGES;
@@ -469,35 +651,44 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
       C_out[node] = C;
       if (SPLIT) write_split<SPLIT>(so, (long long)gy * so.ldp + gx, C);
       bad |= !isfinite(C);
+      macc += static_cast<double>(C);
     }
     buf ^= 1;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
+  block_mass(macc, mpart, mslot);
+}
+
+// linear index of this block in its grid (the slot of its mass partial)
+__device__ __forceinline__ int block_linear() {
+  return static_cast<int>(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
 template <bool MRT, int SPLIT>
 __global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
 collide_stream_march2_kernel(const KConst<float> sp, const float* __restrict__ f_in, const float* __restrict__ F,
                              float* __restrict__ f_out, float* __restrict__ C_out, int* __restrict__ flag,
-                             SplitOut so, int ychunk, int early) {
+                             SplitOut so, int ychunk, int early, double* mpart) {
   extern __shared__ __align__(16) float pipe_stage[];
   if (early) pdl_trigger();
-  march2_pipe<MRT, SPLIT>(sp, f_in, F, f_out, C_out, flag, so, ychunk, blockIdx.x, blockIdx.y, pipe_stage);
+  march2_pipe<MRT, SPLIT>(sp, f_in, F, f_out, C_out, flag, so, ychunk, blockIdx.x, blockIdx.y, pipe_stage, mpart,
+                          block_linear());
   if (!early) pdl_trigger();
 }
 
-template <typename real, int D, bool MRT, int SPLIT>
+template <typename real, int D, bool MRT, int SPLIT, bool FLD = false>
 __global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
 collide_stream_march_kernel(const KConst<real> sp, const real* __restrict__ f_in, const real* __restrict__ F,
                             real* __restrict__ f_out, real* __restrict__ C_out, int* __restrict__ flag, SplitOut so,
-                            int nz, int early) {
+                            int nz, int early, double* mpart, const FieldPtrs<real> fp = FieldPtrs<real>{}) {
   // z chunk blockIdx.z of nz (boundaries bz * n2 / nz): concurrent blocks march the same
   // z window, so the ring loads of neighbouring columns hit L2
   const int n2 = sp.n[2];
   const int bz = blockIdx.z;
   const int z0 = static_cast<int>((long long)bz * n2 / nz), z1 = static_cast<int>((long long)(bz + 1) * n2 / nz);
   if (early) pdl_trigger();
-  march_body<real, D, MRT, SPLIT>(sp, f_in, F, f_out, C_out, flag, so, blockIdx.x, blockIdx.y, z0, z1);
+  march_body<real, D, MRT, SPLIT, FLD>(sp, f_in, F, f_out, C_out, flag, so, blockIdx.x, blockIdx.y, z0, z1, mpart,
+                                       block_linear(), fp);
   if (!early) pdl_trigger();
 }
 
@@ -569,7 +760,8 @@ template <bool MRT, int SPLIT>
 __global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
 collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUtensorMap map_f,
                            const __grid_constant__ CUtensorMap map_F, float* __restrict__ f_out,
-                           float* __restrict__ C_out, int* __restrict__ flag, SplitOut so, int nz, int early) {
+                           float* __restrict__ C_out, int* __restrict__ flag, SplitOut so, int nz, int early,
+                           double* mpart) {
   constexpr int D = 3, Q = 7;
   extern __shared__ uint8_t cs_raw[];
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(cs_raw) + 127) & ~uintptr_t(127));
@@ -683,6 +875,7 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
     issue(z0 + 1);  // z0 + 1 <= z1: needed by the owners' first iteration
   }
   bool bad = false;
+  double macc = 0.0;
   float cur[Q], nxt[Q];
   float prev5 = 0.f;
   if (owner) {
@@ -772,6 +965,7 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
       C_out[node] = C;
       if (SPLIT) write_split<SPLIT>(so, ((long long)z * n1 + gy) * so.ldp + gx, C);
       bad |= !isfinite(C);
+      macc += static_cast<double>(C);
       Cn = C;
     }
     if (owner) {
@@ -791,6 +985,7 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
   if (tid == 0)
     for (int p = (z1 - 2 > z0 - 1 ? z1 - 2 : z0 - 1); p <= z1; ++p) cs_mbar_wait(&full[stage_of(p)], parity_of(p), flag);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
+  block_mass(macc, mpart, block_linear());
   if (!early) pdl_trigger();
 }
 
@@ -830,7 +1025,7 @@ template <bool MRT, int SPLIT>
 __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtensorMap* map_f,
                                            const CUtensorMap* map_F, float* __restrict__ f_out,
                                            float* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
-                                           int ychunk, int bx, int byc, uint8_t* raw) {
+                                           int ychunk, int bx, int byc, uint8_t* raw, double* mpart, int mslot) {
   constexpr int D = 2, Q = 5;
   auto& s_m = s_m2;
   float* s_c = nullptr;
@@ -901,6 +1096,7 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
   if (tid == 0)
     for (int t = tr0; t < tr1 && t < tr0 + nst; ++t) issue(t);
   bool bad = false;
+  double macc = 0.0;
   int buf = 0;
   for (int tr = tr0; tr < tr1; ++tr) {
     cs_mbar_wait(&full[stage_of(tr)], parity_of(tr), flag);
@@ -987,6 +1183,7 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       if (SPLIT) write_split<SPLIT>(so, (long long)gy * so.ldp + gx, C);
       if (SPLIT == 2 && wT) s_c[((tr & 1) * TY + dy) * TCP + dx] = C;
       bad |= !isfinite(C);
+      macc += static_cast<double>(C);
     }
     buf ^= 1;
   }
@@ -1002,16 +1199,19 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(cs_smem_u32(&full[s])) : "memory");
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
+  block_mass(macc, mpart, mslot);
 }
 
 template <bool MRT, int SPLIT>
 __global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
 collide_stream_tma2_kernel(const KConst<float> sp, const __grid_constant__ CUtensorMap map_f,
                            const __grid_constant__ CUtensorMap map_F, float* __restrict__ f_out,
-                           float* __restrict__ C_out, int* __restrict__ flag, SplitOut so, int ychunk, int early) {
+                           float* __restrict__ C_out, int* __restrict__ flag, SplitOut so, int ychunk, int early,
+                           double* mpart) {
   extern __shared__ uint8_t cs_raw2[];
   if (early) pdl_trigger();
-  march2_tma<MRT, SPLIT>(sp, &map_f, &map_F, f_out, C_out, flag, so, ychunk, blockIdx.x, blockIdx.y, cs_raw2);
+  march2_tma<MRT, SPLIT>(sp, &map_f, &map_F, f_out, C_out, flag, so, ychunk, blockIdx.x, blockIdx.y, cs_raw2, mpart,
+                         block_linear());
   if (!early) pdl_trigger();
 }
 
@@ -1058,14 +1258,14 @@ __global__ void __launch_bounds__(NT, 1)
 lbm_fused2_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P, const KConst<float> sp,
                   const __grid_constant__ CUtensorMap mf0, const __grid_constant__ CUtensorMap mf1,
                   const __grid_constant__ CUtensorMap mF, float* f0, float* f1, float* C, SplitOut so, int ychunk,
-                  int nsteps, int parity, unsigned int* gbar, int* flag) {
+                  int nsteps, int parity, unsigned int* gbar, int* flag, double* mpart) {
   extern __shared__ uint8_t fused_raw[];
   __shared__ uint32_t tmem_slot;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(fused_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.y * TX + threadIdx.x;
   if (threadIdx.y == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(BN * 4 <= 512 ? BN * 4 : 512)  // op_item's accumulator regions
+                 "r"(512)  // op_item's accumulator regions (at most 512 columns)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -1087,7 +1287,7 @@ lbm_fused2_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ T
     const CUtensorMap* mf = par ? &mf1 : &mf0;
     float* fo = par ? f0 : f1;
     for (int it = blockIdx.x; it < cs_items; it += G) {
-      march2_tma<MRT, 1>(sp, mf, &mF, fo, C, flag, so, ychunk, it % bxn, it / bxn, smem);
+      march2_tma<MRT, 1>(sp, mf, &mF, fo, C, flag, so, ychunk, it % bxn, it / bxn, smem, mpart, it);
       __syncthreads();
     }
     target += G;
@@ -1097,8 +1297,7 @@ lbm_fused2_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ T
   __syncthreads();
   if (threadIdx.y == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN * 4 <= 512 ? BN * 4 : 512)
-                 : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
 }
 
@@ -1124,6 +1323,7 @@ cudaError_t fused_launch(const lbm_s* h, int nsteps, int grid, cudaStream_t s) {
   SplitOut so{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
   const int bx = (h->sp.n[0] + TX - 1) / TX, by = (h->sp.n[1] + TY - 1) / TY;
   const int ychunk = h->cs_chunk > 0 ? std::min(h->cs_chunk, by) : ychunk_for((long long)bx * by, by);
+  h->cs_nparts = bx * ((by + ychunk - 1) / ychunk);  // one mass partial per collide-stream item
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(TX, TY + HALO_WARPS);
@@ -1136,7 +1336,8 @@ cudaError_t fused_launch(const lbm_s* h, int nsteps, int grid, cudaStream_t s) {
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, lbm_fused2_kernel<BN, KS, MRT>, p->maps, p->prm, sp, pl->f[0], pl->f[1], pl->F,
                             static_cast<float*>(h->dev.f[0]), static_cast<float*>(h->dev.f[1]),
-                            static_cast<float*>(h->dev.C), so, ychunk, nsteps, h->cur, h->fused_bar, h->dev.flag);
+                            static_cast<float*>(h->dev.C), so, ychunk, nsteps, h->cur, h->fused_bar, h->dev.flag,
+                            h->cs_part);
 }
 
 // 2-D batch blocks run either march (per problem): room for the larger ring
@@ -1169,19 +1370,19 @@ collide_stream_batch_kernel(const BatchCS* __restrict__ tab, const int* __restri
     extern __shared__ __align__(128) uint8_t batch_raw[];
     if (e.tma)
       march2_tma<MRT, SPLIT>(s_k, &e.mf[parity], &e.mF, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
-                             e.zchunk, bx, rest, batch_raw);
+                             e.zchunk, bx, rest, batch_raw, e.mpart, lb);
     else
       march2_pipe<MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
-                              e.zchunk, bx, rest, reinterpret_cast<float*>(batch_raw));
+                              e.zchunk, bx, rest, reinterpret_cast<float*>(batch_raw), e.mpart, lb);
   } else {
     march_body<float, D, MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
-                                     bx, rest, 0, e.k.n[2]);
+                                     bx, rest, 0, e.k.n[2], e.mpart, lb);
   }
 }
 
 template <typename real, int D>
 __global__ void init_equilibrium_kernel(const KConst<real> sp, const real* __restrict__ C, const real* __restrict__ F,
-                                        real* __restrict__ f) {
+                                        real* __restrict__ f, const real* __restrict__ advw) {
   const long long nodes = sp.nodes;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
        i += (long long)gridDim.x * blockDim.x) {
@@ -1197,11 +1398,20 @@ __global__ void init_equilibrium_kernel(const KConst<real> sp, const real* __res
 #pragma unroll
     for (int mu = 0; mu < D; ++mu) {
       const real a = sp.wi * Fv[mu];
-      const real b = sp.advw[mu] * c;
+      const real b = (advw ? advw[mu * nodes + i] : sp.advw[mu]) * c;  // u(x) when it varies
       f[(2 * mu + 1) * nodes + i] = a + b;
       f[(2 * mu + 2) * nodes + i] = a - b;
     }
   }
+}
+
+// G_mu = g_mu(x) C, the operator's inputs when g varies in space
+template <typename real>
+__global__ void scale_fields_kernel(long long nodes, int d, const real* __restrict__ C, const real* __restrict__ g,
+                                    real* __restrict__ G) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+       i += (long long)gridDim.x * blockDim.x)
+    for (int mu = 0; mu < d; ++mu) G[mu * nodes + i] = g[mu * nodes + i] * C[i];
 }
 
 template <typename real, int Q>
@@ -1218,20 +1428,21 @@ __global__ void moment_kernel(long long nodes, const real* __restrict__ f, real*
 template <bool MRT, int SPLIT>
 cudaError_t launch_tma3(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, const CUtensorMap& mf,
                         const CUtensorMap& mF, float* fo, float* Co, int* flag, const SplitOut& so, int nz,
-                        int early) {
+                        int early, double* mpart) {
   static std::atomic<unsigned long long> attr{0};
   if (const cudaError_t e = smem_attr_once(attr, collide_stream_tma3_kernel<MRT, SPLIT>, (int)TMA_SMEM); e != cudaSuccess) return e;
-  return cudaLaunchKernelEx(&cfg, collide_stream_tma3_kernel<MRT, SPLIT>, sp, mf, mF, fo, Co, flag, so, nz, early);
+  return cudaLaunchKernelEx(&cfg, collide_stream_tma3_kernel<MRT, SPLIT>, sp, mf, mF, fo, Co, flag, so, nz, early,
+                            mpart);
 }
 
 template <bool MRT, int SPLIT>
 cudaError_t launch_tma2(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, const CUtensorMap& mf,
                         const CUtensorMap& mF, float* fo, float* Co, int* flag, const SplitOut& so, int ychunk,
-                        int early) {
+                        int early, double* mpart) {
   static std::atomic<unsigned long long> attr{0};
   if (const cudaError_t e = smem_attr_once(attr, collide_stream_tma2_kernel<MRT, SPLIT>, (int)tma2_smem(8)); e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, collide_stream_tma2_kernel<MRT, SPLIT>, sp, mf, mF, fo, Co, flag, so, ychunk,
-                            early);
+                            early, mpart);
 }
 
 // at most two blocks per SM resident: the grid runs in one wave
@@ -1239,11 +1450,11 @@ bool one_wave(const dim3& g) { return (long long)g.x * g.y * g.z <= 2LL * device
 
 template <bool MRT, int SPLIT>
 cudaError_t launch_march2(const cudaLaunchConfig_t& cfg, const KConst<float>& sp, const float* fi, const float* F,
-                          float* fo, float* Co, int* flag, const SplitOut& so, int ychunk, int early) {
+                          float* fo, float* Co, int* flag, const SplitOut& so, int ychunk, int early, double* mpart) {
   static std::atomic<unsigned long long> attr{0};
   if (const cudaError_t e = smem_attr_once(attr, collide_stream_march2_kernel<MRT, SPLIT>, PIPE_SMEM); e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, collide_stream_march2_kernel<MRT, SPLIT>, sp, fi, F, fo, Co, flag, so, ychunk,
-                            early);
+                            early, mpart);
 }
 
 // z chunks of the 3-D march over `cols` tile columns: the count that maximises the wave
@@ -1274,16 +1485,25 @@ int ychunk_for(long long tiles, int by) {
   return static_cast<int>(std::max<long long>(1, std::min<long long>(c, by)));
 }
 
+// which operand split of the new C the collide-stream kernel writes (write_split codes)
+int cs_split_code(const lbm_s* h) {
+  if (h->tc == nullptr) return 0;
+  if (!bf16_parts(h->prm.precision)) return 2;
+  return h->prm.precision == LBM_FP32_BF16SPLIT6 ? 3 : 1;
+}
+
 template <typename real, int D, bool MRT>
-cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s) {
+cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s, int tk) {
   const KConst<real> sp = make_const<real>(h->sp);
   SplitOut so{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
-  const int split = (h->tc == nullptr) ? 0 : (bf16_parts(h->prm.precision) ? 1 : 2);
+  so.lo2 = h->dev.Cl2;
+  const int split = cs_split_code(h);
   const real* fi = static_cast<const real*>(f_in);
   const real* F = static_cast<const real*>(h->dev.F);
   real* fo = static_cast<real*>(f_out);
   real* Co = static_cast<real*>(C_out);
   int* flag = h->dev.flag;
+  double* mp = h->cs_part;
   const int bx = (sp.n[0] + TX - 1) / TX, by = (sp.n[1] + TY - 1) / TY;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(TX, TY + HALO_WARPS);
@@ -1293,30 +1513,47 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
   at[0].val.programmaticStreamSerializationAllowed = h->pdl ? 1 : 0;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  if (h->fld.on) {
+    // coefficients per node: the plain march with the per-node collision (2-D: one plane)
+    const int nz = (D == 2) ? 1 : (h->cs_chunk > 0 ? std::min(h->cs_chunk, sp.n[2]) : z_chunks((long long)bx * by, sp.n[2]));
+    cfg.gridDim = dim3(bx, by, nz);
+    h->cs_nparts = bx * by * nz;
+    const int early = one_wave(cfg.gridDim) ? 1 : 0;
+    const FieldPtrs<real> fp{static_cast<const real*>(h->fld.coll), static_cast<const real*>(h->fld.advw),
+                             static_cast<const real*>(h->fld.g),    static_cast<real*>(h->fld.G),
+                             static_cast<const real*>(h->fld.src),  static_cast<const real*>(h->fld.cw),
+                             h->fld.tf ? h->fld.tf + 2 * tk : nullptr};
+    return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 0, true>, sp, fi, F, fo, Co, flag, so,
+                              nz, early, mp, fp);
+  }
   if constexpr (D == 2 && sizeof(real) == 4) {
     // tile rows per block: about one wave of two blocks per SM, unless tuned
     const int ychunk = h->cs_chunk > 0 ? std::min(h->cs_chunk, by) : ychunk_for((long long)bx * by, by);
     cfg.gridDim = dim3(bx, (by + ychunk - 1) / ychunk, 1);
+    h->cs_nparts = static_cast<int>(cfg.gridDim.x * cfg.gridDim.y);
     const int early = one_wave(cfg.gridDim) ? 1 : 0;
     if (h->cs_plan) {
       const CsPlan* pl = static_cast<const CsPlan*>(h->cs_plan);
       const CUtensorMap& mf = pl->f[f_in == h->dev.f[0] ? 0 : 1];
       cfg.dynamicSmemBytes = tma2_smem(h->sp.ksum);
-      if (split == 0) return launch_tma2<MRT, 0>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
-      if (split == 1) return launch_tma2<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
+      if (split == 0) return launch_tma2<MRT, 0>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early, mp);
+      if (split == 1) return launch_tma2<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early, mp);
+      if (split == 3) return launch_tma2<MRT, 3>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early, mp);
       so.thi[0] = static_cast<float*>(h->tc->ct_hi[1]);  // the y operand of the tf32 operator
       so.tlo[0] = static_cast<float*>(h->tc->ct_lo[1]);
       so.tg1 = h->tc->tg[1];
       so.tpx = h->tc->tpx;
-      return launch_tma2<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early);
+      return launch_tma2<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early, mp);
     }
     cfg.dynamicSmemBytes = PIPE_SMEM;
-    if (split == 0) return launch_march2<MRT, 0>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
-    if (split == 1) return launch_march2<MRT, 1>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
-    return launch_march2<MRT, 2>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early);
+    if (split == 0) return launch_march2<MRT, 0>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early, mp);
+    if (split == 1) return launch_march2<MRT, 1>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early, mp);
+    if (split == 3) return launch_march2<MRT, 3>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early, mp);
+    return launch_march2<MRT, 2>(cfg, sp, fi, F, fo, Co, flag, so, ychunk, early, mp);
   }
   const int nz = h->cs_chunk > 0 ? std::min(h->cs_chunk, sp.n[2]) : z_chunks((long long)bx * by, sp.n[2]);
   cfg.gridDim = dim3(bx, by, nz);
+  h->cs_nparts = bx * by * nz;
   const int early = one_wave(cfg.gridDim) ? 1 : 0;
   if constexpr (D == 3 && sizeof(real) == 4) {
     if (h->cs_plan) {
@@ -1324,25 +1561,29 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
       const CsPlan* pl = static_cast<const CsPlan*>(h->cs_plan);
       const CUtensorMap& mf = pl->f[f_in == h->dev.f[0] ? 0 : 1];
       cfg.dynamicSmemBytes = TMA_SMEM;
-      if (split == 0) return launch_tma3<MRT, 0>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early);
-      if (split == 1) return launch_tma3<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early);
+      if (split == 0) return launch_tma3<MRT, 0>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early, mp);
+      if (split == 1) return launch_tma3<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early, mp);
+      if (split == 3) return launch_tma3<MRT, 3>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early, mp);
       for (int a = 0; a < 2; ++a) {  // the y and z operands of the tf32 operator
         so.thi[a] = static_cast<float*>(h->tc->ct_hi[a + 1]);
         so.tlo[a] = static_cast<float*>(h->tc->ct_lo[a + 1]);
       }
       so.tg1 = h->tc->tg[1];
       so.tpx = h->tc->tpx;
-      return launch_tma3<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early);
+      return launch_tma3<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early, mp);
     }
   }
   if (split == 0)
     return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 0>, sp, fi, F, fo, Co, flag, so, nz,
-                              early);
+                              early, mp, FieldPtrs<real>{});
   if (split == 1)
     return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 1>, sp, fi, F, fo, Co, flag, so, nz,
-                              early);
+                              early, mp, FieldPtrs<real>{});
+  if (split == 3)
+    return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 3>, sp, fi, F, fo, Co, flag, so, nz,
+                              early, mp, FieldPtrs<real>{});
   return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 2>, sp, fi, F, fo, Co, flag, so, nz,
-                            early);
+                            early, mp, FieldPtrs<real>{});
 }
 
 int grid_for(long long n) {
@@ -1360,18 +1601,19 @@ bool cs_writes_T(const lbm_s* h) {
          h->prm.precision == LBM_FP32_TF32SPLIT;
 }
 
-cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s) {
+cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s,
+                                  int tk) {
   const bool mrt = h->prm.collision == LBM_MRT;
   if (h->elem == 8) {
-    if (h->d == 2) return mrt ? launch_cs<double, 2, true>(h, f_in, f_out, C_out, s)
-                              : launch_cs<double, 2, false>(h, f_in, f_out, C_out, s);
-    return mrt ? launch_cs<double, 3, true>(h, f_in, f_out, C_out, s)
-               : launch_cs<double, 3, false>(h, f_in, f_out, C_out, s);
+    if (h->d == 2) return mrt ? launch_cs<double, 2, true>(h, f_in, f_out, C_out, s, tk)
+                              : launch_cs<double, 2, false>(h, f_in, f_out, C_out, s, tk);
+    return mrt ? launch_cs<double, 3, true>(h, f_in, f_out, C_out, s, tk)
+               : launch_cs<double, 3, false>(h, f_in, f_out, C_out, s, tk);
   }
-  if (h->d == 2) return mrt ? launch_cs<float, 2, true>(h, f_in, f_out, C_out, s)
-                            : launch_cs<float, 2, false>(h, f_in, f_out, C_out, s);
-  return mrt ? launch_cs<float, 3, true>(h, f_in, f_out, C_out, s)
-             : launch_cs<float, 3, false>(h, f_in, f_out, C_out, s);
+  if (h->d == 2) return mrt ? launch_cs<float, 2, true>(h, f_in, f_out, C_out, s, tk)
+                            : launch_cs<float, 2, false>(h, f_in, f_out, C_out, s, tk);
+  return mrt ? launch_cs<float, 3, true>(h, f_in, f_out, C_out, s, tk)
+             : launch_cs<float, 3, false>(h, f_in, f_out, C_out, s, tk);
 }
 
 constexpr int kBatchYChunk = 16;  // tile rows per block (the autotuner's usual choice on mixed batches)
@@ -1490,7 +1732,7 @@ int cs_batch_prepare(lbm_s* b) {
   std::vector<int> start(P);
   int total = 0;
   for (int i = 0; i < P; ++i) {
-    const lbm_s* h = b->subs[i];
+    lbm_s* h = b->subs[i];
     if (h->elem != 4) return LBM_EINVAL;
     BatchCS& e = tab[i];
     e.k = make_const<float>(h->sp);
@@ -1499,14 +1741,17 @@ int cs_batch_prepare(lbm_s* b) {
     e.F = static_cast<const float*>(h->dev.F);
     e.C = static_cast<float*>(h->dev.C);
     e.so = SplitOut{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
+    e.so.lo2 = h->dev.Cl2;
     e.flag = h->dev.flag;
+    e.mpart = h->cs_part;
     e.tma = (h->d == 2 && h->sp.n[0] % 4 == 0 && encode_2d_maps(h, e.mf, &e.mF)) ? 1 : 0;
     e.bx = (h->sp.n[0] + TX - 1) / TX;
     e.by = (h->sp.n[1] + TY - 1) / TY;
     // 2-D: tile rows per block (the pipelined y-march); 3-D: the whole z extent
     e.zchunk = (h->d == 2) ? std::min(e.by, b->cs_chunk > 0 ? b->cs_chunk : kBatchYChunk) : h->sp.n[2];
     start[i] = total;
-    total += e.bx * ((h->d == 2) ? (e.by + e.zchunk - 1) / e.zchunk : e.by);
+    h->cs_nparts = e.bx * ((h->d == 2) ? (e.by + e.zchunk - 1) / e.zchunk : e.by);
+    total += h->cs_nparts;
   }
   dev_free(b, b->batch_cs);
   dev_free(b, b->batch_cs_start);
@@ -1524,28 +1769,30 @@ int cs_batch_prepare(lbm_s* b) {
 cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t s) {
   const lbm_s* h0 = b->subs[0];
   const bool mrt = h0->prm.collision == LBM_MRT;
-  const int split = (h0->tc == nullptr) ? 0 : 1;
+  const int split = cs_split_code(h0);  // 0, 1 or 3 (batches have no tf32 form)
   const BatchCS* tab = static_cast<const BatchCS*>(b->batch_cs);
   const int P = static_cast<int>(b->subs.size());
   dim3 block(TX, TY + HALO_WARPS);
   const int g = b->batch_cs_blocks;
   const int smem = (h0->d == 2) ? BATCH2_SMEM : 0;
   if (h0->d == 2) {
-    static std::atomic<unsigned long long> attr[2][2] = {{{0}, {0}}, {{0}, {0}}};
+    static std::atomic<unsigned long long> attr[2][4] = {{{0}, {0}, {0}, {0}}, {{0}, {0}, {0}, {0}}};
     cudaError_t e;
-    if (mrt) e = split ? smem_attr_once(attr[1][1], collide_stream_batch_kernel<2, true, 1>, BATCH2_SMEM)
-                       : smem_attr_once(attr[1][0], collide_stream_batch_kernel<2, true, 0>, BATCH2_SMEM);
-    else e = split ? smem_attr_once(attr[0][1], collide_stream_batch_kernel<2, false, 1>, BATCH2_SMEM)
-                   : smem_attr_once(attr[0][0], collide_stream_batch_kernel<2, false, 0>, BATCH2_SMEM);
+    if (mrt) e = split == 3 ? smem_attr_once(attr[1][3], collide_stream_batch_kernel<2, true, 3>, BATCH2_SMEM)
+                 : split    ? smem_attr_once(attr[1][1], collide_stream_batch_kernel<2, true, 1>, BATCH2_SMEM)
+                            : smem_attr_once(attr[1][0], collide_stream_batch_kernel<2, true, 0>, BATCH2_SMEM);
+    else e = split == 3 ? smem_attr_once(attr[0][3], collide_stream_batch_kernel<2, false, 3>, BATCH2_SMEM)
+             : split    ? smem_attr_once(attr[0][1], collide_stream_batch_kernel<2, false, 1>, BATCH2_SMEM)
+                        : smem_attr_once(attr[0][0], collide_stream_batch_kernel<2, false, 0>, BATCH2_SMEM);
     if (e != cudaSuccess) return e;
   }
 #define LBM_CSB(D_, M_, S_) collide_stream_batch_kernel<D_, M_, S_><<<g, block, smem, s>>>(tab, b->batch_cs_start, P, parity)
   if (h0->d == 2) {
-    if (mrt) { if (split) LBM_CSB(2, true, 1); else LBM_CSB(2, true, 0); }
-    else { if (split) LBM_CSB(2, false, 1); else LBM_CSB(2, false, 0); }
+    if (mrt) { if (split == 3) LBM_CSB(2, true, 3); else if (split) LBM_CSB(2, true, 1); else LBM_CSB(2, true, 0); }
+    else { if (split == 3) LBM_CSB(2, false, 3); else if (split) LBM_CSB(2, false, 1); else LBM_CSB(2, false, 0); }
   } else {
-    if (mrt) { if (split) LBM_CSB(3, true, 1); else LBM_CSB(3, true, 0); }
-    else { if (split) LBM_CSB(3, false, 1); else LBM_CSB(3, false, 0); }
+    if (mrt) { if (split == 3) LBM_CSB(3, true, 3); else if (split) LBM_CSB(3, true, 1); else LBM_CSB(3, true, 0); }
+    else { if (split == 3) LBM_CSB(3, false, 3); else if (split) LBM_CSB(3, false, 1); else LBM_CSB(3, false, 0); }
   }
 #undef LBM_CSB
   return cudaGetLastError();
@@ -1553,17 +1800,29 @@ cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t
 
 cudaError_t launch_init_equilibrium(const lbm_s* h, void* f, cudaStream_t s) {
   const int g = grid_for(h->sp.nodes);
+  const void* aw = h->fld.on ? h->fld.advw : nullptr;
   if (h->elem == 8) {
     if (h->d == 2)
-      init_equilibrium_kernel<double, 2><<<g, 256, 0, s>>>(make_const<double>(h->sp), (const double*)h->dev.C, (const double*)h->dev.F, (double*)f);
+      init_equilibrium_kernel<double, 2><<<g, 256, 0, s>>>(make_const<double>(h->sp), (const double*)h->dev.C, (const double*)h->dev.F, (double*)f, (const double*)aw);
     else
-      init_equilibrium_kernel<double, 3><<<g, 256, 0, s>>>(make_const<double>(h->sp), (const double*)h->dev.C, (const double*)h->dev.F, (double*)f);
+      init_equilibrium_kernel<double, 3><<<g, 256, 0, s>>>(make_const<double>(h->sp), (const double*)h->dev.C, (const double*)h->dev.F, (double*)f, (const double*)aw);
   } else {
     if (h->d == 2)
-      init_equilibrium_kernel<float, 2><<<g, 256, 0, s>>>(make_const<float>(h->sp), (const float*)h->dev.C, (const float*)h->dev.F, (float*)f);
+      init_equilibrium_kernel<float, 2><<<g, 256, 0, s>>>(make_const<float>(h->sp), (const float*)h->dev.C, (const float*)h->dev.F, (float*)f, (const float*)aw);
     else
-      init_equilibrium_kernel<float, 3><<<g, 256, 0, s>>>(make_const<float>(h->sp), (const float*)h->dev.C, (const float*)h->dev.F, (float*)f);
+      init_equilibrium_kernel<float, 3><<<g, 256, 0, s>>>(make_const<float>(h->sp), (const float*)h->dev.C, (const float*)h->dev.F, (float*)f, (const float*)aw);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_fields(const lbm_s* h, cudaStream_t s) {
+  const int g = grid_for(h->sp.nodes);
+  if (h->elem == 8)
+    scale_fields_kernel<double><<<g, 256, 0, s>>>(h->sp.nodes, h->d, (const double*)h->dev.C, (const double*)h->fld.g,
+                                                  (double*)h->fld.G);
+  else
+    scale_fields_kernel<float><<<g, 256, 0, s>>>(h->sp.nodes, h->d, (const float*)h->dev.C, (const float*)h->fld.g,
+                                                 (float*)h->fld.G);
   return cudaGetLastError();
 }
 

@@ -166,9 +166,8 @@ void add_axis(GemmPlan& P, int BM, int BN, int M, int N, int K, int batch, const
   P.total += (long long)X.tm * X.tn * batch * P.ks;
 }
 
-// transpose = false: F_mu = K_mu applied along mu to C (one input for every axis);
-// transpose = true:  F_mu = K_mu^T applied along mu to C_mu (C holds one field per axis,
-// field mu at C + mu * cstride)
+// transpose = false: F_mu = K_mu applied along mu to C_mu, transpose = true: K_mu^T; the
+// input of axis mu is the field at C + mu * cstride (cstride = 0: one input for every axis)
 template <typename real, int BM, int BN>
 GemmPlan make_plan(const lbm_s* h, const real* C, real* F, bool transpose, long long cstride, int ks = 1,
                    long long pstride = 0) {
@@ -176,7 +175,6 @@ GemmPlan make_plan(const lbm_s* h, const real* C, real* F, bool transpose, long 
   const long long nodes = h->sp.nodes;
   const real* K = static_cast<const real*>(transpose ? h->dev.KT : h->dev.K);
   const real* KT = static_cast<const real*>(transpose ? h->dev.K : h->dev.KT);
-  if (!transpose) cstride = 0;
   GemmPlan P{};
   P.ks = ks;
   P.pstride = pstride;
@@ -269,8 +267,12 @@ cudaError_t launch_frac_simt_T(const lbm_s* h, const void* in, long long in_stri
 }
 
 cudaError_t launch_frac_simt(const lbm_s* h, const void* C, void* F, cudaStream_t s) {
-  if (h->elem == 8) return frac_all_axes<double>(h, static_cast<const double*>(C), static_cast<double*>(F), s);
-  return frac_all_axes<float>(h, static_cast<const float*>(C), static_cast<float*>(F), s);
+  // spatially varying g: the input along mu is G_mu = g_mu(x) C (Eq. Fg), one field per axis
+  const long long cs = h->fld.on ? h->sp.nodes : 0;
+  if (h->fld.on) C = h->fld.G;
+  if (h->elem == 8)
+    return frac_all_axes<double>(h, static_cast<const double*>(C), static_cast<double*>(F), s, false, cs);
+  return frac_all_axes<float>(h, static_cast<const float*>(C), static_cast<float*>(F), s, false, cs);
 }
 
 }  // namespace lbm

@@ -65,7 +65,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   const TcAxis ax = P.ax[mu];
   const int kb0 = rank * ax.kblocks / ks, kb1 = (rank + 1) * ax.kblocks / ks;
   const int nkb = kb1 - kb0;
-  const int nreg = acc_regions(nkb, BN);  // TMEM accumulators, nreg * BN columns
+  const int nreg = acc_regions(nkb * ksteps<E>(), BN);  // TMEM accumulators, nreg * BN columns
 
   auto issue = [&](int i) {
     const int s = i % G::STAGES;
@@ -120,8 +120,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
       const int s = i % G::STAGES;
       if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
       tc_fence_after();
-      mma_stage<E, BN, KP>(tmem + (uint32_t)((i % nreg) * BN), smem_u32(smem + (size_t)s * G::STAGE), amode,
-                           i < nreg);
+      mma_stage<E, BN, KP>(tmem, i * ksteps<E>(), nreg, smem_u32(smem + (size_t)s * G::STAGE), amode);
       mma_commit(&empty[s]);
     }
     mma_commit(done);
@@ -218,20 +217,30 @@ frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
 // MMAs into one of two TMEM accumulators (the i-th tile of the CTA into buffer i & 1),
 // and warps 2-5 drain the other accumulator (tcgen05.ld, 32 columns at a time, through a
 // double-buffered shared chunk and a TMA store), so a tile's epilogue overlaps the next
-// tile's loads and MMAs.  Every wait is bounded as in the per-tile kernel; on a timeout
+// tile's loads and MMAs.  With 128-column tiles each accumulator buffer has two regions:
+// consecutive k-blocks alternate between them and the epilogue adds the two in FP32 (as
+// the per-tile kernel's regions: shorter accumulation chains, smaller rounding error of
+// the split forms).  Every wait is bounded as in the per-tile kernel; on a timeout
 // the CTA stops issuing, waits (bounded) for its copies and MMAs in flight, releases
 // TMEM and returns with bit 2 of the error flag set.
 constexpr int PBN = 128;
 constexpr int kPersistThreads = 192;
 
-// BN = 128 (three ring stages) or 256 (two; the double accumulator then fills TMEM)
-template <int E, int BN = PBN>
+// BN = 128 (three ring stages; two with the weights in three parts) or 256 (two; the
+// double accumulator then fills TMEM); KP = weight parts (2, or 3 for the five-product
+// bf16 form, BN = 128 only)
+template <int E, int BN = PBN, int KP = 2>
 struct PCfg {
-  using G = Cfg<E, BN>;
-  static constexpr int STAGES = BN == 128 ? 3 : 2;
+  using G = Cfg<E, BN, 1, KP>;
+  static constexpr int STAGES = (BN == 128 && KP == 2) ? 3 : 2;
+  static constexpr int NREG = (2 * 2 * BN <= 512) ? 2 : 1;  // accumulator regions per buffer
+  static_assert(NREG <= ksteps<E>(), "every region is written by a tile's first k-block");
+  static constexpr int TMEM_COLS = 2 * NREG * BN;
   static constexpr uint32_t CHUNK = 32 * BM * 4;  // 32 output rows x 128 x (FP32)
   static constexpr size_t RING = (size_t)STAGES * G::STAGE;
   static constexpr size_t SMEM = RING + 2 * CHUNK + 1024 /*align*/ + 256 /*barriers*/;
+  static_assert(SMEM <= 232448, "persistent operator exceeds the shared memory of one CTA");
+  static_assert(KP == 2 || BN == 128, "three weight parts: 128-column tiles only");
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -241,11 +250,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // Locate(t, maps, prm, cid): the problem and local tile index of global tile t
-template <int E, int BN, class Locate>
+template <int E, int BN, int KP, class Locate>
 __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, int* flag, uint8_t* smem_raw) {
-  using C = PCfg<E, BN>;
+  using C = PCfg<E, BN, KP>;
   using G = typename C::G;
   constexpr int STAGES = C::STAGES;
+  constexpr int NREG = C::NREG;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* stage_out = reinterpret_cast<float*>(smem + C::RING);  // [2][32][128]
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::RING + 2 * C::CHUNK);
@@ -273,7 +283,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * BN)
+                 "r"(C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -302,8 +312,8 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
           ok = false;
           break;
         }
-        mbar_expect_tx(&full[s], G::STAGE);
-        load_stage<E, BN>(*maps, tl, kb * G::BK, smem + (size_t)s * G::STAGE, &full[s]);
+        mbar_expect_tx(&full[s], G::tx_bytes(tl.mu));
+        load_stage<E, BN, KP>(*maps, tl, kb * G::BK, smem + (size_t)s * G::STAGE, &full[s]);
       }
     }
     // every issued copy has landed before the CTA may leave (bounded)
@@ -322,7 +332,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
       const int b = i & 1;
       if (i >= 2 && !mbar_wait(&tempty[b], ((i >> 1) - 1) & 1, flag)) break;
       tc_fence_after();
-      const uint32_t d = tmem + b * BN;
+      const uint32_t d = tmem + b * NREG * BN;
       const int amode = a_mode<E>(tl.mu);
       for (int kb = 0; kb < nkb; ++kb, ++r) {
         const int s = r % STAGES;
@@ -331,7 +341,8 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
           break;
         }
         tc_fence_after();
-        mma_stage<E, BN>(d, smem_u32(smem + (size_t)s * G::STAGE), amode, kb == 0);
+        // k-step c = kb * ksteps + kk accumulates into region c % NREG of this buffer
+        mma_stage<E, BN, KP>(d, kb * ksteps<E>(), NREG, smem_u32(smem + (size_t)s * G::STAGE), amode);
         mma_commit(&empty[s]);
       }
       if (ok) mma_commit(&tfull[b]);
@@ -358,9 +369,18 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
       float* F = P->F + (long long)tl.mu * nodes;
       const int n0 = P->n0, n1 = P->n1;
       const int lim = (tl.mu == 0) ? n1 : P->ax[tl.mu].side;  // output rows that exist
+      // regions written by this tile (every one: a k-block has ksteps >= NREG k-steps)
+      const int nreg = NREG;
       for (int c0 = 0; c0 < BN; c0 += 32, ++chunk) {
         float v[32];
-        tmem_ld32(tmem + b * BN + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
+        const uint32_t abase = tmem + b * NREG * BN + (static_cast<uint32_t>(q * 32) << 16) + c0;
+        tmem_ld32(abase, v);
+        for (int rg = 1; rg < nreg; ++rg) {  // the regions, added in k order
+          float w[32];
+          tmem_ld32(abase + rg * BN, w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
         if (c0 + 32 >= BN) {
           // the accumulator is drained: hand it back to the MMA warp
           tc_fence_before();
@@ -420,7 +440,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
     if (threadIdx.x == 32) mbar_wait(drain, 0, flag);
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
   }
 }
 
@@ -452,19 +472,19 @@ struct LocateBatch {
   }
 };
 
-template <int E, int BN>
+template <int E, int BN, int KP>
 __global__ void __launch_bounds__(kPersistThreads, 1)
 frac_tc_persist_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P) {
   extern __shared__ uint8_t smem_raw[];
-  persist_body<E, BN>(LocateOne{&maps, &P}, P.total_tiles, P.flag, smem_raw);
+  persist_body<E, BN, KP>(LocateOne{&maps, &P}, P.total_tiles, P.flag, smem_raw);
 }
 
-template <int E>
+template <int E, int KP>
 __global__ void __launch_bounds__(kPersistThreads, 1)
 frac_tc_persist_batch_kernel(const TcMaps* __restrict__ maps, const TcParams* __restrict__ prm,
                              const int* __restrict__ start, int nprob, int ntiles, int* flag) {
   extern __shared__ uint8_t smem_raw[];
-  persist_body<E, PBN>(LocateBatch{maps, prm, start, nprob}, ntiles, flag, smem_raw);
+  persist_body<E, PBN, KP>(LocateBatch{maps, prm, start, nprob}, ntiles, flag, smem_raw);
 }
 
 // ---------------------------------------------------------------------------- splits
@@ -476,8 +496,8 @@ __device__ __forceinline__ float tf32_rna(float x) {
 }
 
 template <int E>
-__global__ void split_C_kernel(const float* __restrict__ C, void* __restrict__ hi, void* __restrict__ lo, int n0,
-                               int n1, int n2, int ldp) {
+__global__ void split_C_kernel(const float* __restrict__ C, void* __restrict__ hi, void* __restrict__ lo,
+                               void* __restrict__ lo2, int n0, int n1, int n2, int ldp) {
   const long long total = (long long)n0 * n1 * n2;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -486,9 +506,13 @@ __global__ void split_C_kernel(const float* __restrict__ C, void* __restrict__ h
     const long long o = row * ldp + x;
     const float c = C[i];
     if (E == 2) {
+      // each part the bf16 rounding of what the previous ones left (exact FP32 residuals)
       const __nv_bfloat16 h = __float2bfloat16_rn(c);
+      const float r1 = c - __bfloat162float(h);
+      const __nv_bfloat16 l = __float2bfloat16_rn(r1);
       static_cast<__nv_bfloat16*>(hi)[o] = h;
-      static_cast<__nv_bfloat16*>(lo)[o] = __float2bfloat16_rn(c - __bfloat162float(h));
+      static_cast<__nv_bfloat16*>(lo)[o] = l;
+      if (lo2) static_cast<__nv_bfloat16*>(lo2)[o] = __float2bfloat16_rn(r1 - __bfloat162float(l));
     } else {
       const float h = tf32_rna(c);
       static_cast<float*>(hi)[o] = h;
@@ -604,21 +628,23 @@ cudaError_t launch_bn(const TcPlan* p, cudaStream_t s) {
 }
 
 
-template <int E, int BN>
+template <int E, int BN, int KP = 2>
 cudaError_t launch_persist(const TcPlan* p, cudaStream_t s) {
   static std::atomic<unsigned long long> attr{0};
-  if (const cudaError_t e = smem_attr_once(attr, frac_tc_persist_kernel<E, BN>, (int)PCfg<E, BN>::SMEM); e != cudaSuccess) return e;
+  if (const cudaError_t e = smem_attr_once(attr, frac_tc_persist_kernel<E, BN, KP>, (int)PCfg<E, BN, KP>::SMEM);
+      e != cudaSuccess)
+    return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::min(p->prm.total_tiles, device_sms()), 1, 1);  // one CTA per SM
   cfg.blockDim = dim3(kPersistThreads, 1, 1);
-  cfg.dynamicSmemBytes = PCfg<E, BN>::SMEM;
+  cfg.dynamicSmemBytes = PCfg<E, BN, KP>::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = p->pdl ? 1 : 0;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, frac_tc_persist_kernel<E, BN>, p->maps, p->prm);
+  return cudaLaunchKernelEx(&cfg, frac_tc_persist_kernel<E, BN, KP>, p->maps, p->prm);
 }
 
 }  // namespace
@@ -630,7 +656,8 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   h->tc = p;
   const int E = bf16_parts(h->prm.precision) ? 2 : 4;
   p->elem = E;
-  p->kparts = (h->prm.precision == LBM_FP32_BF16SPLIT5) ? 3 : 2;
+  p->kparts = (h->prm.precision == LBM_FP32_BF16SPLIT5 || h->prm.precision == LBM_FP32_BF16SPLIT6) ? 3 : 2;
+  p->cparts = (h->prm.precision == LBM_FP32_BF16SPLIT6) ? 3 : 2;
   // tf32 parts are fed K-major on every axis: the y and z axes read copies of the C split
   // regrouped along y (resp. z), written each step by the collide-stream kernel (TMA-fed
   // marches) or by split_T_kernel.
@@ -645,6 +672,10 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   if (dev_alloc(h, (void**)&h->dev.Clo, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
   cudaMemset(h->dev.Chi, 0, split_elems * E);
   cudaMemset(h->dev.Clo, 0, split_elems * E);
+  if (p->cparts == 3) {
+    if (dev_alloc(h, (void**)&h->dev.Cl2, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
+    cudaMemset(h->dev.Cl2, 0, split_elems * E);
+  }
   if (E == 4) {
     p->tpx = (n[0] + 15) / 16 * 16;
     for (int mu = 1; mu < h->d; ++mu) {
@@ -724,7 +755,7 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
     bn = force_bn;
     ks = std::max(1, force_ks);
     persist = (force_bn == PBN && ks == 1);
-  } else if (p->kparts == 2 && tc_count_tiles(h, PBN) >= 2 * kSMs) {
+  } else if (tc_count_tiles(h, PBN) >= 2 * kSMs) {
     persist = true;
     bn = PBN;
     ks = 1;
@@ -759,8 +790,8 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
   if (!(bn == 64 || bn == 128 || bn == 256) || !(ks == 1 || ks == 2 || ks == 4 || ks == 8)) return LBM_EINVAL;
   if ((persist && ((bn != PBN && bn != 256) || ks != 1)) || (bn == 256 && ks != 1) || ks > tc_kbmin(h))
     return LBM_EINVAL;
-  // the five-product form keeps a third weight part per stage: per-tile kernel, 64 or 128 columns
-  if (p->kparts == 3 && (persist || bn == 256)) return LBM_EINVAL;
+  // the five- and six-product forms keep third parts per stage: 64 or 128 columns
+  if (p->kparts == 3 && bn == 256) return LBM_EINVAL;
   const int E = p->elem;
   const int n[3] = {h->sp.n[0], h->sp.n[1], h->sp.n[2]};
   const int ldp = p->ldp;
@@ -821,6 +852,7 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
     } else {
       if (!encode(&p->maps.c_hi[mu], E, 3, h->dev.Chi, cdims, cstr, box)) return LBM_ECUDA;
       if (!encode(&p->maps.c_lo[mu], E, 3, h->dev.Clo, cdims, cstr, box)) return LBM_ECUDA;
+      if (p->cparts == 3 && !encode(&p->maps.c_l2[mu], E, 3, h->dev.Cl2, cdims, cstr, box)) return LBM_ECUDA;
     }
     const cuuint64_t kdims[2] = {(cuuint64_t)n[mu], (cuuint64_t)n[mu]};
     const cuuint64_t kstr[1] = {(cuuint64_t)ldk[mu] * E};
@@ -892,7 +924,9 @@ int tc_batch_prepare(lbm_s* b) {
   int total = 0;
   for (int i = 0; i < P; ++i) {
     const TcPlan* t = b->subs[i]->tc;
-    if (!t || !t->persist || t->prm.ksplit != 1 || t->elem != 2) return LBM_EINVAL;
+    if (!t || !t->persist || t->prm.ksplit != 1 || t->elem != 2 || t->kparts != b->subs[0]->tc->kparts ||
+        t->cparts != b->subs[0]->tc->cparts)
+      return LBM_EINVAL;
     maps[i] = t->maps;
     prm[i] = t->prm;
     start[i] = total;
@@ -909,14 +943,23 @@ int tc_batch_prepare(lbm_s* b) {
   return LBM_OK;
 }
 
-cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s) {
+template <int KP>
+cudaError_t launch_batch_kp(const lbm_s* b, cudaStream_t s) {
   static std::atomic<unsigned long long> attr{0};
-  if (const cudaError_t e = smem_attr_once(attr, frac_tc_persist_batch_kernel<2>, (int)PCfg<2>::SMEM); e != cudaSuccess) return e;
+  if (const cudaError_t e = smem_attr_once(attr, frac_tc_persist_batch_kernel<2, KP>, (int)PCfg<2, PBN, KP>::SMEM);
+      e != cudaSuccess)
+    return e;
   const int grid = std::min(b->batch_tc_blocks, device_sms());  // one CTA per SM
-  frac_tc_persist_batch_kernel<2><<<grid, kPersistThreads, PCfg<2>::SMEM, s>>>(
+  frac_tc_persist_batch_kernel<2, KP><<<grid, kPersistThreads, PCfg<2, PBN, KP>::SMEM, s>>>(
       static_cast<const TcMaps*>(b->batch_tc_maps), static_cast<const TcParams*>(b->batch_tc_prm), b->batch_tc_start,
       static_cast<int>(b->subs.size()), b->batch_tc_blocks, b->dev.flag);
   return cudaGetLastError();
+}
+
+cudaError_t launch_frac_tc_batch(const lbm_s* b, cudaStream_t s) {
+  const TcPlan* t = b->subs[0]->tc;
+  if (t->cparts == 3) return launch_batch_kp<6>(b, s);
+  return t->kparts == 3 ? launch_batch_kp<3>(b, s) : launch_batch_kp<2>(b, s);
 }
 
 int tc_split_pitch(const lbm_s* h) { return h->tc ? h->tc->ldp : 0; }
@@ -961,8 +1004,13 @@ void tc_set_pdl(lbm_s* h, bool on) {
 cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s) {
   const TcPlan* p = h->tc;
   if (!p) return cudaErrorNotSupported;
-  if (p->kparts == 3) {  // five-product bf16 form: per-tile kernel, 64 or 128 columns
-    if (p->persist || p->elem != 2 || p->bn == 256) return cudaErrorInvalidConfiguration;
+  if (p->kparts == 3) {  // five- and six-product bf16 forms: 64 or 128 columns, per tile or persistent (128)
+    if (p->elem != 2 || p->bn == 256 || (p->persist && p->bn != PBN)) return cudaErrorInvalidConfiguration;
+    if (p->cparts == 3) {
+      if (p->persist) return launch_persist<2, PBN, 6>(p, s);
+      return (p->bn == 64) ? launch_bn<2, 64, 6>(p, s) : launch_bn<2, 128, 6>(p, s);
+    }
+    if (p->persist) return launch_persist<2, PBN, 3>(p, s);
     return (p->bn == 64) ? launch_bn<2, 64, 3>(p, s) : launch_bn<2, 128, 3>(p, s);
   }
   if (p->persist) {
@@ -1001,11 +1049,12 @@ cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s) {
   const long long cap = 16LL * device_sms();
   if (b > cap) b = cap;
   if (p->elem == 2)
-    split_C_kernel<2><<<(int)b, 256, 0, s>>>(static_cast<const float*>(h->dev.C), h->dev.Chi, h->dev.Clo, h->sp.n[0],
-                                             h->sp.n[1], h->sp.n[2], p->ldp);
+    split_C_kernel<2><<<(int)b, 256, 0, s>>>(static_cast<const float*>(h->dev.C), h->dev.Chi, h->dev.Clo,
+                                             p->cparts == 3 ? h->dev.Cl2 : nullptr, h->sp.n[0], h->sp.n[1],
+                                             h->sp.n[2], p->ldp);
   else
-    split_C_kernel<4><<<(int)b, 256, 0, s>>>(static_cast<const float*>(h->dev.C), h->dev.Chi, h->dev.Clo, h->sp.n[0],
-                                             h->sp.n[1], h->sp.n[2], p->ldp);
+    split_C_kernel<4><<<(int)b, 256, 0, s>>>(static_cast<const float*>(h->dev.C), h->dev.Chi, h->dev.Clo, nullptr,
+                                             h->sp.n[0], h->sp.n[1], h->sp.n[2], p->ldp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_split_T(h, s);

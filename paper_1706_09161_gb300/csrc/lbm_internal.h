@@ -27,6 +27,30 @@ struct StepParams {
   // F_mu(node) = sum_{s < ksum} F[s * pstride + mu * nodes + node], added in order of s
   int ksum;
   long long pstride;
+  double sfree[3];           // MRT rates of the free moments (Eq. MatrixS)
+};
+
+// Coefficients that vary from node to node (lbm_set_fields); device arrays in the working
+// precision, [k][node].  coll: BGK 1/lambda(x), MRT the symmetric flux-block rates
+// R(x) = lambdabar(x)^-1 (d(d+1)/2 entries); advw: (dt/dx) u_mu(x) w_i / e^2; g: g_mu(x);
+// G: g_mu(x) C, the operator's input along mu.
+struct FieldState {
+  bool on = false;     // the per-node kernel path runs (coefficients, source or wall values)
+  bool coeff = false;  // D, g or u vary (lbm_set_fields)
+  void* coll = nullptr;
+  void* advw = nullptr;
+  void* g = nullptr;
+  void* G = nullptr;
+  // the coefficient arrays last given to lbm_set_fields (empty: the constants)
+  std::vector<double> D_host, g_host, u_host;
+  // source S_c(x, t) = S(x) exp(src_rate t) and wall values C_w(x) exp(cw_rate t) (null: none /
+  // the constant C_wall), working precision [node]; tf: per-launch time factors [slot][2]
+  void* src = nullptr;
+  double src_rate = 0.0;
+  void* cw = nullptr;
+  double cw_rate = 0.0;
+  double* tf = nullptr;
+  int tf_slots = 0;
 };
 
 // Device-side buffers of one problem.
@@ -47,6 +71,7 @@ struct DeviceState {
   void* Kl2 = nullptr;               // [mu][side^2] third part of K (five-product bf16 form)
   void* Chi = nullptr;               // [node] hi part of C
   void* Clo = nullptr;               // [node] lo part of C
+  void* Cl2 = nullptr;               // [node] third part of C (six-product bf16 form)
 };
 
 }  // namespace lbm
@@ -65,6 +90,8 @@ struct lbm_s {
   int elem = 8;                        // bytes per real (8 FP64, 4 FP32 forms)
   lbm::StepParams sp;
   lbm::DeviceState dev;
+  lbm::FieldState fld;
+  long long t_steps = 0;               // steps since the last (re-)initialisation: t = t_steps dt
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int cur = 0;                         // index of the current population buffer
@@ -84,6 +111,15 @@ struct lbm_s {
   int fused_grid = 0;
   unsigned int* fused_bar = nullptr;   // grid-barrier counter
   int device = 0;
+  // FP64 block partials of the mass of the concentration each collide-stream launch writes
+  // (one per block of its grid: cs_nparts of them, at most cs_part_cap); mass_valid when the
+  // latest C came from a step (not from a re-initialisation); mass_limit > 0 turns a mass of
+  // larger magnitude (or a non-finite one) into LBM_ERR_UNSTABLE at the next synchronising call
+  double* cs_part = nullptr;
+  long long cs_part_cap = 0;
+  mutable int cs_nparts = 0;
+  bool mass_valid = false;
+  double mass_limit = 0.0;
   lbm::TcPlan* tc = nullptr;           // split-precision tensor-core operator, if used
   void* cs_plan = nullptr;             // TMA-fed 3-D collide-stream (tensor maps), if used
   // batch of independent problems: one sub-handle per problem (each owns its buffers)
@@ -136,9 +172,11 @@ cudaError_t launch_frac_tc(const lbm_s* h, cudaStream_t s);
 // fused equilibrium + collision + streaming + Dirichlet + new concentration; on the
 // tensor-core path it also writes the hi/lo split of the new concentration
 cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out, void* C_out,
-                                  cudaStream_t s);
-// f = feq(C, F)
+                                  cudaStream_t s, int tk = 0);
+// f = feq(C, F) (with u(x) when the coefficients vary)
 cudaError_t launch_init_equilibrium(const lbm_s* h, void* f, cudaStream_t s);
+// G_mu = g_mu(x) C (spatially varying coefficients only)
+cudaError_t launch_scale_fields(const lbm_s* h, cudaStream_t s);
 // C = sum_q f_q
 cudaError_t launch_moment(const lbm_s* h, const void* f, void* C, cudaStream_t s);
 // conversions between the FP64 staging buffer and the working precision
@@ -152,6 +190,10 @@ cudaError_t launch_sum_partials_out(const float* src, int k, long long stride, d
 cudaError_t launch_sum_partials(const float* src, int k, long long stride, float* dst, long long n, cudaStream_t s);
 // mass reduction: partials then final
 cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
+// mass of the latest step from the collide-stream kernel's block partials (one small pass,
+// fixed order) into dev.scalar; with limit > 0 a mass that is not within [-limit, limit]
+// sets the instability bit of the handle's flag
+cudaError_t launch_step_mass(const lbm_s* h, double limit, cudaStream_t s);
 // split C into hi/lo operands for the tensor-core path (tf32: also the regrouped copies)
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s);
 // tf32 only: the transposed copies of the split of the current C (no-op otherwise)
@@ -160,9 +202,9 @@ cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s);
 // transposed split itself (cs_writes_T: tf32, 3-D, TMA-fed march)
 cudaError_t launch_split_T_step(const lbm_s* h, cudaStream_t s);
 bool cs_writes_T(const lbm_s* h);
-// the tensor-core forms with bf16 parts (three or five products)
+// the tensor-core forms with bf16 parts (three, five or six products)
 inline bool bf16_parts(int precision) {
-  return precision == LBM_FP32_BF16SPLIT || precision == LBM_FP32_BF16SPLIT5;
+  return precision == LBM_FP32_BF16SPLIT || precision == LBM_FP32_BF16SPLIT5 || precision == LBM_FP32_BF16SPLIT6;
 }
 int reduce_blocks_for(long long n);
 // tensor-core plan: split K_mu (row-major FP64 per axis), allocate split C, encode TMA maps

@@ -46,6 +46,20 @@ sum_final_kernel(const double* __restrict__ partials, int nparts, double* __rest
   if (threadIdx.x == 0) *out = acc;
 }
 
+// The latest step's mass: the collide-stream kernel's block partials added in a fixed
+// order; with limit > 0, a mass outside [-limit, limit] (or not finite) sets bit 1 of flag.
+__global__ void __launch_bounds__(kReduceThreads)
+step_mass_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out, double limit,
+                 int* __restrict__ flag) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += kReduceThreads) acc += partials[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    *out = acc;
+    if (limit > 0.0 && !(fabs(acc) <= limit)) atomicOr(flag, 1);
+  }
+}
+
 template <typename real>
 __global__ void convert_in_kernel(const double* __restrict__ src, real* __restrict__ dst, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -100,6 +114,11 @@ cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s) {
   else
     sum_partials_kernel<float><<<nb, kReduceThreads, 0, s>>>((const float*)C, n, h->dev.partials);
   sum_final_kernel<<<1, kReduceThreads, 0, s>>>(h->dev.partials, nb, h->dev.scalar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_mass(const lbm_s* h, double limit, cudaStream_t s) {
+  step_mass_kernel<<<1, kReduceThreads, 0, s>>>(h->cs_part, h->cs_nparts, h->dev.scalar, limit, h->dev.flag);
   return cudaGetLastError();
 }
 

@@ -39,8 +39,9 @@ struct TcParams {
 
 struct TcMaps {
   CUtensorMap c_hi[3], c_lo[3];  // C split; box per axis (x: B rows; y, z: MN-major A)
+  CUtensorMap c_l2[3];           // third part of C (six-product bf16 form only)
   CUtensorMap k_hi[3], k_lo[3];  // K_mu split; box BK x 128 for the x axis (A), BK x BN else (B)
-  CUtensorMap k_l2[3];           // third part of K_mu (five-product bf16 form only)
+  CUtensorMap k_l2[3];           // third part of K_mu (five- and six-product bf16 forms)
   CUtensorMap f[3];              // F_mu (FP32), box 128 x (BN / ksplit) output rows
 };
 
@@ -48,7 +49,8 @@ struct TcPlan {
   TcMaps maps;
   TcParams prm;
   int elem = 2;      // 2: bf16 parts, 4: tf32 parts
-  int kparts = 2;    // parts of K_mu: 2 (three products) or 3 (bf16, five products)
+  int kparts = 2;    // parts of K_mu: 2 (three products) or 3 (bf16, five or six products)
+  int cparts = 2;    // parts of C: 2, or 3 (bf16, six products)
   int bn = 64;
   bool persist = false;  // one CTA per SM walking the tile list (frac_tc_persist_kernel)
   bool pdl = false;      // launch with programmatic stream serialization (the handle's choice)
@@ -236,19 +238,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// E: operand bytes; BN: output columns per tile; KS: contraction split; KP: parts of the
-// weights (2, or 3 for the five-product bf16 form; C always has two).  A ring stage holds
-// KP parts of A (from st) and KP parts of B (from st + KP * A_BYTES).
+// Split forms, by KP: 2 = weights and C in two parts (hi*hi + hi*lo + lo*hi); 3 = the
+// weights in three bf16 parts, C in two (five products); 6 = both in three bf16 parts
+// (six products: every pair of parts whose orders sum to at most 2).
+__host__ __device__ constexpr int k_parts(int KP) { return KP == 2 ? 2 : 3; }
+__host__ __device__ constexpr int c_parts(int KP) { return KP == 6 ? 3 : 2; }
+
+// E: operand bytes; BN: output columns per tile; KS: contraction split; KP: split form
+// (above).  A ring stage holds k_parts(KP) slots of A (from st) and as many of B (from
+// st + k_parts(KP) * A_BYTES); C fills two or three of its operand's slots.
 template <int E, int BN, int KS = 1, int KP = 2>
 struct Cfg {
   static constexpr int BK = 128 / E;                 // contraction elements per 128-byte row
-  static constexpr int STAGES = KP == 2 ? ((BN <= 64) ? 4 : (BN <= 128 ? 3 : 2)) : (BN <= 64 ? 3 : 2);
+  static constexpr int NP = k_parts(KP);             // operand slots per side
+  static constexpr int STAGES = NP == 2 ? ((BN <= 64) ? 4 : (BN <= 128 ? 3 : 2)) : (BN <= 64 ? 3 : 2);
   static constexpr uint32_t A_BYTES = BM * 128;      // one operand part of A: 128 rows x 128 B
   static constexpr uint32_t B_BYTES = BN * 128;
-  static constexpr uint32_t STAGE = KP * A_BYTES + KP * B_BYTES;
-  // bytes one k-block of axis mu loads: the weights in KP parts, C in two
+  static constexpr uint32_t STAGE = NP * A_BYTES + NP * B_BYTES;
+  // bytes one k-block of axis mu loads: the weights in k_parts, C in c_parts
   __host__ __device__ static constexpr uint32_t tx_bytes(int mu) {
-    return mu == 0 ? KP * A_BYTES + 2 * B_BYTES : 2 * A_BYTES + KP * B_BYTES;
+    return mu == 0 ? k_parts(KP) * A_BYTES + c_parts(KP) * B_BYTES : c_parts(KP) * A_BYTES + k_parts(KP) * B_BYTES;
   }
   static constexpr size_t RING = (size_t)STAGES * STAGE;
   static constexpr size_t SMEM = RING + 1024 /*align*/ + 256 /*barriers*/;
@@ -287,13 +296,13 @@ __device__ __forceinline__ void load_stage_weights(const TcMaps& maps, const Til
     // A = K_x rows n = m_in..
     tma_load_2d(st, &maps.k_hi[0], k0, t.m_in, bar);
     tma_load_2d(st + G::A_BYTES, &maps.k_lo[0], k0, t.m_in, bar);
-    if (KP == 3) tma_load_2d(st + 2 * G::A_BYTES, &maps.k_l2[0], k0, t.m_in, bar);
+    if (k_parts(KP) == 3) tma_load_2d(st + 2 * G::A_BYTES, &maps.k_l2[0], k0, t.m_in, bar);
   } else {
     // B = K_mu rows n = ncol0..
-    uint8_t* b_hi = st + KP * G::A_BYTES;
+    uint8_t* b_hi = st + G::NP * G::A_BYTES;
     tma_load_2d(b_hi, &maps.k_hi[t.mu], k0, t.ncol0, bar);
     tma_load_2d(b_hi + G::B_BYTES, &maps.k_lo[t.mu], k0, t.ncol0, bar);
-    if (KP == 3) tma_load_2d(b_hi + 2 * G::B_BYTES, &maps.k_l2[t.mu], k0, t.ncol0, bar);
+    if (k_parts(KP) == 3) tma_load_2d(b_hi + 2 * G::B_BYTES, &maps.k_l2[t.mu], k0, t.ncol0, bar);
   }
 }
 
@@ -303,12 +312,13 @@ __device__ __forceinline__ void load_stage_conc(const TcMaps& maps, const TileAt
   using G = Cfg<E, BN, 1, KP>;
   uint8_t* a_hi = st;
   uint8_t* a_lo = st + G::A_BYTES;
-  uint8_t* b_hi = st + KP * G::A_BYTES;
+  uint8_t* b_hi = st + G::NP * G::A_BYTES;
   uint8_t* b_lo = b_hi + G::B_BYTES;
   if (t.mu == 0) {
     // B = C rows y = ncol0.. at z = m_out
     tma_load_3d(b_hi, &maps.c_hi[0], k0, t.ncol0, t.m_out, bar);
     tma_load_3d(b_lo, &maps.c_lo[0], k0, t.ncol0, t.m_out, bar);
+    if (c_parts(KP) == 3) tma_load_3d(b_lo + G::B_BYTES, &maps.c_l2[0], k0, t.ncol0, t.m_out, bar);
   } else if (E == 4) {
     // tf32 parts: A = the regrouped C split (contraction in groups of 4), 128 x-lines
     // (8 blocks of 16), BK / 4 groups: dims (64, x blocks, y groups or y, z or z groups)
@@ -327,9 +337,13 @@ __device__ __forceinline__ void load_stage_conc(const TcMaps& maps, const TileAt
       if (t.mu == 1) {
         tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[1], x, k0, t.m_out, bar);
         tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[1], x, k0, t.m_out, bar);
+        if (c_parts(KP) == 3)
+          tma_load_3d(a_lo + G::A_BYTES + j * G::A_BOX_MN, &maps.c_l2[1], x, k0, t.m_out, bar);
       } else {
         tma_load_3d(a_hi + j * G::A_BOX_MN, &maps.c_hi[2], x, t.m_out, k0, bar);
         tma_load_3d(a_lo + j * G::A_BOX_MN, &maps.c_lo[2], x, t.m_out, k0, bar);
+        if (c_parts(KP) == 3)
+          tma_load_3d(a_lo + G::A_BYTES + j * G::A_BOX_MN, &maps.c_l2[2], x, t.m_out, k0, bar);
       }
     }
   }
@@ -344,13 +358,21 @@ __device__ __forceinline__ void load_stage(const TcMaps& maps, const TileAt& t, 
 // The split products of one k-block from ring stage `st` into accumulator `d` (first =
 // no previous contribution in d).  With KP = 2: hi*hi, hi*lo, lo*hi.  With KP = 3 (the
 // weights in parts k1 + k2 + k3, C in c1 + c2) every product whose part orders sum to at
-// most 2: k1 c1, k1 c2, k2 c1, k2 c2, k3 c1.
+// most 2 that the parts allow: k1 c1, k1 c2, k2 c1, k2 c2, k3 c1; KP = 6 (C in c1 + c2 +
+// c3 too) adds k1 c3.
+//
+// Accumulation chains: the k-steps of a CTA's contraction are numbered c = chain0 + kk
+// (kk = 0..BK/UK-1 within this k-block) and k-step c accumulates into TMEM region c % nreg
+// (BN columns each, from tmem); the first k-step of a region overwrites it.  The tensor
+// cores round each accumulation at the accumulator's own scale, so the error of a long
+// chain grows with its length (measured as a drift of the split forms over many time
+// steps); short chains, added in FP32 by the epilogue, keep it at the FP32 level.
 template <int E, int BN, int KP = 2>
-__device__ __forceinline__ void mma_stage(uint32_t d, uint32_t st, int amode, bool first) {
+__device__ __forceinline__ void mma_stage(uint32_t tmem, int chain0, int nreg, uint32_t st, int amode) {
   using G = Cfg<E, BN, 1, KP>;
   const uint32_t idesc = amode == kAMNSw128 ? G::IDESC_MN : G::IDESC_K;
   const uint32_t a_hi = st, a_lo = st + G::A_BYTES;
-  const uint32_t b_hi = st + KP * G::A_BYTES, b_lo = b_hi + G::B_BYTES;
+  const uint32_t b_hi = st + G::NP * G::A_BYTES, b_lo = b_hi + G::B_BYTES;
 #pragma unroll
   for (int kk = 0; kk < G::BK / Kind<E>::UK; ++kk) {
     uint32_t a_off, a_lbo, a_sbo = 1024, a_lay = 2;
@@ -372,10 +394,12 @@ __device__ __forceinline__ void mma_stage(uint32_t d, uint32_t st, int amode, bo
     const uint64_t dal = smem_desc(a_lo + a_off, a_lbo, a_sbo, a_lay);
     const uint64_t dbh = smem_desc(b_hi + b_off, 16, 1024);
     const uint64_t dbl = smem_desc(b_lo + b_off, 16, 1024);
-    mma<E>(d, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
+    const int c = chain0 + kk;
+    const uint32_t d = tmem + (uint32_t)((c % nreg) * BN);
+    mma<E>(d, dah, dbh, idesc, c >= nreg ? 1u : 0u);
     mma<E>(d, dah, dbl, idesc, 1u);
     mma<E>(d, dal, dbh, idesc, 1u);
-    if (KP == 3) {
+    if (KP >= 3) {
       mma<E>(d, dal, dbl, idesc, 1u);
       if (amode == kAKSw128) {  // A = the weights: k3 c1
         mma<E>(d, smem_desc(a_hi + 2 * G::A_BYTES + a_off, a_lbo, a_sbo, a_lay), dbh, idesc, 1u);
@@ -383,18 +407,33 @@ __device__ __forceinline__ void mma_stage(uint32_t d, uint32_t st, int amode, bo
         mma<E>(d, dah, smem_desc(b_hi + 2 * G::B_BYTES + b_off, 16, 1024), idesc, 1u);
       }
     }
+    if (KP == 6) {
+      if (amode == kAKSw128) {  // B = C: k1 c3
+        mma<E>(d, dah, smem_desc(b_hi + 2 * G::B_BYTES + b_off, 16, 1024), idesc, 1u);
+      } else {                  // A = C: c3 k1
+        mma<E>(d, smem_desc(a_hi + 2 * G::A_BYTES + a_off, a_lbo, a_sbo, a_lay), dbh, idesc, 1u);
+      }
+    }
   }
 }
 
 __device__ __forceinline__ void named_sync128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// Accumulator regions of a CTA that contracts nkb k-blocks into BN columns: k-block i
-// goes to TMEM region i % regions, and the epilogue adds the regions in FP32, in order.
-// A tensor-core accumulator rounds each update at its own scale (measured: the error of
-// the result grows with the number of MMAs into one accumulator), so shorter chains make
-// the split forms more accurate at no extra MMA work.  Up to 4 regions, 512 columns.
-__host__ __device__ constexpr int acc_regions(int nkb, int bn) {
-  return (nkb >= 4 && 4 * bn <= 512) ? 4 : ((nkb >= 2 && 2 * bn <= 512) ? 2 : 1);
+// MMA k-steps per k-block (128-byte rows of UK-element MMAs): 4 for bf16 and tf32
+template <int E>
+__host__ __device__ constexpr int ksteps() {
+  return (128 / E) / Kind<E>::UK;
+}
+
+// Accumulator regions of a CTA that runs `chains` k-steps into BN columns: the largest power
+// of two up to 8 regions, 512 TMEM columns and the number of k-steps; the epilogue adds the
+// regions in FP32, in order.  A tensor-core accumulator rounds each update at its own scale
+// (measured: the error of the result grows with the number of MMAs into one accumulator),
+// so shorter chains make the split forms more accurate at no extra MMA work.
+__host__ __device__ constexpr int acc_regions(int chains, int bn) {
+  int r = 1;
+  while (r < 8 && 2 * r <= chains && 2 * r * bn <= 512) r *= 2;
+  return r;
 }
 
 // One operator work item (tile item / KS, contraction slice item % KS) run by threads
@@ -402,8 +441,8 @@ __host__ __device__ constexpr int acc_regions(int nkb, int bn) {
 // barrier 1 in place of block barriers and a TMEM accumulator of BN columns allocated by
 // the caller.  The item's partial tile goes to its slot of F by one TMA store (the plan
 // must have tma_store set).  Every wait is bounded; a wait that gives up sets bit 2 of
-// the flag and the item stores nothing.  `tmem` holds acc_regions(nkb, BN) * BN columns
-// (at most 512; the caller allocates min(4 BN, 512)).
+// the flag and the item stores nothing.  `tmem` holds acc_regions(nkb k-steps, BN) * BN
+// columns (at most 512; the caller allocates 512).
 template <int E, int BN, int KS>
 __device__ __forceinline__ void op_item(const TcMaps& maps, const TcParams& P, int item, uint8_t* smem, uint32_t tmem,
                                         int tid) {
@@ -417,7 +456,7 @@ __device__ __forceinline__ void op_item(const TcMaps& maps, const TcParams& P, i
   const TcAxis& ax = P.ax[tl.mu];
   const int kb0 = rank * ax.kblocks / KS, kb1 = (rank + 1) * ax.kblocks / KS;
   const int nkb = kb1 - kb0;
-  const int nreg = acc_regions(nkb, BN);
+  const int nreg = acc_regions(nkb * ksteps<E>(), BN);
   auto issue = [&](int i) {
     const int s = i % G::STAGES;
     mbar_expect_tx(&full[s], G::STAGE);
@@ -446,7 +485,7 @@ __device__ __forceinline__ void op_item(const TcMaps& maps, const TcParams& P, i
       const int s = i % G::STAGES;
       if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
       tc_fence_after();
-      mma_stage<E, BN>(tmem + (uint32_t)((i % nreg) * BN), smem_u32(smem + (size_t)s * G::STAGE), amode, i < nreg);
+      mma_stage<E, BN>(tmem, i * ksteps<E>(), nreg, smem_u32(smem + (size_t)s * G::STAGE), amode);
       mma_commit(&empty[s]);
     }
     mma_commit(done);

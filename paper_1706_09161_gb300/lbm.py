@@ -27,9 +27,9 @@ LBM_ETOOBIG = -7
 
 LBM_D2Q5, LBM_D3Q7 = 0, 1
 LBM_BGK, LBM_MRT = 0, 1
-LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT, LBM_FP32_BF16SPLIT5 = 0, 1, 2, 3, 4
+LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT, LBM_FP32_BF16SPLIT5, LBM_FP32_BF16SPLIT6 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16split": LBM_FP32_BF16SPLIT, "tf32split": LBM_FP32_TF32SPLIT,
-              "bf16x5split": LBM_FP32_BF16SPLIT5}
+              "bf16x5split": LBM_FP32_BF16SPLIT5, "bf16x6split": LBM_FP32_BF16SPLIT6}
 
 
 class lbm_params(ctypes.Structure):
@@ -85,6 +85,10 @@ def _load() -> ctypes.CDLL:
         "lbm_save": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
         "lbm_load": (ctypes.c_int, [vp, vp, ctypes.c_longlong]),
         "lbm_mass": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lbm_set_mass_limit": (ctypes.c_int, [vp, ctypes.c_double]),
+        "lbm_set_fields": (ctypes.c_int, [vp, dp, dp, dp]),
+        "lbm_set_source": (ctypes.c_int, [vp, dp, ctypes.c_double]),
+        "lbm_set_wall_values": (ctypes.c_int, [vp, dp, ctypes.c_double]),
         "lbm_sync": (ctypes.c_int, [vp]),
         "lbm_get_stream": (ctypes.c_int, [vp, P(vp)]),
         "lbm_launches_per_step": (ctypes.c_int, [vp, P(ctypes.c_int)]),
@@ -110,7 +114,8 @@ _lib = _load()
 
 # Declared C entry points, re-exported under their own names.
 EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f", "lbm_state_size", "lbm_save", "lbm_load", "lbm_autotune", "lbm_configure",
-            "lbm_mass", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_wait_check", "lbm_set_allocator",
+            "lbm_mass", "lbm_set_mass_limit", "lbm_set_fields", "lbm_set_source", "lbm_set_wall_values",
+            "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_wait_check", "lbm_set_allocator",
             "lbm_frac_matrix",
             "lbm_grad", "lbm_frac_matrix_grad", "lbm_digamma", "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
 
@@ -267,6 +272,31 @@ def lbm_mass(h: int, prob: int = 0) -> float:
     m = ctypes.c_double()
     _check(_lib.lbm_mass(ctypes.c_void_p(h), int(prob), ctypes.byref(m)), "lbm_mass")
     return m.value
+
+
+def lbm_set_mass_limit(h: int, limit: float) -> None:
+    _check(_lib.lbm_set_mass_limit(ctypes.c_void_p(h), float(limit)), "lbm_set_mass_limit")
+
+
+def lbm_set_fields(h: int, D=None, g=None, u=None) -> None:
+    """Spatially varying D(x) (d, d, *shape), g(x) (d, *shape), u(x) (d, *shape); None keeps
+    the constant value (all None: constant coefficients again)."""
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (D, g, u)]
+    ptrs = [None if a is None else _dptr(a) for a in arrs]
+    _check(_lib.lbm_set_fields(ctypes.c_void_p(h), *ptrs), "lbm_set_fields")
+
+
+def lbm_set_source(h: int, S=None, rate: float = 0.0) -> None:
+    """S_c(x, t) = S(x) exp(rate t) (S in the field layout; None removes the source)."""
+    a = None if S is None else np.ascontiguousarray(S, dtype=np.float64)
+    _check(_lib.lbm_set_source(ctypes.c_void_p(h), None if a is None else _dptr(a), float(rate)), "lbm_set_source")
+
+
+def lbm_set_wall_values(h: int, Cw=None, rate: float = 0.0) -> None:
+    """Wall values C_w(x) exp(rate t) (field layout; None: the constant C_wall)."""
+    a = None if Cw is None else np.ascontiguousarray(Cw, dtype=np.float64)
+    _check(_lib.lbm_set_wall_values(ctypes.c_void_p(h), None if a is None else _dptr(a), float(rate)),
+           "lbm_set_wall_values")
 
 
 def lbm_sync(h: int) -> int:
@@ -441,6 +471,23 @@ class Lattice:
 
     def mass(self) -> float:
         return lbm_mass(self.h, 0)
+
+    def set_fields(self, D=None, g=None, u=None) -> None:
+        """Coefficients varying in space (arrays in the field layout with a leading axis per
+        component); re-initialises from the initial concentration."""
+        lbm_set_fields(self.h, D, g, u)
+
+    def set_source(self, S=None, rate: float = 0.0) -> None:
+        """Source S_c(x, t) = S(x) exp(rate t); re-initialises (time 0)."""
+        lbm_set_source(self.h, S, rate)
+
+    def set_wall_values(self, Cw=None, rate: float = 0.0) -> None:
+        """Wall values C_w(x) exp(rate t); re-initialises (time 0)."""
+        lbm_set_wall_values(self.h, Cw, rate)
+
+    def set_mass_limit(self, limit: float) -> None:
+        """Latch LBM_ERR_UNSTABLE at the next synchronising call if |mass| > limit (0: off)."""
+        lbm_set_mass_limit(self.h, limit)
 
     def sync(self) -> None:
         _check(lbm_sync(self.h), "lbm_sync")

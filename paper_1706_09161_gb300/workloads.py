@@ -9,7 +9,8 @@ Array convention: a field on a grid ``(n_1, ..., n_d)`` (nodes per axis,
 walls included) is stored with axis 1 (x) fastest, i.e. a numpy array of
 shape ``(n_2, n_1)`` in 2-D and ``(n_3, n_2, n_1)`` in 3-D.
 
-All named workloads are in lattice units, dx = dt = 1.
+The named workloads are in lattice units (dx = dt = 1) except ``varying_512`` and
+``exact_e5``, which set dx = 1/(side-1) on [0,1]^2 and dt from D.
 
 The named workloads follow the paper's validation style (Section 3: Gaussian
 hills in square domains, homogeneous Dirichlet walls, alpha in ]1,2],
@@ -20,6 +21,9 @@ p in [0,1]) at the sizes of the performance study:
 * ``mrt3d_256``          3-D D3Q7 MRT, 256^3, 2000 steps
 * ``batch64``            64 independent 2-D MRT problems of uneven sizes
 * ``inverse_256``        2-D MRT 256x256 with hidden parameters and noisy snapshots
+* ``varying_512``        2-D MRT 512x512 on [0,1]^2 with D(x), g(x), u(x) varying in space
+* ``exact_e5``           2-D MRT on ]0,1[^2 with the source, varying D(x) and time-dependent wall
+                         values of Section 3.4, whose exact solution is known
 """
 from __future__ import annotations
 
@@ -191,6 +195,79 @@ def inverse_256(side: int = 256, nsteps: int = 3000, nsnap: int = 10
 def observation_noise(shape: Sequence[int], seed: int = 5, std: float = 1e-4) -> np.ndarray:
     """N(0, std^2) noise for the synthetic observations."""
     return np.random.default_rng(seed + 1000).normal(0.0, std, size=tuple(shape))
+
+
+def smooth_fields(rng: np.random.Generator, grid: Sequence[int], collision: str, D0: float, g_amp: float = 0.2,
+                  u_amp: float = 0.0, u0: Sequence[float] = (), offdiag: float = 0.1) -> dict:
+    """Seeded smooth coefficient fields on a grid (array order = reversed grid, leading axis
+    per component): diagonal D(x) = D0 (1 +- 0.5 sin), off-diagonal entries up to
+    offdiag * D0 (MRT only; BGK gets a spherical D(x)), g(x) = 1 +- g_amp, u(x) = u0 +- u_amp.
+    Each component is a sum of one or two plane waves with random phases and wave numbers."""
+    grid = tuple(int(n) for n in grid)
+    d = len(grid)
+    shape = tuple(reversed(grid))
+    axes = np.meshgrid(*[np.linspace(0.0, 1.0, n) for n in shape], indexing="ij")
+
+    def wave(amp):
+        k = rng.uniform(0.5, 2.0, size=d)
+        return amp * np.sin(2 * np.pi * (rng.uniform() + sum(kk * x for kk, x in zip(k, axes))))
+
+    D = np.zeros((d, d) + shape)
+    for i in range(d):
+        D[i, i] = D0 * (1.0 + wave(0.5))
+    if collision == "mrt":
+        for i in range(d):
+            for j in range(i + 1, d):
+                D[i, j] = D[j, i] = D0 * wave(offdiag)
+    else:
+        for i in range(1, d):
+            D[i, i] = D[0, 0]
+    g = np.stack([1.0 + wave(g_amp) for _ in range(d)])
+    u = np.stack([(u0[i] if u0 else 0.0) + wave(u_amp) for i in range(d)])
+    return {"D": D, "g": g, "u": u}
+
+
+def varying_512(side: int = 512) -> Tuple[Problem, np.ndarray, int, dict]:
+    """2-D MRT with spatially varying coefficients, side^2 nodes on [0,1]^2 (dx = 1/(side-1)):
+    D(x) = 0.02 (1 +- 0.5) with off-diagonal entries, g(x) = 1 +- 0.2, u(x) = (0.1, -0.05)
+    +- 0.05, alpha = (1.6, 1.8), p = (0.4, 0.6), dt such that lambda = 1 at the mean D,
+    unit-mass Gaussian (sigma = 0.05) at the centre, 2000 steps (t = 0.04)."""
+    rng = np.random.default_rng(6)
+    dx = 1.0 / (side - 1)
+    D0 = 0.02
+    dt = 0.5 * (1.0 / 3.0) * dx * dx / D0
+    pb = Problem(d=2, collision="mrt", grid=(side, side), alpha=(1.6, 1.8), p=(0.4, 0.6), g=(1.0, 1.0),
+                 D=_diag([D0, D0]), u=(0.1, -0.05), s_free=(1.2, 1.2), dx=dx, dt=dt)
+    fields = smooth_fields(rng, pb.grid, "mrt", D0, g_amp=0.2, u_amp=0.05, u0=(0.1, -0.05))
+    C0 = gaussian_pulse(pb.grid, 0.05 / dx)
+    return pb, C0, 2000, fields
+
+
+def exact_e5(side: int = 256, T: float = 0.1, alpha=(1.5, 1.7), a=(0.4, 0.7), lam_max: float = 1.0) -> dict:
+    """Section 3.4's case with a closed-form solution, on ]0,1[^2 with side^2 nodes (dx =
+    1/(side-1)): p = 1, g = 1, u = 0, diagonal D_mumu(x) = x_mu^alpha_mu Gamma(a_mu + 2 -
+    alpha_mu) / Gamma(a_mu + 2), source S_c = -3 exp(-t) x^a1 y^a2, initial and wall values from
+    C = exp(-t) x^a1 y^a2 (Eqs. Def_D_AS, exsolFADE_3D); MRT with free rates 1.2, dt such that
+    lambda <= lam_max.  These are the paper's formulas for the inputs, written out as fields.
+    Returns a dict: problem, C0, nsteps, coefficient fields, source (profile, rate), walls
+    (profile, rate), exact (the solution at t = nsteps dt)."""
+    import math
+    N = side - 1
+    dx = 1.0 / N
+    x = np.arange(side) * dx
+    X = np.broadcast_to(x[None, :], (side, side))
+    Y = np.broadcast_to(x[:, None], (side, side))
+    D = np.zeros((2, 2, side, side))
+    D[0, 0] = X ** alpha[0] * math.gamma(a[0] + 2 - alpha[0]) / math.gamma(a[0] + 2)
+    D[1, 1] = Y ** alpha[1] * math.gamma(a[1] + 2 - alpha[1]) / math.gamma(a[1] + 2)
+    dt = (lam_max - 0.5) * (1.0 / 3.0) * dx * dx / float(D.max())
+    n = int(round(T / dt))
+    dt = T / n
+    pb = Problem(d=2, collision="mrt", grid=(side, side), alpha=tuple(alpha), p=(1.0, 1.0), g=(1.0, 1.0),
+                 D=_diag([0.1, 0.1]), u=(0.0, 0.0), s_free=(1.2, 1.2), dx=dx, dt=dt)
+    prof = np.ascontiguousarray(X ** a[0] * Y ** a[1])
+    return dict(problem=pb, C0=prof.copy(), nsteps=n, fields={"D": D}, source=(-3.0 * prof, -1.0),
+                walls=(prof, -1.0), exact=math.exp(-T) * prof)
 
 
 # --------------------------------------------------------------------------- random small cases

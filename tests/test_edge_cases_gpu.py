@@ -25,7 +25,7 @@ from paper_1706_09161_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-FORMS = ["fp64", "fp32", "bf16split", "tf32split", "bf16x5split"]
+FORMS = ["fp64", "fp32", "bf16split", "tf32split", "bf16x5split", "bf16x6split"]
 
 
 @pytest.fixture(scope="module")
@@ -127,6 +127,6 @@ def test_batch_read_C_into_device_array_and_mass_by_index(L):
             assert np.array_equal(dev.cpu().numpy(), host)
             assert b.mass(i) == pytest.approx(float(host.sum()), rel=1e-6)
         with pytest.raises(L.LBMError):
-            b.C(3)
+            L.lbm_read_C(b.h, 3, np.empty(probs[0].shape))
         with pytest.raises(L.LBMError):
             L.lbm_mass(b.h, -1)

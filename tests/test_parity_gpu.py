@@ -178,6 +178,69 @@ def test_mass_reduction(L):
         assert lat.mass() == pytest.approx(float(C.sum()), rel=1e-14)
 
 
+@pytest.mark.parametrize("precision,rel", [("fp64", 1e-12), ("fp32", 1e-6), ("bf16split", 1e-6)])
+@pytest.mark.parametrize("grid", [(130, 70), (64, 48, 40), (37, 29)])
+def test_mass_of_every_step_from_the_collide_stream_partials(L, precision, rel, grid):
+    """Algorithm 1, loop item 5: the FP64 mass the collide-stream kernel leaves as block
+    partials after each step equals the oracle's sum of C (FP64 path 1e-12, FP32 paths
+    1e-6, on a well-conditioned problem: alpha >= 1.5, D >= 0.02, where FP32 C itself stays
+    within 1e-6), and the sum of the C the step wrote (same values, summed on the host)."""
+    rng = np.random.default_rng(140 + grid[0] + len(grid))
+    pb = W.random_problem(rng, len(grid), "mrt", grid)
+    d = len(grid)
+    pb = dataclasses.replace(pb, alpha=tuple(1.5 + 0.5 * (a - 1.2) / 0.8 for a in pb.alpha),
+                             D=tuple(tuple(0.02 + 0.5 * v if i == j else 0.0 for j, v in enumerate(row))
+                                     for i, row in enumerate(pb.D)))
+    C0 = W.random_field(rng, grid)
+    ops = O.Operators(pb)
+    f = O.init_populations(ops, torch.tensor(C0))
+    with L.Lattice(pb, C0, precision) as lat:
+        assert lat.mass() == pytest.approx(float(O.concentration(f).sum()), rel=rel)  # no step yet
+        for t in range(1, 31):
+            f = O.step(ops, f)
+            lat.step(1)
+            m = lat.mass()
+            assert m == pytest.approx(float(O.concentration(f).sum()), rel=rel), t
+            if t % 10 == 0:
+                assert m == pytest.approx(float(lat.C().sum()), rel=1e-13), t
+        lat.step(200)  # graph replay: the partials of the last replayed step
+        assert lat.mass() == pytest.approx(float(lat.C().sum()), rel=1e-13)
+
+
+def test_mass_of_batch_members_and_fused_step(L):
+    probs, fields, _ = W.batch64(nprob=5, sides=(64, 130, 256), seed=33)
+    with L.Batch(probs, fields, "bf16split") as b:
+        b.step(17)
+        for i in range(5):
+            assert b.mass(i) == pytest.approx(float(b.C(i).sum()), rel=1e-9), i
+    pb, C0, _ = W.mrt_aniso_512()
+    with L.Lattice(pb, C0, "bf16split") as lat:
+        lat.configure(128, 4, 0, 0, 1)  # the fused step: one partial per collide-stream item
+        lat.step(33)
+        assert lat.mass() == pytest.approx(float(lat.C().sum()), rel=1e-9)
+
+
+def test_mass_limit_latches_instability(L):
+    """A mass limit turns a run whose mass leaves [-limit, limit] into LBM_ERR_UNSTABLE at
+    the next synchronising call (before any value turns non-finite)."""
+    pb = W.Problem(d=2, collision="bgk", grid=(48, 24), alpha=(1.5, 1.5), p=(0.5, 0.5), g=(1, 1),
+                   D=((1e-3, 0), (0, 1e-3)), u=(0.6, 0.0))
+    with L.Lattice(pb, W.gaussian_pulse(pb.grid, 2.0), "fp32") as lat:
+        lat.set_mass_limit(10.0)  # unit initial mass
+        lat.step(20)
+        assert L.lbm_sync(lat.h) == L.LBM_OK
+        lat.step(60)
+        m = lat.mass() if L.lbm_sync(lat.h) == L.LBM_OK else None
+        # this E4-style run grows fast: by 80 steps its mass is far above 10
+        assert m is None
+        with pytest.raises(L.LBMError):
+            lat.C()
+        lat.reset()
+        assert L.lbm_sync(lat.h) == L.LBM_OK
+        with pytest.raises(L.LBMError):
+            lat.set_mass_limit(-1.0)
+
+
 def test_write_read_populations_and_set_C(L):
     rng = np.random.default_rng(12)
     pb = W.random_problem(rng, 2, "bgk", (23, 19), spherical=True)
@@ -219,7 +282,7 @@ def test_zero_steps_is_noop(L):
 
 # ---------------------------------------------------------------- checkpoint / resume
 
-@pytest.mark.parametrize("kind", ["fp64", "fp32", "bf16split", "tf32split", "bf16x5split"])
+@pytest.mark.parametrize("kind", ["fp64", "fp32", "bf16split", "tf32split", "bf16x5split", "bf16x6split"])
 def test_save_load_resumes_bit_exact(L, kind):
     """Saving, stepping k times, loading and stepping k times again gives the same f."""
     rng = np.random.default_rng(91)

@@ -1,0 +1,140 @@
+"""GPU parity of the source term and of wall values that vary with position and time
+(lbm_set_source, lbm_set_wall_values) against the FP64 oracle and Section 3.4's exact
+solution: Eq. (LBE_Ket) w_i S_c dt at the step's start, Eq. (Dirichlet_BC) with
+C_0(x, t) (Section 2.5), Eqs. (Def_D_AS), (exsolFADE_3D)."""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import arith_bounds
+from oracle import lbm_oracle as O
+from paper_1706_09161_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1706_09161_gb300 import build
+    build.build()
+    from paper_1706_09161_gb300 import lbm
+    return lbm
+
+
+def _oracle_e5(case, nsteps):
+    ops = O.with_source_and_walls(O.Operators(case["problem"], fields=case["fields"]), source=case["source"],
+                                  walls=case["walls"])
+    return O.concentration(O.run(case["problem"], case["C0"], nsteps, ops)).numpy()
+
+
+def _gpu(L, case, precision, nsteps, single=False):
+    with L.Lattice(case["problem"], case["C0"], precision) as lat:
+        lat.set_fields(**case["fields"])
+        lat.set_source(*case["source"])
+        lat.set_wall_values(*case["walls"])
+        if single:
+            for _ in range(nsteps):
+                lat.step(1)
+        else:
+            lat.step(nsteps)
+        return lat.C(), lat.f()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_exact_solution_case_matches_oracle_and_exact(L, precision):
+    """Section 3.4 at 21^2 nodes to t = 0.5 (1032 steps, graph replays and single launches):
+    the oracle to 1e-12 (FP64) / 1e-5 (FP32), and the exact solution within 1.5%."""
+    case = W.exact_e5(side=21, T=0.5)
+    n = case["nsteps"]
+    C_ref = _oracle_e5(case, n)
+    C, _ = _gpu(L, case, precision, n)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    arith_bounds.assert_close(C, C_ref, tol, tol, f"e5 {precision}")
+    assert arith_bounds.rel_l2(C, case["exact"]) < 1.5e-2
+
+
+def test_exact_solution_converges_on_the_gpu(L):
+    """dx = 1/40 and 1/80 (FP32): the error against the exact solution drops below 1% and
+    keeps falling with dx, as the oracle's does."""
+    errs = []
+    for side in (41, 81):
+        case = W.exact_e5(side=side, T=0.5)
+        C, _ = _gpu(L, case, "fp32", case["nsteps"])
+        errs.append(arith_bounds.rel_l2(C, case["exact"]))
+    assert errs[0] < 1e-2 and errs[1] < 0.7 * errs[0], errs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_replay_keeps_time(L, precision):
+    """Time factors per step across 128-step graph replays and single launches: identical
+    populations either way (300 steps)."""
+    case = W.exact_e5(side=21, T=0.5)
+    _, f_graph = _gpu(L, case, precision, 300)
+    _, f_single = _gpu(L, case, precision, 300, single=True)
+    assert np.array_equal(f_graph, f_single)
+
+
+@pytest.mark.parametrize("grid", [(40, 33), (19, 13, 11)])
+def test_source_mass_and_time_dependent_walls(L, grid):
+    """FP64: each step adds sum_x S(x) exp(rate t) dt of mass away from the walls, and the
+    wall nodes hold C_w(x) exp(rate t) after the step ending at t (corners included)."""
+    rng = np.random.default_rng(1001 + len(grid))
+    pb = dataclasses.replace(W.random_problem(rng, len(grid), "mrt", grid), dt=0.6)
+    S = np.zeros(pb.shape)
+    c = tuple(n // 2 for n in pb.shape)
+    S[tuple(slice(k - 1, k + 2) for k in c)] = 0.01
+    Cw = rng.uniform(0.01, 0.05, size=pb.shape)
+    C0 = np.zeros(pb.shape)
+    ops = O.with_source_and_walls(O.Operators(pb), source=(S, -0.1), walls=(Cw, 0.3))
+    wall = np.ones(pb.shape, dtype=bool)
+    wall[tuple(slice(1, -1) for _ in grid)] = False
+    with L.Lattice(pb, C0, "fp64") as lat:
+        lat.set_source(S, -0.1)
+        lat.set_wall_values(Cw, 0.3)
+        f = O.init_populations(ops, torch.tensor(C0))
+        for k in range(8):
+            f = O.step(ops, f, k)
+            lat.step(1)
+            C = lat.C()
+            arith_bounds.assert_close(C, O.concentration(f).numpy(), 1e-12, 1e-12, f"step {k}")
+            assert np.max(np.abs(C[wall] - Cw[wall] * math.exp(0.3 * (k + 1) * pb.dt))) < 1e-15
+
+
+def test_save_load_keeps_time_and_source_can_be_removed(L):
+    case = W.exact_e5(side=21, T=0.5)
+    with L.Lattice(case["problem"], case["C0"], "fp64") as lat:
+        lat.set_fields(**case["fields"])
+        lat.set_source(*case["source"])
+        lat.set_wall_values(*case["walls"])
+        lat.step(37)
+        state = lat.save()
+        lat.step(50)
+        f_a = lat.f()
+        lat.load(state)
+        lat.step(50)
+        assert np.array_equal(lat.f(), f_a)
+        # without source, wall values and coefficient fields: the constant-coefficient run
+        lat.set_source(None)
+        lat.set_wall_values(None)
+        lat.set_fields()
+        lat.step(10)
+        with L.Lattice(case["problem"], case["C0"], "fp64") as ref:
+            ref.step(10)
+            assert np.array_equal(lat.C(), ref.C())
+
+
+def test_source_rejects_tensor_core_forms_and_batches(L):
+    case = W.exact_e5(side=21, T=0.5)
+    with L.Lattice(case["problem"], case["C0"], "bf16x6split") as lat:
+        with pytest.raises(L.LBMError) as ei:
+            lat.set_source(*case["source"])
+        assert ei.value.code == L.LBM_ENOTSUP
+    probs, fields, _ = W.batch64(nprob=2, sides=(64,), seed=3)
+    with L.Batch(probs, fields, "fp32") as b:
+        with pytest.raises(L.LBMError):
+            L.lbm_set_source(b.h, np.zeros(probs[0].shape), 0.0)
