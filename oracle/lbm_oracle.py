@@ -14,6 +14,8 @@ autograd.  Every function cites the section / equation it follows:
 * lattices D2Q5 / D3Q7, weights, e^2 .......... Section 2.1, Eq. (weights_c), Fig. 1 caption
 * trapezoidal product-integration weights ..... Section 2.4, Eqs. (1Dminus_discret), (c+), (c-)
 * per-axis fractional term F_mu ............... Section 2.4, Eq. (XXminus_discret); Eq. (M2_FADE_3D)
+* Caputo-type variant F~ ...................... Section 3.5, Eqs. (Fg2), (PSRLdD-a/b), (Fg22),
+                                                 (CoeffA_FADE3DPS)
 * equilibrium ................................. Section 2.2, Eqs. (Feq), (CoeffA_FADE3D)
 * BGK relaxation time from D .................. Section 2.2, Eq. (Diffusion_Coefficient_3D)
 * diagonal D under BGK through h_mu ........... Section 2.2 (end)
@@ -32,8 +34,10 @@ Readings taken where the paper is silent (the same conventions the CUDA path
 implements, each written out independently):
 
 * grid = nodes per axis including both wall nodes, n = 0..N, N = grid-1;
-* the diagonal l = n of both weight matrices is 1, also at n = 0 (W+) and
-  n = N (W-), where the l = 0 / l = N end formula would be undefined;
+* the diagonal l = n of both weight matrices is 1, except at the line's first node
+  for W+ (n = 0) and its last node for W- (n = N): there the integral runs over an
+  empty interval (Eqs. Def_FracInt, Def_FracIntspe: ]l, x[ with x = l) and is 0 for
+  alpha < 2 (at alpha = 2, I^0 is the identity and the entry stays 1);
 * a wall node with k unknown incoming populations (edges, corners) gives each
   of them (C_wall - sum of the known populations) / k;
 * the initial populations are the equilibrium of the initial concentration;
@@ -117,7 +121,9 @@ def weight_matrices(gamma, N: int) -> Tuple[torch.Tensor, torch.Tensor]:
       c-_{ln} = (1+g) (N-n)^g - (N-n)^(g+1) + (N-n-1)^(g+1)  l = N
               = (l-n+1)^(g+1) - 2 (l-n)^(g+1) + (l-n-1)^(g+1)  n < l < N
               = 1                                            l = n
-    The l = n rule takes precedence where two cases meet (n = 0 in c+, n = N in c-).
+    At n = 0 (c+) and n = N (c-) the integral is over an empty interval: the row is 0
+    (Eqs. Def_FracInt, Def_FracIntspe; the end formula there would take (-1)^(g+1)), except
+    at g = 0 where I^0 is the identity (Section 1) and the diagonal stays 1.
     ``gamma`` may be a tensor that requires grad.
     """
     g = _as_t(gamma)
@@ -143,12 +149,14 @@ def weight_matrices(gamma, N: int) -> Tuple[torch.Tensor, torch.Tensor]:
 
     a_lo = a[(n_idx - l_idx).clamp(min=0)]
     b_n = b[n_idx]
-    Wp = torch.where(l_idx == n_idx, one,
+    # the end node's own entry: 0 (empty interval) for gamma > 0; I^0 = Id at gamma = 0
+    end_diag = torch.where(g == 0.0, one, zero)
+    Wp = torch.where(l_idx == n_idx, torch.where(n_idx > 0, one, end_diag),
                      torch.where((l_idx == 0) & (n_idx > 0), b_n,
                                  torch.where((l_idx > 0) & (l_idx < n_idx), a_lo, zero)))
     a_up = a[(l_idx - n_idx).clamp(min=0)]
     b_Nn = b[(N - n_idx).clamp(min=0)]
-    Wm = torch.where(l_idx == n_idx, one,
+    Wm = torch.where(l_idx == n_idx, torch.where(n_idx < N, one, end_diag),
                      torch.where((l_idx == N) & (n_idx < N), b_Nn,
                                  torch.where((l_idx > n_idx) & (l_idx < N), a_up, zero)))
     return Wp, Wm
@@ -166,6 +174,29 @@ def frac_matrix(alpha, p, g, N: int, dx: float = 1.0) -> torch.Tensor:
     scale = _as_t(g) * torch.pow(torch.tensor(float(dx), dtype=DT), gamma) / torch.exp(torch.lgamma(2.0 + gamma))
     p = _as_t(p)
     return scale * (p * Wp + (1.0 - p) * Wm)
+
+
+def caputo_boundary_terms(alpha, p, g, N: int, dx: float = 1.0) -> torch.Tensor:
+    """B such that (B c)[n] = g [p c_0 (n dx)^gamma + (1-p) c_N ((N-n) dx)^gamma] / Gamma(1+gamma).
+
+    Section 3.5, Eqs. (PSRLdD-a/b) and (Fg22): along a line from l = z_+ (node 0) to L = z_-
+    (node N), I+^gamma(d/dx f) = d/dx [I+^gamma f - f(l) (x-l)^gamma / Gamma(3-alpha)] and
+    likewise for I- with f(L) (L-x)^gamma; gamma = 2 - alpha, Gamma(3-alpha) = Gamma(1+gamma).
+    The Caputo-type variant F~ puts the bracket in the equilibrium (Eq. CoeffA_FADE3DPS):
+    F~ = (K - B) g c.
+    """
+    gamma = 2.0 - _as_t(alpha)
+    n = torch.arange(N + 1, dtype=DT)
+    den = torch.exp(torch.lgamma(1.0 + gamma))
+    p = _as_t(p)
+    # x^gamma at x = 0 is 0 for gamma > 0 and 1 at gamma = 0 (the bracket f - f(l) of I^0 = Id)
+    at0 = torch.where(gamma == 0.0, torch.ones((), dtype=DT), torch.zeros((), dtype=DT))
+    left = torch.where(n > 0, torch.pow(torch.clamp(n * dx, min=1e-300), gamma), at0)
+    right = torch.where(n < N, torch.pow(torch.clamp((N - n) * dx, min=1e-300), gamma), at0)
+    B = torch.zeros(N + 1, N + 1, dtype=DT)
+    B[:, 0] = B[:, 0] + _as_t(g) * p * left / den
+    B[:, N] = B[:, N] + _as_t(g) * (1.0 - p) * right / den
+    return B
 
 
 def apply_along_axis(K: torch.Tensor, C: torch.Tensor, mu: int) -> torch.Tensor:
@@ -216,6 +247,18 @@ class Operators:
         self.Omega = self._collision_matrix(pb)
         self.K = [frac_matrix(self.alpha[mu], self.p[mu], self.g[mu] * self.h[mu], self.grid[mu] - 1, self.dx)
                   for mu in range(d)]
+        self._caputo(pb)
+
+    def _caputo(self, pb):
+        """Section 3.5: with the Caputo-type variant F~ (pb.variant == "caputo") the operator
+        along each axis is K - B (caputo_boundary_terms), g (and BGK's h) as in K."""
+        self.variant = getattr(pb, "variant", "fg")
+        if self.variant == "caputo":
+            gfac = [1.0] * self.d if self.fields else [self.g[mu] * self.h[mu] for mu in range(self.d)]
+            self.K = [self.K[mu] - caputo_boundary_terms(self.alpha[mu], self.p[mu], gfac[mu], self.grid[mu] - 1,
+                                                         self.dx) for mu in range(self.d)]
+        elif self.variant != "fg":
+            raise ValueError("variant must be 'fg' (Eq. Fg) or 'caputo' (Eq. Fg2)")
 
     def _set_fields(self, pb, fields):
         """Coefficients that depend on the node (Section 1: D and g may depend on x).
@@ -262,6 +305,7 @@ class Operators:
             self.Omega = Om.movedim(-1, 0).movedim(-1, 0)           # (Q, Q, *shape)
         self.K = [frac_matrix(self.alpha[mu], self.p[mu], 1.0, self.grid[mu] - 1, self.dx) for mu in range(d)]
         self.fields = True
+        self._caputo(pb)
 
     def _collision_matrix(self, pb) -> torch.Tensor:
         """Omega such that the collision is f - Omega (f - feq).

@@ -48,6 +48,7 @@ class Problem:
                  non-conserved, non-flux moments (D2Q5: 2 values, D3Q7: 3)
     dx, dt     : space and time steps
     C_wall     : Dirichlet value imposed on every wall node
+    variant    : "fg" (fractional term of Eq. Fg) or "caputo" (Caputo-type F~, Eq. Fg2)
     """
 
     d: int
@@ -62,6 +63,7 @@ class Problem:
     dx: float = 1.0
     dt: float = 1.0
     C_wall: float = 0.0
+    variant: str = "fg"
 
     @property
     def shape(self) -> Tuple[int, ...]:

@@ -85,15 +85,14 @@ def test_frac_integral_exact_on_linear_functions(gamma, N):
     got_p1, got_px = Kp @ one, Kp @ x
     want_p1 = x ** gamma / math.gamma(1 + gamma)
     want_px = x ** (gamma + 1) / math.gamma(2 + gamma)
-    # node n = 0: the integral over an empty interval is 0; the l = n rule gives
-    # the node value times dx^g/Gamma(2+g) there instead (reading C2), so skip n = 0
-    assert torch.allclose(got_p1[1:], want_p1[1:], rtol=1e-12, atol=1e-14)
-    assert torch.allclose(got_px[1:], want_px[1:], rtol=1e-12, atol=1e-14)
+    # every node, the ends included: at n = 0 (I+) and n = N (I-) the interval is empty
+    assert torch.allclose(got_p1, want_p1, rtol=1e-12, atol=1e-14)
+    assert torch.allclose(got_px, want_px, rtol=1e-12, atol=1e-14)
     got_m1, got_mx = Km @ one, Km @ (L - x)
     want_m1 = (L - x) ** gamma / math.gamma(1 + gamma)
     want_mx = (L - x) ** (gamma + 1) / math.gamma(2 + gamma)
-    assert torch.allclose(got_m1[:-1], want_m1[:-1], rtol=1e-12, atol=1e-14)
-    assert torch.allclose(got_mx[:-1], want_mx[:-1], rtol=1e-12, atol=1e-14)
+    assert torch.allclose(got_m1, want_m1, rtol=1e-12, atol=1e-14)
+    assert torch.allclose(got_mx, want_mx, rtol=1e-12, atol=1e-14)
 
 
 @pytest.mark.parametrize("gamma", [0.2, 0.5, 0.8])
@@ -713,6 +712,69 @@ def test_time_dependent_wall_values_imposed(grid):
         assert np.max(np.abs(C[wall] - want[wall])) < 1e-15
 
 
+# --------------------------------------------------------------------------- Caputo-type variant
+
+@pytest.mark.parametrize("gamma", [0.0, 0.2, 0.5, 0.8])
+@pytest.mark.parametrize("p", [0.0, 0.3, 1.0])
+def test_caputo_operator_exact_on_constants_and_linear_functions(gamma, p):
+    """Section 3.5, Eq. (PSRL1D): the bracket I+^g f - f(l) (x-l)^g / Gamma(1+g) vanishes on
+    constants (uniform equilibria exist) and equals b x^(g+1)/Gamma(2+g) on f = a + b x;
+    mirrored for I- with f(L).  Product integration is exact on linear f: every node."""
+    N, dx = 23, 0.11
+    x = torch.arange(N + 1, dtype=torch.float64) * dx
+    L = N * dx
+    Kt = O.frac_matrix(2.0 - gamma, p, 1.0, N, dx) - O.caputo_boundary_terms(2.0 - gamma, p, 1.0, N, dx)
+    assert torch.max(torch.abs(Kt @ torch.full((N + 1,), 3.7, dtype=torch.float64))) < 1e-13
+    f = 0.4 + 1.3 * x
+    want = p * 1.3 * x ** (gamma + 1) / math.gamma(2 + gamma) + (1 - p) * (-1.3) * (L - x) ** (gamma + 1) / math.gamma(2 + gamma)
+    assert torch.allclose(Kt @ f, want, rtol=1e-12, atol=1e-13)
+
+
+def _caputo_case(N, T=0.1, variant="caputo", alpha=(1.7, 1.2), a=(0.3, 1.2)):
+    """Section 3.5's check: D = 1, g = 1, u = 0, p = 1 on ]0,1[^2, C = exp(-t) prod (x^alpha + a)
+    with the source of Eq. (SourceTerm_PS) and initial / wall values from C; MRT, lambda = 1."""
+    dx = 1.0 / N
+    dt = 0.5 * (1.0 / 3.0) * dx * dx
+    n = int(round(T / dt))
+    dt = T / n
+    x = np.arange(N + 1) * dx
+    X = np.broadcast_to(x[None, :], (N + 1, N + 1))
+    Y = np.broadcast_to(x[:, None], (N + 1, N + 1))
+    px, py = X ** alpha[0] + a[0], Y ** alpha[1] + a[1]
+    prof = px * py
+    S = -(prof + math.gamma(alpha[0] + 1) * py + math.gamma(alpha[1] + 1) * px)
+    pb = W.Problem(d=2, collision="mrt", grid=(N + 1, N + 1), alpha=alpha, p=(1.0, 1.0), g=(1.0, 1.0),
+                   D=((1.0, 0.0), (0.0, 1.0)), u=(0.0, 0.0), s_free=(1.2, 1.2), dx=dx, dt=dt, variant=variant)
+    ops = O.with_source_and_walls(O.Operators(pb), source=(S, -1.0), walls=(prof, -1.0))
+    f = O.init_populations(ops, torch.tensor(prof))
+    for k in range(n):
+        f = O.step(ops, f, k)
+    exact = math.exp(-T) * prof
+    return float(np.linalg.norm(O.concentration(f).numpy() - exact) / np.linalg.norm(exact))
+
+
+def test_caputo_variant_exact_solution():
+    """Section 3.5 (Eqs. Fg22, CoeffA_FADE3DPS, SourceTerm_PS): the variant's equilibrium
+    retrieves C = exp(-t) prod (x^alpha + a), second order in dx (4e-4 at dx = 1/20, 1.2e-4 at
+    1/40); the Riemann-Liouville-type equilibrium (Eq. CoeffA_FADE3D) misses it by > 5%."""
+    e20, e40 = _caputo_case(20), _caputo_case(40)
+    assert e40 < 3e-4 and e40 < 0.4 * e20
+    assert _caputo_case(20, variant="fg") > 5e-2
+
+
+def test_caputo_variant_keeps_uniform_equilibria():
+    """A uniform C with the same wall value and no source stays uniform under F~ (Section 3.5:
+    the variant admits equilibria independent of x), not under F (alpha < 2)."""
+    rng = np.random.default_rng(71)
+    pb = dataclasses.replace(W.random_problem(rng, 2, "mrt", (30, 24)), C_wall=0.7, variant="caputo")
+    pb = dataclasses.replace(pb, u=(0.0, 0.0))
+    C0 = np.full(pb.shape, 0.7)
+    C = O.run_C(pb, C0, 40).numpy()
+    assert np.max(np.abs(C - 0.7)) < 1e-12
+    C_rl = O.run_C(dataclasses.replace(pb, variant="fg"), C0, 40).numpy()
+    assert np.max(np.abs(C_rl - 0.7)) > 1e-3
+
+
 # --------------------------------------------------------------------------- killed stable walk
 
 @pytest.mark.parametrize("alpha,beta", [(1.5, 0.0), (1.5, -0.4), (1.7, 0.6), (1.2, 1.0), (2.0, 0.3)])
@@ -787,6 +849,60 @@ def test_killed_stable_walk_matches_the_oracle():
     import dataclasses
     C_swapped = O.run_C(dataclasses.replace(pb, p=(1 - p[0], 1 - p[1])), C0, nsteps).numpy()
     assert zmax(C_swapped) > 2.5
+
+
+def test_philox_known_answers():
+    """Philox4x32-10 written from its definition reproduces the generator's published
+    known-answer vectors (tests/golden/philox4x32_10_kat.txt)."""
+    from oracle import levy_walk as LW
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = LW.philox4x32_10(*v[:6])
+        assert [int(o) for o in out] == v[6:]
+
+
+@pytest.mark.parametrize("bits", [32, 24])
+def test_philox_uniforms_are_uniform_on_the_open_interval(bits):
+    from oracle import levy_walk as LW
+    idx = np.arange(200_000, dtype=np.uint64)
+    u1, u2 = LW.philox_uniforms(idx, 17, 1, 12345, bits)
+    for u in (u1, u2):
+        assert 0.0 < u.min() and u.max() < 1.0
+        assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / u.size)
+        assert abs(u.var() - 1 / 12) < 5e-3 / 12
+    # different steps, axes and seeds give different streams
+    v1, _ = LW.philox_uniforms(idx[:1000], 18, 1, 12345, bits)
+    w1, _ = LW.philox_uniforms(idx[:1000], 17, 0, 12345, bits)
+    assert not np.array_equal(u1[:1000], v1) and not np.array_equal(u1[:1000], w1)
+
+
+def test_killed_walk_with_philox_draws_matches_the_oracle():
+    """The killed walk driven by the Philox uniforms (the draws the GPU walk replays) also
+    matches the lattice Boltzmann oracle (same comparison as with NumPy's generator)."""
+    from oracle import levy_walk as LW
+    p = (0.3, 0.8)
+    pb, C0, nsteps, sig = _killed_walk_case(p)
+    dx = pb.dx
+    C = O.run_C(pb, C0, nsteps).numpy()
+    mass = float(C.sum()) * dx * dx
+    rng = np.random.default_rng(2018)
+    n = 100_000
+    X0 = np.stack([rng.normal(0.5, sig, n), rng.normal(0.5, sig, n)], 1)
+    alive0 = np.all((X0 > 0) & (X0 < 1), axis=1)
+    X, alive = LW.killed_walk_philox(X0, alive0, pb.alpha, pb.p, [pb.D[0][0], pb.D[1][1]], pb.g, pb.u,
+                                     (0.0, 0.0), (1.0, 1.0), pb.dt, 99, 0, nsteps)
+    surv = float(alive.mean())
+    assert abs(surv - mass) < 4.0 * math.sqrt(surv * (1 - surv) / n) + 2e-3, (surv, mass)
+    N = pb.grid[0] - 1
+    edges = (np.arange(N + 2) - 0.5) * dx
+    for mu in range(2):
+        hist = np.histogram(X[alive][:, mu], bins=edges)[0][1:-1] / n / dx
+        marg = (C.sum(axis=0) if mu == 0 else C.sum(axis=1))[1:-1] * dx
+        se = np.sqrt(np.maximum(hist, 1e-3) * dx / n) / dx
+        assert np.all(np.abs(hist - marg) < 4.0 * se + 0.02 * marg.max())
 
 
 def test_checkpointed_gradient_equals_plain_adjoint():
