@@ -577,6 +577,51 @@ def run_reference(args):
     return 0
 
 
+def measure_walk(lbm, torch, steps=3, warmup=1):
+    """The killed stable-Levy walk (Section 3.1), the paper's Monte-Carlo counterpart: 2^24
+    FP32 paths x 200 increments on the [0,1]^2 case of the oracle's walk pin (alpha = (1.5,
+    1.7), p = (0.3, 0.8), D = 0.1, dt = 1/9600), timed with CUDA events; the FP64 form on 2^20
+    paths; parity with the oracle's walk (same Philox draws) on 4096 paths."""
+    from oracle import levy_walk as LW
+    alpha, p, D, g, u = (1.5, 1.7), (0.3, 0.8), (0.1, 0.1), (1.0, 1.0), (0.0, 0.0)
+    dt, nsteps = 0.5 * (1.0 / 3.0) / 1600.0 / 0.1, 200
+    out = {"desc": "killed stable-Levy walk, 2-D, box ]0,1[^2, alpha=(1.5,1.7), p=(0.3,0.8), D=0.1, "
+                   "dt=1/9600, 200 increments per launch, Philox4x32-10 draws", "unit": "Mpath-steps/s"}
+    for prec, n in (("fp32", 1 << 24), ("fp64", 1 << 20)):
+        prm = lbm.walk_params(2, alpha, p, D, g, u, (0.0, 0.0), (1.0, 1.0), dt, 11, prec)
+        gen = torch.Generator(device="cuda").manual_seed(3)
+        X0 = (0.5 + 0.08 * torch.randn((2, n), dtype=torch.float64, device="cuda", generator=gen)).contiguous()
+        A0 = ((X0 > 0) & (X0 < 1)).all(0).to(torch.uint8)
+        X, A = X0.clone(), A0.clone()
+        times = []
+        for k in range(warmup + steps):
+            X.copy_(X0)
+            A.copy_(A0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            lbm.lbm_walk(prm, n, X.data_ptr(), A.data_ptr(), 0, nsteps, torch.cuda.current_stream().cuda_stream)
+            e1.record()
+            e1.synchronize()
+            if k >= warmup:
+                times.append(e0.elapsed_time(e1))
+        ms = sum(times) / len(times)
+        out[prec] = {"paths": n, "increments": nsteps, "ms_per_launch": ms,
+                     "value": n * nsteps / (ms * 1e-3) / 1e6, "survivors": float(A.float().mean())}
+        # parity on the first 4096 paths against the oracle's walk with the same draws
+        m = 4096
+        Xs = X0[:, :m].cpu().numpy().T
+        As = A0[:m].cpu().numpy().astype(bool)
+        X_ref, A_ref = LW.killed_walk_philox(Xs, As, alpha, p, D, g, u, (0, 0), (1, 1), dt, 11, 0, nsteps,
+                                             bits=24 if prec == "fp32" else 32)
+        Xg = X[:, :m].cpu().numpy().T
+        Ag = A[:m].cpu().numpy().astype(bool)
+        both = Ag & A_ref
+        out[prec]["vs_oracle_walk"] = {"paths": m, "max_abs_position_err": float(np.max(np.abs(Xg[both] - X_ref[both]))),
+                                       "kill_decisions_differing": int(np.count_nonzero(Ag != A_ref))}
+    return out
+
+
 def measure_extra(lbm, torch, name, flush, peaks, peak_src, autotune, steps=2, warmup=1):
     """One entry of the `workloads` block: MLUPS (device and e2e), both rooflines and
     accuracy against an oracle sample (or, for the inverse problem, the gradient against
@@ -748,6 +793,10 @@ def main():
                 extra[name] = measure_extra(lbm, torch, name, flush, peaks, peak_src, not args.no_autotune)
             except Exception as exc:  # reported, not hidden: the entry says what failed
                 extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        try:
+            extra["levy_walk"] = measure_walk(lbm, torch)
+        except Exception as exc:
+            extra["levy_walk"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

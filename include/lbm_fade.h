@@ -79,6 +79,8 @@ enum {
                               LBM_FP32_BF16SPLIT5. */
 };
 
+enum { LBM_VARIANT_FG = 0, LBM_VARIANT_CAPUTO = 1 };  /* Eq. (Fg) / Eq. (Fg2) */
+
 typedef struct {
   int lattice;        /* LBM_D2Q5 or LBM_D3Q7 */
   int collision;      /* LBM_BGK or LBM_MRT */
@@ -96,6 +98,11 @@ typedef struct {
                          (Eq. MatrixS; D2Q5 uses 2, D3Q7 uses 3), each in ]0,2[ */
   double dx, dt;      /* space and time steps (> 0) */
   double C_wall;      /* Dirichlet concentration imposed on every wall node (Eq. Dirichlet_BC) */
+  int variant;        /* LBM_VARIANT_FG: equilibrium moment F of Eq. (Fg), the Riemann-Liouville
+                         form; LBM_VARIANT_CAPUTO: F~ of Eq. (Fg2) (Section 3.5), each integral
+                         less its boundary term f(end) (distance)^gamma / Gamma(1+gamma), which
+                         gives the Caputo-type FADE of Eq. (Fg22) and admits uniform equilibria.
+                         Zero-initialised parameters select LBM_VARIANT_FG. */
 } lbm_params;
 
 /* Create a problem and initialise it from C0.
@@ -293,6 +300,43 @@ int lbm_set_source(lbm_t h, const double* S_field, double rate);
  * constant C_wall of lbm_params.  Otherwise as lbm_set_source. */
 int lbm_set_wall_values(lbm_t h, const double* Cw_field, double rate);
 
+/* Killed stable-Levy random walk (Section 3.1: Eqs. RW_STABLE and distri; the bounded-domain
+ * subsection: a path is killed at its first exit from the box), the paper's Monte-Carlo
+ * counterpart of the scheme.  The density of the live paths solves the FADE with
+ * D'_mumu = (D_mumu g_mu)^(1/alpha_mu), beta_mu = 2 p_mu - 1 and C = 0 on the box's walls. */
+typedef struct {
+  int d;                    /* 2 or 3 */
+  int precision;            /* LBM_FP64: FP64 arithmetic, uniforms (o + 1/2) 2^-32;
+                               LBM_FP32: FP32 arithmetic, uniforms ((o >> 8) + 1/2) 2^-24 */
+  double alpha[3];          /* ]1,2] per axis */
+  double p[3];              /* [0,1] per axis (skewness beta = 2p - 1) */
+  double D[3], g[3];        /* > 0 per axis */
+  double u[3];              /* drift per axis */
+  double lo[3], hi[3];      /* the box ]lo, hi[ */
+  double dt;                /* > 0 */
+  unsigned long long seed;  /* Philox4x32-10 key */
+} lbm_walk_params;
+
+/* Advance n paths by nsteps increments, steps step0 .. step0 + nsteps - 1 of their draws
+ * (Philox4x32-10, counter (i mod 2^32, i div 2^32, step, call), key = seed: a run split over
+ * several calls gives the same paths as one call).  S(alpha, beta) from two uniforms by
+ * Chambers-Mallows-Stuck / Weron (1996).
+ *   X:     device array of d*n doubles, [mu][i] (in/out); a killed path keeps its exit position
+ *   alive: device array of n bytes (in/out): paths with 0 are not moved; a path that leaves the
+ *          box gets 0
+ * Both caller-owned (the call allocates nothing).  Asynchronous on `stream` (NULL: legacy
+ * default).  LBM_EINVAL for parameters outside the ranges above, n < 0, nsteps < 0, step0 < 0
+ * or step0 + nsteps > 2^32 - 1; LBM_ECUDA if the launch fails. */
+int lbm_walk(const lbm_walk_params* prm, long long n, double* X, unsigned char* alive, long long step0, int nsteps,
+             void* stream);
+
+/* Histogram of the live paths on a lattice: counts[node] (device, caller-owned, not cleared)
+ * += the live paths whose position lies in the cell of width dx centred at the node, nodes at
+ * lo + k dx, k = 0..grid[mu]-1, node index x fastest (field layout above).  With n paths the
+ * density at a node is counts / (n dx^d).  Asynchronous; LBM_EINVAL for bad arguments. */
+int lbm_walk_density(const lbm_walk_params* prm, long long n, const double* X, const unsigned char* alive,
+                     const int* grid, double dx, unsigned int* counts, void* stream);
+
 /* Wait for all work of the handle; return a latched device error if any. */
 int lbm_sync(lbm_t h);
 
@@ -317,7 +361,12 @@ int lbm_launches_per_step(lbm_t h, int* n);
 /* Host-only: the (grid[mu])^2 FP64 matrix K_mu, row-major K[n*side + l], such that
  * F_mu[n] = sum_l K[n][l] C[l] along each lattice line of axis mu, i.e.
  * K = g h dx^gamma / Gamma(2+gamma) * (p W+ + (1-p) W-) with gamma = 2 - alpha
- * (Eqs. 1Dminus_discret, c+, c-).  Needs no GPU. */
+ * (Eqs. 1Dminus_discret, c+, c-).  W+ and W- hold 1 on the diagonal except at the
+ * line's own end (W+ at n = 0, W- at n = N), where the integral runs over an empty
+ * interval and the entry is 0 for alpha < 2.  With variant LBM_VARIANT_CAPUTO the
+ * matrix is K - B (Section 3.5, Eqs. PSRLdD-a/b, Fg22): column 0 loses
+ * g h p (n dx)^gamma / Gamma(1+gamma) and column N loses
+ * g h (1-p) ((N-n) dx)^gamma / Gamma(1+gamma), so K~ maps constants to 0.  Needs no GPU. */
 int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host);
 
 /* FP64 sum of n device values (elem_bytes 4: float, 8: double) written to *sum_dev,
@@ -375,7 +424,9 @@ int lbm_grad(lbm_t h, int nsnap, const int* snap_steps, const double* obs, int c
  * p_mu, FP64, row-major (grid[mu])^2 each.  With gamma = 2 - alpha:
  * dK/dp = s (W+ - W-), dK/dalpha = -d/dgamma [ s (p W+ + (1-p) W-) ],
  * s = g h dx^gamma / Gamma(2+gamma), ds/dgamma = s (ln dx - psi(2+gamma))
- * (Eqs. 1Dminus_discret, c+, c- differentiated in gamma).  Needs no GPU. */
+ * (Eqs. 1Dminus_discret, c+, c- differentiated in gamma); with LBM_VARIANT_CAPUTO the
+ * boundary terms' derivatives are included (d/dgamma of x^gamma / Gamma(1+gamma) is
+ * x^gamma (ln x - psi(1+gamma)) / Gamma(1+gamma)).  Needs no GPU. */
 int lbm_frac_matrix_grad(const lbm_params* prm, int mu, double* dK_dalpha, double* dK_dp);
 
 /* Host-only: digamma psi(x), x > 0 (recurrence + asymptotic series, Abramowitz &

@@ -130,6 +130,7 @@ int derive(const lbm_params* p, Derived* out) {
   const int Q = 2 * d + 1;
   if (!(p->dx > 0.0) || !(p->dt > 0.0) || !std::isfinite(p->dx) || !std::isfinite(p->dt)) return LBM_EINVAL;
   if (!std::isfinite(p->C_wall)) return LBM_EINVAL;
+  if (p->variant != LBM_VARIANT_FG && p->variant != LBM_VARIANT_CAPUTO) return LBM_EINVAL;
   for (int mu = 0; mu < 3; ++mu) {
     if (mu < d) {
       if (p->grid[mu] < 3) return LBM_EINVAL;
@@ -432,7 +433,7 @@ static int upload_weights(lbm_s* h, const double* hfac, std::vector<std::vector<
     K.assign((size_t)side * side, 0.0);
     KT.assign((size_t)side * side, 0.0);
     const double scale = h->fld.on ? 1.0 : prm->g[mu] * hfac[mu];
-    lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], scale, side, prm->dx, K.data());
+    lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], scale, side, prm->dx, prm->variant, K.data());
     for (int n = 0; n < side; ++n)
       for (int l = 0; l < side; ++l) KT[(size_t)l * side + n] = K[(size_t)n * side + l];
     const size_t cnt = (size_t)side * side;
@@ -1354,7 +1355,8 @@ int lbm_frac_matrix(const lbm_params* prm, int mu, double* K_host) {
   if (rc) return rc;
   const int d = (prm->lattice == LBM_D2Q5) ? 2 : 3;
   if (mu < 0 || mu >= d) return LBM_EINVAL;
-  lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], prm->g[mu] * dv.h[mu], prm->grid[mu], prm->dx, K_host);
+  lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], prm->g[mu] * dv.h[mu], prm->grid[mu], prm->dx, prm->variant,
+                         K_host);
   return LBM_OK;
 }
 
@@ -1383,7 +1385,8 @@ int lbm_grad(lbm_t h, int nsnap, const int* snap_steps, const double* obs, int c
   for (int mu = 0; mu < d; ++mu) {
     const int side = h->sp.n[mu];
     std::vector<double> da((size_t)side * side), dp((size_t)side * side);
-    lbm::build_frac_matrix_grad(h->prm.alpha[mu], h->prm.p[mu], h->prm.g[mu], side, h->prm.dx, da.data(), dp.data());
+    lbm::build_frac_matrix_grad(h->prm.alpha[mu], h->prm.p[mu], h->prm.g[mu], side, h->prm.dx, h->prm.variant, da.data(),
+                                dp.data());
     double sa = 0.0, sp_ = 0.0;
     for (size_t i = 0; i < da.size(); ++i) {
       sa += da[i] * G[goff + i];
@@ -1405,8 +1408,8 @@ int lbm_frac_matrix_grad(const lbm_params* prm, int mu, double* dK_dalpha, doubl
   if (rc) return rc;
   const int d = (prm->lattice == LBM_D2Q5) ? 2 : 3;
   if (mu < 0 || mu >= d) return LBM_EINVAL;
-  lbm::build_frac_matrix_grad(prm->alpha[mu], prm->p[mu], prm->g[mu] * dv.h[mu], prm->grid[mu], prm->dx, dK_dalpha,
-                              dK_dp);
+  lbm::build_frac_matrix_grad(prm->alpha[mu], prm->p[mu], prm->g[mu] * dv.h[mu], prm->grid[mu], prm->dx, prm->variant,
+                              dK_dalpha, dK_dp);
   return LBM_OK;
 }
 

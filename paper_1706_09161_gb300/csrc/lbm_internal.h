@@ -242,9 +242,10 @@ void tc_release(lbm_s* h);
 int tc_split_pitch(const lbm_s* h);
 
 // host-side weight build (FP64), K row-major [n][l] for one axis
-void build_frac_matrix(double alpha, double p, double scale_g, int side, double dx, double* K);
+void build_frac_matrix(double alpha, double p, double scale_g, int side, double dx, int variant, double* K);
 // its derivatives dK/dalpha and dK/dp (FP64, same layout)
-void build_frac_matrix_grad(double alpha, double p, double scale_g, int side, double dx, double* dKda, double* dKdp);
+void build_frac_matrix_grad(double alpha, double p, double scale_g, int side, double dx, int variant, double* dKda,
+                            double* dKdp);
 double digamma_fn(double x);
 
 // adjoint driver (adjoint.cu); the handle's own reset and step are passed in

@@ -8,7 +8,12 @@
 // c+ and c- are Toeplitz apart from their end columns (l = 0 for c+, l = N for c-):
 //   interior  a(k) = (k+1)^s - 2 k^s + (k-1)^s,  k = |n-l| >= 1, s = g+1
 //   end       b(m) = (1+g) m^g - m^s + (m-1)^s,  m = n (c+) or N-n (c-)
-//   diagonal  1.
+//   diagonal  1, except at the line's own end: I+ at n = 0 and I- at n = N integrate
+//             over an empty interval (Eqs. Def_FracInt, Def_FracIntspe), so that entry
+//             is 0 for g > 0; at g = 0 (alpha = 2) I^0 is the identity and it stays 1.
+// The Caputo-type variant (Section 3.5, Eqs. Fg2, PSRLdD-a/b, Fg22) subtracts the
+// boundary terms p f(0) (n dx)^g / Gamma(1+g) and (1-p) f(N dx) ((N-n) dx)^g / Gamma(1+g),
+// i.e. columns 0 and N of K change; 0^0 = 1 keeps constants in the kernel at g = 0 too.
 // Both a(k) and b(m) are small differences of large powers; for large k, m they
 // are summed from their binomial series instead, so that every entry keeps
 // nearly full FP64 relative accuracy (the direct form loses ~2 log10(k) digits).
@@ -95,7 +100,8 @@ double digamma_fn(double x) { return digamma(x); }
 //   d b(m)/dgamma = m^g + (1+g) m^g ln m - m^s ln m + (m-1)^s ln(m-1).
 // The direct second differences lose ~2 log10(k) digits, far below the precision the
 // gradients are used at.
-void build_frac_matrix_grad(double alpha, double p, double scale_g, int side, double dx, double* dKda, double* dKdp) {
+void build_frac_matrix_grad(double alpha, double p, double scale_g, int side, double dx, int variant, double* dKda,
+                            double* dKdp) {
   const double g = 2.0 - alpha;
   const double s = g + 1.0;
   const long N = side - 1;
@@ -116,8 +122,8 @@ void build_frac_matrix_grad(double alpha, double p, double scale_g, int side, do
     for (long l = 0; l <= N; ++l) {
       double wp = 0.0, wm = 0.0, dwp = 0.0, dwm = 0.0;
       if (l == n) {
-        wp = 1.0;
-        wm = 1.0;
+        wp = (n > 0 || g == 0.0) ? 1.0 : 0.0;
+        wm = (n < N || g == 0.0) ? 1.0 : 0.0;
       } else if (l < n) {
         wp = (l == 0) ? b[n] : a[n - l];
         dwp = (l == 0) ? db[n] : da[n - l];
@@ -129,9 +135,25 @@ void build_frac_matrix_grad(double alpha, double p, double scale_g, int side, do
       dKda[n * side + l] = -(dscale * (p * wp + (1.0 - p) * wm) + scale * (p * dwp + (1.0 - p) * dwm));
     }
   }
+  if (variant) {
+    // K~ = K - B, B = scale_g [p e_0 (n dx)^g + (1-p) e_N ((N-n) dx)^g] / Gamma(1+g):
+    // dB/dp from the two weights, dB/dalpha = -dB/dg = -B (ln(x) - psi(1+g)) per entry
+    const double den = std::tgamma(1.0 + g);
+    const double psi = digamma(1.0 + g);
+    for (long n = 0; n <= N; ++n) {
+      const double xl = n * dx, xr = (N - n) * dx;
+      const double tl = scale_g * std::pow(xl, g) / den, tr = scale_g * std::pow(xr, g) / den;
+      const double dtl = (xl > 0.0) ? tl * (std::log(xl) - psi) : 0.0;
+      const double dtr = (xr > 0.0) ? tr * (std::log(xr) - psi) : 0.0;
+      dKdp[n * side] -= tl;
+      dKdp[n * side + N] += tr;
+      dKda[n * side] += p * dtl;
+      dKda[n * side + N] += (1.0 - p) * dtr;
+    }
+  }
 }
 
-void build_frac_matrix(double alpha, double p, double scale_g, int side, double dx, double* K) {
+void build_frac_matrix(double alpha, double p, double scale_g, int side, double dx, int variant, double* K) {
   const double g = 2.0 - alpha;          // order of the fractional integral
   const double s = g + 1.0;
   const long N = side - 1;
@@ -143,14 +165,21 @@ void build_frac_matrix(double alpha, double p, double scale_g, int side, double 
     for (long l = 0; l <= N; ++l) {
       double wp = 0.0, wm = 0.0;
       if (l == n) {
-        wp = 1.0;
-        wm = 1.0;
+        wp = (n > 0 || g == 0.0) ? 1.0 : 0.0;
+        wm = (n < N || g == 0.0) ? 1.0 : 0.0;
       } else if (l < n) {
         wp = (l == 0) ? b[n] : a[n - l];
       } else {
         wm = (l == N) ? b[N - n] : a[l - n];
       }
       K[n * side + l] = scale * (p * wp + (1.0 - p) * wm);
+    }
+  }
+  if (variant) {
+    const double den = std::tgamma(1.0 + g);
+    for (long n = 0; n <= N; ++n) {
+      K[n * side] -= scale_g * p * std::pow(n * dx, g) / den;
+      K[n * side + N] -= scale_g * (1.0 - p) * std::pow((N - n) * dx, g) / den;
     }
   }
 }

@@ -30,6 +30,8 @@ LBM_BGK, LBM_MRT = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP32_BF16SPLIT, LBM_FP32_TF32SPLIT, LBM_FP32_BF16SPLIT5, LBM_FP32_BF16SPLIT6 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16split": LBM_FP32_BF16SPLIT, "tf32split": LBM_FP32_TF32SPLIT,
               "bf16x5split": LBM_FP32_BF16SPLIT5, "bf16x6split": LBM_FP32_BF16SPLIT6}
+LBM_VARIANT_FG, LBM_VARIANT_CAPUTO = 0, 1
+VARIANTS = {"fg": LBM_VARIANT_FG, "caputo": LBM_VARIANT_CAPUTO}
 
 
 class lbm_params(ctypes.Structure):
@@ -47,6 +49,23 @@ class lbm_params(ctypes.Structure):
         ("dx", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("C_wall", ctypes.c_double),
+        ("variant", ctypes.c_int),
+    ]
+
+
+class lbm_walk_params(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("alpha", ctypes.c_double * 3),
+        ("p", ctypes.c_double * 3),
+        ("D", ctypes.c_double * 3),
+        ("g", ctypes.c_double * 3),
+        ("u", ctypes.c_double * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("dt", ctypes.c_double),
+        ("seed", ctypes.c_ulonglong),
     ]
 
 
@@ -89,6 +108,10 @@ def _load() -> ctypes.CDLL:
         "lbm_set_fields": (ctypes.c_int, [vp, dp, dp, dp]),
         "lbm_set_source": (ctypes.c_int, [vp, dp, ctypes.c_double]),
         "lbm_set_wall_values": (ctypes.c_int, [vp, dp, ctypes.c_double]),
+        "lbm_walk": (ctypes.c_int, [P(lbm_walk_params), ctypes.c_longlong, vp, vp, ctypes.c_longlong, ctypes.c_int,
+                                    vp]),
+        "lbm_walk_density": (ctypes.c_int, [P(lbm_walk_params), ctypes.c_longlong, vp, vp, P(ctypes.c_int),
+                                            ctypes.c_double, vp, vp]),
         "lbm_sync": (ctypes.c_int, [vp]),
         "lbm_get_stream": (ctypes.c_int, [vp, P(vp)]),
         "lbm_launches_per_step": (ctypes.c_int, [vp, P(ctypes.c_int)]),
@@ -115,7 +138,7 @@ _lib = _load()
 # Declared C entry points, re-exported under their own names.
 EXPORTED = ("lbm_create", "lbm_create_batch", "lbm_batch_size", "lbm_batch_set_C", "lbm_set_C", "lbm_reset", "lbm_step", "lbm_profile", "lbm_read_C", "lbm_read_F", "lbm_read_f", "lbm_write_f", "lbm_state_size", "lbm_save", "lbm_load", "lbm_autotune", "lbm_configure",
             "lbm_mass", "lbm_set_mass_limit", "lbm_set_fields", "lbm_set_source", "lbm_set_wall_values",
-            "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_wait_check", "lbm_set_allocator",
+            "lbm_walk", "lbm_walk_density", "lbm_sync", "lbm_get_stream", "lbm_launches_per_step", "lbm_wait_check", "lbm_set_allocator",
             "lbm_frac_matrix",
             "lbm_grad", "lbm_frac_matrix_grad", "lbm_digamma", "lbm_mass_static", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error")
 
@@ -158,6 +181,7 @@ def params_from_problem(pb, precision: str = "fp32") -> lbm_params:
     prm.dx = float(getattr(pb, "dx", 1.0))
     prm.dt = float(getattr(pb, "dt", 1.0))
     prm.C_wall = float(getattr(pb, "C_wall", 0.0))
+    prm.variant = VARIANTS[getattr(pb, "variant", "fg")]
     return prm
 
 
@@ -297,6 +321,39 @@ def lbm_set_wall_values(h: int, Cw=None, rate: float = 0.0) -> None:
     a = None if Cw is None else np.ascontiguousarray(Cw, dtype=np.float64)
     _check(_lib.lbm_set_wall_values(ctypes.c_void_p(h), None if a is None else _dptr(a), float(rate)),
            "lbm_set_wall_values")
+
+
+def walk_params(d: int, alpha, p, D, g, u, lo, hi, dt: float, seed: int, precision: str = "fp32") -> lbm_walk_params:
+    prm = lbm_walk_params()
+    prm.d = int(d)
+    prm.precision = PRECISIONS[precision]
+    for mu in range(3):
+        ok = mu < d
+        prm.alpha[mu] = float(alpha[mu]) if ok else 2.0
+        prm.p[mu] = float(p[mu]) if ok else 0.5
+        prm.D[mu] = float(D[mu]) if ok else 1.0
+        prm.g[mu] = float(g[mu]) if ok else 1.0
+        prm.u[mu] = float(u[mu]) if ok else 0.0
+        prm.lo[mu] = float(lo[mu]) if ok else 0.0
+        prm.hi[mu] = float(hi[mu]) if ok else 1.0
+    prm.dt = float(dt)
+    prm.seed = int(seed)
+    return prm
+
+
+def lbm_walk(prm: lbm_walk_params, n: int, X_ptr: int, alive_ptr: int, step0: int, nsteps: int,
+             stream: Optional[int] = None) -> None:
+    """Advance n paths (device arrays by address: X [d][n] float64, alive uint8) by nsteps."""
+    _check(_lib.lbm_walk(ctypes.byref(prm), int(n), ctypes.c_void_p(X_ptr), ctypes.c_void_p(alive_ptr), int(step0),
+                         int(nsteps), ctypes.c_void_p(stream or 0)), "lbm_walk")
+
+
+def lbm_walk_density(prm: lbm_walk_params, n: int, X_ptr: int, alive_ptr: int, grid, dx: float, counts_ptr: int,
+                     stream: Optional[int] = None) -> None:
+    g = (ctypes.c_int * 3)(*[int(v) for v in list(grid) + [1] * (3 - len(grid))])
+    _check(_lib.lbm_walk_density(ctypes.byref(prm), int(n), ctypes.c_void_p(X_ptr), ctypes.c_void_p(alive_ptr), g,
+                                 float(dx), ctypes.c_void_p(counts_ptr), ctypes.c_void_p(stream or 0)),
+           "lbm_walk_density")
 
 
 def lbm_sync(h: int) -> int:

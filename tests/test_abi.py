@@ -134,6 +134,39 @@ def test_host_weight_matrix_derivatives_match_oracle_autograd(L, side, alpha, p,
     assert float((torch.tensor(dp) * w).sum()) == pytest.approx(float(pp.grad), rel=1e-9, abs=1e-12)
 
 
+@pytest.mark.parametrize("side,alpha,p,g,dx", [(3, 1.5, 0.5, 1.0, 1.0), (21, 1.7, 1.0, 1.0, 0.05),
+                                               (64, 1.2, 0.3, 0.7, 0.25), (40, 2.0, 0.4, 1.0, 1.0)])
+def test_host_caputo_matrix_and_derivatives_match_oracle(L, side, alpha, p, g, dx):
+    """Section 3.5 variant: K~ = K - B (oracle's caputo_boundary_terms), its alpha and p
+    derivatives against the oracle's autograd."""
+    pb = W.Problem(d=2, collision="mrt", grid=(side, 5), alpha=(alpha, 1.5), p=(p, 0.5), g=(g, 1.0),
+                   D=((0.01, 0), (0, 0.01)), u=(0, 0), s_free=(1.0, 1.0), dx=dx, variant="caputo")
+    prm = L.params_from_problem(pb, "fp64")
+    assert prm.variant == L.LBM_VARIANT_CAPUTO
+    K = L.lbm_frac_matrix(prm, 0)
+    a = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+    pp = torch.tensor(p, dtype=torch.float64, requires_grad=True)
+    Ko = O.frac_matrix(a, pp, g, side - 1, dx) - O.caputo_boundary_terms(a, pp, g, side - 1, dx)
+    tol = 1e-15 * side * side + 1e-14
+    assert np.max(np.abs(K - Ko.detach().numpy())) <= tol * np.max(np.abs(Ko.detach().numpy()))
+    assert np.max(np.abs(K.sum(axis=1))) < 1e-12 * np.max(np.abs(K))  # constants map to 0
+    if alpha < 2.0:  # x^gamma is not differentiable in gamma at gamma = 0, x = 0
+        da, dp = L.lbm_frac_matrix_grad(prm, 0)
+        w = torch.tensor(np.random.default_rng(side).normal(size=(side, side)))
+        (Ko * w).sum().backward()
+        assert float((torch.tensor(da) * w).sum()) == pytest.approx(float(a.grad), rel=1e-9, abs=1e-12)
+        assert float((torch.tensor(dp) * w).sum()) == pytest.approx(float(pp.grad), rel=1e-9, abs=1e-12)
+
+
+def test_unknown_variant_rejected(L):
+    pb = W.Problem(d=2, collision="mrt", grid=(8, 8), alpha=(1.5, 1.5), p=(0.5, 0.5), g=(1, 1),
+                   D=((0.01, 0), (0, 0.01)), u=(0, 0), s_free=(1.0, 1.0))
+    prm = L.params_from_problem(pb, "fp64")
+    prm.variant = 2
+    with pytest.raises(L.LBMError):
+        L.lbm_frac_matrix(prm, 0)
+
+
 def test_allocator_hooks_come_in_pairs(L):
     """lbm_set_allocator: both hooks or neither (host-side check, no GPU call)."""
     with pytest.raises(L.LBMError):
