@@ -55,6 +55,8 @@ Parity of every function here is pinned by the tests in
 """
 from __future__ import annotations
 
+import decimal
+import functools
 import math
 from typing import List, Sequence, Tuple
 
@@ -111,6 +113,35 @@ def _as_t(x) -> torch.Tensor:
     return x if isinstance(x, torch.Tensor) else torch.tensor(float(x), dtype=DT)
 
 
+_LN_INT: List[decimal.Decimal] = []   # ln k, k = 1, 2, ..., in 40-digit decimal arithmetic
+
+
+@functools.lru_cache(maxsize=256)
+def _exact_coefficients(gamma: float, N: int) -> Tuple[Tuple[float, ...], Tuple[float, ...]]:
+    """a[k], k = 0..N and b[m], m = 0..N of Eqs. (c+), (c-) (index 0 unused, 0), with every
+    power and difference taken in 40-digit decimal arithmetic and the result rounded to FP64.
+
+    The FP64 evaluation of a second difference of k^(g+1) cancels ~2 log10(k) digits; the
+    extended precision leaves each coefficient correctly rounded (up to a unit in the last
+    place), so the matrices carry no error of their own beyond FP64 rounding.
+    """
+    ctx = decimal.Context(prec=40)
+    while len(_LN_INT) < N + 1:
+        _LN_INT.append(ctx.ln(decimal.Decimal(len(_LN_INT) + 1)))
+    g = decimal.Decimal(gamma)          # the binary value of gamma, exactly
+    s = g + 1
+    # powers k^s (k = 0..N+1) and m^g (m = 1..N); 0^s = 0 since s >= 1; integers at g = 0
+    if g == 0:
+        ps = [decimal.Decimal(k) for k in range(N + 2)]
+        pg = [decimal.Decimal(0)] + [decimal.Decimal(1)] * N
+    else:
+        ps = [decimal.Decimal(0)] + [ctx.exp(ctx.multiply(s, _LN_INT[k - 1])) for k in range(1, N + 2)]
+        pg = [decimal.Decimal(0)] + [ctx.exp(ctx.multiply(g, _LN_INT[m - 1])) for m in range(1, N + 1)]
+    a = [0.0] + [float(ctx.add(ctx.subtract(ps[k + 1], ctx.multiply(2, ps[k])), ps[k - 1])) for k in range(1, N + 1)]
+    b = [0.0] + [float(ctx.add(ctx.subtract(ctx.multiply(s, pg[m]), ps[m]), ps[m - 1])) for m in range(1, N + 1)]
+    return tuple(a), tuple(b)
+
+
 def weight_matrices(gamma, N: int) -> Tuple[torch.Tensor, torch.Tensor]:
     """Coefficient matrices W+[n, l] = c+_{ln}(gamma) (l <= n) and W-[n, l] = c-_{ln}(gamma, N) (l >= n).
 
@@ -141,6 +172,11 @@ def weight_matrices(gamma, N: int) -> Tuple[torch.Tensor, torch.Tensor]:
     pw_m = pw[0:N + 1]                                       # m^(g+1)
     pw_m1 = torch.cat([torch.zeros(1, dtype=DT), pw[0:N]])   # (m-1)^(g+1)
     b = torch.where(m > 0, (1.0 + g) * torch.pow(mc, g) - pw_m + pw_m1, torch.zeros((), dtype=DT))
+    # values from the extended-precision evaluation, derivatives (autograd) from the FP64
+    # expressions above: a + (exact - a) has the exact value and the gradient of a
+    a_ex, b_ex = _exact_coefficients(float(g.detach()), N)
+    a = a + (torch.tensor(a_ex, dtype=DT) - a).detach()
+    b = b + (torch.tensor(b_ex, dtype=DT) - b).detach()
 
     n_idx = torch.arange(N + 1).view(-1, 1).expand(N + 1, N + 1)
     l_idx = torch.arange(N + 1).view(1, -1).expand(N + 1, N + 1)

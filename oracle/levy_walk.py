@@ -22,6 +22,8 @@ Chambers, Mallows & Stuck (1976) in the form given by Weron (1996), valid for
 alpha != 1: V = pi (U1 - 1/2), W = -ln U2,
 B = arctan(beta tan(pi alpha/2)) / alpha, A = (1 + beta^2 tan^2(pi alpha/2))^(1/(2 alpha)),
 S = A sin(alpha (V + B)) / cos(V)^(1/alpha) * (cos(V - alpha (V + B)) / W)^((1-alpha)/alpha).
+cos V is evaluated as sin(pi (1/2 - |U1 - 1/2|)), the same value, so that it keeps its
+relative accuracy as V -> +-pi/2 (where the FP64 rounding of pi (U1 - 1/2) would dominate).
 The uniforms are inputs, so the same draws can be replayed.
 
 For draws shared with another implementation the uniforms come from Philox4x32-10, the
@@ -50,12 +52,14 @@ def stable_from_uniforms(alpha: float, beta: float, u1: np.ndarray, u2: np.ndarr
     """S(alpha, beta) (characteristic function of Appendix A) from uniforms u1, u2 in ]0,1[."""
     if not (0.0 < alpha <= 2.0) or alpha == 1.0 or not (-1.0 <= beta <= 1.0):
         raise ValueError("alpha in ]0,2] \\ {1}, beta in [-1,1]")
-    V = math.pi * (np.asarray(u1, dtype=np.float64) - 0.5)
+    v = np.asarray(u1, dtype=np.float64) - 0.5
+    V = math.pi * v
+    cosV = np.sin(math.pi * (0.5 - np.abs(v)))
     Wexp = -np.log(np.asarray(u2, dtype=np.float64))
     t = beta * math.tan(math.pi * alpha / 2.0)
     B = math.atan(t) / alpha
     A = (1.0 + t * t) ** (1.0 / (2.0 * alpha))
-    return (A * np.sin(alpha * (V + B)) / np.cos(V) ** (1.0 / alpha)
+    return (A * np.sin(alpha * (V + B)) / cosV ** (1.0 / alpha)
             * (np.cos(V - alpha * (V + B)) / Wexp) ** ((1.0 - alpha) / alpha))
 
 

@@ -27,7 +27,8 @@ namespace {
 struct WalkAxis {
   double cu;     // u dt
   double scale;  // (D g)^(1/alpha) (-cos(pi alpha / 2) dt)^(1/alpha)
-  double alpha, inv_alpha, B, A, expo;  // Weron's constants: B, A and (1 - alpha) / alpha
+  double alpha, one_m_alpha, inv_alpha, expo;  // alpha, 1 - alpha, 1/alpha, (1 - alpha) / alpha
+  double Bpi, A;  // alpha B / pi = atan(beta tan(pi alpha / 2)) / pi and Weron's A
   double lo, hi;
 };
 
@@ -69,15 +70,23 @@ __device__ __forceinline__ float uniform_open<float>(unsigned int o) {
   return (static_cast<float>(o >> 8) + 0.5f) * 0x1p-24f;
 }
 
-// S(alpha, beta) from uniforms u1, u2 (Weron 1996, alpha != 1)
+__device__ __forceinline__ double sin_pi(double x) { return sinpi(x); }
+__device__ __forceinline__ float sin_pi(float x) { return sinpif(x); }
+__device__ __forceinline__ double cos_pi(double x) { return cospi(x); }
+__device__ __forceinline__ float cos_pi(float x) { return cospif(x); }
+
+// S(alpha, beta) from uniforms u1, u2 (Weron 1996, alpha != 1).  With V = pi v, v = u1 - 1/2
+// (exact for the generator's uniforms), the angles are taken in units of pi: sin(alpha (V + B))
+// = sin(pi (alpha v + alpha B / pi)), cos(V - alpha (V + B)) = cos(pi ((1 - alpha) v -
+// alpha B / pi)) and cos V = cos(pi v), which keeps cos V accurate as V -> +-pi/2.
 template <typename real>
 __device__ __forceinline__ real stable_sample(const WalkAxis& a, real u1, real u2) {
-  const real pi = static_cast<real>(3.14159265358979323846);
-  const real V = pi * (u1 - static_cast<real>(0.5));
+  const real v = u1 - static_cast<real>(0.5);
   const real W = -log(u2);
-  const real t = static_cast<real>(a.alpha) * (V + static_cast<real>(a.B));
-  const real c = cos(V - t) / W;
-  return static_cast<real>(a.A) * sin(t) / pow(cos(V), static_cast<real>(a.inv_alpha)) *
+  const real Bp = static_cast<real>(a.Bpi);
+  const real c = cos_pi(static_cast<real>(a.one_m_alpha) * v - Bp) / W;
+  return static_cast<real>(a.A) * sin_pi(static_cast<real>(a.alpha) * v + Bp) /
+         pow(cos_pi(v), static_cast<real>(a.inv_alpha)) *
          pow(c > static_cast<real>(0) ? c : static_cast<real>(0), static_cast<real>(a.expo));
 }
 
@@ -153,8 +162,9 @@ int walk_setup(const lbm_walk_params* prm, WalkPrm* P) {
     w.cu = prm->u[mu] * prm->dt;
     w.scale = std::pow(D * g, 1.0 / a) * std::pow(-std::cos(pi * a / 2.0) * prm->dt, 1.0 / a);
     w.alpha = a;
+    w.one_m_alpha = 1.0 - a;
     w.inv_alpha = 1.0 / a;
-    w.B = std::atan(t) / a;
+    w.Bpi = std::atan(t) / pi;
     w.A = std::pow(1.0 + t * t, 1.0 / (2.0 * a));
     w.expo = (1.0 - a) / a;
     w.lo = prm->lo[mu];

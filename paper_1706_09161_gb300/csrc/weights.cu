@@ -14,9 +14,10 @@
 // The Caputo-type variant (Section 3.5, Eqs. Fg2, PSRLdD-a/b, Fg22) subtracts the
 // boundary terms p f(0) (n dx)^g / Gamma(1+g) and (1-p) f(N dx) ((N-n) dx)^g / Gamma(1+g),
 // i.e. columns 0 and N of K change; 0^0 = 1 keeps constants in the kernel at g = 0 too.
-// Both a(k) and b(m) are small differences of large powers; for large k, m they
-// are summed from their binomial series instead, so that every entry keeps
-// nearly full FP64 relative accuracy (the direct form loses ~2 log10(k) digits).
+// Both a(k) and b(m) are small differences of powers; for k, m >= 2 they are summed
+// from their binomial series instead (x = 1/k <= 1/2, so the series converges at least
+// like 4^-j), which keeps every entry within a few units in the last place (the direct
+// form loses ~2 log10(k) digits, and all of them as alpha -> 2).
 #include <cmath>
 #include <vector>
 
@@ -27,19 +28,18 @@ namespace {
 
 // a(k) = k^s * [(1+x)^s + (1-x)^s - 2], x = 1/k
 //      = 2 k^s * sum_{j>=1} binom(s, 2j) x^{2j}
-double interior_coeff(double s, long k) {
-  if (k < 8) {
-    const double kd = static_cast<double>(k);
-    return std::pow(kd + 1.0, s) - 2.0 * std::pow(kd, s) + std::pow(kd - 1.0, s);
-  }
+double interior_coeff(double g, long k) {
+  const double s = g + 1.0;
+  if (k < 2) return 2.0 * std::expm1(g * std::log(2.0));  // k = 1: 2^s - 2, (k-1)^s = 0
   const double x2 = 1.0 / (static_cast<double>(k) * static_cast<double>(k));
   double binom = 1.0;  // binom(s, m), advanced two orders per term
   double xp = 1.0;
   double sum = 0.0;
-  for (int j = 1; j < 60; ++j) {
+  for (int j = 1; j < 200; ++j) {
     const int m = 2 * j;
-    binom *= (s - (m - 2)) / (m - 1);
-    binom *= (s - (m - 1)) / m;
+    // s - (m-2) and s - (m-1) as g - (m-3) and g - (m-2): no rounding of s = g + 1 first
+    binom *= (g - (m - 3)) / (m - 1);
+    binom *= (g - (m - 2)) / m;
     xp *= x2;
     const double term = binom * xp;
     sum += term;
@@ -51,16 +51,13 @@ double interior_coeff(double s, long k) {
 // b(m) = (1+g) m^g - [m^s - (m-1)^s] = m^s * sum_{j>=2} (-1)^j binom(s, j) m^{-j}
 double end_coeff(double g, long m) {
   const double s = g + 1.0;
-  if (m < 16) {
-    const double md = static_cast<double>(m);
-    return (1.0 + g) * std::pow(md, g) - std::pow(md, s) + std::pow(md - 1.0, s);
-  }
+  if (m < 2) return g;  // m = 1: (1+g) - 1 + 0
   const double x = 1.0 / static_cast<double>(m);
   double binom = s;  // binom(s, 1)
   double xp = x;
   double sum = 0.0;
-  for (int j = 2; j < 80; ++j) {
-    binom *= (s - (j - 1)) / j;
+  for (int j = 2; j < 200; ++j) {
+    binom *= (g - (j - 2)) / j;  // s - (j-1), exact in g
     xp *= x;
     const double term = ((j & 1) ? -1.0 : 1.0) * binom * xp;
     sum += term;
@@ -109,7 +106,7 @@ void build_frac_matrix_grad(double alpha, double p, double scale_g, int side, do
   const double dscale = scale * (std::log(dx) - digamma(2.0 + g));
   std::vector<double> a(side + 1, 0.0), b(side + 1, 0.0), da(side + 1, 0.0), db(side + 1, 0.0);
   for (long k = 1; k <= N; ++k) {
-    a[k] = interior_coeff(s, k);
+    a[k] = interior_coeff(g, k);
     const double kd = static_cast<double>(k);
     da[k] = pow_log(kd + 1.0, s) - 2.0 * pow_log(kd, s) + pow_log(kd - 1.0, s);
   }
@@ -159,7 +156,7 @@ void build_frac_matrix(double alpha, double p, double scale_g, int side, double 
   const long N = side - 1;
   const double scale = scale_g * std::pow(dx, g) / std::tgamma(2.0 + g);
   std::vector<double> a(side + 1, 0.0), b(side + 1, 0.0);
-  for (long k = 1; k <= N; ++k) a[k] = interior_coeff(s, k);
+  for (long k = 1; k <= N; ++k) a[k] = interior_coeff(g, k);
   for (long m = 1; m <= N; ++m) b[m] = end_coeff(g, m);
   for (long n = 0; n <= N; ++n) {
     for (long l = 0; l <= N; ++l) {

@@ -61,9 +61,9 @@ def test_host_weight_matrix_matches_oracle(L, side, alpha, p, g, dx):
                    D=((0.01, 0), (0, 0.01)), u=(0, 0), s_free=(1.0, 1.0), dx=dx)
     K = L.lbm_frac_matrix(L.params_from_problem(pb, "fp64"), 0)
     Ko = O.frac_matrix(alpha, p, g, side - 1, dx).numpy()
-    # the oracle evaluates second differences of k^(g+1) directly and loses ~2 log10(k) digits
-    tol = 1e-15 * side * side + 1e-14
-    assert np.max(np.abs(K - Ko)) <= tol * np.max(np.abs(Ko))
+    # both sides are accurate to a few units in the last place of every entry (the oracle
+    # through 40-digit differences, the library through the coefficients' binomial series)
+    assert np.all(np.abs(K - Ko) <= 4e-15 * np.abs(Ko) + 1e-300)
 
 
 def test_host_weight_matrix_bgk_diagonal_D(L):
@@ -147,8 +147,10 @@ def test_host_caputo_matrix_and_derivatives_match_oracle(L, side, alpha, p, g, d
     a = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
     pp = torch.tensor(p, dtype=torch.float64, requires_grad=True)
     Ko = O.frac_matrix(a, pp, g, side - 1, dx) - O.caputo_boundary_terms(a, pp, g, side - 1, dx)
-    tol = 1e-15 * side * side + 1e-14
-    assert np.max(np.abs(K - Ko.detach().numpy())) <= tol * np.max(np.abs(Ko.detach().numpy()))
+    Kd = Ko.detach().numpy()
+    # columns 0 and N subtract the boundary terms, so their entries may cancel: bound them
+    # by the terms' size
+    assert np.max(np.abs(K - Kd)) <= 4e-15 * np.max(np.abs(Kd))
     assert np.max(np.abs(K.sum(axis=1))) < 1e-12 * np.max(np.abs(K))  # constants map to 0
     if alpha < 2.0:  # x^gamma is not differentiable in gamma at gamma = 0, x = 0
         da, dp = L.lbm_frac_matrix_grad(prm, 0)

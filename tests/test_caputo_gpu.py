@@ -38,8 +38,9 @@ def L():
 def _problem(seed, d, collision, grid):
     rng = np.random.default_rng(seed)
     pb = dataclasses.replace(W.random_problem(rng, d, collision, grid, spherical=(collision == "bgk")),
-                             variant="caputo", C_wall=0.05)
-    return pb, W.random_field(rng, grid) + 0.05
+                             variant="caputo", C_wall=0.3)
+    f0 = W.random_field(rng, grid)
+    return pb, 0.3 + f0 / f0.max()  # the wall value and O(1) variations about it
 
 
 @pytest.mark.parametrize("form", ["fp64", "fp32", "bf16split", "tf32split", "bf16x5split", "bf16x6split"])

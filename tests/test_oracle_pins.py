@@ -142,6 +142,35 @@ def test_frac_weights_positive_and_toeplitz():
     assert torch.allclose(Wm, torch.flip(Wp, dims=(0, 1)), atol=0)
 
 
+def _gbinom(gamma, j):
+    """Generalised binomial coefficient C(gamma + 1, j), each factor gamma + 1 - r taken as
+    gamma - (r - 1) so that s = gamma + 1 is never rounded first."""
+    out = 1.0
+    for r in range(j):
+        out *= (gamma + 1.0 if r == 0 else gamma - (r - 1)) / (r + 1)
+    return out
+
+
+@pytest.mark.parametrize("gamma", [1e-6, 0.05, 0.5, 0.95, 1.0 - 1e-6])
+def test_frac_weights_match_their_taylor_series_far_out(gamma):
+    """Eqs. (c+), (c-) far from the diagonal: expanding (1 +- 1/k)^s, s = gamma + 1, gives
+    a(k) = (k+1)^s - 2 k^s + (k-1)^s = 2 sum_{j>=1} C(s, 2j) k^(s-2j) (terms of one sign) and
+    b(m) = (1+g) m^g - m^s + (m-1)^s = sum_{j>=2} (-1)^j C(s, j) m^(s-j).  At k, m ~ 2000 a
+    few terms fix each coefficient to FP64 rounding; the oracle's entries must agree to a few
+    units in the last place (a direct FP64 evaluation of the differences misses by ~1e-10,
+    and by everything as gamma -> 0)."""
+    N = 2000
+    Wp, Wm = O.weight_matrices(gamma, N)
+    s = gamma + 1.0
+    for k in (1500, 1999):
+        a = 2.0 * sum(_gbinom(gamma, 2 * j) * k ** (s - 2 * j) for j in range(1, 8))
+        assert float(Wp[N, N - k]) == pytest.approx(a, rel=4e-16 * 4, abs=0)
+        assert float(Wm[0, k]) == pytest.approx(a, rel=4e-16 * 4, abs=0)
+    b = sum((-1) ** j * _gbinom(gamma, j) * N ** (s - j) for j in range(2, 16))
+    assert float(Wp[N, 0]) == pytest.approx(b, rel=4e-16 * 4, abs=0)
+    assert float(Wm[0, N]) == pytest.approx(b, rel=4e-16 * 4, abs=0)
+
+
 # --------------------------------------------------------------------------- relaxation
 
 def test_relaxation_time_printed_value():
