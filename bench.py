@@ -613,7 +613,7 @@ def measure_walk(lbm, torch, steps=3, warmup=1):
         Xs = X0[:, :m].cpu().numpy().T
         As = A0[:m].cpu().numpy().astype(bool)
         X_ref, A_ref = LW.killed_walk_philox(Xs, As, alpha, p, D, g, u, (0, 0), (1, 1), dt, 11, 0, nsteps,
-                                             bits=24 if prec == "fp32" else 32)
+                                             bits=23 if prec == "fp32" else 32)
         Xg = X[:, :m].cpu().numpy().T
         Ag = A[:m].cpu().numpy().astype(bool)
         both = Ag & A_ref

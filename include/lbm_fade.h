@@ -307,7 +307,8 @@ int lbm_set_wall_values(lbm_t h, const double* Cw_field, double rate);
 typedef struct {
   int d;                    /* 2 or 3 */
   int precision;            /* LBM_FP64: FP64 arithmetic, uniforms (o + 1/2) 2^-32;
-                               LBM_FP32: FP32 arithmetic, uniforms ((o >> 8) + 1/2) 2^-24 */
+                               LBM_FP32: FP32 arithmetic, uniforms ((o >> 9) + 1/2) 2^-23
+                               (exact in FP32) */
   double alpha[3];          /* ]1,2] per axis */
   double p[3];              /* [0,1] per axis (skewness beta = 2p - 1) */
   double D[3], g[3];        /* > 0 per axis */

@@ -35,7 +35,8 @@ counter words 1 and 3 and the key, and permutes; the key is bumped by (0x9E3779B
 0xBB67AE85) between rounds.  Counter of particle i, step n, call c: (i mod 2^32,
 i div 2^32, n, c), key = (seed mod 2^32, seed div 2^32); call c = 0 serves axes 0 and 1,
 c = 1 axis 2; axis a takes output words 2(a mod 2) and 2(a mod 2) + 1 as (U1, U2), each
-mapped to ]0,1[ by (o + 1/2) 2^-32 (bits = 32) or, with 24 bits, ((o >> 8) + 1/2) 2^-24.
+mapped to ]0,1[ by (o + 1/2) 2^-32 (bits = 32) or, with 23 bits, ((o >> 9) + 1/2) 2^-23
+(exactly representable in FP32, as are U - 1/2 and 1 - U).
 
 Parity of this module is pinned in tests/test_oracle_pins.py: the sampler against the
 closed-form characteristic function, the walk against the lattice Boltzmann oracle.
@@ -116,9 +117,11 @@ def philox_uniforms(particles: np.ndarray, step: int, axis: int, seed: int, bits
     out = philox4x32_10(i & _MASK32, i >> np.uint64(32), np.uint64(step), np.uint64(call),
                         np.uint64(seed) & _MASK32, np.uint64(seed) >> np.uint64(32))
     o1, o2 = out[2 * (axis % 2)], out[2 * (axis % 2) + 1]
-    if bits == 24:
-        return ((o1 >> np.uint64(8)).astype(np.float64) + 0.5) * 2.0 ** -24, \
-               ((o2 >> np.uint64(8)).astype(np.float64) + 0.5) * 2.0 ** -24
+    if bits == 23:
+        return ((o1 >> np.uint64(9)).astype(np.float64) + 0.5) * 2.0 ** -23, \
+               ((o2 >> np.uint64(9)).astype(np.float64) + 0.5) * 2.0 ** -23
+    if bits != 32:
+        raise ValueError("bits must be 32 or 23")
     return (o1.astype(np.float64) + 0.5) * 2.0 ** -32, (o2.astype(np.float64) + 0.5) * 2.0 ** -32
 
 

@@ -16,7 +16,8 @@
 // across launches.  Counter (i mod 2^32, i div 2^32, n, call), key (seed mod 2^32, seed div
 // 2^32); call 0 serves axes 0 and 1, call 1 axis 2; axis a takes output words 2(a mod 2) and
 // 2(a mod 2) + 1.  FP64 form: uniforms (o + 1/2) 2^-32 and FP64 arithmetic; FP32 form: uniforms
-// ((o >> 8) + 1/2) 2^-24 (exact in FP32, never 0 or 1) and FP32 arithmetic.
+// ((o >> 9) + 1/2) 2^-23 (exact in FP32, as are u - 1/2 and 1 - u; never 0 or 1) and FP32
+// arithmetic.
 #include <cmath>
 
 #include "lbm_internal.h"
@@ -67,7 +68,7 @@ __device__ __forceinline__ double uniform_open<double>(unsigned int o) {
 }
 template <>
 __device__ __forceinline__ float uniform_open<float>(unsigned int o) {
-  return (static_cast<float>(o >> 8) + 0.5f) * 0x1p-24f;
+  return (static_cast<float>(o >> 9) + 0.5f) * 0x1p-23f;
 }
 
 __device__ __forceinline__ double sin_pi(double x) { return sinpi(x); }
