@@ -57,7 +57,7 @@ WORKLOADS = {
     "batch64": dict(desc="64 independent 2-D D2Q5 MRT problems, sides U{128,256,384,512,768,1024} (seed 4), "
                          "alpha~U[1.2,2], p~U[0,1], D~U[1e-4,3e-3] diagonal, |u|<=0.08, Gaussian pulses sigma~U[2,6], "
                          "free rates U[0.8,1.9], 1000 steps each, grouped launches",
-                    default_precision="bf16x6split", oracle_steps=6),
+                    default_precision="bf16x6split", oracle_steps=6, other_forms=("fp32",)),
     "inverse_256": dict(desc="inverse problem: 2-D D2Q5 MRT 256x256, alpha=(1.45,1.75), p=(0.35,0.65), "
                              "D=diag(1.5e-3,7e-4), u=(0.04,-0.01); loss over 10 snapshots of 3000 steps + N(0,1e-4) noise; "
                              "one bench step = one loss+gradient evaluation (forward, checkpointed recompute, adjoint; "
@@ -76,7 +76,7 @@ WORKLOADS = {
     "mrt3d_256": dict(desc="3-D fractional ADE, D3Q7 MRT, 256^3, alpha=(1.6,1.6,1.9), p=(0.5,0.2,0.8), g=(1,1,1), "
                            "D=diag(1e-3,1e-3,4e-4), u=(0.03,0,0) lattice units, free rates U[0.8,1.9] seed 3, "
                            "Dirichlet C=0, unit-mass Gaussian sigma=3, 2000 steps",
-                      default_precision="tf32split", oracle_steps=30),
+                      default_precision="tf32split", oracle_steps=30, other_forms=("bf16x6split", "fp32")),
 }
 # the other precision forms of the headline workload reported beside it ("forms"); fp32 is
 # the plain FP32 form (SIMT operator) the split forms are compared with
@@ -298,7 +298,14 @@ def errors(got, refs):
     num = sum(float(np.sum((g - r) ** 2)) for g, r in zip(got, refs))
     den = sum(float(np.sum(r ** 2)) for r in refs)
     node = max(float(np.max(np.abs(g - r))) / max(float(np.max(np.abs(r))), 1e-300) for g, r in zip(got, refs))
-    return {"rel_l2_vs_fp64_oracle": float(np.sqrt(num / den)), "max_node_err_rel_to_max": node}
+    out = {"rel_l2_vs_fp64_oracle": float(np.sqrt(num / den)), "max_node_err_rel_to_max": node}
+    if len(got) > 1:
+        # per problem: members with alpha near 1 on long lines or lambda near 1/2 amplify
+        # FP32 rounding in any FP32 form, so the aggregate is dominated by a few of them
+        per = sorted(float(np.sqrt(np.sum((g - r) ** 2) / np.sum(r ** 2))) for g, r in zip(got, refs))
+        out["members"] = {"count": len(per), "within_1e-5": sum(e <= 1e-5 for e in per),
+                          "median_rel_l2": per[len(per) // 2], "worst_rel_l2": per[-1]}
+    return out
 
 
 # --------------------------------------------------------------------------- GPU legs
@@ -667,6 +674,20 @@ def measure_extra(lbm, torch, name, flush, peaks, peak_src, autotune, steps=2, w
             ent["cpu_baseline"] = {"value": nodes * ns / dt / 1e6, "unit": UNIT, "cores": threads,
                                    "host_cpus": os.cpu_count(), "kind": "oracle",
                                    "sample": f"first {ns} of {nlbm} lattice steps (FP64, torch CPU)"}
+            # the same workload in the other forms (the plain FP32 form is the comparison point)
+            for alt in WORKLOADS[name].get("other_forms", ()):
+                r = Runner(lbm, torch, name, probs, fields, nlbm, alt, autotune, flush)
+                try:
+                    ta, st = r.timed(steps, warmup)
+                    ma = sum(ta) / len(ta)
+                    ra, oa = r.rooflines(peaks, peak_src)
+                    ent.setdefault("forms", {})[alt] = {
+                        "dtype": DTYPES[alt], "value": nodes * nlbm / (ma * 1e-3) / 1e6, "unit": UNIT,
+                        "us_per_lattice_step": 1e3 * ma / nlbm, "roofline": ra, "roofline_other": oa,
+                        "launch_config": r.tuned if r.tuned is not None else "built-in",
+                        "accuracy": r.accuracy(refs, ns), "status": lbm.lbm_strerror(st)}
+                finally:
+                    r.close()
         return ent
     finally:
         run.close()

@@ -416,8 +416,13 @@ int lbm_wait_check(int complete, int limit_us, void* stream);
  * ckpt_every steps (memory: ckpt_every + T/ckpt_every states); sums are FP64.
  *   snap_steps : nsnap strictly increasing step indices >= 0 (the last one is T)
  *   obs        : nsnap x nodes host doubles (field layout as lbm_create)
- * MRT handles with the FP64 or FP32 forms only (LBM_ENOTSUP otherwise).  Synchronises;
- * leaves the handle reset to its initial state. */
+ * BGK and MRT handles in the FP64 or FP32 forms with constant coefficients (LBM_ENOTSUP
+ * for batches, split-precision forms and lbm_set_fields / lbm_set_source handles).  BGK:
+ * Omega = I / lambda with lambda from the largest D_mumu and K_mu scaled by
+ * h_mu = D_mumu / max D (end of Section 2.2), so dL/dD_mumu includes both dependences;
+ * where several D_mumu share the maximum, each takes an equal part of d(max D) (the
+ * average of the one-sided derivatives).  Synchronises; leaves the handle reset to its
+ * initial state. */
 int lbm_grad(lbm_t h, int nsnap, const int* snap_steps, const double* obs, int ckpt_every, double* loss,
              double* grad);
 

@@ -218,11 +218,34 @@ int derive(const lbm_params* p, Derived* out) {
 // dOmega/dD_mumu for MRT: Omega = M^-1 Lambda M, Lambda = (Lambda^-1)^-1 and
 // dLambda^-1/dD_mumu = dt/(e^2 dx^2) at the flux entry (1+mu, 1+mu) (Eqs. MatrixS, D_ab),
 // so dOmega/dD_mumu = -M^-1 Lambda E_mu Lambda M.
+// Share of D_mumu in d(max_nu D_nunu): 1 for the unique largest entry, 1/k for each of k
+// equal largest entries (the average of the one-sided derivatives at a tie), 0 otherwise.
+void bgk_max_share(const lbm_params* p, int d, double share[3], double* dmax) {
+  double m = 0.0;
+  for (int i = 0; i < d; ++i) m = std::fmax(m, p->D[4 * i]);
+  int k = 0;
+  for (int i = 0; i < d; ++i) k += (p->D[4 * i] == m);
+  for (int i = 0; i < 3; ++i) share[i] = (i < d && p->D[4 * i] == m) ? 1.0 / k : 0.0;
+  *dmax = m;
+}
+
 int derive_dOmega(const lbm_params* p, double dOm[3][lbm::kMaxQ][lbm::kMaxQ]) {
   const int d = (p->lattice == LBM_D2Q5) ? 2 : 3;
   const int Q = 2 * d + 1;
   const double e2 = (d == 2) ? 1.0 / 3.0 : 1.0 / 4.0;
   const double ratio = p->dt / (p->dx * p->dx);
+  if (p->collision == LBM_BGK) {
+    // Omega = I / lambda, lambda = max D ratio / e^2 + 1/2 (Eq. Diffusion_Coefficient_3D):
+    // dOmega/dD_mumu = -share_mu (ratio / e^2) / lambda^2 I
+    double share[3], dmax;
+    bgk_max_share(p, d, share, &dmax);
+    const double lam = dmax * ratio / e2 + 0.5;
+    for (int mu = 0; mu < 3; ++mu)
+      for (int i = 0; i < lbm::kMaxQ; ++i)
+        for (int j = 0; j < lbm::kMaxQ; ++j)
+          dOm[mu][i][j] = (i == j && i < Q) ? -share[mu] * (ratio / e2) / (lam * lam) : 0.0;
+    return LBM_OK;
+  }
   double laminv[49] = {0}, lam[49], M[49], Minv[49];
   laminv[0] = 1.0;
   for (int i = 0; i < d; ++i)
@@ -1366,13 +1389,16 @@ static int step_hook(lbm_s* h, int& cur, cudaStream_t s) { return one_step(h, cu
 int lbm_grad(lbm_t h, int nsnap, const int* snap_steps, const double* obs, int ckpt_every, double* loss,
              double* grad) {
   if (!h || nsnap < 1 || !snap_steps || !obs || ckpt_every < 1 || !loss || !grad) return LBM_EINVAL;
-  if (h->is_batch() || h->tc || h->fld.on || h->prm.collision != LBM_MRT) return LBM_ENOTSUP;
+  if (h->is_batch() || h->tc || h->fld.on) return LBM_ENOTSUP;
   for (int k = 0; k < nsnap; ++k)
     if (snap_steps[k] < 0 || (k > 0 && snap_steps[k] <= snap_steps[k - 1])) return LBM_EINVAL;
   double dOm[3][lbm::kMaxQ][lbm::kMaxQ];
   int rc = derive_dOmega(&h->prm, dOm);
   if (rc) return rc;
+  Derived dv;
+  if ((rc = derive(&h->prm, &dv))) return rc;
   const int d = h->d;
+  const bool bgk = h->prm.collision == LBM_BGK;
   size_t gsz = 0;
   for (int mu = 0; mu < d; ++mu) gsz += (size_t)h->sp.n[mu] * h->sp.n[mu];
   std::vector<double> G(gsz), gsum(2 * d);
@@ -1382,21 +1408,40 @@ int lbm_grad(lbm_t h, int nsnap, const int* snap_steps, const double* obs, int c
   if (rc) return rc;
   if (rc2) return rc2;
   size_t goff = 0;
+  double KG[3] = {0.0, 0.0, 0.0};  // <K_mu, G_mu>, for BGK's h_mu = D_mumu / max D
   for (int mu = 0; mu < d; ++mu) {
     const int side = h->sp.n[mu];
-    std::vector<double> da((size_t)side * side), dp((size_t)side * side);
-    lbm::build_frac_matrix_grad(h->prm.alpha[mu], h->prm.p[mu], h->prm.g[mu], side, h->prm.dx, h->prm.variant, da.data(),
+    const double scale = h->prm.g[mu] * dv.h[mu];
+    std::vector<double> da((size_t)side * side), dp((size_t)side * side), K;
+    lbm::build_frac_matrix_grad(h->prm.alpha[mu], h->prm.p[mu], scale, side, h->prm.dx, h->prm.variant, da.data(),
                                 dp.data());
-    double sa = 0.0, sp_ = 0.0;
+    if (bgk) {
+      K.resize((size_t)side * side);
+      lbm::build_frac_matrix(h->prm.alpha[mu], h->prm.p[mu], scale, side, h->prm.dx, h->prm.variant, K.data());
+    }
+    double sa = 0.0, sp_ = 0.0, sk = 0.0;
     for (size_t i = 0; i < da.size(); ++i) {
       sa += da[i] * G[goff + i];
       sp_ += dp[i] * G[goff + i];
+      if (bgk) sk += K[i] * G[goff + i];
     }
+    KG[mu] = sk;
     grad[mu] = sa;
     grad[d + mu] = sp_;
     grad[2 * d + mu] = gsum[d + mu];
     grad[3 * d + mu] = gsum[mu];
     goff += (size_t)side * side;
+  }
+  if (bgk) {
+    // K_nu is proportional to h_nu = D_nunu / max D (end of Section 2.2):
+    // dK_nu/dD_mumu = K_nu (delta_nu,mu / D_nunu - share_mu / max D)
+    double share[3], dmax;
+    bgk_max_share(&h->prm, d, share, &dmax);
+    for (int mu = 0; mu < d; ++mu) {
+      double s = KG[mu] / h->prm.D[4 * mu];
+      for (int nu = 0; nu < d; ++nu) s -= share[mu] / dmax * KG[nu];
+      grad[2 * d + mu] += s;
+    }
   }
   return LBM_OK;
 }

@@ -435,10 +435,13 @@ def test_skewness_direction():
 
 # --------------------------------------------------------------------------- adjoint
 
-def test_discrete_adjoint_matches_central_differences():
-    """Autograd gradient of the FP64 snapshot loss vs central finite differences."""
+@pytest.mark.parametrize("collision,variant", [("mrt", "fg"), ("bgk", "fg"), ("mrt", "caputo")])
+def test_discrete_adjoint_matches_central_differences(collision, variant):
+    """Autograd gradient of the FP64 snapshot loss vs central finite differences (BGK with a
+    non-spherical diagonal D: lambda from the largest D_mumu and h_mu = D_mumu / max D, end of
+    Section 2.2; the Caputo-type variant of Section 3.5)."""
     rng = np.random.default_rng(7)
-    pb = W.random_problem(rng, 2, "mrt", (11, 9))
+    pb = dataclasses.replace(W.random_problem(rng, 2, collision, (11, 9)), variant=variant, C_wall=0.02)
     C0 = W.random_field(rng, pb.grid)
     snaps = [6, 12]
     # observations from a perturbed parameter set, so the gradient is not ~0
