@@ -469,10 +469,11 @@ class Runner:
                    "frac": achieved / peak, "traffic": traffic_for(self.name, "collide_stream", precision),
                    "algorithmic_per_launch": bytes_, "launch_ms": dur * 1e3, "peak_source": peak_src}
         if precision in SPLIT_PRODUCTS:
-            # the kernel also writes the operator's operands of the new C: its hi/lo split
-            # (x contiguous) and, for tf32 on the TMA-fed marches (one operator and one
-            # collide-stream launch per step), the copies regrouped along y (and z)
-            per_node = 8 if precision == "tf32split" else 4
+            # the kernel also writes the operator's operands of the new C: its split into
+            # two (hi/lo) or three bf16 parts (x contiguous) and, for tf32 on the TMA-fed
+            # marches (one operator and one collide-stream launch per step), the copies
+            # regrouped along y (and z)
+            per_node = {"tf32split": 8, "bf16split": 4, "bf16x5split": 4, "bf16x6split": 6}[precision]
             if precision == "tf32split" and self.lat.launches_per_step == 2:
                 per_node += 8 * (d - 1)
             ex = bytes_ + float(self.nodes) * per_node
@@ -529,7 +530,8 @@ def traffic_for(workload, kernel, precision):
     if not os.path.exists(path):
         return None
     with open(path) as fh:
-        rec = json.load(fh).get(kernel_key)
+        tab = json.load(fh)
+    rec = tab.get(f"{kernel_key}@{precision}") or tab.get(kernel_key)
     if not rec or rec.get("precision") != precision:
         return None
     if rec.get("source_sha") != source_sha(rec["sources"]):

@@ -295,8 +295,31 @@ __device__ __forceinline__ void write_split(const SplitOut& so, long long o, rea
   }
 }
 
+// Per-thread part of the mass.  FP32 concentrations are summed by TwoSum (Knuth): hi + lo
+// holds the running sum exactly except for the rounding of lo, of order u^2 per addition
+// (u = 2^-24), without FP64 arithmetic per node; FP64 concentrations are summed in FP64.
+template <typename real>
+struct MassAcc;
+template <>
+struct MassAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct MassAcc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(t, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+
 // Block partial of the mass of the new concentration (Algorithm 1, loop item 5): every
-// thread adds the C it wrote in FP64 (macc), the block reduces them in a fixed order
+// thread adds the C it wrote (macc, above), the block reduces them in FP64 in a fixed order
 // (warp shuffles, then warp 0 over the warps) and stores one FP64 partial at part[slot];
 // the handle adds the partials of the latest step in one small pass when asked
 // (lbm_mass), so the mass is a by-product of the step.  Called by every thread of the
@@ -414,7 +437,7 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   const bool in_xy = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
   const long long col = gx + (long long)n0 * gy;
   bool bad = false;
-  double macc = 0.0;
+  MassAcc<real> macc;
 
   real cur[Q], nxt[Q];
   real prev5 = static_cast<real>(0);
@@ -501,7 +524,7 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
         for (int mu = 0; mu < D; ++mu) fp.G[mu * nodes + node] = fp.g[mu * nodes + node] * C;
       }
       bad |= !isfinite(C);
-      macc += static_cast<double>(C);
+      macc.add(C);
     }
     if (owner && D == 3) {
       prev5 = cur[5];
@@ -512,7 +535,7 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   }
   // one flag update per warp at most
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
-  block_mass(macc, mpart, mslot);
+  block_mass(macc.value(), mpart, mslot);
 }
 
 // movers of the current tile plus ring for the 2-D FP32 marches: [buffer][mover 1..4][y+1][x+1]
@@ -570,7 +593,7 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
   issue(tr0, 0);
   if (tr0 + 1 < tr1) issue(tr0 + 1, 1); else cp_async_commit();
   bool bad = false;
-  double macc = 0.0;
+  MassAcc<float> macc;
   int buf = 0;
   for (int tr = tr0; tr < tr1; ++tr) {
     const int slot = (tr - tr0) % PIPE_STAGES;
@@ -651,12 +674,12 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
       C_out[node] = C;
       if (SPLIT) write_split<SPLIT>(so, (long long)gy * so.ldp + gx, C);
       bad |= !isfinite(C);
-      macc += static_cast<double>(C);
+      macc.add(C);
     }
     buf ^= 1;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
-  block_mass(macc, mpart, mslot);
+  block_mass(macc.value(), mpart, mslot);
 }
 
 // linear index of this block in its grid (the slot of its mass partial)
@@ -875,7 +898,7 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
     issue(z0 + 1);  // z0 + 1 <= z1: needed by the owners' first iteration
   }
   bool bad = false;
-  double macc = 0.0;
+  MassAcc<float> macc;
   float cur[Q], nxt[Q];
   float prev5 = 0.f;
   if (owner) {
@@ -965,7 +988,7 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
       C_out[node] = C;
       if (SPLIT) write_split<SPLIT>(so, ((long long)z * n1 + gy) * so.ldp + gx, C);
       bad |= !isfinite(C);
-      macc += static_cast<double>(C);
+      macc.add(C);
       Cn = C;
     }
     if (owner) {
@@ -985,7 +1008,7 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
   if (tid == 0)
     for (int p = (z1 - 2 > z0 - 1 ? z1 - 2 : z0 - 1); p <= z1; ++p) cs_mbar_wait(&full[stage_of(p)], parity_of(p), flag);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
-  block_mass(macc, mpart, block_linear());
+  block_mass(macc.value(), mpart, block_linear());
   if (!early) pdl_trigger();
 }
 
@@ -1096,7 +1119,7 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
   if (tid == 0)
     for (int t = tr0; t < tr1 && t < tr0 + nst; ++t) issue(t);
   bool bad = false;
-  double macc = 0.0;
+  MassAcc<float> macc;
   int buf = 0;
   for (int tr = tr0; tr < tr1; ++tr) {
     cs_mbar_wait(&full[stage_of(tr)], parity_of(tr), flag);
@@ -1183,7 +1206,7 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       if (SPLIT) write_split<SPLIT>(so, (long long)gy * so.ldp + gx, C);
       if (SPLIT == 2 && wT) s_c[((tr & 1) * TY + dy) * TCP + dx] = C;
       bad |= !isfinite(C);
-      macc += static_cast<double>(C);
+      macc.add(C);
     }
     buf ^= 1;
   }
@@ -1199,7 +1222,7 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(cs_smem_u32(&full[s])) : "memory");
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
-  block_mass(macc, mpart, mslot);
+  block_mass(macc.value(), mpart, mslot);
 }
 
 template <bool MRT, int SPLIT>
