@@ -242,8 +242,9 @@ int lbm_load(lbm_t h, const void* src_host, long long bytes);
 
 /* Total mass sum_x C(x) of problem `prob`'s current concentration (Algorithm 1, loop
  * item 5), in FP64, into the host double *mass.  After a step the mass is a by-product
- * of the collide-stream kernel: each of its blocks adds the concentrations it wrote in
- * FP64 and stores one partial; this call adds the partials of the latest step in one
+ * of the collide-stream kernel: each warp of its blocks sums the concentrations it wrote
+ * (per thread by a compensated FP32 sum, then across the warp in
+ * FP64) and stores one FP64 partial; this call adds the partials of the latest step in one
  * small pass (a fixed order: the same result every time).  Right after lbm_create,
  * lbm_set_C, lbm_reset, lbm_write_f or lbm_load it reduces C itself (block partials,
  * then one final pass).  Synchronises; returns the problem's latched error as

@@ -528,9 +528,9 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   if ((rc = alloc_bytes(h, (void**)&h->dev.partials, sizeof(double) * h->reduce_blocks))) return fail(rc);
   if ((rc = alloc_bytes(h, (void**)&h->dev.scalar, sizeof(double)))) return fail(rc);
   if ((rc = alloc_bytes(h, (void**)&h->dev.flag, sizeof(int)))) return fail(rc);
-  // one mass partial per collide-stream block: at most one block per 32 x 16 tile and plane
+  // kMassSlots mass partials per collide-stream block: at most one block per 32 x 16 tile and plane
   h->cs_part_cap = (long long)((prm->grid[0] + 31) / 32) * ((prm->grid[1] + 15) / 16) * prm->grid[2];
-  if ((rc = alloc_bytes(h, (void**)&h->cs_part, sizeof(double) * h->cs_part_cap))) return fail(rc);
+  if ((rc = alloc_bytes(h, (void**)&h->cs_part, sizeof(double) * lbm::kMassSlots * h->cs_part_cap))) return fail(rc);
   if (cudaMemsetAsync(h->dev.flag, 0, sizeof(int), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
 
   // weight matrices K_mu (Section 2.4) in FP64 on the host, then the working precision
@@ -1135,7 +1135,7 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
 int lbm_mass(lbm_t h, int prob, double* mass) {
   lbm_s* p = member(h, prob);
   if (!p || !mass) return LBM_EINVAL;
-  if (p->mass_valid)  // the latest step's block partials: one small pass
+  if (p->mass_valid)  // the latest step's warp partials: one small pass
     LBM_CUDA(lbm::launch_step_mass(p, 0.0, h->stream));
   else                // C from a re-initialisation: reduce C itself
     LBM_CUDA(lbm::launch_mass(p, p->dev.C, h->stream));

@@ -318,12 +318,13 @@ struct MassAcc<float> {
   __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
 };
 
-// Block partial of the mass of the new concentration (Algorithm 1, loop item 5): every
-// thread adds the C it wrote (macc, above), the block reduces them in FP64 in a fixed order
-// (warp shuffles, then warp 0 over the warps) and stores one FP64 partial at part[slot];
-// the handle adds the partials of the latest step in one small pass when asked
-// (lbm_mass), so the mass is a by-product of the step.  Called by every thread of the
-// block; part may be null (no partial wanted).
+// Warp partials of the mass of the new concentration (Algorithm 1, loop item 5): every
+// thread adds the C it wrote (macc, above), each warp reduces its threads' sums in FP64 in
+// a fixed order (shuffles) and stores one partial at part[slot * kMassSlots + warp]; the
+// handle adds the partials of the latest step in one small fixed-order pass when asked
+// (lbm_mass), so the mass is a by-product of the step.  No block-wide barrier: a block
+// reduction on the tail of every block cost ~10% of the 512^2 step.  part may be null (no
+// partial wanted).
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -331,17 +332,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 __device__ __forceinline__ void block_mass(double macc, double* part, int slot) {
-  __shared__ double s_wm[32];
-  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
   macc = warp_sum_d(macc);
-  if ((tid & 31) == 0) s_wm[tid >> 5] = macc;
-  __syncthreads();
-  if (tid < 32) {
-    double v = tid < nw ? s_wm[tid] : 0.0;
-    v = warp_sum_d(v);
-    if (tid == 0 && part) part[slot] = v;
-  }
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  if ((tid & 31) == 0 && part) part[(long long)slot * kMassSlots + (tid >> 5)] = macc;
 }
 
 // Thread block: 16 warps own a 32 x 16 tile of nodes (one node per thread, full
@@ -352,6 +345,7 @@ __device__ __forceinline__ void block_mass(double macc, double* part, int slot) 
 // movers (e_5, e_6) stay in registers (previous plane's f*_5, next plane's f*_6).
 // In 2-D the block handles one plane.  Each node is loaded ~1.19 times per step.
 constexpr int TX = 32, TY = 16, HALO_WARPS = 3;
+static_assert(kMassSlots * 32 == TX * (TY + HALO_WARPS), "one mass partial per warp of a block");
 
 template <typename real, int D, bool MRT, bool FLD = false>
 __device__ __forceinline__ void collide_at(const KConst<real>& sp, const real* __restrict__ f_in,
@@ -1346,7 +1340,7 @@ cudaError_t fused_launch(const lbm_s* h, int nsteps, int grid, cudaStream_t s) {
   SplitOut so{h->dev.Chi, h->dev.Clo, tc_split_pitch(h)};
   const int bx = (h->sp.n[0] + TX - 1) / TX, by = (h->sp.n[1] + TY - 1) / TY;
   const int ychunk = h->cs_chunk > 0 ? std::min(h->cs_chunk, by) : ychunk_for((long long)bx * by, by);
-  h->cs_nparts = bx * ((by + ychunk - 1) / ychunk);  // one mass partial per collide-stream item
+  h->cs_nparts = bx * ((by + ychunk - 1) / ychunk);  // kMassSlots mass partials per collide-stream item
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(TX, TY + HALO_WARPS);

@@ -11,6 +11,8 @@
 namespace lbm {
 
 constexpr int kMaxQ = 7;
+// mass partials per collide-stream block: one per warp of its 32 x (16 + 3) threads
+constexpr int kMassSlots = 19;
 struct TcPlan;  // tensor-core plan (frac_tc.cu)
 
 // Per-problem constants of one time step, passed by value to the kernels.
@@ -111,8 +113,8 @@ struct lbm_s {
   int fused_grid = 0;
   unsigned int* fused_bar = nullptr;   // grid-barrier counter
   int device = 0;
-  // FP64 block partials of the mass of the concentration each collide-stream launch writes
-  // (one per block of its grid: cs_nparts of them, at most cs_part_cap); mass_valid when the
+  // FP64 warp partials of the mass of the concentration each collide-stream launch writes
+  // (kMassSlots per block of its grid: cs_nparts blocks, at most cs_part_cap); mass_valid when the
   // latest C came from a step (not from a re-initialisation); mass_limit > 0 turns a mass of
   // larger magnitude (or a non-finite one) into LBM_ERR_UNSTABLE at the next synchronising call
   double* cs_part = nullptr;
@@ -190,7 +192,7 @@ cudaError_t launch_sum_partials_out(const float* src, int k, long long stride, d
 cudaError_t launch_sum_partials(const float* src, int k, long long stride, float* dst, long long n, cudaStream_t s);
 // mass reduction: partials then final
 cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s);
-// mass of the latest step from the collide-stream kernel's block partials (one small pass,
+// mass of the latest step from the collide-stream kernel's warp partials (one small pass,
 // fixed order) into dev.scalar; with limit > 0 a mass that is not within [-limit, limit]
 // sets the instability bit of the handle's flag
 cudaError_t launch_step_mass(const lbm_s* h, double limit, cudaStream_t s);

@@ -46,7 +46,7 @@ sum_final_kernel(const double* __restrict__ partials, int nparts, double* __rest
   if (threadIdx.x == 0) *out = acc;
 }
 
-// The latest step's mass: the collide-stream kernel's block partials added in a fixed
+// The latest step's mass: the collide-stream kernel's warp partials added in a fixed
 // order; with limit > 0, a mass outside [-limit, limit] (or not finite) sets bit 1 of flag.
 __global__ void __launch_bounds__(kReduceThreads)
 step_mass_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out, double limit,
@@ -118,7 +118,7 @@ cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s) {
 }
 
 cudaError_t launch_step_mass(const lbm_s* h, double limit, cudaStream_t s) {
-  step_mass_kernel<<<1, kReduceThreads, 0, s>>>(h->cs_part, h->cs_nparts, h->dev.scalar, limit, h->dev.flag);
+  step_mass_kernel<<<1, kReduceThreads, 0, s>>>(h->cs_part, h->cs_nparts * kMassSlots, h->dev.scalar, limit, h->dev.flag);
   return cudaGetLastError();
 }
 
