@@ -295,46 +295,61 @@ __device__ __forceinline__ void write_split(const SplitOut& so, long long o, rea
   }
 }
 
-// Per-thread part of the mass.  FP32 concentrations are summed by TwoSum (Knuth): hi + lo
-// holds the running sum exactly except for the rounding of lo, of order u^2 per addition
-// (u = 2^-24), without FP64 arithmetic per node; FP64 concentrations are summed in FP64.
+// Mass of the new concentration (Algorithm 1, loop item 5), as a by-product of the step.
+// Every thread adds the C it wrote; each warp reduces its threads' sums in a fixed order
+// (xor shuffles: every lane ends with the same value) and stores one FP64 partial at
+// part[slot * kMassSlots + warp]; the handle adds the partials of the latest step in one
+// small fixed-order pass when asked (lbm_mass).  FP32 concentrations are carried as an
+// unevaluated sum hi + lo of two floats, combined by TwoSum (Knuth), which keeps the sum
+// exact up to the rounding of lo (of order u^2 per addition, u = 2^-24) without FP64
+// arithmetic: the FP64 pipe is narrow, and the FP64 per-node sum and shuffles on the tail
+// of every block had cost 3-12% of the collide-stream kernels.  FP64 concentrations are
+// summed in FP64.  No block-wide barrier.  part may be null (no partial wanted).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
 template <typename real>
 struct MassAcc;
 template <>
 struct MassAcc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ double warp_total() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+  }
 };
 template <>
 struct MassAcc<float> {
   float hi = 0.0f, lo = 0.0f;
   __device__ __forceinline__ void add(float x) {
-    const float t = __fadd_rn(hi, x);
-    const float bp = __fsub_rn(t, hi);
-    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+    float t, e;
+    two_sum(hi, x, t, e);
     hi = t;
+    lo = __fadd_rn(lo, e);
   }
-  __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+  __device__ __forceinline__ double warp_total() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+      float t, e;
+      two_sum(hi, oh, t, e);
+      hi = t;
+      lo = __fadd_rn(__fadd_rn(lo, ol), e);
+    }
+    return static_cast<double>(hi) + static_cast<double>(lo);
+  }
 };
 
-// Warp partials of the mass of the new concentration (Algorithm 1, loop item 5): every
-// thread adds the C it wrote (macc, above), each warp reduces its threads' sums in FP64 in
-// a fixed order (shuffles) and stores one partial at part[slot * kMassSlots + warp]; the
-// handle adds the partials of the latest step in one small fixed-order pass when asked
-// (lbm_mass), so the mass is a by-product of the step.  No block-wide barrier: a block
-// reduction on the tail of every block cost ~10% of the 512^2 step.  part may be null (no
-// partial wanted).
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ void block_mass(double macc, double* part, int slot) {
-  macc = warp_sum_d(macc);
+template <typename real>
+__device__ __forceinline__ void block_mass(MassAcc<real>& macc, double* part, int slot) {
+  const double v = macc.warp_total();
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  if ((tid & 31) == 0 && part) part[(long long)slot * kMassSlots + (tid >> 5)] = macc;
+  if ((tid & 31) == 0 && part) part[(long long)slot * kMassSlots + (tid >> 5)] = v;
 }
 
 // Thread block: 16 warps own a 32 x 16 tile of nodes (one node per thread, full
@@ -483,30 +498,37 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
         fv[5] = prev5;
         fv[6] = nxt[6];
       }
-      real sum_known = static_cast<real>(0);
-      int n_unknown = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        if (known[q]) {
-          sum_known += fv[q];
-        } else {
-          fv[q] = static_cast<real>(0);
-          ++n_unknown;
-        }
-      }
-      real C = sum_known;
-      if (n_unknown > 0) {
-        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit; the
-        // wall value varies with position and time when given (Section 2.5)
-        real cwall = sp.C_wall;
-        if (FLD && fp.cw) cwall = fp.cw[col + z * plane] * static_cast<real>(fp.tf[1]);
-        const real fill = (cwall - sum_known) / static_cast<real>(n_unknown);
-#pragma unroll
-        for (int q = 0; q < Q; ++q)
-          if (!known[q]) fv[q] = fill;
-        C = fv[0];
+      real C;
+      if (gx > 0 && gx + 1 < n0 && gy > 0 && gy + 1 < n1 && (D == 2 || (z > 0 && z + 1 < n2))) {
+        C = fv[0];  // away from the walls every population is known (same sum, same order)
 #pragma unroll
         for (int q = 1; q < Q; ++q) C += fv[q];
+      } else {
+        real sum_known = static_cast<real>(0);
+        int n_unknown = 0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          if (known[q]) {
+            sum_known += fv[q];
+          } else {
+            fv[q] = static_cast<real>(0);
+            ++n_unknown;
+          }
+        }
+        C = sum_known;
+        if (n_unknown > 0) {
+          // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit; the
+          // wall value varies with position and time when given (Section 2.5)
+          real cwall = sp.C_wall;
+          if (FLD && fp.cw) cwall = fp.cw[col + z * plane] * static_cast<real>(fp.tf[1]);
+          const real fill = (cwall - sum_known) / static_cast<real>(n_unknown);
+#pragma unroll
+          for (int q = 0; q < Q; ++q)
+            if (!known[q]) fv[q] = fill;
+          C = fv[0];
+#pragma unroll
+          for (int q = 1; q < Q; ++q) C += fv[q];
+        }
       }
       const long long node = col + z * plane;
 #pragma unroll
@@ -529,7 +551,7 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   }
   // one flag update per warp at most
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
-  block_mass(macc.value(), mpart, mslot);
+  block_mass(macc, mpart, mslot);
 }
 
 // movers of the current tile plus ring for the 2-D FP32 marches: [buffer][mover 1..4][y+1][x+1]
@@ -640,27 +662,34 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
       fv[2] = s_m[buf][1][sy][sx + 1];
       fv[3] = s_m[buf][2][sy - 1][sx];
       fv[4] = s_m[buf][3][sy + 1][sx];
-      float sum_known = 0.f;
-      int n_unknown = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        if (known[q]) {
-          sum_known += fv[q];
-        } else {
-          fv[q] = 0.f;
-          ++n_unknown;
-        }
-      }
-      float C = sum_known;
-      if (n_unknown > 0) {
-        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
-        const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
-#pragma unroll
-        for (int q = 0; q < Q; ++q)
-          if (!known[q]) fv[q] = fill;
-        C = fv[0];
+      float C;
+      if (gx > 0 && gx + 1 < n0 && gy > 0 && gy + 1 < n1) {
+        C = fv[0];  // away from the walls every population is known (same sum, same order)
 #pragma unroll
         for (int q = 1; q < Q; ++q) C += fv[q];
+      } else {
+        float sum_known = 0.f;
+        int n_unknown = 0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          if (known[q]) {
+            sum_known += fv[q];
+          } else {
+            fv[q] = 0.f;
+            ++n_unknown;
+          }
+        }
+        C = sum_known;
+        if (n_unknown > 0) {
+          // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
+          const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
+#pragma unroll
+          for (int q = 0; q < Q; ++q)
+            if (!known[q]) fv[q] = fill;
+          C = fv[0];
+#pragma unroll
+          for (int q = 1; q < Q; ++q) C += fv[q];
+        }
       }
       const long long node = gx + (long long)n0 * gy;
 #pragma unroll
@@ -673,7 +702,7 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
     buf ^= 1;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
-  block_mass(macc.value(), mpart, mslot);
+  block_mass(macc, mpart, mslot);
 }
 
 // linear index of this block in its grid (the slot of its mass partial)
@@ -954,27 +983,34 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
       fv[4] = s_m[buf][3][sy + 1][sx];
       fv[5] = prev5;
       fv[6] = nxt[6];
-      float sum_known = 0.f;
-      int n_unknown = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        if (known[q]) {
-          sum_known += fv[q];
-        } else {
-          fv[q] = 0.f;
-          ++n_unknown;
-        }
-      }
-      float C = sum_known;
-      if (n_unknown > 0) {
-        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
-        const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
-#pragma unroll
-        for (int q = 0; q < Q; ++q)
-          if (!known[q]) fv[q] = fill;
-        C = fv[0];
+      float C;
+      if (gx > 0 && gx + 1 < n0 && gy > 0 && gy + 1 < n1 && z > 0 && z + 1 < n2) {
+        C = fv[0];  // away from the walls every population is known (same sum, same order)
 #pragma unroll
         for (int q = 1; q < Q; ++q) C += fv[q];
+      } else {
+        float sum_known = 0.f;
+        int n_unknown = 0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          if (known[q]) {
+            sum_known += fv[q];
+          } else {
+            fv[q] = 0.f;
+            ++n_unknown;
+          }
+        }
+        C = sum_known;
+        if (n_unknown > 0) {
+          // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
+          const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
+#pragma unroll
+          for (int q = 0; q < Q; ++q)
+            if (!known[q]) fv[q] = fill;
+          C = fv[0];
+#pragma unroll
+          for (int q = 1; q < Q; ++q) C += fv[q];
+        }
       }
       const long long node = col + z * plane;
 #pragma unroll
@@ -1002,7 +1038,7 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
   if (tid == 0)
     for (int p = (z1 - 2 > z0 - 1 ? z1 - 2 : z0 - 1); p <= z1; ++p) cs_mbar_wait(&full[stage_of(p)], parity_of(p), flag);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
-  block_mass(macc.value(), mpart, block_linear());
+  block_mass(macc, mpart, block_linear());
   if (!early) pdl_trigger();
 }
 
@@ -1171,6 +1207,9 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       if (x0 > 0 && x0 + TX < n0 && tr * TY > 0 && tr * TY + TY < n1) {  // no wall within reach (block-uniform)
 #pragma unroll
         for (int q = 0; q < Q; ++q) C += fv[q];
+      } else if (gx > 0 && gx + 1 < n0 && gy > 0 && gy + 1 < n1) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) C += fv[q];  // away from the walls every population is known
       } else {
         int n_unknown = 0;
 #pragma unroll
@@ -1216,7 +1255,7 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(cs_smem_u32(&full[s])) : "memory");
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
-  block_mass(macc.value(), mpart, mslot);
+  block_mass(macc, mpart, mslot);
 }
 
 template <bool MRT, int SPLIT>
