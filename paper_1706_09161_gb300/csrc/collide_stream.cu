@@ -498,37 +498,30 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
         fv[5] = prev5;
         fv[6] = nxt[6];
       }
-      real C;
-      if (gx > 0 && gx + 1 < n0 && gy > 0 && gy + 1 < n1 && (D == 2 || (z > 0 && z + 1 < n2))) {
-        C = fv[0];  // away from the walls every population is known (same sum, same order)
+      real sum_known = static_cast<real>(0);
+      int n_unknown = 0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (known[q]) {
+          sum_known += fv[q];
+        } else {
+          fv[q] = static_cast<real>(0);
+          ++n_unknown;
+        }
+      }
+      real C = sum_known;
+      if (n_unknown > 0) {
+        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit; the
+        // wall value varies with position and time when given (Section 2.5)
+        real cwall = sp.C_wall;
+        if (FLD && fp.cw) cwall = fp.cw[col + z * plane] * static_cast<real>(fp.tf[1]);
+        const real fill = (cwall - sum_known) / static_cast<real>(n_unknown);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (!known[q]) fv[q] = fill;
+        C = fv[0];
 #pragma unroll
         for (int q = 1; q < Q; ++q) C += fv[q];
-      } else {
-        real sum_known = static_cast<real>(0);
-        int n_unknown = 0;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          if (known[q]) {
-            sum_known += fv[q];
-          } else {
-            fv[q] = static_cast<real>(0);
-            ++n_unknown;
-          }
-        }
-        C = sum_known;
-        if (n_unknown > 0) {
-          // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit; the
-          // wall value varies with position and time when given (Section 2.5)
-          real cwall = sp.C_wall;
-          if (FLD && fp.cw) cwall = fp.cw[col + z * plane] * static_cast<real>(fp.tf[1]);
-          const real fill = (cwall - sum_known) / static_cast<real>(n_unknown);
-#pragma unroll
-          for (int q = 0; q < Q; ++q)
-            if (!known[q]) fv[q] = fill;
-          C = fv[0];
-#pragma unroll
-          for (int q = 1; q < Q; ++q) C += fv[q];
-        }
       }
       const long long node = col + z * plane;
 #pragma unroll
@@ -662,34 +655,27 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
       fv[2] = s_m[buf][1][sy][sx + 1];
       fv[3] = s_m[buf][2][sy - 1][sx];
       fv[4] = s_m[buf][3][sy + 1][sx];
-      float C;
-      if (gx > 0 && gx + 1 < n0 && gy > 0 && gy + 1 < n1) {
-        C = fv[0];  // away from the walls every population is known (same sum, same order)
+      float sum_known = 0.f;
+      int n_unknown = 0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (known[q]) {
+          sum_known += fv[q];
+        } else {
+          fv[q] = 0.f;
+          ++n_unknown;
+        }
+      }
+      float C = sum_known;
+      if (n_unknown > 0) {
+        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
+        const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (!known[q]) fv[q] = fill;
+        C = fv[0];
 #pragma unroll
         for (int q = 1; q < Q; ++q) C += fv[q];
-      } else {
-        float sum_known = 0.f;
-        int n_unknown = 0;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          if (known[q]) {
-            sum_known += fv[q];
-          } else {
-            fv[q] = 0.f;
-            ++n_unknown;
-          }
-        }
-        C = sum_known;
-        if (n_unknown > 0) {
-          // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
-          const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
-#pragma unroll
-          for (int q = 0; q < Q; ++q)
-            if (!known[q]) fv[q] = fill;
-          C = fv[0];
-#pragma unroll
-          for (int q = 1; q < Q; ++q) C += fv[q];
-        }
       }
       const long long node = gx + (long long)n0 * gy;
 #pragma unroll
@@ -983,34 +969,27 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
       fv[4] = s_m[buf][3][sy + 1][sx];
       fv[5] = prev5;
       fv[6] = nxt[6];
-      float C;
-      if (gx > 0 && gx + 1 < n0 && gy > 0 && gy + 1 < n1 && z > 0 && z + 1 < n2) {
-        C = fv[0];  // away from the walls every population is known (same sum, same order)
+      float sum_known = 0.f;
+      int n_unknown = 0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (known[q]) {
+          sum_known += fv[q];
+        } else {
+          fv[q] = 0.f;
+          ++n_unknown;
+        }
+      }
+      float C = sum_known;
+      if (n_unknown > 0) {
+        // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
+        const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (!known[q]) fv[q] = fill;
+        C = fv[0];
 #pragma unroll
         for (int q = 1; q < Q; ++q) C += fv[q];
-      } else {
-        float sum_known = 0.f;
-        int n_unknown = 0;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          if (known[q]) {
-            sum_known += fv[q];
-          } else {
-            fv[q] = 0.f;
-            ++n_unknown;
-          }
-        }
-        C = sum_known;
-        if (n_unknown > 0) {
-          // Eq. (Dirichlet_BC); with k unknown populations each takes 1/k of the deficit
-          const float fill = (sp.C_wall - sum_known) / static_cast<float>(n_unknown);
-#pragma unroll
-          for (int q = 0; q < Q; ++q)
-            if (!known[q]) fv[q] = fill;
-          C = fv[0];
-#pragma unroll
-          for (int q = 1; q < Q; ++q) C += fv[q];
-        }
       }
       const long long node = col + z * plane;
 #pragma unroll
@@ -1207,9 +1186,6 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
       if (x0 > 0 && x0 + TX < n0 && tr * TY > 0 && tr * TY + TY < n1) {  // no wall within reach (block-uniform)
 #pragma unroll
         for (int q = 0; q < Q; ++q) C += fv[q];
-      } else if (gx > 0 && gx + 1 < n0 && gy > 0 && gy + 1 < n1) {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) C += fv[q];  // away from the walls every population is known
       } else {
         int n_unknown = 0;
 #pragma unroll
@@ -1400,27 +1376,20 @@ cudaError_t fused_launch(const lbm_s* h, int nsteps, int grid, cudaStream_t s) {
 constexpr int BATCH2_SMEM = (int)(TMA2_SMEM > (size_t)PIPE_SMEM ? TMA2_SMEM : (size_t)PIPE_SMEM);
 
 // Grouped form for a batch of independent problems: one launch covers every block of
-// every problem; block_start[p] is the first block of problem p (ascending).  The
+// every problem; block_map[b] = (problem, block within it), one load per block.  The
 // problem's constants are staged in shared memory.
 template <int D, bool MRT, int SPLIT>
 __global__ void __launch_bounds__(TX*(TY + HALO_WARPS), 2)
-collide_stream_batch_kernel(const BatchCS* __restrict__ tab, const int* __restrict__ block_start, int nprob,
-                            int parity) {
+collide_stream_batch_kernel(const BatchCS* __restrict__ tab, const int2* __restrict__ block_map, int parity) {
   __shared__ KConst<float> s_k;
-  const int b = blockIdx.x;
-  int lo = 0, hi = nprob - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&block_start[mid]) <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  const BatchCS& e = tab[lo];
+  const int2 pb = __ldg(&block_map[blockIdx.x]);
+  const BatchCS& e = tab[pb.x];
   const int tid = threadIdx.y * TX + threadIdx.x;
   constexpr int words = sizeof(KConst<float>) / sizeof(int);
   for (int i = tid; i < words; i += TX * (TY + HALO_WARPS))
     reinterpret_cast<int*>(&s_k)[i] = reinterpret_cast<const int*>(&e.k)[i];
   __syncthreads();
-  const int lb = b - __ldg(&block_start[lo]);
+  const int lb = pb.y;
   const int bx = lb % e.bx, rest = lb / e.bx;
   if constexpr (D == 2) {
     extern __shared__ __align__(128) uint8_t batch_raw[];
@@ -1785,7 +1754,7 @@ int cs_chunk_default(const lbm_s* h) {
 int cs_batch_prepare(lbm_s* b) {
   const int P = static_cast<int>(b->subs.size());
   std::vector<BatchCS> tab(P);
-  std::vector<int> start(P);
+  std::vector<int2> map;
   int total = 0;
   for (int i = 0; i < P; ++i) {
     lbm_s* h = b->subs[i];
@@ -1805,8 +1774,8 @@ int cs_batch_prepare(lbm_s* b) {
     e.by = (h->sp.n[1] + TY - 1) / TY;
     // 2-D: tile rows per block (the pipelined y-march); 3-D: the whole z extent
     e.zchunk = (h->d == 2) ? std::min(e.by, b->cs_chunk > 0 ? b->cs_chunk : kBatchYChunk) : h->sp.n[2];
-    start[i] = total;
     h->cs_nparts = e.bx * ((h->d == 2) ? (e.by + e.zchunk - 1) / e.zchunk : e.by);
+    for (int k = 0; k < h->cs_nparts; ++k) map.push_back(make_int2(i, k));
     total += h->cs_nparts;
   }
   dev_free(b, b->batch_cs);
@@ -1814,9 +1783,9 @@ int cs_batch_prepare(lbm_s* b) {
   b->batch_cs = nullptr;
   b->batch_cs_start = nullptr;
   if (dev_alloc(b, &b->batch_cs, sizeof(BatchCS) * P) != cudaSuccess) return LBM_ENOMEM;
-  if (dev_alloc(b, (void**)&b->batch_cs_start, sizeof(int) * P) != cudaSuccess) return LBM_ENOMEM;
+  if (dev_alloc(b, (void**)&b->batch_cs_start, sizeof(int2) * total) != cudaSuccess) return LBM_ENOMEM;
   if (cudaMemcpy(b->batch_cs, tab.data(), sizeof(BatchCS) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->batch_cs_start, start.data(), sizeof(int) * P, cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(b->batch_cs_start, map.data(), sizeof(int2) * total, cudaMemcpyHostToDevice) != cudaSuccess)
     return LBM_ECUDA;
   b->batch_cs_blocks = total;
   return LBM_OK;
@@ -1842,7 +1811,8 @@ cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t
                         : smem_attr_once(attr[0][0], collide_stream_batch_kernel<2, false, 0>, BATCH2_SMEM);
     if (e != cudaSuccess) return e;
   }
-#define LBM_CSB(D_, M_, S_) collide_stream_batch_kernel<D_, M_, S_><<<g, block, smem, s>>>(tab, b->batch_cs_start, P, parity)
+#define LBM_CSB(D_, M_, S_) \
+  collide_stream_batch_kernel<D_, M_, S_><<<g, block, smem, s>>>(tab, reinterpret_cast<const int2*>(b->batch_cs_start), parity)
   if (h0->d == 2) {
     if (mrt) { if (split == 3) LBM_CSB(2, true, 3); else if (split) LBM_CSB(2, true, 1); else LBM_CSB(2, true, 0); }
     else { if (split == 3) LBM_CSB(2, false, 3); else if (split) LBM_CSB(2, false, 1); else LBM_CSB(2, false, 0); }

@@ -131,7 +131,7 @@ struct lbm_s {
   int* batch_tc_start = nullptr;       // first CTA of each problem (grouped operator)
   int batch_tc_blocks = 0;
   void* batch_cs = nullptr;            // device table of per-problem collide-stream entries
-  int* batch_cs_start = nullptr;       // first block of each problem (grouped collide-stream)
+  int* batch_cs_start = nullptr;       // (problem, block within it) per block, int2 pairs (grouped collide-stream)
   int batch_cs_blocks = 0;
   bool is_batch() const { return !subs.empty(); }
 };
