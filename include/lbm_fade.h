@@ -275,10 +275,12 @@ int lbm_set_mass_limit(lbm_t h, double limit);
  * All three NULL returns to the constant coefficients.  The step then collides in moment
  * space with the rates of each node and the operator contracts g_mu(x) C along each axis;
  * the handle re-initialises from its initial concentration (as lbm_reset).  The arrays are
- * copied.  Single-problem handles in the LBM_FP64 or LBM_FP32 form (LBM_ENOTSUP for the
- * tensor-core forms, LBM_EINVAL for batches); LBM_EINVAL for a non-finite entry, g <= 0 or a
- * D that breaks the conditions above (the handle is unchanged then).  lbm_grad returns
- * LBM_ENOTSUP on a handle with varying coefficients.  Synchronises. */
+ * copied.  Single-problem handles (LBM_EINVAL for batches) in every precision form; the
+ * tensor-core forms keep g uniform (g_field must be NULL: LBM_ENOTSUP otherwise; g_mu stays
+ * folded into K_mu) and, with BGK, need a spherical constant D (LBM_ENOTSUP otherwise).
+ * LBM_EINVAL for a non-finite entry, g <= 0 or a D that breaks the conditions above (the
+ * handle is unchanged then).  lbm_grad returns LBM_ENOTSUP on a handle with varying
+ * coefficients.  Synchronises. */
 int lbm_set_fields(lbm_t h, const double* D_field, const double* g_field, const double* u_field);
 
 /* Source term S_c(x, t) = S(x) exp(rate t) of Eq. (FADE_moreGeneral), added after the collision
@@ -288,8 +290,9 @@ int lbm_set_fields(lbm_t h, const double* D_field, const double* g_field, const 
  * the handle's nodes (copied), or NULL to remove the source.  rate finite.  Runs the step on
  * the per-node path (as lbm_set_fields, constant coefficients unless set), re-initialises from
  * the initial concentration (as lbm_reset, time 0).  The time is carried by the step counter
- * (lbm_save / lbm_load keep it).  Single FP64 / FP32 problems (LBM_ENOTSUP for the tensor-core
- * forms, LBM_EINVAL for batches); LBM_EINVAL for a non-finite value.  Synchronises; every
+ * (lbm_save / lbm_load keep it).  Single problems in every precision form (LBM_EINVAL for
+ * batches; the tensor-core forms as for lbm_set_fields); LBM_EINVAL for a non-finite value.
+ * Synchronises; every
  * lbm_step call of a handle with a time-dependent source or wall values waits for the
  * handle's earlier work once per 128 steps (it copies that range's time factors). */
 int lbm_set_source(lbm_t h, const double* S_field, double rate);

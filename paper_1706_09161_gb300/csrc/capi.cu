@@ -322,7 +322,8 @@ bool pdl_fits(const lbm_s* h) {
   if (h->is_batch()) return false;
   if (!h->tc) return h->elem == 4 && lbm::cs_one_wave(h) && lbm::simt_one_wave(h);  // FP32 SIMT operator
   const bool adjacent = lbm::bf16_parts(h->prm.precision) || lbm::cs_writes_T(h);
-  return adjacent && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
+  // the field march's grid is not the one cs_one_wave describes: no early launch there
+  return adjacent && !h->fld.on && lbm::cs_one_wave(h) && lbm::tc_one_wave(h);
 }
 
 int alloc_bytes(const lbm_s* h, void** p, size_t bytes) {
@@ -455,7 +456,7 @@ static int upload_weights(lbm_s* h, const double* hfac, std::vector<std::vector<
     const int side = prm->grid[mu];
     K.assign((size_t)side * side, 0.0);
     KT.assign((size_t)side * side, 0.0);
-    const double scale = h->fld.on ? 1.0 : prm->g[mu] * hfac[mu];
+    const double scale = (h->fld.on && !h->tc) ? 1.0 : prm->g[mu] * hfac[mu];
     lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], scale, side, prm->dx, prm->variant, K.data());
     for (int n = 0; n < side; ++n)
       for (int l = 0; l < side; ++l) KT[(size_t)l * side + n] = K[(size_t)n * side + l];
@@ -949,6 +950,7 @@ int apply_cfg(lbm_s* h, const TuneCfg& c) {
       h->pdl = pdl_fits(h);
       lbm::tc_set_pdl(h, h->pdl);
       if (c.fused) {
+        if (h->fld.on) return LBM_EINVAL;  // the fused step runs the constant-coefficient march only
         if ((rc = lbm::fused_prepare(h))) return rc;
         h->fused = true;
       }
@@ -1071,7 +1073,7 @@ int lbm_autotune(lbm_t h, int nsteps, char* desc, int desc_len) {
     // the fused step where the plan is one it covers (2-D bf16, 64/128 columns, split 2 or 4)
     const size_t nops = ops.size();
     for (size_t i = 0; i < nops; ++i)
-      if (h->d == 2 && h->prm.precision == LBM_FP32_BF16SPLIT && !ops[i].persist &&
+      if (h->d == 2 && h->prm.precision == LBM_FP32_BF16SPLIT && !ops[i].persist && !h->fld.on &&
           (ops[i].bn == 64 || ops[i].bn == 128) && (ops[i].ks == 2 || ops[i].ks == 4)) {
         TuneCfg f = ops[i];
         f.fused = 1;
@@ -1215,12 +1217,16 @@ static int rebuild_fields(lbm_s* h) {
   int rc = LBM_OK;
   if (on) {
     const size_t E = h->elem;
-    if ((rc = alloc_bytes(h, &h->fld.coll, E * NC * nodes)) || (rc = alloc_bytes(h, &h->fld.advw, E * d * nodes)) ||
-        (rc = alloc_bytes(h, &h->fld.g, E * d * nodes)) || (rc = alloc_bytes(h, &h->fld.G, E * d * nodes)))
+    if ((rc = alloc_bytes(h, &h->fld.coll, E * NC * nodes)) || (rc = alloc_bytes(h, &h->fld.advw, E * d * nodes)))
+      return rc;
+    // g(x) and the operator input G = g C only for the SIMT operator (tensor-core forms fold
+    // the uniform g into K)
+    if (!h->tc && ((rc = alloc_bytes(h, &h->fld.g, E * d * nodes)) || (rc = alloc_bytes(h, &h->fld.G, E * d * nodes))))
       return rc;
     const std::pair<const std::vector<double>*, void*> ups[3] = {{&coll, h->fld.coll}, {&advw, h->fld.advw},
                                                                  {&gv, h->fld.g}};
     for (const auto& up : ups) {
+      if (!up.second) continue;
       const std::vector<double>& v = *up.first;
       for (size_t off = 0; off < v.size(); off += (size_t)nodes) {  // one plane of nodes at a time
         LBM_CUDA(cudaMemcpyAsync(h->dev.stage, v.data() + off, sizeof(double) * nodes, cudaMemcpyHostToDevice,
@@ -1230,17 +1236,25 @@ static int rebuild_fields(lbm_s* h) {
       }
     }
     h->fld.on = true;
+    h->fused = false;  // the fused step runs the constant-coefficient march only
   }
-  Derived dv;
-  if ((rc = derive(&h->prm, &dv))) return rc;
-  if ((rc = upload_weights(h, dv.h, nullptr))) return rc;  // g inside the integrals, or folded into K
+  h->pdl = pdl_fits(h);  // the march, and with tf32 whether the operands need a launch of their own
+  if (h->tc) lbm::tc_set_pdl(h, h->pdl);
+  if (!h->tc) {  // g inside the integrals (K without g), or folded into K; the tensor-core K keeps g
+    Derived dv;
+    if ((rc = derive(&h->prm, &dv))) return rc;
+    if ((rc = upload_weights(h, dv.h, nullptr))) return rc;
+  }
   return lbm_reset(h);
 }
 
-// the per-node path applies to single FP64 / FP32 problems
+// the per-node path applies to single problems in every form; the tensor-core forms keep g
+// uniform (folded into K, as without fields) and BGK's h_mu = 1 (a spherical constant D)
 static int fields_supported(lbm_t h) {
   if (!h || h->is_batch()) return LBM_EINVAL;
-  if (h->tc || (h->prm.precision != LBM_FP64 && h->prm.precision != LBM_FP32)) return LBM_ENOTSUP;
+  if (h->tc && h->prm.collision == LBM_BGK)
+    for (int a = 1; a < h->d; ++a)
+      if (h->prm.D[4 * a] != h->prm.D[0]) return LBM_ENOTSUP;
   return LBM_OK;
 }
 
@@ -1280,6 +1294,7 @@ static int ensure_time_table(lbm_s* h) {
 int lbm_set_fields(lbm_t h, const double* D_field, const double* g_field, const double* u_field) {
   int rc = fields_supported(h);
   if (rc) return rc;
+  if (g_field && h->tc) return LBM_ENOTSUP;  // g(x) inside the integrals: FP64 / FP32 forms
   const size_t nodes = (size_t)h->sp.nodes, d = (size_t)h->d;
   // validate on a copy first: the handle stays unchanged when the arrays are rejected
   lbm::FieldState keep;

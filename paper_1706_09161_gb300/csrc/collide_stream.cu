@@ -528,7 +528,7 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
       for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
       C_out[node] = C;
       if (SPLIT) write_split<SPLIT>(so, ((long long)z * n1 + gy) * so.ldp + gx, C);
-      if (FLD) {  // the operator's inputs of the next step: g_mu(x) C, one field per axis
+      if (FLD && fp.G) {  // the SIMT operator's inputs of the next step: g_mu(x) C, one field per axis
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) fp.G[mu * nodes + node] = fp.g[mu * nodes + node] * C;
       }
@@ -1548,6 +1548,18 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
                              static_cast<const real*>(h->fld.g),    static_cast<real*>(h->fld.G),
                              static_cast<const real*>(h->fld.src),  static_cast<const real*>(h->fld.cw),
                              h->fld.tf ? h->fld.tf + 2 * tk : nullptr};
+    if constexpr (sizeof(real) == 4) {
+      // tensor-core forms: the march also writes the operator's operands of the new C
+      if (split == 1)
+        return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 1, true>, sp, fi, F, fo, Co, flag, so,
+                                  nz, early, mp, fp);
+      if (split == 2)
+        return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 2, true>, sp, fi, F, fo, Co, flag, so,
+                                  nz, early, mp, fp);
+      if (split == 3)
+        return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 3, true>, sp, fi, F, fo, Co, flag, so,
+                                  nz, early, mp, fp);
+    }
     return cudaLaunchKernelEx(&cfg, collide_stream_march_kernel<real, D, MRT, 0, true>, sp, fi, F, fo, Co, flag, so,
                               nz, early, mp, fp);
   }
@@ -1623,7 +1635,7 @@ int grid_for(long long n) {
 // tf32 handles on the TMA-fed marches: the collide-stream kernel writes the regrouped split
 bool cs_writes_T(const lbm_s* h) {
   return !h->is_batch() && h->elem == 4 && h->cs_plan != nullptr && h->tc != nullptr && h->tc->elem == 4 &&
-         h->prm.precision == LBM_FP32_TF32SPLIT;
+         h->prm.precision == LBM_FP32_TF32SPLIT && !h->fld.on;  // the field march writes x-major operands only
 }
 
 cudaError_t launch_collide_stream(const lbm_s* h, const void* f_in, void* f_out, void* C_out, cudaStream_t s,
@@ -1842,6 +1854,7 @@ cudaError_t launch_init_equilibrium(const lbm_s* h, void* f, cudaStream_t s) {
 }
 
 cudaError_t launch_scale_fields(const lbm_s* h, cudaStream_t s) {
+  if (!h->fld.G) return cudaSuccess;  // tensor-core forms: g is uniform and folded into K
   const int g = grid_for(h->sp.nodes);
   if (h->elem == 8)
     scale_fields_kernel<double><<<g, 256, 0, s>>>(h->sp.nodes, h->d, (const double*)h->dev.C, (const double*)h->fld.g,

@@ -268,8 +268,8 @@ cudaError_t launch_frac_simt_T(const lbm_s* h, const void* in, long long in_stri
 
 cudaError_t launch_frac_simt(const lbm_s* h, const void* C, void* F, cudaStream_t s) {
   // spatially varying g: the input along mu is G_mu = g_mu(x) C (Eq. Fg), one field per axis
-  const long long cs = h->fld.on ? h->sp.nodes : 0;
-  if (h->fld.on) C = h->fld.G;
+  const long long cs = (h->fld.on && h->fld.G) ? h->sp.nodes : 0;
+  if (h->fld.on && h->fld.G) C = h->fld.G;
   if (h->elem == 8)
     return frac_all_axes<double>(h, static_cast<const double*>(C), static_cast<double*>(F), s, false, cs);
   return frac_all_axes<float>(h, static_cast<const float*>(C), static_cast<float*>(F), s, false, cs);

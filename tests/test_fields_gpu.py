@@ -112,6 +112,24 @@ def test_piecewise_constant_regions(L):
         arith_bounds.assert_close(lat.C(), C_ref, 1e-12, 1e-12, "two regions")
 
 
+@pytest.mark.parametrize("form", ["bf16x6split", "bf16x5split", "bf16split", "tf32split"])
+@pytest.mark.parametrize("grid", [(70, 65), (40, 21, 19)])
+def test_fields_tensor_core_forms(L, form, grid):
+    """D(x) and u(x) with the tensor-core operator (g uniform, folded into K): within 6x the
+    same arithmetic re-run on the CPU, the fused mass equal to the sum of C."""
+    pb, C0, fields = _case("mrt", grid, 960 + grid[0] + len(grid))
+    fields = {"D": fields["D"], "u": fields["u"]}
+    n = 12
+    C_ref = O.run_fields_C(pb, C0, n, fields).numpy()
+    with L.Lattice(pb, C0, form) as lat:
+        lat.set_fields(**fields)
+        lat.step(n)
+        C = lat.C()
+        assert lat.mass() == pytest.approx(float(C.sum()), rel=1e-13)
+    l2, node, _ = arith_bounds.bounds(pb, C0, n, form, C_ref=C_ref, fields=fields)
+    arith_bounds.assert_close(C, C_ref, l2, node, f"fields {grid} {form}")
+
+
 def test_fields_reject_invalid_input(L):
     rng = np.random.default_rng(981)
     pb = W.random_problem(rng, 2, "bgk", (30, 20), spherical=True)
