@@ -70,7 +70,7 @@ WORKLOADS = {
     "exact_e5": dict(desc="Section 3.4's exact-solution case: 2-D D2Q5 MRT 256x256 on ]0,1[^2, alpha=(1.5,1.7), "
                           "p=1, D_mumu(x)=x^alpha Gamma(a+2-alpha)/Gamma(a+2), a=(0.4,0.7), source -3 exp(-t) x^a1 y^a2, "
                           "time-dependent wall values from C=exp(-t) x^a1 y^a2, t=0.1 (33564 steps)",
-                     default_precision="fp32", oracle_steps=200),
+                     default_precision="fp32", oracle_steps=200, other_forms=("bf16x6split",)),
     "mrt3d_128": dict(desc="3-D D3Q7 MRT 128^3 with the 256^3 workload's parameters (profiling captures only)",
                       default_precision="tf32split", oracle_steps=20),
     "mrt3d_256": dict(desc="3-D fractional ADE, D3Q7 MRT, 256^3, alpha=(1.6,1.6,1.9), p=(0.5,0.2,0.8), g=(1,1,1), "
