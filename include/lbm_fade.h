@@ -164,7 +164,7 @@ int lbm_set_C(lbm_t h, const double* C_host);
  * error.  No host transfer; asynchronous. */
 int lbm_reset(lbm_t h);
 
-/* Advance nsteps >= 0 time steps (Algorithm 1 time loop, items 1-5): fractional
+/* Advance nsteps >= 0 time steps (Algorithm 1's time loop): fractional
  * terms F_mu (Section 2.4), equilibrium (Eqs. Feq, CoeffA_FADE3D), BGK/MRT collision
  * (Eqs. LBE_Ket, MRT-Coll), push streaming (Eq. Def_Translation), Dirichlet walls
  * (Eq. Dirichlet_BC; k unknown populations at edges/corners share the deficit
@@ -172,7 +172,7 @@ int lbm_reset(lbm_t h);
  * captured CUDA graphs. */
 int lbm_step(lbm_t h, int nsteps);
 
-/* Current concentration C = <1|f> of problem `prob` (Algorithm 1, loop item 5), as
+/* Current concentration C = <1|f> of problem `prob` (the moment of Algorithm 1's time step), as
  * that problem's grid[0]*grid[1]*grid[2] doubles in the field layout above, written to
  * dst: a host array (dst_is_device = 0) or a device array of the handle's GPU
  * (dst_is_device != 0; converted to FP64 on the device, no host round trip), owned by
@@ -240,8 +240,8 @@ long long lbm_state_size(lbm_t h);
 int lbm_save(lbm_t h, void* dst_host, long long bytes);
 int lbm_load(lbm_t h, const void* src_host, long long bytes);
 
-/* Total mass sum_x C(x) of problem `prob`'s current concentration (Algorithm 1, loop
- * item 5), in FP64, into the host double *mass.  After a step the mass is a by-product
+/* Total mass sum_x C(x) of problem `prob`'s current concentration (the moment of
+ * Algorithm 1's time step), in FP64, into the host double *mass.  After a step the mass is a by-product
  * of the collide-stream kernel: each warp of its blocks sums the concentrations it wrote
  * (per thread by a compensated FP32 sum, then across the warp in
  * FP64) and stores one FP64 partial; this call adds the partials of the latest step in one
@@ -413,15 +413,18 @@ int lbm_wait_check(int complete, int limit_us, void* stream);
  * lbm_set_C) with the handle's parameters theta; grad receives 4d doubles,
  * dL/d[alpha_1..d, p_1..d, D_11..D_dd, u_1..d] (D: diagonal entries, physical units).
  * Computed with the discrete adjoint of the step (the exact transpose of Algorithm 1's
- * loop items 1-5 for fixed theta: walls, streaming, collision, equilibrium, K_mu^T),
+ * time step for fixed theta: walls, streaming, collision, equilibrium, K_mu^T),
  * parameter derivatives of K_mu (lbm_frac_matrix_grad), of Omega (Eqs. MatrixS, D_ab)
  * and of the advective equilibrium term (Eq. Feq), including the initial populations
  * feq(C0, K C0).  Forward states are recomputed from checkpoints taken every
  * ckpt_every steps (memory: ckpt_every + T/ckpt_every states); sums are FP64.
  *   snap_steps : nsnap strictly increasing step indices >= 0 (the last one is T)
  *   obs        : nsnap x nodes host doubles (field layout as lbm_create)
- * BGK and MRT handles in the FP64 or FP32 forms with constant coefficients (LBM_ENOTSUP
- * for batches, split-precision forms and lbm_set_fields / lbm_set_source handles).  BGK:
+ * BGK and MRT single-problem handles with constant coefficients (LBM_ENOTSUP for batches and
+ * lbm_set_fields / lbm_set_source handles).  On the split-precision forms the gradient is
+ * that of the plain FP32 scheme (which those forms follow within their stated error),
+ * computed on an FP32 copy of the problem that the call creates and frees (same stream and
+ * device-memory hooks, started from the handle's initial concentration).  BGK:
  * Omega = I / lambda with lambda from the largest D_mumu and K_mu scaled by
  * h_mu = D_mumu / max D (end of Section 2.2), so dL/dD_mumu includes both dependences;
  * where several D_mumu share the maximum, each takes an equal part of d(max D) (the

@@ -248,7 +248,7 @@ def apply_along_axis(K: torch.Tensor, C: torch.Tensor, mu: int) -> torch.Tensor:
 # --------------------------------------------------------------------------- problem -> operators
 
 class Operators:
-    """All per-problem quantities of Algorithm 1's initialisation (items 1-3), as FP64 tensors.
+    """All per-problem quantities of Algorithm 1's initialisation, as FP64 tensors.
 
     Differentiable w.r.t. alpha, p, D (diagonal entries or full tensor) and u when they are
     passed as tensors with requires_grad.
@@ -385,7 +385,7 @@ def _vec(x, d) -> torch.Tensor:
 # --------------------------------------------------------------------------- the time step
 
 def fractional_terms(ops: Operators, C: torch.Tensor) -> List[torch.Tensor]:
-    """F_mu = p_mu I+^{2-alpha_mu}(g_mu C) + (1-p_mu) I-^{2-alpha_mu}(g_mu C), Algorithm 1 loop item 1."""
+    """F_mu = p_mu I+^{2-alpha_mu}(g_mu C) + (1-p_mu) I-^{2-alpha_mu}(g_mu C), the fractional terms of Algorithm 1's time step."""
     if ops.fields:
         return [apply_along_axis(ops.K[mu], ops.gfield[mu] * C, mu) for mu in range(ops.d)]
     return [apply_along_axis(ops.K[mu], C, mu) for mu in range(ops.d)]
@@ -494,7 +494,7 @@ def source_term(ops: Operators, t: float) -> torch.Tensor:
 
 
 def concentration(f: torch.Tensor) -> torch.Tensor:
-    """C = <1|f>, Algorithm 1 loop item 5."""
+    """C = <1|f>, the moment of Algorithm 1's time step."""
     return f.sum(0)
 
 
@@ -504,17 +504,17 @@ def init_populations(ops: Operators, C0: torch.Tensor) -> torch.Tensor:
 
 
 def step(ops: Operators, f: torch.Tensor, n: int = 0) -> torch.Tensor:
-    """One pass of Algorithm 1's time loop (items 1-5) from populations f(t) to f(t+dt),
+    """One pass of Algorithm 1's time loop from populations f(t) to f(t+dt),
     t = n dt (the time matters only for a source or wall values that depend on it)."""
     C = concentration(f)
-    F = fractional_terms(ops, C)                 # item 1
-    feq = equilibrium(ops, C, F)                 # item 2
-    fstar = collide(ops, f, feq)                 # item 2 (right-hand side)
+    F = fractional_terms(ops, C)                 # fractional terms
+    feq = equilibrium(ops, C, F)                 # equilibrium
+    fstar = collide(ops, f, feq)                 # collision
     if ops.source is not None:
         fstar = fstar + source_term(ops, n * ops.dt)
-    fnew = stream(ops, fstar)                    # item 3
-    fnew = dirichlet(ops, fnew, (n + 1) * ops.dt)  # item 4
-    return fnew                                  # item 5: C = concentration(fnew)
+    fnew = stream(ops, fstar)                    # streaming
+    fnew = dirichlet(ops, fnew, (n + 1) * ops.dt)  # walls
+    return fnew                                  # moment: C = concentration(fnew)
 
 
 def run_fields_C(pb, C0, nsteps: int, fields) -> torch.Tensor:

@@ -1,6 +1,6 @@
 // Discrete adjoint of the time step and parameter gradients of a snapshot loss.
 //
-// With the parameters fixed, one step (Algorithm 1, loop items 1-5) is linear in the
+// With the parameters fixed, one time step of Algorithm 1 is linear in the
 // populations f: C = <1|f>, F_mu = K_mu C along axis mu, feq = E(C, F) (Eqs. Feq,
 // CoeffA_FADE3D), f* = f - Omega (f - feq) (Eqs. LBE_Ket / MRT-Coll), push streaming
 // (Eq. Def_Translation) and the walls (Eq. Dirichlet_BC, affine).  Its transpose, in

@@ -1,5 +1,5 @@
-// C ABI of liblbm_fade: handle lifetime, parameter derivation (Algorithm 1,
-// initialisation items 1-4), graph-captured time stepping and host I/O.
+// C ABI of liblbm_fade: handle lifetime, parameter derivation (Algorithm 1's
+// initialisation), graph-captured time stepping and host I/O.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -343,7 +343,7 @@ DevMem current_hooks() {
 
 bool uses_tc(const lbm_s* h) { return h->tc != nullptr; }
 
-// F = fractional terms of the current C (Algorithm 1, loop item 1).  On the tensor-core
+// F = fractional terms of the current C (the first stage of Algorithm 1's time step).  On the tensor-core
 // path the hi/lo split of C is refreshed first (inside the time loop the fused
 // collide-stream kernel writes it, so one_step skips this).
 int run_frac(lbm_s* h, cudaStream_t s) {
@@ -479,7 +479,8 @@ extern "C" {
 // One problem: validation, buffers, weights, initial state.  Sub-problems of a batch
 // (batched = true) run their operator as part of a grouped launch: 128-wide column
 // tiles, no k-split.
-static int create_problem(const lbm_params* prm, const double* C0_host, void* stream, bool batched, lbm_t* out) {
+static int create_problem(const lbm_params* prm, const double* C0_host, void* stream, bool batched, lbm_t* out,
+                          const DevMem* mem = nullptr) {
   if (!out || !C0_host) return LBM_EINVAL;
   *out = nullptr;
   Derived dv;
@@ -493,7 +494,7 @@ static int create_problem(const lbm_params* prm, const double* C0_host, void* st
   h->elem = (prm->precision == LBM_FP64) ? 8 : 4;
   h->sp = dv.sp;
   h->graph_steps = 128;  // steps per captured graph (even); longer graphs, fewer replay boundaries
-  h->mem = current_hooks();
+  h->mem = mem ? *mem : current_hooks();
   cudaGetDevice(&h->device);
   auto fail = [&](int code) {
     free_all(h);
@@ -1404,9 +1405,28 @@ static int step_hook(lbm_s* h, int& cur, cudaStream_t s) { return one_step(h, cu
 int lbm_grad(lbm_t h, int nsnap, const int* snap_steps, const double* obs, int ckpt_every, double* loss,
              double* grad) {
   if (!h || nsnap < 1 || !snap_steps || !obs || ckpt_every < 1 || !loss || !grad) return LBM_EINVAL;
-  if (h->is_batch() || h->tc || h->fld.on) return LBM_ENOTSUP;
+  if (h->is_batch() || h->fld.on) return LBM_ENOTSUP;
   for (int k = 0; k < nsnap; ++k)
     if (snap_steps[k] < 0 || (k > 0 && snap_steps[k] <= snap_steps[k - 1])) return LBM_EINVAL;
+  if (h->tc) {
+    // split-precision forms: the adjoint of the plain FP32 scheme, which these forms follow
+    // within their stated error, on an FP32 copy of the problem started from the handle's
+    // initial concentration (same stream, same device-memory hooks)
+    lbm_params p32 = h->prm;
+    p32.precision = LBM_FP32;
+    const long long nodes = h->sp.nodes;
+    std::vector<double> C0((size_t)nodes);
+    LBM_CUDA(lbm::launch_convert_out(h->dev.C0, h->elem, h->dev.stage, nodes, h->stream));
+    LBM_CUDA(cudaMemcpyAsync(C0.data(), h->dev.stage, sizeof(double) * nodes, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    lbm_t t = nullptr;
+    int rc = create_problem(&p32, C0.data(), h->stream, false, &t, &h->mem);
+    if (rc) return rc;
+    rc = lbm_grad(t, nsnap, snap_steps, obs, ckpt_every, loss, grad);
+    lbm_destroy(t);
+    const int rc2 = lbm_reset(h);
+    return rc ? rc : rc2;
+  }
   double dOm[3][lbm::kMaxQ][lbm::kMaxQ];
   int rc = derive_dOmega(&h->prm, dOm);
   if (rc) return rc;

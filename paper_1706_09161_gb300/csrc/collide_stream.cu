@@ -1,11 +1,11 @@
 // Fused equilibrium + collision + streaming + Dirichlet walls + new concentration.
 //
-// One launch performs items 2-5 of Algorithm 1's time loop for every node:
-//   item 2  equilibrium   feq = A + (C/e^2)(dt/dx) u_mu |e_mu w>            Eqs. (Feq), (CoeffA_FADE3D)
+// One launch performs the rest of Algorithm 1's time step after the fractional terms:
+//           equilibrium   feq = A + (C/e^2)(dt/dx) u_mu |e_mu w>            Eqs. (Feq), (CoeffA_FADE3D)
 //           collision     f* = f - Omega (f - feq)                          Eqs. (LBE_Ket), (MRT-Coll)
-//   item 3  streaming     f_i(x + e_i, t+dt) = f*_i(x, t)                   Eq. (Def_Translation)
-//   item 4  walls         f_b = C_wall - sum_{i != b} f_i                   Eq. (Dirichlet_BC)
-//   item 5  moment        C = <1|f>
+//           streaming     f_i(x + e_i, t+dt) = f*_i(x, t)                   Eq. (Def_Translation)
+//           walls         f_b = C_wall - sum_{i != b} f_i                   Eq. (Dirichlet_BC)
+//           moment        C = <1|f>
 // Populations are stored after streaming and boundary treatment, so a CTA
 // collides its nodes plus a one-node ring and gathers ("pulls") each population
 // from the node it came from; the ring's collisions are recomputed by the
@@ -295,7 +295,7 @@ __device__ __forceinline__ void write_split(const SplitOut& so, long long o, rea
   }
 }
 
-// Mass of the new concentration (Algorithm 1, loop item 5), as a by-product of the step.
+// Mass of the new concentration (the moment C = <1|f> of Algorithm 1), as a by-product of the step.
 // Every thread adds the C it wrote; each warp reduces its threads' sums in a fixed order
 // (xor shuffles: every lane ends with the same value) and stores one FP64 partial at
 // part[slot * kMassSlots + warp]; the handle adds the partials of the latest step in one

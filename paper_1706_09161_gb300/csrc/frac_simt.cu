@@ -1,6 +1,6 @@
 // Fractional terms on CUDA cores (FP64 and plain-FP32 forms).
 //
-// Algorithm 1, loop item 1 / Section 2.4, Eq. (XXminus_discret): along every
+// Algorithm 1 (fractional terms) / Section 2.4, Eq. (XXminus_discret): along every
 // lattice line of axis mu, F_mu[n] = sum_l K_mu[n][l] C[l].  Viewed over all
 // lines this is one dense GEMM per axis:
 //   axis x (fastest):  F[r][n] = sum_l C[r][l] K[n][l]     = C  * K^T   (rows r = other coords)

@@ -1,6 +1,6 @@
 // Fractional terms on the 5th-generation tensor cores (tcgen05), split precision.
 //
-// Algorithm 1, loop item 1 / Section 2.4, Eq. (XXminus_discret): along every lattice
+// Algorithm 1 (fractional terms) / Section 2.4, Eq. (XXminus_discret): along every lattice
 // line of axis mu, F_mu[n] = sum_l K_mu[n][l] C[l].  Over all lines of an axis this is
 // a dense GEMM (the weight matrix is Toeplitz up to its end columns, Eqs. c+ / c-):
 //

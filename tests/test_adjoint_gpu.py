@@ -108,14 +108,28 @@ def test_adjoint_bgk_3d(L):
     check(L, pb, W.random_field(rng, pb.grid), [6, 12], 5, "fp64", 1e-8)
 
 
+@pytest.mark.parametrize("form,coll", [("bf16x6split", "mrt"), ("tf32split", "bgk"), ("bf16split", "mrt")])
+def test_adjoint_split_forms(L, form, coll):
+    """On a split-precision handle lbm_grad returns the plain FP32 scheme's gradient (computed
+    on an FP32 copy of the problem) and leaves the handle at its initial state."""
+    rng = np.random.default_rng(61 + len(form))
+    pb = W.random_problem(rng, 2, coll, (40, 33), spherical=(coll == "bgk"))
+    check(L, pb, W.random_field(rng, pb.grid), [20, 40], 10, form, 1e-4)
+
+
 def test_grad_refuses_unsupported(L):
     rng = np.random.default_rng(1)
-    pb = W.random_problem(rng, 2, "bgk", (32, 32), spherical=True)
+    pb = W.random_problem(rng, 2, "mrt", (32, 32))
     C0 = W.random_field(rng, pb.grid)
-    with L.Lattice(pb, C0, "bf16split") as lat:
+    with L.Lattice(pb, C0, "fp32") as lat:
+        lat.set_fields(u=np.full((2,) + pb.shape, 0.01))
         with pytest.raises(L.LBMError) as ei:
             lat.grad([5], np.zeros((1,) + pb.shape), 2)
         assert ei.value.code == L.LBM_ENOTSUP
+    probs, fields, _ = W.batch64(nprob=2, sides=(64,), seed=3)
+    with L.Batch(probs, fields, "fp32") as b:
+        with pytest.raises(L.LBMError):
+            L.lbm_grad(b.h, [5], np.zeros((1,) + probs[0].shape), 2, 2)
 
 
 def test_autograd_function_fits_parameters(L):

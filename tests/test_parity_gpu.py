@@ -62,7 +62,7 @@ GRIDS_3D = [(3, 3, 3), (19, 13, 11), (40, 9, 6), (44, 21, 37)]
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("grid", GRIDS_2D + GRIDS_3D)
 def test_fractional_terms(L, precision, grid):
-    """Loop item 1 (Section 2.4): F_mu of the initial concentration."""
+    """Fractional terms (Section 2.4): F_mu of the initial concentration."""
     rng = np.random.default_rng(len(grid) * 100 + grid[0])
     d = len(grid)
     pb = W.random_problem(rng, d, "mrt", grid)
@@ -80,7 +80,7 @@ def test_fractional_terms(L, precision, grid):
 @pytest.mark.parametrize("collision", ["bgk", "mrt"])
 @pytest.mark.parametrize("grid", GRIDS_2D + GRIDS_3D)
 def test_steps_match_oracle(L, precision, collision, grid):
-    """Algorithm 1 loop items 1-5, 12 steps: concentration and populations."""
+    """Algorithm 1's time step, 12 steps: concentration and populations."""
     rng = np.random.default_rng(7 + len(grid) * 10 + grid[0])
     d = len(grid)
     pb = W.random_problem(rng, d, collision, grid, spherical=(collision == "bgk"))
@@ -181,7 +181,7 @@ def test_mass_reduction(L):
 @pytest.mark.parametrize("precision,rel", [("fp64", 1e-12), ("fp32", 1e-6), ("bf16split", 1e-6)])
 @pytest.mark.parametrize("grid", [(130, 70), (64, 48, 40), (37, 29)])
 def test_mass_of_every_step_from_the_collide_stream_partials(L, precision, rel, grid):
-    """Algorithm 1, loop item 5: the FP64 mass the collide-stream kernel leaves as block
+    """Algorithm 1's moment: the FP64 mass the collide-stream kernel leaves as block
     partials after each step equals the oracle's sum of C (FP64 path 1e-12, FP32 paths
     1e-6, on a well-conditioned problem: alpha >= 1.5, D >= 0.02, where FP32 C itself stays
     within 1e-6), and the sum of the C the step wrote (same values, summed on the host)."""

@@ -56,7 +56,7 @@ GRIDS = [(3, 3), (37, 29), (130, 70), (200, 131), (19, 13, 11), (40, 9, 6), (131
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("grid", GRIDS)
 def test_tc_fractional_terms(L, kind, grid):
-    """Loop item 1 (Section 2.4) on the tensor cores, every axis."""
+    """Fractional terms (Section 2.4) on the tensor cores, every axis."""
     rng = np.random.default_rng(31 + grid[0] + len(grid))
     d = len(grid)
     pb = W.random_problem(rng, d, "mrt", grid)
