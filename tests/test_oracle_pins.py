@@ -965,13 +965,15 @@ def _pins_pass():
                 return False
         test_wall_concentration_imposed(2, 0.25)
         test_mrt_flux_moments_relax_with_lambdabar_inverse()
+        test_caputo_operator_exact_on_constants_and_linear_functions(0.5, 0.3)
     except AssertionError:
         return False
     return True
 
 
 def test_planted_mistakes_are_caught(monkeypatch):
-    """Each plausible oracle bug below makes at least one pin fail (mistakes planted on the CPU)."""
+    """Each plausible oracle bug below makes at least one pin fail (mistakes planted on the CPU).
+    The literal end-node diagonal is the other reading of Eqs. (c+), (c-) at the line's end."""
     assert _pins_pass()
     orig_wm, orig_fm, orig_eq, orig_bc = O.weight_matrices, O.frac_matrix, O.equilibrium, O.dirichlet
 
@@ -995,6 +997,14 @@ def test_planted_mistakes_are_caught(monkeypatch):
         Wm[:-1, -1] = 0
         return Wp, Wm
 
+    def end_diagonal_literal(g, N):
+        # the diagonal rule "l = n => 1" also at the line's own end (an empty interval)
+        Wp, Wm = orig_wm(g, N)
+        Wp, Wm = Wp.clone(), Wm.clone()
+        Wp[0, 0] = 1.0
+        Wm[N, N] = 1.0
+        return Wp, Wm
+
     def flip_u(ops, C, F):
         saved = ops.u
         ops.u = -saved
@@ -1015,7 +1025,7 @@ def test_planted_mistakes_are_caught(monkeypatch):
         return torch.where(unknown, (ops.C_wall - known_sum).unsqueeze(0).expand_as(f), f)
 
     mistakes = [("weight_matrices", swap_pm), ("frac_matrix", no_gamma_fn), ("frac_matrix", wrong_order),
-                ("weight_matrices", end_coeff_dropped), ("equilibrium", flip_u),
+                ("weight_matrices", end_coeff_dropped), ("weight_matrices", end_diagonal_literal), ("equilibrium", flip_u),
                 ("equilibrium", rest_weight_wrong), ("dirichlet", bc_ignores_corners)]
     for name, fn in mistakes:
         with monkeypatch.context() as m:
