@@ -1,10 +1,10 @@
 """The GPU discrete adjoint (lbm_grad) against the FP64 oracle's adjoint (autograd through
 the plain restatement, itself pinned to central finite differences in the CPU tests).
 
-Bounds: FP64 handles 1e-8 relative per gradient component; FP32 handles 1e-4 relative (the
-stated gradient bar), each on the components larger than 1e-3 of the largest one of their
-own family (alpha, p, D, u).  BGK and MRT, 2-D and 3-D; after lbm_grad the handle holds its
-initial state bit for bit."""
+Bounds: FP64 handles 1e-8, FP32 and split-precision handles 1e-4 (the stated gradient bar):
+every component within that fraction of its family's largest component (alpha, p, D, u), and
+the components above 1e-2 of it within that fraction of themselves.  BGK and MRT, 2-D and
+3-D; after lbm_grad the handle holds its initial state bit for bit."""
 import dataclasses
 
 import numpy as np
@@ -54,9 +54,13 @@ def check(L, pb, C0, snaps, ckpt, precision, rtol):
     assert loss == pytest.approx(loss_ref, rel=max(rtol, 1e-12))
     d = pb.d
     for k, fam in enumerate(("alpha", "p", "D", "u")):
-        # each parameter family against its own largest component
+        # each parameter family against its own largest component: every component within
+        # rtol of that, and the components above 1e-2 of it within rtol of themselves (the
+        # arithmetic's error scales with the family, not with a small component)
         a, b = grad[k * d:(k + 1) * d], grad_ref[k * d:(k + 1) * d]
-        big = np.abs(b) > 1e-3 * np.abs(b).max()
+        top = np.abs(b).max()
+        assert np.all(np.abs(a - b) <= rtol * top), (fam, a, b)
+        big = np.abs(b) > 1e-2 * top
         rel = np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
         assert np.all(rel[big] < rtol), (fam, a, b)
     # the handle is left at its initial state, bit for bit
