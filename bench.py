@@ -66,7 +66,7 @@ WORKLOADS = {
     "varying_512": dict(desc="2-D D2Q5 MRT 512x512 on [0,1]^2 (dx=1/511, dt for lambda=1 at the mean D) with "
                              "spatially varying D(x)=0.02(1+-0.5) incl. off-diagonal entries, g(x)=1+-0.2, "
                              "u(x)=(0.1,-0.05)+-0.05, alpha=(1.6,1.8), p=(0.4,0.6), unit-mass Gaussian sigma=0.05, "
-                             "2000 steps", default_precision="fp32", oracle_steps=200),
+                             "2000 steps", default_precision="fp32", oracle_steps=200, other_forms=("bf16x6split",)),
     "exact_e5": dict(desc="Section 3.4's exact-solution case: 2-D D2Q5 MRT 256x256 on ]0,1[^2, alpha=(1.5,1.7), "
                           "p=1, D_mumu(x)=x^alpha Gamma(a+2-alpha)/Gamma(a+2), a=(0.4,0.7), source -3 exp(-t) x^a1 y^a2, "
                           "time-dependent wall values from C=exp(-t) x^a1 y^a2, t=0.1 (33564 steps)",

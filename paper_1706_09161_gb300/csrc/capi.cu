@@ -456,7 +456,9 @@ static int upload_weights(lbm_s* h, const double* hfac, std::vector<std::vector<
     const int side = prm->grid[mu];
     K.assign((size_t)side * side, 0.0);
     KT.assign((size_t)side * side, 0.0);
-    const double scale = (h->fld.on && !h->tc) ? 1.0 : prm->g[mu] * hfac[mu];
+    // g multiplies C inside the integrals (SIMT operator with fields, or g(x) on the tensor
+    // cores), or is folded into K
+    const double scale = (h->fld.on && (!h->tc || h->fld.gvar)) ? 1.0 : prm->g[mu] * hfac[mu];
     lbm::build_frac_matrix(prm->alpha[mu], prm->p[mu], scale, side, prm->dx, prm->variant, K.data());
     for (int n = 0; n < side; ++n)
       for (int l = 0; l < side; ++l) KT[(size_t)l * side + n] = K[(size_t)n * side + l];
@@ -1220,10 +1222,10 @@ static int rebuild_fields(lbm_s* h) {
     const size_t E = h->elem;
     if ((rc = alloc_bytes(h, &h->fld.coll, E * NC * nodes)) || (rc = alloc_bytes(h, &h->fld.advw, E * d * nodes)))
       return rc;
-    // g(x) and the operator input G = g C only for the SIMT operator (tensor-core forms fold
-    // the uniform g into K)
-    if (!h->tc && ((rc = alloc_bytes(h, &h->fld.g, E * d * nodes)) || (rc = alloc_bytes(h, &h->fld.G, E * d * nodes))))
-      return rc;
+    // g(x) for the SIMT operator's input G = g C, or for the tensor-core operands of g_mu(x) C
+    // (the tensor-core forms fold a uniform g into K and need neither)
+    if ((!h->tc || g_field) && (rc = alloc_bytes(h, &h->fld.g, E * d * nodes))) return rc;
+    if (!h->tc && (rc = alloc_bytes(h, &h->fld.G, E * d * nodes))) return rc;
     const std::pair<const std::vector<double>*, void*> ups[3] = {{&coll, h->fld.coll}, {&advw, h->fld.advw},
                                                                  {&gv, h->fld.g}};
     for (const auto& up : ups) {
@@ -1241,10 +1243,13 @@ static int rebuild_fields(lbm_s* h) {
   }
   h->pdl = pdl_fits(h);  // the march, and with tf32 whether the operands need a launch of their own
   if (h->tc) lbm::tc_set_pdl(h, h->pdl);
-  if (!h->tc) {  // g inside the integrals (K without g), or folded into K; the tensor-core K keeps g
+  h->fld.gvar = h->fld.on && g_field != nullptr;
+  {  // g inside the integrals (K without g), or folded into K
     Derived dv;
     if ((rc = derive(&h->prm, &dv))) return rc;
-    if ((rc = upload_weights(h, dv.h, nullptr))) return rc;
+    std::vector<std::vector<double>> Kall;
+    if ((rc = upload_weights(h, dv.h, h->tc ? &Kall : nullptr))) return rc;
+    if (h->tc && ((rc = lbm::tc_set_weights(h, Kall)) || (rc = lbm::tc_set_gfield(h, h->fld.gvar)))) return rc;
   }
   return lbm_reset(h);
 }
@@ -1295,7 +1300,8 @@ static int ensure_time_table(lbm_s* h) {
 int lbm_set_fields(lbm_t h, const double* D_field, const double* g_field, const double* u_field) {
   int rc = fields_supported(h);
   if (rc) return rc;
-  if (g_field && h->tc) return LBM_ENOTSUP;  // g(x) inside the integrals: FP64 / FP32 forms
+  // g(x) on the tensor cores: an operand g_mu(x) C per axis, bf16 parts only
+  if (g_field && h->tc && h->prm.precision == LBM_FP32_TF32SPLIT) return LBM_ENOTSUP;
   const size_t nodes = (size_t)h->sp.nodes, d = (size_t)h->d;
   // validate on a copy first: the handle stays unchanged when the arrays are rejected
   lbm::FieldState keep;

@@ -61,6 +61,11 @@ struct FieldPtrs {
   const real* src;
   const real* cw;
   const double* tf;
+  // tensor-core forms with g(x): the operand parts of g_mu(x) C per axis ([mu][part], pitch
+  // gldp), written in place of those of C
+  void* gs[3][3];
+  int gsplit;
+  int gldp;
 };
 
 template <typename real>
@@ -527,7 +532,18 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
 #pragma unroll
       for (int q = 0; q < Q; ++q) f_out[q * nodes + node] = fv[q];
       C_out[node] = C;
-      if (SPLIT) write_split<SPLIT>(so, ((long long)z * n1 + gy) * so.ldp + gx, C);
+      if (SPLIT && FLD && fp.gsplit) {
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+          SplitOut sm{};
+          sm.hi = fp.gs[mu][0];
+          sm.lo = fp.gs[mu][1];
+          sm.lo2 = fp.gs[mu][2];
+          write_split<SPLIT>(sm, ((long long)z * n1 + gy) * fp.gldp + gx, fp.g[mu * nodes + node] * C);
+        }
+      } else if (SPLIT) {
+        write_split<SPLIT>(so, ((long long)z * n1 + gy) * so.ldp + gx, C);
+      }
       if (FLD && fp.G) {  // the SIMT operator's inputs of the next step: g_mu(x) C, one field per axis
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) fp.G[mu * nodes + node] = fp.g[mu * nodes + node] * C;
@@ -1544,10 +1560,16 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
     cfg.gridDim = dim3(bx, by, nz);
     h->cs_nparts = bx * by * nz;
     const int early = one_wave(cfg.gridDim) ? 1 : 0;
-    const FieldPtrs<real> fp{static_cast<const real*>(h->fld.coll), static_cast<const real*>(h->fld.advw),
-                             static_cast<const real*>(h->fld.g),    static_cast<real*>(h->fld.G),
-                             static_cast<const real*>(h->fld.src),  static_cast<const real*>(h->fld.cw),
-                             h->fld.tf ? h->fld.tf + 2 * tk : nullptr};
+    FieldPtrs<real> fp{static_cast<const real*>(h->fld.coll), static_cast<const real*>(h->fld.advw),
+                       static_cast<const real*>(h->fld.g),    static_cast<real*>(h->fld.G),
+                       static_cast<const real*>(h->fld.src),  static_cast<const real*>(h->fld.cw),
+                       h->fld.tf ? h->fld.tf + 2 * tk : nullptr, {}, 0, 0};
+    if (h->tc && h->tc->gvar) {
+      fp.gsplit = 1;
+      fp.gldp = h->tc->ldp;
+      for (int mu = 0; mu < 3; ++mu)
+        for (int k = 0; k < 3; ++k) fp.gs[mu][k] = h->tc->gp[mu][k];
+    }
     if constexpr (sizeof(real) == 4) {
       // tensor-core forms: the march also writes the operator's operands of the new C
       if (split == 1)

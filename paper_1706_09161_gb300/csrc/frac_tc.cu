@@ -521,6 +521,31 @@ __global__ void split_C_kernel(const float* __restrict__ C, void* __restrict__ h
   }
 }
 
+// bf16 forms with g(x): for every axis mu the parts of g_mu(x) C (g_mu at g[mu * nodes + i]),
+// each the bf16 rounding of what the previous ones left, at gp.p[mu][part] (pitch ldp)
+struct GParts {
+  void* p[3][3];
+};
+__global__ void split_G_kernel(const float* __restrict__ C, const float* __restrict__ g, GParts gp, int d, int cparts,
+                               int n0, int n1, int n2, int ldp) {
+  const long long total = (long long)n0 * n1 * n2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = static_cast<int>(i % n0);
+    const long long o = (i / n0) * ldp + x;
+    const float c = C[i];
+    for (int mu = 0; mu < d; ++mu) {
+      const float v = g[mu * total + i] * c;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      const float r1 = v - __bfloat162float(h);
+      const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+      static_cast<__nv_bfloat16*>(gp.p[mu][0])[o] = h;
+      static_cast<__nv_bfloat16*>(gp.p[mu][1])[o] = l;
+      if (cparts == 3) static_cast<__nv_bfloat16*>(gp.p[mu][2])[o] = __float2bfloat16_rn(r1 - __bfloat162float(l));
+    }
+  }
+}
+
 // tf32 split of C regrouped along axis mu (1: y, 2: z) in groups of 4 (layout at
 // TcPlan::ct_hi): one thread per (x, group, remaining axis) reads the group's 4 values
 // (coalesced over x) and writes one 16-byte group per part (coalesced over x); values
@@ -649,6 +674,50 @@ cudaError_t launch_persist(const TcPlan* p, cudaStream_t s) {
 
 }  // namespace
 
+// Split K_mu (FP64, row-major side x side) into the plan's parts on the host and upload
+// them (rows padded to ldk[mu], axis blocks at koff[mu]); each part rounds what the previous
+// ones left.
+int tc_set_weights(lbm_s* h, const std::vector<std::vector<double>>& K) {
+  TcPlan* p = h->tc;
+  if (!p) return LBM_EINVAL;
+  const int E = p->elem;
+  const int n[3] = {h->sp.n[0], h->sp.n[1], h->sp.n[2]};
+  size_t ktot = 0;
+  for (int mu = 0; mu < h->d; ++mu) ktot += (size_t)p->ldk[mu] * n[mu];
+  std::vector<uint8_t> hbuf(ktot * E, 0), lbuf(ktot * E, 0), l2buf(p->kparts == 3 ? ktot * E : 0, 0);
+  for (int mu = 0; mu < h->d; ++mu) {
+    const size_t off = p->koff[mu];
+    const int side = n[mu];
+    for (int r = 0; r < side; ++r)
+      for (int c = 0; c < side; ++c) {
+        const double x = K[mu][(size_t)r * side + c];
+        const size_t o = off + (size_t)r * p->ldk[mu] + c;
+        if (E == 2) {
+          const uint16_t hb = bf16_rne_host(static_cast<float>(x));
+          const double r1 = x - bf16_to_float_host(hb);
+          const uint16_t lb = bf16_rne_host(static_cast<float>(r1));
+          std::memcpy(&hbuf[o * 2], &hb, 2);
+          std::memcpy(&lbuf[o * 2], &lb, 2);
+          if (p->kparts == 3) {
+            const uint16_t l2 = bf16_rne_host(static_cast<float>(r1 - bf16_to_float_host(lb)));
+            std::memcpy(&l2buf[o * 2], &l2, 2);
+          }
+        } else {
+          const float hf = tf32_rna_host(static_cast<float>(x));
+          const float lf = tf32_rna_host(static_cast<float>(x - hf));
+          std::memcpy(&hbuf[o * 4], &hf, 4);
+          std::memcpy(&lbuf[o * 4], &lf, 4);
+        }
+      }
+  }
+  if (cudaMemcpy(h->dev.Khi, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return LBM_ECUDA;
+  if (cudaMemcpy(h->dev.Klo, lbuf.data(), lbuf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return LBM_ECUDA;
+  if (p->kparts == 3 &&
+      cudaMemcpy(h->dev.Kl2, l2buf.data(), l2buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return LBM_ECUDA;
+  return LBM_OK;
+}
+
 // Allocate the split operands, split K_mu on the host, encode the tensor maps.
 int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn, int force_ks) {
   TcPlan* p = new (std::nothrow) TcPlan();
@@ -698,46 +767,17 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   if (dev_alloc(h, (void**)&h->dev.Khi, ktot * E) != cudaSuccess) return LBM_ENOMEM;
   if (dev_alloc(h, (void**)&h->dev.Klo, ktot * E) != cudaSuccess) return LBM_ENOMEM;
   if (p->kparts == 3 && dev_alloc(h, (void**)&h->dev.Kl2, ktot * E) != cudaSuccess) return LBM_ENOMEM;
-  std::vector<uint8_t> hbuf(ktot * E, 0), lbuf(ktot * E, 0), l2buf(p->kparts == 3 ? ktot * E : 0, 0);
   size_t koff[3] = {0, 0, 0};
   size_t off = 0;
   for (int mu = 0; mu < h->d; ++mu) {
     koff[mu] = off;
-    const int side = n[mu];
-    for (int r = 0; r < side; ++r)
-      for (int c = 0; c < side; ++c) {
-        const double x = K[mu][(size_t)r * side + c];
-        const size_t o = off + (size_t)r * ldk[mu] + c;
-        if (E == 2) {
-          // parts from the FP64 weight: each part rounds what the previous ones left
-          const uint16_t hb = bf16_rne_host(static_cast<float>(x));
-          const double r1 = x - bf16_to_float_host(hb);
-          const uint16_t lb = bf16_rne_host(static_cast<float>(r1));
-          std::memcpy(&hbuf[o * 2], &hb, 2);
-          std::memcpy(&lbuf[o * 2], &lb, 2);
-          if (p->kparts == 3) {
-            const uint16_t l2 = bf16_rne_host(static_cast<float>(r1 - bf16_to_float_host(lb)));
-            std::memcpy(&l2buf[o * 2], &l2, 2);
-          }
-        } else {
-          const float hf = tf32_rna_host(static_cast<float>(x));
-          const float lf = tf32_rna_host(static_cast<float>(x - hf));
-          std::memcpy(&hbuf[o * 4], &hf, 4);
-          std::memcpy(&lbuf[o * 4], &lf, 4);
-        }
-      }
-    off += (size_t)ldk[mu] * side;
+    off += (size_t)ldk[mu] * n[mu];
   }
-  if (cudaMemcpy(h->dev.Khi, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return LBM_ECUDA;
-  if (cudaMemcpy(h->dev.Klo, lbuf.data(), lbuf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return LBM_ECUDA;
-  if (p->kparts == 3 &&
-      cudaMemcpy(h->dev.Kl2, l2buf.data(), l2buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-    return LBM_ECUDA;
-
   for (int mu = 0; mu < h->d; ++mu) {
     p->ldk[mu] = ldk[mu];
     p->koff[mu] = koff[mu];
   }
+  if (int rc = tc_set_weights(h, K)) return rc;
   p->f_elems = (size_t)h->d * h->sp.nodes;
 
   // default plan: column tiles of 128 (an M = 128 MMA costs the same for any N <= 128)
@@ -850,9 +890,13 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
       if (!encode(&p->maps.c_hi[mu], E, 4, p->ct_hi[mu], tdims, tstr, tbox, false)) return LBM_ECUDA;
       if (!encode(&p->maps.c_lo[mu], E, 4, p->ct_lo[mu], tdims, tstr, tbox, false)) return LBM_ECUDA;
     } else {
-      if (!encode(&p->maps.c_hi[mu], E, 3, h->dev.Chi, cdims, cstr, box)) return LBM_ECUDA;
-      if (!encode(&p->maps.c_lo[mu], E, 3, h->dev.Clo, cdims, cstr, box)) return LBM_ECUDA;
-      if (p->cparts == 3 && !encode(&p->maps.c_l2[mu], E, 3, h->dev.Cl2, cdims, cstr, box)) return LBM_ECUDA;
+      // the split of C, or with g(x) the split of this axis's g_mu(x) C
+      void* c0 = p->gvar ? p->gp[mu][0] : h->dev.Chi;
+      void* c1 = p->gvar ? p->gp[mu][1] : h->dev.Clo;
+      void* c2 = p->gvar ? p->gp[mu][2] : h->dev.Cl2;
+      if (!encode(&p->maps.c_hi[mu], E, 3, c0, cdims, cstr, box)) return LBM_ECUDA;
+      if (!encode(&p->maps.c_lo[mu], E, 3, c1, cdims, cstr, box)) return LBM_ECUDA;
+      if (p->cparts == 3 && !encode(&p->maps.c_l2[mu], E, 3, c2, cdims, cstr, box)) return LBM_ECUDA;
     }
     const cuuint64_t kdims[2] = {(cuuint64_t)n[mu], (cuuint64_t)n[mu]};
     const cuuint64_t kstr[1] = {(cuuint64_t)ldk[mu] * E};
@@ -906,6 +950,7 @@ void tc_release(lbm_s* h) {
     for (int mu = 0; mu < 3; ++mu) {
       dev_free(h, h->tc->ct_hi[mu]);
       dev_free(h, h->tc->ct_lo[mu]);
+      for (int k = 0; k < 3; ++k) dev_free(h, h->tc->gp[mu][k]);
     }
   delete h->tc;
   h->tc = nullptr;
@@ -1042,12 +1087,44 @@ cudaError_t launch_split_T_step(const lbm_s* h, cudaStream_t s) {
   return cs_writes_T(h) ? cudaSuccess : launch_split_T(h, s);
 }
 
+// bf16 forms with g(x): operand parts of g_mu(x) C for every axis mu
+int tc_set_gfield(lbm_s* h, bool on) {
+  TcPlan* p = h->tc;
+  if (!p) return LBM_EINVAL;
+  if (on && p->elem != 2) return LBM_ENOTSUP;
+  if (on == p->gvar) return LBM_OK;
+  for (int mu = 0; mu < 3; ++mu)
+    for (int k = 0; k < 3; ++k) {
+      dev_free(h, p->gp[mu][k]);
+      p->gp[mu][k] = nullptr;
+    }
+  p->gvar = false;
+  if (on) {
+    const size_t bytes = (size_t)p->ldp * h->sp.n[1] * h->sp.n[2] * p->elem;
+    for (int mu = 0; mu < h->d; ++mu)
+      for (int k = 0; k < p->cparts; ++k) {
+        if (dev_alloc(h, &p->gp[mu][k], bytes) != cudaSuccess) return LBM_ENOMEM;
+        if (cudaMemset(p->gp[mu][k], 0, bytes) != cudaSuccess) return LBM_ECUDA;
+      }
+    p->gvar = true;
+  }
+  return tc_replan(h, p->bn, p->prm.ksplit, p->persist ? 1 : 0);  // re-encodes the operand maps
+}
+
 cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s) {
   const TcPlan* p = h->tc;
   if (!p) return cudaErrorNotSupported;
   long long b = (h->sp.nodes + 255) / 256;
   const long long cap = 16LL * device_sms();
   if (b > cap) b = cap;
+  if (p->gvar) {
+    GParts gp{};
+    for (int mu = 0; mu < 3; ++mu)
+      for (int k = 0; k < 3; ++k) gp.p[mu][k] = p->gp[mu][k];
+    split_G_kernel<<<(int)b, 256, 0, s>>>(static_cast<const float*>(h->dev.C), static_cast<const float*>(h->fld.g), gp,
+                                          h->d, p->cparts, h->sp.n[0], h->sp.n[1], h->sp.n[2], p->ldp);
+    return cudaGetLastError();
+  }
   if (p->elem == 2)
     split_C_kernel<2><<<(int)b, 256, 0, s>>>(static_cast<const float*>(h->dev.C), h->dev.Chi, h->dev.Clo,
                                              p->cparts == 3 ? h->dev.Cl2 : nullptr, h->sp.n[0], h->sp.n[1],

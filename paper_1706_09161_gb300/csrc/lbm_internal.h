@@ -39,6 +39,7 @@ struct StepParams {
 struct FieldState {
   bool on = false;     // the per-node kernel path runs (coefficients, source or wall values)
   bool coeff = false;  // D, g or u vary (lbm_set_fields)
+  bool gvar = false;   // g varies (the operator's input is g_mu(x) C, K_mu without g)
   void* coll = nullptr;
   void* advw = nullptr;
   void* g = nullptr;
@@ -241,6 +242,8 @@ bool tc_one_wave(const lbm_s* h);  // the tensor-core operator grid fits in one 
 void tc_set_pdl(lbm_s* h, bool on);
 cudaError_t launch_collide_stream_batch(const lbm_s* b, int parity, cudaStream_t s);
 void tc_release(lbm_s* h);
+int tc_set_weights(lbm_s* h, const std::vector<std::vector<double>>& K);  // re-split K_mu (plan kept)
+int tc_set_gfield(lbm_s* h, bool on);  // bf16 forms: operands g_mu(x) C per axis (or C)
 int tc_split_pitch(const lbm_s* h);
 
 // host-side weight build (FP64), K row-major [n][l] for one axis

@@ -71,6 +71,10 @@ struct TcPlan {
   void* ct_lo[3] = {nullptr, nullptr, nullptr};
   int tg[3] = {0, 0, 0};  // groups of 4 along axis mu: ceil(n_mu / 4)
   int tpx = 0;            // x pitch of the regrouped copies: n0 rounded up to 16
+  // bf16 forms with g varying in space: the operand of axis mu is g_mu(x) C, split into
+  // cparts parts gp[mu][k] (layout of the C split, pitch ldp); K_mu then carries no g
+  bool gvar = false;
+  void* gp[3][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
 };
 
 namespace {
