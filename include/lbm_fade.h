@@ -305,6 +305,17 @@ int lbm_set_source(lbm_t h, const double* S_field, double rate);
  * constant C_wall of lbm_params.  Otherwise as lbm_set_source. */
 int lbm_set_wall_values(lbm_t h, const double* Cw_field, double rate);
 
+/* New constant parameters for an existing single-problem handle: alpha, p, g, D, u, s_free,
+ * dx, dt and C_wall may change; lattice, collision, precision, grid and variant may not
+ * (LBM_EINVAL).  The weights (Section 2.4) and the collision constants (Eqs. MatrixS, D_ab,
+ * Diffusion_Coefficient_3D) are rebuilt in place, the device buffers, the launch plan and any
+ * coefficient fields, source or wall values are kept, and the handle re-initialises from its
+ * initial concentration (as lbm_reset).  This is how a fit of the parameters (lbm_grad in a
+ * loop) avoids a new handle per evaluation.  LBM_EINVAL for inadmissible parameters (as
+ * lbm_create; the handle keeps the old ones then), LBM_ENOTSUP as lbm_set_fields for the
+ * tensor-core forms.  Synchronises. */
+int lbm_set_params(lbm_t h, const lbm_params* prm);
+
 /* Killed stable-Levy random walk (Section 3.1: Eqs. RW_STABLE and distri; the bounded-domain
  * subsection: a path is killed at its first exit from the box), the paper's Monte-Carlo
  * counterpart of the scheme.  The density of the live paths solves the FADE with

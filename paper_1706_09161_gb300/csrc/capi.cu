@@ -1324,6 +1324,53 @@ int lbm_set_fields(lbm_t h, const double* D_field, const double* g_field, const 
   return rc;
 }
 
+int lbm_set_params(lbm_t h, const lbm_params* prm) {
+  if (!h || !prm || h->is_batch()) return LBM_EINVAL;
+  const lbm_params& o = h->prm;
+  if (prm->lattice != o.lattice || prm->collision != o.collision || prm->precision != o.precision ||
+      prm->variant != o.variant)
+    return LBM_EINVAL;
+  for (int mu = 0; mu < 3; ++mu)
+    if (prm->grid[mu] != o.grid[mu]) return LBM_EINVAL;
+  Derived dv;
+  int rc = derive(prm, &dv);
+  if (rc) return rc;
+  if (h->tc && h->fld.on && prm->collision == LBM_BGK)
+    for (int a = 1; a < h->d; ++a)
+      if (prm->D[4 * a] != prm->D[0]) return LBM_ENOTSUP;  // as lbm_set_fields
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  drop_graphs(h);  // the captured launches carry the old constants
+  const lbm_params keep = h->prm;
+  const lbm::StepParams keep_sp = h->sp;
+  h->prm = *prm;
+  lbm::StepParams sp = dv.sp;
+  sp.ksum = keep_sp.ksum;  // the launch plan stays: its partial sums of F
+  sp.pstride = keep_sp.pstride;
+  h->sp = sp;
+  if (h->fld.on) {
+    rc = rebuild_fields(h);  // per-node rates, g and the weights from the new constants
+  } else {
+    std::vector<std::vector<double>> Kall;
+    rc = upload_weights(h, dv.h, h->tc ? &Kall : nullptr);
+    if (!rc && h->tc) rc = lbm::tc_set_weights(h, Kall);
+    if (!rc) rc = lbm_reset(h);
+  }
+  if (rc == LBM_EINVAL) {  // e.g. a field no longer admissible with the new constants
+    h->prm = keep;
+    h->sp = keep_sp;
+    if (h->fld.on) {
+      rebuild_fields(h);
+    } else {
+      std::vector<std::vector<double>> Kall;
+      Derived d0;
+      if (!derive(&keep, &d0) && !upload_weights(h, d0.h, h->tc ? &Kall : nullptr) && h->tc)
+        lbm::tc_set_weights(h, Kall);
+      lbm_reset(h);
+    }
+  }
+  return rc;
+}
+
 int lbm_set_source(lbm_t h, const double* S_field, double rate) {
   int rc = fields_supported(h);
   if (rc) return rc;

@@ -108,6 +108,7 @@ def _load() -> ctypes.CDLL:
         "lbm_set_fields": (ctypes.c_int, [vp, dp, dp, dp]),
         "lbm_set_source": (ctypes.c_int, [vp, dp, ctypes.c_double]),
         "lbm_set_wall_values": (ctypes.c_int, [vp, dp, ctypes.c_double]),
+        "lbm_set_params": (ctypes.c_int, [vp, P(lbm_params)]),
         "lbm_walk": (ctypes.c_int, [P(lbm_walk_params), ctypes.c_longlong, vp, vp, ctypes.c_longlong, ctypes.c_int,
                                     vp]),
         "lbm_walk_density": (ctypes.c_int, [P(lbm_walk_params), ctypes.c_longlong, vp, vp, P(ctypes.c_int),
@@ -323,6 +324,11 @@ def lbm_set_wall_values(h: int, Cw=None, rate: float = 0.0) -> None:
            "lbm_set_wall_values")
 
 
+def lbm_set_params(h: int, prm: lbm_params) -> None:
+    """New constant parameters for the handle (same lattice, collision, precision, grid, variant)."""
+    _check(_lib.lbm_set_params(ctypes.c_void_p(h), ctypes.byref(prm)), "lbm_set_params")
+
+
 def walk_params(d: int, alpha, p, D, g, u, lo, hi, dt: float, seed: int, precision: str = "fp32") -> lbm_walk_params:
     prm = lbm_walk_params()
     prm.d = int(d)
@@ -481,6 +487,13 @@ class Lattice:
 
     def set_C(self, C: np.ndarray) -> None:
         lbm_set_C(self.h, C)
+
+    def set_params(self, pb) -> None:
+        """New constant parameters from a problem of the same lattice, collision and grid;
+        re-initialises from the initial concentration."""
+        prm = params_from_problem(pb, self.prm.precision)
+        lbm_set_params(self.h, prm)
+        self.problem, self.prm = pb, prm
 
     def reset(self) -> None:
         lbm_reset(self.h)
@@ -646,12 +659,14 @@ def _problem_with_theta(problem, theta):
                                D=tuple(tuple(r) for r in D), u=tuple(th[3 * d:4 * d]))
 
 
-def snapshot_loss(problem, C0, snap_steps, obs, theta, precision: str = "fp32", ckpt_every: int = 100):
+def snapshot_loss(problem, C0, snap_steps, obs, theta, precision: str = "fp32", ckpt_every: int = 100,
+                  lattice: Optional["Lattice"] = None):
     """Differentiable L(theta) = sum_k |C(t_k) - obs_k|^2, theta = [alpha, p, D_diag, u] (torch tensor).
 
     Forward and gradient are one lbm_grad call (discrete adjoint on the GPU); backward
-    returns the stored gradient scaled by the incoming one.  Each call builds a handle
-    with the current parameters.
+    returns the stored gradient scaled by the incoming one.  With `lattice` (a Lattice of
+    this problem and C0) the handle is reused across calls (lbm_set_params); otherwise each
+    call builds a handle with the current parameters.
     """
     import torch
 
@@ -659,8 +674,12 @@ def snapshot_loss(problem, C0, snap_steps, obs, theta, precision: str = "fp32", 
         @staticmethod
         def forward(ctx, th):
             pb = _problem_with_theta(problem, th.detach().cpu().tolist())
-            with Lattice(pb, C0, precision) as lat:
-                loss, grad = lat.grad(snap_steps, obs, ckpt_every)
+            if lattice is not None:
+                lattice.set_params(pb)
+                loss, grad = lattice.grad(snap_steps, obs, ckpt_every)
+            else:
+                with Lattice(pb, C0, precision) as lat:
+                    loss, grad = lat.grad(snap_steps, obs, ckpt_every)
             ctx.save_for_backward(torch.as_tensor(grad, dtype=th.dtype, device=th.device))
             return th.new_tensor(loss)
 

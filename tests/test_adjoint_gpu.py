@@ -159,17 +159,23 @@ def test_autograd_function_fits_parameters(L):
     th = theta.detach().clone()
     L0 = float(loss)
     cur = L0
-    for _ in range(6):
-        t = th.clone().requires_grad_(True)
-        lt = L.snapshot_loss(pb, C0, snaps, obs, t, "fp64", 5)
-        lt.backward()
-        step = -(t.grad * mask)
-        step = step / step.abs().max() * 0.01
+    # one handle for the whole fit (lbm_set_params between evaluations)
+    with L.Lattice(pb, C0, "fp64") as lat:
         for _ in range(6):
-            cand = th + step
-            lc = float(L.snapshot_loss(pb, C0, snaps, obs, cand, "fp64", 5))
-            if lc < cur:
-                th, cur = cand, lc
-                break
-            step = step / 2
+            t = th.clone().requires_grad_(True)
+            lt = L.snapshot_loss(pb, C0, snaps, obs, t, "fp64", 5, lattice=lat)
+            lt.backward()
+            # the reused handle gives what a new handle gives
+            t2 = th.clone().requires_grad_(True)
+            L.snapshot_loss(pb, C0, snaps, obs, t2, "fp64", 5).backward()
+            assert torch.allclose(t.grad, t2.grad, rtol=1e-13, atol=0)
+            step = -(t.grad * mask)
+            step = step / step.abs().max() * 0.01
+            for _ in range(6):
+                cand = th + step
+                lc = float(L.snapshot_loss(pb, C0, snaps, obs, cand, "fp64", 5, lattice=lat))
+                if lc < cur:
+                    th, cur = cand, lc
+                    break
+                step = step / 2
     assert cur < 0.5 * L0

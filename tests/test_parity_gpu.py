@@ -359,3 +359,44 @@ def test_fp32_contraction_split_matches_oracle(L, grid):
             lat.configure(0, 1 if ks > 1 else min(2, kbmin))
             lat.step(n)
             arith_bounds.check_form(lat.C(), pb, C0, 2 * n, "fp32", f"split {ks}")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x6split", "tf32split"])
+def test_set_params_equals_a_new_handle(L, precision):
+    """lbm_set_params rebuilds weights and collision constants in place: the run equals a new
+    handle's bit for bit (also with a coefficient field kept); inadmissible parameters leave
+    the handle as it was; a different grid or precision is refused."""
+    rng = np.random.default_rng(1201)
+    pa = W.random_problem(rng, 2, "mrt", (64, 56))
+    pb_ = dataclasses.replace(W.random_problem(rng, 2, "mrt", (64, 56)), s_free=pa.s_free)
+    C0 = W.random_field(rng, pa.grid)
+    with L.Lattice(pb_, C0, precision) as ref:
+        ref.step(30)
+        C_b = ref.C()
+    with L.Lattice(pa, C0, precision) as ref:
+        ref.step(30)
+        C_a = ref.C()
+    with L.Lattice(pa, C0, precision) as lat:
+        lat.step(7)
+        lat.set_params(pb_)
+        lat.step(30)
+        assert np.array_equal(lat.C(), C_b)
+        with pytest.raises(L.LBMError):
+            lat.set_params(dataclasses.replace(pa, alpha=(2.5, 1.5)))
+        lat.set_params(pa)
+        lat.step(30)
+        assert np.array_equal(lat.C(), C_a)
+        with pytest.raises(L.LBMError):
+            L.lbm_set_params(lat.h, L.params_from_problem(dataclasses.replace(pa, grid=(64, 48)), precision))
+        with pytest.raises(L.LBMError):
+            L.lbm_set_params(lat.h, L.params_from_problem(pa, "fp64"))
+    u = np.full((2,) + pa.shape, 0.01)
+    with L.Lattice(pb_, C0, precision) as ref:
+        ref.set_fields(u=u)
+        ref.step(20)
+        C_bu = ref.C()
+    with L.Lattice(pa, C0, precision) as lat:
+        lat.set_fields(u=u)
+        lat.set_params(pb_)
+        lat.step(20)
+        assert np.array_equal(lat.C(), C_bu)
