@@ -12,7 +12,9 @@ plain PyTorch CPU ops so that the discrete adjoint is available through
 autograd.  Every function cites the section / equation it follows:
 
 * lattices D2Q5 / D3Q7, weights, e^2 .......... Section 2.1, Eq. (weights_c), Fig. 1 caption
-* trapezoidal product-integration weights ..... Section 2.4, Eqs. (1Dminus_discret), (c+), (c-)
+* trapezoidal product-integration weights ..... Section 2.4, Eqs. (1Dminus_discret), (c+), (c-);
+                                                 the differences of powers taken in 40-digit
+                                                 decimal arithmetic, then rounded to FP64
 * per-axis fractional term F_mu ............... Section 2.4, Eq. (XXminus_discret); Eq. (M2_FADE_3D)
 * Caputo-type variant F~ ...................... Section 3.5, Eqs. (Fg2), (PSRLdD-a/b), (Fg22),
                                                  (CoeffA_FADE3DPS)
