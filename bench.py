@@ -470,12 +470,12 @@ class Runner:
                    "algorithmic_per_launch": bytes_, "launch_ms": dur * 1e3, "peak_source": peak_src}
         if precision in SPLIT_PRODUCTS:
             # the kernel also writes the operator's operands of the new C: its split into
-            # two (hi/lo) or three bf16 parts (x contiguous) and, for tf32 on the TMA-fed
-            # marches (one operator and one collide-stream launch per step), the copies
-            # regrouped along y (and z)
-            per_node = {"tf32split": 8, "bf16split": 4, "bf16x5split": 4, "bf16x6split": 6}[precision]
+            # two (hi/lo) or three bf16 parts, or for tf32 C itself (FP32, split by the
+            # operator on chip), x contiguous; and for tf32 on the TMA-fed marches (one
+            # operator and one collide-stream launch per step) C regrouped along y (and z)
+            per_node = {"tf32split": 4, "bf16split": 4, "bf16x5split": 4, "bf16x6split": 6}[precision]
             if precision == "tf32split" and self.lat.launches_per_step == 2:
-                per_node += 8 * (d - 1)
+                per_node += 4 * (d - 1)
             ex = bytes_ + float(self.nodes) * per_node
             roof_cs["executed_per_launch"] = ex
             roof_cs["executed_frac"] = ex / dur / 1e9 / peak

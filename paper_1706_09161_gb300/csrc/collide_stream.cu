@@ -244,23 +244,16 @@ __device__ __forceinline__ void collide_moments(const KConst<real>& sp, const Fi
   }
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// Operands of the split-precision fractional operator: C = hi + lo (+ residual), with
-// hi, lo in bf16 (SPLIT = 1) or tf32 (SPLIT = 2), x-pitch ldp.
+// Operands of the split-precision fractional operator, x-pitch ldp: bf16 parts C = hi + lo
+// (SPLIT = 1) or hi + lo + lo2 (SPLIT = 3); tf32 (SPLIT = 2): C itself in hi (FP32).
 struct SplitOut {
   void* hi;
   void* lo;
   int ldp;
-  // tf32 on the TMA-fed marches: the split again, regrouped along y (index 0) and z
-  // (index 1) in groups of 4, the K-major operands of the y and z axes: element (x, y, z)
-  // at thi[0][((z tg1 + y/4) tpx + x) 4 + y%4] and thi[1][((z/4 n1 + y) tpx + x) 4 + z%4]
+  // tf32 on the TMA-fed marches: C again (FP32), regrouped along y (index 0) and z (index 1)
+  // in groups of 4, the K-major operands of the y and z axes: element (x, y, z) at
+  // thi[0][((z tg1 + y/4) tpx + x) 4 + y%4] and thi[1][((z/4 n1 + y) tpx + x) 4 + z%4]
   float* thi[2];
-  float* tlo[2];
   int tg1;  // groups of 4 along y
   int tpx;  // x pitch (n0 rounded up to 16)
   void* lo2;  // bf16 with C in three parts (SPLIT = 3): the third part
@@ -282,7 +275,8 @@ struct BatchCS {
 };
 
 // SPLIT: 1 = bf16 hi + lo, 3 = bf16 in three parts (each the rounding of what the previous
-// ones left: the three add up to C exactly), 2 = tf32 hi + lo
+// ones left: the three add up to C exactly), 2 = tf32: C itself in FP32 (the operator splits
+// it into tf32 hi + lo in shared memory)
 template <int SPLIT, typename real>
 __device__ __forceinline__ void write_split(const SplitOut& so, long long o, real C) {
   const float c = static_cast<float>(C);
@@ -294,9 +288,7 @@ __device__ __forceinline__ void write_split(const SplitOut& so, long long o, rea
     static_cast<__nv_bfloat16*>(so.lo)[o] = l;
     if (SPLIT == 3) static_cast<__nv_bfloat16*>(so.lo2)[o] = __float2bfloat16_rn(r1 - __bfloat162float(l));
   } else if (SPLIT == 2) {
-    const float h = tf32_rna(c);
-    static_cast<float*>(so.hi)[o] = h;
-    static_cast<float*>(so.lo)[o] = tf32_rna(c - h);
+    static_cast<float*>(so.hi)[o] = c;
   }
 }
 
@@ -877,34 +869,17 @@ collide_stream_tma3_kernel(const KConst<float> sp, const __grid_constant__ CUten
     const int zz = (ge & ~3) + (wy & 3), yq = 4 * (wy >> 2);
     if (zz >= gs && zz <= ge && gx < n0 && y0 + yq < n1) {
       const float* r = &s_c[((zz & 3) * TY + yq) * TCP + lane];
-      float4 hi, lo;
-      hi.x = tf32_rna(r[0]);       lo.x = tf32_rna(r[0] - hi.x);
-      hi.y = tf32_rna(r[TCP]);     lo.y = tf32_rna(r[TCP] - hi.y);
-      hi.z = tf32_rna(r[2 * TCP]); lo.z = tf32_rna(r[2 * TCP] - hi.z);
-      hi.w = tf32_rna(r[3 * TCP]); lo.w = tf32_rna(r[3 * TCP] - hi.w);
       const long long o = (((long long)zz * so.tg1 + ((y0 + yq) >> 2)) * so.tpx + gx) * 4;
-      *reinterpret_cast<float4*>(so.thi[0] + o) = hi;
-      *reinterpret_cast<float4*>(so.tlo[0] + o) = lo;
+      *reinterpret_cast<float4*>(so.thi[0] + o) = make_float4(r[0], r[TCP], r[2 * TCP], r[3 * TCP]);
     }
     if (in_xy) {
       const long long o = (((long long)(gs >> 2) * n1 + gy) * so.tpx + gx) * 4 + (gs & 3);
       if (cnt == 4) {
-        float4 hi, lo;
-        const float c0 = s_c[(0 * TY + wy) * TCP + lane], c1 = s_c[(1 * TY + wy) * TCP + lane];
-        const float c2 = s_c[(2 * TY + wy) * TCP + lane], c3 = s_c[(3 * TY + wy) * TCP + lane];
-        hi.x = tf32_rna(c0); lo.x = tf32_rna(c0 - hi.x);
-        hi.y = tf32_rna(c1); lo.y = tf32_rna(c1 - hi.y);
-        hi.z = tf32_rna(c2); lo.z = tf32_rna(c2 - hi.z);
-        hi.w = tf32_rna(c3); lo.w = tf32_rna(c3 - hi.w);
-        *reinterpret_cast<float4*>(so.thi[1] + o) = hi;
-        *reinterpret_cast<float4*>(so.tlo[1] + o) = lo;
+        *reinterpret_cast<float4*>(so.thi[1] + o) =
+            make_float4(s_c[(0 * TY + wy) * TCP + lane], s_c[(1 * TY + wy) * TCP + lane],
+                        s_c[(2 * TY + wy) * TCP + lane], s_c[(3 * TY + wy) * TCP + lane]);
       } else {
-        for (int k = 0; k < cnt; ++k) {
-          const float c = s_c[(((gs + k) & 3) * TY + wy) * TCP + lane];
-          const float h = tf32_rna(c);
-          so.thi[1][o + k] = h;
-          so.tlo[1][o + k] = tf32_rna(c - h);
-        }
+        for (int k = 0; k < cnt; ++k) so.thi[1][o + k] = s_c[(((gs + k) & 3) * TY + wy) * TCP + lane];
       }
     }
   };
@@ -1116,14 +1091,8 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
     const int xi = lane, yq = 4 * wy;
     if (wy < 4 && x0 + xi < n0 && t * TY + yq < n1) {
       const float* r = &s_c[((t & 1) * TY + yq) * TCP + xi];
-      float4 hi, lo;
-      hi.x = tf32_rna(r[0]);       lo.x = tf32_rna(r[0] - hi.x);
-      hi.y = tf32_rna(r[TCP]);     lo.y = tf32_rna(r[TCP] - hi.y);
-      hi.z = tf32_rna(r[2 * TCP]); lo.z = tf32_rna(r[2 * TCP] - hi.z);
-      hi.w = tf32_rna(r[3 * TCP]); lo.w = tf32_rna(r[3 * TCP] - hi.w);
       const long long o = ((long long)((t * TY + yq) >> 2) * so.tpx + x0 + xi) * 4;
-      *reinterpret_cast<float4*>(so.thi[0] + o) = hi;
-      *reinterpret_cast<float4*>(so.tlo[0] + o) = lo;
+      *reinterpret_cast<float4*>(so.thi[0] + o) = make_float4(r[0], r[TCP], r[2 * TCP], r[3 * TCP]);
     }
   };
   auto issue = [&](int t) {
@@ -1599,7 +1568,6 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
       if (split == 1) return launch_tma2<MRT, 1>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early, mp);
       if (split == 3) return launch_tma2<MRT, 3>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early, mp);
       so.thi[0] = static_cast<float*>(h->tc->ct_hi[1]);  // the y operand of the tf32 operator
-      so.tlo[0] = static_cast<float*>(h->tc->ct_lo[1]);
       so.tg1 = h->tc->tg[1];
       so.tpx = h->tc->tpx;
       return launch_tma2<MRT, 2>(cfg, sp, mf, pl->F, fo, Co, flag, so, ychunk, early, mp);
@@ -1625,7 +1593,6 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
       if (split == 3) return launch_tma3<MRT, 3>(cfg, sp, mf, pl->F, fo, Co, flag, so, nz, early, mp);
       for (int a = 0; a < 2; ++a) {  // the y and z operands of the tf32 operator
         so.thi[a] = static_cast<float*>(h->tc->ct_hi[a + 1]);
-        so.tlo[a] = static_cast<float*>(h->tc->ct_lo[a + 1]);
       }
       so.tg1 = h->tc->tg[1];
       so.tpx = h->tc->tpx;

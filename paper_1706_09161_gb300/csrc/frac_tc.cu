@@ -53,6 +53,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   uint64_t* empty = full + G::STAGES;
   uint64_t* done = empty + G::STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* split = done + 2;  // tf32: the stage's C split into hi + lo by warps 2-3
 
   const int warp = threadIdx.x >> 5;
 
@@ -79,6 +80,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     for (int s = 0; s < G::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      if (E == 4) mbar_init(&split[s], 2);  // one arrival per splitting warp
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -114,16 +116,30 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
       issue(i);
     }
   } else if (threadIdx.x == 32) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer (tf32: once the stage's C is split)
     const int amode = a_mode<E>(mu);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % G::STAGES;
-      if (!mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag)) break;
+      if (!mbar_wait(E == 4 ? &split[s] : &full[s], (i / G::STAGES) & 1, P.flag)) break;
       tc_fence_after();
       mma_stage<E, BN, KP>(tmem, i * ksteps<E>(), nreg, smem_u32(smem + (size_t)s * G::STAGE), amode);
       mma_commit(&empty[s]);
     }
     mma_commit(done);
+  } else if (E == 4 && warp >= 2) {
+    // ---------------- tf32: warps 2-3 split each stage's C into hi + lo
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % G::STAGES;
+      int ok = 1;
+      if ((threadIdx.x & 31) == 0) ok = mbar_wait(&full[s], (i / G::STAGES) & 1, P.flag) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);  // the lane's acquire, shared by the warp below
+      if (!ok) break;
+      __syncwarp();
+      split_stage_tf32<E, BN, KP>(smem + (size_t)s * G::STAGE, mu, threadIdx.x - 64, 64);
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&split[s])) : "memory");
+    }
   }
   __syncwarp();
 
@@ -225,6 +241,8 @@ frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
 // TMEM and returns with bit 2 of the error flag set.
 constexpr int PBN = 128;
 constexpr int kPersistThreads = 192;
+// tf32 adds two warps (6, 7) that split each stage's C into hi + lo
+__host__ __device__ constexpr int persist_threads(int E) { return E == 4 ? 256 : kPersistThreads; }
 
 // BN = 128 (three ring stages; two with the weights in three parts) or 256 (two; the
 // double accumulator then fills TMEM); KP = weight parts (2, or 3 for the five-product
@@ -265,6 +283,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   int* s_ok = reinterpret_cast<int*>(tmem_slot + 1);
+  uint64_t* split = drain + 2;  // [STAGES] tf32: the stage's C split into hi + lo by warps 6-7
 
   const int warp = threadIdx.x >> 5;
   const int first = blockIdx.x, stride = gridDim.x;
@@ -273,6 +292,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      if (E == 4) mbar_init(&split[s], 2);  // one arrival per splitting warp
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -336,7 +356,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
       const int amode = a_mode<E>(tl.mu);
       for (int kb = 0; kb < nkb; ++kb, ++r) {
         const int s = r % STAGES;
-        if (!mbar_wait(&full[s], (r / STAGES) & 1, flag)) {
+        if (!mbar_wait(E == 4 ? &split[s] : &full[s], (r / STAGES) & 1, flag)) {
           ok = false;
           break;
         }
@@ -348,6 +368,32 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
       if (ok) mma_commit(&tfull[b]);
     }
     mma_commit(drain);  // fires once every MMA issued above has completed
+  } else if (E == 4 && warp >= 6) {
+    // ---------------- tf32: warps 6-7 split each stage's C into hi + lo
+    int r = 0;
+    bool ok = true;
+    for (int t = first; t < ntiles && ok; t += stride) {
+      const TcMaps* maps;
+      const TcParams* P;
+      int cid;
+      locate(t, maps, P, cid);
+      const TileAt tl = decode_tile(*P, cid, BN);
+      const int nkb = P->ax[tl.mu].kblocks;
+      for (int kb = 0; kb < nkb; ++kb, ++r) {
+        const int s = r % STAGES;
+        int got = 1;
+        if ((threadIdx.x & 31) == 0) got = mbar_wait(&full[s], (r / STAGES) & 1, flag) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);  // the lane's acquire, shared by the warp below
+        if (!got) {
+          ok = false;
+          break;
+        }
+        __syncwarp();
+        split_stage_tf32<E, BN, KP>(smem + (size_t)s * G::STAGE, tl.mu, threadIdx.x - 192, 64);
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&split[s]);
+      }
+    }
   } else if (warp >= 2) {
     // ---------------- epilogue: 128 threads, TMEM lane quarter = warp % 4
     const int et = threadIdx.x - 64;
@@ -473,7 +519,7 @@ struct LocateBatch {
 };
 
 template <int E, int BN, int KP>
-__global__ void __launch_bounds__(kPersistThreads, 1)
+__global__ void __launch_bounds__(persist_threads(E), 1)
 frac_tc_persist_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P) {
   extern __shared__ uint8_t smem_raw[];
   persist_body<E, BN, KP>(LocateOne{&maps, &P}, P.total_tiles, P.flag, smem_raw);
@@ -514,9 +560,7 @@ __global__ void split_C_kernel(const float* __restrict__ C, void* __restrict__ h
       static_cast<__nv_bfloat16*>(lo)[o] = l;
       if (lo2) static_cast<__nv_bfloat16*>(lo2)[o] = __float2bfloat16_rn(r1 - __bfloat162float(l));
     } else {
-      const float h = tf32_rna(c);
-      static_cast<float*>(hi)[o] = h;
-      static_cast<float*>(lo)[o] = tf32_rna(c - h);
+      static_cast<float*>(hi)[o] = c;  // tf32: the operator splits C in shared memory
     }
   }
 }
@@ -546,12 +590,11 @@ __global__ void split_G_kernel(const float* __restrict__ C, const float* __restr
   }
 }
 
-// tf32 split of C regrouped along axis mu (1: y, 2: z) in groups of 4 (layout at
-// TcPlan::ct_hi): one thread per (x, group, remaining axis) reads the group's 4 values
-// (coalesced over x) and writes one 16-byte group per part (coalesced over x); values
-// past the end of the axis are zero.
-__global__ void split_T_kernel(const float* __restrict__ C, float* __restrict__ hi, float* __restrict__ lo, int n0,
-                               int n1, int n2, int mu, int tg, int tpx) {
+// tf32: C regrouped along axis mu (1: y, 2: z) in groups of 4 (layout at TcPlan::ct_hi):
+// one thread per (x, group, remaining axis) reads the group's 4 values (coalesced over x)
+// and writes one 16-byte group (coalesced over x); values past the end of the axis are zero.
+__global__ void split_T_kernel(const float* __restrict__ C, float* __restrict__ out, int n0, int n1, int n2, int mu,
+                               int tg, int tpx) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int g = blockIdx.y;   // group along mu
   const int r = blockIdx.z;   // remaining axis: z for the y copy, y for the z copy
@@ -563,14 +606,8 @@ __global__ void split_T_kernel(const float* __restrict__ C, float* __restrict__ 
   float v[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) v[k] = (4 * g + k < side) ? C[base + (4 * g + k) * step] : 0.0f;
-  float4 h, l;
-  h.x = tf32_rna(v[0]); l.x = tf32_rna(v[0] - h.x);
-  h.y = tf32_rna(v[1]); l.y = tf32_rna(v[1] - h.y);
-  h.z = tf32_rna(v[2]); l.z = tf32_rna(v[2] - h.z);
-  h.w = tf32_rna(v[3]); l.w = tf32_rna(v[3] - h.w);
   const long long o = mu == 1 ? (((long long)r * tg + g) * tpx + x) * 4 : (((long long)g * n1 + r) * tpx + x) * 4;
-  *reinterpret_cast<float4*>(hi + o) = h;
-  *reinterpret_cast<float4*>(lo + o) = l;
+  *reinterpret_cast<float4*>(out + o) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // ---------------------------------------------------------------------------- host
@@ -661,7 +698,7 @@ cudaError_t launch_persist(const TcPlan* p, cudaStream_t s) {
     return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::min(p->prm.total_tiles, device_sms()), 1, 1);  // one CTA per SM
-  cfg.blockDim = dim3(kPersistThreads, 1, 1);
+  cfg.blockDim = dim3(persist_threads(E), 1, 1);
   cfg.dynamicSmemBytes = PCfg<E, BN, KP>::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -737,10 +774,13 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
   const int ldp = (n[0] + 7) / 8 * 8;
   p->ldp = ldp;
   const size_t split_elems = (size_t)ldp * n[1] * n[2];
+  // bf16: the parts of C; tf32: C itself (FP32), split into hi + lo by the operator
   if (dev_alloc(h, (void**)&h->dev.Chi, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
-  if (dev_alloc(h, (void**)&h->dev.Clo, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
   cudaMemset(h->dev.Chi, 0, split_elems * E);
-  cudaMemset(h->dev.Clo, 0, split_elems * E);
+  if (E == 2) {
+    if (dev_alloc(h, (void**)&h->dev.Clo, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
+    cudaMemset(h->dev.Clo, 0, split_elems * E);
+  }
   if (p->cparts == 3) {
     if (dev_alloc(h, (void**)&h->dev.Cl2, split_elems * E) != cudaSuccess) return LBM_ENOMEM;
     cudaMemset(h->dev.Cl2, 0, split_elems * E);
@@ -751,9 +791,7 @@ int tc_prepare(lbm_s* h, const std::vector<std::vector<double>>& K, int force_bn
       p->tg[mu] = (n[mu] + 3) / 4;
       const size_t cnt = (size_t)4 * p->tg[mu] * p->tpx * (h->sp.nodes / n[0] / n[mu]);
       if (dev_alloc(h, &p->ct_hi[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
-      if (dev_alloc(h, &p->ct_lo[mu], cnt * 4) != cudaSuccess) return LBM_ENOMEM;
       cudaMemset(p->ct_hi[mu], 0, cnt * 4);
-      cudaMemset(p->ct_lo[mu], 0, cnt * 4);
     }
   }
 
@@ -888,14 +926,13 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
       const cuuint32_t tbox[4] = {64, (cuuint32_t)BM / 16, mu == 1 ? (cuuint32_t)(BK / 4) : 1u,
                                   mu == 1 ? 1u : (cuuint32_t)(BK / 4)};
       if (!encode(&p->maps.c_hi[mu], E, 4, p->ct_hi[mu], tdims, tstr, tbox, false)) return LBM_ECUDA;
-      if (!encode(&p->maps.c_lo[mu], E, 4, p->ct_lo[mu], tdims, tstr, tbox, false)) return LBM_ECUDA;
     } else {
       // the split of C, or with g(x) the split of this axis's g_mu(x) C
       void* c0 = p->gvar ? p->gp[mu][0] : h->dev.Chi;
       void* c1 = p->gvar ? p->gp[mu][1] : h->dev.Clo;
       void* c2 = p->gvar ? p->gp[mu][2] : h->dev.Cl2;
       if (!encode(&p->maps.c_hi[mu], E, 3, c0, cdims, cstr, box)) return LBM_ECUDA;
-      if (!encode(&p->maps.c_lo[mu], E, 3, c1, cdims, cstr, box)) return LBM_ECUDA;
+      if (E == 2 && !encode(&p->maps.c_lo[mu], E, 3, c1, cdims, cstr, box)) return LBM_ECUDA;
       if (p->cparts == 3 && !encode(&p->maps.c_l2[mu], E, 3, c2, cdims, cstr, box)) return LBM_ECUDA;
     }
     const cuuint64_t kdims[2] = {(cuuint64_t)n[mu], (cuuint64_t)n[mu]};
@@ -949,7 +986,6 @@ void tc_release(lbm_s* h) {
   if (h->tc)
     for (int mu = 0; mu < 3; ++mu) {
       dev_free(h, h->tc->ct_hi[mu]);
-      dev_free(h, h->tc->ct_lo[mu]);
       for (int k = 0; k < 3; ++k) dev_free(h, h->tc->gp[mu][k]);
     }
   delete h->tc;
@@ -1079,7 +1115,7 @@ cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s) {
   const float* C = static_cast<const float*>(h->dev.C);
   for (int mu = 1; mu < h->d; ++mu)
     split_T_kernel<<<dim3((n0 + 127) / 128, p->tg[mu], mu == 1 ? n2 : n1), 128, 0, s>>>(
-        C, static_cast<float*>(p->ct_hi[mu]), static_cast<float*>(p->ct_lo[mu]), n0, n1, n2, mu, p->tg[mu], p->tpx);
+        C, static_cast<float*>(p->ct_hi[mu]), n0, n1, n2, mu, p->tg[mu], p->tpx);
   return cudaGetLastError();
 }
 

@@ -59,8 +59,9 @@ struct TcPlan {
   size_t f_elems = 0;         // capacity of the F buffer (floats)
   size_t smem = 0;
   int ldp = 0;       // padded x pitch of the C split arrays (elements)
-  // tf32 only: the C split regrouped so that axis mu (1: y, 2: z) is the contraction of a
-  // K-major operand, in groups of 4 along mu (16 bytes) with x next (pitch tpx):
+  // tf32 only: C (FP32, split into tf32 hi + lo by the operator in shared memory) regrouped
+  // so that axis mu (1: y, 2: z) is the contraction of a K-major operand, in groups of 4
+  // along mu (16 bytes) with x next (pitch tpx):
   //   y copy  element (x, y, z) at ((z * tg[1] + y / 4) * tpx + x) * 4 + y % 4
   //   z copy  element (x, y, z) at ((z / 4 * n1 + y) * tpx + x) * 4 + z % 4
   // Entries past the end of an axis are zero.  A TMA box of (16 x, 4) x 8 x-blocks x 8
@@ -68,7 +69,6 @@ struct TcPlan {
   // 16-byte core matrices), and the collide-stream kernels write whole 16-byte groups of
   // consecutive x.
   void* ct_hi[3] = {nullptr, nullptr, nullptr};
-  void* ct_lo[3] = {nullptr, nullptr, nullptr};
   int tg[3] = {0, 0, 0};  // groups of 4 along axis mu: ceil(n_mu / 4)
   int tpx = 0;            // x pitch of the regrouped copies: n0 rounded up to 16
   // bf16 forms with g varying in space: the operand of axis mu is g_mu(x) C, split into
@@ -259,9 +259,11 @@ struct Cfg {
   static constexpr uint32_t A_BYTES = BM * 128;      // one operand part of A: 128 rows x 128 B
   static constexpr uint32_t B_BYTES = BN * 128;
   static constexpr uint32_t STAGE = NP * A_BYTES + NP * B_BYTES;
-  // bytes one k-block of axis mu loads: the weights in k_parts, C in c_parts
+  // parts of C one k-block loads: bf16 c_parts(KP); tf32 one (C itself, split on chip)
+  static constexpr int CL = E == 4 ? 1 : c_parts(KP);
+  // bytes one k-block of axis mu loads: the weights in k_parts, C in CL parts
   __host__ __device__ static constexpr uint32_t tx_bytes(int mu) {
-    return mu == 0 ? k_parts(KP) * A_BYTES + c_parts(KP) * B_BYTES : c_parts(KP) * A_BYTES + k_parts(KP) * B_BYTES;
+    return mu == 0 ? k_parts(KP) * A_BYTES + CL * B_BYTES : CL * A_BYTES + k_parts(KP) * B_BYTES;
   }
   static constexpr size_t RING = (size_t)STAGES * STAGE;
   static constexpr size_t SMEM = RING + 1024 /*align*/ + 256 /*barriers*/;
@@ -319,20 +321,16 @@ __device__ __forceinline__ void load_stage_conc(const TcMaps& maps, const TileAt
   uint8_t* b_hi = st + G::NP * G::A_BYTES;
   uint8_t* b_lo = b_hi + G::B_BYTES;
   if (t.mu == 0) {
-    // B = C rows y = ncol0.. at z = m_out
+    // B = C rows y = ncol0.. at z = m_out (tf32: C itself into the hi slot)
     tma_load_3d(b_hi, &maps.c_hi[0], k0, t.ncol0, t.m_out, bar);
-    tma_load_3d(b_lo, &maps.c_lo[0], k0, t.ncol0, t.m_out, bar);
+    if (E == 2) tma_load_3d(b_lo, &maps.c_lo[0], k0, t.ncol0, t.m_out, bar);
     if (c_parts(KP) == 3) tma_load_3d(b_lo + G::B_BYTES, &maps.c_l2[0], k0, t.ncol0, t.m_out, bar);
   } else if (E == 4) {
-    // tf32 parts: A = the regrouped C split (contraction in groups of 4), 128 x-lines
+    // tf32: A = C regrouped (contraction in groups of 4) into the hi slot, 128 x-lines
     // (8 blocks of 16), BK / 4 groups: dims (64, x blocks, y groups or y, z or z groups)
-    if (t.mu == 1) {
-      tma_load_4d(a_hi, &maps.c_hi[1], 0, t.m_in / 16, k0 / 4, t.m_out, bar);
-      tma_load_4d(a_lo, &maps.c_lo[1], 0, t.m_in / 16, k0 / 4, t.m_out, bar);
-    } else {
-      tma_load_4d(a_hi, &maps.c_hi[2], 0, t.m_in / 16, t.m_out, k0 / 4, bar);
-      tma_load_4d(a_lo, &maps.c_lo[2], 0, t.m_in / 16, t.m_out, k0 / 4, bar);
-    }
+    (void)a_lo;
+    if (t.mu == 1) tma_load_4d(a_hi, &maps.c_hi[1], 0, t.m_in / 16, k0 / 4, t.m_out, bar);
+    else tma_load_4d(a_hi, &maps.c_hi[2], 0, t.m_in / 16, t.m_out, k0 / 4, bar);
   } else {
     // bf16 parts: A = the C panel, MN-major (x contiguous), E boxes of 128/E lines
 #pragma unroll
@@ -357,6 +355,37 @@ template <int E, int BN, int KP = 2>
 __device__ __forceinline__ void load_stage(const TcMaps& maps, const TileAt& t, int k0, uint8_t* st, uint64_t* bar) {
   load_stage_weights<E, BN, KP>(maps, t, k0, st, bar);
   load_stage_conc<E, BN, KP>(maps, t, k0, st, bar);
+}
+
+// tf32 forms: C arrives in FP32 in the hi slot of its operand; before the MMAs the splitting
+// warps (nthr threads, this one numbered tid) replace it by its tf32 rounding and write the
+// rounding of the remainder to the lo slot, element by element, so the staged layout
+// (swizzled rows or regrouped core matrices) is kept as it landed.  Rounding: to nearest,
+// ties away from zero (cvt.rna).  The writes are made visible to the tensor cores' async
+// proxy before the caller signals the MMA thread.
+__device__ __forceinline__ float tc_tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <int E, int BN, int KP = 2>
+__device__ __forceinline__ void split_stage_tf32(uint8_t* st, int mu, int tid, int nthr) {
+  using G = Cfg<E, BN, 1, KP>;
+  const uint32_t bytes = mu == 0 ? G::B_BYTES : G::A_BYTES;
+  float4* hi = reinterpret_cast<float4*>(mu == 0 ? st + G::NP * G::A_BYTES : st);
+  float4* lo = hi + bytes / 16;
+  for (uint32_t i = tid; i < bytes / 16; i += nthr) {
+    const float4 v = hi[i];
+    float4 h, l;
+    h.x = tc_tf32_rna(v.x); l.x = tc_tf32_rna(v.x - h.x);
+    h.y = tc_tf32_rna(v.y); l.y = tc_tf32_rna(v.y - h.y);
+    h.z = tc_tf32_rna(v.z); l.z = tc_tf32_rna(v.z - h.z);
+    h.w = tc_tf32_rna(v.w); l.w = tc_tf32_rna(v.w - h.w);
+    hi[i] = h;
+    lo[i] = l;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // The split products of one k-block from ring stage `st` into accumulator `d` (first =
