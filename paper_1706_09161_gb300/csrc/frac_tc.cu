@@ -241,8 +241,9 @@ frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
 // TMEM and returns with bit 2 of the error flag set.
 constexpr int PBN = 128;
 constexpr int kPersistThreads = 192;
-// tf32 adds two warps (6, 7) that split each stage's C into hi + lo
-__host__ __device__ constexpr int persist_threads(int E) { return E == 4 ? 256 : kPersistThreads; }
+// tf32 adds four warps (6-9) that split each stage's C into hi + lo
+constexpr int kSplitWarps = 4;
+__host__ __device__ constexpr int persist_threads(int E) { return E == 4 ? kPersistThreads + 32 * kSplitWarps : kPersistThreads; }
 
 // BN = 128 (three ring stages; two with the weights in three parts) or 256 (two; the
 // double accumulator then fills TMEM); KP = weight parts (2, or 3 for the five-product
@@ -283,7 +284,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   int* s_ok = reinterpret_cast<int*>(tmem_slot + 1);
-  uint64_t* split = drain + 2;  // [STAGES] tf32: the stage's C split into hi + lo by warps 6-7
+  uint64_t* split = drain + 2;  // [STAGES] tf32: the stage's C split into hi + lo by warps 6-9
 
   const int warp = threadIdx.x >> 5;
   const int first = blockIdx.x, stride = gridDim.x;
@@ -292,7 +293,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      if (E == 4) mbar_init(&split[s], 2);  // one arrival per splitting warp
+      if (E == 4) mbar_init(&split[s], kSplitWarps);  // one arrival per splitting warp
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -369,7 +370,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
     }
     mma_commit(drain);  // fires once every MMA issued above has completed
   } else if (E == 4 && warp >= 6) {
-    // ---------------- tf32: warps 6-7 split each stage's C into hi + lo
+    // ---------------- tf32: warps 6-9 split each stage's C into hi + lo
     int r = 0;
     bool ok = true;
     for (int t = first; t < ntiles && ok; t += stride) {
@@ -389,7 +390,8 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
           break;
         }
         __syncwarp();
-        split_stage_tf32<E, BN, KP>(smem + (size_t)s * G::STAGE, tl.mu, threadIdx.x - 192, 64);
+        split_stage_tf32<E, BN, KP>(smem + (size_t)s * G::STAGE, tl.mu, threadIdx.x - kPersistThreads,
+                                    32 * kSplitWarps);
         __syncwarp();
         if ((threadIdx.x & 31) == 0) mbar_arrive(&split[s]);
       }
@@ -534,12 +536,6 @@ frac_tc_persist_batch_kernel(const TcMaps* __restrict__ maps, const TcParams* __
 }
 
 // ---------------------------------------------------------------------------- splits
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
 
 template <int E>
 __global__ void split_C_kernel(const float* __restrict__ C, void* __restrict__ hi, void* __restrict__ lo,

@@ -361,12 +361,11 @@ __device__ __forceinline__ void load_stage(const TcMaps& maps, const TileAt& t, 
 // warps (nthr threads, this one numbered tid) replace it by its tf32 rounding and write the
 // rounding of the remainder to the lo slot, element by element, so the staged layout
 // (swizzled rows or regrouped core matrices) is kept as it landed.  Rounding: to nearest,
-// ties away from zero (cvt.rna).  The writes are made visible to the tensor cores' async
-// proxy before the caller signals the MMA thread.
+// ties away from zero, on the magnitude bits (add half a unit of the 10-bit mantissa, clear
+// the 13 bits below it; finite values); two integer operations per element.  The writes are
+// made visible to the tensor cores' async proxy before the caller signals the MMA thread.
 __device__ __forceinline__ float tc_tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 template <int E, int BN, int KP = 2>
