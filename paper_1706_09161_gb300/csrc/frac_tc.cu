@@ -241,8 +241,8 @@ frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
 // TMEM and returns with bit 2 of the error flag set.
 constexpr int PBN = 128;
 constexpr int kPersistThreads = 192;
-// tf32 adds four warps (6-9) that split each stage's C into hi + lo
-constexpr int kSplitWarps = 4;
+// tf32 adds eight warps (6-13) that split each stage's C into hi + lo
+constexpr int kSplitWarps = 8;
 __host__ __device__ constexpr int persist_threads(int E) { return E == 4 ? kPersistThreads + 32 * kSplitWarps : kPersistThreads; }
 
 // BN = 128 (three ring stages; two with the weights in three parts) or 256 (two; the
@@ -284,7 +284,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   int* s_ok = reinterpret_cast<int*>(tmem_slot + 1);
-  uint64_t* split = drain + 2;  // [STAGES] tf32: the stage's C split into hi + lo by warps 6-9
+  uint64_t* split = drain + 2;  // [STAGES] tf32: the stage's C split into hi + lo by warps 6-13
 
   const int warp = threadIdx.x >> 5;
   const int first = blockIdx.x, stride = gridDim.x;
@@ -370,7 +370,7 @@ __device__ __forceinline__ void persist_body(const Locate& locate, int ntiles, i
     }
     mma_commit(drain);  // fires once every MMA issued above has completed
   } else if (E == 4 && warp >= 6) {
-    // ---------------- tf32: warps 6-9 split each stage's C into hi + lo
+    // ---------------- tf32: warps 6-13 split each stage's C into hi + lo
     int r = 0;
     bool ok = true;
     for (int t = first; t < ntiles && ok; t += stride) {
