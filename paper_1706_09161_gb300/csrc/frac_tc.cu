@@ -45,6 +45,11 @@ namespace {
 
 // One output tile (or one k-slice of it when KS > 1) of one problem; `block` is the
 // CTA's index among that problem's CTAs.  `maps` may live in parameter or global memory.
+// per-tile operator: 4 warps (producer, MMA issuer, all four drain TMEM); tf32 adds warps 4-7,
+// which with warps 2-3 split each stage's C into hi + lo and leave before the epilogue
+constexpr int kTileSplitWarps = 6;
+__host__ __device__ constexpr int tile_threads(int E) { return E == 4 ? 256 : 128; }
+
 template <int E, int BN, int KS, int KP = 2>
 __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams& P, int block, uint8_t* smem_raw) {
   using G = Cfg<E, BN, KS, KP>;
@@ -53,7 +58,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   uint64_t* empty = full + G::STAGES;
   uint64_t* done = empty + G::STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  uint64_t* split = done + 2;  // tf32: the stage's C split into hi + lo by warps 2-3
+  uint64_t* split = done + 2;  // tf32: the stage's C split into hi + lo by warps 2-7
 
   const int warp = threadIdx.x >> 5;
 
@@ -80,7 +85,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     for (int s = 0; s < G::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      if (E == 4) mbar_init(&split[s], 2);  // one arrival per splitting warp
+      if (E == 4) mbar_init(&split[s], kTileSplitWarps);  // one arrival per splitting warp
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -127,7 +132,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     }
     mma_commit(done);
   } else if (E == 4 && warp >= 2) {
-    // ---------------- tf32: warps 2-3 split each stage's C into hi + lo
+    // ---------------- tf32: warps 2-7 split each stage's C into hi + lo
     for (int i = 0; i < nkb; ++i) {
       const int s = i % G::STAGES;
       int ok = 1;
@@ -135,13 +140,14 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
       ok = __shfl_sync(0xffffffffu, ok, 0);  // the lane's acquire, shared by the warp below
       if (!ok) break;
       __syncwarp();
-      split_stage_tf32<E, BN, KP>(smem + (size_t)s * G::STAGE, mu, threadIdx.x - 64, 64);
+      split_stage_tf32<E, BN, KP>(smem + (size_t)s * G::STAGE, mu, threadIdx.x - 64, 32 * kTileSplitWarps);
       __syncwarp();
       if ((threadIdx.x & 31) == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&split[s])) : "memory");
     }
   }
   __syncwarp();
+  if (warp >= 4) return;  // tf32's extra splitting warps: the epilogue is warps 0-3
 
   // ---------------- epilogue
   bool have = mbar_wait(done, 0, P.flag);
@@ -171,7 +177,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   const int n0 = P.n0, n1 = P.n1;
   if (P.tma_store) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    named_sync128();  // warps 0-3 (tf32's extra warps have left)
     if (threadIdx.x == 0 && have) {
       int c1, c2;
       if (mu == 2) {
@@ -198,7 +204,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     }
   } else {
     // rows of F that are not 16-byte aligned: plain stores, coalesced along x
-    __syncthreads();
+    named_sync128();  // warps 0-3 (tf32's extra warps have left)
     const int x = m_in + row;
     if (have && x < n0) {
       for (int rr = r0; rr < r1; ++rr) {
@@ -211,7 +217,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     }
   }
   tc_fence_before();
-  __syncthreads();
+  named_sync128();  // warps 0-3 (tf32's extra warps have left)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(nreg * BN) : "memory");
@@ -220,7 +226,7 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
 }
 
 template <int E, int BN, int KS, int KP>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(tile_threads(E), 1)
 frac_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
   extern __shared__ uint8_t smem_raw[];
   frac_tc_tile<E, BN, KS, KP>(maps, P, blockIdx.x, smem_raw);
@@ -664,7 +670,7 @@ cudaError_t launch_kernel(const TcPlan* p, cudaStream_t s) {
   if (const cudaError_t e = smem_attr_once(attr, frac_tc_kernel<E, BN, KS, KP>, (int)Cfg<E, BN, KS, KP>::SMEM); e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->prm.total_tiles * KS, 1, 1);
-  cfg.blockDim = dim3(128, 1, 1);
+  cfg.blockDim = dim3(tile_threads(E), 1, 1);
   cfg.dynamicSmemBytes = Cfg<E, BN, KS, KP>::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
