@@ -94,8 +94,14 @@ __device__ __forceinline__ real frac_term(const KConst<real>& sp, const real* __
   return acc;
 }
 
+// The FP32 collision matrix of a block's problem in shared memory, rows padded to 8: the
+// grouped (batched) 2-D kernels stage it here and read each row in 128-bit loads
+// (collide_node<float, 2, true, KS = true>).
+__shared__ float4 s_om_rows[kMaxQ][2];
+
 // Equilibrium and collision of one node.  f: populations (in), fs: post-collision (out).
-template <typename real, int D, bool MRT>
+// KS: the matrix is read from s_om_rows (same products in the same order: bit-identical).
+template <typename real, int D, bool MRT, bool KS = false>
 __device__ __forceinline__ void collide_node(const KConst<real>& sp, const real* f, const real* F, real* fs) {
   constexpr int Q = Lat<D>::Q;
   real C = f[0];
@@ -123,9 +129,26 @@ __device__ __forceinline__ void collide_node(const KConst<real>& sp, const real*
     for (int q = 0; q < Q; ++q) dl[q] = f[q] - feq[q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      real acc = sp.omega[i][0] * dl[0];
+      real acc;
+      if constexpr (KS && sizeof(real) == 4) {
+        const float4 a = s_om_rows[i][0];
+        acc = a.x * dl[0];
+        acc += a.y * dl[1];
+        acc += a.z * dl[2];
+        acc += a.w * dl[3];
+        if constexpr (Q == 5) {
+          acc += s_om_rows[i][1].x * dl[4];
+        } else {
+          const float4 b = s_om_rows[i][1];
+          acc += b.x * dl[4];
+          acc += b.y * dl[5];
+          acc += b.z * dl[6];
+        }
+      } else {
+        acc = sp.omega[i][0] * dl[0];
 #pragma unroll
-      for (int j = 1; j < Q; ++j) acc += sp.omega[i][j] * dl[j];
+        for (int j = 1; j < Q; ++j) acc += sp.omega[i][j] * dl[j];
+      }
       fs[i] = f[i] - acc;
     }
   }
@@ -294,14 +317,17 @@ __device__ __forceinline__ void write_split(const SplitOut& so, long long o, rea
 
 // Mass of the new concentration (the moment C = <1|f> of Algorithm 1), as a by-product of the step.
 // Every thread adds the C it wrote; each warp reduces its threads' sums in a fixed order
-// (xor shuffles: every lane ends with the same value) and stores one FP64 partial at
-// part[slot * kMassSlots + warp]; the handle adds the partials of the latest step in one
-// small fixed-order pass when asked (lbm_mass).  FP32 concentrations are carried as an
+// (xor shuffles: every lane ends with the same value) and lane 0 stores the warp's partial
+// at part[slot * kMassSlots + warp]; the handle adds the partials of the latest step in one
+// small fixed-order FP64 pass when asked (lbm_mass).  FP32 concentrations are carried as an
 // unevaluated sum hi + lo of two floats, combined by TwoSum (Knuth), which keeps the sum
 // exact up to the rounding of lo (of order u^2 per addition, u = 2^-24) without FP64
-// arithmetic: the FP64 pipe is narrow, and the FP64 per-node sum and shuffles on the tail
-// of every block had cost 3-12% of the collide-stream kernels.  FP64 concentrations are
-// summed in FP64.  No block-wide barrier.  part may be null (no partial wanted).
+// arithmetic, and the partial is stored as the pair (hi, lo) in the 8-byte slot: the final
+// pass forms hi + lo in FP64.  The FP64 pipe is narrow (a warp instruction on it holds an
+// SM sub-partition for tens of cycles): the FP64 per-node sum had cost 3-12% of the
+// collide-stream kernels, and even the three FP64 operations per warp of a double partial
+// kept that pipe 11% busy at the tail of the 512^2 kernel.  FP64 concentrations are summed
+// and stored in FP64.  No block-wide barrier.  part may be null (no partial wanted).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bp = __fsub_rn(s, a);
@@ -314,11 +340,11 @@ template <>
 struct MassAcc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ double warp_total() {
+  __device__ __forceinline__ void warp_reduce() {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
   }
+  __device__ __forceinline__ void store(double* slot) const { *slot = s; }
 };
 template <>
 struct MassAcc<float> {
@@ -329,7 +355,7 @@ struct MassAcc<float> {
     hi = t;
     lo = __fadd_rn(lo, e);
   }
-  __device__ __forceinline__ double warp_total() {
+  __device__ __forceinline__ void warp_reduce() {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
@@ -338,15 +364,16 @@ struct MassAcc<float> {
       hi = t;
       lo = __fadd_rn(__fadd_rn(lo, ol), e);
     }
-    return static_cast<double>(hi) + static_cast<double>(lo);
   }
+  // the pair (hi, lo) in the slot's 8 bytes; the final pass adds hi + lo in FP64
+  __device__ __forceinline__ void store(double* slot) const { *reinterpret_cast<float2*>(slot) = make_float2(hi, lo); }
 };
 
 template <typename real>
 __device__ __forceinline__ void block_mass(MassAcc<real>& macc, double* part, int slot) {
-  const double v = macc.warp_total();
+  macc.warp_reduce();
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  if ((tid & 31) == 0 && part) part[(long long)slot * kMassSlots + (tid >> 5)] = v;
+  if ((tid & 31) == 0 && part) macc.store(part + (long long)slot * kMassSlots + (tid >> 5));
 }
 
 // Thread block: 16 warps own a 32 x 16 tile of nodes (one node per thread, full
@@ -359,7 +386,7 @@ __device__ __forceinline__ void block_mass(MassAcc<real>& macc, double* part, in
 constexpr int TX = 32, TY = 16, HALO_WARPS = 3;
 static_assert(kMassSlots * 32 == TX * (TY + HALO_WARPS), "one mass partial per warp of a block");
 
-template <typename real, int D, bool MRT, bool FLD = false>
+template <typename real, int D, bool MRT, bool FLD = false, bool KS = false>
 __device__ __forceinline__ void collide_at(const KConst<real>& sp, const real* __restrict__ f_in,
                                            const real* __restrict__ F, bool inside, long long node, real* fs,
                                            const FieldPtrs<real>& fp) {
@@ -376,7 +403,7 @@ __device__ __forceinline__ void collide_at(const KConst<real>& sp, const real* _
 #pragma unroll
   for (int mu = 0; mu < D; ++mu) Fv[mu] = frac_term(sp, F, mu, node);
   if (FLD) collide_node_field<real, D, MRT>(sp, fp, node, f, Fv, fs);
-  else collide_node<real, D, MRT>(sp, f, Fv, fs);
+  else collide_node<real, D, MRT, KS>(sp, f, Fv, fs);
 }
 
 // Asynchronous prefetch of the 2-D march (FP32): every thread copies the populations and
@@ -407,7 +434,7 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // One block's column (tile bx, by; planes z0 .. z1-1) of one problem.
-template <typename real, int D, bool MRT, int SPLIT, bool FLD = false>
+template <typename real, int D, bool MRT, int SPLIT, bool FLD = false, bool KS = false>
 __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* __restrict__ f_in,
                                            const real* __restrict__ F, real* __restrict__ f_out,
                                            real* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
@@ -450,22 +477,22 @@ __device__ __forceinline__ void march_body(const KConst<real>& sp, const real* _
   if (owner) {
     if (D == 3) {
       real t[Q];
-      collide_at<real, D, MRT, FLD>(sp, f_in, F, in_xy && z0 > 0, col + (z0 - 1) * plane, t, fp);
+      collide_at<real, D, MRT, FLD, KS>(sp, f_in, F, in_xy && z0 > 0, col + (z0 - 1) * plane, t, fp);
       prev5 = t[5];
     }
-    collide_at<real, D, MRT, FLD>(sp, f_in, F, in_xy, col + z0 * plane, cur, fp);
+    collide_at<real, D, MRT, FLD, KS>(sp, f_in, F, in_xy, col + z0 * plane, cur, fp);
   }
   int buf = 0;
   for (int z = z0; z < z1; ++z) {
     if (owner) {
-      if (D == 3) collide_at<real, D, MRT, FLD>(sp, f_in, F, in_xy && z + 1 < n2, col + (z + 1) * plane, nxt, fp);
+      if (D == 3) collide_at<real, D, MRT, FLD, KS>(sp, f_in, F, in_xy && z + 1 < n2, col + (z + 1) * plane, nxt, fp);
       s_m[buf][0][sy][sx] = cur[1];
       s_m[buf][1][sy][sx] = cur[2];
       s_m[buf][2][sy][sx] = cur[3];
       s_m[buf][3][sy][sx] = cur[4];
     } else {
       real h[Q];
-      collide_at<real, D, MRT, FLD>(sp, f_in, F, in_xy, col + z * plane, h, fp);
+      collide_at<real, D, MRT, FLD, KS>(sp, f_in, F, in_xy, col + z * plane, h, fp);
       if (wy == TY) {
         if (lane < 16) s_m[buf][0][sy][sx] = h[1];  // moves +x into the tile
         else s_m[buf][1][sy][sx] = h[2];            // moves -x into the tile
@@ -563,7 +590,7 @@ __shared__ float s_m2[2][4][TY + 2][TX + 2];
 // rows tr0 .. tr0 + ychunk - 1 of column bx), each thread prefetching its node of the
 // next two tiles through the cp.async ring while the current tile is collided.  The
 // per-tile work is that of march_body with one plane.
-template <bool MRT, int SPLIT>
+template <bool MRT, int SPLIT, bool KS = false>
 __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float* __restrict__ f_in,
                                             const float* __restrict__ F, float* __restrict__ f_out,
                                             float* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
@@ -631,7 +658,7 @@ __device__ __forceinline__ void march2_pipe(const KConst<float>& sp, const float
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) Fv[mu] = frac_term(sp, F, mu, gx + (long long)n0 * gy);
       }
-      collide_node<float, D, MRT>(sp, fv, Fv, fs);
+      collide_node<float, D, MRT, KS>(sp, fv, Fv, fs);
     } else {
 #pragma unroll
       for (int q = 0; q < Q; ++q) fs[q] = 0.f;
@@ -1044,7 +1071,7 @@ __device__ __forceinline__ void cs_tma_3d(void* dst, const CUtensorMap* map, int
 // tf32: C of the last two tile rows (slot t & 1), the source of the y-contiguous split
 __shared__ float s_c2[2 * TY * TCP];
 
-template <bool MRT, int SPLIT>
+template <bool MRT, int SPLIT, bool KS = false>
 __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtensorMap* map_f,
                                            const CUtensorMap* map_F, float* __restrict__ f_out,
                                            float* __restrict__ C_out, int* __restrict__ flag, const SplitOut& so,
@@ -1130,7 +1157,7 @@ __device__ __forceinline__ void march2_tma(const KConst<float>& sp, const CUtens
         for (int k = 1; k < ks; ++k) acc += st[TMA2_FF_OFF / 4 + ((k * D + mu) * TH + ly) * TW + lx];
         Fv[mu] = acc;
       }
-      collide_node<float, D, MRT>(sp, fv, Fv, fs);
+      collide_node<float, D, MRT, KS>(sp, fv, Fv, fs);
     }
     if (owner) {
       s_m[buf][0][sy][sx] = fs[1];
@@ -1373,16 +1400,20 @@ collide_stream_batch_kernel(const BatchCS* __restrict__ tab, const int2* __restr
   constexpr int words = sizeof(KConst<float>) / sizeof(int);
   for (int i = tid; i < words; i += TX * (TY + HALO_WARPS))
     reinterpret_cast<int*>(&s_k)[i] = reinterpret_cast<const int*>(&e.k)[i];
+  if (D == 2 && MRT && tid < kMaxQ * 8) {
+    const int r = tid >> 3, c = tid & 7;
+    reinterpret_cast<float*>(&s_om_rows[r][0])[c] = c < kMaxQ ? e.k.omega[r][c] : 0.0f;
+  }
   __syncthreads();
   const int lb = pb.y;
   const int bx = lb % e.bx, rest = lb / e.bx;
   if constexpr (D == 2) {
     extern __shared__ __align__(128) uint8_t batch_raw[];
     if (e.tma)
-      march2_tma<MRT, SPLIT>(s_k, &e.mf[parity], &e.mF, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
+      march2_tma<MRT, SPLIT, true>(s_k, &e.mf[parity], &e.mF, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
                              e.zchunk, bx, rest, batch_raw, e.mpart, lb);
     else
-      march2_pipe<MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
+      march2_pipe<MRT, SPLIT, true>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,
                               e.zchunk, bx, rest, reinterpret_cast<float*>(batch_raw), e.mpart, lb);
   } else {
     march_body<float, D, MRT, SPLIT>(s_k, e.f[parity], e.F, const_cast<float*>(e.f[parity ^ 1]), e.C, e.flag, e.so,

@@ -48,11 +48,21 @@ sum_final_kernel(const double* __restrict__ partials, int nparts, double* __rest
 
 // The latest step's mass: the collide-stream kernel's warp partials added in a fixed
 // order; with limit > 0, a mass outside [-limit, limit] (or not finite) sets bit 1 of flag.
+// FP32 forms store each warp's partial as a float pair (hi, lo) in the 8-byte slot (pair = 1):
+// its value is hi + lo, formed here in FP64 (exact for such a pair).
 __global__ void __launch_bounds__(kReduceThreads)
-step_mass_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out, double limit,
+step_mass_kernel(const double* __restrict__ partials, int nparts, int pair, double* __restrict__ out, double limit,
                  int* __restrict__ flag) {
   double acc = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += kReduceThreads) acc += partials[i];
+  if (pair) {
+    const float2* p2 = reinterpret_cast<const float2*>(partials);
+    for (int i = threadIdx.x; i < nparts; i += kReduceThreads) {
+      const float2 v = p2[i];
+      acc += static_cast<double>(v.x) + static_cast<double>(v.y);
+    }
+  } else {
+    for (int i = threadIdx.x; i < nparts; i += kReduceThreads) acc += partials[i];
+  }
   acc = block_sum(acc);
   if (threadIdx.x == 0) {
     *out = acc;
@@ -118,7 +128,8 @@ cudaError_t launch_mass(const lbm_s* h, const void* C, cudaStream_t s) {
 }
 
 cudaError_t launch_step_mass(const lbm_s* h, double limit, cudaStream_t s) {
-  step_mass_kernel<<<1, kReduceThreads, 0, s>>>(h->cs_part, h->cs_nparts * kMassSlots, h->dev.scalar, limit, h->dev.flag);
+  step_mass_kernel<<<1, kReduceThreads, 0, s>>>(h->cs_part, h->cs_nparts * kMassSlots, h->elem == 4 ? 1 : 0,
+                                                 h->dev.scalar, limit, h->dev.flag);
   return cudaGetLastError();
 }
 
