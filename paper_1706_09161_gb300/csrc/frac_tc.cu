@@ -156,7 +156,15 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
   const int row = threadIdx.x;                   // accumulator lane = x offset in the tile
   const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
   int r0 = 0, r1 = BN;  // tile rows (output nodes n) this CTA writes
-  // TMEM -> shared tile [BN][128] (lane = x)
+  // KS > 1: this CTA's partial sum over its k-range goes to partial slot `rank` of F
+  // (F is [rank][axis][node]); the consumers add the KS partials in rank order
+  const long long nodes = P.nodes;
+  float* F = P.F + (long long)rank * P.naxes * nodes + (long long)mu * nodes;
+  const int n0 = P.n0, n1 = P.n1;
+  const int lim = (mu == 0) ? n1 : ax.side;  // output rows that exist
+  // TMEM -> shared tile [BN][128] (lane = x), 32 rows at a time; with TMA stores each
+  // 32-row chunk leaves by its own store as soon as it is in shared memory, so the stores
+  // overlap the drain of the next chunk (each chunk has its own 16 KB of the tile)
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
     float v[32], w[32];
@@ -168,40 +176,36 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     }
 #pragma unroll
     for (int j = 0; j < 32; ++j) tile[(c0 + j) * BM + row] = have ? v[j] : 0.0f;
-  }
-  // KS > 1: this CTA's partial sum over its k-range goes to partial slot `rank` of F
-  // (F is [rank][axis][node]); the consumers add the KS partials in rank order
-
-  const long long nodes = P.nodes;
-  float* F = P.F + (long long)rank * P.naxes * nodes + (long long)mu * nodes;
-  const int n0 = P.n0, n1 = P.n1;
-  if (P.tma_store) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    named_sync128();  // warps 0-3 (tf32's extra warps have left)
-    if (threadIdx.x == 0 && have) {
-      int c1, c2;
-      if (mu == 2) {
-        c1 = m_out;
-        c2 = ncol0 + r0;
-      } else {
-        c1 = ncol0 + r0;
-        c2 = m_out;
+    if (P.tma_store) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      named_sync128();  // warps 0-3 (tf32's extra warps have left)
+      if (threadIdx.x == 0 && have && ncol0 + c0 < lim) {
+        int c1, c2;
+        if (mu == 2) {
+          c1 = m_out;
+          c2 = ncol0 + c0;
+        } else {
+          c1 = ncol0 + c0;
+          c2 = m_out;
+        }
+        if (KS == 1)
+          asm volatile(
+              "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                  reinterpret_cast<uint64_t>(&maps.f[mu])),
+              "r"(m_in), "r"(c1), "r"(c2), "r"(smem_u32(tile + c0 * BM))
+              : "memory");
+        else
+          asm volatile(
+              "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                  reinterpret_cast<uint64_t>(&maps.f[mu])),
+              "r"(m_in), "r"(c1), "r"(c2), "r"(rank), "r"(smem_u32(tile + c0 * BM))
+              : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
-      if (KS == 1)
-        asm volatile(
-            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                reinterpret_cast<uint64_t>(&maps.f[mu])),
-            "r"(m_in), "r"(c1), "r"(c2), "r"(smem_u32(tile))
-            : "memory");
-      else
-        asm volatile(
-            "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
-                reinterpret_cast<uint64_t>(&maps.f[mu])),
-            "r"(m_in), "r"(c1), "r"(c2), "r"(rank), "r"(smem_u32(tile))
-            : "memory");
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
+  }
+  if (P.tma_store) {
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   } else {
     // rows of F that are not 16-byte aligned: plain stores, coalesced along x
     named_sync128();  // warps 0-3 (tf32's extra warps have left)
@@ -209,7 +213,6 @@ __device__ __forceinline__ void frac_tc_tile(const TcMaps& maps, const TcParams&
     if (have && x < n0) {
       for (int rr = r0; rr < r1; ++rr) {
         const int n = ncol0 + rr;  // x axis: row y at z = m_out; y/z axes: node along mu
-        const int lim = (mu == 0) ? n1 : ax.side;
         if (n >= lim) break;
         const long long idx = (mu == 2) ? ((long long)n * n1 + m_out) * n0 + x : ((long long)m_out * n1 + n) * n0 + x;
         F[idx] = tile[(rr - r0) * BM + row];
@@ -963,8 +966,8 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
   h->sp.pstride = (ks > 1) ? (long long)h->d * h->sp.nodes : 0;
   if (P.tma_store) {
     for (int mu = 0; mu < h->d; ++mu) {
-      // persistent: 32-row chunks; per tile: the whole tile (one rank's partial when ks > 1)
-      const cuuint32_t rows = p->persist ? 32u : (cuuint32_t)p->bn;
+      // 32-row chunks of an output tile (per tile: of one rank's partial when ks > 1)
+      const cuuint32_t rows = 32u;
       const cuuint64_t fd[4] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2], (cuuint64_t)ks};
       const cuuint64_t fs[3] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4,
                                 (cuuint64_t)h->d * h->sp.nodes * 4};

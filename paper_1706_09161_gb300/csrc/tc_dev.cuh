@@ -547,26 +547,31 @@ __device__ __forceinline__ void op_item(const TcMaps& maps, const TcParams& P, i
     for (int i = (nkb > G::STAGES ? nkb - G::STAGES : 0); i < nkb; ++i)
       mbar_wait(&full[i % G::STAGES], (i / G::STAGES) & 1, P.flag);
     if (have) {
-      int c1, c2;
-      if (tl.mu == 2) {
-        c1 = tl.m_out;
-        c2 = tl.ncol0;
-      } else {
-        c1 = tl.ncol0;
-        c2 = tl.m_out;
+      // the tile in 32-row chunks (the box of the F maps); chunks past the last output row
+      // are not stored
+      const int lim = (tl.mu == 0) ? P.n1 : P.ax[tl.mu].side;
+      for (int c0 = 0; c0 < BN && tl.ncol0 + c0 < lim; c0 += 32) {
+        int c1, c2;
+        if (tl.mu == 2) {
+          c1 = tl.m_out;
+          c2 = tl.ncol0 + c0;
+        } else {
+          c1 = tl.ncol0 + c0;
+          c2 = tl.m_out;
+        }
+        if (KS == 1)
+          asm volatile(
+              "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                  reinterpret_cast<uint64_t>(&maps.f[tl.mu])),
+              "r"(tl.m_in), "r"(c1), "r"(c2), "r"(smem_u32(tile + c0 * BM))
+              : "memory");
+        else
+          asm volatile(
+              "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                  reinterpret_cast<uint64_t>(&maps.f[tl.mu])),
+              "r"(tl.m_in), "r"(c1), "r"(c2), "r"(rank), "r"(smem_u32(tile + c0 * BM))
+              : "memory");
       }
-      if (KS == 1)
-        asm volatile(
-            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                reinterpret_cast<uint64_t>(&maps.f[tl.mu])),
-            "r"(tl.m_in), "r"(c1), "r"(c2), "r"(smem_u32(tile))
-            : "memory");
-      else
-        asm volatile(
-            "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
-                reinterpret_cast<uint64_t>(&maps.f[tl.mu])),
-            "r"(tl.m_in), "r"(c1), "r"(c2), "r"(rank), "r"(smem_u32(tile))
-            : "memory");
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
       asm volatile("fence.proxy.async.global;" ::: "memory");  // F visible past the grid barrier
