@@ -65,7 +65,8 @@ enum {
   LBM_FP32_BF16SPLIT = 2,  /* FP32 collision, fractional operator on tensor cores with
                               bf16 hi+lo operands (3 products), FP32 accumulation */
   LBM_FP32_TF32SPLIT = 3,  /* FP32 collision, fractional operator on tensor cores with
-                              tf32 hi+lo operands (3 products), FP32 accumulation */
+                              tf32 hi+lo operands (3 products; the operator splits C
+                              into hi + lo in shared memory), FP32 accumulation */
   LBM_FP32_BF16SPLIT5 = 4, /* as LBM_FP32_BF16SPLIT with K_mu in three bf16 parts
                               k1+k2+k3 and C in two, five products (k1c1, k1c2, k2c1,
                               k2c2, k3c1): the weights' rounding, which the three-product
@@ -363,7 +364,7 @@ int lbm_get_stream(lbm_t h, void** stream);
 /* Run nsteps time steps (0 <= nsteps <= 4096) with one-kernel launches bracketed by
  * CUDA events on the handle's stream and accumulate the device time of each kernel
  * class:
- *   ms[0] = fractional operator (all axes, with the tf32 transposes),
+ *   ms[0] = fractional operator (all axes),
  *   ms[1] = fused collide/stream/walls/moment.
  * All steps are queued before one synchronisation, so the intervals exclude the host's
  * submission of each launch.  Divide by nsteps for the mean duration per launch.
