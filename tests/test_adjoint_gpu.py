@@ -157,7 +157,7 @@ def test_autograd_function_fits_parameters(L):
     mask[:d] = 1.0
     mask[3 * d:] = 1.0
     th = theta.detach().clone()
-    L0 = float(loss)
+    L0 = float(loss.detach())
     cur = L0
     # one handle for the whole fit (lbm_set_params between evaluations)
     with L.Lattice(pb, C0, "fp64") as lat:
