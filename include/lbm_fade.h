@@ -277,9 +277,10 @@ int lbm_set_mass_limit(lbm_t h, double limit);
  * space with the rates of each node and the operator contracts g_mu(x) C along each axis;
  * the handle re-initialises from its initial concentration (as lbm_reset).  The arrays are
  * copied.  Single-problem handles (LBM_EINVAL for batches) in every precision form.  On the
- * tensor cores the bf16 forms take g(x) as one operand g_mu(x) C per axis (K_mu then without
- * g); the tf32 form keeps g uniform, folded into K_mu (g_field must be NULL: LBM_ENOTSUP
- * otherwise); with BGK the tensor-core forms need a spherical constant D (LBM_ENOTSUP).
+ * tensor cores g(x) enters as one operand g_mu(x) C per axis (K_mu then without g): bf16
+ * parts of it, or for tf32 the FP32 product (split into hi + lo by the operator); a
+ * uniform g stays folded into K_mu; with BGK the tensor-core forms need a spherical
+ * constant D (LBM_ENOTSUP).
  * LBM_EINVAL for a non-finite entry, g <= 0 or a D that breaks the conditions above (the
  * handle is unchanged then).  lbm_grad returns LBM_ENOTSUP on a handle with varying
  * coefficients.  Synchronises. */

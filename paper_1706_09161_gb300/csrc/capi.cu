@@ -1223,9 +1223,11 @@ static int rebuild_fields(lbm_s* h) {
     if ((rc = alloc_bytes(h, &h->fld.coll, E * NC * nodes)) || (rc = alloc_bytes(h, &h->fld.advw, E * d * nodes)))
       return rc;
     // g(x) for the SIMT operator's input G = g C, or for the tensor-core operands of g_mu(x) C
-    // (the tensor-core forms fold a uniform g into K and need neither)
+    // (the tensor-core forms fold a uniform g into K and need neither); G itself for the
+    // SIMT operator and for tf32, whose operands are regrouped from it
+    const bool tf32 = h->prm.precision == LBM_FP32_TF32SPLIT;
     if ((!h->tc || g_field) && (rc = alloc_bytes(h, &h->fld.g, E * d * nodes))) return rc;
-    if (!h->tc && (rc = alloc_bytes(h, &h->fld.G, E * d * nodes))) return rc;
+    if ((!h->tc || (g_field && tf32)) && (rc = alloc_bytes(h, &h->fld.G, E * d * nodes))) return rc;
     const std::pair<const std::vector<double>*, void*> ups[3] = {{&coll, h->fld.coll}, {&advw, h->fld.advw},
                                                                  {&gv, h->fld.g}};
     for (const auto& up : ups) {
@@ -1254,8 +1256,8 @@ static int rebuild_fields(lbm_s* h) {
   return lbm_reset(h);
 }
 
-// the per-node path applies to single problems in every form; the tensor-core forms keep g
-// uniform (folded into K, as without fields) and BGK's h_mu = 1 (a spherical constant D)
+// the per-node path applies to single problems in every form; the tensor-core forms fold a
+// uniform g into K (as without fields) and need BGK's h_mu = 1 (a spherical constant D)
 static int fields_supported(lbm_t h) {
   if (!h || h->is_batch()) return LBM_EINVAL;
   if (h->tc && h->prm.collision == LBM_BGK)
@@ -1300,8 +1302,6 @@ static int ensure_time_table(lbm_s* h) {
 int lbm_set_fields(lbm_t h, const double* D_field, const double* g_field, const double* u_field) {
   int rc = fields_supported(h);
   if (rc) return rc;
-  // g(x) on the tensor cores: an operand g_mu(x) C per axis, bf16 parts only
-  if (g_field && h->tc && h->prm.precision == LBM_FP32_TF32SPLIT) return LBM_ENOTSUP;
   const size_t nodes = (size_t)h->sp.nodes, d = (size_t)h->d;
   // validate on a copy first: the handle stays unchanged when the arrays are rejected
   lbm::FieldState keep;

@@ -1564,7 +1564,7 @@ cudaError_t launch_cs(const lbm_s* h, const void* f_in, void* f_out, void* C_out
                        static_cast<const real*>(h->fld.g),    static_cast<real*>(h->fld.G),
                        static_cast<const real*>(h->fld.src),  static_cast<const real*>(h->fld.cw),
                        h->fld.tf ? h->fld.tf + 2 * tk : nullptr, {}, 0, 0};
-    if (h->tc && h->tc->gvar) {
+    if (h->tc && h->tc->gvar && h->tc->elem == 2) {  // bf16: the parts of g_mu(x) C per axis
       fp.gsplit = 1;
       fp.gldp = h->tc->ldp;
       for (int mu = 0; mu < 3; ++mu)

@@ -932,10 +932,12 @@ int tc_replan(lbm_s* h, int bn, int ks, int persist) {
                                   mu == 1 ? 1u : (cuuint32_t)(BK / 4)};
       if (!encode(&p->maps.c_hi[mu], E, 4, p->ct_hi[mu], tdims, tstr, tbox, false)) return LBM_ECUDA;
     } else {
-      // the split of C, or with g(x) the split of this axis's g_mu(x) C
-      void* c0 = p->gvar ? p->gp[mu][0] : h->dev.Chi;
-      void* c1 = p->gvar ? p->gp[mu][1] : h->dev.Clo;
-      void* c2 = p->gvar ? p->gp[mu][2] : h->dev.Cl2;
+      // the split of C, or with g(x) the bf16 split of this axis's g_mu(x) C (tf32: Chi holds
+      // G_0 then)
+      const bool gparts = p->gvar && E == 2;
+      void* c0 = gparts ? p->gp[mu][0] : h->dev.Chi;
+      void* c1 = gparts ? p->gp[mu][1] : h->dev.Clo;
+      void* c2 = gparts ? p->gp[mu][2] : h->dev.Cl2;
       if (!encode(&p->maps.c_hi[mu], E, 3, c0, cdims, cstr, box)) return LBM_ECUDA;
       if (E == 2 && !encode(&p->maps.c_lo[mu], E, 3, c1, cdims, cstr, box)) return LBM_ECUDA;
       if (p->cparts == 3 && !encode(&p->maps.c_l2[mu], E, 3, c2, cdims, cstr, box)) return LBM_ECUDA;
@@ -1117,10 +1119,20 @@ cudaError_t launch_split_T(const lbm_s* h, cudaStream_t s) {
   const TcPlan* p = h->tc;
   if (!p || p->elem != 4) return cudaSuccess;
   const int n0 = h->sp.n[0], n1 = h->sp.n[1], n2 = h->sp.n[2];
+  const long long nodes = h->sp.nodes;
+  // the operator's input along mu: C, or with g(x) G_mu = g_mu(x) C (the collide-stream
+  // kernel's or launch_scale_fields' FP32 fields); the x operand is then G_0 at pitch ldp
   const float* C = static_cast<const float*>(h->dev.C);
+  const float* G = static_cast<const float*>(h->fld.G);
+  if (p->gvar) {
+    long long b = (nodes + 255) / 256;
+    const long long cap = 16LL * device_sms();
+    if (b > cap) b = cap;
+    split_C_kernel<4><<<(int)b, 256, 0, s>>>(G, h->dev.Chi, nullptr, nullptr, n0, n1, n2, p->ldp);
+  }
   for (int mu = 1; mu < h->d; ++mu)
     split_T_kernel<<<dim3((n0 + 127) / 128, p->tg[mu], mu == 1 ? n2 : n1), 128, 0, s>>>(
-        C, static_cast<float*>(p->ct_hi[mu]), n0, n1, n2, mu, p->tg[mu], p->tpx);
+        p->gvar ? G + mu * nodes : C, static_cast<float*>(p->ct_hi[mu]), n0, n1, n2, mu, p->tg[mu], p->tpx);
   return cudaGetLastError();
 }
 
@@ -1128,12 +1140,16 @@ cudaError_t launch_split_T_step(const lbm_s* h, cudaStream_t s) {
   return cs_writes_T(h) ? cudaSuccess : launch_split_T(h, s);
 }
 
-// bf16 forms with g(x): operand parts of g_mu(x) C for every axis mu
+// g(x) on the tensor cores: the bf16 forms keep operand parts of g_mu(x) C for every axis
+// mu; tf32 takes its operands from the FP32 fields G_mu = g_mu(x) C (launch_split_T)
 int tc_set_gfield(lbm_s* h, bool on) {
   TcPlan* p = h->tc;
   if (!p) return LBM_EINVAL;
-  if (on && p->elem != 2) return LBM_ENOTSUP;
   if (on == p->gvar) return LBM_OK;
+  if (p->elem == 4) {  // tf32: the operands come from the FP32 fields G_mu (launch_split_T)
+    p->gvar = on;
+    return LBM_OK;
+  }
   for (int mu = 0; mu < 3; ++mu)
     for (int k = 0; k < 3; ++k) {
       dev_free(h, p->gp[mu][k]);
@@ -1158,6 +1174,11 @@ cudaError_t launch_split_C(const lbm_s* h, cudaStream_t s) {
   long long b = (h->sp.nodes + 255) / 256;
   const long long cap = 16LL * device_sms();
   if (b > cap) b = cap;
+  if (p->gvar && p->elem == 4) {  // tf32 with g(x): G = g C, then the operands from G
+    cudaError_t e = launch_scale_fields(h, s);
+    if (e != cudaSuccess) return e;
+    return launch_split_T(h, s);
+  }
   if (p->gvar) {
     GParts gp{};
     for (int mu = 0; mu < 3; ++mu)

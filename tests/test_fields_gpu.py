@@ -115,12 +115,10 @@ def test_piecewise_constant_regions(L):
 @pytest.mark.parametrize("form", ["bf16x6split", "bf16x5split", "bf16split", "tf32split"])
 @pytest.mark.parametrize("grid", [(70, 65), (40, 21, 19)])
 def test_fields_tensor_core_forms(L, form, grid):
-    """D(x), u(x) and, in the bf16 forms, g(x) (operands g_mu(x) C per axis, K_mu without g)
-    with the tensor-core operator; tf32 keeps g uniform (folded into K).  Within 6x the same
-    arithmetic re-run on the CPU, the fused mass equal to the sum of C."""
+    """D(x), u(x) and g(x) (operands g_mu(x) C per axis, K_mu without g: bf16 parts, or for
+    tf32 the FP32 product split into hi + lo on chip) with the tensor-core operator.  Within
+    6x the same arithmetic re-run on the CPU, the fused mass equal to the sum of C."""
     pb, C0, fields = _case("mrt", grid, 960 + grid[0] + len(grid))
-    if form == "tf32split":
-        fields = {"D": fields["D"], "u": fields["u"]}
     n = 12
     C_ref = O.run_fields_C(pb, C0, n, fields).numpy()
     with L.Lattice(pb, C0, form) as lat:
@@ -154,20 +152,17 @@ def test_fields_reject_invalid_input(L):
     with L.Lattice(pbm, C0, "fp64") as lat:
         with pytest.raises(L.LBMError):
             lat.set_fields(D=D)
-    with L.Lattice(pbm, C0, "tf32split") as lat:
-        with pytest.raises(L.LBMError) as ei:
-            lat.set_fields(g=f["g"])
-        assert ei.value.code == L.LBM_ENOTSUP
 
 
-def test_g_field_on_and_off_tensor_core(L):
-    """bf16x6: switching g(x) on re-splits K without g and the operands per axis; switching it
-    off restores the constant run bit for bit."""
-    pb, C0, fields = _case("mrt", (70, 65), 977)
-    with L.Lattice(pb, C0, "bf16x6split") as ref:
+@pytest.mark.parametrize("form,grid", [("bf16x6split", (70, 65)), ("tf32split", (70, 65)), ("tf32split", (36, 29, 23))])
+def test_g_field_on_and_off_tensor_core(L, form, grid):
+    """Switching g(x) on re-splits K without g and takes the operands per axis from
+    g_mu(x) C; switching it off restores the constant run bit for bit."""
+    pb, C0, fields = _case("mrt", grid, 977)
+    with L.Lattice(pb, C0, form) as ref:
         ref.step(20)
         C_const = ref.C()
-    with L.Lattice(pb, C0, "bf16x6split") as lat:
+    with L.Lattice(pb, C0, form) as lat:
         lat.set_fields(g=fields["g"])
         lat.step(20)
         C_g = lat.C()
@@ -175,8 +170,8 @@ def test_g_field_on_and_off_tensor_core(L):
         lat.step(20)
         assert np.array_equal(lat.C(), C_const)
     C_ref = O.run_fields_C(pb, C0, 20, {"g": fields["g"]}).numpy()
-    l2, node, _ = arith_bounds.bounds(pb, C0, 20, "bf16x6split", C_ref=C_ref, fields={"g": fields["g"]})
-    arith_bounds.assert_close(C_g, C_ref, l2, node, "g(x) bf16x6")
+    l2, node, _ = arith_bounds.bounds(pb, C0, 20, form, C_ref=C_ref, fields={"g": fields["g"]})
+    arith_bounds.assert_close(C_g, C_ref, l2, node, f"g(x) {form} {grid}")
 
 
 def test_varying_512_workload(L):
