@@ -4,6 +4,7 @@ g(x) inside the integrals, u(x) in the equilibrium (Section 1; Eqs. Fg, MatrixS,
 Feq with x-dependent coefficients).  FP64: 1e-12 relative L2 and node by node; FP32: 6x
 the error of the same FP32 arithmetic re-run on the CPU, never below 1e-5."""
 import dataclasses
+import functools
 
 import numpy as np
 import pytest
@@ -174,12 +175,20 @@ def test_g_field_on_and_off_tensor_core(L, form, grid):
     arith_bounds.assert_close(C_g, C_ref, l2, node, f"g(x) {form} {grid}")
 
 
-def test_varying_512_workload(L):
-    """The 512^2 workload with varying coefficients (bench entry), first 200 steps (FP32)."""
+@functools.lru_cache(maxsize=1)
+def _varying_512_ref(n):
+    pb, C0, _, fields = W.varying_512()
+    return O.run_fields_C(pb, C0, n, fields).numpy()
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x6split", "tf32split"])
+def test_varying_512_workload(L, form):
+    """The 512^2 workload with varying D(x), g(x), u(x) (bench entry), first 200 steps, in the
+    plain FP32 form and in both tensor-core forms that carry g(x) per axis."""
     pb, C0, _, fields = W.varying_512()
     n = 200
-    C_ref = O.run_fields_C(pb, C0, n, fields).numpy()
-    with L.Lattice(pb, C0, "fp32") as lat:
+    C_ref = _varying_512_ref(n)
+    with L.Lattice(pb, C0, form) as lat:
         lat.set_fields(**fields)
         lat.step(n)
-        arith_bounds.assert_close(lat.C(), C_ref, 1e-5, 1e-5, "varying_512 fp32")
+        arith_bounds.assert_close(lat.C(), C_ref, 1e-5, 1e-5, f"varying_512 {form}")
