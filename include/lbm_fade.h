@@ -244,9 +244,9 @@ int lbm_load(lbm_t h, const void* src_host, long long bytes);
 /* Total mass sum_x C(x) of problem `prob`'s current concentration (the moment of
  * Algorithm 1's time step), in FP64, into the host double *mass.  After a step the mass is a by-product
  * of the collide-stream kernel: each warp of its blocks sums the concentrations it wrote
- * (per thread by a compensated FP32 sum, then across the warp in
- * FP64) and stores one FP64 partial; this call adds the partials of the latest step in one
- * small pass (a fixed order: the same result every time).  Right after lbm_create,
+ * (FP32 forms: per thread and across the warp as a compensated two-float sum, stored as
+ * that pair; FP64: in FP64) and stores one partial; this call adds the partials of the
+ * latest step in FP64 in one small pass (a fixed order: the same result every time).  Right after lbm_create,
  * lbm_set_C, lbm_reset, lbm_write_f or lbm_load it reduces C itself (block partials,
  * then one final pass).  Synchronises; returns the problem's latched error as
  * lbm_read_C does. */
