@@ -539,6 +539,55 @@ def traffic_for(workload, kernel, precision):
     return rec.get("bytes_per_launch")
 
 
+# ncu DRAM captures (one kernel, one launch, built-in launch configuration) behind
+# profiles/traffic.json: key -> (CSV name under the capture directory, precision, summary file)
+TRAFFIC_CAPTURES = {
+    "mrt_aniso_512:fractional_operator": ("dram_512_x6_op.csv", "bf16x6split", "profiles/frac_tc_mrt_aniso_512.md"),
+    "mrt_aniso_512:collide_stream": ("dram_512_x6_cs.csv", "bf16x6split", "profiles/collide_stream_mrt_aniso_512.md"),
+    "mrt3d_256:collide_stream": ("dram_3d_tf32_cs.csv", "tf32split", "profiles/dram_mrt3d_256.md"),
+    "mrt3d_256:fractional_operator": ("dram_3d_tf32_op.csv", "tf32split", "profiles/dram_mrt3d_256.md"),
+    "mrt3d_256:collide_stream@bf16x6split": ("dram_3d_x6_cs.csv", "bf16x6split", "profiles/dram_mrt3d_256.md"),
+    "mrt3d_256:fractional_operator@bf16x6split": ("dram_3d_x6_op.csv", "bf16x6split", "profiles/dram_mrt3d_256.md"),
+    "batch64:collide_stream": ("dram_b64_cs.csv", "bf16x6split", "profiles/dram_batch64.md"),
+    "batch64:fractional_operator": ("dram_b64_op.csv", "bf16x6split", "profiles/dram_batch64.md"),
+}
+KERNEL_SOURCES = {
+    "fractional_operator": ["paper_1706_09161_gb300/csrc/frac_tc.cu", "paper_1706_09161_gb300/csrc/tc_dev.cuh",
+                            "paper_1706_09161_gb300/csrc/lbm_internal.h"],
+    "collide_stream": ["paper_1706_09161_gb300/csrc/collide_stream.cu", "paper_1706_09161_gb300/csrc/tc_dev.cuh",
+                       "paper_1706_09161_gb300/csrc/lbm_internal.h"],
+}
+
+
+def record_traffic(capture_dir, path=None):
+    """Write profiles/traffic.json from the ncu CSVs of TRAFFIC_CAPTURES in capture_dir
+    (dram__bytes_read.sum + dram__bytes_write.sum and gpu__time_duration.sum of the one
+    captured launch), stamped with the current sources' hash; keys without a CSV keep
+    their entry."""
+    import csv
+    path = path or os.path.join(ROOT, "profiles", "traffic.json")
+    tab = json.load(open(path)) if os.path.exists(path) else {}
+    for key, (name, precision, summary) in TRAFFIC_CAPTURES.items():
+        f = os.path.join(capture_dir, name)
+        if not os.path.exists(f):
+            continue
+        rows = [r for r in csv.reader(open(f)) if len(r) > 10]
+        hdr = rows[0]
+        mi, vi = hdr.index("Metric Name"), hdr.index("Metric Value")
+        m = {r[mi]: float(r[vi].replace(",", "")) for r in rows[1:]}
+        kernel = key.split(":")[1].split("@")[0]
+        tab[key] = {"bytes_per_launch": int(m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"]),
+                    "sources": KERNEL_SOURCES[kernel], "source_sha": source_sha(KERNEL_SOURCES[kernel]),
+                    "from": f"{summary} (dram__bytes_read.sum + dram__bytes_write.sum, one launch, full size) "
+                            "(built-in launch configuration)",
+                    "precision": precision, "duration_ns": m["gpu__time_duration.sum"]}
+        print(f"{key}: {tab[key]['bytes_per_launch']} B, {m['gpu__time_duration.sum']:.0f} ns")
+    with open(path, "w") as fh:
+        json.dump(tab, fh, indent=1)
+        fh.write("\n")
+    return 0
+
+
 def source_sha(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -711,8 +760,12 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch configuration")
     ap.add_argument("--lattice-steps", type=int, default=None,
                     help="override the workload's lattice steps per bench step (profiling runs only)")
+    ap.add_argument("--record-traffic", metavar="DIR", default=None,
+                    help="write profiles/traffic.json from the ncu DRAM CSVs in DIR and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.record_traffic:
+        return record_traffic(args.record_traffic)
 
     if args.impl == "reference":
         return run_reference(args)
